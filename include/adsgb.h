@@ -1,0 +1,243 @@
+/*
+ * adsgb.h -- C ABI of the GB300 (sm_103a) IGA-ADS + CRVPINN hybrid time step.
+ *
+ * The library computes, on one GPU, the hybrid CO2-sequestration time step:
+ *   - the IGA-ADS explicit saturation update: Gauss-quadrature assembly of the
+ *     right-hand side of the L2 projection (Sec. 4, Eqs. 10b-13, i.e. the weak
+ *     form Eq. 10a of Eq. 6) followed by the Kronecker-factored mass solve
+ *     M = Mx (x) My (x) Mz (Eq. 14) as banded LDL^T line sweeps along x, y, z;
+ *   - the CRVPINN pressure update: MLP over the collocation grid (Eq. 21),
+ *     the discrete residual (Eqs. 23b-25), the robust loss RES^T G^-1 RES
+ *     (Eqs. 26-28), its hand-written gradient and Adam (Sec. 8.3);
+ *   - the hybrid loop of Sec. 6 (projection of the network pressure into the
+ *     B-spline space, 10 saturation steps, 100 Adam iterations).
+ *
+ * Conventions (every entry point):
+ *   - Every call returns an ads_status; no exception crosses the ABI.
+ *   - A context owns all its device memory and enqueues all work on the
+ *     stream given at ads_init (NULL = the legacy default stream).  Calls
+ *     return after enqueueing, except those that return host data (ads_get,
+ *     a non-NULL loss/stat output), which wait for the stream with a deadline
+ *     (ADS_ERR_TIMEOUT if it passes).
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Device
+ *     pointers handed out by ads_device_ptr are borrowed and valid until
+ *     ads_destroy.
+ *   - A CUDA error makes the context's status sticky (ADS_ERR_CUDA); later
+ *     calls on it return that status.  ads_last_error gives the message.
+ *   - One context is used by one host thread at a time.
+ *   - Array layout: row-major with x fastest: [y][x] in 2D, [z][y][x] in 3D.
+ *     B-spline coefficient arrays have (n+2)^dim entries (quadratic, C1);
+ *     nodal arrays (n+1)^dim; interior collocation arrays (n-1)^dim.
+ *   - Non-dimensional parameters: the viscosity and density ratios of the
+ *     paper's Sec. 8.1 table; gravity acts along -vertical (y in 2D, z in 3D).
+ */
+#ifndef ADSGB_H
+#define ADSGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ads_ctx ads_ctx;
+
+typedef enum {
+  ADS_OK = 0,
+  ADS_ERR_INVALID_ARG = 1,  /* a pointer, size or parameter is out of range */
+  ADS_ERR_OOM = 2,          /* device allocation failed                      */
+  ADS_ERR_CUDA = 3,         /* a CUDA call failed (sticky)                   */
+  ADS_ERR_NONFINITE = 4,    /* a loss, step size or field became non-finite  */
+  ADS_ERR_TIMEOUT = 5,      /* waiting for the stream exceeded the deadline  */
+  ADS_ERR_STATE = 6,        /* call not valid in this state (e.g. no network)*/
+  ADS_ERR_UNSUPPORTED = 7   /* valid request this build does not implement   */
+} ads_status;
+
+/* arithmetic types */
+typedef enum { ADS_F64 = 0, ADS_F32 = 1, ADS_BF16 = 2 } ads_dtype;
+
+#define ADS_MAX_SOURCES 8
+typedef struct {
+  double center[3];  /* (x, y, z) in [0,1]^dim                                */
+  double sigma;      /* width of the normalised Gaussian                      */
+  double rate;       /* Q >= 0                                                */
+  int kind;          /* 0: gas injector q_g += Q G; 1: producer, total Q G
+                        removed, gas share = fractional flow f_g(S)           */
+} ads_source;
+
+typedef struct {
+  int dim;           /* 2 (or 3 where supported)                              */
+  int n;             /* elements per axis (>= 2); collocation intervals N = n  */
+  double phi;        /* porosity when no porosity map is given (> 0)          */
+  double mu_w, mu_g, rho_w, rho_g;
+  double grav;       /* |g| >= 0                                              */
+  double grav_sign;  /* +1: gravity term derived from Eq. 2; -1: as printed in
+                        Eq. 9 (saturation equation only)                      */
+  double kz_ratio;   /* 3D vertical permeability ratio (1 = isotropic)        */
+  int n_src;         /* 0..ADS_MAX_SOURCES                                    */
+  ads_source src[ADS_MAX_SOURCES];
+  int ads_dtype;     /* ADS_F64 or ADS_F32: saturation-step arithmetic        */
+} ads_params;
+
+typedef struct {
+  int width;         /* hidden width: 64 or 128                               */
+  int hidden_layers; /* 4                                                     */
+  int dtype;         /* ADS_F64 or ADS_F32 (network, residual, Gram, Adam)    */
+} crvpinn_params;
+
+typedef struct {
+  int n_sub;         /* saturation steps per hybrid step (Sec. 6 uses 10)     */
+  double dt;         /* fixed step (dt_policy 0) or upper bound (policy 1)    */
+  int dt_policy;     /* 0 fixed, 1 CFL: min(cfl*h/v_max, src_frac/s_max, dt)  */
+  double cfl;        /* e.g. 0.1                                              */
+  double src_frac;   /* e.g. 0.05                                             */
+  int adam_iters;    /* Adam iterations per pressure update (100)             */
+  double lr;         /* Adam learning rate                                    */
+} hybrid_params;
+
+typedef struct {
+  double dt_used;    /* step size of the last saturation steps                */
+  double loss_last;  /* robust loss at the last Adam iteration                */
+  double mass_err;   /* sum over the last saturation steps of
+                        int S_{k+1} - int S_k - dt int q_g/phi                */
+  double mass_total; /* int S after the step                                  */
+} hybrid_stats;
+
+/* fields for ads_get / ads_device_ptr */
+typedef enum {
+  ADS_FIELD_S = 0,        /* saturation coefficients (n+2)^dim            */
+  ADS_FIELD_P = 1,        /* pressure coefficients   (n+2)^dim            */
+  ADS_FIELD_K = 2,        /* nodal permeability      (n+1)^dim            */
+  ADS_FIELD_ALPHA = 3,    /* nodal alpha = lambda K  (n+1)^dim (Eq. 23b)  */
+  ADS_FIELD_F = 4,        /* interior RHS            (n-1)^dim (Eq. 23b)  */
+  ADS_FIELD_U = 5,        /* network at interior nodes (n-1)^dim          */
+  ADS_FIELD_RES = 6,      /* residual RES            (n-1)^dim (Eq. 25)   */
+  ADS_FIELD_Z = 7,        /* G^-1 RES                (n-1)^dim (Eq. 28)   */
+  ADS_FIELD_GU = 8,       /* dLOSS/du                (n-1)^dim            */
+  ADS_FIELD_THETA = 9,    /* network parameters      nparams              */
+  ADS_FIELD_GRAD = 10,    /* dLOSS/dtheta            nparams              */
+  ADS_FIELD_LOSS = 11,    /* loss of the last Adam iteration (1 value)    */
+  ADS_FIELD_DT = 12,      /* current step size (1 value)                  */
+  ADS_FIELD_MASS = 13,    /* [int S, accumulated mass error, source int.] */
+  ADS_FIELD_LOSS_LOG = 14 /* ring of the last 4096 losses                 */
+} ads_field;
+
+/* ---- lifetime ------------------------------------------------------------
+ * ads_init: create a context on the current CUDA device.
+ *   K_nodal   (n+1)^dim permeability, > 0, finite (required)
+ *   phi_nodal (n+1)^dim porosity > 0 or NULL (constant params->phi)
+ *   S0        (n+2)^dim initial saturation coefficients or NULL (zero)
+ *   crv       network description, or NULL for a saturation-only context
+ *   stream    cudaStream_t to enqueue on (NULL: legacy default stream)
+ * Builds the basis tables, the 1D mass matrices and their LDL^T factors
+ * (Eq. 14, factored once in FP64), the sine transform and shifted
+ * tridiagonal factors of the Gram matrix (Eq. 28, factored once in FP64).
+ * Errors: ADS_ERR_INVALID_ARG (bad sizes/values, NULL K or out),
+ * ADS_ERR_NONFINITE (non-finite K/phi/S0), ADS_ERR_OOM, ADS_ERR_CUDA. */
+ads_status ads_init(const ads_params* params, const crvpinn_params* crv,
+                    const double* K_nodal, const double* phi_nodal,
+                    const double* S0, void* stream, ads_ctx** out);
+void ads_destroy(ads_ctx* ctx);
+
+/* Bytes of device memory ads_init would allocate (for admission control). */
+size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv);
+
+/* ---- saturation (Secs. 2-4) -----------------------------------------------
+ * ads_saturation_step: n_sub explicit steps S_{k+1} = M^-1 R(S_k, p) of Eq. 6
+ * in the weak form Eq. 10a/10b with the current pressure coefficients and a
+ * fixed step dt > 0.  Each step is one fused quadrature + x-sweep kernel and
+ * one y-sweep kernel (which also accumulates the mass balance).  dt <= 0
+ * uses the step size currently held on the device (e.g. from ads_cfl_dt).
+ * Errors: ADS_ERR_INVALID_ARG (n_sub < 0). */
+ads_status ads_saturation_step(ads_ctx* ctx, double dt, int n_sub);
+
+/* ads_cfl_dt: device step size min(cfl*h/v_max, src_frac/s_max, dt_cap),
+ * v_max = max over Gauss points of |K (grad p + s rho_g g e)|/(mu_g phi),
+ * s_max = max q_inj/phi (the paper fixes tau; this is the CFL reading).  The
+ * result stays on the device for the next ads_saturation_step(dt <= 0);
+ * dt_out (nullable) receives it after a synchronisation. */
+ads_status ads_cfl_dt(ads_ctx* ctx, double cfl, double src_frac, double dt_cap,
+                      double* dt_out);
+
+/* Replace the pressure / saturation coefficients ((n+2)^dim host doubles). */
+ads_status ads_set_pressure_coeffs(ads_ctx* ctx, const double* host_p);
+ads_status ads_set_saturation(ads_ctx* ctx, const double* host_s);
+
+/* ---- CRVPINN pressure (Sec. 5) ---------------------------------------------
+ * crvpinn_set_theta: load network parameters (nparams host doubles, layout
+ * [W_1 (out x in, row-major), b_1, ..., W_5, b_5]) and reset Adam (m=v=0,t=0).
+ * crvpinn_num_params: nparams for this context's network. */
+ads_status crvpinn_set_theta(ads_ctx* ctx, const double* theta);
+ads_status crvpinn_num_params(const ads_ctx* ctx, int* nparams);
+
+/* crvpinn_update_coefficients: alpha = lambda(S) K and RHS (Eq. 23b) at the
+ * collocation nodes from the current saturation coefficients. */
+ads_status crvpinn_update_coefficients(ads_ctx* ctx);
+
+/* crvpinn_loss_grad: one evaluation of the robust loss (Eq. 27) and its
+ * gradient dLOSS/dtheta at the current parameters, without an update:
+ * MLP forward, residual (Eq. 25), G^-1 RES through the sine transform along x
+ * and shifted tridiagonal line solves along y (Eq. 28), loss, adjoint
+ * 2 A G^-1 RES, MLP backward.  loss_out (nullable) is filled after a
+ * synchronisation; the gradient is kept on the device (ADS_FIELD_GRAD). */
+ads_status crvpinn_loss_grad(ads_ctx* ctx, double* loss_out);
+
+/* crvpinn_pretrain: coefficients from the current saturation, reset Adam,
+ * then `iters` Adam iterations at learning rate lr (Sec. 6 step 2).
+ * crvpinn_pressure_update: same without the Adam reset (Sec. 6 step 7; Adam
+ * moments persist across updates).  loss_out (nullable): loss of the last
+ * iteration, after a synchronisation. */
+ads_status crvpinn_pretrain(ads_ctx* ctx, int iters, double lr, double* loss_out);
+ads_status crvpinn_pressure_update(ads_ctx* ctx, int iters, double lr, double* loss_out);
+
+/* ads_project_pressure: network at the interior nodes (boundary 0), L2
+ * projection of its piecewise-(bi)linear interpolant into the B-spline space
+ * (Sec. 6 step 4) -> pressure coefficients. */
+ads_status ads_project_pressure(ads_ctx* ctx);
+
+/* ---- hybrid step (Sec. 6) ---------------------------------------------------
+ * hybrid_step: project the network pressure; step size (fixed or CFL); n_sub
+ * saturation steps; coefficients from the new saturation; adam_iters Adam
+ * iterations.  The whole step is replayed from a CUDA graph.  stats (nullable)
+ * is filled after a synchronisation; ADS_ERR_NONFINITE if the loss or dt is
+ * not finite. */
+ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stats);
+
+/* hybrid_step_batch: hybrid_step for n independent contexts sharing the
+ * same stream; the contexts' work is enqueued back to back on that stream
+ * so that it overlaps on the device.  stats: NULL or n entries. */
+ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
+                             hybrid_stats* stats);
+
+/* ---- data access -------------------------------------------------------------
+ * ads_get: copy a field to host doubles (count = number of values expected
+ * for the field; ADS_ERR_INVALID_ARG if it differs).  Waits for the stream.
+ * ads_device_ptr: borrowed device pointer, its element count and dtype. */
+ads_status ads_get(ads_ctx* ctx, int field, double* host_dst, size_t count);
+ads_status ads_field_count(const ads_ctx* ctx, int field, size_t* count);
+ads_status ads_device_ptr(ads_ctx* ctx, int field, void** dptr, size_t* count, int* dtype);
+ads_status ads_sync(ads_ctx* ctx, double timeout_s);
+
+/* ---- diagnostics (no counterpart in the paper) ------------------------------
+ * ads_kernel_launches: number of library kernels enqueued on this context so
+ * far (a graph replay counts the kernels it contains).
+ * ads_profile_train: run `iters` Adam iterations without a graph, each kernel
+ * bracketed by CUDA events on the context's stream; ms_out[10] receives the
+ * average duration of: network forward, residual, sine transform, tridiagonal
+ * sweeps, inverse transform, loss partials, loss finalise, adjoint stencil,
+ * network backward, gradient sum + Adam.  Updates the parameters like
+ * crvpinn_pressure_update at the learning rate last set.
+ * ads_profile_saturation: `steps` saturation steps (current dt) likewise;
+ * ms_out[3]: quadrature + x sweep, y sweep, mass bookkeeping. */
+ads_status ads_kernel_launches(const ads_ctx* ctx, unsigned long long* count);
+ads_status ads_profile_train(ads_ctx* ctx, int iters, double* ms_out);
+ads_status ads_profile_saturation(ads_ctx* ctx, int steps, double* ms_out);
+
+const char* ads_last_error(const ads_ctx* ctx);
+const char* ads_status_str(ads_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADSGB_H */

@@ -1,0 +1,114 @@
+"""ctypes declarations of the libadsgb C ABI (include/adsgb.h).
+
+Marshalling only: every computation happens in the CUDA library.  Loading
+fails loudly if the library has not been built or cannot be loaded; there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadsgb.so")
+
+ADS_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+                4: "non-finite value", 5: "timeout", 6: "invalid state", 7: "unsupported"}
+ADS_F64, ADS_F32, ADS_BF16 = 0, 1, 2
+MAX_SOURCES = 8
+
+FIELD = dict(S=0, P=1, K=2, ALPHA=3, F=4, U=5, RES=6, Z=7, GU=8, THETA=9, GRAD=10, LOSS=11,
+             DT=12, MASS=13, LOSS_LOG=14)
+
+
+class ads_source(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("sigma", C.c_double), ("rate", C.c_double),
+                ("kind", C.c_int)]
+
+
+class ads_params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int), ("phi", C.c_double), ("mu_w", C.c_double),
+                ("mu_g", C.c_double), ("rho_w", C.c_double), ("rho_g", C.c_double),
+                ("grav", C.c_double), ("grav_sign", C.c_double), ("kz_ratio", C.c_double),
+                ("n_src", C.c_int), ("src", ads_source * MAX_SOURCES), ("ads_dtype", C.c_int)]
+
+
+class crvpinn_params(C.Structure):
+    _fields_ = [("width", C.c_int), ("hidden_layers", C.c_int), ("dtype", C.c_int)]
+
+
+class hybrid_params(C.Structure):
+    _fields_ = [("n_sub", C.c_int), ("dt", C.c_double), ("dt_policy", C.c_int),
+                ("cfl", C.c_double), ("src_frac", C.c_double), ("adam_iters", C.c_int),
+                ("lr", C.c_double)]
+
+
+class hybrid_stats(C.Structure):
+    _fields_ = [("dt_used", C.c_double), ("loss_last", C.c_double), ("mass_err", C.c_double),
+                ("mass_total", C.c_double)]
+
+
+# every exported symbol with its signature (restype, argtypes)
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+SIGNATURES = {
+    "ads_init": (C.c_int, [C.POINTER(ads_params), C.POINTER(crvpinn_params), _D, _D, _D, _P,
+                           C.POINTER(_P)]),
+    "ads_destroy": (None, [_P]),
+    "ads_hbm_estimate": (C.c_size_t, [C.POINTER(ads_params), C.POINTER(crvpinn_params)]),
+    "ads_saturation_step": (C.c_int, [_P, C.c_double, C.c_int]),
+    "ads_cfl_dt": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _D]),
+    "ads_set_pressure_coeffs": (C.c_int, [_P, _D]),
+    "ads_set_saturation": (C.c_int, [_P, _D]),
+    "crvpinn_set_theta": (C.c_int, [_P, _D]),
+    "crvpinn_num_params": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "crvpinn_update_coefficients": (C.c_int, [_P]),
+    "crvpinn_loss_grad": (C.c_int, [_P, _D]),
+    "crvpinn_pretrain": (C.c_int, [_P, C.c_int, C.c_double, _D]),
+    "crvpinn_pressure_update": (C.c_int, [_P, C.c_int, C.c_double, _D]),
+    "ads_project_pressure": (C.c_int, [_P]),
+    "hybrid_step": (C.c_int, [_P, C.POINTER(hybrid_params), C.POINTER(hybrid_stats)]),
+    "hybrid_step_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(hybrid_params),
+                                    C.POINTER(hybrid_stats)]),
+    "ads_get": (C.c_int, [_P, C.c_int, _D, C.c_size_t]),
+    "ads_field_count": (C.c_int, [_P, C.c_int, C.POINTER(C.c_size_t)]),
+    "ads_device_ptr": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_size_t),
+                                 C.POINTER(C.c_int)]),
+    "ads_sync": (C.c_int, [_P, C.c_double]),
+    "ads_kernel_launches": (C.c_int, [_P, C.POINTER(C.c_ulonglong)]),
+    "ads_profile_train": (C.c_int, [_P, C.c_int, _D]),
+    "ads_profile_saturation": (C.c_int, [_P, C.c_int, _D]),
+    "ads_last_error": (C.c_char_p, [_P]),
+    "ads_status_str": (C.c_char_p, [C.c_int]),
+}
+
+TRAIN_KERNELS = ["mlp_fwd", "residual", "dst_gemm", "tridiag", "idst_gemm", "loss_partial",
+                 "loss_finalize", "adjoint", "mlp_bwd", "grad_adam"]
+SAT_KERNELS = ["quad_xsolve", "ysolve", "mass_finalize"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libadsgb.so (raises if it is missing: build it with build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libadsgb.so not found at {path}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class AdsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}"
+                         + (f" ({detail})" if detail else ""))

@@ -1,0 +1,599 @@
+// IGA-ADS explicit saturation step on the GPU (Secs. 2-4 of the paper).
+//
+//  * one-off tables: B-spline values/derivatives at the Gauss points of every
+//    element (Cox-de Boor, degree 2, open uniform knots), the 1D mass matrix
+//    int B_i B_k (Eq. 14) and its LDL^T factors, per-axis Gaussian source
+//    factors -- all in FP64;
+//  * the fused strip kernel: Gauss quadrature of the right-hand side of the
+//    L2 projection (Eq. 10b, weak form Eq. 10a) for a strip of element rows,
+//    accumulated in shared memory, then the x-direction banded solve of the
+//    strip's rows in shared memory (M^-1 = Mx^-1 (x) My^-1, Eq. 14);
+//  * the y-direction sweep: one thread per column, coalesced row access,
+//    adding the rows the strip above spilled, and accumulating int S.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace adsgb {
+
+// ---------------------------------------------------------------------------
+// one-off tables (FP64)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double knot(int i, int n) {
+  // open uniform knot vector of degree 2: 0,0,0,1/n,...,(n-1)/n,1,1,1
+  if (i <= 2) return 0.0;
+  if (i >= n + 2) return 1.0;
+  return double(i - 2) / double(n);
+}
+
+// Nonzero basis functions of degree p (<= 2) at x in knot span s (the
+// triangular Cox-de Boor scheme); N[0..p] = B_{s-p..s}.
+__device__ void nonzero_basis(int n, int s, double x, int p, double* N) {
+  double left[3], right[3];
+  N[0] = 1.0;
+  for (int j = 1; j <= p; ++j) {
+    left[j] = x - knot(s + 1 - j, n);
+    right[j] = knot(s + j, n) - x;
+    double saved = 0.0;
+    for (int r = 0; r < j; ++r) {
+      double tmp = N[r] / (right[r + 1] + left[j - r]);
+      N[r] = saved + right[r + 1] * tmp;
+      saved = left[j - r] * tmp;
+    }
+    N[j] = saved;
+  }
+}
+
+__global__ void k_axis_tables(int n, double* B, double* dB) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * 3) return;
+  int e = t / 3, q = t % 3;
+  double h = 1.0 / n;
+  double x = (e + gauss_x(q)) * h;
+  int s = e + 2;
+  double N2[3], N1[3];
+  nonzero_basis(n, s, x, 2, N2);
+  nonzero_basis(n, s, x, 1, N1);
+  double c0 = 2.0 / (knot(s + 1, n) - knot(s - 1, n));
+  double c1 = 2.0 / (knot(s + 2, n) - knot(s, n));
+  double d[3] = {-c0 * N1[0], c0 * N1[0] - c1 * N1[1], c1 * N1[1]};
+  for (int a = 0; a < 3; ++a) {
+    B[(e * 3 + a) * 3 + q] = N2[a];
+    dB[(e * 3 + a) * 3 + q] = d[a];
+  }
+}
+
+__global__ void k_source_tables(int n, int n_src, const double* centers, const double* sigmas,
+                                double* gsrc, double* gnode) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double h = 1.0 / n;
+  const double two_pi = 6.283185307179586477;
+  int total_g = 3 * kMaxSrc * n * 3;
+  if (t < total_g) {
+    int q = t % 3, e = (t / 3) % n, s = (t / (3 * n)) % kMaxSrc, c = t / (3 * n * kMaxSrc);
+    double v = 0.0;
+    if (s < n_src) {
+      double x = (e + gauss_x(q)) * h, cen = centers[s * 3 + c], sg = sigmas[s];
+      v = exp(-(x - cen) * (x - cen) / (2.0 * sg * sg)) / sqrt(two_pi * sg * sg);
+    }
+    gsrc[t] = v;
+  }
+  int total_n = 3 * kMaxSrc * (n + 1);
+  if (t < total_n) {
+    int i = t % (n + 1), s = (t / (n + 1)) % kMaxSrc, c = t / ((n + 1) * kMaxSrc);
+    double v = 0.0;
+    if (s < n_src) {
+      double x = i * h, cen = centers[s * 3 + c], sg = sigmas[s];
+      v = exp(-(x - cen) * (x - cen) / (2.0 * sg * sg)) / sqrt(two_pi * sg * sg);
+    }
+    gnode[t] = v;
+  }
+}
+
+// 1D mass matrix by the same quadrature, then LDL^T of the symmetric
+// pentadiagonal matrix (no pivoting: the matrix is SPD).  One thread: O(n).
+__global__ void k_mass_ldlt(int n, const double* B, double* m0, double* m1, double* m2,
+                            double* l1, double* l2, double* dinv, double* Iw) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int nb = n + 2;
+  double h = 1.0 / n;
+  for (int i = 0; i < nb; ++i) { m0[i] = m1[i] = m2[i] = 0.0; Iw[i] = 0.0; }
+  for (int e = 0; e < n; ++e)
+    for (int q = 0; q < 3; ++q) {
+      double w = gauss_w(q) * h;
+      for (int a = 0; a < 3; ++a) {
+        double ba = B[(e * 3 + a) * 3 + q];
+        Iw[e + a] += w * ba;
+        for (int b = 0; b <= a; ++b) {
+          double v = w * ba * B[(e * 3 + b) * 3 + q];
+          int d = a - b;
+          if (d == 0) m0[e + a] += v;
+          else if (d == 1) m1[e + a] += v;
+          else m2[e + a] += v;
+        }
+      }
+    }
+  double D1 = 0.0, D2 = 0.0, a1 = 0.0;  // D_{l-1}, D_{l-2}, a_{l-1}
+  for (int l = 0; l < nb + 2; ++l) { l1[l] = 0.0; l2[l] = 0.0; }
+  for (int l = 0; l < nb; ++l) {
+    double bl = (l >= 2) ? m2[l] / D2 : 0.0;
+    double al = (l >= 1) ? (m1[l] - bl * a1 * D2) / D1 : 0.0;
+    double Dl = m0[l] - al * al * D1 - bl * bl * D2;
+    l1[l] = al;
+    l2[l] = bl;
+    dinv[l] = 1.0 / Dl;
+    D2 = D1;
+    D1 = Dl;
+    a1 = al;
+  }
+}
+
+cudaError_t launch_axis_init(int n, const double* centers, const double* sigmas, int n_src,
+                             double* B, double* dB, double* l1, double* l2, double* dinv,
+                             double* Iw, double* gsrc, double* gnode, double* tmp, cudaStream_t st) {
+  k_axis_tables<<<(n * 3 + 127) / 128, 128, 0, st>>>(n, B, dB);
+  int tot = 3 * kMaxSrc * n * 3;
+  if (3 * kMaxSrc * (n + 1) > tot) tot = 3 * kMaxSrc * (n + 1);
+  k_source_tables<<<(tot + 255) / 256, 256, 0, st>>>(n, n_src, centers, sigmas, gsrc, gnode);
+  // tmp: 3 x (n+4) doubles for the three diagonals of the mass matrix
+  k_mass_ldlt<<<1, 1, 0, st>>>(n, B, tmp, tmp + (n + 4), tmp + 2 * (n + 4), l1, l2, dinv, Iw);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_convert(const double* s, T* d, size_t c) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < c) d[i] = (T)s[i];
+}
+template <typename T>
+__global__ void k_to_double(const T* s, double* d, size_t c) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < c) d[i] = (double)s[i];
+}
+template <typename T>
+cudaError_t launch_convert(const double* src, T* dst, size_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  k_convert<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  k_to_double<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double>(const double*, double*, size_t, cudaStream_t);
+template cudaError_t launch_convert<float>(const double*, float*, size_t, cudaStream_t);
+template cudaError_t launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
+template cudaError_t launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// element quadrature (2D)
+// ---------------------------------------------------------------------------
+// Computes the 3x3 local contributions loc[b][a] of element (ex, ey) to the
+// right-hand side entries (ey+b, ex+a), and adds tau int q_g/phi over the
+// element to `src`.  Fields at the Gauss points are sum-factorised: a
+// contraction along x first, then along y; the test functions are applied in
+// the reverse order.
+template <typename T, int MODE>
+__device__ __forceinline__ void element_rhs_2d(const QuadArgs<T>& a, int ex, int ey, T loc[3][3],
+                                               double& src) {
+  const int nb = a.nb, n1 = a.n + 1;
+  const T* Bx = a.ax.B + ex * 9;
+  const T* dBx = a.ax.dB + ex * 9;
+  const T* By = a.ax.B + ey * 9;
+  const T* dBy = a.ax.dB + ey * 9;
+  T bx[3][3], dbx[3][3], by[3][3], dby[3][3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    bx[i / 3][i % 3] = __ldg(Bx + i);
+    dbx[i / 3][i % 3] = __ldg(dBx + i);
+    by[i / 3][i % 3] = __ldg(By + i);
+    dby[i / 3][i % 3] = __ldg(dBy + i);
+  }
+  T c0[3][3], cx[3][3], cy[3][3];  // [qy][qx]
+  const T h2 = a.h * a.h;
+  if (MODE == 0) {
+    T Sx[3][3], Px[3][3], Pdx[3][3];  // [b][qx]
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T* srow = a.S + (size_t)(ey + b) * nb + ex;
+      const T* prow = a.P + (size_t)(ey + b) * nb + ex;
+      T s0 = __ldg(srow), s1 = __ldg(srow + 1), s2 = __ldg(srow + 2);
+      T p0 = __ldg(prow), p1 = __ldg(prow + 1), p2 = __ldg(prow + 2);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        Sx[b][q] = s0 * bx[0][q] + s1 * bx[1][q] + s2 * bx[2][q];
+        Px[b][q] = p0 * bx[0][q] + p1 * bx[1][q] + p2 * bx[2][q];
+        Pdx[b][q] = p0 * dbx[0][q] + p1 * dbx[1][q] + p2 * dbx[2][q];
+      }
+    }
+    const T* Kr = a.K + (size_t)ey * n1 + ex;
+    T k00 = __ldg(Kr), k01 = __ldg(Kr + 1), k10 = __ldg(Kr + n1), k11 = __ldg(Kr + n1 + 1);
+    T f00 = a.phi_c, f01 = a.phi_c, f10 = a.phi_c, f11 = a.phi_c;
+    if (a.phi) {
+      const T* Fr = a.phi + (size_t)ey * n1 + ex;
+      f00 = __ldg(Fr); f01 = __ldg(Fr + 1); f10 = __ldg(Fr + n1); f11 = __ldg(Fr + n1 + 1);
+    }
+    const T dt = (T)(*a.dt);
+    T gx[kMaxSrc][3], gy[kMaxSrc][3];
+    for (int s = 0; s < a.n_src; ++s)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gx[s][q] = __ldg(a.ax.gsrc + ((size_t)(0 * kMaxSrc + s) * a.n + ex) * 3 + q);
+        gy[s][q] = __ldg(a.ax.gsrc + ((size_t)(1 * kMaxSrc + s) * a.n + ey) * 3 + q);
+      }
+#pragma unroll
+    for (int qy = 0; qy < 3; ++qy) {
+      const T eta = (T)gauss_x(qy);
+#pragma unroll
+      for (int qx = 0; qx < 3; ++qx) {
+        const T xi = (T)gauss_x(qx);
+        T Sv = by[0][qy] * Sx[0][qx] + by[1][qy] * Sx[1][qx] + by[2][qy] * Sx[2][qx];
+        T dpx = by[0][qy] * Pdx[0][qx] + by[1][qy] * Pdx[1][qx] + by[2][qy] * Pdx[2][qx];
+        T dpy = dby[0][qy] * Px[0][qx] + dby[1][qy] * Px[1][qx] + dby[2][qy] * Px[2][qx];
+        T Kq = (T(1) - eta) * ((T(1) - xi) * k00 + xi * k01) + eta * ((T(1) - xi) * k10 + xi * k11);
+        T phq = (T(1) - eta) * ((T(1) - xi) * f00 + xi * f01) + eta * ((T(1) - xi) * f10 + xi * f11);
+        T St = clamp01(Sv);
+        T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
+        T qi = T(0), qp = T(0);
+        for (int s = 0; s < a.n_src; ++s) {
+          T g = a.rate[s] * gx[s][qx] * gy[s][qy];
+          if (a.kind[s] == 0) qi += g; else qp += g;
+        }
+        T qg = qi - lg / (lg + lw) * qp;
+        T w = (T)(gauss_w(qx) * gauss_w(qy)) * h2;
+        T dtphi = dt / phq;
+        c0[qy][qx] = w * (Sv + dtphi * qg);
+        T cf = -w * dtphi * lg * Kq;
+        cx[qy][qx] = cf * dpx;
+        cy[qy][qx] = cf * (dpy + a.grav_term);
+        src += (double)(w * dtphi * qg);
+      }
+    }
+  } else {
+    const T* Ur = a.nodal + (size_t)ey * n1 + ex;
+    T u00 = __ldg(Ur), u01 = __ldg(Ur + 1), u10 = __ldg(Ur + n1), u11 = __ldg(Ur + n1 + 1);
+#pragma unroll
+    for (int qy = 0; qy < 3; ++qy) {
+      const T eta = (T)gauss_x(qy);
+#pragma unroll
+      for (int qx = 0; qx < 3; ++qx) {
+        const T xi = (T)gauss_x(qx);
+        T uq = (T(1) - eta) * ((T(1) - xi) * u00 + xi * u01) + eta * ((T(1) - xi) * u10 + xi * u11);
+        c0[qy][qx] = (T)(gauss_w(qx) * gauss_w(qy)) * h2 * uq;
+        cx[qy][qx] = T(0);
+        cy[qy][qx] = T(0);
+      }
+    }
+  }
+  // test functions: along x, then along y
+  T T0[3][3], T1[3][3];  // [qy][a]
+#pragma unroll
+  for (int qy = 0; qy < 3; ++qy)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      T t0 = T(0), t1 = T(0);
+#pragma unroll
+      for (int qx = 0; qx < 3; ++qx) {
+        t0 += c0[qy][qx] * bx[aa][qx];
+        if (MODE == 0) {
+          t0 += cx[qy][qx] * dbx[aa][qx];
+          t1 += cy[qy][qx] * bx[aa][qx];
+        }
+      }
+      T0[qy][aa] = t0;
+      T1[qy][aa] = t1;
+    }
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      T v = T(0);
+#pragma unroll
+      for (int qy = 0; qy < 3; ++qy) {
+        v += by[b][qy] * T0[qy][aa];
+        if (MODE == 0) v += dby[b][qy] * T1[qy][aa];
+      }
+      loc[b][aa] = v;
+    }
+}
+
+// In-place LDL^T solve of one line of length nb with element stride `str`.
+template <typename T>
+__device__ __forceinline__ void ldlt_line(T* x, int nb, int str, const T* l1, const T* l2,
+                                          const T* dinv) {
+  T ym1 = T(0), ym2 = T(0);
+  for (int l = 0; l < nb; ++l) {
+    T y = x[(size_t)l * str] - l1[l] * ym1 - l2[l] * ym2;
+    x[(size_t)l * str] = y;
+    ym2 = ym1;
+    ym1 = y;
+  }
+  T xp1 = T(0), xp2 = T(0);
+  for (int l = nb - 1; l >= 0; --l) {
+    T v = x[(size_t)l * str] * dinv[l] - l1[l + 1] * xp1 - l2[l + 2] * xp2;
+    x[(size_t)l * str] = v;
+    xp2 = xp1;
+    xp1 = v;
+  }
+}
+
+constexpr int kQuadThreads = 256;
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kQuadThreads) k_quad_xsolve_2d(QuadArgs<T> a, int re, T* Xm,
+                                                                  T* Xs, double* src_part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  T* acc = reinterpret_cast<T*>(smraw);
+  const int nb = a.nb, n = a.n, tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const int e0 = b * re;
+  const int e1 = min(e0 + re, n);
+  const int nrows = e1 - e0 + 2;
+  for (int i = tid; i < nrows * nb; i += blockDim.x) acc[i] = T(0);
+  __syncthreads();
+  double src = 0.0;
+  for (int er = e0; er < e1; ++er) {
+    for (int base = 0; base < n; base += blockDim.x) {
+      const int ex = base + tid;
+      const bool ok = ex < n;
+      T loc[3][3];
+      if (ok) element_rhs_2d<T, MODE>(a, ex, er, loc, src);
+      // three colours by ex mod 3: elements of one colour touch disjoint columns
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (ok && (ex % 3) == c) {
+#pragma unroll
+          for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa) acc[(er - e0 + bb) * nb + ex + aa] += loc[bb][aa];
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (tid < nrows) ldlt_line<T>(acc + tid * nb, nb, 1, a.ax.l1, a.ax.l2, a.ax.dinv);
+  __syncthreads();
+  const int own = e1 - e0;
+  for (int i = tid; i < nrows * nb; i += blockDim.x) {
+    int r = i / nb, k = i - r * nb;
+    if (r < own || e1 == n) Xm[(size_t)(e0 + r) * nb + k] = acc[i];
+    else Xs[((size_t)b * 2 + (r - own)) * nb + k] = acc[i];
+  }
+  if (MODE == 0) {
+    double tot = block_sum(src, red);
+    if (tid == 0) src_part[b] = tot;
+  }
+}
+
+int quad_blocks(int dim, int n, int re) {
+  if (dim == 2) return (n + re - 1) / re;
+  return n * ((n + re - 1) / re);
+}
+
+template <typename T>
+cudaError_t launch_quad_xsolve(const QuadArgs<T>& a, int mode, int re, T* Xm, T* Xs,
+                               double* src_part, cudaStream_t st) {
+  if (a.dim != 2) return cudaErrorNotSupported;
+  int nblk = quad_blocks(2, a.n, re);
+  size_t smem = (size_t)(re + 2) * a.nb * sizeof(T);
+  if (mode == 0) {
+    auto k = k_quad_xsolve_2d<T, 0>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, kQuadThreads, smem, st>>>(a, re, Xm, Xs, src_part);
+  } else {
+    auto k = k_quad_xsolve_2d<T, 1>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, kQuadThreads, smem, st>>>(a, re, Xm, Xs, src_part);
+  }
+  return cudaGetLastError();
+}
+
+// y sweep: thread per column k; row l of the right-hand side is Xm[l] plus,
+// when l is one of the first two rows of a strip other than the first, the
+// row spilled by the strip above.
+template <typename T>
+__global__ void __launch_bounds__(128) k_ysolve_2d(int n, int re, T* X, const T* Xs, const T* l1,
+                                                   const T* l2, const T* dinv, const T* Iw,
+                                                   double* mass_part) {
+  __shared__ double red[32];
+  const int nb = n + 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double mass = 0.0;
+  if (k < nb) {
+    T ym1 = T(0), ym2 = T(0);
+    for (int l = 0; l < nb; ++l) {
+      T v = X[(size_t)l * nb + k];
+      int r = l % re;
+      int top = l - r;
+      if (r < 2 && l >= re && top < n) v += Xs[((size_t)(top / re - 1) * 2 + r) * nb + k];
+      T y = v - l1[l] * ym1 - l2[l] * ym2;
+      X[(size_t)l * nb + k] = y;
+      ym2 = ym1;
+      ym1 = y;
+    }
+    T xp1 = T(0), xp2 = T(0);
+    for (int l = nb - 1; l >= 0; --l) {
+      T v = X[(size_t)l * nb + k] * dinv[l] - l1[l + 1] * xp1 - l2[l + 2] * xp2;
+      X[(size_t)l * nb + k] = v;
+      mass += (double)v * (double)Iw[l];
+      xp2 = xp1;
+      xp1 = v;
+    }
+    mass *= (double)Iw[k];
+  }
+  double tot = block_sum(mass, red);
+  if (threadIdx.x == 0) mass_part[blockIdx.x] = tot;
+}
+
+int ysolve_blocks(int dim, int n) {
+  int nb = n + 2;
+  if (dim == 2) return (nb + 127) / 128;
+  return (nb * nb + 127) / 128;
+}
+
+template <typename T>
+cudaError_t launch_ysolve(const QuadArgs<T>& a, int re, T* X, const T* Xs, double* mass_part,
+                          cudaStream_t st) {
+  if (a.dim != 2) return cudaErrorNotSupported;
+  k_ysolve_2d<T><<<ysolve_blocks(2, a.n), 128, 0, st>>>(a.n, re, X, Xs, a.ax.l1, a.ax.l2,
+                                                        a.ax.dinv, a.ax.Iw, mass_part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zsolve(const QuadArgs<T>&, T*, double*, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+
+// int S = sum_kl S_kl (int B_k)(int B_l): thread per column
+template <typename T>
+__global__ void __launch_bounds__(128) k_mass_2d(int n, const T* S, const T* Iw, double* part) {
+  __shared__ double red[32];
+  const int nb = n + 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (k < nb) {
+    for (int l = 0; l < nb; ++l) m += (double)S[(size_t)l * nb + k] * (double)Iw[l];
+    m *= (double)Iw[k];
+  }
+  double tot = block_sum(m, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <typename T>
+cudaError_t launch_mass(const QuadArgs<T>& a, const T* S, double* mass_part, cudaStream_t st) {
+  if (a.dim != 2) return cudaErrorNotSupported;
+  k_mass_2d<T><<<ysolve_blocks(2, a.n), 128, 0, st>>>(a.n, S, a.ax.Iw, mass_part);
+  return cudaGetLastError();
+}
+
+// stats[0] = int S, stats[1] += step mass error, stats[2] += source integral
+__global__ void k_mass_finalize(const double* mp, int nm, const double* sp, int ns, int mode,
+                                double* stats, int* flags) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double m = 0.0;
+  for (int i = 0; i < nm; ++i) m += mp[i];
+  if (mode == 0) {
+    stats[0] = m;
+  } else {
+    double s = 0.0;
+    for (int i = 0; i < ns; ++i) s += sp[i];
+    stats[1] += m - stats[0] - s;
+    stats[2] += s;
+    stats[0] = m;
+  }
+  if (!isfinite(m)) flags[0] |= 1;
+}
+
+cudaError_t launch_mass_finalize(const double* mass_part, int nmass, const double* src_part,
+                                 int nsrc, int mode, double* stats, int* flags, cudaStream_t st) {
+  k_mass_finalize<<<1, 32, 0, st>>>(mass_part, nmass, src_part, nsrc, mode, stats, flags);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CFL step size: max over Gauss points of |K (grad p + s rho_g g e)|/(mu_g phi)
+// and of q_inj/phi
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl_2d(QuadArgs<T> a, double* part) {
+  __shared__ double red[32];
+  const int n = a.n, nb = a.nb, n1 = n + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double vmax = 0.0, smax = 0.0;
+  if (e < n * n) {
+    const int ex = e % n, ey = e / n;
+    const T* Bx = a.ax.B + ex * 9; const T* dBx = a.ax.dB + ex * 9;
+    const T* By = a.ax.B + ey * 9; const T* dBy = a.ax.dB + ey * 9;
+    T Px[3][3], Pdx[3][3];
+    for (int b = 0; b < 3; ++b) {
+      const T* prow = a.P + (size_t)(ey + b) * nb + ex;
+      for (int q = 0; q < 3; ++q) {
+        Px[b][q] = prow[0] * Bx[q] + prow[1] * Bx[3 + q] + prow[2] * Bx[6 + q];
+        Pdx[b][q] = prow[0] * dBx[q] + prow[1] * dBx[3 + q] + prow[2] * dBx[6 + q];
+      }
+    }
+    const T* Kr = a.K + (size_t)ey * n1 + ex;
+    T k00 = Kr[0], k01 = Kr[1], k10 = Kr[n1], k11 = Kr[n1 + 1];
+    T f00 = a.phi_c, f01 = a.phi_c, f10 = a.phi_c, f11 = a.phi_c;
+    if (a.phi) {
+      const T* Fr = a.phi + (size_t)ey * n1 + ex;
+      f00 = Fr[0]; f01 = Fr[1]; f10 = Fr[n1]; f11 = Fr[n1 + 1];
+    }
+    for (int qy = 0; qy < 3; ++qy)
+      for (int qx = 0; qx < 3; ++qx) {
+        T xi = (T)gauss_x(qx), eta = (T)gauss_x(qy);
+        T dpx = By[qy] * Pdx[0][qx] + By[3 + qy] * Pdx[1][qx] + By[6 + qy] * Pdx[2][qx];
+        T dpy = dBy[qy] * Px[0][qx] + dBy[3 + qy] * Px[1][qx] + dBy[6 + qy] * Px[2][qx];
+        T Kq = (T(1) - eta) * ((T(1) - xi) * k00 + xi * k01) + eta * ((T(1) - xi) * k10 + xi * k11);
+        T phq = (T(1) - eta) * ((T(1) - xi) * f00 + xi * f01) + eta * ((T(1) - xi) * f10 + xi * f11);
+        T fx = Kq * dpx, fy = Kq * (dpy + a.grav_term);
+        double v = sqrt((double)(fx * fx + fy * fy)) * (double)a.inv_mu_g / (double)phq;
+        vmax = fmax(vmax, v);
+        T qi = T(0);
+        for (int s = 0; s < a.n_src; ++s)
+          if (a.kind[s] == 0)
+            qi += a.rate[s] * a.ax.gsrc[((size_t)(0 * kMaxSrc + s) * n + ex) * 3 + qx] *
+                  a.ax.gsrc[((size_t)(1 * kMaxSrc + s) * n + ey) * 3 + qy];
+        smax = fmax(smax, (double)(qi / phq));
+      }
+  }
+  double r1 = block_max(vmax, red);
+  __syncthreads();
+  double r2 = block_max(smax, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r1;
+    part[2 * blockIdx.x + 1] = r2;
+  }
+}
+
+int cfl_blocks(int dim, int n) {
+  long long ne = 1;
+  for (int i = 0; i < dim; ++i) ne *= n;
+  return (int)((ne + 255) / 256);
+}
+
+template <typename T>
+cudaError_t launch_cfl(const QuadArgs<T>& a, double* part, cudaStream_t st) {
+  if (a.dim != 2) return cudaErrorNotSupported;
+  k_cfl_2d<T><<<cfl_blocks(2, a.n), 256, 0, st>>>(a, part);
+  return cudaGetLastError();
+}
+
+__global__ void k_cfl_finalize(const double* part, int nblk, double cfl, double frac, double cap,
+                               double h, double* dt, int* flags) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double vmax = 0.0, smax = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    vmax = fmax(vmax, part[2 * i]);
+    smax = fmax(smax, part[2 * i + 1]);
+  }
+  double d = cap;
+  if (vmax > 0.0) d = fmin(d, cfl * h / vmax);
+  if (smax > 0.0) d = fmin(d, frac / smax);
+  if (!isfinite(d) || d <= 0.0) flags[0] |= 2;
+  *dt = d;
+}
+
+cudaError_t launch_cfl_finalize(const double* part, int nblk, double cfl, double src_frac,
+                                double dt_cap, double h, double* dt, int* flags, cudaStream_t st) {
+  k_cfl_finalize<<<1, 32, 0, st>>>(part, nblk, cfl, src_frac, dt_cap, h, dt, flags);
+  return cudaGetLastError();
+}
+
+#define ADS_INST(T)                                                                              \
+  template cudaError_t launch_quad_xsolve<T>(const QuadArgs<T>&, int, int, T*, T*, double*,      \
+                                             cudaStream_t);                                      \
+  template cudaError_t launch_ysolve<T>(const QuadArgs<T>&, int, T*, const T*, double*,          \
+                                        cudaStream_t);                                           \
+  template cudaError_t launch_zsolve<T>(const QuadArgs<T>&, T*, double*, cudaStream_t);          \
+  template cudaError_t launch_mass<T>(const QuadArgs<T>&, const T*, double*, cudaStream_t);      \
+  template cudaError_t launch_cfl<T>(const QuadArgs<T>&, double*, cudaStream_t);
+ADS_INST(double)
+ADS_INST(float)
+
+}  // namespace adsgb

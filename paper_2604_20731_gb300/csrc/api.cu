@@ -1,0 +1,1083 @@
+// C ABI of the adsgb library: context lifetime, device buffers, the hybrid
+// time step of Sec. 6 as a replayed CUDA graph, and data access.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/adsgb.h"
+#include "kernels.cuh"
+
+using namespace adsgb;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+size_t tsize(int dt) { return dt == ADS_F64 ? 8 : 4; }
+
+}  // namespace
+
+struct ads_ctx {
+  ads_params prm{};
+  crvpinn_params cp{};
+  bool has_crv = false;
+  int dim = 2, n = 0, nb = 0, N = 0, M = 0, m1 = 0, nparams = 0;
+  int ta = ADS_F64, tc = ADS_F64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ads_status status = ADS_OK;
+  std::string err;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+
+  // FP64 tables
+  double *B64 = nullptr, *dB64 = nullptr, *l1_64 = nullptr, *l2_64 = nullptr, *dinv64 = nullptr,
+         *Iw64 = nullptr, *gsrc64 = nullptr, *gnode64 = nullptr, *tmp64 = nullptr,
+         *cen64 = nullptr, *sig64 = nullptr;
+  // ADS-precision tables and fields
+  void *B = nullptr, *dB = nullptr, *l1 = nullptr, *l2 = nullptr, *dinv = nullptr, *Iw = nullptr,
+       *gsrc = nullptr, *gnode = nullptr;
+  void *S[2] = {nullptr, nullptr}, *P = nullptr, *K = nullptr, *phi = nullptr, *Xs = nullptr,
+       *nodal = nullptr;
+  int cur = 0;
+  double *src_part = nullptr, *mass_part = nullptr, *cfl_part = nullptr, *stats = nullptr,
+         *dt = nullptr, *scal = nullptr;
+  int* flags = nullptr;
+  int re = 4, nquad = 0, nys = 0, ncfl = 0;
+  // CRVPINN (network precision)
+  void *alpha = nullptr, *f = nullptr, *u = nullptr, *res = nullptr, *rhat = nullptr, *z = nullptr,
+       *gu = nullptr, *Sdst = nullptr, *invd = nullptr, *theta = nullptr, *am = nullptr,
+       *av = nullptr, *grad = nullptr, *gpart = nullptr, *acts = nullptr;
+  double *dot_part = nullptr, *loss = nullptr, *loss_log = nullptr, *bc = nullptr, *lr = nullptr;
+  int* t = nullptr;
+  int ndot = 0, nbwd = 0, ld = 0;
+  // host staging (pinned)
+  double* h_stage = nullptr;
+  size_t h_stage_count = 0;
+  // graphs keyed by (kind, parameters, buffer parity) with their kernel counts
+  std::map<std::tuple<int, int, int, int, long long>, std::pair<cudaGraphExec_t, long long>> graphs;
+  // diagnostics: kernels enqueued (graph replays count their kernels) and
+  // optional per-kernel events
+  unsigned long long nlaunch = 0;
+  cudaEvent_t* prof = nullptr;
+};
+
+namespace {
+
+ads_status fail(ads_ctx* c, ads_status st, const std::string& msg) {
+  if (c) {
+    if (c->status == ADS_OK || st == ADS_ERR_CUDA) c->status = st;
+    c->err = msg;
+  }
+  return st;
+}
+
+#define CK(...)                                                                    \
+  do {                                                                             \
+    cudaError_t e_ = (__VA_ARGS__);                                                \
+    if (e_ != cudaSuccess) {                                                       \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? ADS_ERR_OOM : ADS_ERR_CUDA, \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));      \
+    }                                                                              \
+  } while (0)
+
+ads_status alloc(ads_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, ADS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  c->bytes += bytes;
+  return ADS_OK;
+}
+template <typename X>
+ads_status allocT(ads_ctx* c, X** p, size_t count) {
+  return alloc(c, reinterpret_cast<void**>(p), count * sizeof(X));
+}
+
+// enqueue one kernel: check, count, and bracket it with profiling events
+#define LK(k, ...)                                                        \
+  do {                                                                    \
+    if (c->prof) cudaEventRecord(c->prof[(k)], c->stream);                \
+    CK(__VA_ARGS__);                                                      \
+    if (c->prof) cudaEventRecord(c->prof[(k) + 1], c->stream);            \
+    c->nlaunch++;                                                         \
+  } while (0)
+
+#define CA(...)                      \
+  do {                               \
+    ads_status s_ = (__VA_ARGS__);   \
+    if (s_ != ADS_OK) return s_;     \
+  } while (0)
+
+ads_status wait(ads_ctx* c, double timeout_s) {
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) return ADS_OK;
+    if (e != cudaErrorNotReady)
+      return fail(c, ADS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_s) return fail(c, ADS_ERR_TIMEOUT, "timed out waiting for the stream");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+constexpr double kDefaultTimeout = 600.0;
+
+size_t ncoef(const ads_ctx* c) {
+  size_t v = 1;
+  for (int i = 0; i < c->dim; ++i) v *= (size_t)c->nb;
+  return v;
+}
+size_t nnode(const ads_ctx* c) {
+  size_t v = 1;
+  for (int i = 0; i < c->dim; ++i) v *= (size_t)(c->n + 1);
+  return v;
+}
+
+template <typename TA>
+QuadArgs<TA> quad_args(ads_ctx* c, const void* S) {
+  QuadArgs<TA> a{};
+  a.dim = c->dim;
+  a.n = c->n;
+  a.nb = c->nb;
+  a.h = TA(1.0 / c->n);
+  a.S = (const TA*)S;
+  a.P = (const TA*)c->P;
+  a.K = (const TA*)c->K;
+  a.phi = (const TA*)c->phi;
+  a.phi_c = (TA)c->prm.phi;
+  a.nodal = (const TA*)c->nodal;
+  a.ax.B = (const TA*)c->B;
+  a.ax.dB = (const TA*)c->dB;
+  a.ax.l1 = (const TA*)c->l1;
+  a.ax.l2 = (const TA*)c->l2;
+  a.ax.dinv = (const TA*)c->dinv;
+  a.ax.Iw = (const TA*)c->Iw;
+  a.ax.gsrc = (const TA*)c->gsrc;
+  a.ax.gnode = (const TA*)c->gnode;
+  a.n_src = c->prm.n_src;
+  for (int s = 0; s < kMaxSrc; ++s) {
+    a.rate[s] = s < c->prm.n_src ? (TA)c->prm.src[s].rate : TA(0);
+    a.kind[s] = s < c->prm.n_src ? c->prm.src[s].kind : 0;
+  }
+  a.inv_mu_g = TA(1.0 / c->prm.mu_g);
+  a.inv_mu_w = TA(1.0 / c->prm.mu_w);
+  a.grav_term = TA(c->prm.grav_sign * c->prm.rho_g * c->prm.grav);
+  a.kz = TA(c->prm.kz_ratio);
+  a.dt = c->dt;
+  return a;
+}
+
+// ---- enqueue helpers ---------------------------------------------------------
+
+template <typename TA>
+ads_status enq_sat_steps(ads_ctx* c, int n_sub) {
+  for (int s = 0; s < n_sub; ++s) {
+    void* in = c->S[c->cur];
+    void* out = c->S[1 - c->cur];
+    QuadArgs<TA> a = quad_args<TA>(c, in);
+    LK(0, launch_quad_xsolve<TA>(a, 0, c->re, (TA*)out, (TA*)c->Xs, c->src_part, c->stream));
+    LK(1, launch_ysolve<TA>(a, c->re, (TA*)out, (const TA*)c->Xs, c->mass_part, c->stream));
+    LK(2, launch_mass_finalize(c->mass_part, c->nys, c->src_part, c->nquad, 1, c->stats, c->flags,
+                               c->stream));
+    c->cur = 1 - c->cur;
+  }
+  return ADS_OK;
+}
+
+template <typename TA>
+ads_status enq_mass_set(ads_ctx* c) {
+  QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
+  CK(launch_mass<TA>(a, (const TA*)c->S[c->cur], c->mass_part, c->stream));
+  CK(launch_mass_finalize(c->mass_part, c->nys, c->src_part, 0, 0, c->stats, c->flags, c->stream));
+  c->nlaunch += 2;
+  return ADS_OK;
+}
+
+template <typename TA>
+ads_status enq_cfl(ads_ctx* c, double cfl, double frac, double cap) {
+  QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
+  CK(launch_cfl<TA>(a, c->cfl_part, c->stream));
+  CK(launch_cfl_finalize(c->cfl_part, c->ncfl, cfl, frac, cap, 1.0 / c->n, c->dt, c->flags,
+                         c->stream));
+  c->nlaunch += 2;
+  return ADS_OK;
+}
+
+template <typename TC>
+MlpArgs<TC> mlp_args(ads_ctx* c, bool store) {
+  MlpArgs<TC> a{};
+  a.din = c->dim;
+  a.width = c->cp.width;
+  a.npts = c->M;
+  a.N = c->N;
+  a.ld = c->ld;
+  a.theta = (const TC*)c->theta;
+  a.u = (TC*)c->u;
+  a.acts = store ? (TC*)c->acts : nullptr;
+  a.gu = (const TC*)c->gu;
+  a.gpart = (TC*)c->gpart;
+  a.nparams = c->nparams;
+  return a;
+}
+
+template <typename TC, typename TA>
+ads_status enq_coeffs(ads_ctx* c) {
+  CrvArgs<TC, TA> a{};
+  a.dim = c->dim;
+  a.N = c->N;
+  a.M = c->M;
+  a.h = TC(1.0 / c->N);
+  a.S = (const TA*)c->S[c->cur];
+  a.K = (const TA*)c->K;
+  a.ax.gnode = (const TA*)c->gnode;
+  a.n_src = c->prm.n_src;
+  for (int s = 0; s < kMaxSrc; ++s) {
+    a.rate[s] = s < c->prm.n_src ? c->prm.src[s].rate : 0.0;
+    a.kind[s] = s < c->prm.n_src ? c->prm.src[s].kind : 0;
+  }
+  a.inv_mu_g = 1.0 / c->prm.mu_g;
+  a.inv_mu_w = 1.0 / c->prm.mu_w;
+  a.rho_w = c->prm.rho_w;
+  a.rho_g = c->prm.rho_g;
+  a.grav = c->prm.grav;
+  a.kz = c->prm.kz_ratio;
+  a.alpha = (TC*)c->alpha;
+  a.f = (TC*)c->f;
+  CK(launch_crv_coeffs<TC, TA>(a, c->stream));
+  c->nlaunch += 1;
+  return ADS_OK;
+}
+
+// one Adam iteration (upd = 1) or one loss/gradient evaluation (upd = 0)
+template <typename TC>
+ads_status enq_train_iter(ads_ctx* c, int upd) {
+  const int m = c->m1;
+  const TC h = TC(1.0 / c->N);
+  LK(0, launch_mlp_fwd<TC>(mlp_args<TC>(c, true), c->stream));
+  LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->u,
+                           (const TC*)c->f, h * h, TC(1), (TC*)c->res, c->stream));
+  LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
+                        TC(1), c->stream));
+  LK(3, launch_tridiag_cols<TC>(m, m, (const TC*)c->invd, (TC*)c->rhat, c->stream));
+  LK(4, launch_gemm<TC>(m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
+                        h * h, c->stream));
+  LK(5, launch_dot_partial<TC>((const TC*)c->res, (const TC*)c->z, c->M, c->dot_part, c->ndot,
+                               c->stream));
+  LK(6, launch_loss_finalize(c->dot_part, c->ndot, c->loss, c->loss_log, c->t, c->bc, c->flags,
+                             upd, c->stream));
+  LK(7, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
+                           nullptr, TC(0), TC(2), (TC*)c->gu, c->stream));
+  LK(8, launch_mlp_bwd<TC>(mlp_args<TC>(c, true), c->nbwd, c->stream));
+  LK(9, launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->nbwd, c->nparams, (TC*)c->grad,
+                                    (TC*)c->theta, (TC*)c->am, (TC*)c->av, c->bc, c->lr, upd,
+                                    c->stream));
+  return ADS_OK;
+}
+
+template <typename TC, typename TA>
+ads_status enq_project(ads_ctx* c) {
+  CK(launch_mlp_fwd<TC>(mlp_args<TC>(c, false), c->stream));
+  CK(launch_embed<TC, TA>(c->dim, c->N, (const TC*)c->u, (TA*)c->nodal, c->stream));
+  QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
+  CK(launch_quad_xsolve<TA>(a, 1, c->re, (TA*)c->P, (TA*)c->Xs, c->src_part, c->stream));
+  CK(launch_ysolve<TA>(a, c->re, (TA*)c->P, (const TA*)c->Xs, c->mass_part, c->stream));
+  c->nlaunch += 4;
+  return ADS_OK;
+}
+
+// dispatch on (network type, ADS type)
+template <template <typename, typename> class F>
+ads_status dispatch2(ads_ctx* c) {
+  if (c->tc == ADS_F64 && c->ta == ADS_F64) return F<double, double>::run(c);
+  if (c->tc == ADS_F32 && c->ta == ADS_F64) return F<float, double>::run(c);
+  if (c->tc == ADS_F32 && c->ta == ADS_F32) return F<float, float>::run(c);
+  return F<double, float>::run(c);
+}
+
+ads_status set_scalar(ads_ctx* c, double* dptr, double v) {
+  // value baked into a 1-thread kernel so that it is stream-ordered
+  CK(cudaMemcpyAsync(dptr, &v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return wait(c, kDefaultTimeout);
+}
+
+ads_status run_graph(ads_ctx* c, std::tuple<int, int, int, int, long long> key,
+                     ads_status (*body)(ads_ctx*, const void*), const void* arg, int cur_after) {
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    int cur0 = c->cur;
+    unsigned long long n0 = c->nlaunch;
+    cudaEvent_t* prof = c->prof;
+    c->prof = nullptr;  // events are not captured into graphs
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    ads_status st = body(c, arg);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->prof = prof;
+    long long nk = (long long)(c->nlaunch - n0);
+    c->nlaunch = n0;
+    c->cur = cur0;
+    if (st != ADS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(c, ADS_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, ADS_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    c->graphs[key] = std::make_pair(ex, nk);
+    it = c->graphs.find(key);
+  }
+  CK(cudaGraphLaunch(it->second.first, c->stream));
+  c->nlaunch += (unsigned long long)it->second.second;
+  c->cur = cur_after;
+  return ADS_OK;
+}
+
+struct TrainBody {
+  int iters, upd;
+};
+template <typename TC, typename TA>
+struct TrainF {
+  static ads_status body(ads_ctx* c, const void* arg) {
+    const TrainBody* b = (const TrainBody*)arg;
+    for (int i = 0; i < b->iters; ++i) CA(enq_train_iter<TC>(c, b->upd));
+    return ADS_OK;
+  }
+};
+
+template <typename TC, typename TA>
+ads_status train(ads_ctx* c, int iters, int upd) {
+  const int chunk = 50;
+  TrainBody full{chunk, upd};
+  int done = 0;
+  while (iters - done >= chunk) {
+    CA(run_graph(c, std::make_tuple(1, chunk, upd, 0, 0LL), &TrainF<TC, TA>::body, &full, c->cur));
+    done += chunk;
+  }
+  int rest = iters - done;
+  if (rest > 0) {
+    TrainBody b{rest, upd};
+    CA(run_graph(c, std::make_tuple(1, rest, upd, 0, 0LL), &TrainF<TC, TA>::body, &b, c->cur));
+  }
+  return ADS_OK;
+}
+
+struct HybridBody {
+  hybrid_params hp;
+};
+template <typename TC, typename TA>
+struct HybridF {
+  static ads_status body(ads_ctx* c, const void* arg) {
+    const hybrid_params& hp = ((const HybridBody*)arg)->hp;
+    CA((enq_project<TC, TA>(c)));
+    if (hp.dt_policy == 1) CA(enq_cfl<TA>(c, hp.cfl, hp.src_frac, hp.dt));
+    CA(enq_sat_steps<TA>(c, hp.n_sub));
+    CA((enq_coeffs<TC, TA>(c)));
+    for (int i = 0; i < hp.adam_iters; ++i) CA(enq_train_iter<TC>(c, 1));
+    return ADS_OK;
+  }
+};
+
+template <typename TA>
+struct SatBody {
+  static ads_status body(ads_ctx* c, const void* arg) {
+    return enq_sat_steps<TA>(c, *(const int*)arg);
+  }
+};
+
+ads_status check(ads_ctx* c) {
+  if (!c) return ADS_ERR_INVALID_ARG;
+  if (c->status == ADS_ERR_CUDA) return c->status;
+  return ADS_OK;
+}
+
+ads_status read_flags(ads_ctx* c, int* flags) {
+  CK(cudaMemcpyAsync(c->h_stage, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CA(wait(c, kDefaultTimeout));
+  std::memcpy(flags, c->h_stage, sizeof(int));
+  return ADS_OK;
+}
+
+ads_status read_doubles(ads_ctx* c, const double* dptr, double* out, size_t count) {
+  if (count > c->h_stage_count) return fail(c, ADS_ERR_INVALID_ARG, "staging too small");
+  CK(cudaMemcpyAsync(c->h_stage, dptr, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CA(wait(c, kDefaultTimeout));
+  std::memcpy(out, c->h_stage, count * sizeof(double));
+  return ADS_OK;
+}
+
+// copy host doubles to a device field of dtype dt (via the FP64 scratch)
+ads_status upload(ads_ctx* c, void* dst, int dt, const double* host, size_t count) {
+  if (dt == ADS_F64) {
+    CK(cudaMemcpyAsync(dst, host, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, count * sizeof(double), c->stream));
+    CK(cudaMemcpyAsync(tmp, host, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_convert<float>(tmp, (float*)dst, count, c->stream));
+    CK(cudaFreeAsync(tmp, c->stream));
+  }
+  return wait(c, kDefaultTimeout);
+}
+
+ads_status field_info(const ads_ctx* c, int field, void** ptr, size_t* count, int* dt) {
+  size_t nc = ncoef(c), nn = nnode(c);
+  switch (field) {
+    case ADS_FIELD_S: *ptr = c->S[c->cur]; *count = nc; *dt = c->ta; return ADS_OK;
+    case ADS_FIELD_P: *ptr = c->P; *count = nc; *dt = c->ta; return ADS_OK;
+    case ADS_FIELD_K: *ptr = c->K; *count = nn; *dt = c->ta; return ADS_OK;
+    case ADS_FIELD_DT: *ptr = c->dt; *count = 1; *dt = ADS_F64; return ADS_OK;
+    case ADS_FIELD_MASS: *ptr = c->stats; *count = 3; *dt = ADS_F64; return ADS_OK;
+    default: break;
+  }
+  if (!c->has_crv) return ADS_ERR_STATE;
+  switch (field) {
+    case ADS_FIELD_ALPHA: *ptr = c->alpha; *count = nn; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_F: *ptr = c->f; *count = c->M; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_U: *ptr = c->u; *count = c->M; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_RES: *ptr = c->res; *count = c->M; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_Z: *ptr = c->z; *count = c->M; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_GU: *ptr = c->gu; *count = c->M; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_THETA: *ptr = c->theta; *count = c->nparams; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_GRAD: *ptr = c->grad; *count = c->nparams; *dt = c->tc; return ADS_OK;
+    case ADS_FIELD_LOSS: *ptr = c->loss; *count = 1; *dt = ADS_F64; return ADS_OK;
+    case ADS_FIELD_LOSS_LOG: *ptr = c->loss_log; *count = kLossRing; *dt = ADS_F64; return ADS_OK;
+    default: return ADS_ERR_INVALID_ARG;
+  }
+}
+
+int mlp_params(int din, int w, int hl) {
+  int p = w * din + w;
+  p += (hl - 1) * (w * w + w);
+  p += w + 1;
+  return p;
+}
+
+ads_status validate(const ads_params* p, const crvpinn_params* cp) {
+  if (!p) return ADS_ERR_INVALID_ARG;
+  if (p->dim != 2) return ADS_ERR_UNSUPPORTED;
+  if (p->n < 2 || p->n > 8192) return ADS_ERR_INVALID_ARG;
+  if (!(p->phi > 0) || !(p->mu_w > 0) || !(p->mu_g > 0)) return ADS_ERR_INVALID_ARG;
+  if (!(p->grav >= 0) || !std::isfinite(p->grav) || !std::isfinite(p->grav_sign)) return ADS_ERR_INVALID_ARG;
+  if (p->n_src < 0 || p->n_src > ADS_MAX_SOURCES) return ADS_ERR_INVALID_ARG;
+  for (int s = 0; s < p->n_src; ++s) {
+    if (!(p->src[s].sigma > 0) || !(p->src[s].rate >= 0) || !std::isfinite(p->src[s].rate))
+      return ADS_ERR_INVALID_ARG;
+    if (p->src[s].kind != 0 && p->src[s].kind != 1) return ADS_ERR_INVALID_ARG;
+  }
+  if (p->ads_dtype != ADS_F64 && p->ads_dtype != ADS_F32) return ADS_ERR_INVALID_ARG;
+  if (cp) {
+    if (cp->hidden_layers != 4) return ADS_ERR_UNSUPPORTED;
+    if (cp->width != 64 && cp->width != 128) return ADS_ERR_UNSUPPORTED;
+    if (cp->dtype != ADS_F64 && cp->dtype != ADS_F32) return ADS_ERR_UNSUPPORTED;
+    if (cp->dtype == ADS_F64 && cp->width != 64) return ADS_ERR_UNSUPPORTED;
+    if (p->n < 3) return ADS_ERR_INVALID_ARG;
+  }
+  return ADS_OK;
+}
+
+bool all_finite(const double* x, size_t n, bool positive) {
+  for (size_t i = 0; i < n; ++i) {
+    if (!std::isfinite(x[i])) return false;
+    if (positive && !(x[i] > 0)) return false;
+  }
+  return true;
+}
+
+size_t estimate(const ads_params* p, const crvpinn_params* cp) {
+  size_t n = p->n, nb = n + 2, n1 = n + 1;
+  size_t ta = tsize(p->ads_dtype);
+  size_t nc = nb * nb, nn = n1 * n1;
+  size_t b = 0;
+  b += 8 * (18 * n + 3 * (n + 4) + 2 * nb + 3 * kMaxSrc * (3 * n + n1) + 3 * (n + 4) + 64);
+  b += ta * (18 * n + 3 * (n + 4) + 2 * nb + 3 * kMaxSrc * (3 * n + n1));
+  b += ta * (3 * nc + 2 * nn + 2 * ((n + 3) / 4) * 2 * nb + nn);
+  b += 8 * 4 * (nb + 1024);
+  if (cp) {
+    size_t tc = tsize(cp->dtype);
+    size_t m = n - 1, M = m * m, w = cp->width;
+    size_t np = mlp_params(2, cp->width, cp->hidden_layers);
+    size_t ld = ((M + 63) / 64) * 64;
+    b += tc * (nn + 6 * M + 2 * m * m + 5 * np + 4 * w * ld + 2 * 152 * np);
+    b += 8 * (2 * m * m + kLossRing + 2048);
+  }
+  return b;
+}
+
+template <typename TC, typename TA>
+struct CoeffF {
+  static ads_status run(ads_ctx* c) { return enq_coeffs<TC, TA>(c); }
+};
+template <typename TC, typename TA>
+struct ProjF {
+  static ads_status run(ads_ctx* c) { return enq_project<TC, TA>(c); }
+};
+template <typename TC, typename TA>
+struct EvalF {
+  static ads_status run(ads_ctx* c) { return enq_train_iter<TC>(c, 0); }
+};
+template <typename TC, typename TA>
+struct TrainRun {
+  static ads_status go(ads_ctx* c, int iters) { return train<TC, TA>(c, iters, 1); }
+};
+
+template <typename TC>
+ads_status profile_train_t(ads_ctx* c, int iters, double* ms) {
+  const int NK = 10;
+  cudaEvent_t ev[NK + 1];
+  for (int k = 0; k <= NK; ++k) CK(cudaEventCreate(&ev[k]));
+  for (int k = 0; k < NK; ++k) ms[k] = 0.0;
+  ads_status st = ADS_OK;
+  for (int it = 0; it < iters && st == ADS_OK; ++it) {
+    c->prof = ev;
+    st = enq_train_iter<TC>(c, 1);
+    c->prof = nullptr;
+    if (st != ADS_OK) break;
+    st = wait(c, kDefaultTimeout);
+    for (int k = 0; k < NK && st == ADS_OK; ++k) {
+      float f = 0.f;
+      cudaEventElapsedTime(&f, ev[k], ev[k + 1]);
+      ms[k] += f;
+    }
+  }
+  for (int k = 0; k <= NK; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < NK; ++k) ms[k] /= (iters > 0 ? iters : 1);
+  return st;
+}
+
+template <typename TA>
+ads_status profile_sat_t(ads_ctx* c, int steps, double* ms) {
+  const int NK = 3;
+  cudaEvent_t ev[NK + 1];
+  for (int k = 0; k <= NK; ++k) CK(cudaEventCreate(&ev[k]));
+  for (int k = 0; k < NK; ++k) ms[k] = 0.0;
+  ads_status st = ADS_OK;
+  for (int it = 0; it < steps && st == ADS_OK; ++it) {
+    c->prof = ev;
+    st = enq_sat_steps<TA>(c, 1);
+    c->prof = nullptr;
+    if (st != ADS_OK) break;
+    st = wait(c, kDefaultTimeout);
+    for (int k = 0; k < NK && st == ADS_OK; ++k) {
+      float f = 0.f;
+      cudaEventElapsedTime(&f, ev[k], ev[k + 1]);
+      ms[k] += f;
+    }
+  }
+  for (int k = 0; k <= NK; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < NK; ++k) ms[k] /= (steps > 0 ? steps : 1);
+  return st;
+}
+
+
+}  // namespace
+
+// =============================================================================
+// exported entry points
+// =============================================================================
+extern "C" {
+
+const char* ads_status_str(ads_status st) {
+  switch (st) {
+    case ADS_OK: return "ok";
+    case ADS_ERR_INVALID_ARG: return "invalid argument";
+    case ADS_ERR_OOM: return "out of device memory";
+    case ADS_ERR_CUDA: return "CUDA error";
+    case ADS_ERR_NONFINITE: return "non-finite value";
+    case ADS_ERR_TIMEOUT: return "timeout";
+    case ADS_ERR_STATE: return "invalid state";
+    case ADS_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown";
+}
+
+const char* ads_last_error(const ads_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv) {
+  if (validate(params, crv) != ADS_OK) return 0;
+  return estimate(params, crv);
+}
+
+void ads_destroy(ads_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const double* K_nodal,
+                    const double* phi_nodal, const double* S0, void* stream, ads_ctx** out) {
+  if (!out) return ADS_ERR_INVALID_ARG;
+  *out = nullptr;
+  ads_status v = validate(params, crv);
+  if (v != ADS_OK) return v;
+  if (!K_nodal) return ADS_ERR_INVALID_ARG;
+  ads_ctx* c = new ads_ctx();
+  c->prm = *params;
+  c->dim = params->dim;
+  c->n = params->n;
+  c->nb = c->n + 2;
+  c->N = c->n;
+  c->m1 = c->N - 1;
+  c->M = c->m1 * c->m1;
+  c->ta = params->ads_dtype;
+  size_t nc = ncoef(c), nn = nnode(c);
+  if (!all_finite(K_nodal, nn, true) || (phi_nodal && !all_finite(phi_nodal, nn, true)) ||
+      (S0 && !all_finite(S0, nc, false))) {
+    delete c;
+    return ADS_ERR_NONFINITE;
+  }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return ADS_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  auto bail = [&](ads_status st) {
+    ads_destroy(c);
+    return st;
+  };
+  const int n = c->n, nb = c->nb;
+  const size_t ta = tsize(c->ta);
+  // stage buffer: the largest host transfer
+  size_t stage = nc > nn ? nc : nn;
+  if (crv) stage = stage > (size_t)kLossRing ? stage : (size_t)kLossRing;
+  stage += 1024;
+  if (crv) {
+    int np = mlp_params(2, crv->width, crv->hidden_layers);
+    if ((size_t)np > stage) stage = np + 16;
+    if ((size_t)c->M > stage) stage = c->M + 16;
+  }
+  if (cudaMallocHost((void**)&c->h_stage, stage * sizeof(double)) != cudaSuccess)
+    return bail(ADS_ERR_OOM);
+  c->h_stage_count = stage;
+  ads_status st;
+#define AL(p, cnt)                                   \
+  if ((st = allocT(c, &(p), (cnt))) != ADS_OK) return bail(st)
+#define ALV(p, bytes)                                \
+  if ((st = alloc(c, &(p), (bytes))) != ADS_OK) return bail(st)
+  // FP64 tables
+  AL(c->B64, 9 * (size_t)n);
+  AL(c->dB64, 9 * (size_t)n);
+  AL(c->l1_64, (size_t)n + 4);
+  AL(c->l2_64, (size_t)n + 4);
+  AL(c->dinv64, (size_t)nb);
+  AL(c->Iw64, (size_t)nb);
+  AL(c->gsrc64, 3 * (size_t)kMaxSrc * n * 3);
+  AL(c->gnode64, 3 * (size_t)kMaxSrc * (n + 1));
+  AL(c->tmp64, 3 * ((size_t)n + 4));
+  AL(c->cen64, 3 * (size_t)kMaxSrc);
+  AL(c->sig64, (size_t)kMaxSrc);
+  {
+    double cen[3 * kMaxSrc] = {0}, sig[kMaxSrc];
+    for (int s = 0; s < kMaxSrc; ++s) sig[s] = 1.0;
+    for (int s = 0; s < params->n_src; ++s) {
+      for (int d = 0; d < 3; ++d) cen[s * 3 + d] = params->src[s].center[d];
+      sig[s] = params->src[s].sigma;
+    }
+    if (cudaMemcpy(c->cen64, cen, sizeof(cen), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->sig64, sig, sizeof(sig), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(c, ADS_ERR_CUDA, "upload sources"));
+  }
+  if (launch_axis_init(n, c->cen64, c->sig64, params->n_src, c->B64, c->dB64, c->l1_64, c->l2_64,
+                       c->dinv64, c->Iw64, c->gsrc64, c->gnode64, c->tmp64, c->stream) != cudaSuccess)
+    return bail(ADS_ERR_CUDA);
+  // ADS-precision copies of the tables
+  if (c->ta == ADS_F64) {
+    c->B = c->B64; c->dB = c->dB64; c->l1 = c->l1_64; c->l2 = c->l2_64; c->dinv = c->dinv64;
+    c->Iw = c->Iw64; c->gsrc = c->gsrc64; c->gnode = c->gnode64;
+  } else {
+    ALV(c->B, 4 * 9 * (size_t)n);
+    ALV(c->dB, 4 * 9 * (size_t)n);
+    ALV(c->l1, 4 * ((size_t)n + 4));
+    ALV(c->l2, 4 * ((size_t)n + 4));
+    ALV(c->dinv, 4 * (size_t)nb);
+    ALV(c->Iw, 4 * (size_t)nb);
+    ALV(c->gsrc, 4 * 3 * (size_t)kMaxSrc * n * 3);
+    ALV(c->gnode, 4 * 3 * (size_t)kMaxSrc * (n + 1));
+    launch_convert<float>(c->B64, (float*)c->B, 9 * (size_t)n, c->stream);
+    launch_convert<float>(c->dB64, (float*)c->dB, 9 * (size_t)n, c->stream);
+    launch_convert<float>(c->l1_64, (float*)c->l1, (size_t)n + 4, c->stream);
+    launch_convert<float>(c->l2_64, (float*)c->l2, (size_t)n + 4, c->stream);
+    launch_convert<float>(c->dinv64, (float*)c->dinv, (size_t)nb, c->stream);
+    launch_convert<float>(c->Iw64, (float*)c->Iw, (size_t)nb, c->stream);
+    launch_convert<float>(c->gsrc64, (float*)c->gsrc, 3 * (size_t)kMaxSrc * n * 3, c->stream);
+    launch_convert<float>(c->gnode64, (float*)c->gnode, 3 * (size_t)kMaxSrc * (n + 1), c->stream);
+  }
+  // fields
+  ALV(c->S[0], ta * nc);
+  ALV(c->S[1], ta * nc);
+  ALV(c->P, ta * nc);
+  ALV(c->K, ta * nn);
+  ALV(c->nodal, ta * nn);
+  if (phi_nodal) ALV(c->phi, ta * nn);
+  c->re = 4;
+  c->nquad = quad_blocks(c->dim, n, c->re);
+  c->nys = ysolve_blocks(c->dim, n);
+  c->ncfl = cfl_blocks(c->dim, n);
+  ALV(c->Xs, ta * 2 * (size_t)c->nquad * nb);
+  AL(c->src_part, (size_t)c->nquad + 1);
+  AL(c->mass_part, (size_t)c->nys + 1);
+  AL(c->cfl_part, 2 * (size_t)c->ncfl + 2);
+  AL(c->stats, 8);
+  AL(c->dt, 1);
+  AL(c->scal, 8);
+  AL(c->flags, 4);
+  if (cudaMemsetAsync(c->P, 0, ta * nc, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->S[0], 0, ta * nc, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->nodal, 0, ta * nn, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->stats, 0, 8 * sizeof(double), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->dt, 0, sizeof(double), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->stream) != cudaSuccess)
+    return bail(fail(c, ADS_ERR_CUDA, "memset"));
+  if ((st = upload(c, c->K, c->ta, K_nodal, nn)) != ADS_OK) return bail(st);
+  if (phi_nodal && (st = upload(c, c->phi, c->ta, phi_nodal, nn)) != ADS_OK) return bail(st);
+  if (S0 && (st = upload(c, c->S[0], c->ta, S0, nc)) != ADS_OK) return bail(st);
+  c->cur = 0;
+  st = c->ta == ADS_F64 ? enq_mass_set<double>(c) : enq_mass_set<float>(c);
+  if (st != ADS_OK) return bail(st);
+
+  if (crv) {
+    c->has_crv = true;
+    c->cp = *crv;
+    c->tc = crv->dtype;
+    const size_t tc = tsize(c->tc);
+    const int m = c->m1;
+    c->nparams = mlp_params(2, crv->width, crv->hidden_layers);
+    c->ld = ((c->M + 63) / 64) * 64;
+    c->ndot = dot_blocks(c->M);
+    c->nbwd = mlp_bwd_blocks(c->M, crv->width, (int)tc);
+    ALV(c->alpha, tc * nn);
+    ALV(c->f, tc * c->M);
+    ALV(c->u, tc * c->M);
+    ALV(c->res, tc * c->M);
+    ALV(c->rhat, tc * c->M);
+    ALV(c->z, tc * c->M);
+    ALV(c->gu, tc * c->M);
+    ALV(c->theta, tc * c->nparams);
+    ALV(c->am, tc * c->nparams);
+    ALV(c->av, tc * c->nparams);
+    ALV(c->grad, tc * c->nparams);
+    ALV(c->gpart, tc * (size_t)c->nbwd * c->nparams);
+    ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
+    double *S64 = nullptr, *inv64 = nullptr;
+    AL(S64, (size_t)m * m);
+    AL(inv64, (size_t)m * m);
+    if (launch_gram_init(c->dim, c->N, S64, inv64, c->stream) != cudaSuccess)
+      return bail(fail(c, ADS_ERR_CUDA, "gram init"));
+    if (c->tc == ADS_F64) {
+      c->Sdst = S64;
+      c->invd = inv64;
+    } else {
+      ALV(c->Sdst, 4 * (size_t)m * m);
+      ALV(c->invd, 4 * (size_t)m * m);
+      launch_convert<float>(S64, (float*)c->Sdst, (size_t)m * m, c->stream);
+      launch_convert<float>(inv64, (float*)c->invd, (size_t)m * m, c->stream);
+    }
+    AL(c->dot_part, (size_t)c->ndot + 1);
+    AL(c->loss, 1);
+    AL(c->loss_log, kLossRing);
+    AL(c->bc, 2);
+    AL(c->lr, 1);
+    AL(c->t, 1);
+    if (cudaMemsetAsync(c->theta, 0, tc * c->nparams, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->am, 0, tc * c->nparams, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->av, 0, tc * c->nparams, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->t, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->loss, 0, sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->loss_log, 0, kLossRing * sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->u, 0, tc * c->M, c->stream) != cudaSuccess)
+      return bail(fail(c, ADS_ERR_CUDA, "memset"));
+  }
+#undef AL
+#undef ALV
+  if ((st = wait(c, kDefaultTimeout)) != ADS_OK) return bail(st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(fail(c, ADS_ERR_CUDA, cudaGetErrorString(e)));
+  *out = c;
+  return ADS_OK;
+}
+
+ads_status ads_sync(ads_ctx* c, double timeout_s) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  return wait(c, timeout_s > 0 ? timeout_s : kDefaultTimeout);
+}
+
+ads_status ads_set_pressure_coeffs(ads_ctx* c, const double* host_p) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!host_p) return ADS_ERR_INVALID_ARG;
+  if (!all_finite(host_p, ncoef(c), false)) return ADS_ERR_NONFINITE;
+  return upload(c, c->P, c->ta, host_p, ncoef(c));
+}
+
+ads_status ads_set_saturation(ads_ctx* c, const double* host_s) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!host_s) return ADS_ERR_INVALID_ARG;
+  if (!all_finite(host_s, ncoef(c), false)) return ADS_ERR_NONFINITE;
+  CA(upload(c, c->S[c->cur], c->ta, host_s, ncoef(c)));
+  return c->ta == ADS_F64 ? enq_mass_set<double>(c) : enq_mass_set<float>(c);
+}
+
+ads_status ads_saturation_step(ads_ctx* c, double dt, int n_sub) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (n_sub < 0 || !std::isfinite(dt)) return ADS_ERR_INVALID_ARG;
+  if (n_sub == 0) return ADS_OK;
+  if (dt > 0) CA(set_scalar(c, c->dt, dt));
+  CK(cudaMemsetAsync(c->stats + 1, 0, 2 * sizeof(double), c->stream));
+  int after = (c->cur + n_sub) & 1;
+  if (c->ta == ADS_F64)
+    return run_graph(c, std::make_tuple(2, n_sub, 0, c->cur, 0LL), &SatBody<double>::body, &n_sub, after);
+  return run_graph(c, std::make_tuple(2, n_sub, 0, c->cur, 0LL), &SatBody<float>::body, &n_sub, after);
+}
+
+ads_status ads_cfl_dt(ads_ctx* c, double cfl, double src_frac, double dt_cap, double* dt_out) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!(cfl > 0) || !(src_frac > 0) || !(dt_cap > 0)) return ADS_ERR_INVALID_ARG;
+  CA(c->ta == ADS_F64 ? enq_cfl<double>(c, cfl, src_frac, dt_cap) : enq_cfl<float>(c, cfl, src_frac, dt_cap));
+  if (dt_out) {
+    CA(read_doubles(c, c->dt, dt_out, 1));
+    if (!std::isfinite(*dt_out) || *dt_out <= 0) return ADS_ERR_NONFINITE;
+  }
+  return ADS_OK;
+}
+
+ads_status crvpinn_num_params(const ads_ctx* c, int* np) {
+  if (!c || !np) return ADS_ERR_INVALID_ARG;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  *np = c->nparams;
+  return ADS_OK;
+}
+
+ads_status crvpinn_set_theta(ads_ctx* c, const double* theta) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  if (!theta) return ADS_ERR_INVALID_ARG;
+  if (!all_finite(theta, c->nparams, false)) return ADS_ERR_NONFINITE;
+  CA(upload(c, c->theta, c->tc, theta, c->nparams));
+  size_t tc = tsize(c->tc);
+  CK(cudaMemsetAsync(c->am, 0, tc * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->av, 0, tc * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->t, 0, sizeof(int), c->stream));
+  return wait(c, kDefaultTimeout);
+}
+
+
+ads_status crvpinn_update_coefficients(ads_ctx* c) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  return dispatch2<CoeffF>(c);
+}
+
+ads_status crvpinn_loss_grad(ads_ctx* c, double* loss_out) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  CA(dispatch2<EvalF>(c));
+  if (loss_out) {
+    CA(read_doubles(c, c->loss, loss_out, 1));
+    if (!std::isfinite(*loss_out)) return ADS_ERR_NONFINITE;
+  }
+  return ADS_OK;
+}
+
+
+static ads_status train_dispatch(ads_ctx* c, int iters) {
+  if (c->tc == ADS_F64 && c->ta == ADS_F64) return TrainRun<double, double>::go(c, iters);
+  if (c->tc == ADS_F32 && c->ta == ADS_F64) return TrainRun<float, double>::go(c, iters);
+  if (c->tc == ADS_F32 && c->ta == ADS_F32) return TrainRun<float, float>::go(c, iters);
+  return TrainRun<double, float>::go(c, iters);
+}
+
+static ads_status pressure_update(ads_ctx* c, int iters, double lr, double* loss_out, bool reset) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  if (iters < 0 || !(lr > 0) || !std::isfinite(lr)) return ADS_ERR_INVALID_ARG;
+  if (reset) {
+    size_t tc = tsize(c->tc);
+    CK(cudaMemsetAsync(c->am, 0, tc * c->nparams, c->stream));
+    CK(cudaMemsetAsync(c->av, 0, tc * c->nparams, c->stream));
+    CK(cudaMemsetAsync(c->t, 0, sizeof(int), c->stream));
+  }
+  CA(set_scalar(c, c->lr, lr));
+  CA(dispatch2<CoeffF>(c));
+  CA(train_dispatch(c, iters));
+  if (loss_out) {
+    CA(read_doubles(c, c->loss, loss_out, 1));
+    if (!std::isfinite(*loss_out)) return ADS_ERR_NONFINITE;
+  }
+  return ADS_OK;
+}
+
+ads_status crvpinn_pretrain(ads_ctx* c, int iters, double lr, double* loss_out) {
+  return pressure_update(c, iters, lr, loss_out, true);
+}
+
+ads_status crvpinn_pressure_update(ads_ctx* c, int iters, double lr, double* loss_out) {
+  return pressure_update(c, iters, lr, loss_out, false);
+}
+
+ads_status ads_project_pressure(ads_ctx* c) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  return dispatch2<ProjF>(c);
+}
+
+static ads_status hybrid_enqueue(ads_ctx* c, const hybrid_params* hp) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  if (!hp || hp->n_sub < 0 || hp->adam_iters < 0 || !(hp->dt > 0) || !std::isfinite(hp->dt) ||
+      !(hp->lr > 0) || (hp->dt_policy != 0 && hp->dt_policy != 1) ||
+      (hp->dt_policy == 1 && (!(hp->cfl > 0) || !(hp->src_frac > 0))))
+    return ADS_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(c->lr, &hp->lr, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (hp->dt_policy == 0)
+    CK(cudaMemcpyAsync(c->dt, &hp->dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->stats + 1, 0, 2 * sizeof(double), c->stream));
+  // graph key: the step's shape (sub-steps, Adam iterations, dt policy) and
+  // the saturation buffer parity; CFL constants are part of the captured work
+  long long key5 = (long long)std::llround(hp->cfl * 1e6) * 1000003LL +
+                   (long long)std::llround(hp->src_frac * 1e6) +
+                   (hp->dt_policy == 1 ? (long long)std::llround(std::log(hp->dt) * 1e6) * 7919LL : 0LL);
+  HybridBody body{*hp};
+  int after = (c->cur + hp->n_sub) & 1;
+  auto key = std::make_tuple(3 + hp->dt_policy, hp->n_sub, hp->adam_iters, c->cur, key5);
+  if (c->tc == ADS_F64 && c->ta == ADS_F64)
+    return run_graph(c, key, &HybridF<double, double>::body, &body, after);
+  if (c->tc == ADS_F32 && c->ta == ADS_F64)
+    return run_graph(c, key, &HybridF<float, double>::body, &body, after);
+  if (c->tc == ADS_F32 && c->ta == ADS_F32)
+    return run_graph(c, key, &HybridF<float, float>::body, &body, after);
+  return run_graph(c, key, &HybridF<double, float>::body, &body, after);
+}
+
+static ads_status hybrid_stats_read(ads_ctx* c, hybrid_stats* out) {
+  double v[4];
+  CA(read_doubles(c, c->dt, &v[0], 1));
+  CA(read_doubles(c, c->loss, &v[1], 1));
+  double m3[3];
+  CA(read_doubles(c, c->stats, m3, 3));
+  out->dt_used = v[0];
+  out->loss_last = v[1];
+  out->mass_err = m3[1];
+  out->mass_total = m3[0];
+  int fl = 0;
+  CA(read_flags(c, &fl));
+  if (fl != 0 || !std::isfinite(v[0]) || !std::isfinite(v[1]))
+    return fail(c, ADS_ERR_NONFINITE, "non-finite loss, step size or mass");
+  return ADS_OK;
+}
+
+ads_status hybrid_step(ads_ctx* c, const hybrid_params* hp, hybrid_stats* stats) {
+  CA(hybrid_enqueue(c, hp));
+  if (stats) return hybrid_stats_read(c, stats);
+  return ADS_OK;
+}
+
+ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
+                             hybrid_stats* stats) {
+  if (!ctxs || n < 0 || !hp) return ADS_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    ads_status s = hybrid_enqueue(ctxs[i], hp);
+    if (s != ADS_OK) return s;
+  }
+  if (stats)
+    for (int i = 0; i < n; ++i) {
+      ads_status s = hybrid_stats_read(ctxs[i], &stats[i]);
+      if (s != ADS_OK) return s;
+    }
+  return ADS_OK;
+}
+
+ads_status ads_kernel_launches(const ads_ctx* c, unsigned long long* count) {
+  if (!c || !count) return ADS_ERR_INVALID_ARG;
+  *count = c->nlaunch;
+  return ADS_OK;
+}
+
+ads_status ads_profile_train(ads_ctx* c, int iters, double* ms_out) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  if (iters < 1 || !ms_out) return ADS_ERR_INVALID_ARG;
+  CA(wait(c, kDefaultTimeout));
+  return c->tc == ADS_F64 ? profile_train_t<double>(c, iters, ms_out)
+                          : profile_train_t<float>(c, iters, ms_out);
+}
+
+ads_status ads_profile_saturation(ads_ctx* c, int steps, double* ms_out) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (steps < 1 || !ms_out) return ADS_ERR_INVALID_ARG;
+  CA(wait(c, kDefaultTimeout));
+  return c->ta == ADS_F64 ? profile_sat_t<double>(c, steps, ms_out)
+                          : profile_sat_t<float>(c, steps, ms_out);
+}
+
+ads_status ads_field_count(const ads_ctx* c, int field, size_t* count) {
+  if (!c || !count) return ADS_ERR_INVALID_ARG;
+  void* p;
+  int dt;
+  return field_info(c, field, &p, count, &dt);
+}
+
+ads_status ads_device_ptr(ads_ctx* c, int field, void** dptr, size_t* count, int* dtype) {
+  if (!c || !dptr || !count || !dtype) return ADS_ERR_INVALID_ARG;
+  return field_info(c, field, dptr, count, dtype);
+}
+
+ads_status ads_get(ads_ctx* c, int field, double* host_dst, size_t count) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!host_dst) return ADS_ERR_INVALID_ARG;
+  void* p;
+  size_t cnt;
+  int dt;
+  CA(field_info(c, field, &p, &cnt, &dt));
+  if (cnt != count) return fail(c, ADS_ERR_INVALID_ARG, "ads_get: count mismatch");
+  if (dt == ADS_F64) {
+    CK(cudaMemcpyAsync(host_dst, p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return wait(c, kDefaultTimeout);
+  }
+  double* tmp = nullptr;
+  CK(cudaMallocAsync((void**)&tmp, cnt * sizeof(double), c->stream));
+  CK(launch_to_double<float>((const float*)p, tmp, cnt, c->stream));
+  CK(cudaMemcpyAsync(host_dst, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaFreeAsync(tmp, c->stream));
+  return wait(c, kDefaultTimeout);
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Shared device helpers for the adsgb kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define ADS_HD __host__ __device__ __forceinline__
+#define ADS_D __device__ __forceinline__
+
+namespace adsgb {
+
+constexpr int kMaxSrc = 8;
+constexpr int kLossRing = 4096;
+
+// Gauss-Legendre rule with 3 points on [0,1]: 0.5 -+ sqrt(15)/10, 0.5;
+// weights 5/18, 8/18, 5/18.
+ADS_HD double gauss_x(int q) {
+  return q == 0 ? 0.5 - 0.3872983346207416885 : (q == 1 ? 0.5 : 0.5 + 0.3872983346207416885);
+}
+ADS_HD double gauss_w(int q) { return q == 1 ? 8.0 / 18.0 : 5.0 / 18.0; }
+
+// Scalar parameters needed by the saturation and collocation kernels.
+struct PhysParams {
+  int dim, n;
+  double h;
+  double phi;
+  double inv_mu_w, inv_mu_g, rho_w, rho_g;
+  double grav, grav_sign, kz_ratio;
+  int n_src;
+  double src_rate[kMaxSrc];
+  int src_kind[kMaxSrc];
+};
+
+template <typename T>
+ADS_D T clamp01(T s) { return s < T(0) ? T(0) : (s > T(1) ? T(1) : s); }
+
+// tanh from the exponential identity tanh|x| = (1 - e^{-2|x|}) / (1 + e^{-2|x|})
+// with the hardware base-2 exponential; absolute error a few 1e-7.
+ADS_D float tanh_f32(float x) {
+  float ax = fabsf(x);
+  float t;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(-2.8853900817779268f * ax));  // -2 log2(e) |x|
+  float r = __fdividef(1.0f - t, 1.0f + t);
+  return copysignf(r, x);
+}
+ADS_D double tanh_any(double x) { return tanh(x); }
+ADS_D float tanh_any(float x) { return tanh_f32(x); }
+
+// Deterministic block sum of doubles (blockDim.x multiple of 32, <= 1024).
+ADS_D double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r += sh[i];
+  }
+  return r;  // valid in thread 0
+}
+
+ADS_D double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = sh[0];
+    for (int i = 1; i < nw; ++i) r = fmax(r, sh[i]);
+  }
+  return r;
+}
+
+}  // namespace adsgb

@@ -1,0 +1,325 @@
+// CRVPINN pressure kernels (Sec. 5 of the paper): nodal coefficients
+// (Eq. 23b), the residual stencil (Eqs. 24-25) and its adjoint, the Gram
+// matrix inverse (Eqs. 26-28) applied by fast diagonalisation, and the loss.
+//
+// G = h^-2 (I (x) T + T (x) I), T = tridiag(-1, 2, -1) = S Lambda S with the
+// orthonormal sine matrix S_ik = sqrt(2/N) sin(pi i k / N).  Hence
+//   G^-1 r = h^2 (I (x) S) (T (x) I + I (x) Lambda)^-1 (I (x) S) r:
+// a sine transform along x (a dense (N-1)^2 GEMM), one shifted tridiagonal
+// solve (Lambda_k + T) along y per mode k, and the inverse transform.  The
+// paper's "LU once, substitutions per iteration" (Eq. 28) becomes: the
+// shifted tridiagonal LU factors are computed once (FP64), the substitutions
+// run every iteration.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace adsgb {
+
+// ---------------------------------------------------------------------------
+// nodal coefficients alpha = lambda(S) K, f = D+ . (g K rho lambda) - q  (2D)
+// ---------------------------------------------------------------------------
+// Value of a quadratic C1 spline at knot i of an open uniform knot vector:
+// c_0 at the left end, c_{n+1} at the right end, (c_i + c_{i+1})/2 inside.
+__device__ __forceinline__ void knot_weights(int i, int n, int& i0, double& w0, double& w1) {
+  if (i == 0) { i0 = 0; w0 = 1.0; w1 = 0.0; }
+  else if (i == n) { i0 = n; w0 = 0.0; w1 = 1.0; }
+  else { i0 = i; w0 = 0.5; w1 = 0.5; }
+}
+
+template <typename T, typename TA>
+__device__ __forceinline__ double nodal_sat_2d(const CrvArgs<T, TA>& a, int j, int i) {
+  const int n = a.N, nb = n + 2;
+  int i0, j0;
+  double wx0, wx1, wy0, wy1;
+  knot_weights(i, n, i0, wx0, wx1);
+  knot_weights(j, n, j0, wy0, wy1);
+  const TA* r0 = a.S + (size_t)j0 * nb + i0;
+  const TA* r1 = r0 + nb;
+  double v = wy0 * (wx0 * (double)r0[0] + wx1 * (double)r0[1]) +
+             wy1 * (wx0 * (double)r1[0] + wx1 * (double)r1[1]);
+  return v;
+}
+
+template <typename T, typename TA>
+__global__ void k_crv_coeffs_2d(CrvArgs<T, TA> a) {
+  const int N = a.N, n1 = N + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n1 * n1) return;
+  const int j = t / n1, i = t % n1;
+  double s = nodal_sat_2d(a, j, i);
+  s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+  double lw = (1.0 - s) * a.inv_mu_w, lg = s * a.inv_mu_g;
+  double K = (double)a.K[(size_t)j * n1 + i];
+  a.alpha[t] = (T)((lw + lg) * K);
+  if (i >= 1 && i <= N - 1 && j >= 1 && j <= N - 1) {
+    // forward difference along the vertical (y) of F = -g K (rho_w lw + rho_g lg)
+    double s1 = nodal_sat_2d(a, j + 1, i);
+    s1 = s1 < 0.0 ? 0.0 : (s1 > 1.0 ? 1.0 : s1);
+    double K1 = (double)a.K[(size_t)(j + 1) * n1 + i];
+    double F0 = -a.grav * K * (a.rho_w * lw + a.rho_g * lg);
+    double F1 = -a.grav * K1 * (a.rho_w * (1.0 - s1) * a.inv_mu_w + a.rho_g * s1 * a.inv_mu_g);
+    double q = 0.0;
+    for (int k = 0; k < a.n_src; ++k) {
+      double g = a.rate[k] * (double)a.ax.gnode[(size_t)(0 * kMaxSrc + k) * n1 + i] *
+                 (double)a.ax.gnode[(size_t)(1 * kMaxSrc + k) * n1 + j];
+      q += (a.kind[k] == 0) ? g : -g;
+    }
+    a.f[(size_t)(j - 1) * (N - 1) + (i - 1)] = (T)((F1 - F0) * (double)N - q);
+  }
+}
+
+template <typename T, typename TA>
+cudaError_t launch_crv_coeffs(const CrvArgs<T, TA>& a, cudaStream_t st) {
+  if (a.dim != 2) return cudaErrorNotSupported;
+  int tot = (a.N + 1) * (a.N + 1);
+  k_crv_coeffs_2d<T, TA><<<(tot + 255) / 256, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// stencil: out_k = scale * sum_dir [alpha_{k-e}(v_k - v_{k-e}) - alpha_k(v_{k+e} - v_k)]
+//                  + h2 * f_k  (f nullable), v = 0 on the boundary.
+// RES = A u + h^2 f uses scale 1; the adjoint dL/du = 2 A z uses scale 2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__ alpha,
+                                                    const T* __restrict__ v, const T* __restrict__ f,
+                                                    T h2, T scale, T* __restrict__ out) {
+  const int m = N - 1, n1 = N + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  const int jj = t / m, ii = t % m;  // interior index
+  const int j = jj + 1, i = ii + 1;  // node index
+  T c = v[t];
+  T w = ii > 0 ? v[t - 1] : T(0);
+  T e = ii < m - 1 ? v[t + 1] : T(0);
+  T s = jj > 0 ? v[t - m] : T(0);
+  T nn = jj < m - 1 ? v[t + m] : T(0);
+  T ac = alpha[(size_t)j * n1 + i];
+  T aw = alpha[(size_t)j * n1 + i - 1];
+  T as = alpha[(size_t)(j - 1) * n1 + i];
+  T r = aw * (c - w) - ac * (e - c) + as * (c - s) - ac * (nn - c);
+  r *= scale;
+  if (f) r += h2 * f[t];
+  out[t] = r;
+}
+
+template <typename T>
+cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, const T* f, T h2,
+                           T scale, T* out, cudaStream_t st) {
+  if (dim != 2) return cudaErrorNotSupported;
+  int m = (N - 1) * (N - 1);
+  if (m <= 0) return cudaSuccess;
+  k_stencil_2d<T><<<(m + 255) / 256, 256, 0, st>>>(N, alpha, u, f, h2, scale, out);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TA>
+__global__ void k_embed_2d(int N, const T* u, TA* nodal) {
+  const int n1 = N + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n1 * n1) return;
+  const int j = t / n1, i = t % n1;
+  TA v = TA(0);
+  if (i >= 1 && i <= N - 1 && j >= 1 && j <= N - 1) v = (TA)u[(size_t)(j - 1) * (N - 1) + (i - 1)];
+  nodal[t] = v;
+}
+
+template <typename T, typename TA>
+cudaError_t launch_embed(int dim, int N, const T* u, TA* nodal, cudaStream_t st) {
+  if (dim != 2) return cudaErrorNotSupported;
+  int tot = (N + 1) * (N + 1);
+  k_embed_2d<T, TA><<<(tot + 255) / 256, 256, 0, st>>>(N, u, nodal);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gram tables (FP64, once): S (m x m), inverse pivots of (Lambda_k + T)
+// stored [j][k] so that a thread per mode k reads coalesced rows.
+// ---------------------------------------------------------------------------
+__global__ void k_gram_sine(int N, double* S) {
+  const int m = N - 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  const int i = t / m + 1, k = t % m + 1;
+  long long ik = (long long)i * k % (2LL * N);  // sin(pi ik/N) is 2N-periodic in ik
+  S[t] = sqrt(2.0 / N) * sinpi((double)ik / (double)N);
+}
+
+__global__ void k_gram_pivots(int N, double* invd) {
+  const int m = N - 1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  double sk = sinpi((double)(k + 1) / (2.0 * N));
+  double b = 2.0 + 4.0 * sk * sk;
+  double d = b;
+  for (int j = 0; j < m; ++j) {
+    invd[(size_t)j * m + k] = 1.0 / d;
+    d = b - 1.0 / d;
+  }
+}
+
+cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStream_t st) {
+  if (dim != 2) return cudaErrorNotSupported;
+  int m = N - 1;
+  k_gram_sine<<<(m * m + 255) / 256, 256, 0, st>>>(N, Sdst);
+  k_gram_pivots<<<(m + 127) / 128, 128, 0, st>>>(N, invd);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// C = alpha * A * B (row-major, M x K times K x Nn), 64x64 tiles, 4x4 per
+// thread, register-blocked SIMT (the sine transform of the Gram inverse).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(int M, int Nn, int K, const T* __restrict__ A, int lda,
+                                              const T* __restrict__ B, int ldb, T* __restrict__ C,
+                                              int ldc, T alpha) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  T acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      int mm = e / BK, kk = e % BK;
+      int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : T(0);
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      int kk = e / BN, nn = e % BN;
+      int gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < K && gn < Nn) ? B[(size_t)gk * ldb + gn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gn = n0 + tx * 4 + j;
+      if (gn < Nn) C[(size_t)gm * ldc + gn] = alpha * acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_gemm(int M, int Nn, int K, const T* A, int lda, const T* B, int ldb, T* C,
+                        int ldc, T alpha, cudaStream_t st) {
+  dim3 grid((Nn + 63) / 64, (M + 63) / 64);
+  k_gemm<T><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha);
+  return cudaGetLastError();
+}
+
+// (Lambda_k + T) x = r along rows j for every column k: forward elimination
+// then back substitution with the precomputed inverse pivots.
+template <typename T>
+__global__ void __launch_bounds__(128) k_tridiag_cols(int m, int ncols, const T* __restrict__ invd,
+                                                      T* X) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ncols) return;
+  T y = T(0);
+  for (int j = 0; j < m; ++j) {
+    T v = X[(size_t)j * ncols + k] + y * (j > 0 ? invd[(size_t)(j - 1) * ncols + k] : T(0));
+    X[(size_t)j * ncols + k] = v;
+    y = v;
+  }
+  T x = T(0);
+  for (int j = m - 1; j >= 0; --j) {
+    T v = (X[(size_t)j * ncols + k] + x) * invd[(size_t)j * ncols + k];
+    X[(size_t)j * ncols + k] = v;
+    x = v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaStream_t st) {
+  k_tridiag_cols<T><<<(ncols + 127) / 128, 128, 0, st>>>(nrows, ncols, invd, X);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// loss = r . z (FP64 accumulation, fixed-order two-stage reduction)
+// ---------------------------------------------------------------------------
+int dot_blocks(int n) {
+  int b = (n + 2047) / 2048;
+  return b < 1 ? 1 : (b > 1024 ? 1024 : b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_partial(const T* a, const T* b, int n, double* part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  double tot = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <typename T>
+cudaError_t launch_dot_partial(const T* a, const T* b, int n, double* part, int nblk,
+                               cudaStream_t st) {
+  k_dot_partial<T><<<nblk, 256, 0, st>>>(a, b, n, part);
+  return cudaGetLastError();
+}
+
+__global__ void k_loss_finalize(const double* part, int nblk, double* loss, double* log, int* t,
+                                double* bc, int* flags, int bump) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < nblk; ++i) s += part[i];
+  *loss = s;
+  if (!isfinite(s)) flags[0] |= 4;
+  if (bump) {
+    int tt = *t + 1;
+    *t = tt;
+    log[(tt - 1) % kLossRing] = s;
+    bc[0] = 1.0 / (1.0 - pow(0.9, (double)tt));
+    bc[1] = 1.0 / (1.0 - pow(0.999, (double)tt));
+  }
+}
+
+cudaError_t launch_loss_finalize(const double* part, int nblk, double* loss, double* loss_log,
+                                 int* t, double* bc, int* flags, int bump_t, cudaStream_t st) {
+  k_loss_finalize<<<1, 32, 0, st>>>(part, nblk, loss, loss_log, t, bc, flags, bump_t);
+  return cudaGetLastError();
+}
+
+#define CRV_INST(T, TA)                                                                          \
+  template cudaError_t launch_crv_coeffs<T, TA>(const CrvArgs<T, TA>&, cudaStream_t);            \
+  template cudaError_t launch_embed<T, TA>(int, int, const T*, TA*, cudaStream_t);
+CRV_INST(double, double)
+CRV_INST(float, double)
+CRV_INST(float, float)
+CRV_INST(double, float)
+
+#define CRV_INST1(T)                                                                              \
+  template cudaError_t launch_stencil<T>(int, int, T, const T*, const T*, const T*, T, T, T*,    \
+                                         cudaStream_t);                                           \
+  template cudaError_t launch_gemm<T>(int, int, int, const T*, int, const T*, int, T*, int, T,   \
+                                      cudaStream_t);                                              \
+  template cudaError_t launch_tridiag_cols<T>(int, int, const T*, T*, cudaStream_t);             \
+  template cudaError_t launch_dot_partial<T>(const T*, const T*, int, double*, int, cudaStream_t);
+CRV_INST1(double)
+CRV_INST1(float)
+
+}  // namespace adsgb

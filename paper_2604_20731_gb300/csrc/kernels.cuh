@@ -1,0 +1,142 @@
+// Kernel argument structs and launcher declarations shared by the adsgb
+// translation units.  Every launcher enqueues on the given stream and
+// returns the launch status.
+#pragma once
+#include "common.cuh"
+
+namespace adsgb {
+
+// ---------------------------------------------------------------------------
+// per-axis tables (identical axes: uniform open knot vector, degree 2)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct AxisTabs {
+  const T* B;      // [n][3 local fn][3 gauss pt]  basis values
+  const T* dB;     // [n][3][3]                    d/dx (physical)
+  const T* l1;     // [n+4] LDL^T of the 1D mass matrix: L[l][l-1] (0-padded)
+  const T* l2;     // [n+4] L[l][l-2]
+  const T* dinv;   // [n+2] 1/D[l]
+  const T* Iw;     // [n+2] int B_l
+  const T* gsrc;   // [3 axes][kMaxSrc][n][3] per-axis Gaussian factor at Gauss points
+  const T* gnode;  // [3 axes][kMaxSrc][n+1] per-axis Gaussian factor at nodes
+};
+
+template <typename T>
+struct QuadArgs {
+  int dim, n, nb;        // nb = n + 2
+  T h;
+  const T* S;            // coefficients (n+2)^d
+  const T* P;            // coefficients (n+2)^d
+  const T* K;            // nodal (n+1)^d
+  const T* phi;          // nodal (n+1)^d or nullptr
+  T phi_c;
+  const T* nodal;        // projection: nodal values (n+1)^d
+  AxisTabs<T> ax;
+  int n_src;
+  T rate[kMaxSrc];
+  int kind[kMaxSrc];
+  T inv_mu_g, inv_mu_w;
+  T grav_term;           // grav_sign * rho_g * grav
+  T kz;                  // vertical permeability ratio (3D)
+  const double* dt;      // device step size
+};
+
+// ---- init (FP64, one-off) ----
+cudaError_t launch_axis_init(int n, const double* centers /*[kMaxSrc][3]*/, const double* sigmas,
+                             int n_src, double* B, double* dB, double* l1, double* l2, double* dinv,
+                             double* Iw, double* gsrc, double* gnode, double* tmp /*3(n+4)*/,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_convert(const double* src, T* dst, size_t count, cudaStream_t st);
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream_t st);
+
+// ---- saturation step ----
+// Fused quadrature (MODE 0: saturation RHS of Eq. 10b; MODE 1: L2
+// projection RHS of nodal values) + x-direction mass solve for a strip of
+// `re` element rows.  Rows shared with the next strip go to `Xs`.
+template <typename T>
+cudaError_t launch_quad_xsolve(const QuadArgs<T>& a, int mode, int re, T* Xm, T* Xs,
+                               double* src_part, cudaStream_t st);
+// y-direction (and z in 3D) sweep adding the spill rows; writes the solution
+// over Xm and per-block partials of int S.
+template <typename T>
+cudaError_t launch_ysolve(const QuadArgs<T>& a, int re, T* X, const T* Xs, double* mass_part,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_zsolve(const QuadArgs<T>& a, T* X, double* mass_part, cudaStream_t st);
+int quad_blocks(int dim, int n, int re);
+int ysolve_blocks(int dim, int n);
+// mass bookkeeping: mode 0 = set int S from partials; mode 1 = step update
+cudaError_t launch_mass_finalize(const double* mass_part, int nmass, const double* src_part,
+                                 int nsrc, int mode, double* stats, int* flags, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mass(const QuadArgs<T>& a, const T* S, double* mass_part, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cfl(const QuadArgs<T>& a, double* part /*2 per block*/, cudaStream_t st);
+int cfl_blocks(int dim, int n);
+cudaError_t launch_cfl_finalize(const double* part, int nblk, double cfl, double src_frac,
+                                double dt_cap, double h, double* dt, int* flags, cudaStream_t st);
+
+// ---- CRVPINN ----
+template <typename T, typename TA>
+struct CrvArgs {
+  int dim, N, M;         // N intervals, M = (N-1)^dim interior nodes
+  T h;
+  const TA* S;           // saturation coefficients (ADS precision)
+  const TA* K;           // nodal permeability (ADS precision)
+  AxisTabs<TA> ax;       // for the nodal source factors
+  int n_src;
+  double rate[kMaxSrc];
+  int kind[kMaxSrc];
+  double inv_mu_g, inv_mu_w, rho_w, rho_g, grav, kz;
+  T* alpha;              // (N+1)^dim
+  T* f;                  // M
+};
+template <typename T, typename TA>
+cudaError_t launch_crv_coeffs(const CrvArgs<T, TA>& a, cudaStream_t st);
+// RES = A u + h^2 f (fwd = 1) or g = 2 A z (fwd = 0)
+template <typename T>
+cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, const T* f, T h2,
+                           T scale, T* out, cudaStream_t st);
+// nodal array (N+1)^dim (ADS precision) from interior values (boundary 0)
+template <typename T, typename TA>
+cudaError_t launch_embed(int dim, int N, const T* u, TA* nodal, cudaStream_t st);
+
+// Gram: sine transform matrix, per-mode tridiagonal inverse pivots
+cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gemm(int M, int Nn, int K, const T* A, int lda, const T* B, int ldb, T* C,
+                        int ldc, T alpha, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dot_partial(const T* a, const T* b, int n, double* part, int nblk, cudaStream_t st);
+int dot_blocks(int n);
+// loss finalize: loss = sum(part); writes loss, log ring, t += 1 and the
+// Adam bias corrections
+cudaError_t launch_loss_finalize(const double* part, int nblk, double* loss, double* loss_log,
+                                 int* t, double* bc, int* flags, int bump_t, cudaStream_t st);
+
+// ---- MLP ----
+template <typename T>
+struct MlpArgs {
+  int din, width, npts, N, ld;  // ld: leading dimension of stored activations
+  const T* theta;
+  T* u;                         // [npts]
+  T* acts;                      // [4][width][ld]
+  const T* gu;                  // [npts] dL/du (backward)
+  T* gpart;                     // [nblk][nparams]
+  int nparams;
+};
+template <typename T>
+cudaError_t launch_mlp_fwd(const MlpArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mlp_bwd(const MlpArgs<T>& a, int nblk, cudaStream_t st);
+int mlp_bwd_blocks(int npts, int width, int elem_bytes);
+template <typename T>
+cudaError_t launch_grad_reduce_adam(const T* gpart, int nblk, int nparams, T* grad, T* theta,
+                                    T* m, T* v, const double* bc, const double* lr, int do_update,
+                                    cudaStream_t st);
+
+}  // namespace adsgb

@@ -1,0 +1,201 @@
+"""Python binding of the hybrid IGA-ADS + CRVPINN solver (one context per
+scenario).  Argument marshalling only: every step runs in libadsgb's CUDA
+kernels; the names follow the C ABI in include/adsgb.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import _lib as L
+
+_DT = {"f64": L.ADS_F64, "f32": L.ADS_F32}
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_params(sc, ads_dtype: str = "f64") -> L.ads_params:
+    p = L.ads_params()
+    p.dim, p.n = sc.dim, sc.n
+    p.phi = float(sc.phi)
+    p.mu_w, p.mu_g, p.rho_w, p.rho_g = sc.mu_w, sc.mu_g, sc.rho_w, sc.rho_g
+    p.grav, p.grav_sign, p.kz_ratio = sc.grav, sc.grav_sign, sc.kz_ratio
+    if len(sc.sources) > L.MAX_SOURCES:
+        raise ValueError("too many sources")
+    p.n_src = len(sc.sources)
+    for i, s in enumerate(sc.sources):
+        c = list(s.center) + [0.0] * (3 - len(s.center))
+        p.src[i].center[:] = c[:3]
+        p.src[i].sigma, p.src[i].rate, p.src[i].kind = s.sigma, s.rate, s.kind
+    p.ads_dtype = _DT[ads_dtype]
+    return p
+
+
+class HybridSolver:
+    """One scenario resident on the GPU: saturation, pressure, network, Adam."""
+
+    def __init__(self, sc, width: Optional[int] = 64, crv_dtype: str = "f32",
+                 ads_dtype: str = "f64", stream=None):
+        self.lib = L.load()
+        self.sc = sc
+        self.params = make_params(sc, ads_dtype)
+        self.crv = None
+        if width is not None:
+            self.crv = L.crvpinn_params(width, 4, _DT[crv_dtype])
+        K = np.ascontiguousarray(sc.K, dtype=np.float64)
+        phi = None if sc.phi_map is None else np.ascontiguousarray(sc.phi_map, dtype=np.float64)
+        S0 = np.ascontiguousarray(sc.S0_or_zero(), dtype=np.float64)
+        handle = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = self.lib.ads_init(C.byref(self.params), C.byref(self.crv) if self.crv else None,
+                               _dptr(K), _dptr(phi) if phi is not None else None, _dptr(S0),
+                               st, C.byref(handle))
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, "ads_init")
+        self.ctx = handle
+        self.n = sc.n
+        self.dim = sc.dim
+
+    # ---- helpers ----
+    def _check(self, rc, where):
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, where, self.lib.ads_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ads_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def count(self, field: str) -> int:
+        c = C.c_size_t()
+        self._check(self.lib.ads_field_count(self.ctx, L.FIELD[field], C.byref(c)), "ads_field_count")
+        return c.value
+
+    def get(self, field: str) -> np.ndarray:
+        n = self.count(field)
+        out = np.empty(n, dtype=np.float64)
+        self._check(self.lib.ads_get(self.ctx, L.FIELD[field], _dptr(out), n), f"ads_get({field})")
+        d = self.dim
+        if field in ("S", "P"):
+            return out.reshape((self.n + 2,) * d)
+        if field in ("K", "ALPHA"):
+            return out.reshape((self.n + 1,) * d)
+        return out
+
+    def device_ptr(self, field: str):
+        p, c, dt = C.c_void_p(), C.c_size_t(), C.c_int()
+        self._check(self.lib.ads_device_ptr(self.ctx, L.FIELD[field], C.byref(p), C.byref(c),
+                                            C.byref(dt)), "ads_device_ptr")
+        return p.value, c.value, dt.value
+
+    @property
+    def nparams(self) -> int:
+        v = C.c_int()
+        self._check(self.lib.crvpinn_num_params(self.ctx, C.byref(v)), "crvpinn_num_params")
+        return v.value
+
+    # ---- entry points ----
+    def set_theta(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        if th.size != self.nparams:
+            raise ValueError("theta has the wrong size")
+        self._check(self.lib.crvpinn_set_theta(self.ctx, _dptr(th)), "crvpinn_set_theta")
+
+    def set_pressure(self, P):
+        a = np.ascontiguousarray(P, dtype=np.float64)
+        self._check(self.lib.ads_set_pressure_coeffs(self.ctx, _dptr(a)), "ads_set_pressure_coeffs")
+
+    def set_saturation(self, S):
+        a = np.ascontiguousarray(S, dtype=np.float64)
+        self._check(self.lib.ads_set_saturation(self.ctx, _dptr(a)), "ads_set_saturation")
+
+    def saturation_step(self, dt: float, n_sub: int = 1):
+        self._check(self.lib.ads_saturation_step(self.ctx, float(dt), int(n_sub)), "ads_saturation_step")
+
+    def cfl_dt(self, cfl=0.1, src_frac=0.05, dt_cap=1e30) -> float:
+        out = C.c_double()
+        self._check(self.lib.ads_cfl_dt(self.ctx, cfl, src_frac, dt_cap, C.byref(out)), "ads_cfl_dt")
+        return out.value
+
+    def update_coefficients(self):
+        self._check(self.lib.crvpinn_update_coefficients(self.ctx), "crvpinn_update_coefficients")
+
+    def loss_grad(self) -> float:
+        out = C.c_double()
+        self._check(self.lib.crvpinn_loss_grad(self.ctx, C.byref(out)), "crvpinn_loss_grad")
+        return out.value
+
+    def pretrain(self, iters: int, lr: float) -> float:
+        out = C.c_double()
+        self._check(self.lib.crvpinn_pretrain(self.ctx, int(iters), float(lr), C.byref(out)),
+                    "crvpinn_pretrain")
+        return out.value
+
+    def pressure_update(self, iters: int, lr: float, sync: bool = True):
+        out = C.c_double()
+        self._check(self.lib.crvpinn_pressure_update(self.ctx, int(iters), float(lr),
+                                                     C.byref(out) if sync else None),
+                    "crvpinn_pressure_update")
+        return out.value if sync else None
+
+    def project_pressure(self):
+        self._check(self.lib.ads_project_pressure(self.ctx), "ads_project_pressure")
+
+    @staticmethod
+    def hybrid_params(n_sub=10, dt=1.0, dt_policy=1, cfl=0.1, src_frac=0.05, adam_iters=100,
+                      lr=1e-3) -> L.hybrid_params:
+        return L.hybrid_params(int(n_sub), float(dt), int(dt_policy), float(cfl), float(src_frac),
+                               int(adam_iters), float(lr))
+
+    def hybrid_step(self, hp: L.hybrid_params, stats: bool = True):
+        s = L.hybrid_stats()
+        self._check(self.lib.hybrid_step(self.ctx, C.byref(hp), C.byref(s) if stats else None),
+                    "hybrid_step")
+        if stats:
+            return dict(dt_used=s.dt_used, loss_last=s.loss_last, mass_err=s.mass_err,
+                        mass_total=s.mass_total)
+        return None
+
+    def kernel_launches(self) -> int:
+        v = C.c_ulonglong()
+        self._check(self.lib.ads_kernel_launches(self.ctx, C.byref(v)), "ads_kernel_launches")
+        return v.value
+
+    def profile_train(self, iters: int = 20) -> dict:
+        ms = np.zeros(len(L.TRAIN_KERNELS))
+        self._check(self.lib.ads_profile_train(self.ctx, int(iters), _dptr(ms)), "ads_profile_train")
+        return dict(zip(L.TRAIN_KERNELS, ms.tolist()))
+
+    def profile_saturation(self, steps: int = 10) -> dict:
+        ms = np.zeros(len(L.SAT_KERNELS))
+        self._check(self.lib.ads_profile_saturation(self.ctx, int(steps), _dptr(ms)),
+                    "ads_profile_saturation")
+        return dict(zip(L.SAT_KERNELS, ms.tolist()))
+
+    def sync(self, timeout_s: float = 600.0):
+        self._check(self.lib.ads_sync(self.ctx, timeout_s), "ads_sync")
+
+
+def hybrid_step_batch(solvers, hp: L.hybrid_params, stats: bool = False):
+    lib = L.load()
+    arr = (C.c_void_p * len(solvers))(*[s.ctx for s in solvers])
+    out = (L.hybrid_stats * len(solvers))() if stats else None
+    rc = lib.hybrid_step_batch(arr, len(solvers), C.byref(hp), out)
+    if rc != L.ADS_OK:
+        raise L.AdsError(rc, "hybrid_step_batch")
+    if stats:
+        return [dict(dt_used=s.dt_used, loss_last=s.loss_last, mass_err=s.mass_err,
+                     mass_total=s.mass_total) for s in out]
+    return None

@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/adsgb.h declares, and its pure-host helpers behave."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "adsgb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\*?([a-z_][a-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("typedef")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_20731_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_parses():
+    names = declared_functions()
+    for must in ("ads_init", "ads_saturation_step", "crvpinn_pretrain", "crvpinn_pressure_update",
+                 "hybrid_step", "ads_destroy", "ads_get"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2604_20731_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in adsgb.h but not exported"
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature"
+
+
+def test_status_strings(lib):
+    assert lib.ads_status_str(0) == b"ok"
+    assert lib.ads_status_str(5) == b"timeout"
+    assert lib.ads_status_str(99) == b"unknown"
+
+
+def test_struct_layouts_match_header():
+    from paper_2604_20731_gb300 import _lib
+    # ads_source: 3 doubles + sigma + rate + int (padded to 8)
+    assert C.sizeof(_lib.ads_source) == 48
+    assert C.sizeof(_lib.crvpinn_params) == 12
+    assert C.sizeof(_lib.hybrid_stats) == 32
+
+
+def test_hbm_estimate_and_validation(lib):
+    from paper_2604_20731_gb300 import _lib
+    from paper_2604_20731_gb300 import scenario as scn
+    from paper_2604_20731_gb300.solver import make_params
+    sc = scn.make_scenario(2, 256)
+    p = make_params(sc, "f64")
+    crv = _lib.crvpinn_params(64, 4, _lib.ADS_F32)
+    b = lib.ads_hbm_estimate(C.byref(p), C.byref(crv))
+    assert 10e6 < b < 2e9
+    b0 = lib.ads_hbm_estimate(C.byref(p), None)
+    assert 0 < b0 < b
+    p.n = 1  # invalid
+    assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) == 0
+    p.n = 256
+    crv.width = 96  # unsupported width
+    assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) == 0
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
+    """Argument validation happens before any CUDA call."""
+    from paper_2604_20731_gb300 import _lib
+    from paper_2604_20731_gb300 import scenario as scn
+    from paper_2604_20731_gb300.solver import make_params
+    sc = scn.make_scenario(2, 8)
+    p = make_params(sc)
+    out = C.c_void_p()
+    assert lib.ads_init(C.byref(p), None, None, None, None, None, C.byref(out)) == 1  # K missing
+    p.dim = 4
+    K = (C.c_double * 81)(*([1.0] * 81))
+    assert lib.ads_init(C.byref(p), None, K, None, None, None, C.byref(out)) == 7
+    p.dim = 2
+    p.mu_g = -1.0
+    assert lib.ads_init(C.byref(p), None, K, None, None, None, C.byref(out)) == 1
+    p.mu_g = 1.0
+    K[3] = float("nan")
+    assert lib.ads_init(C.byref(p), None, K, None, None, None, C.byref(out)) == 4
+    assert not out.value
