@@ -175,7 +175,7 @@ def measured_peaks():
 def traffic_record(kernel):
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
     source is unchanged since the capture (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     with open(p) as f:
