@@ -219,6 +219,30 @@ ads_status ads_field_count(const ads_ctx* ctx, int field, size_t* count);
 ads_status ads_device_ptr(ads_ctx* ctx, int field, void** dptr, size_t* count, int* dtype);
 ads_status ads_sync(ads_ctx* ctx, double timeout_s);
 
+/* ---- saturation step without allocation (no counterpart in the paper) -------
+ * For callers that cannot call cudaMalloc -- e.g. a serving process whose own
+ * allocator owns the whole device memory budget, or a latency-critical loop
+ * that must not risk the device synchronisation cudaMalloc/cudaFree can imply.
+ * One explicit saturation step S_out = M^-1 R(S, p) (the same kernels as
+ * ads_saturation_step), with no context and no allocation: the caller passes
+ * device pointers to its inputs and output (FP64, layouts as above:
+ * d_K (n+1)^2, d_phi (n+1)^2 or NULL for params->phi, d_S, d_P and d_S_out
+ * (n+2)^2; d_S_out must not be d_S) and a step size dt > 0.  All working
+ * memory lives in one fixed 4 MiB device array inside the library, reserved on
+ * every GPU that loads the library until the process exits; meshes up to
+ * n = 512 fit, larger n returns ADS_ERR_INVALID_ARG.  2D, ads_dtype = ADS_F64
+ * only (else ADS_ERR_UNSUPPORTED).  The first call on a device looks up that
+ * array's device address (set-up), so make the first call before any stream
+ * capture.  Every call shares the one array: calls that may overlap on the
+ * GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Nothing in the array needs to start at zero;
+ * each call rewrites what it reads.  Work is enqueued on `stream` (cudaStream_t,
+ * NULL = legacy default stream); the call returns after enqueueing. */
+ads_status ads_saturation_step_noalloc(const ads_params* params, const double* d_K,
+                                       const double* d_phi, const double* d_S,
+                                       const double* d_P, double dt, double* d_S_out,
+                                       void* stream);
+
 /* ---- diagnostics (no counterpart in the paper) ------------------------------
  * ads_kernel_launches: number of library kernels enqueued on this context so
  * far (a graph replay counts the kernels it contains).

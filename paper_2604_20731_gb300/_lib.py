@@ -76,6 +76,8 @@ SIGNATURES = {
     "ads_device_ptr": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_size_t),
                                  C.POINTER(C.c_int)]),
     "ads_sync": (C.c_int, [_P, C.c_double]),
+    "ads_saturation_step_noalloc": (C.c_int, [C.POINTER(ads_params), _P, _P, _P, _P, C.c_double,
+                                              _P, _P]),
     "ads_kernel_launches": (C.c_int, [_P, C.POINTER(C.c_ulonglong)]),
     "ads_profile_train": (C.c_int, [_P, C.c_int, _D]),
     "ads_profile_saturation": (C.c_int, [_P, C.c_int, _D]),
