@@ -247,10 +247,10 @@ ads_status ads_saturation_step_noalloc(const ads_params* params, const double* d
  * ads_kernel_launches: number of library kernels enqueued on this context so
  * far (a graph replay counts the kernels it contains).
  * ads_profile_train: run `iters` Adam iterations without a graph, each kernel
- * bracketed by CUDA events on the context's stream; ms_out[10] receives the
+ * bracketed by CUDA events on the context's stream; ms_out[8] receives the
  * average duration of: network forward, residual, sine transform, tridiagonal
- * sweeps, inverse transform, loss partials, loss finalise, adjoint stencil,
- * network backward, gradient sum + Adam.  Updates the parameters like
+ * sweeps, inverse transform (+ loss partials), adjoint stencil (+ loss
+ * finalise), network backward, gradient sum + Adam.  Updates the parameters like
  * crvpinn_pressure_update at the learning rate last set.
  * ads_profile_saturation: `steps` saturation steps (current dt) likewise;
  * ms_out[3]: quadrature + x sweep, y sweep, mass bookkeeping. */

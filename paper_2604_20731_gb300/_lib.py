@@ -85,8 +85,8 @@ SIGNATURES = {
     "ads_status_str": (C.c_char_p, [C.c_int]),
 }
 
-TRAIN_KERNELS = ["mlp_fwd", "residual", "dst_gemm", "tridiag", "idst_gemm", "loss_partial",
-                 "loss_finalize", "adjoint", "mlp_bwd", "grad_adam"]
+TRAIN_KERNELS = ["mlp_fwd", "residual", "dst_gemm", "tridiag", "idst_gemm_loss",
+                 "adjoint_loss_finalize", "mlp_bwd", "grad_adam"]
 SAT_KERNELS = ["quad_xsolve", "ysolve", "mass_finalize"]
 
 _lib = None

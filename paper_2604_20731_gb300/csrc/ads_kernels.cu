@@ -392,46 +392,102 @@ cudaError_t launch_quad_xsolve(const QuadArgs<T>& a, int mode, int re, T* Xm, T*
   return cudaGetLastError();
 }
 
-// y sweep: thread per column k; row l of the right-hand side is Xm[l] plus,
-// when l is one of the first two rows of a strip other than the first, the
-// row spilled by the strip above.
+// y sweep.  A CTA owns a block of CW columns: all nb rows of the block (and
+// the rows the strips spilled into it) are staged in shared memory with
+// asynchronous copies, the spill rows are added, one thread per column runs
+// the LDL^T forward/backward sweeps in shared memory (accumulating int S with
+// the basis integrals), and the block is written back.
 template <typename T>
-__global__ void __launch_bounds__(128) k_ysolve_2d(int n, int re, T* X, const T* Xs, const T* l1,
-                                                   const T* l2, const T* dinv, const T* Iw,
-                                                   double* mass_part) {
+__global__ void __launch_bounds__(256) k_ysolve_2d(int n, int re, int cw, T* X, const T* Xs,
+                                                   const T* l1, const T* l2, const T* dinv,
+                                                   const T* Iw, double* mass_part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   const int nb = n + 2;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nstrip = (n + re - 1) / re;
+  const int nsp = 2 * (nstrip - 1);      // spill rows
+  T* xs = reinterpret_cast<T*>(smraw);    // [nb][cw]
+  T* ss = xs + (size_t)nb * cw;           // [nsp][cw]
+  T* f1 = ss + (size_t)nsp * cw;          // l1 [nb+2]
+  T* f2 = f1 + nb + 2;                    // l2 [nb+2]
+  T* fd = f2 + nb + 2;                    // dinv [nb]
+  T* fi = fd + nb;                        // Iw [nb]
+  const int k0 = blockIdx.x * cw;
+  const int ncw = min(cw, nb - k0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * cw; e += blockDim.x) {
+    const int l = e / cw, c = e % cw;
+    if (c < ncw) cp_async_elem(&xs[e], &X[(size_t)l * nb + k0 + c]);
+  }
+  for (int e = tid; e < nsp * cw; e += blockDim.x) {
+    const int r = e / cw, c = e % cw;
+    if (c < ncw) cp_async_elem(&ss[e], &Xs[(size_t)r * nb + k0 + c]);
+  }
+  for (int e = tid; e < nb + 2; e += blockDim.x) {
+    cp_async_elem(&f1[e], &l1[e]);
+    cp_async_elem(&f2[e], &l2[e]);
+    if (e < nb) {
+      cp_async_elem(&fd[e], &dinv[e]);
+      cp_async_elem(&fi[e], &Iw[e]);
+    }
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  // spill row r = 2*(b'-... ) holds row (b+1)*re + (r % 2) of strip b = r / 2
+  for (int e = tid; e < nsp * cw; e += blockDim.x) {
+    const int r = e / cw, c = e % cw;
+    const int l = (r / 2 + 1) * re + (r % 2);
+    if (c < ncw && l < nb) xs[l * cw + c] += ss[e];
+  }
+  __syncthreads();
   double mass = 0.0;
-  if (k < nb) {
+  const int c = tid;
+  if (c < ncw) {
     T ym1 = T(0), ym2 = T(0);
     for (int l = 0; l < nb; ++l) {
-      T v = X[(size_t)l * nb + k];
-      int r = l % re;
-      int top = l - r;
-      if (r < 2 && l >= re && top < n) v += Xs[((size_t)(top / re - 1) * 2 + r) * nb + k];
-      T y = v - l1[l] * ym1 - l2[l] * ym2;
-      X[(size_t)l * nb + k] = y;
+      T y = xs[l * cw + c] - f1[l] * ym1 - f2[l] * ym2;
+      xs[l * cw + c] = y;
       ym2 = ym1;
       ym1 = y;
     }
     T xp1 = T(0), xp2 = T(0);
     for (int l = nb - 1; l >= 0; --l) {
-      T v = X[(size_t)l * nb + k] * dinv[l] - l1[l + 1] * xp1 - l2[l + 2] * xp2;
-      X[(size_t)l * nb + k] = v;
-      mass += (double)v * (double)Iw[l];
+      T v = xs[l * cw + c] * fd[l] - f1[l + 1] * xp1 - f2[l + 2] * xp2;
+      xs[l * cw + c] = v;
+      mass += (double)v * (double)fi[l];
       xp2 = xp1;
       xp1 = v;
     }
-    mass *= (double)Iw[k];
+    mass *= (double)fi[k0 + c];
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * cw; e += blockDim.x) {
+    const int l = e / cw, cc = e % cw;
+    if (cc < ncw) X[(size_t)l * nb + k0 + cc] = xs[e];
   }
   double tot = block_sum(mass, red);
-  if (threadIdx.x == 0) mass_part[blockIdx.x] = tot;
+  if (tid == 0) mass_part[blockIdx.x] = tot;
+}
+
+static int ysolve_cw(int n, int re, size_t esize) {
+  const int nb = n + 2, nstrip = (n + re - 1) / re, nsp = 2 * (nstrip - 1);
+  int cw = 32;
+  while (cw > 1 && esize * ((size_t)(nb + nsp) * cw + 4 * (size_t)nb + 8) > 200 * 1024) cw /= 2;
+  return cw;
+}
+
+static size_t ysolve_smem(int n, int re, int cw, size_t esize) {
+  const int nb = n + 2, nstrip = (n + re - 1) / re, nsp = 2 * (nstrip - 1);
+  return esize * ((size_t)(nb + nsp) * cw + 4 * (size_t)nb + 8);
 }
 
 int ysolve_blocks(int dim, int n) {
+  // the column block width depends on the element size; size the partial
+  // buffer for the narrowest (FP64) blocks
   int nb = n + 2;
-  if (dim == 2) return (nb + 127) / 128;
+  int cw = ysolve_cw(n, 2, 8);
+  if (dim == 2) return (nb + cw - 1) / cw;
   return (nb * nb + 127) / 128;
 }
 
@@ -439,8 +495,16 @@ template <typename T>
 cudaError_t launch_ysolve(const QuadArgs<T>& a, int re, T* X, const T* Xs, double* mass_part,
                           cudaStream_t st) {
   if (a.dim != 2) return cudaErrorNotSupported;
-  k_ysolve_2d<T><<<ysolve_blocks(2, a.n), 128, 0, st>>>(a.n, re, X, Xs, a.ax.l1, a.ax.l2,
-                                                        a.ax.dinv, a.ax.Iw, mass_part);
+  int cw = ysolve_cw(a.n, re, sizeof(T));
+  size_t smem = ysolve_smem(a.n, re, cw, sizeof(T));
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  auto k = k_ysolve_2d<T>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nblk = (a.nb + cw - 1) / cw;
+  k<<<nblk, 256, smem, st>>>(a.n, re, cw, X, Xs, a.ax.l1, a.ax.l2, a.ax.dinv, a.ax.Iw, mass_part);
+  // unused partial slots of a wider block layout stay zero
+  int nmax = ysolve_blocks(2, a.n);
+  if (nblk < nmax) cudaMemsetAsync(mass_part + nblk, 0, sizeof(double) * (nmax - nblk), st);
   return cudaGetLastError();
 }
 
@@ -467,7 +531,10 @@ __global__ void __launch_bounds__(128) k_mass_2d(int n, const T* S, const T* Iw,
 template <typename T>
 cudaError_t launch_mass(const QuadArgs<T>& a, const T* S, double* mass_part, cudaStream_t st) {
   if (a.dim != 2) return cudaErrorNotSupported;
-  k_mass_2d<T><<<ysolve_blocks(2, a.n), 128, 0, st>>>(a.n, S, a.ax.Iw, mass_part);
+  int nblk = (a.nb + 127) / 128;
+  k_mass_2d<T><<<nblk, 128, 0, st>>>(a.n, S, a.ax.Iw, mass_part);
+  int nmax = ysolve_blocks(2, a.n);
+  if (nblk < nmax) cudaMemsetAsync(mass_part + nblk, 0, sizeof(double) * (nmax - nblk), st);
   return cudaGetLastError();
 }
 

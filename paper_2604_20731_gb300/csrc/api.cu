@@ -272,20 +272,17 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   const TC h = TC(1.0 / c->N);
   LK(0, launch_mlp_fwd<TC>(mlp_args<TC>(c, true), c->stream));
   LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->u,
-                           (const TC*)c->f, h * h, TC(1), (TC*)c->res, c->stream));
+                           (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr, c->stream));
   LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
-                        TC(1), c->stream));
+                        TC(1), nullptr, nullptr, c->stream));
   LK(3, launch_tridiag_cols<TC>(m, m, (const TC*)c->invd, (TC*)c->rhat, c->stream));
   LK(4, launch_gemm<TC>(m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
-                        h * h, c->stream));
-  LK(5, launch_dot_partial<TC>((const TC*)c->res, (const TC*)c->z, c->M, c->dot_part, c->ndot,
-                               c->stream));
-  LK(6, launch_loss_finalize(c->dot_part, c->ndot, c->loss, c->loss_log, c->t, c->bc, c->flags,
-                             upd, c->stream));
-  LK(7, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
-                           nullptr, TC(0), TC(2), (TC*)c->gu, c->stream));
-  LK(8, launch_mlp_bwd<TC>(mlp_args<TC>(c, true), c->nbwd, c->stream));
-  LK(9, launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->nbwd, c->nparams, (TC*)c->grad,
+                        h * h, (const TC*)c->res, c->dot_part, c->stream));
+  LossFin lf{c->dot_part, gemm_blocks(m, m), c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
+  LK(5, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
+                           nullptr, TC(0), TC(2), (TC*)c->gu, &lf, c->stream));
+  LK(6, launch_mlp_bwd<TC>(mlp_args<TC>(c, true), c->nbwd, c->stream));
+  LK(7, launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->nbwd, c->nparams, (TC*)c->grad,
                                     (TC*)c->theta, (TC*)c->am, (TC*)c->av, c->bc, c->lr, upd,
                                     c->stream));
   return ADS_OK;
@@ -541,7 +538,7 @@ struct TrainRun {
 
 template <typename TC>
 ads_status profile_train_t(ads_ctx* c, int iters, double* ms) {
-  const int NK = 10;
+  const int NK = 8;
   cudaEvent_t ev[NK + 1];
   for (int k = 0; k <= NK; ++k) CK(cudaEventCreate(&ev[k]));
   for (int k = 0; k < NK; ++k) ms[k] = 0.0;
@@ -735,7 +732,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   ALV(c->K, ta * nn);
   ALV(c->nodal, ta * nn);
   if (phi_nodal) ALV(c->phi, ta * nn);
-  c->re = 4;
+  c->re = (n + 3) / 4 < 152 ? 2 : 4;  // strips of 2 element rows on small meshes
   c->nquad = quad_blocks(c->dim, n, c->re);
   c->nys = ysolve_blocks(c->dim, n);
   c->ncfl = cfl_blocks(c->dim, n);
@@ -770,7 +767,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     c->nparams = mlp_params(2, crv->width, crv->hidden_layers);
     c->ld = ((c->M + 63) / 64) * 64;
     c->ndot = dot_blocks(c->M);
-    c->nbwd = mlp_bwd_blocks(c->M, crv->width, (int)tc);
+    c->nbwd = mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
     ALV(c->alpha, tc * nn);
     ALV(c->f, tc * c->M);
     ALV(c->u, tc * c->M);
@@ -798,7 +795,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
       launch_convert<float>(S64, (float*)c->Sdst, (size_t)m * m, c->stream);
       launch_convert<float>(inv64, (float*)c->invd, (size_t)m * m, c->stream);
     }
-    AL(c->dot_part, (size_t)c->ndot + 1);
+    AL(c->dot_part, (size_t)gemm_blocks(c->m1, c->m1) + 1);
     AL(c->loss, 1);
     AL(c->loss_log, kLossRing);
     AL(c->bc, 2);

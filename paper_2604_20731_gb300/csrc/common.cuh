@@ -75,4 +75,27 @@ ADS_D double block_max(double v, double* sh) {
   return r;
 }
 
+// Asynchronous global -> shared copies (cp.async): the copy does not pass
+// through registers, so a thread can keep many in flight and wait once.
+ADS_D unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+ADS_D void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+ADS_D void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+ADS_D void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+template <typename T>
+ADS_D void cp_async_elem(T* smem, const T* gmem) {
+  if (sizeof(T) == 8) cp_async8(smem, gmem);
+  else cp_async4(smem, gmem);
+}
+ADS_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+ADS_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+ADS_D void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 }  // namespace adsgb

@@ -83,12 +83,30 @@ cudaError_t launch_crv_coeffs(const CrvArgs<T, TA>& a, cudaStream_t st) {
 //                  + h2 * f_k  (f nullable), v = 0 on the boundary.
 // RES = A u + h^2 f uses scale 1; the adjoint dL/du = 2 A z uses scale 2.
 // ---------------------------------------------------------------------------
+// Loss finalisation (sum of the per-CTA partials of RES . z in a fixed
+// order), fused into the adjoint stencil's first thread: it also advances the
+// Adam step counter, logs the loss and stores the bias corrections.
+__device__ __forceinline__ void loss_finalize_dev(const LossFin& lf) {
+  double s = 0.0;
+  for (int i = 0; i < lf.nparts; ++i) s += lf.part[i];
+  *lf.loss = s;
+  if (!isfinite(s)) lf.flags[0] |= 4;
+  if (lf.bump) {
+    int tt = *lf.t + 1;
+    *lf.t = tt;
+    lf.log[(tt - 1) % kLossRing] = s;
+    lf.bc[0] = 1.0 / (1.0 - pow(0.9, (double)tt));
+    lf.bc[1] = 1.0 / (1.0 - pow(0.999, (double)tt));
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__ alpha,
                                                     const T* __restrict__ v, const T* __restrict__ f,
-                                                    T h2, T scale, T* __restrict__ out) {
+                                                    T h2, T scale, T* __restrict__ out, LossFin lf) {
   const int m = N - 1, n1 = N + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lf.part && t == 0) loss_finalize_dev(lf);
   if (t >= m * m) return;
   const int jj = t / m, ii = t % m;  // interior index
   const int j = jj + 1, i = ii + 1;  // node index
@@ -108,11 +126,12 @@ __global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__
 
 template <typename T>
 cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, const T* f, T h2,
-                           T scale, T* out, cudaStream_t st) {
+                           T scale, T* out, const LossFin* lf, cudaStream_t st) {
   if (dim != 2) return cudaErrorNotSupported;
   int m = (N - 1) * (N - 1);
   if (m <= 0) return cudaSuccess;
-  k_stencil_2d<T><<<(m + 255) / 256, 256, 0, st>>>(N, alpha, u, f, h2, scale, out);
+  LossFin none{};
+  k_stencil_2d<T><<<(m + 255) / 256, 256, 0, st>>>(N, alpha, u, f, h2, scale, out, lf ? *lf : none);
   return cudaGetLastError();
 }
 
@@ -170,46 +189,75 @@ cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// C = alpha * A * B (row-major, M x K times K x Nn), 64x64 tiles, 4x4 per
-// thread, register-blocked SIMT (the sine transform of the Gram inverse).
+// C = alpha * A * B (row-major, M x K times K x Nn), BM x BN tiles, 4x4 outputs
+// per thread, register-blocked SIMT (the sine transforms of the Gram inverse).
+// With dotB != nullptr the epilogue also forms this tile's part of
+// sum_ij C_ij dotB_ij (the loss RES^T z) in FP64.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(int M, int Nn, int K, const T* __restrict__ A, int lda,
-                                              const T* __restrict__ B, int ldb, T* __restrict__ C,
-                                              int ldc, T alpha) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ T As[BK][BM + 4];
-  __shared__ T Bs[BK][BN + 4];
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_gemm(int M, int Nn, int K,
+    const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb, T* __restrict__ C, int ldc,
+    T alpha, const T* __restrict__ dotB, double* dot_part) {
+  constexpr int BK = 16, NT = (BM / 4) * (BN / 4), TX = BN / 4;
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;  // loads per thread per k-tile
+  __shared__ T As[2][BK][BM + 4];
+  __shared__ T Bs[2][BK][BN + 4];
+  __shared__ double red[32];
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % TX, ty = tid / TX;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  T acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 256) {
-      int mm = e / BK, kk = e % BK;
+  T ra[LA], rb[LB];
+  // the next k-tile is loaded into registers while the current one is used
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      int e = tid + r * NT, mm = e / BK, kk = e % BK;
       int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : T(0);
+      ra[r] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : T(0);
     }
-    for (int e = tid; e < BK * BN; e += 256) {
-      int kk = e / BN, nn = e % BN;
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      int e = tid + r * NT, kk = e / BN, nn = e % BN;
       int gk = k0 + kk, gn = n0 + nn;
-      Bs[kk][nn] = (gk < K && gn < Nn) ? B[(size_t)gk * ldb + gn] : T(0);
+      rb[r] = (gk < K && gn < Nn) ? B[(size_t)gk * ldb + gn] : T(0);
     }
-    __syncthreads();
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      int e = tid + r * NT, mm = e / BK, kk = e % BK;
+      As[buf][kk][mm] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      int e = tid + r * NT, kk = e / BN, nn = e % BN;
+      Bs[buf][kk][nn] = rb[r];
+    }
+  };
+  T acc[4][4] = {};
+  const int nk = (K + BK - 1) / BK;
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int t = 0; t < nk; ++t) {
+    const int buf = t & 1;
+    if (t + 1 < nk) gload((t + 1) * BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a4[4], b4[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < 4; ++i) a4[i] = As[buf][kk][ty * 4 + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < 4; ++j) b4[j] = Bs[buf][kk][tx * 4 + j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < 4; ++j) acc[i][j] += a4[i] * b4[j];
     }
+    if (t + 1 < nk) sstore(buf ^ 1);
     __syncthreads();
   }
+  double dsum = 0.0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     int gm = m0 + ty * 4 + i;
@@ -217,43 +265,116 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int Nn, int K, const T* __r
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int gn = n0 + tx * 4 + j;
-      if (gn < Nn) C[(size_t)gm * ldc + gn] = alpha * acc[i][j];
+      if (gn < Nn) {
+        T v = alpha * acc[i][j];
+        C[(size_t)gm * ldc + gn] = v;
+        if (dotB) dsum += (double)v * (double)dotB[(size_t)gm * ldc + gn];
+      }
     }
   }
+  if (dotB) {
+    double tot = block_sum(dsum, red);
+    if (tid == 0) dot_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+static bool small_tiles(int M, int Nn) {
+  return ((M + 63) / 64) * ((Nn + 63) / 64) < 304;
+}
+
+int gemm_blocks(int M, int Nn) {
+  if (small_tiles(M, Nn)) return ((M + 31) / 32) * ((Nn + 31) / 32);
+  return ((M + 63) / 64) * ((Nn + 63) / 64);
 }
 
 template <typename T>
 cudaError_t launch_gemm(int M, int Nn, int K, const T* A, int lda, const T* B, int ldb, T* C,
-                        int ldc, T alpha, cudaStream_t st) {
-  dim3 grid((Nn + 63) / 64, (M + 63) / 64);
-  k_gemm<T><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha);
+                        int ldc, T alpha, const T* dotB, double* dot_part, cudaStream_t st) {
+  if (small_tiles(M, Nn)) {
+    dim3 grid((Nn + 31) / 32, (M + 31) / 32);
+    k_gemm<T, 32, 32><<<grid, 64, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha, dotB, dot_part);
+  } else {
+    dim3 grid((Nn + 63) / 64, (M + 63) / 64);
+    k_gemm<T, 64, 64><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha, dotB, dot_part);
+  }
   return cudaGetLastError();
 }
 
-// (Lambda_k + T) x = r along rows j for every column k: forward elimination
-// then back substitution with the precomputed inverse pivots.
+// (Lambda_k + T) x = r along rows j for every column k, forward elimination
+// then back substitution with the precomputed inverse pivots.  A CTA stages
+// a block of CW columns (all rows, and their pivots) in shared memory with
+// coalesced loads; one thread per column then runs the two sweeps there.
 template <typename T>
-__global__ void __launch_bounds__(128) k_tridiag_cols(int m, int ncols, const T* __restrict__ invd,
-                                                      T* X) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ncols) return;
-  T y = T(0);
-  for (int j = 0; j < m; ++j) {
-    T v = X[(size_t)j * ncols + k] + y * (j > 0 ? invd[(size_t)(j - 1) * ncols + k] : T(0));
-    X[(size_t)j * ncols + k] = v;
-    y = v;
+__global__ void __launch_bounds__(256) k_tridiag_smem(int m, int ncols, int cw,
+                                                      const T* __restrict__ invd, T* X) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);  // [m][cw]
+  T* cs = xs + (size_t)m * cw;          // [m][cw]
+  const int k0 = blockIdx.x * cw;
+  const int ncw = min(cw, ncols - k0);
+  for (int e = threadIdx.x; e < m * cw; e += blockDim.x) {
+    int j = e / cw, kk = e % cw;
+    if (kk < ncw) {
+      cp_async_elem(&xs[e], &X[(size_t)j * ncols + k0 + kk]);
+      cp_async_elem(&cs[e], &invd[(size_t)j * ncols + k0 + kk]);
+    }
   }
-  T x = T(0);
-  for (int j = m - 1; j >= 0; --j) {
-    T v = (X[(size_t)j * ncols + k] + x) * invd[(size_t)j * ncols + k];
-    X[(size_t)j * ncols + k] = v;
-    x = v;
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  const int kk = threadIdx.x;
+  if (kk < ncw) {
+    T y = xs[kk];
+    int j = 1;
+    for (; j + 4 <= m; j += 4) {
+      T x0 = xs[(j + 0) * cw + kk], x1 = xs[(j + 1) * cw + kk];
+      T x2 = xs[(j + 2) * cw + kk], x3 = xs[(j + 3) * cw + kk];
+      T c0 = cs[(j - 1) * cw + kk], c1 = cs[(j + 0) * cw + kk];
+      T c2 = cs[(j + 1) * cw + kk], c3 = cs[(j + 2) * cw + kk];
+      y = x0 + y * c0; xs[(j + 0) * cw + kk] = y;
+      y = x1 + y * c1; xs[(j + 1) * cw + kk] = y;
+      y = x2 + y * c2; xs[(j + 2) * cw + kk] = y;
+      y = x3 + y * c3; xs[(j + 3) * cw + kk] = y;
+    }
+    for (; j < m; ++j) {
+      y = xs[j * cw + kk] + y * cs[(j - 1) * cw + kk];
+      xs[j * cw + kk] = y;
+    }
+    T x = xs[(m - 1) * cw + kk] * cs[(m - 1) * cw + kk];
+    xs[(m - 1) * cw + kk] = x;
+    j = m - 2;
+    for (; j - 3 >= 0; j -= 4) {
+      T y0 = xs[(j - 0) * cw + kk], y1 = xs[(j - 1) * cw + kk];
+      T y2 = xs[(j - 2) * cw + kk], y3 = xs[(j - 3) * cw + kk];
+      T c0 = cs[(j - 0) * cw + kk], c1 = cs[(j - 1) * cw + kk];
+      T c2 = cs[(j - 2) * cw + kk], c3 = cs[(j - 3) * cw + kk];
+      x = (y0 + x) * c0; xs[(j - 0) * cw + kk] = x;
+      x = (y1 + x) * c1; xs[(j - 1) * cw + kk] = x;
+      x = (y2 + x) * c2; xs[(j - 2) * cw + kk] = x;
+      x = (y3 + x) * c3; xs[(j - 3) * cw + kk] = x;
+    }
+    for (; j >= 0; --j) {
+      x = (xs[j * cw + kk] + x) * cs[j * cw + kk];
+      xs[j * cw + kk] = x;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * cw; e += blockDim.x) {
+    int j = e / cw, c = e % cw;
+    if (c < ncw) X[(size_t)j * ncols + k0 + c] = xs[e];
   }
 }
 
 template <typename T>
 cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaStream_t st) {
-  k_tridiag_cols<T><<<(ncols + 127) / 128, 128, 0, st>>>(nrows, ncols, invd, X);
+  // columns per CTA: as many as fit 200 KB of shared memory, at most 32
+  int cw = 32;
+  while (cw > 1 && (size_t)2 * nrows * cw * sizeof(T) > 200 * 1024) cw /= 2;
+  size_t smem = (size_t)2 * nrows * cw * sizeof(T);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  auto k = k_tridiag_smem<T>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<(ncols + cw - 1) / cw, 256, smem, st>>>(nrows, ncols, cw, invd, X);
   return cudaGetLastError();
 }
 
@@ -314,9 +435,9 @@ CRV_INST(double, float)
 
 #define CRV_INST1(T)                                                                              \
   template cudaError_t launch_stencil<T>(int, int, T, const T*, const T*, const T*, T, T, T*,    \
-                                         cudaStream_t);                                           \
+                                         const LossFin*, cudaStream_t);                           \
   template cudaError_t launch_gemm<T>(int, int, int, const T*, int, const T*, int, T*, int, T,   \
-                                      cudaStream_t);                                              \
+                                      const T*, double*, cudaStream_t);                           \
   template cudaError_t launch_tridiag_cols<T>(int, int, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_dot_partial<T>(const T*, const T*, int, double*, int, cudaStream_t);
 CRV_INST1(double)

@@ -95,10 +95,21 @@ struct CrvArgs {
 };
 template <typename T, typename TA>
 cudaError_t launch_crv_coeffs(const CrvArgs<T, TA>& a, cudaStream_t st);
-// RES = A u + h^2 f (fwd = 1) or g = 2 A z (fwd = 0)
+// loss finalisation fused into the adjoint stencil (part == nullptr: none)
+struct LossFin {
+  const double* part;
+  int nparts;
+  double* loss;
+  double* log;
+  int* t;
+  double* bc;
+  int* flags;
+  int bump;
+};
+// RES = A u + h^2 f (scale 1) or g = 2 A z (scale 2, f = nullptr)
 template <typename T>
 cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, const T* f, T h2,
-                           T scale, T* out, cudaStream_t st);
+                           T scale, T* out, const LossFin* lf, cudaStream_t st);
 // nodal array (N+1)^dim (ADS precision) from interior values (boundary 0)
 template <typename T, typename TA>
 cudaError_t launch_embed(int dim, int N, const T* u, TA* nodal, cudaStream_t st);
@@ -107,7 +118,8 @@ cudaError_t launch_embed(int dim, int N, const T* u, TA* nodal, cudaStream_t st)
 cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gemm(int M, int Nn, int K, const T* A, int lda, const T* B, int ldb, T* C,
-                        int ldc, T alpha, cudaStream_t st);
+                        int ldc, T alpha, const T* dotB, double* dot_part, cudaStream_t st);
+int gemm_blocks(int M, int Nn);
 template <typename T>
 cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaStream_t st);
 template <typename T>
@@ -133,7 +145,7 @@ template <typename T>
 cudaError_t launch_mlp_fwd(const MlpArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_mlp_bwd(const MlpArgs<T>& a, int nblk, cudaStream_t st);
-int mlp_bwd_blocks(int npts, int width, int elem_bytes);
+int mlp_bwd_blocks(int npts, int width, int elem_bytes, int din);
 template <typename T>
 cudaError_t launch_grad_reduce_adam(const T* gpart, int nblk, int nparams, T* grad, T* theta,
                                     T* m, T* v, const double* bc, const double* lr, int do_update,

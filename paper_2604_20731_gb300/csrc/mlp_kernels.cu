@@ -61,11 +61,12 @@ ADS_D void point_coords(int idx, int N, T c[3]) {
 template <typename T, int W, int DIN, int P>
 __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(MlpArgs<T> a) {
   constexpr int PS = P + 4;  // padded row stride of the activation tiles
+  constexpr bool ALLW = (3 * W * W * sizeof(T) <= 64 * 1024);  // all hidden weights resident
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Ws = reinterpret_cast<T*>(smraw);  // [W][W]
-  T* bufA = Ws + W * W;                 // [W][PS]
-  T* bufB = bufA + W * PS;              // [W][PS]
-  T* xin = bufB + W * PS;               // [DIN][P]
+  T* Ws = reinterpret_cast<T*>(smraw);   // ALLW ? [3][W][W] : [W][W]
+  T* bufA = Ws + (ALLW ? 3 : 1) * W * W; // [W][PS]
+  T* bufB = bufA + W * PS;               // [W][PS]
+  T* xin = bufB + W * PS;                // [DIN][P]
   const int tid = threadIdx.x;
   const int ntiles = (a.npts + P - 1) / P;
   const T* th = a.theta;
@@ -74,6 +75,11 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(MlpArgs<T> a) {
   constexpr int TP = 4, NPG = P / TP, NOG = kMlpThreads / NPG, TO = W / NOG;
   static_assert(TO * NOG == W, "tile mapping");
   const int pg = tid % NPG, og = tid / NPG;
+  if (ALLW)
+    for (int e = tid; e < 3 * W * W; e += kMlpThreads) {
+      int l = e / (W * W), r = e % (W * W);
+      Ws[e] = th[o2 + l * (W * W + W) + r];
+    }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int p0 = tile * P;
     for (int p = tid; p < P; p += kMlpThreads) {
@@ -92,11 +98,13 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(MlpArgs<T> a) {
       if (a.acts) a.acts[(size_t)o * a.ld + p0 + p] = v;
     }
     for (int l = 0; l < 3; ++l) {
-      const T* Wl = th + o2 + l * (W * W + W);
-      const T* bl = Wl + W * W;
+      const T* bl = th + o2 + l * (W * W + W) + W * W;
       __syncthreads();
-      for (int e = tid; e < W * W; e += kMlpThreads) Ws[e] = Wl[e];
-      __syncthreads();
+      if (!ALLW) {
+        for (int e = tid; e < W * W; e += kMlpThreads) Ws[e] = th[o2 + l * (W * W + W) + e];
+        __syncthreads();
+      }
+      const T* Wl = ALLW ? Ws + l * W * W : Ws;
       T acc[TO][TP];
 #pragma unroll
       for (int i = 0; i < TO; ++i)
@@ -106,7 +114,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(MlpArgs<T> a) {
       for (int k = 0; k < W; k += 4) {
         T wv[TO][4], av[4][TP];
 #pragma unroll
-        for (int i = 0; i < TO; ++i) ld4<T>(&Ws[(og * TO + i) * W + k], wv[i]);
+        for (int i = 0; i < TO; ++i) ld4<T>(&Wl[(og * TO + i) * W + k], wv[i]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) ld4<T>(&bufA[(k + j) * PS + pg * TP], av[j]);
 #pragma unroll
@@ -139,31 +147,105 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(MlpArgs<T> a) {
   }
 }
 
+// shared memory of the backward kernel with nbuf activation buffers
+template <typename T, int W, int DIN, int P>
+constexpr size_t bwd_bytes(int nbuf) {
+  return sizeof(T) * (((3 * W * W * sizeof(T) <= 64 * 1024) ? 3 : 1) * W * W +
+                      (2 + nbuf) * W * (P + 4) + P + DIN * P + (W + 1 + 3 * W + W * DIN + W));
+}
+// two activation buffers only if two CTAs still fit on an SM (or if even one
+// buffer does not allow two)
+template <typename T, int W, int DIN, int P>
+constexpr int bwd_nbuf() {
+  return (bwd_bytes<T, W, DIN, P>(2) <= 112 * 1024 || bwd_bytes<T, W, DIN, P>(1) > 112 * 1024) ? 2 : 1;
+}
+
+template <typename T>
+ADS_D T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Backward pass.  Thread mappings are chosen so that shared-memory reads are
+// conflict-free: in the dW product a thread owns rows o = og*TOd + i of
+// delta (broadcast within a half-warp) and rows k = kg + NKG*j of the
+// activations (consecutive rows across lanes); the delta product reads
+// weight rows by broadcast and activation columns contiguously.  For W <= 64
+// the hidden-layer dW of all the CTA's tiles accumulate in registers and are
+// written once; the small gradients (output layer, biases, first layer) are
+// warp reductions accumulated in shared memory by a fixed owner.
 template <typename T, int W, int DIN, int P>
 __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
   constexpr int PS = P + 4;
+  constexpr bool ALLW = (3 * W * W * sizeof(T) <= 64 * 1024);
+  constexpr bool REGACC = (W <= 64);
+  constexpr int NBUF = bwd_nbuf<T, W, DIN, P>();
+  constexpr int NWARP = kMlpThreads / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Ws = reinterpret_cast<T*>(smraw);  // [W][W]
-  T* dA = Ws + W * W;                   // delta_l        [W][PS]
-  T* dB = dA + W * PS;                  // delta_{l-1}    [W][PS]
-  T* aS = dB + W * PS;                  // a_{l-1}        [W][PS]
-  T* gP = aS + W * PS;                  // [P]
-  T* xin = gP + P;                      // [DIN][P]
-  const int tid = threadIdx.x;
+  T* Ws = reinterpret_cast<T*>(smraw);   // ALLW ? [3][W][W] : [W][W]
+  T* dA = Ws + (ALLW ? 3 : 1) * W * W;   // delta_l      [W][PS]
+  T* dB = dA + W * PS;                   // delta_{l-1}  [W][PS]
+  T* aBuf = dB + W * PS;                 // activations [NBUF][W][PS]
+  T* gP = aBuf + NBUF * W * PS;          // [P]
+  T* xin = gP + P;                       // [DIN][P]
+  T* gsm = xin + DIN * P;                // small gradients
+  T* g5 = gsm;                           // dW_5 [W]
+  T* gb5 = g5 + W;                       // db_5 [1]
+  T* gbh = gb5 + 1;                      // db of hidden layers [3][W]
+  T* g1 = gbh + 3 * W;                   // dW_1 [W][DIN]
+  T* gb1 = g1 + W * DIN;                 // db_1 [W]
+  constexpr int NSMALL = W + 1 + 3 * W + W * DIN + W;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ntiles = (a.npts + P - 1) / P;
   const T* th = a.theta;
   const int ob1 = W * DIN, o2 = ob1 + W;
   const int o5 = o2 + 3 * (W * W + W);
   T* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
-  for (int i = tid; i < a.nparams; i += kMlpThreads) gacc[i] = T(0);
-  // dW tile mapping (o, k) and delta tile mapping (k, p)
   constexpr int TK = W / 16, NKG = W / TK, NOGd = kMlpThreads / NKG, TOd = W / NOGd;
   static_assert(TOd * NOGd == W, "dW tile mapping");
   constexpr int TP = 4, NPG = P / TP, NKGp = kMlpThreads / NPG, TKp = W / NKGp;
   static_assert(TKp * NKGp == W, "delta tile mapping");
+  const int kg = tid % NKG, og = tid / NKG;
+  // stage activations of `layer` for the tile at p0 with 16-byte async copies
+  auto stage = [&](T* dst, int layer, int p0) {
+    constexpr int CH = 16 / sizeof(T), PCH = P / CH;
+    for (int c = tid; c < W * PCH; c += kMlpThreads) {
+      const int k = c / PCH, pc = (c % PCH) * CH;
+      cp_async16(&dst[k * PS + pc], &a.acts[((size_t)layer * W + k) * a.ld + p0 + pc]);
+    }
+    cp_async_commit();
+  };
+  T accW[REGACC ? 3 : 1][TOd][TK];
+#pragma unroll
+  for (int l = 0; l < (REGACC ? 3 : 1); ++l)
+#pragma unroll
+    for (int i = 0; i < TOd; ++i)
+#pragma unroll
+      for (int j = 0; j < TK; ++j) accW[l][i][j] = T(0);
+  for (int i = tid; i < NSMALL; i += kMlpThreads) gsm[i] = T(0);
+  if (!REGACC)
+    for (int i = tid; i < a.nparams; i += kMlpThreads) gacc[i] = T(0);
+  if (ALLW)
+    for (int e = tid; e < 3 * W * W; e += kMlpThreads) {
+      int l = e / (W * W), r = e % (W * W);
+      Ws[e] = th[o2 + l * (W * W + W) + r];
+    }
+  // With two activation buffers the next stage's copy overlaps this stage's
+  // math; with one (when two would not leave room for 2 CTAs per SM) each
+  // stage issues its own copy and waits for it.
+  auto buf_of = [&](int stg) { return aBuf + (NBUF == 2 ? (stg & 1) : 0) * W * PS; };
+  int st = 0;
+  if (NBUF == 2 && (int)blockIdx.x < ntiles) stage(aBuf, 3, blockIdx.x * P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int p0 = tile * P;
+    if (NBUF == 1) {
+      __syncthreads();
+      stage(aBuf, 3, p0);
+    }
+    cp_async_wait_all();
     __syncthreads();
+    if (NBUF == 2) stage(buf_of(st + 1), 2, p0);
     for (int p = tid; p < P; p += kMlpThreads) {
       const int idx = p0 + p;
       gP[p] = idx < a.npts ? a.gu[idx] : T(0);
@@ -171,40 +253,50 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
       point_coords<T, DIN>(min(idx, a.npts - 1), a.N, c);
       for (int d = 0; d < DIN; ++d) xin[d * P + p] = c[d];
     }
-    for (int e = tid; e < W * P; e += kMlpThreads) {
-      const int k = e / P, p = e % P;
-      aS[k * PS + p] = a.acts[((size_t)3 * W + k) * a.ld + p0 + p];
-    }
     __syncthreads();
-    // output layer
-    for (int k = tid; k < W; k += kMlpThreads) {
-      T s = T(0);
-      for (int p = 0; p < P; ++p) s += gP[p] * aS[k * PS + p];
-      gacc[o5 + k] += s;
-    }
-    if (tid == 0) {
-      T s = T(0);
-      for (int p = 0; p < P; ++p) s += gP[p];
-      gacc[o5 + W] += s;
-    }
-    for (int e = tid; e < W * P; e += kMlpThreads) {
-      const int k = e / P, p = e % P;
-      const T av = aS[k * PS + p];
-      dA[k * PS + p] = th[o5 + k] * gP[p] * (T(1) - av * av);
-    }
-    for (int hl = 2; hl >= 0; --hl) {
-      const T* Wl = th + o2 + hl * (W * W + W);
-      const int ow = o2 + hl * (W * W + W);
-      __syncthreads();
-      for (int e = tid; e < W * W; e += kMlpThreads) Ws[e] = Wl[e];
+    {
+      const T* aS = buf_of(st);
+      // output layer: dW_5[k] = sum_p g_p a_4[k][p], db_5 = sum_p g_p
+      for (int k = warp; k < W; k += NWARP) {
+        T sum = T(0);
+        for (int p = lane; p < P; p += 32) sum += gP[p] * aS[k * PS + p];
+        sum = warp_sum(sum);
+        if (lane == 0) g5[k] += sum;
+      }
+      if (warp == 0) {
+        T sum = T(0);
+        for (int p = lane; p < P; p += 32) sum += gP[p];
+        sum = warp_sum(sum);
+        if (lane == 0) gb5[0] += sum;
+      }
       for (int e = tid; e < W * P; e += kMlpThreads) {
         const int k = e / P, p = e % P;
-        aS[k * PS + p] = a.acts[((size_t)hl * W + k) * a.ld + p0 + p];
+        const T av = aS[k * PS + p];
+        dA[k * PS + p] = th[o5 + k] * gP[p] * (T(1) - av * av);
       }
+      ++st;
+    }
+#pragma unroll
+    for (int hl = 2; hl >= 0; --hl) {
+      const int ow = o2 + hl * (W * W + W);
+      if (NBUF == 1) {
+        __syncthreads();
+        stage(aBuf, hl, p0);
+      }
+      cp_async_wait_all();
       __syncthreads();
+      if (NBUF == 2) {
+        if (hl > 0) stage(buf_of(st + 1), hl - 1, p0);
+        else if (tile + (int)gridDim.x < ntiles) stage(buf_of(st + 1), 3, (tile + gridDim.x) * P);
+      }
+      if (!ALLW) {
+        for (int e = tid; e < W * W; e += kMlpThreads) Ws[e] = th[ow + e];
+        __syncthreads();
+      }
+      const T* Wl = ALLW ? Ws + hl * W * W : Ws;
+      const T* aS = buf_of(st);
       // dW[o][k] += sum_p dA[o][p] aS[k][p]
       {
-        const int kg = tid % NKG, og = tid / NKG;
         T acc[TOd][TK];
 #pragma unroll
         for (int i = 0; i < TOd; ++i)
@@ -216,7 +308,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
 #pragma unroll
           for (int i = 0; i < TOd; ++i) ld4<T>(&dA[(og * TOd + i) * PS + p], dv[i]);
 #pragma unroll
-          for (int j = 0; j < TK; ++j) ld4<T>(&aS[(kg * TK + j) * PS + p], av[j]);
+          for (int j = 0; j < TK; ++j) ld4<T>(&aS[(kg + NKG * j) * PS + p], av[j]);
 #pragma unroll
           for (int i = 0; i < TOd; ++i)
 #pragma unroll
@@ -224,19 +316,29 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
 #pragma unroll
               for (int q = 0; q < 4; ++q) acc[i][j] += dv[i][q] * av[j][q];
         }
+        if (REGACC) {
 #pragma unroll
-        for (int i = 0; i < TOd; ++i)
+          for (int i = 0; i < TOd; ++i)
 #pragma unroll
-          for (int j = 0; j < TK; ++j) gacc[ow + (og * TOd + i) * W + kg * TK + j] += acc[i][j];
+            for (int j = 0; j < TK; ++j) accW[REGACC ? hl : 0][i][j] += acc[i][j];
+        } else {
+#pragma unroll
+          for (int i = 0; i < TOd; ++i)
+#pragma unroll
+            for (int j = 0; j < TK; ++j)
+              gacc[ow + (og * TOd + i) * W + kg + NKG * j] += acc[i][j];
+        }
       }
-      for (int o = tid; o < W; o += kMlpThreads) {
-        T s = T(0);
-        for (int p = 0; p < P; ++p) s += dA[o * PS + p];
-        gacc[ow + W * W + o] += s;
+      // db[o] += sum_p dA[o][p]
+      for (int o = warp; o < W; o += NWARP) {
+        T sum = T(0);
+        for (int p = lane; p < P; p += 32) sum += dA[o * PS + p];
+        sum = warp_sum(sum);
+        if (lane == 0) gbh[hl * W + o] += sum;
       }
-      // delta_{l-1}[k][p] = (sum_o Ws[o][k] dA[o][p]) (1 - aS[k][p]^2)
+      // delta_{l-1}[k][p] = (sum_o W[o][k] dA[o][p]) (1 - aS[k][p]^2)
       {
-        const int pg = tid % NPG, kg = tid / NPG;
+        const int pg = tid % NPG, kgp = tid / NPG;
         T acc[TKp][TP];
 #pragma unroll
         for (int i = 0; i < TKp; ++i)
@@ -246,7 +348,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
         for (int o = 0; o < W; ++o) {
           T wv[TKp], dv[TP];
 #pragma unroll
-          for (int i = 0; i < TKp; i += 4) ld4<T>(&Ws[o * W + kg * TKp + i], &wv[i]);
+          for (int i = 0; i < TKp; i += 4) ld4<T>(&Wl[o * W + kgp * TKp + i], &wv[i]);
           ld4<T>(&dA[o * PS + pg * TP], dv);
 #pragma unroll
           for (int i = 0; i < TKp; ++i)
@@ -255,7 +357,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
         }
 #pragma unroll
         for (int i = 0; i < TKp; ++i) {
-          const int k = kg * TKp + i;
+          const int k = kgp * TKp + i;
           T av[TP], v[TP];
           ld4<T>(&aS[k * PS + pg * TP], av);
 #pragma unroll
@@ -263,36 +365,63 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(MlpArgs<T> a) {
           st4<T>(&dB[k * PS + pg * TP], v);
         }
       }
-      __syncthreads();
+      ++st;
+      if (!ALLW) __syncthreads();  // Ws is reloaded by the next layer
       T* tmp = dA; dA = dB; dB = tmp;
     }
+    __syncthreads();
     // first layer: dW_1[o][d] += sum_p delta_1[o][p] x'_d[p], db_1[o] += sum_p delta_1[o][p]
-    for (int o = tid; o < W; o += kMlpThreads) {
+    for (int o = warp; o < W; o += NWARP) {
       T s[DIN + 1];
 #pragma unroll
       for (int d = 0; d <= DIN; ++d) s[d] = T(0);
-      for (int p = 0; p < P; ++p) {
+      for (int p = lane; p < P; p += 32) {
         const T dv = dA[o * PS + p];
 #pragma unroll
         for (int d = 0; d < DIN; ++d) s[d] += dv * xin[d * P + p];
         s[DIN] += dv;
       }
 #pragma unroll
-      for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] += s[d];
-      gacc[ob1 + o] += s[DIN];
+      for (int d = 0; d <= DIN; ++d) s[d] = warp_sum(s[d]);
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < DIN; ++d) g1[o * DIN + d] += s[d];
+        gb1[o] += s[DIN];
+      }
     }
   }
+  cp_async_wait_all();
+  __syncthreads();
+  // write this CTA's gradient row
+  if (REGACC) {
+#pragma unroll
+    for (int hl = 0; hl < 3; ++hl) {
+      const int ow = o2 + hl * (W * W + W);
+#pragma unroll
+      for (int i = 0; i < TOd; ++i)
+#pragma unroll
+        for (int j = 0; j < TK; ++j)
+          gacc[ow + (og * TOd + i) * W + kg + NKG * j] = accW[REGACC ? hl : 0][i][j];
+    }
+  }
+  for (int i = tid; i < W; i += kMlpThreads) {
+    gacc[o5 + i] = g5[i];
+    gacc[ob1 + i] = gb1[i];
+    for (int hl = 0; hl < 3; ++hl) gacc[o2 + hl * (W * W + W) + W * W + i] = gbh[hl * W + i];
+    for (int d = 0; d < DIN; ++d) gacc[i * DIN + d] = g1[i * DIN + d];
+  }
+  if (tid == 0) gacc[o5 + W] = gb5[0];
 }
 
 template <typename T, int W, int DIN>
 static size_t fwd_smem() {
   constexpr int P = 64, PS = P + 4;
-  return sizeof(T) * (W * W + 2 * W * PS + DIN * P);
+  constexpr bool ALLW = (3 * W * W * sizeof(T) <= 64 * 1024);
+  return sizeof(T) * ((ALLW ? 3 : 1) * W * W + 2 * W * PS + DIN * P);
 }
 template <typename T, int W, int DIN>
 static size_t bwd_smem() {
-  constexpr int P = 64, PS = P + 4;
-  return sizeof(T) * (W * W + 3 * W * PS + P + DIN * P);
+  return bwd_bytes<T, W, DIN, 64>(bwd_nbuf<T, W, DIN, 64>());
 }
 
 static int g_num_sms = 0;
@@ -335,14 +464,25 @@ static cudaError_t bwd_dispatch(const MlpArgs<T>& a, int nblk, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-int mlp_bwd_blocks(int npts, int width, int elem_bytes) {
+template <typename T, int W, int DIN>
+static int bwd_grid(int npts) {
+  auto k = k_mlp_bwd<T, W, DIN, 64>;
+  size_t smem = bwd_smem<T, W, DIN>();
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kMlpThreads, smem);
+  if (occ < 1) occ = 1;
   int ntiles = (npts + 63) / 64;
-  size_t smem = (size_t)elem_bytes * (width * width + 3 * width * 68 + 64 + 3 * 64);
-  int per_sm = (int)((220 * 1024) / (smem + 1024));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
-  int nb = per_sm * num_sms();
-  return ntiles < nb ? ntiles : nb;
+  return ntiles < occ * num_sms() ? ntiles : occ * num_sms();
+}
+
+int mlp_bwd_blocks(int npts, int width, int elem_bytes, int din) {
+  if (elem_bytes == 4) {
+    if (din == 2) return width == 64 ? bwd_grid<float, 64, 2>(npts) : bwd_grid<float, 128, 2>(npts);
+    return width == 64 ? bwd_grid<float, 64, 3>(npts) : bwd_grid<float, 128, 3>(npts);
+  }
+  if (din == 2) return bwd_grid<double, 64, 2>(npts);
+  return bwd_grid<double, 64, 3>(npts);
 }
 
 template <typename T>
