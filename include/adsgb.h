@@ -81,9 +81,14 @@ typedef struct {
 } ads_params;
 
 typedef struct {
-  int width;         /* hidden width: 64 or 128                               */
+  int width;         /* hidden width: 64 or 128 (ADS_BF16 and ADS_F64: 64)    */
   int hidden_layers; /* 4                                                     */
-  int dtype;         /* ADS_F64 or ADS_F32 (network, residual, Gram, Adam)    */
+  int dtype;         /* ADS_F64 or ADS_F32: network, residual, Gram and Adam
+                        in that precision on the CUDA cores.  ADS_BF16: the
+                        network's layer products on the tcgen05 tensor cores
+                        with BF16 operands and FP32 accumulation, stored
+                        activations in BF16, everything else (residual, Gram,
+                        Adam, master parameters) in FP32.                     */
 } crvpinn_params;
 
 typedef struct {

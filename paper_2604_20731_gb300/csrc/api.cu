@@ -34,6 +34,7 @@ struct ads_ctx {
   bool has_crv = false;
   int dim = 2, n = 0, nb = 0, N = 0, M = 0, m1 = 0, nparams = 0;
   int ta = ADS_F64, tc = ADS_F64;
+  bool use_tc = false;  // network on tcgen05 tensor cores (BF16 operands, FP32 accumulation)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   ads_status status = ADS_OK;
@@ -237,6 +238,33 @@ MlpArgs<TC> mlp_args(ads_ctx* c, bool store) {
   return a;
 }
 
+MlpTcArgs mlp_tc_args(ads_ctx* c, bool store) {
+  MlpTcArgs a{};
+  a.din = c->dim;
+  a.width = c->cp.width;
+  a.npts = c->M;
+  a.N = c->N;
+  a.theta = (const float*)c->theta;
+  a.u = (float*)c->u;
+  a.acts = store ? (unsigned char*)c->acts : nullptr;
+  a.gu = (const float*)c->gu;
+  a.gpart = (float*)c->gpart;
+  a.nparams = c->nparams;
+  a.flags = c->flags;
+  return a;
+}
+
+template <typename TC>
+cudaError_t launch_fwd(ads_ctx* c, bool store) {
+  if (c->use_tc) return launch_mlp_fwd_tc(mlp_tc_args(c, store), c->stream);
+  return launch_mlp_fwd<TC>(mlp_args<TC>(c, store), c->stream);
+}
+template <typename TC>
+cudaError_t launch_bwd(ads_ctx* c) {
+  if (c->use_tc) return launch_mlp_bwd_tc(mlp_tc_args(c, true), c->nbwd, c->stream);
+  return launch_mlp_bwd<TC>(mlp_args<TC>(c, true), c->nbwd, c->stream);
+}
+
 template <typename TC, typename TA>
 ads_status enq_coeffs(ads_ctx* c) {
   CrvArgs<TC, TA> a{};
@@ -270,7 +298,7 @@ template <typename TC>
 ads_status enq_train_iter(ads_ctx* c, int upd) {
   const int m = c->m1;
   const TC h = TC(1.0 / c->N);
-  LK(0, launch_mlp_fwd<TC>(mlp_args<TC>(c, true), c->stream));
+  LK(0, launch_fwd<TC>(c, true));
   LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->u,
                            (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr, c->stream));
   LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
@@ -281,7 +309,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   LossFin lf{c->dot_part, gemm_blocks(m, m), c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
   LK(5, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
                            nullptr, TC(0), TC(2), (TC*)c->gu, &lf, c->stream));
-  LK(6, launch_mlp_bwd<TC>(mlp_args<TC>(c, true), c->nbwd, c->stream));
+  LK(6, launch_bwd<TC>(c));
   LK(7, launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->nbwd, c->nparams, (TC*)c->grad,
                                     (TC*)c->theta, (TC*)c->am, (TC*)c->av, c->bc, c->lr, upd,
                                     c->stream));
@@ -290,7 +318,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
 
 template <typename TC, typename TA>
 ads_status enq_project(ads_ctx* c) {
-  CK(launch_mlp_fwd<TC>(mlp_args<TC>(c, false), c->stream));
+  CK(launch_fwd<TC>(c, false));
   CK(launch_embed<TC, TA>(c->dim, c->N, (const TC*)c->u, (TA*)c->nodal, c->stream));
   QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
   CK(launch_quad_xsolve<TA>(a, 1, c->re, (TA*)c->P, (TA*)c->Xs, c->src_part, c->stream));
@@ -484,8 +512,9 @@ ads_status validate(const ads_params* p, const crvpinn_params* cp) {
   if (cp) {
     if (cp->hidden_layers != 4) return ADS_ERR_UNSUPPORTED;
     if (cp->width != 64 && cp->width != 128) return ADS_ERR_UNSUPPORTED;
-    if (cp->dtype != ADS_F64 && cp->dtype != ADS_F32) return ADS_ERR_UNSUPPORTED;
+    if (cp->dtype != ADS_F64 && cp->dtype != ADS_F32 && cp->dtype != ADS_BF16) return ADS_ERR_UNSUPPORTED;
     if (cp->dtype == ADS_F64 && cp->width != 64) return ADS_ERR_UNSUPPORTED;
+    if (cp->dtype == ADS_BF16 && cp->width != 64) return ADS_ERR_UNSUPPORTED;
     if (p->n < 3) return ADS_ERR_INVALID_ARG;
   }
   return ADS_OK;
@@ -509,7 +538,7 @@ size_t estimate(const ads_params* p, const crvpinn_params* cp) {
   b += ta * (3 * nc + 2 * nn + 2 * ((n + 3) / 4) * 2 * nb + nn);
   b += 8 * 4 * (nb + 1024);
   if (cp) {
-    size_t tc = tsize(cp->dtype);
+    size_t tc = cp->dtype == ADS_BF16 ? 4 : tsize(cp->dtype);
     size_t m = n - 1, M = m * m, w = cp->width;
     size_t np = mlp_params(2, cp->width, cp->hidden_layers);
     size_t ld = ((M + 63) / 64) * 64;
@@ -673,10 +702,14 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     return bail(ADS_ERR_OOM);
   c->h_stage_count = stage;
   ads_status st;
-#define AL(p, cnt)                                   \
-  if ((st = allocT(c, &(p), (cnt))) != ADS_OK) return bail(st)
-#define ALV(p, bytes)                                \
-  if ((st = alloc(c, &(p), (bytes))) != ADS_OK) return bail(st)
+#define AL(p, cnt)                                                  \
+  do {                                                              \
+    if ((st = allocT(c, &(p), (cnt))) != ADS_OK) return bail(st);   \
+  } while (0)
+#define ALV(p, bytes)                                               \
+  do {                                                              \
+    if ((st = alloc(c, &(p), (bytes))) != ADS_OK) return bail(st);  \
+  } while (0)
   // FP64 tables
   AL(c->B64, 9 * (size_t)n);
   AL(c->dB64, 9 * (size_t)n);
@@ -731,7 +764,9 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   ALV(c->P, ta * nc);
   ALV(c->K, ta * nn);
   ALV(c->nodal, ta * nn);
-  if (phi_nodal) ALV(c->phi, ta * nn);
+  if (phi_nodal) {
+    ALV(c->phi, ta * nn);
+  }
   c->re = (n + 3) / 4 < 152 ? 2 : 4;  // strips of 2 element rows on small meshes
   c->nquad = quad_blocks(c->dim, n, c->re);
   c->nys = ysolve_blocks(c->dim, n);
@@ -761,13 +796,14 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   if (crv) {
     c->has_crv = true;
     c->cp = *crv;
-    c->tc = crv->dtype;
+    c->use_tc = crv->dtype == ADS_BF16;
+    c->tc = c->use_tc ? ADS_F32 : crv->dtype;  // buffers outside the network stay FP32
     const size_t tc = tsize(c->tc);
     const int m = c->m1;
     c->nparams = mlp_params(2, crv->width, crv->hidden_layers);
     c->ld = ((c->M + 63) / 64) * 64;
     c->ndot = dot_blocks(c->M);
-    c->nbwd = mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
+    c->nbwd = c->use_tc ? mlp_tc_bwd_blocks(c->M) : mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
     ALV(c->alpha, tc * nn);
     ALV(c->f, tc * c->M);
     ALV(c->u, tc * c->M);
@@ -780,7 +816,11 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     ALV(c->av, tc * c->nparams);
     ALV(c->grad, tc * c->nparams);
     ALV(c->gpart, tc * (size_t)c->nbwd * c->nparams);
-    ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
+    if (c->use_tc) {
+      ALV(c->acts, mlp_tc_acts_bytes(c->M, crv->width));
+    } else {
+      ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
+    }
     double *S64 = nullptr, *inv64 = nullptr;
     AL(S64, (size_t)m * m);
     AL(inv64, (size_t)m * m);
@@ -993,6 +1033,7 @@ static ads_status hybrid_stats_read(ads_ctx* c, hybrid_stats* out) {
   out->mass_total = m3[0];
   int fl = 0;
   CA(read_flags(c, &fl));
+  if (fl & 8) return fail(c, ADS_ERR_TIMEOUT, "a tensor-core wait timed out on the device");
   if (fl != 0 || !std::isfinite(v[0]) || !std::isfinite(v[1]))
     return fail(c, ADS_ERR_NONFINITE, "non-finite loss, step size or mass");
   return ADS_OK;

@@ -151,4 +151,20 @@ cudaError_t launch_grad_reduce_adam(const T* gpart, int nblk, int nparams, T* gr
                                     T* m, T* v, const double* bc, const double* lr, int do_update,
                                     cudaStream_t st);
 
+// ---- MLP on tcgen05 tensor cores (BF16 operands, FP32 accumulation, width 64) ----
+struct MlpTcArgs {
+  int din, width, npts, N;
+  const float* theta;     // FP32 master parameters
+  float* u;               // [npts]
+  unsigned char* acts;    // BF16 activations, [tile][4][128 x width] core-matrix tiles (nullable)
+  const float* gu;        // [npts] dL/du
+  float* gpart;           // [nblk][nparams]
+  int nparams;
+  int* flags;             // bit 8: a tensor-core wait timed out
+};
+cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
+cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
+size_t mlp_tc_acts_bytes(int npts, int width);
+int mlp_tc_bwd_blocks(int npts);
+
 }  // namespace adsgb

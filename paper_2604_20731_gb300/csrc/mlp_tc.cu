@@ -1,0 +1,600 @@
+// CRVPINN network on the 5th-generation tensor cores (tcgen05, sm_103a):
+// BF16 operands, FP32 accumulation in tensor memory (TMEM).  Width 64.
+//
+// Operand tiles live in shared memory in the no-swizzle canonical layout:
+// 8-row x 16-byte core matrices; within a tile of R rows and C columns the
+// byte offset of element (r, c) is (r/8)*RG + (c/8)*128 + (r%8)*16 + (c%8)*2
+// with RG = (C/8)*128.  The same tile serves as a K-major operand (rows = M or
+// N, columns = K; descriptor LBO = 128, SBO = RG) or as an MN-major operand
+// (rows = K, columns = M or N; LBO = RG, SBO = 128).
+//
+// Forward, per tile of 128 collocation points (one CTA of 128 threads, thread
+// t = point t = TMEM lane t):
+//   a_1 = tanh(W_1 x' + b_1) on the CUDA cores (K = 2 or 3);
+//   for the three hidden layers: D[t][o] = sum_k a[t][k] W[o][k] (one
+//   128 x 64 x 64 MMA chain, issued by one thread), then each thread reads
+//   its row of D from TMEM, adds the bias, applies tanh and writes the BF16
+//   row back as the next A operand (and, for the backward pass, to HBM);
+//   u = W_5 a_4 + b_5 from registers.
+// Backward, per tile (persistent CTAs; gradients accumulate in TMEM over all
+// of a CTA's tiles):
+//   D_l (for dW_l, db_l) += Delta_l^T [a_{l-1} | 1] -- M = 128 output rows
+//   (zero-padded), N = 80 (64 inputs + a ones column giving db), K = 128
+//   points, both operands MN-major views of the [point][feature] tiles;
+//   Delta_{l-1} = (Delta_l W_l) (1 - a_{l-1}^2) -- M = 128 points, N = 64,
+//   K = 64, W_l read MN-major from the same weight tile as the forward.
+//   The output layer is the same product with Delta_5 = [g, 0, ...] and the
+//   first layer with [x' | 1] as the second operand.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace adsgb {
+namespace {
+
+constexpr int kW = 64;           // hidden width of this path
+constexpr int kTP = 128;         // points per tile = MMA M = TMEM lanes
+constexpr int kWP = kW + 16;     // activation tile width incl. ones column
+constexpr int kDP = 128;         // delta tile width (zero-padded to M = 128)
+constexpr int kXP = 16;          // input tile width: x', 1, zeros
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+
+ADS_D uint32_t core_off(int r, int c, int rg) {
+  return (uint32_t)((r >> 3) * rg + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+
+ADS_D uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, no swizzle
+}
+// K-major view of a tile (rows = M/N, columns = K), k-step of 16 columns
+ADS_D uint64_t desc_k(uint32_t base, int rg, int kstep) {
+  return sdesc(base + kstep * 256, 128, rg);
+}
+// MN-major view of a tile (rows = K, columns = M/N), k-step of 16 rows
+ADS_D uint64_t desc_mn(uint32_t base, int rg, int kstep) {
+  return sdesc(base + kstep * 2 * rg, rg, 128);
+}
+// instruction descriptor: BF16 x BF16 -> FP32, M x N, operand majors
+ADS_HD uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+ADS_D void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+ADS_D void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_addr(mbar)));
+}
+ADS_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+ADS_D void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+ADS_D void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+ADS_D unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the mbarrier phase `parity`, giving up after about a second
+// (returns false then; the caller records an error and stops)
+ADS_D bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (now_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+
+
+// CTA barrier that also orders tcgen05 operations and generic-proxy shared
+// stores before the tensor cores read them; returns the CTA-uniform abort flag
+ADS_D bool sync_abort(volatile int* abort_flag) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *abort_flag != 0;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+ADS_D void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+ADS_D float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+ADS_D uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// write 8 values (one 16-byte atom) of row r starting at column c (c % 8 == 0)
+ADS_D void st_atom(unsigned char* tile, int rg, int r, int c, const float v[8]) {
+  uint4 q;
+  q.x = pack_bf16(v[0], v[1]);
+  q.y = pack_bf16(v[2], v[3]);
+  q.z = pack_bf16(v[4], v[5]);
+  q.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(tile + core_off(r, c, rg)) = q;
+}
+ADS_D void ld_atom(const unsigned char* tile, int rg, int r, int c, float v[8]) {
+  uint4 q = *reinterpret_cast<const uint4*>(tile + core_off(r, c, rg));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 f = __bfloat1622float2(h[j]);
+    v[2 * j] = f.x;
+    v[2 * j + 1] = f.y;
+  }
+}
+
+template <int DIN>
+ADS_D void coords(int idx, int N, float c[3]) {
+  const int m = N - 1;
+  const float invN = 1.0f / (float)N;
+  c[0] = 2.0f * (float)(idx % m + 1) * invN - 1.0f;
+  c[1] = 2.0f * (float)((idx / m) % m + 1) * invN - 1.0f;
+  c[2] = DIN == 3 ? 2.0f * (float)(idx / (m * m) + 1) * invN - 1.0f : 0.0f;
+}
+
+// load the three hidden weight matrices W_l[o][k] (FP32 master) as BF16 tiles
+ADS_D void load_hidden_weights(const float* th, int o2, unsigned char* wt, int tid, int nthr) {
+  constexpr int RG = (kW / 8) * 128;
+  for (int e = tid; e < 3 * kW * (kW / 8); e += nthr) {
+    const int l = e / (kW * (kW / 8)), rem = e % (kW * (kW / 8));
+    const int o = rem / (kW / 8), c = (rem % (kW / 8)) * 8;
+    const float* src = th + o2 + l * (kW * kW + kW) + o * kW + c;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = src[j];
+    st_atom(wt + l * kW * kW * 2, RG, o, c, v);
+  }
+}
+
+struct TcSmemF {
+  // byte offsets
+  static constexpr int W = 0;                          // 3 x [64][64] bf16 = 24 KB
+  static constexpr int ACT = W + 3 * kW * kW * 2;      // [128][64] bf16 = 16 KB
+  static constexpr int BIAS = ACT + kTP * kW * 2;      // fp32: b1 b2 b3 b4 [4][64], W1 [64][3], W5 [64], b5
+  static constexpr int NBIAS = 4 * kW + 3 * kW + kW + 4;
+  static constexpr int BAR = BIAS + NBIAS * 4;         // mbarrier (8 B) + tmem base (4 B)
+  static constexpr int TOTAL = BAR + 32;
+};
+
+template <int DIN>
+__global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* wt = sm + TcSmemF::W;
+  unsigned char* act = sm + TcSmemF::ACT;
+  float* fb = reinterpret_cast<float*>(sm + TcSmemF::BIAS);
+  float* fW1 = fb + 4 * kW;
+  float* fW5 = fW1 + 3 * kW;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemF::BAR);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemF::BAR + 8);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemF::BAR + 12);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int RG = (kW / 8) * 128;
+  const float* th = a.theta;
+  const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
+  load_hidden_weights(th, o2, wt, tid, kTP);
+  for (int i = tid; i < kW; i += kTP) {
+    fb[i] = th[ob1 + i];
+    for (int l = 0; l < 3; ++l) fb[(l + 1) * kW + i] = th[o2 + l * (kW * kW + kW) + kW * kW + i];
+    for (int d = 0; d < DIN; ++d) fW1[i * 3 + d] = th[i * DIN + d];
+    fW5[i] = th[o5 + i];
+  }
+  if (tid == 0) {
+    fW5[kW] = th[o5 + kW];
+    *abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tbase)), "r"(kW));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t idesc = idesc_bf16(kTP, kW, 0, 0);
+  const uint32_t act_s = smem_addr(act), wt_s = smem_addr(wt);
+  uint32_t phase = 0;
+  bool aborted = false;
+  const int ntiles = (a.npts + kTP - 1) / kTP;
+  const float b5 = fW5[kW];
+  for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+    const int p0 = tile * kTP;
+    const int idx = min(p0 + tid, a.npts - 1);
+    float x[3];
+    coords<DIN>(idx, a.N, x);
+    unsigned char* gtile = a.acts ? a.acts + (size_t)tile * 4 * kTP * kW * 2 : nullptr;
+    // layer 1 on the CUDA cores
+#pragma unroll
+    for (int c = 0; c < kW; c += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int o = c + j;
+        float z = fb[o];
+#pragma unroll
+        for (int d = 0; d < DIN; ++d) z += fW1[o * 3 + d] * x[d];
+        v[j] = tanh_fast(z);
+      }
+      st_atom(act, RG, tid, c, v);
+      if (gtile) st_atom(gtile, RG, tid, c, v);
+    }
+    float u = b5;
+    for (int l = 0; l < 3; ++l) {
+      if (sync_abort(abort_flag)) {
+        aborted = true;
+        break;
+      }
+      if (tid == 0) {
+#pragma unroll
+        for (int ks = 0; ks < kW / 16; ++ks)
+          mma_bf16(tmem, desc_k(act_s, RG, ks), desc_k(wt_s + l * kW * kW * 2, RG, ks), idesc,
+                   ks > 0);
+        mma_commit(mbar);
+      }
+      if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+      phase ^= 1;
+      tc_fence_after();
+      const float* bl = fb + (l + 1) * kW;
+#pragma unroll
+      for (int c = 0; c < kW; c += 16) {
+        float d[16];
+        tmem_ld16(lane_base + c, d);
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = tanh_fast(d[j] + bl[c + j]);
+        st_atom(act, RG, tid, c, v);
+        st_atom(act, RG, tid, c + 8, v + 8);
+        unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * kW * 2 : nullptr;
+        if (g) {
+          st_atom(g, RG, tid, c, v);
+          st_atom(g, RG, tid, c + 8, v + 8);
+        }
+        if (l == 2) {
+          // the output layer uses the BF16-rounded activations, like the backward
+          float r[8];
+          ld_atom(act, RG, tid, c, r);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) u += fW5[c + j] * r[j];
+          ld_atom(act, RG, tid, c + 8, r);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) u += fW5[c + 8 + j] * r[j];
+        }
+      }
+    }
+    if (!aborted && p0 + tid < a.npts) a.u[p0 + tid] = u;
+  }
+  if (sync_abort(abort_flag) && tid == 0) atomicOr(a.flags, 8);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kW));
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+struct TcSmemB {
+  static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
+  static constexpr int ACT = W + 3 * kW * kW * 2;          // 4 x [128][80] bf16      80 KB
+  static constexpr int ACT_SZ = kTP * kWP * 2;
+  static constexpr int DEL = ACT + 4 * ACT_SZ;             // 2 x [128][128] bf16     64 KB
+  static constexpr int DEL_SZ = kTP * kDP * 2;
+  static constexpr int XIN = DEL + 2 * DEL_SZ;             // [128][16] bf16          4 KB
+  static constexpr int VEC = XIN + kTP * kXP * 2;          // fp32: W5 [64], g [128]
+  static constexpr int BAR = VEC + (kW + kTP) * 4;
+  static constexpr int TOTAL = BAR + 32;
+};
+// TMEM columns: delta product [0,64), dW5 [64,144), dW4 [144,224),
+// dW3 [224,304), dW2 [304,384), dW1 [384,400)
+constexpr int kColDel = 0, kColW5 = 64, kColW4 = 144, kColW1 = 384;
+ADS_D int col_dw(int L) { return L == 5 ? kColW5 : (L == 1 ? kColW1 : kColW4 + (4 - L) * kWP); }
+
+template <int DIN>
+__global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* wt = sm + TcSmemB::W;
+  unsigned char* act = sm + TcSmemB::ACT;  // a_1..a_4 with ones column
+  unsigned char* del = sm + TcSmemB::DEL;  // two delta tiles
+  unsigned char* xin = sm + TcSmemB::XIN;
+  float* fW5 = reinterpret_cast<float*>(sm + TcSmemB::VEC);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB::BAR);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 8);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 12);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int RGW = (kW / 8) * 128, RGA = (kWP / 8) * 128, RGD = (kDP / 8) * 128,
+                RGX = (kXP / 8) * 128;
+  const float* th = a.theta;
+  const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
+  load_hidden_weights(th, o2, wt, tid, kTP);
+  for (int i = tid; i < kW; i += kTP) fW5[i] = th[o5 + i];
+  // constant columns: ones column of the activation tiles and of the input
+  // tile, zero padding of the delta tiles
+  {
+    float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int L = 0; L < 4; ++L) {
+      st_atom(act + L * TcSmemB::ACT_SZ, RGA, tid, kW, one);
+      st_atom(act + L * TcSmemB::ACT_SZ, RGA, tid, kW + 8, zero);
+    }
+    for (int b = 0; b < 2; ++b)
+      for (int c = kW; c < kDP; c += 8) st_atom(del + b * TcSmemB::DEL_SZ, RGD, tid, c, zero);
+  }
+  if (tid == 0) {
+    *abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tbase)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
+                 xin_s = smem_addr(xin);
+  const uint32_t id_dw = idesc_bf16(kDP, kWP, 1, 1);   // dW_l: M = 128 (o), N = 80, K = points
+  const uint32_t id_dw1 = idesc_bf16(kDP, kXP, 1, 1);  // dW_1: N = 16
+  const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);    // delta product: M = points, N = 64, K = 64
+  uint32_t phase = 0;
+  bool aborted = false;
+  bool first = true;  // first tile of this CTA: overwrite the dW accumulators
+  const int ntiles = (a.npts + kTP - 1) / kTP;
+  auto wait_mma = [&]() {
+    if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+    phase ^= 1;
+    tc_fence_after();
+  };
+  for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+    const int p0 = tile * kTP;
+    // every product of the previous tile completed (waited) before its end;
+    // stage this tile's activations (16-byte async copies into the padded tiles)
+    const unsigned char* gtile = a.acts + (size_t)tile * 4 * kTP * kW * 2;
+    for (int ch = tid; ch < 4 * kTP * (kW / 8); ch += kTP) {
+      const int L = ch / (kTP * (kW / 8)), rem = ch % (kTP * (kW / 8));
+      const int r = rem / (kW / 8), c = (rem % (kW / 8)) * 8;
+      cp_async16(act + L * TcSmemB::ACT_SZ + core_off(r, c, RGA),
+                 gtile + (size_t)L * kTP * kW * 2 + core_off(r, c, RGW));
+    }
+    cp_async_commit();
+    const int idx = p0 + tid;
+    const float g = idx < a.npts ? a.gu[idx] : 0.0f;
+    {
+      float x[3];
+      coords<DIN>(min(idx, a.npts - 1), a.N, x);
+      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int d = 0; d < DIN; ++d) v[d] = x[d];
+      v[DIN] = 1.0f;
+      st_atom(xin, RGX, tid, 0, v);
+      st_atom(xin, RGX, tid, 8, z);
+      // Delta_5 = [g, 0, ..., 0] in delta tile 0
+      float d5[8] = {g, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      st_atom(del, RGD, tid, 0, d5);
+      for (int c = 8; c < kW; c += 8) st_atom(del, RGD, tid, c, z);
+    }
+    cp_async_wait_all();
+    if (sync_abort(abort_flag)) {
+      aborted = true;
+      break;
+    }
+    // output layer: dW_5 (row 0) and db_5 from Delta_5^T [a_4 | 1]
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kTP / 16; ++ks)
+        mma_bf16(tmem + col_dw(5), desc_mn(del_s, RGD, ks), desc_mn(act_s + 3 * TcSmemB::ACT_SZ, RGA, ks),
+                 id_dw, (ks > 0 || !first) ? 1u : 0u);
+    }
+    // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1
+    {
+      unsigned char* d4 = del + TcSmemB::DEL_SZ;
+#pragma unroll
+      for (int c = 0; c < kW; c += 8) {
+        float av[8], v[8];
+        ld_atom(act + 3 * TcSmemB::ACT_SZ, RGA, tid, c, av);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
+        st_atom(d4, RGD, tid, c, v);
+      }
+    }
+    int cur = 1;  // delta tile holding Delta_L
+    for (int L = 4; L >= 2; --L) {
+      if (sync_abort(abort_flag)) {
+        aborted = true;
+        break;
+      }
+      const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
+      const uint32_t ain = act_s + (L - 2) * TcSmemB::ACT_SZ;  // a_{L-1}
+      if (tid == 0) {
+        // dW_L, db_L += Delta_L^T [a_{L-1} | 1]
+#pragma unroll
+        for (int ks = 0; ks < kTP / 16; ++ks)
+          mma_bf16(tmem + col_dw(L), desc_mn(dcur, RGD, ks), desc_mn(ain, RGA, ks), id_dw,
+                   (ks > 0 || !first) ? 1u : 0u);
+        // Delta_L W_L
+        const uint32_t wl = wt_s + (L - 2) * kW * kW * 2;
+#pragma unroll
+        for (int ks = 0; ks < kW / 16; ++ks)
+          mma_bf16(tmem + kColDel, desc_k(dcur, RGD, ks), desc_mn(wl, RGW, ks), id_dp, ks > 0);
+        mma_commit(mbar);
+      }
+      wait_mma();
+      // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
+      unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
+#pragma unroll
+      for (int c = 0; c < kW; c += 16) {
+        float dv[16];
+        tmem_ld16(lane_base + kColDel + c, dv);
+        float av[8], v[8];
+        ld_atom(act + (L - 2) * TcSmemB::ACT_SZ, RGA, tid, c, av);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = dv[j] * (1.0f - av[j] * av[j]);
+        st_atom(dn, RGD, tid, c, v);
+        ld_atom(act + (L - 2) * TcSmemB::ACT_SZ, RGA, tid, c + 8, av);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = dv[8 + j] * (1.0f - av[j] * av[j]);
+        st_atom(dn, RGD, tid, c + 8, v);
+      }
+      cur = 1 - cur;
+    }
+    if (aborted) break;
+    // first layer: dW_1, db_1 += Delta_1^T [x' | 1]
+    if (sync_abort(abort_flag)) {
+      aborted = true;
+      break;
+    }
+    if (tid == 0) {
+      const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
+#pragma unroll
+      for (int ks = 0; ks < kTP / 16; ++ks)
+        mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s, RGX, ks), id_dw1,
+                 (ks > 0 || !first) ? 1u : 0u);
+      mma_commit(mbar);
+    }
+    wait_mma();  // all of this tile's products are complete before its tiles are reused
+    first = false;
+  }
+  // gradient row of this CTA: TMEM lane o = thread; rows o >= 64 are padding.
+  // Every thread issues the same TMEM loads (they are warp-collective).
+  float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
+  const int o = tid;
+  aborted = sync_abort(abort_flag);
+  if (!aborted && !first) {
+    for (int L = 4; L >= 2; --L) {
+      const int ow = o2 + (L - 2) * (kW * kW + kW);
+      for (int c = 0; c < kWP; c += 16) {
+        float v[16];
+        tmem_ld16(lane_base + col_dw(L) + c, v);
+        if (o < kW) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int k = c + j;
+            if (k < kW) gacc[ow + o * kW + k] = v[j];
+            else if (k == kW) gacc[ow + kW * kW + o] = v[j];
+          }
+        }
+      }
+    }
+    {
+      float v[16];
+      tmem_ld16(lane_base + col_dw(1), v);
+      if (o < kW) {
+        for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
+        gacc[ob1 + o] = v[DIN];
+      }
+    }
+    for (int c = 0; c < kWP; c += 16) {
+      float v[16];
+      tmem_ld16(lane_base + col_dw(5) + c, v);
+      if (o == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = c + j;
+          if (k < kW) gacc[o5 + k] = v[j];
+          else if (k == kW) gacc[o5 + kW] = v[j];
+        }
+      }
+    }
+  } else if (first) {
+    for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;  // CTA without tiles
+  }
+  if (aborted && tid == 0) atomicOr(a.flags, 8);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+int g_sms = 0;
+int sms() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+}  // namespace
+
+size_t mlp_tc_acts_bytes(int npts, int width) {
+  int ntiles = (npts + kTP - 1) / kTP;
+  return (size_t)ntiles * 4 * kTP * width * 2;
+}
+
+int mlp_tc_bwd_blocks(int npts) {
+  int ntiles = (npts + kTP - 1) / kTP;
+  return ntiles < sms() ? ntiles : sms();  // 512 TMEM columns: one CTA per SM
+}
+
+cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
+  if (a.width != kW) return cudaErrorNotSupported;
+  if (a.npts <= 0) return cudaSuccess;
+  const int ntiles = (a.npts + kTP - 1) / kTP;
+  const size_t smem = TcSmemF::TOTAL;
+  if (a.din == 2) {
+    cudaFuncSetAttribute(k_mlp_fwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = ntiles < 4 * sms() ? ntiles : 4 * sms();
+    k_mlp_fwd_tc<2><<<grid, kTP, smem, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_mlp_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = ntiles < 4 * sms() ? ntiles : 4 * sms();
+    k_mlp_fwd_tc<3><<<grid, kTP, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
+  if (a.width != kW) return cudaErrorNotSupported;
+  const size_t smem = TcSmemB::TOTAL;
+  if (a.din == 2) {
+    cudaFuncSetAttribute(k_mlp_bwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mlp_bwd_tc<2><<<nblk, kTP, smem, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_mlp_bwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mlp_bwd_tc<3><<<nblk, kTP, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace adsgb

@@ -11,7 +11,7 @@ import numpy as np
 
 from . import _lib as L
 
-_DT = {"f64": L.ADS_F64, "f32": L.ADS_F32}
+_DT = {"f64": L.ADS_F64, "f32": L.ADS_F32, "bf16": L.ADS_BF16}
 
 
 def _dptr(a: np.ndarray):
@@ -42,6 +42,8 @@ class HybridSolver:
                  ads_dtype: str = "f64", stream=None):
         self.lib = L.load()
         self.sc = sc
+        if ads_dtype not in ("f64", "f32"):
+            raise ValueError("ads_dtype must be f64 or f32")
         self.params = make_params(sc, ads_dtype)
         self.crv = None
         if width is not None:

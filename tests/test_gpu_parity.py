@@ -293,3 +293,85 @@ def test_pretrain_reduces_loss_and_approaches_direct_solution():
     print(f"pressure rel L2 vs direct after 1500 Adam iterations: {err:.3e}")
     assert err < 0.2
     s.close()
+
+
+# ----------------------------------------------------------------------------
+# BF16 tensor-core network (tcgen05): operands rounded to BF16 (unit
+# round-off 2^-9 ~ 2e-3), FP32 accumulation.  Each stored activation and
+# weight carries ~2e-3 relative rounding, so the loss and gradient are
+# compared at 1e-2 (loss) and 2e-2 (gradient, relative L2), and the gradient
+# direction must agree to cosine >= 0.9995.
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [3, 9, 33, 130])
+def test_loss_and_gradient_bf16_tensor_cores(n):
+    sc, s, crv, theta, alpha, f = _crv_case(n, "bf16", width=64)
+    loss = s.loss_grad()
+    ref_loss, ref_grad, parts = crv.loss_grad(MLP(2, 64, 4), theta, alpha, f)
+    assert np.abs(s.get("U") - parts["u"]).max() <= 2e-2 * max(1.0, np.abs(parts["u"]).max())
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    g = s.get("GRAD")
+    assert rel_l2(g, ref_grad) <= 2e-2
+    assert g @ ref_grad / (np.linalg.norm(g) * np.linalg.norm(ref_grad)) >= 0.9995
+    s.close()
+
+
+def test_bf16_training_converges_to_direct_solution():
+    n = 64
+    sc = scn.make_scenario(2, n, seed=1000)
+    s = solver(sc, width=64, crv_dtype="bf16", ads_dtype="f32")
+    s.set_theta(scn.make_theta0(2, 64, 4, seed=7))
+    s.update_coefficients()
+    l0 = s.loss_grad()
+    l1 = s.pretrain(3000, 1e-3)
+    assert l1 < 0.02 * l0
+    crv = CrvOracle(sc)
+    alpha, f = crv.coefficients(sc.S0_or_zero())
+    ustar = crv.direct_solution(alpha, f)
+    s.project_pressure()
+    err = rel_l2(s.get("U"), ustar)
+    print(f"BF16 network: pressure rel L2 vs direct after 3000 Adam iterations: {err:.3e}")
+    assert err < 0.15
+    s.close()
+
+
+def test_bf16_hybrid_step_runs_and_conserves_mass():
+    n = 48
+    sc = scn.make_scenario(2, n, seed=1001)
+    s = solver(sc, width=64, crv_dtype="bf16", ads_dtype="f32")
+    s.set_theta(scn.make_theta0(2, 64, 4, seed=7))
+    s.pretrain(200, 1e-3)
+    hp = s.hybrid_params(n_sub=10, dt=1.0, dt_policy=1, adam_iters=20, lr=1e-3)
+    for _ in range(3):
+        st = s.hybrid_step(hp)
+    assert np.isfinite(st["loss_last"]) and st["dt_used"] > 0
+    assert abs(st["mass_err"]) <= 1e-5 * max(st["mass_total"], 1e-3)
+    s.close()
+
+
+# ----------------------------------------------------------------------------
+# hand-written adjoint (the FP64 GPU gradient) against central finite
+# differences of the oracle's FP64 loss along 16 random unit directions
+# ----------------------------------------------------------------------------
+
+def test_adjoint_vs_finite_differences_16_directions():
+    n = 24
+    sc, s, crv, theta, alpha, f = _crv_case(n, "f64", seed=11)
+    s.loss_grad()
+    g = s.get("GRAD")
+    mlp = MLP(2, 64, 4)
+    rng = np.random.default_rng(11)
+    scale = np.linalg.norm(theta)
+    for eps_rel in (1e-2, 1e-3):
+        errs = []
+        for _ in range(16):
+            d = rng.normal(size=theta.size)
+            d /= np.linalg.norm(d)
+            eps = eps_rel * scale / np.sqrt(theta.size)
+            lp = crv.loss_grad(mlp, theta + eps * d, alpha, f, with_grad=False)[0]
+            lm = crv.loss_grad(mlp, theta - eps * d, alpha, f, with_grad=False)[0]
+            fd = (lp - lm) / (2 * eps)
+            errs.append(abs(g @ d - fd) / max(abs(fd), 1e-12 * np.linalg.norm(g)))
+        print(f"FD check eps_rel={eps_rel}: max relative deviation {max(errs):.2e}")
+        assert max(errs) < 1e-3
+    s.close()
