@@ -215,6 +215,63 @@ ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stat
 ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
                              hybrid_stats* stats);
 
+/* ---- serving: continuous batching of many scenarios (the benchmark spec pattern; the
+ * paper has one scenario) ---------------------------------------------------
+ * A server owns a worker thread and n_streams CUDA streams on the current
+ * device.  ads_server_submit copies a scenario (parameters, network, hybrid
+ * step parameters, number of hybrid steps, pretraining at admission, and its
+ * host arrays) into the arrival queue and returns at once.  Between rounds the
+ * worker admits the oldest waiting scenarios while the sum of their
+ * ads_hbm_estimate stays within hbm_budget and at most max_active are
+ * resident; each round enqueues one hybrid step of every resident scenario
+ * (streams round-robin, so their kernels overlap) and records each step's
+ * latency from enqueue to completion.  A scenario that has run n_steps copies
+ * its saturation and pressure coefficients out and frees its memory, which
+ * admits the next arrivals.  Results depend only on the scenario's inputs:
+ * alone or in any mix they are identical.
+ * ads_server_wait blocks until request `id` finished (or timeout_s passed:
+ * ADS_ERR_TIMEOUT), copies S and P ((n+2)^dim doubles each, nullable) and its
+ * statistics, and forgets the request.  A scenario whose estimate exceeds the
+ * whole budget is refused at submission (ADS_ERR_OOM).
+ * ads_server_destroy stops the worker, releases resident scenarios and drops
+ * waiting ones. */
+typedef struct ads_server ads_server;
+typedef struct {
+  size_t hbm_budget;   /* bytes of device memory for resident scenarios      */
+  int max_active;      /* cap on resident scenarios                           */
+  int n_streams;       /* CUDA streams the resident scenarios share (1..64)   */
+} ads_server_config;
+typedef struct {
+  ads_params params;
+  crvpinn_params crv;
+  hybrid_params hp;
+  int n_steps;         /* hybrid steps to run                                 */
+  int pretrain_iters;  /* Adam iterations at admission (0: none)              */
+  double pretrain_lr;
+} ads_request_spec;
+typedef struct {
+  int status;          /* ads_status of the request                           */
+  int steps;
+  double queue_ms;     /* submission to admission                             */
+  double total_ms;     /* submission to completion                            */
+  double p50_step_ms, p99_step_ms;
+  hybrid_stats last;
+} ads_request_result;
+typedef struct {
+  int64_t completed, rejected, steps, pending, active;
+  int peak_active;
+  size_t bytes_in_use, peak_bytes;
+  double p50_step_ms, p99_step_ms;  /* over all completed scenarios' steps     */
+} ads_server_stats_t;
+ads_status ads_server_create(const ads_server_config* cfg, ads_server** out);
+ads_status ads_server_submit(ads_server* s, const ads_request_spec* spec, const double* K_nodal,
+                             const double* phi_nodal, const double* S0, const double* theta0,
+                             int64_t* id_out);
+ads_status ads_server_wait(ads_server* s, int64_t id, double timeout_s, double* S_out,
+                           double* P_out, ads_request_result* result);
+ads_status ads_server_stats(ads_server* s, ads_server_stats_t* out);
+void ads_server_destroy(ads_server* s);
+
 /* ---- data access -------------------------------------------------------------
  * ads_get: copy a field to host doubles (count = number of values expected
  * for the field; ADS_ERR_INVALID_ARG if it differs).  Waits for the stream.

@@ -49,6 +49,28 @@ class hybrid_stats(C.Structure):
                 ("mass_total", C.c_double)]
 
 
+class ads_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("n_streams", C.c_int)]
+
+
+class ads_request_spec(C.Structure):
+    _fields_ = [("params", ads_params), ("crv", crvpinn_params), ("hp", hybrid_params),
+                ("n_steps", C.c_int), ("pretrain_iters", C.c_int), ("pretrain_lr", C.c_double)]
+
+
+class ads_request_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("steps", C.c_int), ("queue_ms", C.c_double),
+                ("total_ms", C.c_double), ("p50_step_ms", C.c_double), ("p99_step_ms", C.c_double),
+                ("last", hybrid_stats)]
+
+
+class ads_server_stats_t(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("rejected", C.c_int64), ("steps", C.c_int64),
+                ("pending", C.c_int64), ("active", C.c_int64), ("peak_active", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("p50_step_ms", C.c_double), ("p99_step_ms", C.c_double)]
+
+
 # every exported symbol with its signature (restype, argtypes)
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
@@ -81,6 +103,12 @@ SIGNATURES = {
     "ads_kernel_launches": (C.c_int, [_P, C.POINTER(C.c_ulonglong)]),
     "ads_profile_train": (C.c_int, [_P, C.c_int, _D]),
     "ads_profile_saturation": (C.c_int, [_P, C.c_int, _D]),
+    "ads_server_create": (C.c_int, [C.POINTER(ads_server_config), C.POINTER(_P)]),
+    "ads_server_submit": (C.c_int, [_P, C.POINTER(ads_request_spec), _D, _D, _D, _D,
+                                    C.POINTER(C.c_int64)]),
+    "ads_server_wait": (C.c_int, [_P, C.c_int64, C.c_double, _D, _D, C.POINTER(ads_request_result)]),
+    "ads_server_stats": (C.c_int, [_P, C.POINTER(ads_server_stats_t)]),
+    "ads_server_destroy": (None, [_P]),
     "ads_last_error": (C.c_char_p, [_P]),
     "ads_status_str": (C.c_char_p, [C.c_int]),
 }

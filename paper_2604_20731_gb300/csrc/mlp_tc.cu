@@ -11,11 +11,14 @@
 // Forward, per tile of 128 collocation points (one CTA of 128 threads, thread
 // t = point t = TMEM lane t):
 //   a_1 = tanh(W_1 x' + b_1) on the CUDA cores (K = 2 or 3);
-//   for the three hidden layers: D[t][o] = sum_k a[t][k] W[o][k] (one
-//   128 x 64 x 64 MMA chain, issued by one thread), then each thread reads
-//   its row of D from TMEM, adds the bias, applies tanh and writes the BF16
-//   row back as the next A operand (and, for the backward pass, to HBM);
-//   u = W_5 a_4 + b_5 from registers.
+//   for the three hidden layers: D[t][o] = sum_k a[t][k] W[o][k] with the
+//   activations held as a BF16 pair a = a_hi + a_lo (two 128 x 64 x 64 MMA
+//   chains into one FP32 accumulator, issued by one thread) -- the residual
+//   differences neighbouring network values, so per-point rounding of the
+//   activations to BF16 alone would swamp it on fine grids; each thread then
+//   reads its row of D from TMEM, adds the bias, applies tanh and writes the
+//   next pair (and, for the backward pass, the BF16 row to HBM);
+//   u = W_5 a_4 + b_5 in FP32 from registers.
 // Backward, per tile (persistent CTAs; gradients accumulate in TMEM over all
 // of a CTA's tiles):
 //   D_l (for dW_l, db_l) += Delta_l^T [a_{l-1} | 1] -- M = 128 output rows
@@ -129,11 +132,6 @@ ADS_D void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-ADS_D float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 ADS_D uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -149,6 +147,23 @@ ADS_D void st_atom(unsigned char* tile, int rg, int r, int c, const float v[8]) 
   q.w = pack_bf16(v[6], v[7]);
   *reinterpret_cast<uint4*>(tile + core_off(r, c, rg)) = q;
 }
+// the same 8 values as a BF16 pair hi + lo (hi = bf16(v), lo = bf16(v - hi)):
+// together they carry about 16 significant bits
+ADS_D void st_atom_split(unsigned char* hi, unsigned char* lo, int rg, int r, int c, const float v[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    float2 bf = __bfloat1622float2(b);
+    __nv_bfloat162 r2 = __floats2bfloat162_rn(v[2 * j] - bf.x, v[2 * j + 1] - bf.y);
+    h[j] = *reinterpret_cast<uint32_t*>(&b);
+    l[j] = *reinterpret_cast<uint32_t*>(&r2);
+  }
+  const uint32_t off = core_off(r, c, rg);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 ADS_D void ld_atom(const unsigned char* tile, int rg, int r, int c, float v[8]) {
   uint4 q = *reinterpret_cast<const uint4*>(tile + core_off(r, c, rg));
   const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
@@ -186,8 +201,9 @@ ADS_D void load_hidden_weights(const float* th, int o2, unsigned char* wt, int t
 struct TcSmemF {
   // byte offsets
   static constexpr int W = 0;                          // 3 x [64][64] bf16 = 24 KB
-  static constexpr int ACT = W + 3 * kW * kW * 2;      // [128][64] bf16 = 16 KB
-  static constexpr int BIAS = ACT + kTP * kW * 2;      // fp32: b1 b2 b3 b4 [4][64], W1 [64][3], W5 [64], b5
+  static constexpr int ACT = W + 3 * kW * kW * 2;      // [128][64] bf16 hi = 16 KB
+  static constexpr int ACTLO = ACT + kTP * kW * 2;     // [128][64] bf16 lo = 16 KB
+  static constexpr int BIAS = ACTLO + kTP * kW * 2;    // fp32: b1 b2 b3 b4 [4][64], W1 [64][3], W5 [64], b5
   static constexpr int NBIAS = 4 * kW + 3 * kW + kW + 4;
   static constexpr int BAR = BIAS + NBIAS * 4;         // mbarrier (8 B) + tmem base (4 B)
   static constexpr int TOTAL = BAR + 32;
@@ -198,6 +214,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemF::W;
   unsigned char* act = sm + TcSmemF::ACT;
+  unsigned char* actlo = sm + TcSmemF::ACTLO;
   float* fb = reinterpret_cast<float*>(sm + TcSmemF::BIAS);
   float* fW1 = fb + 4 * kW;
   float* fW5 = fW1 + 3 * kW;
@@ -233,7 +250,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   const uint32_t tmem = *tbase;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
   const uint32_t idesc = idesc_bf16(kTP, kW, 0, 0);
-  const uint32_t act_s = smem_addr(act), wt_s = smem_addr(wt);
+  const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(wt);
   uint32_t phase = 0;
   bool aborted = false;
   const int ntiles = (a.npts + kTP - 1) / kTP;
@@ -254,9 +271,9 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
         float z = fb[o];
 #pragma unroll
         for (int d = 0; d < DIN; ++d) z += fW1[o * 3 + d] * x[d];
-        v[j] = tanh_fast(z);
+        v[j] = tanh_f32(z);
       }
-      st_atom(act, RG, tid, c, v);
+      st_atom_split(act, actlo, RG, tid, c, v);
       if (gtile) st_atom(gtile, RG, tid, c, v);
     }
     float u = b5;
@@ -266,10 +283,14 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
         break;
       }
       if (tid == 0) {
+        // (a_hi + a_lo) W: two BF16 products into one FP32 accumulator
 #pragma unroll
         for (int ks = 0; ks < kW / 16; ++ks)
           mma_bf16(tmem, desc_k(act_s, RG, ks), desc_k(wt_s + l * kW * kW * 2, RG, ks), idesc,
                    ks > 0);
+#pragma unroll
+        for (int ks = 0; ks < kW / 16; ++ks)
+          mma_bf16(tmem, desc_k(actlo_s, RG, ks), desc_k(wt_s + l * kW * kW * 2, RG, ks), idesc, 1u);
         mma_commit(mbar);
       }
       if (!mbar_wait(mbar, phase)) *abort_flag = 1;
@@ -282,23 +303,20 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
         tmem_ld16(lane_base + c, d);
         float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = tanh_fast(d[j] + bl[c + j]);
-        st_atom(act, RG, tid, c, v);
-        st_atom(act, RG, tid, c + 8, v + 8);
+        for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[j] + bl[c + j]);
+        if (l < 2) {
+          st_atom_split(act, actlo, RG, tid, c, v);
+          st_atom_split(act, actlo, RG, tid, c + 8, v + 8);
+        }
         unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * kW * 2 : nullptr;
         if (g) {
           st_atom(g, RG, tid, c, v);
           st_atom(g, RG, tid, c + 8, v + 8);
         }
         if (l == 2) {
-          // the output layer uses the BF16-rounded activations, like the backward
-          float r[8];
-          ld_atom(act, RG, tid, c, r);
+          // the output layer in FP32 from the unrounded activations
 #pragma unroll
-          for (int j = 0; j < 8; ++j) u += fW5[c + j] * r[j];
-          ld_atom(act, RG, tid, c + 8, r);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) u += fW5[c + 8 + j] * r[j];
+          for (int j = 0; j < 16; ++j) u += fW5[c + j] * v[j];
         }
       }
     }

@@ -201,3 +201,75 @@ def hybrid_step_batch(solvers, hp: L.hybrid_params, stats: bool = False):
         return [dict(dt_used=s.dt_used, loss_last=s.loss_last, mass_err=s.mass_err,
                      mass_total=s.mass_total) for s in out]
     return None
+
+
+class Server:
+    """Continuous-batching server (ads_server_* in the C ABI): scenarios are
+    submitted as they arrive, admitted by device-memory budget, stepped in
+    rounds on several streams, and collected with wait()."""
+
+    def __init__(self, hbm_budget: int = 8 << 30, max_active: int = 64, n_streams: int = 8):
+        self.lib = L.load()
+        cfg = L.ads_server_config(int(hbm_budget), int(max_active), int(n_streams))
+        h = C.c_void_p()
+        rc = self.lib.ads_server_create(C.byref(cfg), C.byref(h))
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, "ads_server_create")
+        self.h = h
+        self._shapes = {}
+
+    def submit(self, sc, n_steps: int, hp: L.hybrid_params, width: int = 64,
+               crv_dtype: str = "bf16", ads_dtype: str = "f32", pretrain_iters: int = 300,
+               pretrain_lr: float = 1e-3, theta0=None) -> int:
+        spec = L.ads_request_spec()
+        spec.params = make_params(sc, ads_dtype)
+        spec.crv = L.crvpinn_params(width, 4, _DT[crv_dtype])
+        spec.hp = hp
+        spec.n_steps = int(n_steps)
+        spec.pretrain_iters = int(pretrain_iters)
+        spec.pretrain_lr = float(pretrain_lr)
+        K = np.ascontiguousarray(sc.K, dtype=np.float64)
+        phi = None if sc.phi_map is None else np.ascontiguousarray(sc.phi_map, dtype=np.float64)
+        S0 = np.ascontiguousarray(sc.S0_or_zero(), dtype=np.float64)
+        th = None if theta0 is None else np.ascontiguousarray(theta0, dtype=np.float64)
+        rid = C.c_int64()
+        rc = self.lib.ads_server_submit(self.h, C.byref(spec), _dptr(K),
+                                        _dptr(phi) if phi is not None else None, _dptr(S0),
+                                        _dptr(th) if th is not None else None, C.byref(rid))
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, "ads_server_submit")
+        self._shapes[rid.value] = (sc.n + 2,) * sc.dim
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 600.0):
+        shape = self._shapes.pop(rid)
+        S = np.empty(shape)
+        P = np.empty(shape)
+        res = L.ads_request_result()
+        rc = self.lib.ads_server_wait(self.h, int(rid), float(timeout_s), _dptr(S), _dptr(P),
+                                      C.byref(res))
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, f"ads_server_wait({rid})")
+        info = dict(steps=res.steps, queue_ms=res.queue_ms, total_ms=res.total_ms,
+                    p50_step_ms=res.p50_step_ms, p99_step_ms=res.p99_step_ms,
+                    dt_used=res.last.dt_used, loss_last=res.last.loss_last,
+                    mass_err=res.last.mass_err, mass_total=res.last.mass_total)
+        return S, P, info
+
+    def stats(self) -> dict:
+        st = L.ads_server_stats_t()
+        rc = self.lib.ads_server_stats(self.h, C.byref(st))
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, "ads_server_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ads_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+"""Serving (continuous batching) on the GPU: admission by device-memory
+budget, overlap of resident scenarios, and identical results alone and in a
+mix of other scenarios."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2604_20731_gb300 import scenario as scn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _hp(solver_cls, steps_adam=20):
+    return solver_cls.hybrid_params(n_sub=10, dt=1.0, dt_policy=1, cfl=0.1, src_frac=0.05,
+                                    adam_iters=steps_adam, lr=1e-3)
+
+
+def test_alone_equals_in_mix():
+    from paper_2604_20731_gb300.solver import HybridSolver, Server
+    hp = _hp(HybridSolver)
+    target = scn.make_scenario(2, 48, seed=1200, rate=1.3)
+    theta = scn.make_theta0(2, 64, 4, seed=7)
+    srv = Server(hbm_budget=4 << 30, max_active=8, n_streams=4)
+    rid = srv.submit(target, n_steps=4, hp=hp, pretrain_iters=50, theta0=theta)
+    S_alone, P_alone, info = srv.wait(rid)
+    assert info["steps"] == 4
+    # the same scenario among others of different sizes, arriving while they run
+    ids = []
+    for k, n in enumerate((32, 64, 96, 40)):
+        sc = scn.make_scenario(2, n, seed=1300 + k, sigma=0.5 + 0.4 * k, rate=0.5 + 0.4 * k)
+        ids.append(srv.submit(sc, n_steps=6, hp=hp, pretrain_iters=50, theta0=theta))
+        if k == 1:
+            time.sleep(0.02)
+            rid2 = srv.submit(target, n_steps=4, hp=hp, pretrain_iters=50, theta0=theta)
+    S_mix, P_mix, info2 = srv.wait(rid2)
+    for i in ids:
+        S, P, inf = srv.wait(i)
+        assert inf["steps"] == 6 and np.isfinite(S).all()
+    assert np.array_equal(S_mix, S_alone)
+    assert np.array_equal(P_mix, P_alone)
+    st = srv.stats()
+    assert st["completed"] == 6 and st["p99_step_ms"] >= st["p50_step_ms"] > 0
+    assert st["peak_active"] >= 2  # the mix really overlapped
+    srv.close()
+
+
+def test_admission_respects_budget_and_rejects_oversize():
+    import ctypes as C
+    from paper_2604_20731_gb300 import _lib
+    from paper_2604_20731_gb300.solver import HybridSolver, Server, make_params
+    hp = _hp(HybridSolver, steps_adam=5)
+    lib = _lib.load()
+    sc = scn.make_scenario(2, 64, seed=5)
+    p = make_params(sc, "f32")
+    crv = _lib.crvpinn_params(64, 4, _lib.ADS_BF16)
+    est = lib.ads_hbm_estimate(C.byref(p), C.byref(crv))
+    srv = Server(hbm_budget=int(2.5 * est), max_active=16, n_streams=4)
+    ids = [srv.submit(scn.make_scenario(2, 64, seed=10 + i), n_steps=3, hp=hp, pretrain_iters=10)
+           for i in range(6)]
+    for i in ids:
+        srv.wait(i)
+    st = srv.stats()
+    assert st["completed"] == 6
+    assert st["peak_active"] <= 2
+    assert st["peak_bytes"] <= 2.5 * est
+    big = scn.make_scenario(2, 256, seed=1)
+    with pytest.raises(_lib.AdsError):
+        srv.submit(big, n_steps=1, hp=hp)
+    srv.close()
