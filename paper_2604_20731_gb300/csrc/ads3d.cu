@@ -1,0 +1,469 @@
+// IGA-ADS explicit saturation step in 3D (tensor quadratic B-splines on the
+// unit cube; Secs. 3-4 of the paper, written there for 2D, extended with the
+// third Kronecker factor: M = Mx (x) My (x) Mz).
+//
+//   k_elem3d:   one thread per element; fields at its 27 Gauss points are
+//               sum-factorised along x, y, z; the 27 local contributions to
+//               the right-hand side of the L2 projection are written to a
+//               per-element buffer (MODE 0: saturation step, MODE 1: L2
+//               projection of nodal values).
+//   k_gather3d: one thread per DOF sums the contributions of its (up to) 27
+//               elements in a fixed order (deterministic, no atomics).
+//   k_xsolve3d: LDL^T sweeps along x (contiguous rows staged in shared memory).
+//   k_line_slow: LDL^T sweeps along the slowest axis of a [batch][rows][cols]
+//               view (y: batch = z-planes; z: one batch of nb^2 columns), one
+//               thread per column, the column block staged in shared memory;
+//               optionally accumulates int S (z sweep).
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace adsgb {
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) k_elem3d(QuadArgs<T> a, T* C, double* src_part) {
+  __shared__ double red[32];
+  const int n = a.n, nb = a.nb, n1 = n + 1;
+  const long long ne = (long long)n * n * n;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double src = 0.0;
+  if (e < ne) {
+    const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((long long)n * n));
+    T bx[3][3], dbx[3][3], by[3][3], dby[3][3], bz[3][3], dbz[3][3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      bx[i / 3][i % 3] = a.ax.B[ex * 9 + i];
+      dbx[i / 3][i % 3] = a.ax.dB[ex * 9 + i];
+      by[i / 3][i % 3] = a.ax.B[ey * 9 + i];
+      dby[i / 3][i % 3] = a.ax.dB[ey * 9 + i];
+      bz[i / 3][i % 3] = a.ax.B[ez * 9 + i];
+      dbz[i / 3][i % 3] = a.ax.dB[ez * 9 + i];
+    }
+    // c-coefficients at the 27 Gauss points [qz][qy][qx]
+    T c0[3][3][3], cx[3][3][3], cy[3][3][3], cz[3][3][3];
+    const T h3 = a.h * a.h * a.h;
+    if (MODE == 0) {
+      // contraction along x for each (bz, by) row: S, P, dP/dx
+      T Sx[3][3][3], Px[3][3][3], Pdx[3][3][3];  // [bz][by][qx]
+#pragma unroll
+      for (int b2 = 0; b2 < 3; ++b2)
+#pragma unroll
+        for (int b1 = 0; b1 < 3; ++b1) {
+          const size_t row = ((size_t)(ez + b2) * nb + (ey + b1)) * nb + ex;
+          const T s0 = a.S[row], s1 = a.S[row + 1], s2 = a.S[row + 2];
+          const T p0 = a.P[row], p1 = a.P[row + 1], p2 = a.P[row + 2];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            Sx[b2][b1][q] = s0 * bx[0][q] + s1 * bx[1][q] + s2 * bx[2][q];
+            Px[b2][b1][q] = p0 * bx[0][q] + p1 * bx[1][q] + p2 * bx[2][q];
+            Pdx[b2][b1][q] = p0 * dbx[0][q] + p1 * dbx[1][q] + p2 * dbx[2][q];
+          }
+        }
+      // along y: S, P, dP/dx, dP/dy at (bz, qy, qx)
+      T Sy[3][3][3], Py[3][3][3], Pdxy[3][3][3], Pdy[3][3][3];
+#pragma unroll
+      for (int b2 = 0; b2 < 3; ++b2)
+#pragma unroll
+        for (int qy = 0; qy < 3; ++qy)
+#pragma unroll
+          for (int qx = 0; qx < 3; ++qx) {
+            Sy[b2][qy][qx] = by[0][qy] * Sx[b2][0][qx] + by[1][qy] * Sx[b2][1][qx] + by[2][qy] * Sx[b2][2][qx];
+            Py[b2][qy][qx] = by[0][qy] * Px[b2][0][qx] + by[1][qy] * Px[b2][1][qx] + by[2][qy] * Px[b2][2][qx];
+            Pdxy[b2][qy][qx] = by[0][qy] * Pdx[b2][0][qx] + by[1][qy] * Pdx[b2][1][qx] + by[2][qy] * Pdx[b2][2][qx];
+            Pdy[b2][qy][qx] = dby[0][qy] * Px[b2][0][qx] + dby[1][qy] * Px[b2][1][qx] + dby[2][qy] * Px[b2][2][qx];
+          }
+      // nodal K and phi at the 8 corners
+      T kc[2][2][2], fc[2][2][2];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
+        const size_t nd = ((size_t)(ez + dz) * n1 + (ey + dy)) * n1 + (ex + dx);
+        kc[dz][dy][dx] = a.K[nd];
+        fc[dz][dy][dx] = a.phi ? a.phi[nd] : a.phi_c;
+      }
+      const T dt = (T)(*a.dt);
+      for (int qz = 0; qz < 3; ++qz) {
+        const T zeta = (T)gauss_x(qz);
+        for (int qy = 0; qy < 3; ++qy) {
+          const T eta = (T)gauss_x(qy);
+          for (int qx = 0; qx < 3; ++qx) {
+            const T xi = (T)gauss_x(qx);
+            T Sv = bz[0][qz] * Sy[0][qy][qx] + bz[1][qz] * Sy[1][qy][qx] + bz[2][qz] * Sy[2][qy][qx];
+            T dpx = bz[0][qz] * Pdxy[0][qy][qx] + bz[1][qz] * Pdxy[1][qy][qx] + bz[2][qz] * Pdxy[2][qy][qx];
+            T dpy = bz[0][qz] * Pdy[0][qy][qx] + bz[1][qz] * Pdy[1][qy][qx] + bz[2][qz] * Pdy[2][qy][qx];
+            T dpz = dbz[0][qz] * Py[0][qy][qx] + dbz[1][qz] * Py[1][qy][qx] + dbz[2][qz] * Py[2][qy][qx];
+            T wz[2] = {T(1) - zeta, zeta}, wy[2] = {T(1) - eta, eta}, wx[2] = {T(1) - xi, xi};
+            T Kq = T(0), phq = T(0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
+              const T w = wz[dz] * wy[dy] * wx[dx];
+              Kq += w * kc[dz][dy][dx];
+              phq += w * fc[dz][dy][dx];
+            }
+            T St = clamp01(Sv);
+            T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
+            T qi = T(0), qp = T(0);
+            for (int s = 0; s < a.n_src; ++s) {
+              T g = a.rate[s] * a.ax.gsrc[((size_t)(0 * kMaxSrc + s) * n + ex) * 3 + qx] *
+                    a.ax.gsrc[((size_t)(1 * kMaxSrc + s) * n + ey) * 3 + qy] *
+                    a.ax.gsrc[((size_t)(2 * kMaxSrc + s) * n + ez) * 3 + qz];
+              if (a.kind[s] == 0) qi += g; else qp += g;
+            }
+            T qg = qi - lg / (lg + lw) * qp;
+            T w = (T)(gauss_w(qx) * gauss_w(qy) * gauss_w(qz)) * h3;
+            T dtphi = dt / phq;
+            c0[qz][qy][qx] = w * (Sv + dtphi * qg);
+            T cf = -w * dtphi * lg * Kq;
+            cx[qz][qy][qx] = cf * dpx;
+            cy[qz][qy][qx] = cf * dpy;
+            cz[qz][qy][qx] = cf * a.kz * (dpz + a.grav_term);
+            src += (double)(w * dtphi * qg);
+          }
+        }
+      }
+    } else {
+      T uc[2][2][2];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
+        uc[dz][dy][dx] = a.nodal[((size_t)(ez + dz) * n1 + (ey + dy)) * n1 + (ex + dx)];
+      }
+      for (int qz = 0; qz < 3; ++qz)
+        for (int qy = 0; qy < 3; ++qy)
+          for (int qx = 0; qx < 3; ++qx) {
+            const T zeta = (T)gauss_x(qz), eta = (T)gauss_x(qy), xi = (T)gauss_x(qx);
+            T wz[2] = {T(1) - zeta, zeta}, wy[2] = {T(1) - eta, eta}, wx[2] = {T(1) - xi, xi};
+            T uq = T(0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
+              uq += wz[dz] * wy[dy] * wx[dx] * uc[dz][dy][dx];
+            }
+            c0[qz][qy][qx] = (T)(gauss_w(qx) * gauss_w(qy) * gauss_w(qz)) * h3 * uq;
+            cx[qz][qy][qx] = cy[qz][qy][qx] = cz[qz][qy][qx] = T(0);
+          }
+    }
+    // test functions: along x, then y, then z
+    T Tx0[3][3][3], Txy[3][3][3], Txz[3][3][3];  // [qz][qy][a]
+#pragma unroll
+    for (int qz = 0; qz < 3; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < 3; ++qy)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          T t0 = T(0), t1 = T(0), t2 = T(0);
+#pragma unroll
+          for (int qx = 0; qx < 3; ++qx) {
+            t0 += c0[qz][qy][qx] * bx[aa][qx] + cx[qz][qy][qx] * dbx[aa][qx];
+            t1 += cy[qz][qy][qx] * bx[aa][qx];
+            t2 += cz[qz][qy][qx] * bx[aa][qx];
+          }
+          Tx0[qz][qy][aa] = t0;
+          Txy[qz][qy][aa] = t1;
+          Txz[qz][qy][aa] = t2;
+        }
+    T Ty0[3][3][3], Tyz[3][3][3];  // [qz][b][a]
+#pragma unroll
+    for (int qz = 0; qz < 3; ++qz)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          T t0 = T(0), t2 = T(0);
+#pragma unroll
+          for (int qy = 0; qy < 3; ++qy) {
+            t0 += by[b][qy] * Tx0[qz][qy][aa] + dby[b][qy] * Txy[qz][qy][aa];
+            t2 += by[b][qy] * Txz[qz][qy][aa];
+          }
+          Ty0[qz][b][aa] = t0;
+          Tyz[qz][b][aa] = t2;
+        }
+    T* out = C + (size_t)e * 27;
+#pragma unroll
+    for (int cz2 = 0; cz2 < 3; ++cz2)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          T v = T(0);
+#pragma unroll
+          for (int qz = 0; qz < 3; ++qz) v += bz[cz2][qz] * Ty0[qz][b][aa] + dbz[cz2][qz] * Tyz[qz][b][aa];
+          out[(cz2 * 3 + b) * 3 + aa] = v;
+        }
+  }
+  if (MODE == 0) {
+    double tot = block_sum(src, red);
+    if (threadIdx.x == 0) src_part[blockIdx.x] = tot;
+  }
+}
+
+// R[kz][ky][kx] = sum over elements e with e_d in [k_d - 2, k_d] of
+// C[e][(kz-ez)*9 + (ky-ey)*3 + (kx-ex)], in a fixed order
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather3d(int n, const T* __restrict__ C, T* __restrict__ R) {
+  const int nb = n + 2;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nb * nb * nb) return;
+  const int kx = (int)(t % nb), ky = (int)((t / nb) % nb), kz = (int)(t / ((long long)nb * nb));
+  T v = T(0);
+  for (int dz = 0; dz < 3; ++dz) {
+    const int ez = kz - dz;
+    if (ez < 0 || ez >= n) continue;
+    for (int dy = 0; dy < 3; ++dy) {
+      const int ey = ky - dy;
+      if (ey < 0 || ey >= n) continue;
+      for (int dx = 0; dx < 3; ++dx) {
+        const int ex = kx - dx;
+        if (ex < 0 || ex >= n) continue;
+        const size_t e = ((size_t)ez * n + ey) * n + ex;
+        v += C[e * 27 + (dz * 3 + dy) * 3 + dx];
+      }
+    }
+  }
+  R[t] = v;
+}
+
+// x sweeps: a CTA stages 32 contiguous rows (padded stride) and 32 threads
+// run the LDL^T recurrences in shared memory
+template <typename T>
+__global__ void __launch_bounds__(256) k_xsolve3d(int nrows, int nb, T* X, const T* l1,
+                                                  const T* l2, const T* dinv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int ps = nb + 1;
+  const int r0 = blockIdx.x * 32;
+  const int nr = min(32, nrows - r0);
+  for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    cp_async_elem(&xs[r * ps + c], &X[(size_t)(r0 + r) * nb + c]);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < nr) {
+    T* x = xs + r * ps;
+    T ym1 = T(0), ym2 = T(0);
+    for (int l = 0; l < nb; ++l) {
+      T y = x[l] - l1[l] * ym1 - l2[l] * ym2;
+      x[l] = y;
+      ym2 = ym1;
+      ym1 = y;
+    }
+    T xp1 = T(0), xp2 = T(0);
+    for (int l = nb - 1; l >= 0; --l) {
+      T v = x[l] * dinv[l] - l1[l + 1] * xp1 - l2[l + 2] * xp2;
+      x[l] = v;
+      xp2 = xp1;
+      xp1 = v;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
+    const int rr = e / nb, c = e % nb;
+    X[(size_t)(r0 + rr) * nb + c] = xs[rr * ps + c];
+  }
+}
+
+// sweeps along the slowest axis of X viewed as [batch][nb rows][ncols]; CTA =
+// (column block of cw, batch); with Iw != nullptr each column also sums
+// x_l Iw[l] and, if its column index decomposes as (y, x) over nb x nb,
+// multiplies by Iw[y] Iw[x] (the z sweep of int S)
+template <typename T>
+__global__ void __launch_bounds__(256) k_line_slow(int nb, int ncols, int cw, T* X, const T* l1,
+                                                   const T* l2, const T* dinv, const T* Iw,
+                                                   double* mass_part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  T* xs = reinterpret_cast<T*>(smraw);  // [nb][cw]
+  const int c0 = blockIdx.x * cw;
+  const int ncw = min(cw, ncols - c0);
+  T* base = X + (size_t)blockIdx.y * nb * ncols;
+  for (int e = threadIdx.x; e < nb * cw; e += blockDim.x) {
+    const int l = e / cw, c = e % cw;
+    if (c < ncw) cp_async_elem(&xs[e], &base[(size_t)l * ncols + c0 + c]);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  double mass = 0.0;
+  const int c = threadIdx.x;
+  if (c < ncw) {
+    T ym1 = T(0), ym2 = T(0);
+    for (int l = 0; l < nb; ++l) {
+      T y = xs[l * cw + c] - l1[l] * ym1 - l2[l] * ym2;
+      xs[l * cw + c] = y;
+      ym2 = ym1;
+      ym1 = y;
+    }
+    T xp1 = T(0), xp2 = T(0);
+    for (int l = nb - 1; l >= 0; --l) {
+      T v = xs[l * cw + c] * dinv[l] - l1[l + 1] * xp1 - l2[l + 2] * xp2;
+      xs[l * cw + c] = v;
+      if (Iw) mass += (double)v * (double)Iw[l];
+      xp2 = xp1;
+      xp1 = v;
+    }
+    if (Iw) {
+      const int col = c0 + c;
+      mass *= (double)Iw[col / nb] * (double)Iw[col % nb];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nb * cw; e += blockDim.x) {
+    const int l = e / cw, cc = e % cw;
+    if (cc < ncw) base[(size_t)l * ncols + c0 + cc] = xs[e];
+  }
+  if (mass_part) {
+    double tot = block_sum(mass, red);
+    if (threadIdx.x == 0) mass_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+static int slow_cw(int nb, size_t es) {
+  int cw = 32;
+  while (cw > 1 && es * (size_t)nb * cw > 160 * 1024) cw /= 2;
+  return cw;
+}
+
+size_t elem3d_scratch(int n, size_t es) { return (size_t)n * n * n * 27 * es; }
+int quad3d_blocks(int n) { return (int)(((long long)n * n * n + 127) / 128); }
+int zsolve3d_blocks(int n) {
+  const int nb = n + 2;
+  const int cw = slow_cw(nb, 8);
+  return (nb * nb + cw - 1) / cw;
+}
+
+// RHS (element contributions + gather) into R
+template <typename T>
+cudaError_t launch_quad3d(const QuadArgs<T>& a, int mode, T* Cbuf, T* R, double* src_part,
+                          cudaStream_t st) {
+  const int nblk = quad3d_blocks(a.n);
+  if (mode == 0) k_elem3d<T, 0><<<nblk, 128, 0, st>>>(a, Cbuf, src_part);
+  else k_elem3d<T, 1><<<nblk, 128, 0, st>>>(a, Cbuf, src_part);
+  const long long nd = (long long)a.nb * a.nb * a.nb;
+  k_gather3d<T><<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(a.n, Cbuf, R);
+  return cudaGetLastError();
+}
+
+// the three sweeps of M^-1 = Mx^-1 (x) My^-1 (x) Mz^-1, int S from the z sweep
+template <typename T>
+cudaError_t launch_solve3d(const QuadArgs<T>& a, T* X, double* mass_part, cudaStream_t st) {
+  const int nb = a.nb;
+  const int nrows = nb * nb;
+  size_t smx = sizeof(T) * 32 * (size_t)(nb + 1);
+  if (smx > 48 * 1024) cudaFuncSetAttribute(k_xsolve3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+  k_xsolve3d<T><<<(nrows + 31) / 32, 256, smx, st>>>(nrows, nb, X, a.ax.l1, a.ax.l2, a.ax.dinv);
+  const int cw = slow_cw(nb, sizeof(T));
+  const size_t sms = sizeof(T) * (size_t)nb * cw;
+  if (sms > 48 * 1024) cudaFuncSetAttribute(k_line_slow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  // y: batch = z planes, rows = y, columns = x
+  dim3 gy((nb + cw - 1) / cw, nb);
+  k_line_slow<T><<<gy, 256, sms, st>>>(nb, nb, cw, X, a.ax.l1, a.ax.l2, a.ax.dinv, nullptr, nullptr);
+  // z: one batch, rows = z, columns = (y, x)
+  dim3 gz((nb * nb + cw - 1) / cw, 1);
+  k_line_slow<T><<<gz, 256, sms, st>>>(nb, nb * nb, cw, X, a.ax.l1, a.ax.l2, a.ax.dinv,
+                                       mass_part ? a.ax.Iw : nullptr, mass_part);
+  const int nmax = zsolve3d_blocks(a.n);
+  if (mass_part && (int)gz.x < nmax)
+    cudaMemsetAsync(mass_part + gz.x, 0, sizeof(double) * (nmax - gz.x), st);
+  return cudaGetLastError();
+}
+
+// int S = sum S_ijk Iw_i Iw_j Iw_k: thread per (y, x) column
+template <typename T>
+__global__ void __launch_bounds__(128) k_mass3d(int n, const T* S, const T* Iw, double* part) {
+  __shared__ double red[32];
+  const int nb = n + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (c < nb * nb) {
+    for (int l = 0; l < nb; ++l) m += (double)S[(size_t)l * nb * nb + c] * (double)Iw[l];
+    m *= (double)Iw[c / nb] * (double)Iw[c % nb];
+  }
+  double tot = block_sum(m, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <typename T>
+cudaError_t launch_mass3d(const QuadArgs<T>& a, const T* S, double* mass_part, cudaStream_t st) {
+  const int nb = a.nb;
+  const int nblk = (nb * nb + 127) / 128;
+  k_mass3d<T><<<nblk, 128, 0, st>>>(a.n, S, a.ax.Iw, mass_part);
+  const int nmax = zsolve3d_blocks(a.n);
+  if (nblk < nmax) cudaMemsetAsync(mass_part + nblk, 0, sizeof(double) * (nmax - nblk), st);
+  return cudaGetLastError();
+}
+
+// CFL in 3D: max over Gauss points of |K (grad p + s rho_g g e_z)|/(mu_g phi)
+// and of q_inj/phi
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl3d(QuadArgs<T> a, double* part) {
+  __shared__ double red[32];
+  const int n = a.n, nb = a.nb, n1 = n + 1;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double vmax = 0.0, smax = 0.0;
+  if (e < (long long)n * n * n) {
+    const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((long long)n * n));
+    const T* Bx = a.ax.B + ex * 9; const T* dBx = a.ax.dB + ex * 9;
+    const T* By = a.ax.B + ey * 9; const T* dBy = a.ax.dB + ey * 9;
+    const T* Bz = a.ax.B + ez * 9; const T* dBz = a.ax.dB + ez * 9;
+    for (int qz = 0; qz < 3; ++qz)
+      for (int qy = 0; qy < 3; ++qy)
+        for (int qx = 0; qx < 3; ++qx) {
+          T dpx = T(0), dpy = T(0), dpz = T(0);
+          for (int c2 = 0; c2 < 3; ++c2)
+            for (int b = 0; b < 3; ++b)
+              for (int aa = 0; aa < 3; ++aa) {
+                const T pv = a.P[((size_t)(ez + c2) * nb + (ey + b)) * nb + ex + aa];
+                dpx += pv * dBx[aa * 3 + qx] * By[b * 3 + qy] * Bz[c2 * 3 + qz];
+                dpy += pv * Bx[aa * 3 + qx] * dBy[b * 3 + qy] * Bz[c2 * 3 + qz];
+                dpz += pv * Bx[aa * 3 + qx] * By[b * 3 + qy] * dBz[c2 * 3 + qz];
+              }
+          const T zeta = (T)gauss_x(qz), eta = (T)gauss_x(qy), xi = (T)gauss_x(qx);
+          T wz[2] = {T(1) - zeta, zeta}, wy[2] = {T(1) - eta, eta}, wx[2] = {T(1) - xi, xi};
+          T Kq = T(0), phq = T(0);
+          for (int i = 0; i < 8; ++i) {
+            const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
+            const size_t nd = ((size_t)(ez + dz) * n1 + (ey + dy)) * n1 + (ex + dx);
+            const T w = wz[dz] * wy[dy] * wx[dx];
+            Kq += w * a.K[nd];
+            phq += w * (a.phi ? a.phi[nd] : a.phi_c);
+          }
+          T fx = Kq * dpx, fy = Kq * dpy, fz = a.kz * Kq * (dpz + a.grav_term);
+          double v = sqrt((double)(fx * fx + fy * fy + fz * fz)) * (double)a.inv_mu_g / (double)phq;
+          vmax = fmax(vmax, v);
+          T qi = T(0);
+          for (int s = 0; s < a.n_src; ++s)
+            if (a.kind[s] == 0)
+              qi += a.rate[s] * a.ax.gsrc[((size_t)(0 * kMaxSrc + s) * n + ex) * 3 + qx] *
+                    a.ax.gsrc[((size_t)(1 * kMaxSrc + s) * n + ey) * 3 + qy] *
+                    a.ax.gsrc[((size_t)(2 * kMaxSrc + s) * n + ez) * 3 + qz];
+          smax = fmax(smax, (double)(qi / phq));
+        }
+  }
+  double r1 = block_max(vmax, red);
+  __syncthreads();
+  double r2 = block_max(smax, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r1;
+    part[2 * blockIdx.x + 1] = r2;
+  }
+}
+
+template <typename T>
+cudaError_t launch_cfl3d(const QuadArgs<T>& a, double* part, cudaStream_t st) {
+  k_cfl3d<T><<<cfl_blocks(3, a.n), 256, 0, st>>>(a, part);
+  return cudaGetLastError();
+}
+
+#define ADS3_INST(T)                                                                              \
+  template cudaError_t launch_quad3d<T>(const QuadArgs<T>&, int, T*, T*, double*, cudaStream_t); \
+  template cudaError_t launch_solve3d<T>(const QuadArgs<T>&, T*, double*, cudaStream_t);         \
+  template cudaError_t launch_mass3d<T>(const QuadArgs<T>&, const T*, double*, cudaStream_t);    \
+  template cudaError_t launch_cfl3d<T>(const QuadArgs<T>&, double*, cudaStream_t);
+ADS3_INST(double)
+ADS3_INST(float)
+
+}  // namespace adsgb

@@ -193,8 +193,13 @@ ads_status enq_sat_steps(ads_ctx* c, int n_sub) {
     void* in = c->S[c->cur];
     void* out = c->S[1 - c->cur];
     QuadArgs<TA> a = quad_args<TA>(c, in);
-    LK(0, launch_quad_xsolve<TA>(a, 0, c->re, (TA*)out, (TA*)c->Xs, c->src_part, c->stream));
-    LK(1, launch_ysolve<TA>(a, c->re, (TA*)out, (const TA*)c->Xs, c->mass_part, c->stream));
+    if (c->dim == 3) {
+      LK(0, launch_quad3d<TA>(a, 0, (TA*)c->Xs, (TA*)out, c->src_part, c->stream));
+      LK(1, launch_solve3d<TA>(a, (TA*)out, c->mass_part, c->stream));
+    } else {
+      LK(0, launch_quad_xsolve<TA>(a, 0, c->re, (TA*)out, (TA*)c->Xs, c->src_part, c->stream));
+      LK(1, launch_ysolve<TA>(a, c->re, (TA*)out, (const TA*)c->Xs, c->mass_part, c->stream));
+    }
     LK(2, launch_mass_finalize(c->mass_part, c->nys, c->src_part, c->nquad, 1, c->stats, c->flags,
                                c->stream));
     c->cur = 1 - c->cur;
@@ -205,7 +210,11 @@ ads_status enq_sat_steps(ads_ctx* c, int n_sub) {
 template <typename TA>
 ads_status enq_mass_set(ads_ctx* c) {
   QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
-  CK(launch_mass<TA>(a, (const TA*)c->S[c->cur], c->mass_part, c->stream));
+  if (c->dim == 3) {
+    CK(launch_mass3d<TA>(a, (const TA*)c->S[c->cur], c->mass_part, c->stream));
+  } else {
+    CK(launch_mass<TA>(a, (const TA*)c->S[c->cur], c->mass_part, c->stream));
+  }
   CK(launch_mass_finalize(c->mass_part, c->nys, c->src_part, 0, 0, c->stats, c->flags, c->stream));
   c->nlaunch += 2;
   return ADS_OK;
@@ -214,7 +223,11 @@ ads_status enq_mass_set(ads_ctx* c) {
 template <typename TA>
 ads_status enq_cfl(ads_ctx* c, double cfl, double frac, double cap) {
   QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
-  CK(launch_cfl<TA>(a, c->cfl_part, c->stream));
+  if (c->dim == 3) {
+    CK(launch_cfl3d<TA>(a, c->cfl_part, c->stream));
+  } else {
+    CK(launch_cfl<TA>(a, c->cfl_part, c->stream));
+  }
   CK(launch_cfl_finalize(c->cfl_part, c->ncfl, cfl, frac, cap, 1.0 / c->n, c->dt, c->flags,
                          c->stream));
   c->nlaunch += 2;
@@ -301,12 +314,28 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   LK(0, launch_fwd<TC>(c, true));
   LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->u,
                            (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr, c->stream));
-  LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
-                        TC(1), nullptr, nullptr, c->stream));
-  LK(3, launch_tridiag_cols<TC>(m, m, (const TC*)c->invd, (TC*)c->rhat, c->stream));
-  LK(4, launch_gemm<TC>(m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
-                        h * h, (const TC*)c->res, c->dot_part, c->stream));
-  LossFin lf{c->dot_part, gemm_blocks(m, m), c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
+  if (c->dim == 3) {
+    // G^-1 r: sine transforms along x (one GEMM over all (z, y) rows) and y
+    // (batched over z), shifted tridiagonal sweeps along z, inverse transforms
+    const long long mm = (long long)m * m;
+    LK(2, launch_gemm<TC>(m * m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
+                          TC(1), nullptr, nullptr, c->stream));
+    CK(launch_gemm<TC>(m, m, m, (const TC*)c->Sdst, m, (const TC*)c->rhat, m, (TC*)c->z, m, TC(1),
+                       nullptr, nullptr, c->stream, m, 0, mm, mm));
+    LK(3, launch_tridiag_cols<TC>(m, m * m, (const TC*)c->invd, (TC*)c->z, c->stream));
+    CK(launch_gemm<TC>(m, m, m, (const TC*)c->Sdst, m, (const TC*)c->z, m, (TC*)c->rhat, m, TC(1),
+                       nullptr, nullptr, c->stream, m, 0, mm, mm));
+    LK(4, launch_gemm<TC>(m * m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
+                          h * h, (const TC*)c->res, c->dot_part, c->stream));
+    c->nlaunch += 2;
+  } else {
+    LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
+                          TC(1), nullptr, nullptr, c->stream));
+    LK(3, launch_tridiag_cols<TC>(m, m, (const TC*)c->invd, (TC*)c->rhat, c->stream));
+    LK(4, launch_gemm<TC>(m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
+                          h * h, (const TC*)c->res, c->dot_part, c->stream));
+  }
+  LossFin lf{c->dot_part, c->dim == 3 ? gemm_blocks(m * m, m) : gemm_blocks(m, m), c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
   LK(5, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
                            nullptr, TC(0), TC(2), (TC*)c->gu, &lf, c->stream));
   LK(6, launch_bwd<TC>(c));
@@ -321,8 +350,13 @@ ads_status enq_project(ads_ctx* c) {
   CK(launch_fwd<TC>(c, false));
   CK(launch_embed<TC, TA>(c->dim, c->N, (const TC*)c->u, (TA*)c->nodal, c->stream));
   QuadArgs<TA> a = quad_args<TA>(c, c->S[c->cur]);
-  CK(launch_quad_xsolve<TA>(a, 1, c->re, (TA*)c->P, (TA*)c->Xs, c->src_part, c->stream));
-  CK(launch_ysolve<TA>(a, c->re, (TA*)c->P, (const TA*)c->Xs, c->mass_part, c->stream));
+  if (c->dim == 3) {
+    CK(launch_quad3d<TA>(a, 1, (TA*)c->Xs, (TA*)c->P, c->src_part, c->stream));
+    CK(launch_solve3d<TA>(a, (TA*)c->P, nullptr, c->stream));
+  } else {
+    CK(launch_quad_xsolve<TA>(a, 1, c->re, (TA*)c->P, (TA*)c->Xs, c->src_part, c->stream));
+    CK(launch_ysolve<TA>(a, c->re, (TA*)c->P, (const TA*)c->Xs, c->mass_part, c->stream));
+  }
   c->nlaunch += 4;
   return ADS_OK;
 }
@@ -498,8 +532,8 @@ int mlp_params(int din, int w, int hl) {
 
 ads_status validate(const ads_params* p, const crvpinn_params* cp) {
   if (!p) return ADS_ERR_INVALID_ARG;
-  if (p->dim != 2) return ADS_ERR_UNSUPPORTED;
-  if (p->n < 2 || p->n > 8192) return ADS_ERR_INVALID_ARG;
+  if (p->dim != 2 && p->dim != 3) return ADS_ERR_UNSUPPORTED;
+  if (p->n < 2 || p->n > (p->dim == 3 ? 512 : 8192)) return ADS_ERR_INVALID_ARG;
   if (!(p->phi > 0) || !(p->mu_w > 0) || !(p->mu_g > 0)) return ADS_ERR_INVALID_ARG;
   if (!(p->grav >= 0) || !std::isfinite(p->grav) || !std::isfinite(p->grav_sign)) return ADS_ERR_INVALID_ARG;
   if (p->n_src < 0 || p->n_src > ADS_MAX_SOURCES) return ADS_ERR_INVALID_ARG;
@@ -529,21 +563,24 @@ bool all_finite(const double* x, size_t n, bool positive) {
 }
 
 size_t estimate(const ads_params* p, const crvpinn_params* cp) {
-  size_t n = p->n, nb = n + 2, n1 = n + 1;
-  size_t ta = tsize(p->ads_dtype);
-  size_t nc = nb * nb, nn = n1 * n1;
+  const size_t n = p->n, nb = n + 2, n1 = n + 1, d = p->dim;
+  const size_t ta = tsize(p->ads_dtype);
+  const size_t nc = d == 3 ? nb * nb * nb : nb * nb, nn = d == 3 ? n1 * n1 * n1 : n1 * n1;
   size_t b = 0;
   b += 8 * (18 * n + 3 * (n + 4) + 2 * nb + 3 * kMaxSrc * (3 * n + n1) + 3 * (n + 4) + 64);
   b += ta * (18 * n + 3 * (n + 4) + 2 * nb + 3 * kMaxSrc * (3 * n + n1));
-  b += ta * (3 * nc + 2 * nn + 2 * ((n + 3) / 4) * 2 * nb + nn);
-  b += 8 * 4 * (nb + 1024);
+  b += ta * (3 * nc + 2 * nn);  // S (2), P, K, nodal (phi optional)
+  if (d == 3) b += ta * n * n * n * 27;           // per-element contributions
+  else b += ta * 2 * ((n + 1) / 2) * nb;          // spill rows
+  b += 8 * 4 * (nb * nb + 1024);                  // partial sums
   if (cp) {
-    size_t tc = cp->dtype == ADS_BF16 ? 4 : tsize(cp->dtype);
-    size_t m = n - 1, M = m * m, w = cp->width;
-    size_t np = mlp_params(2, cp->width, cp->hidden_layers);
-    size_t ld = ((M + 63) / 64) * 64;
-    b += tc * (nn + 6 * M + 2 * m * m + 5 * np + 4 * w * ld + 2 * 152 * np);
-    b += 8 * (2 * m * m + kLossRing + 2048);
+    const size_t tc = cp->dtype == ADS_BF16 ? 4 : tsize(cp->dtype);
+    const size_t m = n - 1, M = d == 3 ? m * m * m : m * m, w = cp->width;
+    const size_t np = mlp_params((int)d, cp->width, cp->hidden_layers);
+    const size_t ld = ((M + 127) / 128) * 128;
+    const size_t acts = cp->dtype == ADS_BF16 ? 2 * 4 * w * ld : tc * 4 * w * ld;
+    b += tc * (nn + 6 * M + m * m + 5 * np + 2 * 152 * np) + acts;
+    b += 8 * (m * m + (d == 3 ? m * m * m : m * m) + kLossRing + 4096);
   }
   return b;
 }
@@ -666,7 +703,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   c->nb = c->n + 2;
   c->N = c->n;
   c->m1 = c->N - 1;
-  c->M = c->m1 * c->m1;
+  c->M = c->m1 * c->m1 * (c->dim == 3 ? c->m1 : 1);
   c->ta = params->ads_dtype;
   size_t nc = ncoef(c), nn = nnode(c);
   if (!all_finite(K_nodal, nn, true) || (phi_nodal && !all_finite(phi_nodal, nn, true)) ||
@@ -694,7 +731,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   if (crv) stage = stage > (size_t)kLossRing ? stage : (size_t)kLossRing;
   stage += 1024;
   if (crv) {
-    int np = mlp_params(2, crv->width, crv->hidden_layers);
+    int np = mlp_params(params->dim, crv->width, crv->hidden_layers);
     if ((size_t)np > stage) stage = np + 16;
     if ((size_t)c->M > stage) stage = c->M + 16;
   }
@@ -768,10 +805,15 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     ALV(c->phi, ta * nn);
   }
   c->re = (n + 3) / 4 < 152 ? 2 : 4;  // strips of 2 element rows on small meshes
-  c->nquad = quad_blocks(c->dim, n, c->re);
-  c->nys = ysolve_blocks(c->dim, n);
+  c->nquad = c->dim == 3 ? quad3d_blocks(n) : quad_blocks(c->dim, n, c->re);
+  c->nys = c->dim == 3 ? zsolve3d_blocks(n) : ysolve_blocks(c->dim, n);
   c->ncfl = cfl_blocks(c->dim, n);
-  ALV(c->Xs, ta * 2 * (size_t)c->nquad * nb);
+  // 2D: rows spilled between strips; 3D: per-element contributions
+  if (c->dim == 3) {
+    ALV(c->Xs, elem3d_scratch(n, ta));
+  } else {
+    ALV(c->Xs, ta * 2 * (size_t)c->nquad * nb);
+  }
   AL(c->src_part, (size_t)c->nquad + 1);
   AL(c->mass_part, (size_t)c->nys + 1);
   AL(c->cfl_part, 2 * (size_t)c->ncfl + 2);
@@ -800,7 +842,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     c->tc = c->use_tc ? ADS_F32 : crv->dtype;  // buffers outside the network stay FP32
     const size_t tc = tsize(c->tc);
     const int m = c->m1;
-    c->nparams = mlp_params(2, crv->width, crv->hidden_layers);
+    c->nparams = mlp_params(c->dim, crv->width, crv->hidden_layers);
     c->ld = ((c->M + 63) / 64) * 64;
     c->ndot = dot_blocks(c->M);
     c->nbwd = c->use_tc ? mlp_tc_bwd_blocks(c->M) : mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
@@ -822,8 +864,9 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
       ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
     }
     double *S64 = nullptr, *inv64 = nullptr;
+    const size_t npiv = (size_t)m * m * (c->dim == 3 ? m : 1);
     AL(S64, (size_t)m * m);
-    AL(inv64, (size_t)m * m);
+    AL(inv64, npiv);
     if (launch_gram_init(c->dim, c->N, S64, inv64, c->stream) != cudaSuccess)
       return bail(fail(c, ADS_ERR_CUDA, "gram init"));
     if (c->tc == ADS_F64) {
@@ -831,11 +874,11 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
       c->invd = inv64;
     } else {
       ALV(c->Sdst, 4 * (size_t)m * m);
-      ALV(c->invd, 4 * (size_t)m * m);
+      ALV(c->invd, 4 * npiv);
       launch_convert<float>(S64, (float*)c->Sdst, (size_t)m * m, c->stream);
-      launch_convert<float>(inv64, (float*)c->invd, (size_t)m * m, c->stream);
+      launch_convert<float>(inv64, (float*)c->invd, npiv, c->stream);
     }
-    AL(c->dot_part, (size_t)gemm_blocks(c->m1, c->m1) + 1);
+    AL(c->dot_part, (size_t)gemm_blocks(c->dim == 3 ? c->m1 * c->m1 : c->m1, c->m1) + 1);
     AL(c->loss, 1);
     AL(c->loss_log, kLossRing);
     AL(c->bc, 2);

@@ -70,9 +70,60 @@ __global__ void k_crv_coeffs_2d(CrvArgs<T, TA> a) {
   }
 }
 
+// 3D: nodal saturation from the three per-axis knot weights; the vertical
+// axis is z and carries kz_ratio in the gravity flux
+template <typename T, typename TA>
+__device__ __forceinline__ double nodal_sat_3d(const CrvArgs<T, TA>& a, int k, int j, int i) {
+  const int n = a.N, nb = n + 2;
+  int i0, j0, k0;
+  double wx[2], wy[2], wz[2];
+  knot_weights(i, n, i0, wx[0], wx[1]);
+  knot_weights(j, n, j0, wy[0], wy[1]);
+  knot_weights(k, n, k0, wz[0], wz[1]);
+  double v = 0.0;
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b) {
+      const TA* r = a.S + ((size_t)(k0 + c) * nb + (j0 + b)) * nb + i0;
+      v += wz[c] * wy[b] * (wx[0] * (double)r[0] + wx[1] * (double)r[1]);
+    }
+  return v;
+}
+
+template <typename T, typename TA>
+__global__ void k_crv_coeffs_3d(CrvArgs<T, TA> a) {
+  const int N = a.N, n1 = N + 1, m = N - 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n1 * n1 * n1) return;
+  const int i = (int)(t % n1), j = (int)((t / n1) % n1), k = (int)(t / ((long long)n1 * n1));
+  double s = nodal_sat_3d(a, k, j, i);
+  s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+  double lw = (1.0 - s) * a.inv_mu_w, lg = s * a.inv_mu_g;
+  double K = (double)a.K[t];
+  a.alpha[t] = (T)((lw + lg) * K);
+  if (i >= 1 && i <= N - 1 && j >= 1 && j <= N - 1 && k >= 1 && k <= N - 1) {
+    double s1 = nodal_sat_3d(a, k + 1, j, i);
+    s1 = s1 < 0.0 ? 0.0 : (s1 > 1.0 ? 1.0 : s1);
+    double K1 = (double)a.K[t + (long long)n1 * n1];
+    double F0 = -a.grav * a.kz * K * (a.rho_w * lw + a.rho_g * lg);
+    double F1 = -a.grav * a.kz * K1 * (a.rho_w * (1.0 - s1) * a.inv_mu_w + a.rho_g * s1 * a.inv_mu_g);
+    double q = 0.0;
+    for (int c = 0; c < a.n_src; ++c) {
+      double g = a.rate[c] * (double)a.ax.gnode[(size_t)(0 * kMaxSrc + c) * n1 + i] *
+                 (double)a.ax.gnode[(size_t)(1 * kMaxSrc + c) * n1 + j] *
+                 (double)a.ax.gnode[(size_t)(2 * kMaxSrc + c) * n1 + k];
+      q += (a.kind[c] == 0) ? g : -g;
+    }
+    a.f[((size_t)(k - 1) * m + (j - 1)) * m + (i - 1)] = (T)((F1 - F0) * (double)N - q);
+  }
+}
+
 template <typename T, typename TA>
 cudaError_t launch_crv_coeffs(const CrvArgs<T, TA>& a, cudaStream_t st) {
-  if (a.dim != 2) return cudaErrorNotSupported;
+  if (a.dim == 3) {
+    long long tot = (long long)(a.N + 1) * (a.N + 1) * (a.N + 1);
+    k_crv_coeffs_3d<T, TA><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   int tot = (a.N + 1) * (a.N + 1);
   k_crv_coeffs_2d<T, TA><<<(tot + 255) / 256, 256, 0, st>>>(a);
   return cudaGetLastError();
@@ -124,13 +175,49 @@ __global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__
   out[t] = r;
 }
 
+// 7-point form: the z differences are weighted by kz
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil_3d(int N, T kz, const T* __restrict__ alpha,
+                                                    const T* __restrict__ v, const T* __restrict__ f,
+                                                    T h2, T scale, T* __restrict__ out, LossFin lf) {
+  const int m = N - 1, n1 = N + 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (lf.part && t == 0) loss_finalize_dev(lf);
+  if (t >= (long long)m * m * m) return;
+  const int ii = (int)(t % m), jj = (int)((t / m) % m), kk = (int)(t / ((long long)m * m));
+  const int i = ii + 1, j = jj + 1, k = kk + 1;
+  const long long mm = (long long)m * m;
+  T c = v[t];
+  T w = ii > 0 ? v[t - 1] : T(0);
+  T e = ii < m - 1 ? v[t + 1] : T(0);
+  T s = jj > 0 ? v[t - m] : T(0);
+  T nn = jj < m - 1 ? v[t + m] : T(0);
+  T d = kk > 0 ? v[t - mm] : T(0);
+  T up = kk < m - 1 ? v[t + mm] : T(0);
+  const size_t nd = ((size_t)k * n1 + j) * n1 + i;
+  T ac = alpha[nd];
+  T aw = alpha[nd - 1];
+  T as = alpha[nd - n1];
+  T ad = alpha[nd - (size_t)n1 * n1];
+  T r = aw * (c - w) - ac * (e - c) + as * (c - s) - ac * (nn - c) + kz * (ad * (c - d) - ac * (up - c));
+  r *= scale;
+  if (f) r += h2 * f[t];
+  out[t] = r;
+}
+
 template <typename T>
 cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, const T* f, T h2,
                            T scale, T* out, const LossFin* lf, cudaStream_t st) {
-  if (dim != 2) return cudaErrorNotSupported;
+  LossFin none{};
+  if (dim == 3) {
+    long long m = (long long)(N - 1) * (N - 1) * (N - 1);
+    if (m <= 0) return cudaSuccess;
+    k_stencil_3d<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(N, kz, alpha, u, f, h2, scale, out,
+                                                                  lf ? *lf : none);
+    return cudaGetLastError();
+  }
   int m = (N - 1) * (N - 1);
   if (m <= 0) return cudaSuccess;
-  LossFin none{};
   k_stencil_2d<T><<<(m + 255) / 256, 256, 0, st>>>(N, alpha, u, f, h2, scale, out, lf ? *lf : none);
   return cudaGetLastError();
 }
@@ -147,8 +234,24 @@ __global__ void k_embed_2d(int N, const T* u, TA* nodal) {
 }
 
 template <typename T, typename TA>
+__global__ void k_embed_3d(int N, const T* u, TA* nodal) {
+  const int n1 = N + 1, m = N - 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n1 * n1 * n1) return;
+  const int i = (int)(t % n1), j = (int)((t / n1) % n1), k = (int)(t / ((long long)n1 * n1));
+  TA v = TA(0);
+  if (i >= 1 && i <= N - 1 && j >= 1 && j <= N - 1 && k >= 1 && k <= N - 1)
+    v = (TA)u[((size_t)(k - 1) * m + (j - 1)) * m + (i - 1)];
+  nodal[t] = v;
+}
+
+template <typename T, typename TA>
 cudaError_t launch_embed(int dim, int N, const T* u, TA* nodal, cudaStream_t st) {
-  if (dim != 2) return cudaErrorNotSupported;
+  if (dim == 3) {
+    long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
+    k_embed_3d<T, TA><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(N, u, nodal);
+    return cudaGetLastError();
+  }
   int tot = (N + 1) * (N + 1);
   k_embed_2d<T, TA><<<(tot + 255) / 256, 256, 0, st>>>(N, u, nodal);
   return cudaGetLastError();
@@ -180,11 +283,27 @@ __global__ void k_gram_pivots(int N, double* invd) {
   }
 }
 
+// 3D: for the z sweep of mode (ky, kx) the shift is Lambda_ky + Lambda_kx;
+// pivots stored [z][ky*m + kx]
+__global__ void k_gram_pivots3d(int N, double* invd) {
+  const int m = N - 1;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m * m) return;
+  const int ky = c / m + 1, kx = c % m + 1;
+  double sy = sinpi((double)ky / (2.0 * N)), sx = sinpi((double)kx / (2.0 * N));
+  double b = 2.0 + 4.0 * sy * sy + 4.0 * sx * sx;
+  double d = b;
+  for (int j = 0; j < m; ++j) {
+    invd[(size_t)j * m * m + c] = 1.0 / d;
+    d = b - 1.0 / d;
+  }
+}
+
 cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStream_t st) {
-  if (dim != 2) return cudaErrorNotSupported;
   int m = N - 1;
   k_gram_sine<<<(m * m + 255) / 256, 256, 0, st>>>(N, Sdst);
-  k_gram_pivots<<<(m + 127) / 128, 128, 0, st>>>(N, invd);
+  if (dim == 3) k_gram_pivots3d<<<(m * m + 127) / 128, 128, 0, st>>>(N, invd);
+  else k_gram_pivots<<<(m + 127) / 128, 128, 0, st>>>(N, invd);
   return cudaGetLastError();
 }
 
@@ -197,8 +316,11 @@ cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStr
 template <typename T, int BM, int BN>
 __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_gemm(int M, int Nn, int K,
     const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb, T* __restrict__ C, int ldc,
-    T alpha, const T* __restrict__ dotB, double* dot_part) {
+    T alpha, const T* __restrict__ dotB, double* dot_part, long long sA, long long sB, long long sC) {
   constexpr int BK = 16, NT = (BM / 4) * (BN / 4), TX = BN / 4;
+  A += sA * blockIdx.z;
+  B += sB * blockIdx.z;
+  C += sC * blockIdx.z;
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;  // loads per thread per k-tile
   __shared__ T As[2][BK][BM + 4];
   __shared__ T Bs[2][BK][BN + 4];
@@ -289,13 +411,17 @@ int gemm_blocks(int M, int Nn) {
 
 template <typename T>
 cudaError_t launch_gemm(int M, int Nn, int K, const T* A, int lda, const T* B, int ldb, T* C,
-                        int ldc, T alpha, const T* dotB, double* dot_part, cudaStream_t st) {
-  if (small_tiles(M, Nn)) {
-    dim3 grid((Nn + 31) / 32, (M + 31) / 32);
-    k_gemm<T, 32, 32><<<grid, 64, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha, dotB, dot_part);
+                        int ldc, T alpha, const T* dotB, double* dot_part, cudaStream_t st,
+                        int batch, long long sA, long long sB, long long sC) {
+  if (batch > 1 && dotB) return cudaErrorInvalidValue;
+  if (small_tiles(M, Nn) && batch == 1) {
+    dim3 grid((Nn + 31) / 32, (M + 31) / 32, 1);
+    k_gemm<T, 32, 32><<<grid, 64, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha, dotB, dot_part,
+                                           sA, sB, sC);
   } else {
-    dim3 grid((Nn + 63) / 64, (M + 63) / 64);
-    k_gemm<T, 64, 64><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha, dotB, dot_part);
+    dim3 grid((Nn + 63) / 64, (M + 63) / 64, batch);
+    k_gemm<T, 64, 64><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, B, ldb, C, ldc, alpha, dotB, dot_part,
+                                            sA, sB, sC);
   }
   return cudaGetLastError();
 }
@@ -437,7 +563,8 @@ CRV_INST(double, float)
   template cudaError_t launch_stencil<T>(int, int, T, const T*, const T*, const T*, T, T, T*,    \
                                          const LossFin*, cudaStream_t);                           \
   template cudaError_t launch_gemm<T>(int, int, int, const T*, int, const T*, int, T*, int, T,   \
-                                      const T*, double*, cudaStream_t);                           \
+                                      const T*, double*, cudaStream_t, int, long long, long long, \
+                                      long long);                                                 \
   template cudaError_t launch_tridiag_cols<T>(int, int, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_dot_partial<T>(const T*, const T*, int, double*, int, cudaStream_t);
 CRV_INST1(double)

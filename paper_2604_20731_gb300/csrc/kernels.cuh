@@ -78,6 +78,20 @@ int cfl_blocks(int dim, int n);
 cudaError_t launch_cfl_finalize(const double* part, int nblk, double cfl, double src_frac,
                                 double dt_cap, double h, double* dt, int* flags, cudaStream_t st);
 
+// ---- 3D saturation step ----
+template <typename T>
+cudaError_t launch_quad3d(const QuadArgs<T>& a, int mode, T* Cbuf, T* R, double* src_part,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve3d(const QuadArgs<T>& a, T* X, double* mass_part, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mass3d(const QuadArgs<T>& a, const T* S, double* mass_part, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cfl3d(const QuadArgs<T>& a, double* part, cudaStream_t st);
+size_t elem3d_scratch(int n, size_t es);
+int quad3d_blocks(int n);
+int zsolve3d_blocks(int n);
+
 // ---- CRVPINN ----
 template <typename T, typename TA>
 struct CrvArgs {
@@ -118,7 +132,8 @@ cudaError_t launch_embed(int dim, int N, const T* u, TA* nodal, cudaStream_t st)
 cudaError_t launch_gram_init(int dim, int N, double* Sdst, double* invd, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gemm(int M, int Nn, int K, const T* A, int lda, const T* B, int ldb, T* C,
-                        int ldc, T alpha, const T* dotB, double* dot_part, cudaStream_t st);
+                        int ldc, T alpha, const T* dotB, double* dot_part, cudaStream_t st,
+                        int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
 int gemm_blocks(int M, int Nn);
 template <typename T>
 cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaStream_t st);
