@@ -278,7 +278,7 @@ def serving_mix(count, seed=3):
         n = int(rng.choice([128, 256, 512]))
         sigma = float(rng.uniform(0.5, 2.0))
         rate = float(rng.uniform(0.5, 2.0))
-        out.append(scn.make_scenario(2, n, seed=1000 + i, sigma=sigma, rate=rate))
+        out.append(scn.make_scenario(2, n, seed=1000 + i + 100000 * (seed - 3), sigma=sigma, rate=rate))
     return out
 
 
