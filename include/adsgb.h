@@ -81,7 +81,7 @@ typedef struct {
 } ads_params;
 
 typedef struct {
-  int width;         /* hidden width: 64 or 128 (ADS_BF16 and ADS_F64: 64)    */
+  int width;         /* hidden width: 64 or 128 (ADS_F64: 64)                 */
   int hidden_layers; /* 4                                                     */
   int dtype;         /* ADS_F64 or ADS_F32: network, residual, Gram and Adam
                         in that precision on the CUDA cores.  ADS_BF16: the

@@ -185,62 +185,64 @@ ADS_D void coords(int idx, int N, float c[3]) {
 }
 
 // load the three hidden weight matrices W_l[o][k] (FP32 master) as BF16 tiles
+template <int W = kW>
 ADS_D void load_hidden_weights(const float* th, int o2, unsigned char* wt, int tid, int nthr) {
-  constexpr int RG = (kW / 8) * 128;
-  for (int e = tid; e < 3 * kW * (kW / 8); e += nthr) {
-    const int l = e / (kW * (kW / 8)), rem = e % (kW * (kW / 8));
-    const int o = rem / (kW / 8), c = (rem % (kW / 8)) * 8;
-    const float* src = th + o2 + l * (kW * kW + kW) + o * kW + c;
+  constexpr int RG = (W / 8) * 128;
+  for (int e = tid; e < 3 * W * (W / 8); e += nthr) {
+    const int l = e / (W * (W / 8)), rem = e % (W * (W / 8));
+    const int o = rem / (W / 8), c = (rem % (W / 8)) * 8;
+    const float* src = th + o2 + l * (W * W + W) + o * W + c;
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = src[j];
-    st_atom(wt + l * kW * kW * 2, RG, o, c, v);
+    st_atom(wt + l * W * W * 2, RG, o, c, v);
   }
 }
 
+template <int W>
 struct TcSmemF {
   // byte offsets
-  static constexpr int W = 0;                          // 3 x [64][64] bf16 = 24 KB
-  static constexpr int ACT = W + 3 * kW * kW * 2;      // [128][64] bf16 hi = 16 KB
-  static constexpr int ACTLO = ACT + kTP * kW * 2;     // [128][64] bf16 lo = 16 KB
-  static constexpr int BIAS = ACTLO + kTP * kW * 2;    // fp32: b1 b2 b3 b4 [4][64], W1 [64][3], W5 [64], b5
-  static constexpr int NBIAS = 4 * kW + 3 * kW + kW + 4;
-  static constexpr int BAR = BIAS + NBIAS * 4;         // mbarrier (8 B) + tmem base (4 B)
+  static constexpr int WT = 0;                         // 3 x [W][W] bf16
+  static constexpr int ACT = WT + 3 * W * W * 2;       // [128][W] bf16 hi
+  static constexpr int ACTLO = ACT + kTP * W * 2;      // [128][W] bf16 lo
+  static constexpr int BIAS = ACTLO + kTP * W * 2;     // fp32: b1 b2 b3 b4 [4][W], W1 [W][3], W5 [W], b5
+  static constexpr int NBIAS = 4 * W + 3 * W + W + 4;
+  static constexpr int BAR = BIAS + NBIAS * 4;         // mbarrier (8 B), tmem base (4 B), abort flag (4 B)
   static constexpr int TOTAL = BAR + 32;
 };
 
-template <int DIN>
+template <int W, int DIN>
 __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* wt = sm + TcSmemF::W;
-  unsigned char* act = sm + TcSmemF::ACT;
-  unsigned char* actlo = sm + TcSmemF::ACTLO;
-  float* fb = reinterpret_cast<float*>(sm + TcSmemF::BIAS);
-  float* fW1 = fb + 4 * kW;
-  float* fW5 = fW1 + 3 * kW;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemF::BAR);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemF::BAR + 8);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemF::BAR + 12);
+  unsigned char* wt = sm + TcSmemF<W>::WT;
+  unsigned char* act = sm + TcSmemF<W>::ACT;
+  unsigned char* actlo = sm + TcSmemF<W>::ACTLO;
+  float* fb = reinterpret_cast<float*>(sm + TcSmemF<W>::BIAS);
+  float* fW1 = fb + 4 * W;
+  float* fW5 = fW1 + 3 * W;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemF<W>::BAR);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemF<W>::BAR + 8);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemF<W>::BAR + 12);
   const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int RG = (kW / 8) * 128;
+  constexpr int RG = (W / 8) * 128;
   const float* th = a.theta;
-  const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
-  load_hidden_weights(th, o2, wt, tid, kTP);
-  for (int i = tid; i < kW; i += kTP) {
+  const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
+  load_hidden_weights<W>(th, o2, wt, tid, kTP);
+  for (int i = tid; i < W; i += kTP) {
     fb[i] = th[ob1 + i];
-    for (int l = 0; l < 3; ++l) fb[(l + 1) * kW + i] = th[o2 + l * (kW * kW + kW) + kW * kW + i];
+    for (int l = 0; l < 3; ++l) fb[(l + 1) * W + i] = th[o2 + l * (W * W + W) + W * W + i];
     for (int d = 0; d < DIN; ++d) fW1[i * 3 + d] = th[i * DIN + d];
     fW5[i] = th[o5 + i];
   }
   if (tid == 0) {
-    fW5[kW] = th[o5 + kW];
+    fW5[W] = th[o5 + W];
     *abort_flag = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(tbase)), "r"(kW));
+                     smem_addr(tbase)), "r"(W));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_async_smem();
@@ -249,21 +251,21 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tbase;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-  const uint32_t idesc = idesc_bf16(kTP, kW, 0, 0);
+  const uint32_t idesc = idesc_bf16(kTP, W, 0, 0);
   const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(wt);
   uint32_t phase = 0;
   bool aborted = false;
   const int ntiles = (a.npts + kTP - 1) / kTP;
-  const float b5 = fW5[kW];
+  const float b5 = fW5[W];
   for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
     const int p0 = tile * kTP;
     const int idx = min(p0 + tid, a.npts - 1);
     float x[3];
     coords<DIN>(idx, a.N, x);
-    unsigned char* gtile = a.acts ? a.acts + (size_t)tile * 4 * kTP * kW * 2 : nullptr;
+    unsigned char* gtile = a.acts ? a.acts + (size_t)tile * 4 * kTP * W * 2 : nullptr;
     // layer 1 on the CUDA cores
 #pragma unroll
-    for (int c = 0; c < kW; c += 8) {
+    for (int c = 0; c < W; c += 8) {
       float v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -285,20 +287,20 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
       if (tid == 0) {
         // (a_hi + a_lo) W: two BF16 products into one FP32 accumulator
 #pragma unroll
-        for (int ks = 0; ks < kW / 16; ++ks)
-          mma_bf16(tmem, desc_k(act_s, RG, ks), desc_k(wt_s + l * kW * kW * 2, RG, ks), idesc,
+        for (int ks = 0; ks < W / 16; ++ks)
+          mma_bf16(tmem, desc_k(act_s, RG, ks), desc_k(wt_s + l * W * W * 2, RG, ks), idesc,
                    ks > 0);
 #pragma unroll
-        for (int ks = 0; ks < kW / 16; ++ks)
-          mma_bf16(tmem, desc_k(actlo_s, RG, ks), desc_k(wt_s + l * kW * kW * 2, RG, ks), idesc, 1u);
+        for (int ks = 0; ks < W / 16; ++ks)
+          mma_bf16(tmem, desc_k(actlo_s, RG, ks), desc_k(wt_s + l * W * W * 2, RG, ks), idesc, 1u);
         mma_commit(mbar);
       }
       if (!mbar_wait(mbar, phase)) *abort_flag = 1;
       phase ^= 1;
       tc_fence_after();
-      const float* bl = fb + (l + 1) * kW;
+      const float* bl = fb + (l + 1) * W;
 #pragma unroll
-      for (int c = 0; c < kW; c += 16) {
+      for (int c = 0; c < W; c += 16) {
         float d[16];
         tmem_ld16(lane_base + c, d);
         float v[16];
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
           st_atom_split(act, actlo, RG, tid, c, v);
           st_atom_split(act, actlo, RG, tid, c + 8, v + 8);
         }
-        unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * kW * 2 : nullptr;
+        unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * W * 2 : nullptr;
         if (g) {
           st_atom(g, RG, tid, c, v);
           st_atom(g, RG, tid, c + 8, v + 8);
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
     if (!aborted && p0 + tid < a.npts) a.u[p0 + tid] = u;
   }
   if (sync_abort(abort_flag) && tid == 0) atomicOr(a.flags, 8);
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kW));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(W));
 }
 
 // ---------------------------------------------------------------------------
@@ -562,6 +564,211 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---------------------------------------------------------------------------
+// backward, width 128: the three hidden dW accumulators (3 x 128 TMEM columns)
+// and the delta product (128 columns) fill the 512 TMEM columns, so the small
+// gradients (biases, output layer, first layer) are per-thread FP32 sums over
+// the points (thread o owns output o; fixed order).  Activation tiles stream
+// through a two-slot ring; the delta tile is rewritten in place once the
+// products that read it have completed.
+// ---------------------------------------------------------------------------
+constexpr int kW2 = 128;
+struct TcSmemB2 {
+  static constexpr int WT = 0;                             // 3 x [128][128] bf16     96 KB
+  static constexpr int ACT = WT + 3 * kW2 * kW2 * 2;       // 2 x [128][128] bf16     64 KB
+  static constexpr int ACT_SZ = kTP * kW2 * 2;
+  static constexpr int DEL = ACT + 2 * ACT_SZ;             // [128][128] bf16         32 KB
+  static constexpr int VEC = DEL + kTP * kW2 * 2;          // fp32: W5 [128], g [128], x' [3][128]
+  static constexpr int BAR = VEC + (kW2 + kTP + 3 * kTP) * 4;
+  static constexpr int TOTAL = BAR + 32;
+};
+
+template <int DIN>
+__global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
+  constexpr int W = kW2;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* wt = sm + TcSmemB2::WT;
+  unsigned char* act = sm + TcSmemB2::ACT;  // two slots
+  unsigned char* del = sm + TcSmemB2::DEL;
+  float* fW5 = reinterpret_cast<float*>(sm + TcSmemB2::VEC);
+  float* gs = fW5 + W;
+  float* xs = gs + kTP;  // [3][128]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB2::BAR);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB2::BAR + 8);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB2::BAR + 12);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int RG = (W / 8) * 128;
+  const float* th = a.theta;
+  const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
+  load_hidden_weights<W>(th, o2, wt, tid, kTP);
+  fW5[tid] = th[o5 + tid];
+  if (tid == 0) {
+    *abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tbase)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del);
+  const uint32_t id_dw = idesc_bf16(kTP, W, 1, 1);  // dW_l: M = 128 (o), N = 128 (k), K = points
+  const uint32_t id_dp = idesc_bf16(kTP, W, 0, 1);  // delta product: M = points, N = 128, K = 128
+  auto col_dw2 = [](int L) { return 128 + (4 - L) * 128; };  // dW4 128, dW3 256, dW2 384
+  // per-thread small gradients (thread o)
+  float g_w5 = 0.f, g_b5 = 0.f, g_b1 = 0.f, g_w1[3] = {0.f, 0.f, 0.f}, g_bh[3] = {0.f, 0.f, 0.f};
+  uint32_t phase = 0;
+  bool aborted = false, first = true;
+  const int ntiles = (a.npts + kTP - 1) / kTP;
+  auto stage = [&](int slot, int L, int tile) {  // activations a_{L+1} (L = 0..3) of `tile`
+    const unsigned char* src = a.acts + ((size_t)tile * 4 + L) * kTP * W * 2;
+    unsigned char* dst = act + slot * TcSmemB2::ACT_SZ;
+    for (int ch = tid; ch < kTP * W * 2 / 16; ch += kTP) cp_async16(dst + ch * 16, src + ch * 16);
+    cp_async_commit();
+  };
+  if ((int)blockIdx.x < ntiles) stage(0, 3, blockIdx.x);
+  for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+    const int p0 = tile * kTP;
+    const int idx = p0 + tid;
+    const float g = idx < a.npts ? a.gu[idx] : 0.0f;
+    {
+      float x[3];
+      coords<DIN>(min(idx, a.npts - 1), a.N, x);
+      gs[tid] = g;
+      for (int d = 0; d < 3; ++d) xs[d * kTP + tid] = x[d];
+    }
+    cp_async_wait_all();
+    if (sync_abort(abort_flag)) {
+      aborted = true;
+      break;
+    }
+    stage(1, 2, tile);  // a_3 into the other slot
+    const unsigned char* a4 = act;  // slot 0
+    // output layer: dW_5[o] += sum_t g_t a_4[t][o], db_5 += sum_t g_t
+    {
+      float sw = 0.f, sb = 0.f;
+      for (int t = 0; t < kTP; ++t) {
+        const float gt = gs[t];
+        const __nv_bfloat16 v = *reinterpret_cast<const __nv_bfloat16*>(a4 + core_off(t, tid, RG));
+        sw += gt * __bfloat162float(v);
+        sb += gt;
+      }
+      g_w5 += sw;
+      g_b5 += sb;
+    }
+    // Delta_4 = W_5 g (1 - a_4^2), row tid
+#pragma unroll
+    for (int c = 0; c < W; c += 8) {
+      float av[8], v[8];
+      ld_atom(a4, RG, tid, c, av);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
+      st_atom(del, RG, tid, c, v);
+    }
+    int slot = 1;  // slot of a_{L-1}
+    for (int L = 4; L >= 2; --L) {
+      cp_async_wait_all();
+      if (sync_abort(abort_flag)) {
+        aborted = true;
+        break;
+      }
+      // the slot not holding a_{L-1} is free: prefetch the next activations
+      if (L > 2) stage(1 - slot, L - 3, tile);                     // a_{L-2}
+      else if (tile + (int)gridDim.x < ntiles) stage(1 - slot, 3, tile + gridDim.x);  // next a_4
+      const uint32_t ain = act_s + slot * TcSmemB2::ACT_SZ;
+      if (tid == 0) {
+#pragma unroll
+        for (int ks = 0; ks < kTP / 16; ++ks)
+          mma_bf16(tmem + col_dw2(L), desc_mn(del_s, RG, ks), desc_mn(ain, RG, ks), id_dw,
+                   (ks > 0 || !first) ? 1u : 0u);
+        const uint32_t wl = wt_s + (L - 2) * W * W * 2;
+#pragma unroll
+        for (int ks = 0; ks < W / 16; ++ks)
+          mma_bf16(tmem, desc_k(del_s, RG, ks), desc_mn(wl, RG, ks), id_dp, ks > 0);
+        mma_commit(mbar);
+      }
+      // db_L[o] += sum_t Delta_L[t][o] while the products run
+      {
+        float sb = 0.f;
+        for (int t = 0; t < kTP; ++t)
+          sb += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(del + core_off(t, tid, RG)));
+        g_bh[L - 2] += sb;
+      }
+      if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+      phase ^= 1;
+      tc_fence_after();
+      __syncthreads();  // every column sum has read Delta_L
+      // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2), rewritten in place
+      const unsigned char* aprev = act + slot * TcSmemB2::ACT_SZ;
+#pragma unroll 2
+      for (int c = 0; c < W; c += 16) {
+        float dv[16];
+        tmem_ld16(lane_base + c, dv);
+        float av[8], v[8];
+        ld_atom(aprev, RG, tid, c, av);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = dv[j] * (1.0f - av[j] * av[j]);
+        st_atom(del, RG, tid, c, v);
+        ld_atom(aprev, RG, tid, c + 8, av);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = dv[8 + j] * (1.0f - av[j] * av[j]);
+        st_atom(del, RG, tid, c + 8, v);
+      }
+      slot = 1 - slot;
+    }
+    if (aborted) break;
+    __syncthreads();
+    // first layer: dW_1[o][d] += sum_t Delta_1[t][o] x'_d[t], db_1[o] += sum_t Delta_1[t][o]
+    {
+      float sw[3] = {0.f, 0.f, 0.f}, sb = 0.f;
+      for (int t = 0; t < kTP; ++t) {
+        const float dv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(del + core_off(t, tid, RG)));
+#pragma unroll
+        for (int d = 0; d < DIN; ++d) sw[d] += dv * xs[d * kTP + t];
+        sb += dv;
+      }
+#pragma unroll
+      for (int d = 0; d < DIN; ++d) g_w1[d] += sw[d];
+      g_b1 += sb;
+    }
+    first = false;
+    __syncthreads();  // column sums above read every row of Delta_1, g and x'
+  }
+  cp_async_wait_all();
+  float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
+  const int o = tid;
+  aborted = sync_abort(abort_flag);
+  if (!aborted && !first) {
+    for (int L = 4; L >= 2; --L) {
+      const int ow = o2 + (L - 2) * (W * W + W);
+      for (int c = 0; c < W; c += 16) {
+        float v[16];
+        tmem_ld16(lane_base + col_dw2(L) + c, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) gacc[ow + o * W + c + j] = v[j];
+      }
+      gacc[ow + W * W + o] = g_bh[L - 2];
+    }
+    gacc[o5 + o] = g_w5;
+    if (o == 0) gacc[o5 + W] = g_b5;
+    for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = g_w1[d];
+    gacc[ob1 + o] = g_b1;
+  } else if (first) {
+    for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;
+  }
+  if (aborted && tid == 0) atomicOr(a.flags, 8);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 int g_sms = 0;
 int sms() {
   if (!g_sms) {
@@ -585,32 +792,49 @@ int mlp_tc_bwd_blocks(int npts) {
   return ntiles < sms() ? ntiles : sms();  // 512 TMEM columns: one CTA per SM
 }
 
-cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
-  if (a.width != kW) return cudaErrorNotSupported;
-  if (a.npts <= 0) return cudaSuccess;
+template <int W, int DIN>
+static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
+  const size_t smem = TcSmemF<W>::TOTAL;
+  auto k = k_mlp_fwd_tc<W, DIN>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTP, smem);
+  if (occ < 1) occ = 1;
+  if (occ > 4) occ = 4;  // TMEM: 4 x 128 columns at most
   const int ntiles = (a.npts + kTP - 1) / kTP;
-  const size_t smem = TcSmemF::TOTAL;
-  if (a.din == 2) {
-    cudaFuncSetAttribute(k_mlp_fwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int grid = ntiles < 4 * sms() ? ntiles : 4 * sms();
-    k_mlp_fwd_tc<2><<<grid, kTP, smem, st>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_mlp_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int grid = ntiles < 4 * sms() ? ntiles : 4 * sms();
-    k_mlp_fwd_tc<3><<<grid, kTP, smem, st>>>(a);
-  }
+  const int grid = ntiles < occ * sms() ? ntiles : occ * sms();
+  k<<<grid, kTP, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
+  if (a.npts <= 0) return cudaSuccess;
+  if (a.width == 64) return a.din == 2 ? fwd_tc<64, 2>(a, st) : fwd_tc<64, 3>(a, st);
+  if (a.width == 128) return a.din == 2 ? fwd_tc<128, 2>(a, st) : fwd_tc<128, 3>(a, st);
+  return cudaErrorNotSupported;
+}
+
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
-  if (a.width != kW) return cudaErrorNotSupported;
-  const size_t smem = TcSmemB::TOTAL;
-  if (a.din == 2) {
-    cudaFuncSetAttribute(k_mlp_bwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mlp_bwd_tc<2><<<nblk, kTP, smem, st>>>(a);
+  if (a.width == 64) {
+    const size_t smem = TcSmemB::TOTAL;
+    if (a.din == 2) {
+      cudaFuncSetAttribute(k_mlp_bwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mlp_bwd_tc<2><<<nblk, kTP, smem, st>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_mlp_bwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mlp_bwd_tc<3><<<nblk, kTP, smem, st>>>(a);
+    }
+  } else if (a.width == 128) {
+    const size_t smem = TcSmemB2::TOTAL;
+    if (a.din == 2) {
+      cudaFuncSetAttribute(k_mlp_bwd_tc128<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mlp_bwd_tc128<2><<<nblk, kTP, smem, st>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_mlp_bwd_tc128<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mlp_bwd_tc128<3><<<nblk, kTP, smem, st>>>(a);
+    }
   } else {
-    cudaFuncSetAttribute(k_mlp_bwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mlp_bwd_tc<3><<<nblk, kTP, smem, st>>>(a);
+    return cudaErrorNotSupported;
   }
   return cudaGetLastError();
 }

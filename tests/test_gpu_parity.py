@@ -375,3 +375,73 @@ def test_adjoint_vs_finite_differences_16_directions():
         print(f"FD check eps_rel={eps_rel}: max relative deviation {max(errs):.2e}")
         assert max(errs) < 1e-3
     s.close()
+
+
+@pytest.mark.parametrize("n", [3, 17, 70])
+def test_loss_and_gradient_bf16_width128(n):
+    """Width-128 tensor-core network (the 2-128x4-1 network of the 1024^2
+    mixed-precision configuration): dW of the hidden layers on the tensor
+    cores, the small gradients as FP32 sums on the CUDA cores."""
+    sc, s, crv, theta, alpha, f = _crv_case(n, "bf16", width=128)
+    loss = s.loss_grad()
+    ref_loss, ref_grad, parts = crv.loss_grad(MLP(2, 128, 4), theta, alpha, f)
+    assert np.abs(s.get("U") - parts["u"]).max() <= 2e-2 * max(1.0, np.abs(parts["u"]).max())
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    g = s.get("GRAD")
+    assert rel_l2(g, ref_grad) <= 2e-2
+    assert g @ ref_grad / (np.linalg.norm(g) * np.linalg.norm(ref_grad)) >= 0.9995
+    s.close()
+
+
+def test_config3_mesh_1024_mixed_precision():
+    """1024^2 elements, FP32 saturation step vs the FP64 oracle (1e-5) and the
+    BF16 width-128 network's loss and gradient vs the FP64 oracle at the
+    1025^2 collocation grid (1,046,529 interior points)."""
+    n = 1024
+    sc = scn.make_scenario(2, n, seed=1000, S0="random")
+    P = np.random.default_rng(0).normal(size=(n + 2, n + 2))
+    s = solver(sc, width=128, crv_dtype="bf16", ads_dtype="f32")
+    s.set_pressure(P)
+    s.saturation_step(1e-5, 1)
+    S1 = s.get("S")
+    assert rel_inf(S1, AdsOracle(sc).step(sc.S0, P, 1e-5)) <= 1e-5
+    theta = scn.make_theta0(2, 128, 4, seed=7)
+    s.set_theta(theta)
+    s.update_coefficients()
+    loss = s.loss_grad()
+    crv = CrvOracle(sc)
+    alpha, f = crv.coefficients(S1)
+    ref_loss, ref_grad, _ = crv.loss_grad(MLP(2, 128, 4), theta, alpha, f, gram="fd")
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    g = s.get("GRAD")
+    assert g @ ref_grad / (np.linalg.norm(g) * np.linalg.norm(ref_grad)) >= 0.999
+    s.close()
+
+
+def test_adjoint_vs_finite_differences_1024_fp64():
+    """The FP64 GPU gradient against central differences of the GPU's own FP64
+    loss on 16 random unit directions at 1024^2 (a property at any size)."""
+    n = 1024
+    sc = scn.make_scenario(2, n, seed=1000, S0="random")
+    theta = scn.make_theta0(2, 64, 4, seed=7) + 0.01 * np.random.default_rng(1).normal(
+        size=scn.mlp_num_params(2, 64, 4))
+    s = solver(sc, width=64, crv_dtype="f64", ads_dtype="f64")
+    s.set_theta(theta)
+    s.update_coefficients()
+    s.loss_grad()
+    g = s.get("GRAD")
+    rng = np.random.default_rng(11)
+    eps = 1e-3 * np.linalg.norm(theta) / np.sqrt(theta.size)
+    worst = 0.0
+    for _ in range(16):
+        d = rng.normal(size=theta.size)
+        d /= np.linalg.norm(d)
+        s.set_theta(theta + eps * d)
+        lp = s.loss_grad()
+        s.set_theta(theta - eps * d)
+        lm = s.loss_grad()
+        fd = (lp - lm) / (2 * eps)
+        worst = max(worst, abs(g @ d - fd) / max(abs(fd), 1e-6 * np.linalg.norm(g)))
+    print(f"1024^2 FD check: max relative deviation {worst:.2e}")
+    assert worst < 1e-4
+    s.close()
