@@ -844,7 +844,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     c->nparams = mlp_params(c->dim, crv->width, crv->hidden_layers);
     c->ld = ((c->M + 63) / 64) * 64;
     c->ndot = dot_blocks(c->M);
-    c->nbwd = c->use_tc ? mlp_tc_bwd_blocks(c->M) : mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
+    c->nbwd = c->use_tc ? mlp_tc_bwd_blocks(c->M, crv->width, c->dim) : mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
     ALV(c->alpha, tc * nn);
     ALV(c->f, tc * c->M);
     ALV(c->u, tc * c->M);

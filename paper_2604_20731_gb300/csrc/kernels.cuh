@@ -180,6 +180,6 @@ struct MlpTcArgs {
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
 size_t mlp_tc_acts_bytes(int npts, int width);
-int mlp_tc_bwd_blocks(int npts);
+int mlp_tc_bwd_blocks(int npts, int width, int din);
 
 }  // namespace adsgb

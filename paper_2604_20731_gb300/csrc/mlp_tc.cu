@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// backward
-// ---------------------------------------------------------------------------
+// backward, width 64: every gradient on the tensor cores.  The activation
+// tiles carry a ones column (biases), the delta tiles are zero-padded to
+// M = 128, and the accumulators fill the 512 TMEM columns, so one CTA per SM.
 struct TcSmemB {
   static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
   static constexpr int ACT = W + 3 * kW * kW * 2;          // 4 x [128][80] bf16      80 KB
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
                 RGX = (kXP / 8) * 128;
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
-  load_hidden_weights(th, o2, wt, tid, kTP);
+  load_hidden_weights<kW>(th, o2, wt, tid, kTP);
   for (int i = tid; i < kW; i += kTP) fW5[i] = th[o5 + i];
   // constant columns: ones column of the activation tiles and of the input
   // tile, zero padding of the delta tiles
@@ -564,44 +565,99 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// backward, ring form (W = 128; it also compiles for W = 64).  TMEM holds
+// the delta product (W columns) and the three hidden dW accumulators (3 x W):
+// all 512 columns for W = 128.  The small gradients (biases,
+// output layer, first layer) are per-thread FP32 sums over the points
+// (thread o owns output o; fixed order).  Activation tiles stream through a
+// two-slot ring, each prefetched while the previous stage computes; the delta
+// tile (zero-padded to 128 columns so that dW is an M = 128 product) is
+// rewritten in place once the products that read it have completed.
 // ---------------------------------------------------------------------------
-// backward, width 128: the three hidden dW accumulators (3 x 128 TMEM columns)
-// and the delta product (128 columns) fill the 512 TMEM columns, so the small
-// gradients (biases, output layer, first layer) are per-thread FP32 sums over
-// the points (thread o owns output o; fixed order).  Activation tiles stream
-// through a two-slot ring; the delta tile is rewritten in place once the
-// products that read it have completed.
-// ---------------------------------------------------------------------------
-constexpr int kW2 = 128;
+
+// Weighted column sums of a BF16 [128][C] core-matrix tile over its 128 rows:
+// out[k][o] += sum_t w_k[t] T[t][o] for o < W, k < NW.  Thread layout: ri =
+// tid % 8 (row within a core matrix), cg = (tid / 8) % (W / 8) (column group),
+// and the row groups are split over the remaining thread index, so that a
+// quarter-warp reads 8 consecutive rows of one core-matrix column (128
+// contiguous bytes, conflict-free).  Partial sums meet in `red` and are added
+// in a fixed order by thread o.
+template <int W, int NW>
+ADS_D void tile_colsums(const unsigned char* tile, int rg, const float* const* w, float* red,
+                        float* out) {
+  constexpr int CG = W / 8, NSETS = kTP / (8 * CG), NPART = 8 * NSETS;
+  static_assert(kTP % (8 * CG) == 0 && NW <= 4, "one block of kTP threads covers whole row sets");
+  const int tid = threadIdx.x;
+  const int ri = tid % 8, cg = (tid / 8) % CG, set = tid / (8 * CG);
+  float acc[NW][8];
+#pragma unroll
+  for (int k = 0; k < NW; ++k)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
+  for (int g = set; g < kTP / 8; g += NSETS) {
+    const int t = g * 8 + ri;
+    float v[8];
+    ld_atom(tile, rg, t, cg * 8, v);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const float wk = w[k] ? w[k][t] : 1.0f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[k][j] += wk * v[j];
+    }
+  }
+  const int part = ri + 8 * set;
+#pragma unroll
+  for (int k = 0; k < NW; ++k)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[(k * NPART + part) * W + cg * 8 + j] = acc[k][j];
+  __syncthreads();
+  if (tid < W) {
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      float sum = 0.f;
+      for (int q = 0; q < NPART; ++q) sum += red[(k * NPART + q) * W + tid];
+      out[k] += sum;
+    }
+  }
+  __syncthreads();
+}
+
+template <int W>
 struct TcSmemB2 {
-  static constexpr int WT = 0;                             // 3 x [128][128] bf16     96 KB
-  static constexpr int ACT = WT + 3 * kW2 * kW2 * 2;       // 2 x [128][128] bf16     64 KB
-  static constexpr int ACT_SZ = kTP * kW2 * 2;
-  static constexpr int DEL = ACT + 2 * ACT_SZ;             // [128][128] bf16         32 KB
-  static constexpr int VEC = DEL + kTP * kW2 * 2;          // fp32: W5 [128], g [128], x' [3][128]
-  static constexpr int BAR = VEC + (kW2 + kTP + 3 * kTP) * 4;
+  static constexpr int WT = 0;                             // 3 x [W][W] bf16
+  static constexpr int ACT = WT + 3 * W * W * 2;           // 2 x [128][W] bf16
+  static constexpr int ACT_SZ = kTP * W * 2;
+  static constexpr int DEL = ACT + 2 * ACT_SZ;             // [128][128] bf16
+  static constexpr int VEC = DEL + kTP * kDP * 2;          // fp32: W5 [W], g [128], x' [3][128]
+  static constexpr int RED = VEC + (W + kTP + 3 * kTP) * 4;  // column-sum partials [4][1024/W][W] fp32
+  static constexpr int BAR = RED + 4 * (8 * kTP / W) * W * 4;
   static constexpr int TOTAL = BAR + 32;
 };
 
-template <int DIN>
-__global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
-  constexpr int W = kW2;
+template <int W, int DIN>
+__global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
+  constexpr int NCOL = 4 * W;  // TMEM columns: delta product + three dW
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* wt = sm + TcSmemB2::WT;
-  unsigned char* act = sm + TcSmemB2::ACT;  // two slots
-  unsigned char* del = sm + TcSmemB2::DEL;
-  float* fW5 = reinterpret_cast<float*>(sm + TcSmemB2::VEC);
+  unsigned char* wt = sm + TcSmemB2<W>::WT;
+  unsigned char* act = sm + TcSmemB2<W>::ACT;  // two slots
+  unsigned char* del = sm + TcSmemB2<W>::DEL;
+  float* fW5 = reinterpret_cast<float*>(sm + TcSmemB2<W>::VEC);
   float* gs = fW5 + W;
   float* xs = gs + kTP;  // [3][128]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB2::BAR);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB2::BAR + 8);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB2::BAR + 12);
+  float* red = reinterpret_cast<float*>(sm + TcSmemB2<W>::RED);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB2<W>::BAR);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB2<W>::BAR + 8);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB2<W>::BAR + 12);
   const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int RG = (W / 8) * 128;
+  constexpr int RG = (W / 8) * 128, RGD = (kDP / 8) * 128;
   const float* th = a.theta;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
   load_hidden_weights<W>(th, o2, wt, tid, kTP);
-  fW5[tid] = th[o5 + tid];
+  if (tid < W) fW5[tid] = th[o5 + tid];
+  if (W < kDP) {  // zero padding columns of the delta tile (never rewritten)
+    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = W; c < kDP; c += 8) st_atom(del, RGD, tid, c, z);
+  }
   if (tid == 0) {
     *abort_flag = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
@@ -609,7 +665,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(tbase)), "r"(512));
+                     smem_addr(tbase)), "r"(NCOL));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_async_smem();
@@ -619,9 +675,9 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
   const uint32_t tmem = *tbase;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
   const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del);
-  const uint32_t id_dw = idesc_bf16(kTP, W, 1, 1);  // dW_l: M = 128 (o), N = 128 (k), K = points
-  const uint32_t id_dp = idesc_bf16(kTP, W, 0, 1);  // delta product: M = points, N = 128, K = 128
-  auto col_dw2 = [](int L) { return 128 + (4 - L) * 128; };  // dW4 128, dW3 256, dW2 384
+  const uint32_t id_dw = idesc_bf16(kDP, W, 1, 1);  // dW_l: M = 128 (o, padded), N = W (k), K = points
+  const uint32_t id_dp = idesc_bf16(kTP, W, 0, 1);  // delta product: M = points, N = W, K = W
+  auto col_dw2 = [](int L) { return W + (4 - L) * W; };  // dW4, dW3, dW2 after the delta product
   // per-thread small gradients (thread o)
   float g_w5 = 0.f, g_b5 = 0.f, g_b1 = 0.f, g_w1[3] = {0.f, 0.f, 0.f}, g_bh[3] = {0.f, 0.f, 0.f};
   uint32_t phase = 0;
@@ -629,7 +685,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
   const int ntiles = (a.npts + kTP - 1) / kTP;
   auto stage = [&](int slot, int L, int tile) {  // activations a_{L+1} (L = 0..3) of `tile`
     const unsigned char* src = a.acts + ((size_t)tile * 4 + L) * kTP * W * 2;
-    unsigned char* dst = act + slot * TcSmemB2::ACT_SZ;
+    unsigned char* dst = act + slot * TcSmemB2<W>::ACT_SZ;
     for (int ch = tid; ch < kTP * W * 2 / 16; ch += kTP) cp_async16(dst + ch * 16, src + ch * 16);
     cp_async_commit();
   };
@@ -653,15 +709,13 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
     const unsigned char* a4 = act;  // slot 0
     // output layer: dW_5[o] += sum_t g_t a_4[t][o], db_5 += sum_t g_t
     {
-      float sw = 0.f, sb = 0.f;
-      for (int t = 0; t < kTP; ++t) {
-        const float gt = gs[t];
-        const __nv_bfloat16 v = *reinterpret_cast<const __nv_bfloat16*>(a4 + core_off(t, tid, RG));
-        sw += gt * __bfloat162float(v);
-        sb += gt;
+      const float* wts[1] = {gs};
+      tile_colsums<W, 1>(a4, RG, wts, red, &g_w5);
+      if (tid == 0) {
+        float sb = 0.f;
+        for (int t = 0; t < kTP; ++t) sb += gs[t];
+        g_b5 += sb;
       }
-      g_w5 += sw;
-      g_b5 += sb;
     }
     // Delta_4 = W_5 g (1 - a_4^2), row tid
 #pragma unroll
@@ -670,7 +724,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
       ld_atom(a4, RG, tid, c, av);
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
-      st_atom(del, RG, tid, c, v);
+      st_atom(del, RGD, tid, c, v);
     }
     int slot = 1;  // slot of a_{L-1}
     for (int L = 4; L >= 2; --L) {
@@ -682,31 +736,29 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
       // the slot not holding a_{L-1} is free: prefetch the next activations
       if (L > 2) stage(1 - slot, L - 3, tile);                     // a_{L-2}
       else if (tile + (int)gridDim.x < ntiles) stage(1 - slot, 3, tile + gridDim.x);  // next a_4
-      const uint32_t ain = act_s + slot * TcSmemB2::ACT_SZ;
+      const uint32_t ain = act_s + slot * TcSmemB2<W>::ACT_SZ;
       if (tid == 0) {
 #pragma unroll
         for (int ks = 0; ks < kTP / 16; ++ks)
-          mma_bf16(tmem + col_dw2(L), desc_mn(del_s, RG, ks), desc_mn(ain, RG, ks), id_dw,
+          mma_bf16(tmem + col_dw2(L), desc_mn(del_s, RGD, ks), desc_mn(ain, RG, ks), id_dw,
                    (ks > 0 || !first) ? 1u : 0u);
         const uint32_t wl = wt_s + (L - 2) * W * W * 2;
 #pragma unroll
         for (int ks = 0; ks < W / 16; ++ks)
-          mma_bf16(tmem, desc_k(del_s, RG, ks), desc_mn(wl, RG, ks), id_dp, ks > 0);
+          mma_bf16(tmem, desc_k(del_s, RGD, ks), desc_mn(wl, RG, ks), id_dp, ks > 0);
         mma_commit(mbar);
       }
-      // db_L[o] += sum_t Delta_L[t][o] while the products run
+      // db_L[o] += sum_t Delta_L[t][o] while the products run (ends with a CTA barrier,
+      // so every column sum has read Delta_L before it is rewritten below)
       {
-        float sb = 0.f;
-        for (int t = 0; t < kTP; ++t)
-          sb += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(del + core_off(t, tid, RG)));
-        g_bh[L - 2] += sb;
+        const float* wts[1] = {nullptr};
+        tile_colsums<W, 1>(del, RGD, wts, red, &g_bh[L - 2]);
       }
       if (!mbar_wait(mbar, phase)) *abort_flag = 1;
       phase ^= 1;
       tc_fence_after();
-      __syncthreads();  // every column sum has read Delta_L
       // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2), rewritten in place
-      const unsigned char* aprev = act + slot * TcSmemB2::ACT_SZ;
+      const unsigned char* aprev = act + slot * TcSmemB2<W>::ACT_SZ;
 #pragma unroll 2
       for (int c = 0; c < W; c += 16) {
         float dv[16];
@@ -715,11 +767,11 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
         ld_atom(aprev, RG, tid, c, av);
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = dv[j] * (1.0f - av[j] * av[j]);
-        st_atom(del, RG, tid, c, v);
+        st_atom(del, RGD, tid, c, v);
         ld_atom(aprev, RG, tid, c + 8, av);
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = dv[8 + j] * (1.0f - av[j] * av[j]);
-        st_atom(del, RG, tid, c + 8, v);
+        st_atom(del, RGD, tid, c + 8, v);
       }
       slot = 1 - slot;
     }
@@ -727,19 +779,19 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
     __syncthreads();
     // first layer: dW_1[o][d] += sum_t Delta_1[t][o] x'_d[t], db_1[o] += sum_t Delta_1[t][o]
     {
-      float sw[3] = {0.f, 0.f, 0.f}, sb = 0.f;
-      for (int t = 0; t < kTP; ++t) {
-        const float dv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(del + core_off(t, tid, RG)));
+      float sums[DIN + 1];
 #pragma unroll
-        for (int d = 0; d < DIN; ++d) sw[d] += dv * xs[d * kTP + t];
-        sb += dv;
-      }
+      for (int d = 0; d <= DIN; ++d) sums[d] = 0.f;
+      const float* wts[DIN + 1];
 #pragma unroll
-      for (int d = 0; d < DIN; ++d) g_w1[d] += sw[d];
-      g_b1 += sb;
+      for (int d = 0; d < DIN; ++d) wts[d] = xs + d * kTP;
+      wts[DIN] = nullptr;
+      tile_colsums<W, DIN + 1>(del, RGD, wts, red, sums);  // ends with a CTA barrier
+#pragma unroll
+      for (int d = 0; d < DIN; ++d) g_w1[d] += sums[d];
+      g_b1 += sums[DIN];
     }
     first = false;
-    __syncthreads();  // column sums above read every row of Delta_1, g and x'
   }
   cp_async_wait_all();
   float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
@@ -750,23 +802,27 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc128(MlpTcArgs a) {
       const int ow = o2 + (L - 2) * (W * W + W);
       for (int c = 0; c < W; c += 16) {
         float v[16];
-        tmem_ld16(lane_base + col_dw2(L) + c, v);
+        tmem_ld16(lane_base + col_dw2(L) + c, v);  // warp-collective: every thread issues it
+        if (o < W) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) gacc[ow + o * W + c + j] = v[j];
+          for (int j = 0; j < 16; ++j) gacc[ow + o * W + c + j] = v[j];
+        }
       }
-      gacc[ow + W * W + o] = g_bh[L - 2];
+      if (o < W) gacc[ow + W * W + o] = g_bh[L - 2];
     }
-    gacc[o5 + o] = g_w5;
+    if (o < W) {
+      gacc[o5 + o] = g_w5;
+      for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = g_w1[d];
+      gacc[ob1 + o] = g_b1;
+    }
     if (o == 0) gacc[o5 + W] = g_b5;
-    for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = g_w1[d];
-    gacc[ob1 + o] = g_b1;
   } else if (first) {
     for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;
   }
   if (aborted && tid == 0) atomicOr(a.flags, 8);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
 }
 
 int g_sms = 0;
@@ -787,9 +843,25 @@ size_t mlp_tc_acts_bytes(int npts, int width) {
   return (size_t)ntiles * 4 * kTP * width * 2;
 }
 
-int mlp_tc_bwd_blocks(int npts) {
-  int ntiles = (npts + kTP - 1) / kTP;
-  return ntiles < sms() ? ntiles : sms();  // 512 TMEM columns: one CTA per SM
+template <int W, int DIN>
+static int bwd_tc_occ() {
+  auto k = k_mlp_bwd_tcr<W, DIN>;
+  const size_t smem = TcSmemB2<W>::TOTAL;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTP, smem);
+  const int by_tmem = 512 / (4 * W);
+  if (occ > by_tmem) occ = by_tmem;
+  return occ < 1 ? 1 : occ;
+}
+
+int mlp_tc_bwd_blocks(int npts, int width, int din) {
+  const int ntiles = (npts + kTP - 1) / kTP;
+  int occ = 1;
+  if (width != 64) occ = din == 2 ? bwd_tc_occ<128, 2>() : bwd_tc_occ<128, 3>();
+  // width 64: the all-tensor-core kernel holds 512 TMEM columns, one CTA per SM
+  const int nb = occ * sms();
+  return ntiles < nb ? ntiles : nb;
 }
 
 template <int W, int DIN>
@@ -800,7 +872,7 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTP, smem);
   if (occ < 1) occ = 1;
-  if (occ > 4) occ = 4;  // TMEM: 4 x 128 columns at most
+  if (occ > 512 / W) occ = 512 / W;  // TMEM columns per SM
   const int ntiles = (a.npts + kTP - 1) / kTP;
   const int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   k<<<grid, kTP, smem, st>>>(a);
@@ -814,29 +886,25 @@ cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   return cudaErrorNotSupported;
 }
 
+template <int W, int DIN>
+static cudaError_t bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
+  auto k = k_mlp_bwd_tcr<W, DIN>;
+  const size_t smem = TcSmemB2<W>::TOTAL;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<nblk, kTP, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
   if (a.width == 64) {
     const size_t smem = TcSmemB::TOTAL;
-    if (a.din == 2) {
-      cudaFuncSetAttribute(k_mlp_bwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mlp_bwd_tc<2><<<nblk, kTP, smem, st>>>(a);
-    } else {
-      cudaFuncSetAttribute(k_mlp_bwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mlp_bwd_tc<3><<<nblk, kTP, smem, st>>>(a);
-    }
-  } else if (a.width == 128) {
-    const size_t smem = TcSmemB2::TOTAL;
-    if (a.din == 2) {
-      cudaFuncSetAttribute(k_mlp_bwd_tc128<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mlp_bwd_tc128<2><<<nblk, kTP, smem, st>>>(a);
-    } else {
-      cudaFuncSetAttribute(k_mlp_bwd_tc128<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mlp_bwd_tc128<3><<<nblk, kTP, smem, st>>>(a);
-    }
-  } else {
-    return cudaErrorNotSupported;
+    auto k = a.din == 2 ? k_mlp_bwd_tc<2> : k_mlp_bwd_tc<3>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, kTP, smem, st>>>(a);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  if (a.width == 128) return a.din == 2 ? bwd_tc<128, 2>(a, nblk, st) : bwd_tc<128, 3>(a, nblk, st);
+  return cudaErrorNotSupported;
 }
 
 }  // namespace adsgb
