@@ -10,8 +10,10 @@
 //    strip's rows in shared memory (M^-1 = Mx^-1 (x) My^-1, Eq. 14);
 //  * the y-direction sweep: one thread per column, coalesced row access,
 //    adding the rows the strip above spilled, and accumulating int S.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "kernels.cuh"
 
@@ -169,204 +171,393 @@ template cudaError_t launch_to_double<double>(const double*, double*, size_t, cu
 template cudaError_t launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// element quadrature (2D)
+// 2D saturation step (Eq. 10b, Eqs. 14-15): element quadrature fused with the
+// x-direction mass solve, then the y-direction mass solve
 // ---------------------------------------------------------------------------
-// Computes the 3x3 local contributions loc[b][a] of element (ex, ey) to the
-// right-hand side entries (ey+b, ex+a), and adds tau int q_g/phi over the
-// element to `src`.  Fields at the Gauss points are sum-factorised: a
-// contraction along x first, then along y; the test functions are applied in
-// the reverse order.
-template <typename T, int MODE>
-__device__ __forceinline__ void element_rhs_2d(const QuadArgs<T>& a, int ex, int ey, T loc[3][3],
-                                               double& src) {
-  const int nb = a.nb, n1 = a.n + 1;
-  const T* Bx = a.ax.B + ex * 9;
-  const T* dBx = a.ax.dB + ex * 9;
-  const T* By = a.ax.B + ey * 9;
-  const T* dBy = a.ax.dB + ey * 9;
-  T bx[3][3], dbx[3][3], by[3][3], dby[3][3];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    bx[i / 3][i % 3] = __ldg(Bx + i);
-    dbx[i / 3][i % 3] = __ldg(dBx + i);
-    by[i / 3][i % 3] = __ldg(By + i);
-    dby[i / 3][i % 3] = __ldg(dBy + i);
-  }
-  T c0[3][3], cx[3][3], cy[3][3];  // [qy][qx]
-  const T h2 = a.h * a.h;
-  if (MODE == 0) {
-    T Sx[3][3], Px[3][3], Pdx[3][3];  // [b][qx]
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const T* srow = a.S + (size_t)(ey + b) * nb + ex;
-      const T* prow = a.P + (size_t)(ey + b) * nb + ex;
-      T s0 = __ldg(srow), s1 = __ldg(srow + 1), s2 = __ldg(srow + 2);
-      T p0 = __ldg(prow), p1 = __ldg(prow + 1), p2 = __ldg(prow + 2);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        Sx[b][q] = s0 * bx[0][q] + s1 * bx[1][q] + s2 * bx[2][q];
-        Px[b][q] = p0 * bx[0][q] + p1 * bx[1][q] + p2 * bx[2][q];
-        Pdx[b][q] = p0 * dbx[0][q] + p1 * dbx[1][q] + p2 * dbx[2][q];
-      }
-    }
-    const T* Kr = a.K + (size_t)ey * n1 + ex;
-    T k00 = __ldg(Kr), k01 = __ldg(Kr + 1), k10 = __ldg(Kr + n1), k11 = __ldg(Kr + n1 + 1);
-    T f00 = a.phi_c, f01 = a.phi_c, f10 = a.phi_c, f11 = a.phi_c;
-    if (a.phi) {
-      const T* Fr = a.phi + (size_t)ey * n1 + ex;
-      f00 = __ldg(Fr); f01 = __ldg(Fr + 1); f10 = __ldg(Fr + n1); f11 = __ldg(Fr + n1 + 1);
-    }
-    const T dt = (T)(*a.dt);
-    T gx[kMaxSrc][3], gy[kMaxSrc][3];
-    for (int s = 0; s < a.n_src; ++s)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        gx[s][q] = __ldg(a.ax.gsrc + ((size_t)(0 * kMaxSrc + s) * a.n + ex) * 3 + q);
-        gy[s][q] = __ldg(a.ax.gsrc + ((size_t)(1 * kMaxSrc + s) * a.n + ey) * 3 + q);
-      }
-#pragma unroll
-    for (int qy = 0; qy < 3; ++qy) {
-      const T eta = (T)gauss_x(qy);
-#pragma unroll
-      for (int qx = 0; qx < 3; ++qx) {
-        const T xi = (T)gauss_x(qx);
-        T Sv = by[0][qy] * Sx[0][qx] + by[1][qy] * Sx[1][qx] + by[2][qy] * Sx[2][qx];
-        T dpx = by[0][qy] * Pdx[0][qx] + by[1][qy] * Pdx[1][qx] + by[2][qy] * Pdx[2][qx];
-        T dpy = dby[0][qy] * Px[0][qx] + dby[1][qy] * Px[1][qx] + dby[2][qy] * Px[2][qx];
-        T Kq = (T(1) - eta) * ((T(1) - xi) * k00 + xi * k01) + eta * ((T(1) - xi) * k10 + xi * k11);
-        T phq = (T(1) - eta) * ((T(1) - xi) * f00 + xi * f01) + eta * ((T(1) - xi) * f10 + xi * f11);
-        T St = clamp01(Sv);
-        T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
-        T qi = T(0), qp = T(0);
-        for (int s = 0; s < a.n_src; ++s) {
-          T g = a.rate[s] * gx[s][qx] * gy[s][qy];
-          if (a.kind[s] == 0) qi += g; else qp += g;
-        }
-        T qg = qi - lg / (lg + lw) * qp;
-        T w = (T)(gauss_w(qx) * gauss_w(qy)) * h2;
-        T dtphi = dt / phq;
-        c0[qy][qx] = w * (Sv + dtphi * qg);
-        T cf = -w * dtphi * lg * Kq;
-        cx[qy][qx] = cf * dpx;
-        cy[qy][qx] = cf * (dpy + a.grav_term);
-        src += (double)(w * dtphi * qg);
-      }
-    }
-  } else {
-    const T* Ur = a.nodal + (size_t)ey * n1 + ex;
-    T u00 = __ldg(Ur), u01 = __ldg(Ur + 1), u10 = __ldg(Ur + n1), u11 = __ldg(Ur + n1 + 1);
-#pragma unroll
-    for (int qy = 0; qy < 3; ++qy) {
-      const T eta = (T)gauss_x(qy);
-#pragma unroll
-      for (int qx = 0; qx < 3; ++qx) {
-        const T xi = (T)gauss_x(qx);
-        T uq = (T(1) - eta) * ((T(1) - xi) * u00 + xi * u01) + eta * ((T(1) - xi) * u10 + xi * u11);
-        c0[qy][qx] = (T)(gauss_w(qx) * gauss_w(qy)) * h2 * uq;
-        cx[qy][qx] = T(0);
-        cy[qy][qx] = T(0);
-      }
-    }
-  }
-  // test functions: along x, then along y
-  T T0[3][3], T1[3][3];  // [qy][a]
-#pragma unroll
-  for (int qy = 0; qy < 3; ++qy)
-#pragma unroll
-    for (int aa = 0; aa < 3; ++aa) {
-      T t0 = T(0), t1 = T(0);
-#pragma unroll
-      for (int qx = 0; qx < 3; ++qx) {
-        t0 += c0[qy][qx] * bx[aa][qx];
-        if (MODE == 0) {
-          t0 += cx[qy][qx] * dbx[aa][qx];
-          t1 += cy[qy][qx] * bx[aa][qx];
-        }
-      }
-      T0[qy][aa] = t0;
-      T1[qy][aa] = t1;
-    }
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int aa = 0; aa < 3; ++aa) {
-      T v = T(0);
-#pragma unroll
-      for (int qy = 0; qy < 3; ++qy) {
-        v += by[b][qy] * T0[qy][aa];
-        if (MODE == 0) v += dby[b][qy] * T1[qy][aa];
-      }
-      loc[b][aa] = v;
-    }
-}
-
-// In-place LDL^T solve of one line of length nb with element stride `str`.
+// Chunked LDL^T sweeps.  The banded factors are those of the whole line; a
+// line is cut into chunks so that many threads sweep it at once.  A chunk
+// runs the forward substitution from a zero state H rows before its first
+// row, and the backward substitution from a zero state H rows after its last
+// row (a start at or beyond the end of the line is exact).  The error of a
+// zero start obeys the homogeneous recurrence of the unit lower factor, whose
+// solutions shrink by rho = 0.43058 per row: rho is the root inside the unit
+// circle of z^4 + 26 z^3 + 66 z^2 + 26 z + 1, the symbol of the interior row
+// h [1, 26, 66, 26, 1] / 120 of the quadratic B-spline mass matrix.  With
+// H = 32 (FP32) the truncation is 2e-12 of the solution's size and with
+// H = 48 (FP64) 2.4e-18, both below the unit roundoff.
 template <typename T>
-__device__ __forceinline__ void ldlt_line(T* x, int nb, int str, const T* l1, const T* l2,
-                                          const T* dinv) {
-  T ym1 = T(0), ym2 = T(0);
-  for (int l = 0; l < nb; ++l) {
-    T y = x[(size_t)l * str] - l1[l] * ym1 - l2[l] * ym2;
-    x[(size_t)l * str] = y;
-    ym2 = ym1;
-    ym1 = y;
-  }
-  T xp1 = T(0), xp2 = T(0);
-  for (int l = nb - 1; l >= 0; --l) {
-    T v = x[(size_t)l * str] * dinv[l] - l1[l + 1] * xp1 - l2[l + 2] * xp2;
-    x[(size_t)l * str] = v;
-    xp2 = xp1;
-    xp1 = v;
-  }
-}
+struct SweepHalo;
+template <>
+struct SweepHalo<float> {
+  static constexpr int H = 32;
+};
+template <>
+struct SweepHalo<double> {
+  static constexpr int H = 48;
+};
 
 constexpr int kQuadThreads = 256;
+constexpr int kQuadCols = 30;  // DOF columns a warp completes per pass (32 element columns)
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kQuadThreads) k_quad_xsolve_2d(QuadArgs<T> a, int re, T* Xm,
-                                                                  T* Xs, double* src_part) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double red[32];
-  T* acc = reinterpret_cast<T*>(smraw);
-  const int nb = a.nb, n = a.n, tid = threadIdx.x;
-  const int b = blockIdx.x;
-  const int e0 = b * re;
-  const int e1 = min(e0 + re, n);
-  const int nrows = e1 - e0 + 2;
-  for (int i = tid; i < nrows * nb; i += blockDim.x) acc[i] = T(0);
-  __syncthreads();
-  double src = 0.0;
-  for (int er = e0; er < e1; ++er) {
-    for (int base = 0; base < n; base += blockDim.x) {
-      const int ex = base + tid;
-      const bool ok = ex < n;
-      T loc[3][3];
-      if (ok) element_rhs_2d<T, MODE>(a, ex, er, loc, src);
-      // three colours by ex mod 3: elements of one colour touch disjoint columns
+// In-place chunked LDL^T solve of `nrows` lines of length nb in shared memory
+// (row stride ld).  Thread t sweeps chunk t % nch of line t / nch; the host
+// picks the chunk length so that every task has a thread.  The halo values
+// of a chunk are copied to registers before its neighbours overwrite them.
+template <typename T>
+ADS_D void sweep_lines_smem(T* buf, int nrows, int nb, int ld, int chunk,
+                            const T* __restrict__ l1, const T* __restrict__ l2,
+                            const T* __restrict__ dinv) {
+  constexpr int H = SweepHalo<T>::H;
+  const int nch = (nb + chunk - 1) / chunk;
+  const int t = threadIdx.x;
+  const bool act = t < nrows * nch;
+  const int row = act ? t / nch : 0, ch = act ? t % nch : 0;
+  T* line = buf + (size_t)row * ld;
+  const int s = ch * chunk, e = min(nb, s + chunk);
+  T hv[H];
+  if (act) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (ok && (ex % 3) == c) {
-#pragma unroll
-          for (int bb = 0; bb < 3; ++bb)
-#pragma unroll
-            for (int aa = 0; aa < 3; ++aa) acc[(er - e0 + bb) * nb + ex + aa] += loc[bb][aa];
-        }
-        __syncthreads();
-      }
+    for (int k = 0; k < H; ++k) {
+      const int l = s - H + k;
+      hv[k] = l >= 0 ? line[l] : T(0);
     }
   }
-  if (tid < nrows) ldlt_line<T>(acc + tid * nb, nb, 1, a.ax.l1, a.ax.l2, a.ax.dinv);
   __syncthreads();
+  if (act) {
+    T y1 = T(0), y2 = T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int l = s - H + k;
+      if (l >= 0) {
+        const T y = hv[k] - __ldg(l1 + l) * y1 - __ldg(l2 + l) * y2;
+        y2 = y1;
+        y1 = y;
+      }
+    }
+    constexpr int U = 8;  // batches: loads, recurrence in registers, stores
+    int l = s;
+    for (; l + U <= e; l += U) {
+      T v[U], a1[U], a2[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        v[k] = line[l + k];
+        a1[k] = __ldg(l1 + l + k);
+        a2[k] = __ldg(l2 + l + k);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        v[k] = v[k] - a1[k] * y1 - a2[k] * y2;
+        y2 = y1;
+        y1 = v[k];
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) line[l + k] = v[k];
+    }
+    for (; l < e; ++l) {
+      const T y = line[l] - __ldg(l1 + l) * y1 - __ldg(l2 + l) * y2;
+      line[l] = y;
+      y2 = y1;
+      y1 = y;
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int l = e + k;
+      hv[k] = l < nb ? line[l] : T(0);
+    }
+  }
+  __syncthreads();
+  if (act) {
+    T x1 = T(0), x2 = T(0);
+#pragma unroll
+    for (int k = H - 1; k >= 0; --k) {
+      const int l = e + k;
+      if (l < nb) {
+        const T x = hv[k] * __ldg(dinv + l) - __ldg(l1 + l + 1) * x1 - __ldg(l2 + l + 2) * x2;
+        x2 = x1;
+        x1 = x;
+      }
+    }
+    constexpr int U = 8;
+    int l = e - 1;
+    for (; l - U + 1 >= s; l -= U) {
+      T v[U], dd[U], a1[U], a2[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        v[k] = line[l - k];
+        dd[k] = __ldg(dinv + l - k);
+        a1[k] = __ldg(l1 + l - k + 1);
+        a2[k] = __ldg(l2 + l - k + 2);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        v[k] = v[k] * dd[k] - a1[k] * x1 - a2[k] * x2;
+        x2 = x1;
+        x1 = v[k];
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) line[l - k] = v[k];
+    }
+    for (; l >= s; --l) {
+      const T x = line[l] * __ldg(dinv + l) - __ldg(l1 + l + 1) * x1 - __ldg(l2 + l + 2) * x2;
+      line[l] = x;
+      x2 = x1;
+      x1 = x;
+    }
+  }
+  __syncthreads();
+}
+
+// x-contractions of the coefficients of one DOF row over the three basis
+// functions of element column ex, at the three Gauss abscissae
+template <typename T>
+struct XRow {
+  T s[3], p[3], pd[3];
+};
+template <typename T>
+ADS_D void xrow_load(const QuadArgs<T>& a, int r, int ex, const T (&bx)[3][3],
+                     const T (&dbx)[3][3], XRow<T>& w) {
+  const T* srow = a.S + (size_t)r * a.nb + ex;
+  const T* prow = a.P + (size_t)r * a.nb + ex;
+  const T s0 = __ldg(srow), s1 = __ldg(srow + 1), s2 = __ldg(srow + 2);
+  const T p0 = __ldg(prow), p1 = __ldg(prow + 1), p2 = __ldg(prow + 2);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    w.s[q] = s0 * bx[0][q] + s1 * bx[1][q] + s2 * bx[2][q];
+    w.p[q] = p0 * bx[0][q] + p1 * bx[1][q] + p2 * bx[2][q];
+    w.pd[q] = p0 * dbx[0][q] + p1 * dbx[1][q] + p2 * dbx[2][q];
+  }
+}
+
+template <typename T>
+ADS_D T frac_div(T a, T b) { return a / b; }
+template <>
+ADS_D float frac_div<float>(float a, float b) { return __fdividef(a, b); }
+
+// Strip b of `re` element rows.  Phase 1: warp w takes DOF columns
+// [30 g, 30 g + 30) for g = w, w + 8, ...; lane j evaluates element column
+// 30 g - 2 + j down the strip.  An element adds to the DOF columns ex, ex+1,
+// ex+2, so lane j's column sums its own first-column term and the shuffled
+// second- and third-column terms of lanes j-1 and j-2 (lanes 0 and 1 only
+// feed their neighbours).  DOF-row sums roll down the strip in registers; a
+// row is stored once no later element row touches it.  Phase 2: the x sweeps
+// of the strip's rows in shared memory.  Phase 3: rows owned by the strip go
+// to Xm, the two rows it shares with the next strip to Xs.
+template <typename T, int MODE, int NS>
+__global__ void __launch_bounds__(kQuadThreads, sizeof(T) == 4 ? 2 : 1)
+    k_quad_xsweep_2d(QuadArgs<T> a, int re, int xchunk, T* __restrict__ Xm, T* __restrict__ Xs,
+                     int ldx, double* src_part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  T* acc = reinterpret_cast<T*>(smraw);  // [re + 2][nb]
+  const int nb = a.nb, n = a.n, n1 = n + 1, tid = threadIdx.x, lane = tid & 31;
+  const int nwarp = blockDim.x >> 5;
+  const int b = blockIdx.x;
+  const int e0 = b * re, e1 = min(e0 + re, n);
+  const int nrows = e1 - e0 + 2;
+  const T h2 = a.h * a.h;
+  const T dt = MODE == 0 ? (T)(*a.dt) : T(0);
+  const T dtphi_c = MODE == 0 ? dt / a.phi_c : T(0);
+  CompSum<T> src;
+  const int ngroups = (nb + kQuadCols - 1) / kQuadCols;
+  for (int g = tid >> 5; g < ngroups; g += nwarp) {
+    const int ex = g * kQuadCols - 2 + lane;  // element column of this lane = its DOF column
+    const bool live = ex >= 0 && ex < n;
+    const int xc = live ? ex : 0;
+    T bx[3][3], dbx[3][3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      bx[i / 3][i % 3] = __ldg(a.ax.B + xc * 9 + i);
+      dbx[i / 3][i % 3] = __ldg(a.ax.dB + xc * 9 + i);
+    }
+    T gx[NS][3];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        gx[s][q] = s < a.n_src ? __ldg(a.ax.gsrc + ((size_t)(0 * kMaxSrc + s) * n + xc) * 3 + q) : T(0);
+    XRow<T> w0, w1, w2;
+    // K (or the nodal values) and phi at the element's lower and upper nodes
+    T k0[2] = {T(0), T(0)}, k1[2] = {T(0), T(0)}, f0[2] = {T(0), T(0)}, f1[2] = {T(0), T(0)};
+    if (MODE == 0) {
+      xrow_load(a, e0, xc, bx, dbx, w0);
+      xrow_load(a, e0 + 1, xc, bx, dbx, w1);
+      const T* Kr = a.K + (size_t)e0 * n1 + xc;
+      k0[0] = __ldg(Kr);
+      k0[1] = __ldg(Kr + 1);
+      if (a.phi) {
+        const T* Fr = a.phi + (size_t)e0 * n1 + xc;
+        f0[0] = __ldg(Fr);
+        f0[1] = __ldg(Fr + 1);
+      }
+    } else {
+      const T* Ur = a.nodal + (size_t)e0 * n1 + xc;
+      k0[0] = __ldg(Ur);
+      k0[1] = __ldg(Ur + 1);
+    }
+    T A0 = T(0), A1 = T(0), A2 = T(0);
+    for (int er = e0; er < e1; ++er) {
+      T by[3][3], dby[3][3];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        by[i / 3][i % 3] = __ldg(a.ax.B + er * 9 + i);
+        dby[i / 3][i % 3] = __ldg(a.ax.dB + er * 9 + i);
+      }
+      T loc[3][3];
+      if (MODE == 0) {
+        xrow_load(a, er + 2, xc, bx, dbx, w2);
+        const T* Kr = a.K + (size_t)(er + 1) * n1 + xc;
+        k1[0] = __ldg(Kr);
+        k1[1] = __ldg(Kr + 1);
+        if (a.phi) {
+          const T* Fr = a.phi + (size_t)(er + 1) * n1 + xc;
+          f1[0] = __ldg(Fr);
+          f1[1] = __ldg(Fr + 1);
+        }
+        T gy[NS][3];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            gy[s][q] = s < a.n_src ? __ldg(a.ax.gsrc + ((size_t)(1 * kMaxSrc + s) * n + er) * 3 + q) : T(0);
+        T T0[3][3], T1[3][3];  // [qy][a]: test functions along x applied
+        T esrc = T(0);  // tau/phi int q_g over the element (9 terms)
+#pragma unroll
+        for (int qy = 0; qy < 3; ++qy) {
+          const T eta = (T)gauss_x(qy);
+          T c0[3], cx[3], cy[3];
+#pragma unroll
+          for (int qx = 0; qx < 3; ++qx) {
+            const T xi = (T)gauss_x(qx);
+            const T Sv = by[0][qy] * w0.s[qx] + by[1][qy] * w1.s[qx] + by[2][qy] * w2.s[qx];
+            const T dpx = by[0][qy] * w0.pd[qx] + by[1][qy] * w1.pd[qx] + by[2][qy] * w2.pd[qx];
+            const T dpy = dby[0][qy] * w0.p[qx] + dby[1][qy] * w1.p[qx] + dby[2][qy] * w2.p[qx];
+            const T Kq = (T(1) - eta) * ((T(1) - xi) * k0[0] + xi * k0[1]) +
+                         eta * ((T(1) - xi) * k1[0] + xi * k1[1]);
+            T dtphi = dtphi_c;
+            if (a.phi) {
+              const T phq = (T(1) - eta) * ((T(1) - xi) * f0[0] + xi * f0[1]) +
+                            eta * ((T(1) - xi) * f1[0] + xi * f1[1]);
+              dtphi = dt / phq;
+            }
+            const T St = clamp01(Sv);
+            const T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
+            T qi = T(0), qp = T(0);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              const T gv = a.rate[s] * gx[s][qx] * gy[s][qy];
+              if (a.kind[s] == 0) qi += gv;
+              else qp += gv;
+            }
+            // the producer draws the mobile fraction f_g of the total rate
+            T qg = qi;
+            if (qp != T(0)) qg -= frac_div(lg, lg + lw) * qp;
+            const T w = (T)(gauss_w(qx) * gauss_w(qy)) * h2;
+            c0[qx] = w * (Sv + dtphi * qg);
+            const T cf = -w * dtphi * lg * Kq;
+            cx[qx] = cf * dpx;
+            cy[qx] = cf * (dpy + a.grav_term);
+            esrc += w * dtphi * qg;
+          }
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) {
+            T t0 = T(0), t1 = T(0);
+#pragma unroll
+            for (int qx = 0; qx < 3; ++qx) {
+              t0 += c0[qx] * bx[aa][qx] + cx[qx] * dbx[aa][qx];
+              t1 += cy[qx] * bx[aa][qx];
+            }
+            T0[qy][aa] = t0;
+            T1[qy][aa] = t1;
+          }
+        }
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) {
+            T v = T(0);
+#pragma unroll
+            for (int qy = 0; qy < 3; ++qy) v += by[bb][qy] * T0[qy][aa] + dby[bb][qy] * T1[qy][aa];
+            loc[bb][aa] = live ? v : T(0);
+          }
+        // lanes 0 and 1 recompute elements the previous group owns
+        if (live && lane >= 2) src.add(esrc);
+        w0 = w1;
+        w1 = w2;
+        k0[0] = k1[0];
+        k0[1] = k1[1];
+        f0[0] = f1[0];
+        f0[1] = f1[1];
+      } else {
+        const T* Ur = a.nodal + (size_t)(er + 1) * n1 + xc;
+        k1[0] = __ldg(Ur);
+        k1[1] = __ldg(Ur + 1);
+        T T0[3][3];
+#pragma unroll
+        for (int qy = 0; qy < 3; ++qy) {
+          const T eta = (T)gauss_x(qy);
+          T c0[3];
+#pragma unroll
+          for (int qx = 0; qx < 3; ++qx) {
+            const T xi = (T)gauss_x(qx);
+            const T uq = (T(1) - eta) * ((T(1) - xi) * k0[0] + xi * k0[1]) +
+                         eta * ((T(1) - xi) * k1[0] + xi * k1[1]);
+            c0[qx] = (T)(gauss_w(qx) * gauss_w(qy)) * h2 * uq;
+          }
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa)
+            T0[qy][aa] = c0[0] * bx[aa][0] + c0[1] * bx[aa][1] + c0[2] * bx[aa][2];
+        }
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) {
+            const T v = by[bb][0] * T0[0][aa] + by[bb][1] * T0[1][aa] + by[bb][2] * T0[2][aa];
+            loc[bb][aa] = live ? v : T(0);
+          }
+        k0[0] = k1[0];
+        k0[1] = k1[1];
+      }
+      // column sums across the warp: own first-column term + neighbours' terms
+      T col[3];
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        const T from1 = __shfl_up_sync(0xffffffffu, loc[bb][1], 1);
+        const T from2 = __shfl_up_sync(0xffffffffu, loc[bb][2], 2);
+        col[bb] = loc[bb][0] + from1 + from2;
+      }
+      A0 += col[0];
+      A1 += col[1];
+      A2 += col[2];
+      if (lane >= 2 && ex < nb) acc[(size_t)(er - e0) * nb + ex] = A0;
+      A0 = A1;
+      A1 = A2;
+      A2 = T(0);
+    }
+    if (lane >= 2 && ex < nb) {
+      acc[(size_t)(e1 - e0) * nb + ex] = A0;
+      acc[(size_t)(e1 - e0 + 1) * nb + ex] = A1;
+    }
+  }
+  __syncthreads();
+  sweep_lines_smem<T>(acc, nrows, nb, nb, xchunk, a.ax.l1, a.ax.l2, a.ax.dinv);
   const int own = e1 - e0;
-  for (int i = tid; i < nrows * nb; i += blockDim.x) {
-    int r = i / nb, k = i - r * nb;
-    if (r < own || e1 == n) Xm[(size_t)(e0 + r) * nb + k] = acc[i];
-    else Xs[((size_t)b * 2 + (r - own)) * nb + k] = acc[i];
+  for (int r = 0; r < nrows; ++r) {
+    T* dst = (r < own || e1 == n) ? Xm + (size_t)(e0 + r) * ldx : Xs + ((size_t)b * 2 + (r - own)) * ldx;
+    for (int k = tid; k < nb; k += blockDim.x) dst[k] = acc[(size_t)r * nb + k];
   }
   if (MODE == 0) {
-    double tot = block_sum(src, red);
+    const double tot = block_sum(src.value(), red);
     if (tid == 0) src_part[b] = tot;
   }
+}
+
+int quad_rows(int n, size_t esize) {
+  // strips of 4 element rows (two spill rows per 4) while two strips fit in
+  // one SM's shared memory, else 2
+  return (size_t)6 * (n + 2) * esize <= 110 * 1024 ? 4 : 2;
 }
 
 int quad_blocks(int dim, int n, int re) {
@@ -374,137 +565,283 @@ int quad_blocks(int dim, int n, int re) {
   return n * ((n + re - 1) / re);
 }
 
-template <typename T>
-cudaError_t launch_quad_xsolve(const QuadArgs<T>& a, int mode, int re, T* Xm, T* Xs,
-                               double* src_part, cudaStream_t st) {
-  if (a.dim != 2) return cudaErrorNotSupported;
-  int nblk = quad_blocks(2, a.n, re);
-  size_t smem = (size_t)(re + 2) * a.nb * sizeof(T);
-  if (mode == 0) {
-    auto k = k_quad_xsolve_2d<T, 0>;
+int sweep_ld(int n) { return ((n + 2 + 31) / 32) * 32; }
+
+static int xsweep_chunk(int nrows, int nb) {
+  int ch = 127;  // odd: the chunks of a row start in distinct shared-memory banks
+  while ((long)nrows * ((nb + ch - 1) / ch) > kQuadThreads) ch += 2;
+  return ch;
+}
+
+template <typename T, int MODE>
+static cudaError_t quad_launch(const QuadArgs<T>& a, int re, int xch, T* Xm, T* Xs, int ldx,
+                               double* src_part, size_t smem, cudaStream_t st) {
+  const int nblk = quad_blocks(2, a.n, re);
+  if (a.n_src <= 2) {
+    auto k = k_quad_xsweep_2d<T, MODE, 2>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<nblk, kQuadThreads, smem, st>>>(a, re, Xm, Xs, src_part);
+    k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
   } else {
-    auto k = k_quad_xsolve_2d<T, 1>;
+    auto k = k_quad_xsweep_2d<T, MODE, kMaxSrc>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<nblk, kQuadThreads, smem, st>>>(a, re, Xm, Xs, src_part);
+    k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
   }
   return cudaGetLastError();
 }
 
-// y sweep.  A CTA owns a block of CW columns: all nb rows of the block (and
-// the rows the strips spilled into it) are staged in shared memory with
-// asynchronous copies, the spill rows are added, one thread per column runs
-// the LDL^T forward/backward sweeps in shared memory (accumulating int S with
-// the basis integrals), and the block is written back.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ysolve_2d(int n, int re, int cw, T* X, const T* Xs,
-                                                   const T* l1, const T* l2, const T* dinv,
-                                                   const T* Iw, double* mass_part) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double red[32];
+cudaError_t launch_quad_xsweep(const QuadArgs<T>& a, int mode, int re, T* Xm, T* Xs, int ldx,
+                               double* src_part, cudaStream_t st) {
+  if (a.dim != 2 || re < 2) return cudaErrorNotSupported;
+  if (ldx < a.nb || (ldx * sizeof(T)) % 16 != 0) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(re + 2) * a.nb * sizeof(T);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const int xch = xsweep_chunk(re + 2, a.nb);
+  return mode == 0 ? quad_launch<T, 0>(a, re, xch, Xm, Xs, ldx, src_part, smem, st)
+                   : quad_launch<T, 1>(a, re, xch, Xm, Xs, ldx, src_part, smem, st);
+}
+
+// y sweep.  CTA (i, j) owns rows [M i, M i + M) of the CW columns from CW j.
+// Bulk tensor copies bring rows [M i - H, M i + M + H) of those columns of Xm
+// (zero outside the mesh) and the spill rows of Xs that fall among them into
+// shared memory; the spill rows are added, and thread c sweeps column c down
+// and up the tile (the halo rows start the chunked sweeps, see above).  The
+// owned rows go to `out` and their share of int S (basis integrals,
+// compensated sum) to mass_part.
+template <typename T>
+struct YTile;
+template <>
+struct YTile<float> {
+  static constexpr int CW = 128, M = 64;
+};
+template <>
+struct YTile<double> {
+  static constexpr int CW = 64, M = 64;
+};
+template <typename T>
+__host__ __device__ constexpr int ytile_rows() { return YTile<T>::M + 2 * SweepHalo<T>::H; }
+// spill rows a tile can meet: pairs at rows q re + {0, 1}
+static int yspill_rows(int rb, int re) { return 2 * ((rb + re - 1) / re + 2); }
+
+constexpr unsigned long long kCopyWaitNs = 1000000000ull;  // 1 s
+
+template <typename T>
+__global__ void __launch_bounds__(YTile<T>::CW)
+    k_ysweep_2d(const __grid_constant__ CUtensorMap xm_map, const __grid_constant__ CUtensorMap xs_map,
+                int n, int re, int nsp, int sb, T* __restrict__ out, const T* __restrict__ l1,
+                const T* __restrict__ l2, const T* __restrict__ dinv, const T* __restrict__ Iw,
+                double* mass_part, int* flags) {
+  constexpr int CW = YTile<T>::CW, M = YTile<T>::M, H = SweepHalo<T>::H, RB = ytile_rows<T>();
+  extern __shared__ __align__(1024) unsigned char ysm[];
+  T* tile = reinterpret_cast<T*>(ysm);  // [RB][CW]
+  T* stile = tile + RB * CW;              // [sb][CW] spill rows
+  T* fl1 = stile + (size_t)sb * CW;       // factor rows of the tile: l1, l2 [RB + 2], dinv, Iw [RB]
+  T* fl2 = fl1 + RB + 2;
+  T* fdi = fl2 + RB + 2;
+  T* fiw = fdi + RB;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(fiw + RB + ((8 / sizeof(T)) - 1)) ;
+  mbar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(mbar) + 7) & ~uintptr_t(7));
+  double* red = reinterpret_cast<double*>(mbar + 1);
+  const int nb = n + 2, tid = threadIdx.x;
+  const int s = blockIdx.x * M, e = min(nb, s + M), r0 = s - H;
+  const int L0 = max(r0, 0), L1 = min(r0 + RB, nb);
+  const int col = blockIdx.y * CW + tid;
+  // first spill pair touching [L0, L1): q re + 1 >= L0, q >= 1
+  const int qlo = max(1, (L0 - 1 + re - 1) / re);
+  const int y0 = 2 * (qlo - 1);
+  if (tid == 0) mbar_init_cta(mbar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_tx(mbar, (unsigned)((RB + (nsp > 0 ? sb : 0)) * CW * sizeof(T)));
+    tma_load_2d(tile, &xm_map, blockIdx.y * CW, r0, mbar);
+    if (nsp > 0) tma_load_2d(stile, &xs_map, blockIdx.y * CW, y0, mbar);
+  }
+  for (int i = tid; i < RB + 2; i += CW) {
+    const int l = r0 + i;
+    const bool in = l >= 0 && l < nb + 2;
+    fl1[i] = in ? __ldg(l1 + l) : T(0);
+    fl2[i] = in ? __ldg(l2 + l) : T(0);
+    if (i < RB) {
+      fdi[i] = (l >= 0 && l < nb) ? __ldg(dinv + l) : T(0);
+      fiw[i] = (l >= 0 && l < nb) ? __ldg(Iw + l) : T(0);
+    }
+  }
+  const bool ok = mbar_wait_for(mbar, 0, kCopyWaitNs);
+  if (__syncthreads_or(!ok)) {
+    // a copy did not land in time: record it, give it one more bounded wait
+    // so that it no longer writes into this CTA's shared memory, stop
+    if (tid == 0) atomicOr(flags, 8);
+    mbar_wait_for(mbar, 0, kCopyWaitNs);
+    return;
+  }
+  T* cp = tile + tid;  // column `col` of the tile, row stride CW
+  if (nsp > 0) {
+    // DOF row l = q re + j (j = 0, 1; q >= 1) also holds the part of the strip
+    // above it, Xs row 2 (q - 1) + j
+    for (int q = qlo; q * re < L1; ++q)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int l = q * re + j, r = 2 * (q - 1) + j;
+        if (l >= L0 && l < L1 && r < nsp) cp[(l - r0) * CW] += stile[(r - y0) * CW + tid];
+      }
+  }
+  const int ilo = L0 - r0, ihi = L1 - r0;
+  const int iown = e - r0;  // rows [H, iown) are owned
+  // sweeps in batches of 8 rows: loads first, then the recurrence in
+  // registers, then the stores (the tile and the factor rows share one
+  // shared array, so the compiler would not move loads above stores)
+  constexpr int U = 8;
+  T y1 = T(0), y2 = T(0);
+  int i = ilo;
+  for (; i + U <= ihi; i += U) {
+    T v[U], a1[U], a2[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      v[k] = cp[(i + k) * CW];
+      a1[k] = fl1[i + k];
+      a2[k] = fl2[i + k];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      v[k] = v[k] - a1[k] * y1 - a2[k] * y2;
+      y2 = y1;
+      y1 = v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) cp[(i + k) * CW] = v[k];
+  }
+  for (; i < ihi; ++i) {
+    const T y = cp[i * CW] - fl1[i] * y1 - fl2[i] * y2;
+    cp[i * CW] = y;
+    y2 = y1;
+    y1 = y;
+  }
+  T x1 = T(0), x2 = T(0);
+  CompSum<T> mass;
+  i = ihi - 1;
+  for (; i - U + 1 >= H; i -= U) {
+    T v[U], dd[U], a1[U], a2[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      v[k] = cp[(i - k) * CW];
+      dd[k] = fdi[i - k];
+      a1[k] = fl1[i - k + 1];
+      a2[k] = fl2[i - k + 2];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      v[k] = v[k] * dd[k] - a1[k] * x1 - a2[k] * x2;
+      x2 = x1;
+      x1 = v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      cp[(i - k) * CW] = v[k];
+      if (i - k < iown) mass.add(v[k] * fiw[i - k]);
+    }
+  }
+  for (; i >= H; --i) {
+    const T x = cp[i * CW] * fdi[i] - fl1[i + 1] * x1 - fl2[i + 2] * x2;
+    cp[i * CW] = x;
+    if (i < iown) mass.add(x * fiw[i]);
+    x2 = x1;
+    x1 = x;
+  }
+  double mcol = 0.0;
+  if (col < nb) {
+    for (int i = H; i < iown; ++i) out[(size_t)(r0 + i) * nb + col] = cp[i * CW];
+    mcol = mass.value() * (double)__ldg(Iw + col);
+  }
+  const double tot = block_sum(mcol, red);
+  if (tid == 0) mass_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+template <typename T>
+static size_t ysweep_smem(int sb) {
+  constexpr int RB = ytile_rows<T>();
+  return sizeof(T) * ((size_t)(RB + sb) * YTile<T>::CW + 4 * (size_t)RB + 4) + 16 + 32 * sizeof(double);
+}
+
+template <typename T>
+static void ysweep_grid(int n, int* gx, int* gy) {
   const int nb = n + 2;
-  const int nstrip = (n + re - 1) / re;
-  const int nsp = 2 * (nstrip - 1);      // spill rows
-  T* xs = reinterpret_cast<T*>(smraw);    // [nb][cw]
-  T* ss = xs + (size_t)nb * cw;           // [nsp][cw]
-  T* f1 = ss + (size_t)nsp * cw;          // l1 [nb+2]
-  T* f2 = f1 + nb + 2;                    // l2 [nb+2]
-  T* fd = f2 + nb + 2;                    // dinv [nb]
-  T* fi = fd + nb;                        // Iw [nb]
-  const int k0 = blockIdx.x * cw;
-  const int ncw = min(cw, nb - k0);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < nb * cw; e += blockDim.x) {
-    const int l = e / cw, c = e % cw;
-    if (c < ncw) cp_async_elem(&xs[e], &X[(size_t)l * nb + k0 + c]);
-  }
-  for (int e = tid; e < nsp * cw; e += blockDim.x) {
-    const int r = e / cw, c = e % cw;
-    if (c < ncw) cp_async_elem(&ss[e], &Xs[(size_t)r * nb + k0 + c]);
-  }
-  for (int e = tid; e < nb + 2; e += blockDim.x) {
-    cp_async_elem(&f1[e], &l1[e]);
-    cp_async_elem(&f2[e], &l2[e]);
-    if (e < nb) {
-      cp_async_elem(&fd[e], &dinv[e]);
-      cp_async_elem(&fi[e], &Iw[e]);
-    }
-  }
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncthreads();
-  // spill row r = 2*(b'-... ) holds row (b+1)*re + (r % 2) of strip b = r / 2
-  for (int e = tid; e < nsp * cw; e += blockDim.x) {
-    const int r = e / cw, c = e % cw;
-    const int l = (r / 2 + 1) * re + (r % 2);
-    if (c < ncw && l < nb) xs[l * cw + c] += ss[e];
-  }
-  __syncthreads();
-  double mass = 0.0;
-  const int c = tid;
-  if (c < ncw) {
-    T ym1 = T(0), ym2 = T(0);
-    for (int l = 0; l < nb; ++l) {
-      T y = xs[l * cw + c] - f1[l] * ym1 - f2[l] * ym2;
-      xs[l * cw + c] = y;
-      ym2 = ym1;
-      ym1 = y;
-    }
-    T xp1 = T(0), xp2 = T(0);
-    for (int l = nb - 1; l >= 0; --l) {
-      T v = xs[l * cw + c] * fd[l] - f1[l + 1] * xp1 - f2[l + 2] * xp2;
-      xs[l * cw + c] = v;
-      mass += (double)v * (double)fi[l];
-      xp2 = xp1;
-      xp1 = v;
-    }
-    mass *= (double)fi[k0 + c];
-  }
-  __syncthreads();
-  for (int e = tid; e < nb * cw; e += blockDim.x) {
-    const int l = e / cw, cc = e % cw;
-    if (cc < ncw) X[(size_t)l * nb + k0 + cc] = xs[e];
-  }
-  double tot = block_sum(mass, red);
-  if (tid == 0) mass_part[blockIdx.x] = tot;
-}
-
-static int ysolve_cw(int n, int re, size_t esize) {
-  const int nb = n + 2, nstrip = (n + re - 1) / re, nsp = 2 * (nstrip - 1);
-  int cw = 32;
-  while (cw > 1 && esize * ((size_t)(nb + nsp) * cw + 4 * (size_t)nb + 8) > 200 * 1024) cw /= 2;
-  return cw;
-}
-
-static size_t ysolve_smem(int n, int re, int cw, size_t esize) {
-  const int nb = n + 2, nstrip = (n + re - 1) / re, nsp = 2 * (nstrip - 1);
-  return esize * ((size_t)(nb + nsp) * cw + 4 * (size_t)nb + 8);
+  *gx = (nb + YTile<T>::M - 1) / YTile<T>::M;
+  *gy = (nb + YTile<T>::CW - 1) / YTile<T>::CW;
 }
 
 int ysolve_blocks(int dim, int n) {
-  // the column block width depends on the element size; size the partial
-  // buffer for the narrowest (FP64) blocks
-  int nb = n + 2;
-  int cw = ysolve_cw(n, 2, 8);
-  if (dim == 2) return (nb + cw - 1) / cw;
-  return (nb * nb + 127) / 128;
+  if (dim != 2) return ((n + 2) * (n + 2) + 127) / 128;
+  int a, b, c, d;
+  ysweep_grid<float>(n, &a, &b);
+  ysweep_grid<double>(n, &c, &d);
+  return a * b > c * d ? a * b : c * d;
+}
+
+// cuTensorMapEncodeTiled, taken from the driver at run time
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// row-major [rows][cols] array with row stride ld (elements), boxes of
+// box_rows x box_cols, zero fill outside
+template <typename T>
+static cudaError_t tile_map(const T* base, int rows, int cols, int ld, int box_rows, int box_cols,
+                            CUtensorMap* map) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(T)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  if (enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+          2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t launch_ysolve(const QuadArgs<T>& a, int re, T* X, const T* Xs, double* mass_part,
-                          cudaStream_t st) {
-  if (a.dim != 2) return cudaErrorNotSupported;
-  int cw = ysolve_cw(a.n, re, sizeof(T));
-  size_t smem = ysolve_smem(a.n, re, cw, sizeof(T));
-  if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  auto k = k_ysolve_2d<T>;
+cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs, int ldx, T* out,
+                          double* mass_part, int* flags, cudaStream_t st) {
+  if (a.dim != 2 || re < 2) return cudaErrorNotSupported;
+  if (ldx < a.nb || (ldx * sizeof(T)) % 16 != 0 || (reinterpret_cast<uintptr_t>(Xm) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(Xs) & 15) != 0)
+    return cudaErrorInvalidValue;
+  constexpr int RB = ytile_rows<T>(), CW = YTile<T>::CW;
+  const int nb = a.nb;
+  const int nstrip = (a.n + re - 1) / re, nsp = 2 * (nstrip - 1);
+  const int sb = yspill_rows(RB, re);
+  if (sb > 256) return cudaErrorInvalidValue;
+  CUtensorMap xm_map, xs_map;
+  cudaError_t err = tile_map<T>(Xm, nb, nb, ldx, RB, CW, &xm_map);
+  if (err != cudaSuccess) return err;
+  if (nsp > 0) err = tile_map<T>(Xs, nsp, nb, ldx, sb, CW, &xs_map);
+  else xs_map = xm_map;  // not read
+  if (err != cudaSuccess) return err;
+  int gx, gy;
+  ysweep_grid<T>(a.n, &gx, &gy);
+  const size_t smem = ysweep_smem<T>(sb);
+  auto k = k_ysweep_2d<T>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int nblk = (a.nb + cw - 1) / cw;
-  k<<<nblk, 256, smem, st>>>(a.n, re, cw, X, Xs, a.ax.l1, a.ax.l2, a.ax.dinv, a.ax.Iw, mass_part);
-  // unused partial slots of a wider block layout stay zero
-  int nmax = ysolve_blocks(2, a.n);
-  if (nblk < nmax) cudaMemsetAsync(mass_part + nblk, 0, sizeof(double) * (nmax - nblk), st);
+  k<<<dim3(gx, gy), CW, smem, st>>>(xm_map, xs_map, a.n, re, nsp, sb, out, a.ax.l1, a.ax.l2,
+                                    a.ax.dinv, a.ax.Iw, mass_part, flags);
+  // unused partial slots of the other precision's (larger) grid stay zero
+  const int nmax = ysolve_blocks(2, a.n);
+  if (gx * gy < nmax) cudaMemsetAsync(mass_part + gx * gy, 0, sizeof(double) * (nmax - gx * gy), st);
   return cudaGetLastError();
 }
 
@@ -539,16 +876,18 @@ cudaError_t launch_mass(const QuadArgs<T>& a, const T* S, double* mass_part, cud
 }
 
 // stats[0] = int S, stats[1] += step mass error, stats[2] += source integral
-__global__ void k_mass_finalize(const double* mp, int nm, const double* sp, int ns, int mode,
-                                double* stats, int* flags) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double m = 0.0;
-  for (int i = 0; i < nm; ++i) m += mp[i];
+__global__ void __launch_bounds__(256) k_mass_finalize(const double* mp, int nm, const double* sp,
+                                                       int ns, int mode, double* stats, int* flags) {
+  __shared__ double red[32];
+  double m = 0.0, s = 0.0;
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) m += mp[i];
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) s += sp[i];
+  m = block_sum(m, red);
+  s = block_sum(s, red);
+  if (threadIdx.x != 0) return;
   if (mode == 0) {
     stats[0] = m;
   } else {
-    double s = 0.0;
-    for (int i = 0; i < ns; ++i) s += sp[i];
     stats[1] += m - stats[0] - s;
     stats[2] += s;
     stats[0] = m;
@@ -558,7 +897,7 @@ __global__ void k_mass_finalize(const double* mp, int nm, const double* sp, int 
 
 cudaError_t launch_mass_finalize(const double* mass_part, int nmass, const double* src_part,
                                  int nsrc, int mode, double* stats, int* flags, cudaStream_t st) {
-  k_mass_finalize<<<1, 32, 0, st>>>(mass_part, nmass, src_part, nsrc, mode, stats, flags);
+  k_mass_finalize<<<1, 256, 0, st>>>(mass_part, nmass, src_part, nsrc, mode, stats, flags);
   return cudaGetLastError();
 }
 
@@ -653,10 +992,10 @@ cudaError_t launch_cfl_finalize(const double* part, int nblk, double cfl, double
 }
 
 #define ADS_INST(T)                                                                              \
-  template cudaError_t launch_quad_xsolve<T>(const QuadArgs<T>&, int, int, T*, T*, double*,      \
+  template cudaError_t launch_quad_xsweep<T>(const QuadArgs<T>&, int, int, T*, T*, int, double*, \
                                              cudaStream_t);                                      \
-  template cudaError_t launch_ysolve<T>(const QuadArgs<T>&, int, T*, const T*, double*,          \
-                                        cudaStream_t);                                           \
+  template cudaError_t launch_ysweep<T>(const QuadArgs<T>&, int, const T*, const T*, int, T*,    \
+                                        double*, int*, cudaStream_t);                            \
   template cudaError_t launch_zsolve<T>(const QuadArgs<T>&, T*, double*, cudaStream_t);          \
   template cudaError_t launch_mass<T>(const QuadArgs<T>&, const T*, double*, cudaStream_t);      \
   template cudaError_t launch_cfl<T>(const QuadArgs<T>&, double*, cudaStream_t);

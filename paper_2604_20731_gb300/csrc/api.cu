@@ -50,12 +50,12 @@ struct ads_ctx {
   void *B = nullptr, *dB = nullptr, *l1 = nullptr, *l2 = nullptr, *dinv = nullptr, *Iw = nullptr,
        *gsrc = nullptr, *gnode = nullptr;
   void *S[2] = {nullptr, nullptr}, *P = nullptr, *K = nullptr, *phi = nullptr, *Xs = nullptr,
-       *nodal = nullptr;
+       *Xm = nullptr, *nodal = nullptr;
   int cur = 0;
   double *src_part = nullptr, *mass_part = nullptr, *cfl_part = nullptr, *stats = nullptr,
          *dt = nullptr, *scal = nullptr;
   int* flags = nullptr;
-  int re = 4, nquad = 0, nys = 0, ncfl = 0;
+  int re = 4, nquad = 0, nys = 0, ncfl = 0, ldx = 0;  // ldx: row stride of Xm / Xs (2D)
   // CRVPINN (network precision)
   void *alpha = nullptr, *f = nullptr, *u = nullptr, *res = nullptr, *rhat = nullptr, *z = nullptr,
        *gu = nullptr, *Sdst = nullptr, *invd = nullptr, *theta = nullptr, *am = nullptr,
@@ -197,8 +197,10 @@ ads_status enq_sat_steps(ads_ctx* c, int n_sub) {
       LK(0, launch_quad3d<TA>(a, 0, (TA*)c->Xs, (TA*)out, c->src_part, c->stream));
       LK(1, launch_solve3d<TA>(a, (TA*)out, c->mass_part, c->stream));
     } else {
-      LK(0, launch_quad_xsolve<TA>(a, 0, c->re, (TA*)out, (TA*)c->Xs, c->src_part, c->stream));
-      LK(1, launch_ysolve<TA>(a, c->re, (TA*)out, (const TA*)c->Xs, c->mass_part, c->stream));
+      LK(0, launch_quad_xsweep<TA>(a, 0, c->re, (TA*)c->Xm, (TA*)c->Xs, c->ldx, c->src_part,
+                                   c->stream));
+      LK(1, launch_ysweep<TA>(a, c->re, (const TA*)c->Xm, (const TA*)c->Xs, c->ldx, (TA*)out,
+                              c->mass_part, c->flags, c->stream));
     }
     LK(2, launch_mass_finalize(c->mass_part, c->nys, c->src_part, c->nquad, 1, c->stats, c->flags,
                                c->stream));
@@ -354,8 +356,9 @@ ads_status enq_project(ads_ctx* c) {
     CK(launch_quad3d<TA>(a, 1, (TA*)c->Xs, (TA*)c->P, c->src_part, c->stream));
     CK(launch_solve3d<TA>(a, (TA*)c->P, nullptr, c->stream));
   } else {
-    CK(launch_quad_xsolve<TA>(a, 1, c->re, (TA*)c->P, (TA*)c->Xs, c->src_part, c->stream));
-    CK(launch_ysolve<TA>(a, c->re, (TA*)c->P, (const TA*)c->Xs, c->mass_part, c->stream));
+    CK(launch_quad_xsweep<TA>(a, 1, c->re, (TA*)c->Xm, (TA*)c->Xs, c->ldx, c->src_part, c->stream));
+    CK(launch_ysweep<TA>(a, c->re, (const TA*)c->Xm, (const TA*)c->Xs, c->ldx, (TA*)c->P,
+                         c->mass_part, c->flags, c->stream));
   }
   c->nlaunch += 4;
   return ADS_OK;
@@ -534,6 +537,8 @@ ads_status validate(const ads_params* p, const crvpinn_params* cp) {
   if (!p) return ADS_ERR_INVALID_ARG;
   if (p->dim != 2 && p->dim != 3) return ADS_ERR_UNSUPPORTED;
   if (p->n < 2 || p->n > (p->dim == 3 ? 512 : 8192)) return ADS_ERR_INVALID_ARG;
+  // 2D FP64: four rows of n + 2 doubles per strip must fit in shared memory
+  if (p->dim == 2 && p->ads_dtype == ADS_F64 && p->n > 7168) return ADS_ERR_INVALID_ARG;
   if (!(p->phi > 0) || !(p->mu_w > 0) || !(p->mu_g > 0)) return ADS_ERR_INVALID_ARG;
   if (!(p->grav >= 0) || !std::isfinite(p->grav) || !std::isfinite(p->grav_sign)) return ADS_ERR_INVALID_ARG;
   if (p->n_src < 0 || p->n_src > ADS_MAX_SOURCES) return ADS_ERR_INVALID_ARG;
@@ -570,7 +575,7 @@ size_t estimate(const ads_params* p, const crvpinn_params* cp) {
   b += ta * (18 * n + 3 * (n + 4) + 2 * nb + 3 * kMaxSrc * (3 * n + n1));
   b += ta * (3 * nc + 2 * nn);  // S (2), P, K, nodal (phi optional)
   if (d == 3) b += ta * n * n * n * 27;           // per-element contributions
-  else b += ta * 2 * ((n + 1) / 2) * nb;          // spill rows
+  else b += ta * (nb + 2 * ((n + 1) / 2)) * (size_t)sweep_ld((int)n);  // x-swept rows + spill rows
   b += 8 * 4 * (nb * nb + 1024);                  // partial sums
   if (cp) {
     const size_t tc = cp->dtype == ADS_BF16 ? 4 : tsize(cp->dtype);
@@ -803,7 +808,8 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   if (phi_nodal) {
     ALV(c->phi, ta * nn);
   }
-  c->re = (n + 3) / 4 < 152 ? 2 : 4;  // strips of 2 element rows on small meshes
+  c->re = quad_rows(n, ta);
+  c->ldx = sweep_ld(n);
   c->nquad = c->dim == 3 ? quad3d_blocks(n) : quad_blocks(c->dim, n, c->re);
   c->nys = c->dim == 3 ? zsolve3d_blocks(n) : ysolve_blocks(c->dim, n);
   c->ncfl = cfl_blocks(c->dim, n);
@@ -811,7 +817,8 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
   if (c->dim == 3) {
     ALV(c->Xs, elem3d_scratch(n, ta));
   } else {
-    ALV(c->Xs, ta * 2 * (size_t)c->nquad * nb);
+    ALV(c->Xs, ta * 2 * (size_t)c->nquad * c->ldx);
+    ALV(c->Xm, ta * (size_t)nb * c->ldx);
   }
   AL(c->src_part, (size_t)c->nquad + 1);
   AL(c->mass_part, (size_t)c->nys + 1);
@@ -1075,7 +1082,7 @@ static ads_status hybrid_stats_read(ads_ctx* c, hybrid_stats* out) {
   out->mass_total = m3[0];
   int fl = 0;
   CA(read_flags(c, &fl));
-  if (fl & 8) return fail(c, ADS_ERR_TIMEOUT, "a tensor-core wait timed out on the device");
+  if (fl & 8) return fail(c, ADS_ERR_TIMEOUT, "a bounded device wait (tensor core or bulk copy) timed out");
   if (fl != 0 || !std::isfinite(v[0]) || !std::isfinite(v[1]))
     return fail(c, ADS_ERR_NONFINITE, "non-finite loss, step size or mass");
   return ADS_OK;

@@ -98,4 +98,69 @@ ADS_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 ADS_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 ADS_D void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// ---- bulk tensor copies (TMA) with bounded mbarrier waits ----
+ADS_D unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+ADS_D void mbar_init_cta(uint64_t* mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// arrive once and announce `bytes` of bulk-copy traffic on the barrier
+ADS_D void mbar_arrive_tx(uint64_t* mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+// wait for phase `parity`; false after `limit_ns` nanoseconds without it
+ADS_D bool mbar_wait_for(uint64_t* mbar, unsigned parity, unsigned long long limit_ns) {
+  const unsigned a = smem_addr(mbar);
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it == 0) t0 = gtimer_ns();
+    else if (gtimer_ns() - t0 > limit_ns) return false;
+  }
+}
+// 2D tile load: box at element coordinates (x, y) of the tensor map into
+// shared memory, completing on `mbar`.  x must be a multiple of 16 bytes'
+// worth of elements; y may be negative (rows outside the tensor read as 0).
+ADS_D void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(smem_dst)),
+      "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// Compensated (Kahan) running sum.  FP32 sums whose small terms matter (the
+// mass and source integrals) use it instead of an FP64 accumulator: FP64
+// arithmetic on this GPU runs at a small fraction of the FP32 rate.
+template <typename T>
+struct CompSum {
+  T s = T(0), c = T(0);
+  ADS_D void add(T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  ADS_D double value() const { return (double)s - (double)c; }
+};
+template <>
+struct CompSum<double> {
+  double s = 0.0;
+  ADS_D void add(double v) { s += v; }
+  ADS_D double value() const { return s; }
+};
+
 }  // namespace adsgb

@@ -54,19 +54,24 @@ cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream
 // ---- saturation step ----
 // Fused quadrature (MODE 0: saturation RHS of Eq. 10b; MODE 1: L2
 // projection RHS of nodal values) + x-direction mass solve for a strip of
-// `re` element rows.  Rows shared with the next strip go to `Xs`.
+// `re` (>= 2) element rows.  Rows owned by the strip go to Xm, the two rows
+// it shares with the next strip to Xs (both with row stride ldx, a multiple
+// of 16 bytes; ldx >= n + 2).
 template <typename T>
-cudaError_t launch_quad_xsolve(const QuadArgs<T>& a, int mode, int re, T* Xm, T* Xs,
+cudaError_t launch_quad_xsweep(const QuadArgs<T>& a, int mode, int re, T* Xm, T* Xs, int ldx,
                                double* src_part, cudaStream_t st);
-// y-direction (and z in 3D) sweep adding the spill rows; writes the solution
-// over Xm and per-block partials of int S.
+// y-direction sweep of Xm plus the spill rows Xs into `out` (row stride n+2),
+// with per-block partials of int S; sets bit 8 of flags if a bulk copy wait
+// timed out.
 template <typename T>
-cudaError_t launch_ysolve(const QuadArgs<T>& a, int re, T* X, const T* Xs, double* mass_part,
-                          cudaStream_t st);
+cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs, int ldx, T* out,
+                          double* mass_part, int* flags, cudaStream_t st);
 template <typename T>
 cudaError_t launch_zsolve(const QuadArgs<T>& a, T* X, double* mass_part, cudaStream_t st);
+int quad_rows(int n, size_t esize);  // element rows per strip of the 2D quadrature
 int quad_blocks(int dim, int n, int re);
 int ysolve_blocks(int dim, int n);
+int sweep_ld(int n);  // row stride of the 2D sweep intermediates
 // mass bookkeeping: mode 0 = set int S from partials; mode 1 = step update
 cudaError_t launch_mass_finalize(const double* mass_part, int nmass, const double* src_part,
                                  int nsrc, int mode, double* stats, int* flags, cudaStream_t st);

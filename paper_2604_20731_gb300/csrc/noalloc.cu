@@ -50,12 +50,16 @@ struct SrcVals {
   double dt;
 };
 
-// writes the sources' centres/widths and the step size into the scratch
-__global__ void k_noalloc_put(SrcVals v, double* cen, double* sig, double* dt) {
+// writes the sources' centres/widths and the step size into the scratch and
+// clears the device status word
+__global__ void k_noalloc_put(SrcVals v, double* cen, double* sig, double* dt, int* flags) {
   int t = threadIdx.x;
   if (t < 3 * kMaxSrc) cen[t] = v.cen[t];
   if (t < kMaxSrc) sig[t] = v.sig[t];
-  if (t == 0) *dt = v.dt;
+  if (t == 0) {
+    *dt = v.dt;
+    *flags = 0;
+  }
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -88,6 +92,7 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
   const int n = p->n, nb = n + 2;
   const int nquad = quad_blocks(2, n, kStripRows);
   const int nys = ysolve_blocks(2, n);
+  const int ldx = sweep_ld(n);
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ADS_ERR_CUDA;
@@ -107,7 +112,9 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
   double* cen = cv.take(3 * kMaxSrc);
   double* sig = cv.take(kMaxSrc);
   double* dtp = cv.take(1);
-  double* Xs = cv.take(2 * (size_t)nquad * nb);
+  double* Xs = cv.take(2 * (size_t)nquad * ldx);
+  double* Xm = cv.take((size_t)nb * ldx);
+  int* flags = reinterpret_cast<int*>(cv.take(1));
   double* src_part = cv.take((size_t)nquad);
   double* mass_part = cv.take((size_t)nys);
   if (cv.off > kScratchBytes) return ADS_ERR_INVALID_ARG;  // cannot happen for n <= kMaxN
@@ -120,7 +127,7 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
     v.sig[s] = p->src[s].sigma;
   }
   v.dt = dt;
-  k_noalloc_put<<<1, 32, 0, st>>>(v, cen, sig, dtp);
+  k_noalloc_put<<<1, 32, 0, st>>>(v, cen, sig, dtp, flags);
   // every table, spill row and partial below is fully rewritten before it is
   // read, so nothing in the shared array has to start at zero
   if (launch_axis_init(n, cen, sig, p->n_src, B, dB, l1, l2, dinv, Iw, gsrc, gnode, tmp, st) !=
@@ -156,9 +163,10 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
   a.grav_term = p->grav_sign * p->rho_g * p->grav;
   a.kz = p->kz_ratio;
   a.dt = dtp;
-  if (launch_quad_xsolve<double>(a, 0, kStripRows, d_S_out, Xs, src_part, st) != cudaSuccess)
+  if (launch_quad_xsweep<double>(a, 0, kStripRows, Xm, Xs, ldx, src_part, st) != cudaSuccess)
     return ADS_ERR_CUDA;
-  if (launch_ysolve<double>(a, kStripRows, d_S_out, Xs, mass_part, st) != cudaSuccess)
+  if (launch_ysweep<double>(a, kStripRows, Xm, Xs, ldx, d_S_out, mass_part, flags, st) !=
+      cudaSuccess)
     return ADS_ERR_CUDA;
   return ADS_OK;
 }

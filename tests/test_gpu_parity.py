@@ -82,6 +82,35 @@ def test_saturation_step_fp32(n):
     s.close()
 
 
+@pytest.mark.parametrize("n,dtype,tol", [(600, "f64", 1e-12), (2, "f64", 1e-12), (700, "f32", 1e-5)])
+def test_saturation_step_four_wells(n, dtype, tol):
+    """More than two sources (the general source path of the quadrature) on
+    meshes whose lines the sweeps split into several chunks."""
+    sc = _scenario(n, seed=n + 11, grav=0.4)
+    sc.sources = [
+        scn.Source(center=(0.2, 0.3), rate=1.3, kind=scn.SRC_INJECT),
+        scn.Source(center=(0.7, 0.25), rate=0.6, sigma=0.05, kind=scn.SRC_INJECT),
+        scn.Source(center=(0.8, 0.8), rate=1.1, kind=scn.SRC_PRODUCE),
+        scn.Source(center=(0.3, 0.75), rate=0.8, sigma=0.04, kind=scn.SRC_PRODUCE),
+    ]
+    P = np.random.default_rng(n).normal(size=(n + 2, n + 2))
+    dt = 2e-4
+    s = solver(sc, width=None, ads_dtype=dtype)
+    s.set_pressure(P)
+    # FP32: one step (the random pressure makes a second step ill-conditioned:
+    # |S| grows to ~1e4 and FP32 rounding of the first step is amplified)
+    steps = 2 if dtype == "f64" else 1
+    s.saturation_step(dt, steps)
+    a = AdsOracle(sc)
+    ref = sc.S0
+    for _ in range(steps):
+        ref = a.step(ref, P, dt)
+    assert rel_inf(s.get("S"), ref) <= tol
+    mass = s.get("MASS")
+    assert mass[0] == pytest.approx(a.mesh.integral(ref), rel=1e-12 if dtype == "f64" else 1e-6)
+    s.close()
+
+
 def test_ten_steps_and_mass_balance_fp64():
     n = 48
     sc = _scenario(n, seed=9, grav=0.3)
