@@ -113,9 +113,9 @@ SIGNATURES = {
     "ads_status_str": (C.c_char_p, [C.c_int]),
 }
 
-TRAIN_KERNELS = ["mlp_fwd", "residual", "dst_gemm", "tridiag", "idst_gemm_loss",
+TRAIN_KERNELS = ["mlp_fwd", "residual", "gram_x", "gram_y", "gram_x_loss",
                  "adjoint_loss_finalize", "mlp_bwd", "grad_adam"]
-SAT_KERNELS = ["quad_xsolve", "ysolve", "mass_finalize"]
+SAT_KERNELS = ["quad_xsweep", "ysweep", "mass_finalize"]
 
 _lib = None
 

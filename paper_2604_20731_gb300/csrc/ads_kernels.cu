@@ -579,11 +579,11 @@ static cudaError_t quad_launch(const QuadArgs<T>& a, int re, int xch, T* Xm, T* 
   const int nblk = quad_blocks(2, a.n, re);
   if (a.n_src <= 2) {
     auto k = k_quad_xsweep_2d<T, MODE, 2>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
   } else {
     auto k = k_quad_xsweep_2d<T, MODE, kMaxSrc>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
   }
   return cudaGetLastError();
@@ -769,6 +769,13 @@ static void ysweep_grid(int n, int* gx, int* gy) {
   *gy = (nb + YTile<T>::CW - 1) / YTile<T>::CW;
 }
 
+int ysweep_blocks(int n, size_t esize) {
+  int gx, gy;
+  if (esize == sizeof(float)) ysweep_grid<float>(n, &gx, &gy);
+  else ysweep_grid<double>(n, &gx, &gy);
+  return gx * gy;
+}
+
 int ysolve_blocks(int dim, int n) {
   if (dim != 2) return ((n + 2) * (n + 2) + 127) / 128;
   int a, b, c, d;
@@ -836,12 +843,9 @@ cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs
   ysweep_grid<T>(a.n, &gx, &gy);
   const size_t smem = ysweep_smem<T>(sb);
   auto k = k_ysweep_2d<T>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<dim3(gx, gy), CW, smem, st>>>(xm_map, xs_map, a.n, re, nsp, sb, out, a.ax.l1, a.ax.l2,
                                     a.ax.dinv, a.ax.Iw, mass_part, flags);
-  // unused partial slots of the other precision's (larger) grid stay zero
-  const int nmax = ysolve_blocks(2, a.n);
-  if (gx * gy < nmax) cudaMemsetAsync(mass_part + gx * gy, 0, sizeof(double) * (nmax - gx * gy), st);
   return cudaGetLastError();
 }
 

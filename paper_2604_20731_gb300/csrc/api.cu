@@ -58,11 +58,13 @@ struct ads_ctx {
   int re = 4, nquad = 0, nys = 0, ncfl = 0, ldx = 0;  // ldx: row stride of Xm / Xs (2D)
   // CRVPINN (network precision)
   void *alpha = nullptr, *f = nullptr, *u = nullptr, *res = nullptr, *rhat = nullptr, *z = nullptr,
-       *gu = nullptr, *Sdst = nullptr, *invd = nullptr, *theta = nullptr, *am = nullptr,
+       *gu = nullptr, *Sdst = nullptr, *invd = nullptr, *gtw = nullptr, *glam = nullptr,
+       *theta = nullptr, *am = nullptr,
        *av = nullptr, *grad = nullptr, *gpart = nullptr, *acts = nullptr;
   double *dot_part = nullptr, *loss = nullptr, *loss_log = nullptr, *bc = nullptr, *lr = nullptr;
   int* t = nullptr;
   int ndot = 0, nbwd = 0, ld = 0;
+  bool gram_fft = false;  // 2D, N a power of two: Gram solve by FFT sine transforms
   // host staging (pinned)
   double* h_stage = nullptr;
   size_t h_stage_count = 0;
@@ -202,7 +204,8 @@ ads_status enq_sat_steps(ads_ctx* c, int n_sub) {
       LK(1, launch_ysweep<TA>(a, c->re, (const TA*)c->Xm, (const TA*)c->Xs, c->ldx, (TA*)out,
                               c->mass_part, c->flags, c->stream));
     }
-    LK(2, launch_mass_finalize(c->mass_part, c->nys, c->src_part, c->nquad, 1, c->stats, c->flags,
+    const int nmass = c->dim == 3 ? c->nys : ysweep_blocks(c->n, sizeof(TA));
+    LK(2, launch_mass_finalize(c->mass_part, nmass, c->src_part, c->nquad, 1, c->stats, c->flags,
                                c->stream));
     c->cur = 1 - c->cur;
   }
@@ -330,6 +333,11 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
     LK(4, launch_gemm<TC>(m * m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
                           h * h, (const TC*)c->res, c->dot_part, c->stream));
     c->nlaunch += 2;
+  } else if (c->gram_fft) {
+    for (int pass = 0; pass < 3; ++pass)
+      LK(2 + pass, launch_gram_fft<TC>(pass, c->N, (const TC*)c->res, (TC*)c->rhat, (TC*)c->z,
+                                       (const TC*)c->gtw, (const TC*)c->glam, h * h, c->dot_part,
+                                       c->stream));
   } else {
     LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
                           TC(1), nullptr, nullptr, c->stream));
@@ -337,7 +345,9 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
     LK(4, launch_gemm<TC>(m, m, m, (const TC*)c->rhat, m, (const TC*)c->Sdst, m, (TC*)c->z, m,
                           h * h, (const TC*)c->res, c->dot_part, c->stream));
   }
-  LossFin lf{c->dot_part, c->dim == 3 ? gemm_blocks(m * m, m) : gemm_blocks(m, m), c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
+  const int nparts = c->dim == 3 ? gemm_blocks(m * m, m)
+                                 : (c->gram_fft ? gram_fft_dot_parts(c->N) : gemm_blocks(m, m));
+  LossFin lf{c->dot_part, nparts, c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
   LK(5, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
                            nullptr, TC(0), TC(2), (TC*)c->gu, &lf, c->stream));
   LK(6, launch_bwd<TC>(c));
@@ -869,22 +879,36 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     } else {
       ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
     }
-    double *S64 = nullptr, *inv64 = nullptr;
-    const size_t npiv = (size_t)m * m * (c->dim == 3 ? m : 1);
-    AL(S64, (size_t)m * m);
-    AL(inv64, npiv);
-    if (launch_gram_init(c->dim, c->N, S64, inv64, c->stream) != cudaSuccess)
-      return bail(fail(c, ADS_ERR_CUDA, "gram init"));
-    if (c->tc == ADS_F64) {
-      c->Sdst = S64;
-      c->invd = inv64;
+    c->gram_fft = gram_fft_supported(c->dim, c->N);
+    if (c->gram_fft) {
+      ALV(c->gtw, tc * 2 * (size_t)c->N);
+      ALV(c->glam, tc * (size_t)m);
+      const cudaError_t e = c->tc == ADS_F64
+                                ? gram_fft_tables<double>(c->N, (double*)c->gtw, (double*)c->glam)
+                                : gram_fft_tables<float>(c->N, (float*)c->gtw, (float*)c->glam);
+      if (e != cudaSuccess) return bail(fail(c, ADS_ERR_CUDA, "gram tables"));
     } else {
-      ALV(c->Sdst, 4 * (size_t)m * m);
-      ALV(c->invd, 4 * npiv);
-      launch_convert<float>(S64, (float*)c->Sdst, (size_t)m * m, c->stream);
-      launch_convert<float>(inv64, (float*)c->invd, npiv, c->stream);
+      double *S64 = nullptr, *inv64 = nullptr;
+      const size_t npiv = (size_t)m * m * (c->dim == 3 ? m : 1);
+      AL(S64, (size_t)m * m);
+      AL(inv64, npiv);
+      if (launch_gram_init(c->dim, c->N, S64, inv64, c->stream) != cudaSuccess)
+        return bail(fail(c, ADS_ERR_CUDA, "gram init"));
+      if (c->tc == ADS_F64) {
+        c->Sdst = S64;
+        c->invd = inv64;
+      } else {
+        ALV(c->Sdst, 4 * (size_t)m * m);
+        ALV(c->invd, 4 * npiv);
+        launch_convert<float>(S64, (float*)c->Sdst, (size_t)m * m, c->stream);
+        launch_convert<float>(inv64, (float*)c->invd, npiv, c->stream);
+      }
     }
-    AL(c->dot_part, (size_t)gemm_blocks(c->dim == 3 ? c->m1 * c->m1 : c->m1, c->m1) + 1);
+    {
+      const int ng = gemm_blocks(c->dim == 3 ? c->m1 * c->m1 : c->m1, c->m1);
+      const int nf = c->gram_fft ? gram_fft_dot_parts(c->N) : 0;
+      AL(c->dot_part, (size_t)(ng > nf ? ng : nf) + 1);
+    }
     AL(c->loss, 1);
     AL(c->loss_log, kLossRing);
     AL(c->bc, 2);

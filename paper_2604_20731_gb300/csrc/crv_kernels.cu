@@ -137,9 +137,14 @@ cudaError_t launch_crv_coeffs(const CrvArgs<T, TA>& a, cudaStream_t st) {
 // Loss finalisation (sum of the per-CTA partials of RES . z in a fixed
 // order), fused into the adjoint stencil's first thread: it also advances the
 // Adam step counter, logs the loss and stores the bias corrections.
+// warp 0 of block 0: lane sums of parts lane, lane + 32, ..., then a fixed
+// shuffle tree (deterministic), lane 0 finishes
 __device__ __forceinline__ void loss_finalize_dev(const LossFin& lf) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int i = 0; i < lf.nparts; ++i) s += lf.part[i];
+  for (int i = lane; i < lf.nparts; i += 32) s += lf.part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
   *lf.loss = s;
   if (!isfinite(s)) lf.flags[0] |= 4;
   if (lf.bump) {
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__
                                                     T h2, T scale, T* __restrict__ out, LossFin lf) {
   const int m = N - 1, n1 = N + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (lf.part && t == 0) loss_finalize_dev(lf);
+  if (lf.part && t < 32) loss_finalize_dev(lf);
   if (t >= m * m) return;
   const int jj = t / m, ii = t % m;  // interior index
   const int j = jj + 1, i = ii + 1;  // node index
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(256) k_stencil_3d(int N, T kz, const T* __rest
                                                     T h2, T scale, T* __restrict__ out, LossFin lf) {
   const int m = N - 1, n1 = N + 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (lf.part && t == 0) loss_finalize_dev(lf);
+  if (lf.part && t < 32) loss_finalize_dev(lf);
   if (t >= (long long)m * m * m) return;
   const int ii = (int)(t % m), jj = (int)((t / m) % m), kk = (int)(t / ((long long)m * m));
   const int i = ii + 1, j = jj + 1, k = kk + 1;
@@ -499,7 +504,7 @@ cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaS
   size_t smem = (size_t)2 * nrows * cw * sizeof(T);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto k = k_tridiag_smem<T>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<(ncols + cw - 1) / cw, 256, smem, st>>>(nrows, ncols, cw, invd, X);
   return cudaGetLastError();
 }

@@ -70,7 +70,8 @@ template <typename T>
 cudaError_t launch_zsolve(const QuadArgs<T>& a, T* X, double* mass_part, cudaStream_t st);
 int quad_rows(int n, size_t esize);  // element rows per strip of the 2D quadrature
 int quad_blocks(int dim, int n, int re);
-int ysolve_blocks(int dim, int n);
+int ysolve_blocks(int dim, int n);       // partial-sum slots (largest layout of either precision)
+int ysweep_blocks(int n, size_t esize);  // slots one 2D y sweep writes
 int sweep_ld(int n);  // row stride of the 2D sweep intermediates
 // mass bookkeeping: mode 0 = set int S from partials; mode 1 = step update
 cudaError_t launch_mass_finalize(const double* mass_part, int nmass, const double* src_part,
@@ -182,6 +183,16 @@ struct MlpTcArgs {
   int nparams;
   int* flags;             // bit 8: a tensor-core wait timed out
 };
+// Gram solve by sine transforms computed with FFTs (2D, N a power of two,
+// 8 <= N <= 2048): tables, partial count of the loss, and the three passes
+bool gram_fft_supported(int dim, int N);
+int gram_fft_dot_parts(int N);
+template <typename T>
+cudaError_t gram_fft_tables(int N, T* tw /*2N*/, T* lam /*N-1*/);
+template <typename T>
+cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const T* tw, const T* lam,
+                            T h2, double* dot_part, cudaStream_t st);
+
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
 size_t mlp_tc_acts_bytes(int npts, int width);

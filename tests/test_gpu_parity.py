@@ -179,7 +179,9 @@ def test_coefficients_fp64(n):
     s.close()
 
 
-@pytest.mark.parametrize("n", [3, 5, 33, 96])
+# N a power of two (8, 64, 128) takes the FFT sine-transform Gram solve; the
+# other sizes the dense-transform + tridiagonal route
+@pytest.mark.parametrize("n", [3, 5, 8, 33, 64, 96, 128])
 def test_loss_and_gradient_fp64(n):
     sc, s, crv, theta, alpha, f = _crv_case(n, "f64")
     loss = s.loss_grad()
@@ -193,7 +195,8 @@ def test_loss_and_gradient_fp64(n):
     s.close()
 
 
-@pytest.mark.parametrize("n,width", [(3, 64), (33, 64), (65, 128), (130, 64)])
+@pytest.mark.parametrize("n,width", [(3, 64), (8, 64), (33, 64), (64, 64), (65, 128), (128, 128),
+                                     (130, 64)])
 def test_loss_and_gradient_fp32(n, width):
     sc, s, crv, theta, alpha, f = _crv_case(n, "f32", width=width)
     assert rel_inf(s.get("ALPHA").ravel(), alpha.ravel()) <= 1e-6
@@ -332,7 +335,7 @@ def test_pretrain_reduces_loss_and_approaches_direct_solution():
 # direction must agree to cosine >= 0.9995.
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [3, 9, 33, 130])
+@pytest.mark.parametrize("n", [3, 9, 16, 33, 64, 130])
 def test_loss_and_gradient_bf16_tensor_cores(n):
     sc, s, crv, theta, alpha, f = _crv_case(n, "bf16", width=64)
     loss = s.loss_grad()
