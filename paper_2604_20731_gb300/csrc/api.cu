@@ -881,7 +881,7 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     }
     c->gram_fft = gram_fft_supported(c->dim, c->N);
     if (c->gram_fft) {
-      ALV(c->gtw, tc * 2 * (size_t)c->N);
+      ALV(c->gtw, tc * 4 * (size_t)c->N);
       ALV(c->glam, tc * (size_t)m);
       const cudaError_t e = c->tc == ADS_F64
                                 ? gram_fft_tables<double>(c->N, (double*)c->gtw, (double*)c->glam)

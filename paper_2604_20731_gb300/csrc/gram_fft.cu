@@ -12,7 +12,11 @@
 // route reaches the same z (up to rounding) with O(N^2 log N) work per
 // application.  D is computed with a complex FFT of length L = 2N of the odd
 // extension y = (0, x_1..x_{N-1}, 0, -x_{N-1}..-x_1): its transform is
-// Y_k = -2i (D x)_k, so (D x)_k = -Im(Y_k) / 2.
+// Y_k = -2i (D x)_k, so (D x)_k = -Im(Y_k) / 2.  Two lines a, b share one
+// FFT: the transform of y_a + i y_b is -2i (D a)_k + 2 (D b)_k, so
+// (D a)_k = -Im / 2 and (D b)_k = Re / 2.  The FFT is the Stockham
+// self-sorting form with radix-4 passes (and one radix-2 pass when log2 L is
+// odd) between two shared-memory buffers.
 //
 // Three passes over the m x m grid (row-major, x fastest):
 //   rows:    D along x of every row                           (k_dst_rows)
@@ -37,30 +41,61 @@ struct __align__(2 * sizeof(T)) Cx {
 
 constexpr int kFftThreads = 256;
 
-// Radix-2 decimation-in-time FFT, in place, of nl lines of length L = 2^lg
-// held one after another in shared memory, input in bit-reversed order.
-// Twiddles tw[k] = exp(-2 pi i k / L), k < L / 2.
 template <typename T>
-__device__ __forceinline__ void fft_lines(Cx<T>* buf, int nl, int lg, const Cx<T>* tw) {
-  const int hl = 1 << (lg - 1);  // butterflies per line and stage
-  const int nbf = nl * hl;
-  for (int s = 0; s < lg; ++s) {
-    const int half = 1 << s;
-    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      const int line = b >> (lg - 1), bl = b & (hl - 1);
-      const int pos = bl & (half - 1), grp = bl >> s;
-      const int i0 = (line << lg) + (grp << (s + 1)) + pos, i1 = i0 + half;
-      const Cx<T> w = tw[pos << (lg - 1 - s)];
-      const Cx<T> a = buf[i0], c = buf[i1];
-      const T cr = c.re * w.re - c.im * w.im, ci = c.re * w.im + c.im * w.re;
-      buf[i0] = Cx<T>{a.re + cr, a.im + ci};
-      buf[i1] = Cx<T>{a.re - cr, a.im - ci};
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> w) {
+  return Cx<T>{a.re * w.re - a.im * w.im, a.re * w.im + a.im * w.re};
 }
 
-__device__ __forceinline__ int bitrev(int j, int lg) { return (int)(__brev((unsigned)j) >> (32 - lg)); }
+// Stockham FFT of P lines of length L = 2^lg stored one after another in a
+// (b is scratch of the same size); twiddles tw[q] = exp(-2 pi i q / L),
+// q < L.  A pass of radix R over sub-transforms of length Ns: butterfly j
+// reads x[j + r L/R], multiplies by exp(-2 pi i r k / (Ns R)) with
+// k = j mod Ns, takes the R-point DFT and writes y[(j - k) R + k + r Ns].
+// Returns the buffer that holds the result.
+template <typename T>
+__device__ __forceinline__ Cx<T>* fft_stockham(Cx<T>* a, Cx<T>* b, int P, int lg, const Cx<T>* tw) {
+  const int L = 1 << lg;
+  int Ns = 1, rem = lg;
+  while (rem > 0) {
+    const int lr = rem >= 2 ? 2 : 1, R = 1 << lr;
+    const int nbl = L >> lr;  // butterflies per line
+    for (int t = threadIdx.x; t < P * nbl; t += blockDim.x) {
+      const int line = t >> (lg - lr), j = t & (nbl - 1);
+      const Cx<T>* x = a + (line << lg);
+      Cx<T>* y = b + (line << lg);
+      const int k = j & (Ns - 1);
+      const int step = k * (L / (Ns * R));
+      const int base = (j - k) * R + k;
+      if (R == 4) {
+        Cx<T> v0 = x[j], v1 = x[j + nbl], v2 = x[j + 2 * nbl], v3 = x[j + 3 * nbl];
+        if (k) {
+          v1 = cmul(v1, tw[step]);
+          v2 = cmul(v2, tw[2 * step]);
+          v3 = cmul(v3, tw[3 * step]);
+        }
+        const Cx<T> a0{v0.re + v2.re, v0.im + v2.im}, a1{v0.re - v2.re, v0.im - v2.im};
+        const Cx<T> a2{v1.re + v3.re, v1.im + v3.im};
+        const Cx<T> a3{v1.im - v3.im, v3.re - v1.re};  // (v1 - v3) (-i)
+        y[base] = Cx<T>{a0.re + a2.re, a0.im + a2.im};
+        y[base + Ns] = Cx<T>{a1.re + a3.re, a1.im + a3.im};
+        y[base + 2 * Ns] = Cx<T>{a0.re - a2.re, a0.im - a2.im};
+        y[base + 3 * Ns] = Cx<T>{a1.re - a3.re, a1.im - a3.im};
+      } else {
+        Cx<T> v0 = x[j], v1 = x[j + nbl];
+        if (k) v1 = cmul(v1, tw[step]);
+        y[base] = Cx<T>{v0.re + v1.re, v0.im + v1.im};
+        y[base + Ns] = Cx<T>{v0.re - v1.re, v0.im - v1.im};
+      }
+    }
+    __syncthreads();
+    Cx<T>* tmp = a;
+    a = b;
+    b = tmp;
+    Ns <<= lr;
+    rem -= lr;
+  }
+  return a;
+}
 
 // value j of the odd extension (length 2N) of x_1..x_{N-1} = v[0..N-2]
 template <typename T>
@@ -70,33 +105,37 @@ __device__ __forceinline__ T odd_ext(const T* v, int j, int N, int stride) {
   return T(0);
 }
 
-// D along x for rows [r0, r0 + rpc) of `in` into `out`, times `scale`.  With
-// dotw != nullptr, also a partial of sum dotw * out over the CTA's rows.
+// D along x for rows [r0, r0 + 2P) of `in` into `out` (rows 2p and 2p + 1 of
+// the CTA share line p).  With dotw != nullptr, also a partial of
+// sum dotw * out over the CTA's rows.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
-    k_dst_rows(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int rpc,
-               const Cx<T>* __restrict__ tw, T scale, const T* __restrict__ dotw, double* dot_part) {
+    k_dst_rows(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int P,
+               const Cx<T>* __restrict__ tw, const T* __restrict__ dotw, double* dot_part) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int L = 1 << lg, m = N - 1;
-  Cx<T>* buf = reinterpret_cast<Cx<T>*>(fsm);  // [rpc][L]
-  Cx<T>* tws = buf + (size_t)rpc * L;         // [L / 2]
+  Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
+  Cx<T>* buf0 = tws + L;                       // [P][L]
+  Cx<T>* buf1 = buf0 + (size_t)P * L;          // [P][L]
   __shared__ double red[32];
-  const int r0 = blockIdx.x * rpc;
-  for (int k = threadIdx.x; k < L / 2; k += blockDim.x) tws[k] = tw[k];
-  for (int idx = threadIdx.x; idx < rpc * L; idx += blockDim.x) {
+  const int r0 = blockIdx.x * 2 * P;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
+  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
     const int line = idx >> lg, j = idx & (L - 1);
-    const int row = r0 + line;
-    const T v = row < m ? odd_ext(in + (size_t)row * m, j, N, 1) : T(0);
-    buf[(line << lg) + bitrev(j, lg)] = Cx<T>{v, T(0)};
+    const int ra = r0 + 2 * line, rb = ra + 1;
+    const T va = ra < m ? odd_ext(in + (size_t)ra * m, j, N, 1) : T(0);
+    const T vb = rb < m ? odd_ext(in + (size_t)rb * m, j, N, 1) : T(0);
+    buf0[idx] = Cx<T>{va, vb};
   }
   __syncthreads();
-  fft_lines(buf, rpc, lg, tws);
+  const Cx<T>* z = fft_stockham(buf0, buf1, P, lg, tws);
   CompSum<T> dot;
-  for (int idx = threadIdx.x; idx < rpc * m; idx += blockDim.x) {
-    const int line = idx / m, k = idx - line * m + 1;
-    const int row = r0 + line;
+  for (int idx = threadIdx.x; idx < 2 * P * m; idx += blockDim.x) {
+    const int rr = idx / m, k = idx - rr * m + 1;
+    const int row = r0 + rr;
     if (row < m) {
-      const T v = T(-0.5) * buf[(line << lg) + k].im * scale;
+      const Cx<T> zk = z[((rr >> 1) << lg) + k];
+      const T v = (rr & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
       out[(size_t)row * m + k - 1] = v;
       if (dotw) dot.add(v * dotw[(size_t)row * m + k - 1]);
     }
@@ -107,45 +146,50 @@ __global__ void __launch_bounds__(kFftThreads)
   }
 }
 
-// For x-modes i in [c0, c0 + cb): D along y, times scale / (lam_i + lam_j),
-// D along y again; in place.
+// For x-modes i in [c0, c0 + 2P): D along y, times scale / (lam_i + lam_j),
+// D along y again; in place.  Columns 2p and 2p + 1 of the CTA share line p.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
-    k_gram_cols(T* __restrict__ data, int N, int lg, int cb, const Cx<T>* __restrict__ tw,
+    k_gram_cols(T* __restrict__ data, int N, int lg, int P, const Cx<T>* __restrict__ tw,
                 const T* __restrict__ lam, T scale) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const int L = 1 << lg, m = N - 1;
-  Cx<T>* buf = reinterpret_cast<Cx<T>*>(fsm);  // [cb][L]
-  Cx<T>* tws = buf + (size_t)cb * L;          // [L / 2]
-  T* vt = reinterpret_cast<T*>(tws + L / 2);  // [cb][N]: transformed, scaled columns
-  const int c0 = blockIdx.x * cb;
-  for (int k = threadIdx.x; k < L / 2; k += blockDim.x) tws[k] = tw[k];
-  // column c fastest: a warp reads cb neighbouring values of several rows
-  for (int idx = threadIdx.x; idx < cb * L; idx += blockDim.x) {
-    const int c = idx % cb, j = idx / cb;
+  const int L = 1 << lg, m = N - 1, C = 2 * P;
+  Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
+  Cx<T>* buf0 = tws + L;                       // [P][L]
+  Cx<T>* buf1 = buf0 + (size_t)P * L;          // [P][L]
+  const int c0 = blockIdx.x * C;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
+  // column c of the CTA fastest: a warp reads C neighbouring values of rows
+  for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+    const int c = idx % C, j = idx / C;
     const int col = c0 + c;
     const T v = col < m ? odd_ext(data + col, j, N, m) : T(0);
-    buf[c * L + bitrev(j, lg)] = Cx<T>{v, T(0)};
+    T* slot = reinterpret_cast<T*>(buf0 + ((c >> 1) << lg) + j);
+    slot[c & 1] = v;
   }
   __syncthreads();
-  fft_lines(buf, cb, lg, tws);
-  for (int idx = threadIdx.x; idx < cb * m; idx += blockDim.x) {
+  Cx<T>* z = fft_stockham(buf0, buf1, P, lg, tws);
+  T* vt = reinterpret_cast<T*>(z == buf0 ? buf1 : buf0);  // [C][N] scaled transforms
+  for (int idx = threadIdx.x; idx < C * m; idx += blockDim.x) {
     const int c = idx / m, k = idx - c * m + 1;
     const int col = c0 + c;
+    const Cx<T> zk = z[((c >> 1) << lg) + k];
+    const T d = (c & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
     const T li = col < m ? lam[col] : T(1);
-    vt[c * N + k - 1] = T(-0.5) * buf[c * L + k].im * (scale / (li + lam[k - 1]));
+    vt[c * N + k - 1] = d * (scale / (li + lam[k - 1]));
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < cb * L; idx += blockDim.x) {
-    const int c = idx >> lg, j = idx & (L - 1);
-    buf[c * L + bitrev(j, lg)] = Cx<T>{odd_ext(vt + c * N, j, N, 1), T(0)};
+  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
+    const int line = idx >> lg, j = idx & (L - 1);
+    z[idx] = Cx<T>{odd_ext(vt + (2 * line) * N, j, N, 1), odd_ext(vt + (2 * line + 1) * N, j, N, 1)};
   }
   __syncthreads();
-  fft_lines(buf, cb, lg, tws);
-  for (int idx = threadIdx.x; idx < cb * m; idx += blockDim.x) {
-    const int c = idx % cb, k = idx / cb + 1;
+  Cx<T>* w = fft_stockham(z, reinterpret_cast<Cx<T>*>(vt), P, lg, tws);
+  for (int idx = threadIdx.x; idx < C * m; idx += blockDim.x) {
+    const int c = idx % C, k = idx / C + 1;
     const int col = c0 + c;
-    if (col < m) data[(size_t)(k - 1) * m + col] = T(-0.5) * buf[c * L + k].im;
+    const Cx<T> wk = w[((c >> 1) << lg) + k];
+    if (col < m) data[(size_t)(k - 1) * m + col] = (c & 1) ? T(0.5) * wk.re : T(-0.5) * wk.im;
   }
 }
 
@@ -155,27 +199,20 @@ int log2_exact(int N) {
   return (1 << lg) == N ? lg : -1;
 }
 
-int rows_per_cta(int L) { return L >= 2 * kFftThreads ? 1 : (2 * kFftThreads) / L; }
-
+// twiddles and two buffers of P lines of L complex values
 template <typename T>
-size_t rows_smem(int L) {
-  return ((size_t)rows_per_cta(L) * L + L / 2) * sizeof(Cx<T>);
+size_t fft_smem(int L, int P) {
+  return ((size_t)L + 2 * (size_t)P * L) * sizeof(Cx<T>);
 }
 
-// cb lines of L complex values, the twiddles and cb lines of N = L / 2 reals
+// line pairs per CTA: enough butterflies for the threads, within the shared memory
 template <typename T>
-size_t cols_smem(int L, int cb) {
-  return ((size_t)cb * L + L / 2) * sizeof(Cx<T>) + (size_t)cb * (L / 2) * sizeof(T);
-}
-
-// x-modes per CTA: enough CTAs to cover the SMs where the grid allows, 2..8
-template <typename T>
-int cols_per_cta(int L) {
-  const int m = L / 2 - 1;
-  int cb = 2;
-  while (cb < 8 && m / (2 * cb) >= 152) cb *= 2;
-  while (cb > 1 && cols_smem<T>(L, cb) > 200 * 1024) cb /= 2;
-  return cb;
+int lines_per_cta(int L, int minP) {
+  int P = 1024 / L;
+  if (P < minP) P = minP;
+  if (P < 1) P = 1;
+  while (P > 1 && fft_smem<T>(L, P) > 200 * 1024) P /= 2;
+  return P;
 }
 
 }  // namespace
@@ -186,26 +223,28 @@ bool gram_fft_supported(int dim, int N) {
 }
 
 int gram_fft_dot_parts(int N) {
-  const int m = N - 1, rpc = rows_per_cta(2 * N);
-  return (m + rpc - 1) / rpc;
+  const int m = N - 1, P = lines_per_cta<double>(2 * N, 1);  // the row kernel's grid (FP64 bound)
+  const int Pf = lines_per_cta<float>(2 * N, 1);
+  const int g = (m + 2 * P - 1) / (2 * P), gf = (m + 2 * Pf - 1) / (2 * Pf);
+  return g > gf ? g : gf;
 }
 
 template <typename T>
 cudaError_t gram_fft_tables(int N, T* tw, T* lam) {
   const int L = 2 * N, m = N - 1;
-  std::vector<T> h((size_t)L + m);
+  std::vector<T> h(2 * (size_t)L + m);
   const double pi = 3.14159265358979323846;
-  for (int k = 0; k < L / 2; ++k) {
-    h[2 * k] = (T)std::cos(2.0 * pi * k / L);
-    h[2 * k + 1] = (T)(-std::sin(2.0 * pi * k / L));
+  for (int q = 0; q < L; ++q) {
+    h[2 * q] = (T)std::cos(2.0 * pi * q / L);
+    h[2 * q + 1] = (T)(-std::sin(2.0 * pi * q / L));
   }
   for (int k = 1; k <= m; ++k) {
     const double s = std::sin(pi * k / (2.0 * N));
-    h[L + k - 1] = (T)(4.0 * s * s);  // 2 - 2 cos(pi k / N)
+    h[2 * L + k - 1] = (T)(4.0 * s * s);  // 2 - 2 cos(pi k / N)
   }
-  cudaError_t e = cudaMemcpy(tw, h.data(), sizeof(T) * L, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(tw, h.data(), sizeof(T) * 2 * L, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(lam, h.data() + L, sizeof(T) * m, cudaMemcpyHostToDevice);
+  return cudaMemcpy(lam, h.data() + 2 * L, sizeof(T) * m, cudaMemcpyHostToDevice);
 }
 
 // pass 0: work = D_x res; pass 1: work <- h^2 (2/N)^2 D_y Lambda^-1 D_y work;
@@ -216,20 +255,21 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
   const int lg = log2_exact(N) + 1, L = 2 * N, m = N - 1;
   if (lg < 4 || lg > 12) return cudaErrorInvalidValue;
   const Cx<T>* twc = reinterpret_cast<const Cx<T>*>(tw);
-  const int rpc = rows_per_cta(L), cb = cols_per_cta<T>(L);
   if (pass == 1) {
-    const size_t smem = cols_smem<T>(L, cb);
+    const int P = lines_per_cta<T>(L, 2);
+    const size_t smem = fft_smem<T>(L, P);
     auto k = k_gram_cols<T>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const T s = h2 * T(4.0 / ((double)N * N));  // h^2 (2 / N)^2
-    k<<<(m + cb - 1) / cb, kFftThreads, smem, st>>>(work, N, lg, cb, twc, lam, s);
+    k<<<(m + 2 * P - 1) / (2 * P), kFftThreads, smem, st>>>(work, N, lg, P, twc, lam, s);
   } else {
-    const size_t smem = rows_smem<T>(L);
+    const int P = lines_per_cta<T>(L, 1);
+    const size_t smem = fft_smem<T>(L, P);
     auto k = k_dst_rows<T>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int g = (m + rpc - 1) / rpc;
-    if (pass == 0) k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, rpc, twc, T(1), nullptr, nullptr);
-    else k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, rpc, twc, T(1), res, dot_part);
+    const int g = (m + 2 * P - 1) / (2 * P);
+    if (pass == 0) k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, P, twc, nullptr, nullptr);
+    else k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, P, twc, res, dot_part);
   }
   return cudaGetLastError();
 }

@@ -188,7 +188,7 @@ struct MlpTcArgs {
 bool gram_fft_supported(int dim, int N);
 int gram_fft_dot_parts(int N);
 template <typename T>
-cudaError_t gram_fft_tables(int N, T* tw /*2N*/, T* lam /*N-1*/);
+cudaError_t gram_fft_tables(int N, T* tw /*4N: 2N complex twiddles*/, T* lam /*N-1*/);
 template <typename T>
 cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const T* tw, const T* lam,
                             T h2, double* dot_part, cudaStream_t st);

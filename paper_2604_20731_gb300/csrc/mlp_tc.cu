@@ -329,57 +329,75 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// backward, width 64: every gradient on the tensor cores.  The activation
-// tiles carry a ones column (biases), the delta tiles are zero-padded to
-// M = 128, and the accumulators fill the 512 TMEM columns, so one CTA per SM.
+// backward, width 64: every gradient on the tensor cores, one CTA per SM (the
+// accumulators fill the 512 TMEM columns).  The four stored activation tiles
+// of a point tile (64 KB, the forward's layout) arrive by one bulk copy into a
+// double buffer, the next tile's copy running under the current tile's
+// products.  Bias gradients come from a second product against a constant
+// ones tile; the delta tiles are zero-padded to M = 128.
 struct TcSmemB {
   static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
-  static constexpr int ACT = W + 3 * kW * kW * 2;          // 4 x [128][80] bf16      80 KB
-  static constexpr int ACT_SZ = kTP * kWP * 2;
-  static constexpr int DEL = ACT + 4 * ACT_SZ;             // 2 x [128][128] bf16     64 KB
+  static constexpr int ACT_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
+  static constexpr int ACT = W + 3 * kW * kW * 2;          // 2 buffers x 4 tiles    128 KB
   static constexpr int DEL_SZ = kTP * kDP * 2;
-  static constexpr int XIN = DEL + 2 * DEL_SZ;             // [128][16] bf16          4 KB
-  static constexpr int VEC = XIN + kTP * kXP * 2;          // fp32: W5 [64], g [128]
-  static constexpr int BAR = VEC + (kW + kTP) * 4;
-  static constexpr int TOTAL = BAR + 32;
+  static constexpr int DEL = ACT + 8 * ACT_SZ;             // 2 x [128][128] bf16     64 KB
+  static constexpr int XIN = DEL + 2 * DEL_SZ;             // [128][16] bf16: x', 1, 0  4 KB
+  static constexpr int ONES = XIN + kTP * kXP * 2;         // [128][16] bf16: 1, 0     4 KB
+  static constexpr int VEC = ONES + kTP * kXP * 2;         // fp32: W5 [64]
+  static constexpr int BAR = VEC + kW * 4;                 // 3 mbarriers, tmem base, abort flag
+  static constexpr int TOTAL = BAR + 48;
 };
 // TMEM columns: delta product [0,64), dW5 [64,144), dW4 [144,224),
-// dW3 [224,304), dW2 [304,384), dW1 [384,400)
+// dW3 [224,304), dW2 [304,384), dW1 [384,400); in each dW block the weight
+// part is columns [0,64) and the bias part column 64 (of [64,80))
 constexpr int kColDel = 0, kColW5 = 64, kColW4 = 144, kColW1 = 384;
 ADS_D int col_dw(int L) { return L == 5 ? kColW5 : (L == 1 ? kColW1 : kColW4 + (4 - L) * kWP); }
+
+// one-dimensional bulk copy global -> shared, completing on `mbar`
+ADS_D void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
 
 template <int DIN>
 __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemB::W;
-  unsigned char* act = sm + TcSmemB::ACT;  // a_1..a_4 with ones column
+  unsigned char* act = sm + TcSmemB::ACT;  // [buffer][a_1..a_4]
   unsigned char* del = sm + TcSmemB::DEL;  // two delta tiles
   unsigned char* xin = sm + TcSmemB::XIN;
+  unsigned char* ones = sm + TcSmemB::ONES;
   float* fW5 = reinterpret_cast<float*>(sm + TcSmemB::VEC);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB::BAR);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 8);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 12);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB::BAR);  // [0] products, [1], [2] loads
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 24);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 28);
   const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int RGW = (kW / 8) * 128, RGA = (kWP / 8) * 128, RGD = (kDP / 8) * 128,
-                RGX = (kXP / 8) * 128;
+  constexpr int RGW = (kW / 8) * 128, RGD = (kDP / 8) * 128, RGX = (kXP / 8) * 128;
+  constexpr uint32_t kTileBytes = 4 * TcSmemB::ACT_SZ;
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
+  const int ntiles = (a.npts + kTP - 1) / kTP;
   load_hidden_weights<kW>(th, o2, wt, tid, kTP);
   for (int i = tid; i < kW; i += kTP) fW5[i] = th[o5 + i];
-  // constant columns: ones column of the activation tiles and of the input
-  // tile, zero padding of the delta tiles
+  // constant tiles: the ones column, the zero padding of the delta tiles
   {
     float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int L = 0; L < 4; ++L) {
-      st_atom(act + L * TcSmemB::ACT_SZ, RGA, tid, kW, one);
-      st_atom(act + L * TcSmemB::ACT_SZ, RGA, tid, kW + 8, zero);
-    }
+    st_atom(ones, RGX, tid, 0, one);
+    st_atom(ones, RGX, tid, 8, zero);
     for (int b = 0; b < 2; ++b)
       for (int c = kW; c < kDP; c += 8) st_atom(del + b * TcSmemB::DEL_SZ, RGD, tid, c, zero);
   }
   if (tid == 0) {
     *abort_flag = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    for (int i = 0; i < 3; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + i)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -391,34 +409,34 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // the first tile's activations
+  if (tid == 0 && (int)blockIdx.x < ntiles) {
+    mbar_expect(mbar + 1, kTileBytes);
+    bulk_load(act, a.acts + (size_t)blockIdx.x * kTileBytes, kTileBytes, mbar + 1);
+  }
   const uint32_t tmem = *tbase;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
   const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
-                 xin_s = smem_addr(xin);
-  const uint32_t id_dw = idesc_bf16(kDP, kWP, 1, 1);   // dW_l: M = 128 (o), N = 80, K = points
-  const uint32_t id_dw1 = idesc_bf16(kDP, kXP, 1, 1);  // dW_1: N = 16
-  const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);    // delta product: M = points, N = 64, K = 64
-  uint32_t phase = 0;
+                 xin_s = smem_addr(xin), ones_s = smem_addr(ones);
+  const uint32_t id_dw = idesc_bf16(kDP, kW, 1, 1);   // dW_l weights: M = 128 (o), N = 64, K = points
+  const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // bias column (and dW_1): N = 16
+  const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
+  uint32_t phase = 0;           // product barrier
+  uint32_t lphase = 0;          // load barriers: bit b = phase of barrier 1 + b
   bool aborted = false;
   bool first = true;  // first tile of this CTA: overwrite the dW accumulators
-  const int ntiles = (a.npts + kTP - 1) / kTP;
+  bool pending = false;  // a prefetch was issued and not yet waited for
   auto wait_mma = [&]() {
     if (!mbar_wait(mbar, phase)) *abort_flag = 1;
     phase ^= 1;
     tc_fence_after();
   };
-  for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int buf = it & 1;
+    unsigned char* actb = act + buf * 4 * TcSmemB::ACT_SZ;
+    const uint32_t actb_s = act_s + buf * 4 * TcSmemB::ACT_SZ;
     const int p0 = tile * kTP;
-    // every product of the previous tile completed (waited) before its end;
-    // stage this tile's activations (16-byte async copies into the padded tiles)
-    const unsigned char* gtile = a.acts + (size_t)tile * 4 * kTP * kW * 2;
-    for (int ch = tid; ch < 4 * kTP * (kW / 8); ch += kTP) {
-      const int L = ch / (kTP * (kW / 8)), rem = ch % (kTP * (kW / 8));
-      const int r = rem / (kW / 8), c = (rem % (kW / 8)) * 8;
-      cp_async16(act + L * TcSmemB::ACT_SZ + core_off(r, c, RGA),
-                 gtile + (size_t)L * kTP * kW * 2 + core_off(r, c, RGW));
-    }
-    cp_async_commit();
     const int idx = p0 + tid;
     const float g = idx < a.npts ? a.gu[idx] : 0.0f;
     {
@@ -434,17 +452,33 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
       st_atom(del, RGD, tid, 0, d5);
       for (int c = 8; c < kW; c += 8) st_atom(del, RGD, tid, c, z);
     }
-    cp_async_wait_all();
+    // this tile's activations
+    if (!mbar_wait(mbar + 1 + buf, (lphase >> buf) & 1u)) *abort_flag = 1;
+    lphase ^= 1u << buf;
+    pending = false;
     if (sync_abort(abort_flag)) {
       aborted = true;
       break;
     }
+    // the next tile's activations into the other buffer (its previous
+    // readers, the products and epilogues of the tile before, are done)
+    if (tile + (int)gridDim.x < ntiles) {
+      pending = true;
+      if (tid == 0) {
+        mbar_expect(mbar + 2 - buf, kTileBytes);
+        bulk_load(act + (1 - buf) * 4 * TcSmemB::ACT_SZ,
+                  a.acts + (size_t)(tile + gridDim.x) * kTileBytes, kTileBytes, mbar + 2 - buf);
+      }
+    }
     // output layer: dW_5 (row 0) and db_5 from Delta_5^T [a_4 | 1]
     if (tid == 0) {
 #pragma unroll
-      for (int ks = 0; ks < kTP / 16; ++ks)
-        mma_bf16(tmem + col_dw(5), desc_mn(del_s, RGD, ks), desc_mn(act_s + 3 * TcSmemB::ACT_SZ, RGA, ks),
-                 id_dw, (ks > 0 || !first) ? 1u : 0u);
+      for (int ks = 0; ks < kTP / 16; ++ks) {
+        const uint64_t da = desc_mn(del_s, RGD, ks);
+        const uint32_t acc = (ks > 0 || !first) ? 1u : 0u;
+        mma_bf16(tmem + col_dw(5), da, desc_mn(actb_s + 3 * TcSmemB::ACT_SZ, RGW, ks), id_dw, acc);
+        mma_bf16(tmem + col_dw(5) + kW, da, desc_mn(ones_s, RGX, ks), id_db, acc);
+      }
     }
     // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1
     {
@@ -452,7 +486,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
 #pragma unroll
       for (int c = 0; c < kW; c += 8) {
         float av[8], v[8];
-        ld_atom(act + 3 * TcSmemB::ACT_SZ, RGA, tid, c, av);
+        ld_atom(actb + 3 * TcSmemB::ACT_SZ, RGW, tid, c, av);
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
         st_atom(d4, RGD, tid, c, v);
@@ -465,13 +499,16 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
         break;
       }
       const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
-      const uint32_t ain = act_s + (L - 2) * TcSmemB::ACT_SZ;  // a_{L-1}
+      const uint32_t ain = actb_s + (L - 2) * TcSmemB::ACT_SZ;  // a_{L-1}
       if (tid == 0) {
         // dW_L, db_L += Delta_L^T [a_{L-1} | 1]
 #pragma unroll
-        for (int ks = 0; ks < kTP / 16; ++ks)
-          mma_bf16(tmem + col_dw(L), desc_mn(dcur, RGD, ks), desc_mn(ain, RGA, ks), id_dw,
-                   (ks > 0 || !first) ? 1u : 0u);
+        for (int ks = 0; ks < kTP / 16; ++ks) {
+          const uint64_t da = desc_mn(dcur, RGD, ks);
+          const uint32_t acc = (ks > 0 || !first) ? 1u : 0u;
+          mma_bf16(tmem + col_dw(L), da, desc_mn(ain, RGW, ks), id_dw, acc);
+          mma_bf16(tmem + col_dw(L) + kW, da, desc_mn(ones_s, RGX, ks), id_db, acc);
+        }
         // Delta_L W_L
         const uint32_t wl = wt_s + (L - 2) * kW * kW * 2;
 #pragma unroll
@@ -482,16 +519,17 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
       wait_mma();
       // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
       unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
+      const unsigned char* aprev = actb + (L - 2) * TcSmemB::ACT_SZ;
 #pragma unroll
       for (int c = 0; c < kW; c += 16) {
         float dv[16];
         tmem_ld16(lane_base + kColDel + c, dv);
         float av[8], v[8];
-        ld_atom(act + (L - 2) * TcSmemB::ACT_SZ, RGA, tid, c, av);
+        ld_atom(aprev, RGW, tid, c, av);
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = dv[j] * (1.0f - av[j] * av[j]);
         st_atom(dn, RGD, tid, c, v);
-        ld_atom(act + (L - 2) * TcSmemB::ACT_SZ, RGA, tid, c + 8, av);
+        ld_atom(aprev, RGW, tid, c + 8, av);
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = dv[8 + j] * (1.0f - av[j] * av[j]);
         st_atom(dn, RGD, tid, c + 8, v);
@@ -508,18 +546,24 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
       const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
 #pragma unroll
       for (int ks = 0; ks < kTP / 16; ++ks)
-        mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s, RGX, ks), id_dw1,
+        mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s, RGX, ks), id_db,
                  (ks > 0 || !first) ? 1u : 0u);
       mma_commit(mbar);
     }
     wait_mma();  // all of this tile's products are complete before its tiles are reused
     first = false;
   }
+  // after an abort a prefetch may still be in flight: it must land before
+  // the CTA's shared memory is released (bounded wait on its barrier)
+  aborted = sync_abort(abort_flag);
+  if (aborted && pending && tid == 0) {
+    const int nb = 1 - (it & 1);
+    mbar_wait(mbar + 1 + nb, (lphase >> nb) & 1u);
+  }
   // gradient row of this CTA: TMEM lane o = thread; rows o >= 64 are padding.
   // Every thread issues the same TMEM loads (they are warp-collective).
   float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
   const int o = tid;
-  aborted = sync_abort(abort_flag);
   if (!aborted && !first) {
     for (int L = 4; L >= 2; --L) {
       const int ow = o2 + (L - 2) * (kW * kW + kW);
@@ -556,7 +600,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
         }
       }
     }
-  } else if (first) {
+  } else if (first && !aborted) {
     for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;  // CTA without tiles
   }
   if (aborted && tid == 0) atomicOr(a.flags, 8);
@@ -843,16 +887,38 @@ size_t mlp_tc_acts_bytes(int npts, int width) {
   return (size_t)ntiles * 4 * kTP * width * 2;
 }
 
+
+
+// CTAs of a tensor-memory kernel that fit on one SM: shared memory (with the
+// per-block reservation), registers, threads and TMEM columns.  (The runtime's
+// occupancy query reports one block per SM for kernels that allocate TMEM.)
+template <typename K>
+static int tc_residency(K k, size_t smem, int tmem_cols) {
+  static int per_sm = 0, reserved = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, k);
+  int occ = per_sm / (int)(smem + reserved);
+  const int regs_per_warp = ((fa.numRegs > 0 ? fa.numRegs : 255) * 32 + 255) / 256 * 256;
+  const int by_regs = 65536 / (regs_per_warp * (kTP / 32));
+  if (by_regs < occ) occ = by_regs;
+  if (2048 / kTP < occ) occ = 2048 / kTP;
+  if (512 / tmem_cols < occ) occ = 512 / tmem_cols;
+  return occ < 1 ? 1 : occ;
+}
+
 template <int W, int DIN>
 static int bwd_tc_occ() {
   auto k = k_mlp_bwd_tcr<W, DIN>;
   const size_t smem = TcSmemB2<W>::TOTAL;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTP, smem);
-  const int by_tmem = 512 / (4 * W);
-  if (occ > by_tmem) occ = by_tmem;
-  return occ < 1 ? 1 : occ;
+  return tc_residency(k, smem, 4 * W);
 }
 
 int mlp_tc_bwd_blocks(int npts, int width, int din) {
@@ -869,10 +935,7 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   const size_t smem = TcSmemF<W>::TOTAL;
   auto k = k_mlp_fwd_tc<W, DIN>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTP, smem);
-  if (occ < 1) occ = 1;
-  if (occ > 512 / W) occ = 512 / W;  // TMEM columns per SM
+  const int occ = tc_residency(k, smem, W);
   const int ntiles = (a.npts + kTP - 1) / kTP;
   const int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   k<<<grid, kTP, smem, st>>>(a);
