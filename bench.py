@@ -54,8 +54,11 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--c2-steps", type=int, default=20)
-    ap.add_argument("--err-iters", type=int, default=40000)
+    ap.add_argument("--err-iters", type=int, default=60000)
     ap.add_argument("--err-steps", type=int, default=3)
+    ap.add_argument("--sat-n", type=int, default=4096)
+    ap.add_argument("--only-saturation", action="store_true",
+                    help="run only the saturation-kernel block (a profiling aid) and print it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-iters", type=int, default=30)
     return ap.parse_args()
@@ -283,6 +286,44 @@ def serving_mix(count, seed=3):
     return out
 
 
+def saturation_roofline(n, scn, HybridSolver):
+    """One 2D saturation sub-step (quadrature + x sweep, y sweep, mass
+    bookkeeping) on an n^2 mesh, FP32 and FP64, timed per kernel with CUDA
+    events (20 sub-steps after 2 untimed).  Algorithmic bytes: the quadrature
+    reads S, P (n+2)^2 and K (n+1)^2 and writes the x-swept rows and the rows
+    strips share (Xm, Xs); the y sweep reads Xm and Xs and writes S.  Each
+    sub-step's arrays total > L2 at n = 4096."""
+    import numpy as np
+    peaks, kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sc = scn.make_scenario(2, n, seed=1000, S0="random")
+    x = np.linspace(0.0, 1.0, n + 2)
+    P = np.outer(np.sin(np.pi * x), np.cos(2 * np.pi * x)) * 10.0
+    out = {"mesh": f"{n}^2 elements", "hbm_peak_gbs": hbm, "peak_note": kind}
+    for dt, es in (("f32", 4), ("f64", 8)):
+        s = HybridSolver(sc, width=None, ads_dtype=dt)
+        s.set_pressure(P)
+        s.saturation_step(1e-6, 2)
+        ms = s.profile_saturation(20)
+        s.close()
+        nb = n + 2
+        re = 4 if 6 * nb * es <= 110 * 1024 else 2
+        nsp = 2 * ((n + re - 1) // re - 1)
+        quad_b = es * (2 * nb * nb + (n + 1) ** 2 + nb * nb + nsp * nb)
+        ysw_b = es * (2 * nb * nb + nsp * nb)
+        tot = sum(ms.values())
+        out[dt] = {"ms_per_substep": tot, "kernel_ms": ms,
+                   "element_steps_per_s": n * n / (tot * 1e-3),
+                   "quad_xsweep_gbs": quad_b / (ms["quad_xsweep"] * 1e-3) / 1e9,
+                   "ysweep_gbs": ysw_b / (ms["ysweep"] * 1e-3) / 1e9,
+                   "ysweep_frac_of_hbm": ysw_b / (ms["ysweep"] * 1e-3) / 1e9 / hbm,
+                   "quad_xsweep_frac_of_hbm": quad_b / (ms["quad_xsweep"] * 1e-3) / 1e9 / hbm,
+                   "algorithmic_bytes": {"quad_xsweep": quad_b, "ysweep": ysw_b}}
+    out["note"] = ("the quadrature + x sweep is bound by FP32 (FP64) instruction issue, not by "
+                   "HBM; the y sweep is the bandwidth-bound line solve")
+    return out
+
+
 def run_ours(a, world, rank, local):
     import numpy as np
     import torch
@@ -295,6 +336,10 @@ def run_ours(a, world, rank, local):
     from paper_2604_20731_gb300 import scenario as scn
     from paper_2604_20731_gb300.solver import HybridSolver, Server
 
+    if a.only_saturation:
+        if rank == 0:
+            print(json.dumps({"saturation": saturation_roofline(a.sat_n, scn, HybridSolver)}), flush=True)
+        return 0
     hp = HybridSolver.hybrid_params(n_sub=a.n_sub, dt=1.0, dt_policy=1, cfl=0.1, src_frac=0.05,
                                     adam_iters=a.adam_iters, lr=a.lr)
     theta0 = scn.make_theta0(2, a.width, 4, seed=7)
@@ -533,6 +578,11 @@ def run_ours(a, world, rank, local):
               "note": "single scenario, L2-resident working set"}
         s.close()
 
+    # ---- (4b) saturation kernels on a mesh larger than L2 (FP32 and FP64) ----
+    sat = None
+    if rank == 0 and a.sat_n > 0:
+        sat = saturation_roofline(a.sat_n, scn, HybridSolver)
+
     # ---- (5) CPU baseline (rank 0, N=1 only): the oracle on the mix ----
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -558,7 +608,7 @@ def run_ours(a, world, rank, local):
                "latency_note": "resident run: a scenario's step latency is the round time (all "
                                "scenarios step once per round); e2e holds the server's per-step latency",
                "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2,
+               "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2, "saturation": sat,
                "gpu_launches": launches, "clocks": clk, "kernel_ms_by_n": prof_by_n,
                "server": server_stats}
         print(json.dumps(out), flush=True)

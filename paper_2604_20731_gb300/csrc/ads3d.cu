@@ -353,11 +353,11 @@ cudaError_t launch_solve3d(const QuadArgs<T>& a, T* X, double* mass_part, cudaSt
   const int nb = a.nb;
   const int nrows = nb * nb;
   size_t smx = sizeof(T) * 32 * (size_t)(nb + 1);
-  cudaFuncSetAttribute(k_xsolve3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+  smem_optin(k_xsolve3d<T>);
   k_xsolve3d<T><<<(nrows + 31) / 32, 256, smx, st>>>(nrows, nb, X, a.ax.l1, a.ax.l2, a.ax.dinv);
   const int cw = slow_cw(nb, sizeof(T));
   const size_t sms = sizeof(T) * (size_t)nb * cw;
-  cudaFuncSetAttribute(k_line_slow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  smem_optin(k_line_slow<T>);
   // y: batch = z planes, rows = y, columns = x
   dim3 gy((nb + cw - 1) / cw, nb);
   k_line_slow<T><<<gy, 256, sms, st>>>(nb, nb, cw, X, a.ax.l1, a.ax.l2, a.ax.dinv, nullptr, nullptr);

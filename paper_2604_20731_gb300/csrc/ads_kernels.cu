@@ -579,11 +579,11 @@ static cudaError_t quad_launch(const QuadArgs<T>& a, int re, int xch, T* Xm, T* 
   const int nblk = quad_blocks(2, a.n, re);
   if (a.n_src <= 2) {
     auto k = k_quad_xsweep_2d<T, MODE, 2>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_optin(k);
     k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
   } else {
     auto k = k_quad_xsweep_2d<T, MODE, kMaxSrc>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_optin(k);
     k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
   }
   return cudaGetLastError();
@@ -843,7 +843,7 @@ cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs
   ysweep_grid<T>(a.n, &gx, &gy);
   const size_t smem = ysweep_smem<T>(sb);
   auto k = k_ysweep_2d<T>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   k<<<dim3(gx, gy), CW, smem, st>>>(xm_map, xs_map, a.n, re, nsp, sb, out, a.ax.l1, a.ax.l2,
                                     a.ax.dinv, a.ax.Iw, mass_part, flags);
   return cudaGetLastError();

@@ -98,6 +98,23 @@ ADS_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 ADS_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 ADS_D void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Allow a kernel the device's full opt-in dynamic shared memory (less its
+// static shared memory).  Setting the limit to one launch's need would lower it
+// for other launches of the same kernel (graphs captured for other sizes).
+template <typename K>
+inline void smem_optin(K k) {
+  static int optin = 0;
+  if (!optin) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (optin <= 0) optin = 48 * 1024;
+  }
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 // ---- bulk tensor copies (TMA) with bounded mbarrier waits ----
 ADS_D unsigned long long gtimer_ns() {
   unsigned long long t;

@@ -504,7 +504,7 @@ cudaError_t launch_tridiag_cols(int nrows, int ncols, const T* invd, T* X, cudaS
   size_t smem = (size_t)2 * nrows * cw * sizeof(T);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto k = k_tridiag_smem<T>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   k<<<(ncols + cw - 1) / cw, 256, smem, st>>>(nrows, ncols, cw, invd, X);
   return cudaGetLastError();
 }

@@ -259,14 +259,14 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
     const int P = lines_per_cta<T>(L, 2);
     const size_t smem = fft_smem<T>(L, P);
     auto k = k_gram_cols<T>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_optin(k);
     const T s = h2 * T(4.0 / ((double)N * N));  // h^2 (2 / N)^2
     k<<<(m + 2 * P - 1) / (2 * P), kFftThreads, smem, st>>>(work, N, lg, P, twc, lam, s);
   } else {
     const int P = lines_per_cta<T>(L, 1);
     const size_t smem = fft_smem<T>(L, P);
     auto k = k_dst_rows<T>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_optin(k);
     const int g = (m + 2 * P - 1) / (2 * P);
     if (pass == 0) k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, P, twc, nullptr, nullptr);
     else k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, P, twc, res, dot_part);

@@ -442,7 +442,7 @@ static cudaError_t fwd_dispatch(const MlpArgs<T>& a, cudaStream_t st) {
   }
   auto k = k_mlp_fwd<T, W, DIN, 64>;
   size_t smem = fwd_smem<T, W, DIN>();
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   int ntiles = (a.npts + 63) / 64;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kMlpThreads, smem);
@@ -459,7 +459,7 @@ static cudaError_t bwd_dispatch(const MlpArgs<T>& a, int nblk, cudaStream_t st) 
   }
   auto k = k_mlp_bwd<T, W, DIN, 64>;
   size_t smem = bwd_smem<T, W, DIN>();
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   k<<<nblk, kMlpThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -468,7 +468,7 @@ template <typename T, int W, int DIN>
 static int bwd_grid(int npts) {
   auto k = k_mlp_bwd<T, W, DIN, 64>;
   size_t smem = bwd_smem<T, W, DIN>();
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kMlpThreads, smem);
   if (occ < 1) occ = 1;

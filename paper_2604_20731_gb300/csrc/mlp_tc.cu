@@ -917,7 +917,7 @@ template <int W, int DIN>
 static int bwd_tc_occ() {
   auto k = k_mlp_bwd_tcr<W, DIN>;
   const size_t smem = TcSmemB2<W>::TOTAL;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   return tc_residency(k, smem, 4 * W);
 }
 
@@ -934,7 +934,7 @@ template <int W, int DIN>
 static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   const size_t smem = TcSmemF<W>::TOTAL;
   auto k = k_mlp_fwd_tc<W, DIN>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   const int occ = tc_residency(k, smem, W);
   const int ntiles = (a.npts + kTP - 1) / kTP;
   const int grid = ntiles < occ * sms() ? ntiles : occ * sms();
@@ -953,7 +953,7 @@ template <int W, int DIN>
 static cudaError_t bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
   auto k = k_mlp_bwd_tcr<W, DIN>;
   const size_t smem = TcSmemB2<W>::TOTAL;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_optin(k);
   k<<<nblk, kTP, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -962,7 +962,7 @@ cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
   if (a.width == 64) {
     const size_t smem = TcSmemB::TOTAL;
     auto k = a.din == 2 ? k_mlp_bwd_tc<2> : k_mlp_bwd_tc<3>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_optin(k);
     k<<<nblk, kTP, smem, st>>>(a);
     return cudaGetLastError();
   }
