@@ -48,21 +48,25 @@ ADS_D uint32_t core_off(int r, int c, int rg) {
   return (uint32_t)((r >> 3) * rg + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
 
-ADS_D uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  return d;                // base offset 0, no swizzle
-}
-// K-major view of a tile (rows = M/N, columns = K), k-step of 16 columns
+// Shared-memory matrix descriptor (no swizzle): bits 0-13 start address >> 4,
+// 16-29 leading-dimension byte offset >> 4, 32-45 stride-dimension byte offset
+// >> 4, bit 46 the descriptor version of tcgen05, base offset and swizzle 0.
+// The two views below give the same bits as sdesc, written so that a k-step
+// costs one 32-bit add: shared addresses are below 256 KB, so the start
+// address field (bits 0-13, address >> 4) never carries into the fields above.
+// K-major view of a tile (rows = M/N, columns = K), k-step of 16 columns:
+// LBO 128 B, SBO = rg
 ADS_D uint64_t desc_k(uint32_t base, int rg, int kstep) {
-  return sdesc(base + kstep * 256, 128, rg);
+  const uint32_t lo = (base >> 4) + (uint32_t)kstep * 16u + (8u << 16);
+  const uint32_t hi = ((uint32_t)rg >> 4) | (1u << 14);  // SBO, descriptor version
+  return ((uint64_t)hi << 32) | lo;
 }
-// MN-major view of a tile (rows = K, columns = M/N), k-step of 16 rows
+// MN-major view of a tile (rows = K, columns = M/N), k-step of 16 rows:
+// LBO = rg, SBO 128 B
 ADS_D uint64_t desc_mn(uint32_t base, int rg, int kstep) {
-  return sdesc(base + kstep * 2 * rg, rg, 128);
+  const uint32_t lo = (base >> 4) + (uint32_t)kstep * ((2u * (uint32_t)rg) >> 4) + (((uint32_t)rg >> 4) << 16);
+  const uint32_t hi = 8u | (1u << 14);
+  return ((uint64_t)hi << 32) | lo;
 }
 // instruction descriptor: BF16 x BF16 -> FP32, M x N, operand majors
 ADS_HD uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
@@ -93,8 +97,8 @@ ADS_D unsigned long long now_ns() {
 // wait for the mbarrier phase `parity`, giving up after about a second
 // (returns false then; the caller records an error and stops)
 ADS_D bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  const unsigned long long t0 = now_ns();
-  for (;;) {
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -103,7 +107,8 @@ ADS_D bool mbar_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(smem_addr(mbar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (now_ns() - t0 > kWaitNs) return false;
+    if (it == 0) t0 = now_ns();
+    else if (now_ns() - t0 > kWaitNs) return false;
   }
 }
 
@@ -132,6 +137,42 @@ ADS_D void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+
+// 32 consecutive TMEM columns of this warp's lanes, without waiting; the
+// values are valid after tmem_wait32 on the same registers
+ADS_D void tmem_ld32_async(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// pin 32 registers after the preceding wait (no instruction is emitted)
+ADS_D void reg_pin32(uint32_t r[32]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+// 64 consecutive TMEM columns with one wait
+ADS_D void tmem_ld64(uint32_t taddr, float v[64]) {
+  uint32_t r0[32], r1[32];
+  tmem_ld32_async(taddr, r0);
+  tmem_ld32_async(taddr + 32, r1);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  reg_pin32(r0);
+  reg_pin32(r1);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    v[j] = __uint_as_float(r0[j]);
+    v[32 + j] = __uint_as_float(r1[j]);
+  }
+}
 
 ADS_D uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -299,26 +340,28 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
       phase ^= 1;
       tc_fence_after();
       const float* bl = fb + (l + 1) * W;
+      unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * W * 2 : nullptr;
+      for (int c0 = 0; c0 < W; c0 += 64) {
+        float d[64];
+        tmem_ld64(lane_base + c0, d);  // 64 columns, one wait
 #pragma unroll
-      for (int c = 0; c < W; c += 16) {
-        float d[16];
-        tmem_ld16(lane_base + c, d);
-        float v[16];
+        for (int c = 0; c < 64; c += 16) {
+          float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[j] + bl[c + j]);
-        if (l < 2) {
-          st_atom_split(act, actlo, RG, tid, c, v);
-          st_atom_split(act, actlo, RG, tid, c + 8, v + 8);
-        }
-        unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * W * 2 : nullptr;
-        if (g) {
-          st_atom(g, RG, tid, c, v);
-          st_atom(g, RG, tid, c + 8, v + 8);
-        }
-        if (l == 2) {
-          // the output layer in FP32 from the unrounded activations
+          for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[c + j] + bl[c0 + c + j]);
+          if (l < 2) {
+            st_atom_split(act, actlo, RG, tid, c0 + c, v);
+            st_atom_split(act, actlo, RG, tid, c0 + c + 8, v + 8);
+          }
+          if (g) {
+            st_atom(g, RG, tid, c0 + c, v);
+            st_atom(g, RG, tid, c0 + c + 8, v + 8);
+          }
+          if (l == 2) {
+            // the output layer in FP32 from the unrounded activations
 #pragma unroll
-          for (int j = 0; j < 16; ++j) u += fW5[c + j] * v[j];
+            for (int j = 0; j < 16; ++j) u += fW5[c0 + c + j] * v[j];
+          }
         }
       }
     }
@@ -330,11 +373,19 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
 
 // ---------------------------------------------------------------------------
 // backward, width 64: every gradient on the tensor cores, one CTA per SM (the
-// accumulators fill the 512 TMEM columns).  The four stored activation tiles
-// of a point tile (64 KB, the forward's layout) arrive by one bulk copy into a
-// double buffer, the next tile's copy running under the current tile's
-// products.  Bias gradients come from a second product against a constant
-// ones tile; the delta tiles are zero-padded to M = 128.
+// accumulators fill the 512 TMEM columns).  Warp-specialised: warps 0-3 own
+// the 128 point rows of a tile (delta epilogues), warp 4 issues every product.
+// A product is a single-thread instruction that takes tens of cycles to issue
+// while these shapes (N = 16..64) take fewer cycles to run, so only each
+// layer's delta product Delta_L W_L sits on the epilogues' path; the weight
+// and bias gradient products run under the epilogues.  One thread issues all
+// products of an accumulator, in a fixed order (deterministic sums); products
+// complete in issue order.  The four stored activation tiles of a point tile
+// (64 KB, the forward's layout) arrive by one bulk copy into a double buffer,
+// the next tile's copy running under the current tile.  Bias gradients come
+// from a product against a constant ones tile; delta tiles are zero-padded to
+// M = 128.
+constexpr int kBwdThreads = kTP + 32;  // four epilogue warps, one issuing warp
 struct TcSmemB {
   static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
   static constexpr int ACT_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
@@ -344,8 +395,8 @@ struct TcSmemB {
   static constexpr int XIN = DEL + 2 * DEL_SZ;             // [128][16] bf16: x', 1, 0  4 KB
   static constexpr int ONES = XIN + kTP * kXP * 2;         // [128][16] bf16: 1, 0     4 KB
   static constexpr int VEC = ONES + kTP * kXP * 2;         // fp32: W5 [64]
-  static constexpr int BAR = VEC + kW * 4;                 // 3 mbarriers, tmem base, abort flag
-  static constexpr int TOTAL = BAR + 48;
+  static constexpr int BAR = VEC + kW * 4;                 // 5 mbarriers, tmem base, abort flag
+  static constexpr int TOTAL = BAR + 64;
 };
 // TMEM columns: delta product [0,64), dW5 [64,144), dW4 [144,224),
 // dW3 [224,304), dW2 [304,384), dW1 [384,400); in each dW block the weight
@@ -365,9 +416,12 @@ ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
                : "memory");
 }
+ADS_D void mbar_arrive1(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
 
 template <int DIN>
-__global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
+__global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemB::W;
   unsigned char* act = sm + TcSmemB::ACT;  // [buffer][a_1..a_4]
@@ -375,19 +429,24 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   unsigned char* xin = sm + TcSmemB::XIN;
   unsigned char* ones = sm + TcSmemB::ONES;
   float* fW5 = reinterpret_cast<float*>(sm + TcSmemB::VEC);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB::BAR);  // [0] products, [1], [2] loads
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 24);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 28);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB::BAR);
+  uint64_t* mb_prod = mbar;       // delta product of a layer complete (issuer commit)
+  uint64_t* mb_load = mbar + 1;   // [2] activation buffers loaded (bulk copy)
+  uint64_t* mb_ready = mbar + 3;  // a delta tile written (one arrive per epilogue warp)
+  uint64_t* mb_done = mbar + 4;   // every product of a tile complete (issuer commit)
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 40);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 44);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool epi = tid < kTP;
   constexpr int RGW = (kW / 8) * 128, RGD = (kDP / 8) * 128, RGX = (kXP / 8) * 128;
   constexpr uint32_t kTileBytes = 4 * TcSmemB::ACT_SZ;
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
   const int ntiles = (a.npts + kTP - 1) / kTP;
-  load_hidden_weights<kW>(th, o2, wt, tid, kTP);
-  for (int i = tid; i < kW; i += kTP) fW5[i] = th[o5 + i];
-  // constant tiles: the ones column, the zero padding of the delta tiles
-  {
+  if (epi) {
+    load_hidden_weights<kW>(th, o2, wt, tid, kTP);
+    for (int i = tid; i < kW; i += kTP) fW5[i] = th[o5 + i];
+    // constant tiles: the ones column, the zero padding of the delta tiles
     float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     st_atom(ones, RGX, tid, 0, one);
     st_atom(ones, RGX, tid, 8, zero);
@@ -396,8 +455,11 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   }
   if (tid == 0) {
     *abort_flag = 0;
-    for (int i = 0; i < 3; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + i)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_prod)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_load)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_load + 1)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(mb_ready)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_done)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -409,69 +471,48 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // the first tile's activations
-  if (tid == 0 && (int)blockIdx.x < ntiles) {
-    mbar_expect(mbar + 1, kTileBytes);
-    bulk_load(act, a.acts + (size_t)blockIdx.x * kTileBytes, kTileBytes, mbar + 1);
-  }
   const uint32_t tmem = *tbase;
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-  const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
-                 xin_s = smem_addr(xin), ones_s = smem_addr(ones);
-  const uint32_t id_dw = idesc_bf16(kDP, kW, 1, 1);   // dW_l weights: M = 128 (o), N = 64, K = points
-  const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // bias column (and dW_1): N = 16
-  const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
-  uint32_t phase = 0;           // product barrier
-  uint32_t lphase = 0;          // load barriers: bit b = phase of barrier 1 + b
-  bool aborted = false;
-  bool first = true;  // first tile of this CTA: overwrite the dW accumulators
-  bool pending = false;  // a prefetch was issued and not yet waited for
-  auto wait_mma = [&]() {
-    if (!mbar_wait(mbar, phase)) *abort_flag = 1;
-    phase ^= 1;
-    tc_fence_after();
-  };
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int buf = it & 1;
-    unsigned char* actb = act + buf * 4 * TcSmemB::ACT_SZ;
-    const uint32_t actb_s = act_s + buf * 4 * TcSmemB::ACT_SZ;
-    const int p0 = tile * kTP;
-    const int idx = p0 + tid;
-    const float g = idx < a.npts ? a.gu[idx] : 0.0f;
-    {
-      float x[3];
-      coords<DIN>(min(idx, a.npts - 1), a.N, x);
-      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int d = 0; d < DIN; ++d) v[d] = x[d];
-      v[DIN] = 1.0f;
-      st_atom(xin, RGX, tid, 0, v);
-      st_atom(xin, RGX, tid, 8, z);
-      // Delta_5 = [g, 0, ..., 0] in delta tile 0
-      float d5[8] = {g, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      st_atom(del, RGD, tid, 0, d5);
-      for (int c = 8; c < kW; c += 8) st_atom(del, RGD, tid, c, z);
+  bool first = true;  // this CTA has not finished a tile
+
+  if (tid == kTP) {
+    // ---------------- issuing thread ----------------
+    const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
+                   xin_s = smem_addr(xin), ones_s = smem_addr(ones);
+    const uint32_t id_dw = idesc_bf16(kDP, kW, 1, 1);   // dW_l weights: M = 128 (o), N = 64, K = points
+    const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // bias column (and dW_1): N = 16
+    const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
+    uint32_t ph_ready = 0, ph_done = 0, lph = 0;
+    int pend = -1;  // buffer whose bulk copy is in flight (at most one), or -1
+    auto fail = [&]() { *abort_flag = 1; };
+    if ((int)blockIdx.x < ntiles) {
+      mbar_expect(mb_load, kTileBytes);
+      bulk_load(act, a.acts + (size_t)blockIdx.x * kTileBytes, kTileBytes, mb_load);
+      pend = 0;
     }
-    // this tile's activations
-    if (!mbar_wait(mbar + 1 + buf, (lphase >> buf) & 1u)) *abort_flag = 1;
-    lphase ^= 1u << buf;
-    pending = false;
-    if (sync_abort(abort_flag)) {
-      aborted = true;
-      break;
-    }
-    // the next tile's activations into the other buffer (its previous
-    // readers, the products and epilogues of the tile before, are done)
-    if (tile + (int)gridDim.x < ntiles) {
-      pending = true;
-      if (tid == 0) {
-        mbar_expect(mbar + 2 - buf, kTileBytes);
-        bulk_load(act + (1 - buf) * 4 * TcSmemB::ACT_SZ,
-                  a.acts + (size_t)(tile + gridDim.x) * kTileBytes, kTileBytes, mbar + 2 - buf);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+      const int buf = it & 1;
+      const uint32_t actb_s = act_s + buf * kTileBytes;
+      if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { fail(); break; }
+      lph ^= 1u << buf;
+      pend = -1;
+      // the previous tile's products have read the other buffer: wait for
+      // them, then fetch the next tile into it
+      if (it > 0) {
+        if (!mbar_wait(mb_done, ph_done)) { fail(); break; }
+        ph_done ^= 1;
       }
-    }
-    // output layer: dW_5 (row 0) and db_5 from Delta_5^T [a_4 | 1]
-    if (tid == 0) {
+      if (tile + (int)gridDim.x < ntiles) {
+        mbar_expect(mb_load + 1 - buf, kTileBytes);
+        bulk_load(act + (1 - buf) * kTileBytes, a.acts + (size_t)(tile + gridDim.x) * kTileBytes,
+                  kTileBytes, mb_load + 1 - buf);
+        pend = 1 - buf;
+      }
+      // Delta_5, x' and Delta_4 written
+      if (!mbar_wait(mb_ready, ph_ready)) { fail(); break; }
+      ph_ready ^= 1;
+      tc_fence_after();
+      // output layer: dW_5 (row 0) and db_5 from Delta_5^T [a_4 | 1]
 #pragma unroll
       for (int ks = 0; ks < kTP / 16; ++ks) {
         const uint64_t da = desc_mn(del_s, RGD, ks);
@@ -479,28 +520,22 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
         mma_bf16(tmem + col_dw(5), da, desc_mn(actb_s + 3 * TcSmemB::ACT_SZ, RGW, ks), id_dw, acc);
         mma_bf16(tmem + col_dw(5) + kW, da, desc_mn(ones_s, RGX, ks), id_db, acc);
       }
-    }
-    // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1
-    {
-      unsigned char* d4 = del + TcSmemB::DEL_SZ;
+      int cur = 1;  // delta tile holding Delta_L
+      bool bad = false;
+      for (int L = 4; L >= 2; --L) {
+        if (L < 4) {
+          if (!mbar_wait(mb_ready, ph_ready)) { bad = true; break; }
+          ph_ready ^= 1;
+          tc_fence_after();
+        }
+        const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
+        const uint32_t ain = actb_s + (L - 2) * TcSmemB::ACT_SZ;  // a_{L-1}
+        const uint32_t wl = wt_s + (L - 2) * kW * kW * 2;
+        // Delta_L W_L, then its commit: the epilogues wait for this alone
 #pragma unroll
-      for (int c = 0; c < kW; c += 8) {
-        float av[8], v[8];
-        ld_atom(actb + 3 * TcSmemB::ACT_SZ, RGW, tid, c, av);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
-        st_atom(d4, RGD, tid, c, v);
-      }
-    }
-    int cur = 1;  // delta tile holding Delta_L
-    for (int L = 4; L >= 2; --L) {
-      if (sync_abort(abort_flag)) {
-        aborted = true;
-        break;
-      }
-      const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
-      const uint32_t ain = actb_s + (L - 2) * TcSmemB::ACT_SZ;  // a_{L-1}
-      if (tid == 0) {
+        for (int ks = 0; ks < kW / 16; ++ks)
+          mma_bf16(tmem + kColDel, desc_k(dcur, RGD, ks), desc_mn(wl, RGW, ks), id_dp, ks > 0);
+        mma_commit(mb_prod);
         // dW_L, db_L += Delta_L^T [a_{L-1} | 1]
 #pragma unroll
         for (int ks = 0; ks < kTP / 16; ++ks) {
@@ -509,99 +544,156 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tc(MlpTcArgs a) {
           mma_bf16(tmem + col_dw(L), da, desc_mn(ain, RGW, ks), id_dw, acc);
           mma_bf16(tmem + col_dw(L) + kW, da, desc_mn(ones_s, RGX, ks), id_db, acc);
         }
-        // Delta_L W_L
-        const uint32_t wl = wt_s + (L - 2) * kW * kW * 2;
-#pragma unroll
-        for (int ks = 0; ks < kW / 16; ++ks)
-          mma_bf16(tmem + kColDel, desc_k(dcur, RGD, ks), desc_mn(wl, RGW, ks), id_dp, ks > 0);
-        mma_commit(mbar);
+        cur = 1 - cur;
       }
-      wait_mma();
-      // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
-      unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
-      const unsigned char* aprev = actb + (L - 2) * TcSmemB::ACT_SZ;
+      if (bad) { fail(); break; }
+      // Delta_1 written: dW_1, db_1 += Delta_1^T [x' | 1]
+      if (!mbar_wait(mb_ready, ph_ready)) { fail(); break; }
+      ph_ready ^= 1;
+      tc_fence_after();
+      {
+        const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
 #pragma unroll
-      for (int c = 0; c < kW; c += 16) {
-        float dv[16];
-        tmem_ld16(lane_base + kColDel + c, dv);
-        float av[8], v[8];
-        ld_atom(aprev, RGW, tid, c, av);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = dv[j] * (1.0f - av[j] * av[j]);
-        st_atom(dn, RGD, tid, c, v);
-        ld_atom(aprev, RGW, tid, c + 8, av);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = dv[8 + j] * (1.0f - av[j] * av[j]);
-        st_atom(dn, RGD, tid, c + 8, v);
+        for (int ks = 0; ks < kTP / 16; ++ks)
+          mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s, RGX, ks), id_db,
+                   (ks > 0 || !first) ? 1u : 0u);
       }
-      cur = 1 - cur;
+      mma_commit(mb_done);
+      first = false;
     }
-    if (aborted) break;
-    // first layer: dW_1, db_1 += Delta_1^T [x' | 1]
-    if (sync_abort(abort_flag)) {
-      aborted = true;
-      break;
-    }
-    if (tid == 0) {
-      const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
+    // a prefetch still in flight after an abort must land before the CTA's
+    // shared memory is released
+    if (*abort_flag && pend >= 0) mbar_wait(mb_load + pend, (lph >> pend) & 1u);
+  } else if (epi) {
+    // ---------------- epilogue warps: point row tid ----------------
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    uint32_t ph_prod = 0, ph_done = 0, lph = 0;
+    auto arrive_ready = [&]() {
+      fence_async_smem();  // generic stores before the tensor cores read them
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(mb_ready);
+    };
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+      const int buf = it & 1;
+      const unsigned char* actb = act + buf * kTileBytes;
+      const int idx = tile * kTP + tid;
+      const float g = idx < a.npts ? a.gu[idx] : 0.0f;
+      float x[3];
+      coords<DIN>(min(idx, a.npts - 1), a.N, x);
+      // the previous tile's products read x' and the delta tiles
+      if (it > 0) {
+        if (!mbar_wait(mb_done, ph_done)) { *abort_flag = 1; break; }
+        ph_done ^= 1;
+        tc_fence_after();
+      }
+      {
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int d = 0; d < DIN; ++d) v[d] = x[d];
+        v[DIN] = 1.0f;
+        st_atom(xin, RGX, tid, 0, v);
+        st_atom(xin, RGX, tid, 8, z);
+        // Delta_5 = [g, 0, ..., 0] in delta tile 0
+        float d5[8] = {g, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        st_atom(del, RGD, tid, 0, d5);
+        for (int c = 8; c < kW; c += 8) st_atom(del, RGD, tid, c, z);
+      }
+      if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { *abort_flag = 1; break; }
+      lph ^= 1u << buf;
+      // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1
+      {
+        unsigned char* d4 = del + TcSmemB::DEL_SZ;
 #pragma unroll
-      for (int ks = 0; ks < kTP / 16; ++ks)
-        mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s, RGX, ks), id_db,
-                 (ks > 0 || !first) ? 1u : 0u);
-      mma_commit(mbar);
-    }
-    wait_mma();  // all of this tile's products are complete before its tiles are reused
-    first = false;
-  }
-  // after an abort a prefetch may still be in flight: it must land before
-  // the CTA's shared memory is released (bounded wait on its barrier)
-  aborted = sync_abort(abort_flag);
-  if (aborted && pending && tid == 0) {
-    const int nb = 1 - (it & 1);
-    mbar_wait(mbar + 1 + nb, (lphase >> nb) & 1u);
-  }
-  // gradient row of this CTA: TMEM lane o = thread; rows o >= 64 are padding.
-  // Every thread issues the same TMEM loads (they are warp-collective).
-  float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
-  const int o = tid;
-  if (!aborted && !first) {
-    for (int L = 4; L >= 2; --L) {
-      const int ow = o2 + (L - 2) * (kW * kW + kW);
-      for (int c = 0; c < kWP; c += 16) {
-        float v[16];
-        tmem_ld16(lane_base + col_dw(L) + c, v);
-        if (o < kW) {
+        for (int c = 0; c < kW; c += 8) {
+          float av[8], v[8];
+          ld_atom(actb + 3 * TcSmemB::ACT_SZ, RGW, tid, c, av);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int k = c + j;
-            if (k < kW) gacc[ow + o * kW + k] = v[j];
-            else if (k == kW) gacc[ow + kW * kW + o] = v[j];
+          for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
+          st_atom(d4, RGD, tid, c, v);
+        }
+      }
+      arrive_ready();
+      int cur = 1;
+      bool bad = false;
+      for (int L = 4; L >= 2; --L) {
+        if (!mbar_wait(mb_prod, ph_prod)) { bad = true; break; }
+        ph_prod ^= 1;
+        tc_fence_after();
+        // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
+        unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
+        const unsigned char* aprev = actb + (L - 2) * TcSmemB::ACT_SZ;
+        float dv[64];
+        tmem_ld64(lane_base + kColDel, dv);
+#pragma unroll
+        for (int c = 0; c < kW; c += 8) {
+          float av[8], v[8];
+          ld_atom(aprev, RGW, tid, c, av);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = dv[c + j] * (1.0f - av[j] * av[j]);
+          st_atom(dn, RGD, tid, c, v);
+        }
+        arrive_ready();
+        cur = 1 - cur;
+      }
+      if (bad) { *abort_flag = 1; break; }
+      first = false;
+    }
+    // the last tile's products, before the accumulators are read
+    if (!first && !*abort_flag) {
+      if (!mbar_wait(mb_done, ph_done)) *abort_flag = 1;
+      tc_fence_after();
+    }
+  }
+  __syncthreads();
+  const bool aborted = *abort_flag != 0;
+  if (epi) {
+    // gradient row of this CTA: TMEM lane o = thread; rows o >= 64 are
+    // padding.  Every epilogue thread issues the same TMEM loads (they are
+    // warp-collective).
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
+    const int o = tid;
+    const bool had_tiles = (int)blockIdx.x < ntiles;
+    if (!aborted && had_tiles) {
+      for (int L = 4; L >= 2; --L) {
+        const int ow = o2 + (L - 2) * (kW * kW + kW);
+        for (int c = 0; c < kWP; c += 16) {
+          float v[16];
+          tmem_ld16(lane_base + col_dw(L) + c, v);
+          if (o < kW) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int k = c + j;
+              if (k < kW) gacc[ow + o * kW + k] = v[j];
+              else if (k == kW) gacc[ow + kW * kW + o] = v[j];
+            }
           }
         }
       }
-    }
-    {
-      float v[16];
-      tmem_ld16(lane_base + col_dw(1), v);
-      if (o < kW) {
-        for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
-        gacc[ob1 + o] = v[DIN];
-      }
-    }
-    for (int c = 0; c < kWP; c += 16) {
-      float v[16];
-      tmem_ld16(lane_base + col_dw(5) + c, v);
-      if (o == 0) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int k = c + j;
-          if (k < kW) gacc[o5 + k] = v[j];
-          else if (k == kW) gacc[o5 + kW] = v[j];
+      {
+        float v[16];
+        tmem_ld16(lane_base + col_dw(1), v);
+        if (o < kW) {
+          for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
+          gacc[ob1 + o] = v[DIN];
         }
       }
+      for (int c = 0; c < kWP; c += 16) {
+        float v[16];
+        tmem_ld16(lane_base + col_dw(5) + c, v);
+        if (o == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int k = c + j;
+            if (k < kW) gacc[o5 + k] = v[j];
+            else if (k == kW) gacc[o5 + kW] = v[j];
+          }
+        }
+      }
+    } else if (!had_tiles) {
+      for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;  // CTA without tiles
     }
-  } else if (first && !aborted) {
-    for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;  // CTA without tiles
   }
   if (aborted && tid == 0) atomicOr(a.flags, 8);
   tc_fence_before();
@@ -963,7 +1055,7 @@ cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
     const size_t smem = TcSmemB::TOTAL;
     auto k = a.din == 2 ? k_mlp_bwd_tc<2> : k_mlp_bwd_tc<3>;
     smem_optin(k);
-    k<<<nblk, kTP, smem, st>>>(a);
+    k<<<nblk, kBwdThreads, smem, st>>>(a);
     return cudaGetLastError();
   }
   if (a.width == 128) return a.din == 2 ? bwd_tc<128, 2>(a, nblk, st) : bwd_tc<128, 3>(a, nblk, st);
