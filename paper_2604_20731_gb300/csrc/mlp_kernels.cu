@@ -507,14 +507,32 @@ cudaError_t launch_mlp_bwd(const MlpArgs<T>& a, int nblk, cudaStream_t st) {
 
 // grad = sum over CTA partial rows (fixed order); Adam (Kingma & Ba) with
 // beta1 = 0.9, beta2 = 0.999, eps = 1e-8; bc = bias corrections 1/(1-beta^t).
+// Sum of the per-block gradient partials and the Adam step.  A block covers
+// 32 parameters; its 8 warps take every 8th partial (two accumulation chains
+// each, for memory-level parallelism) and warp 0 adds the 8 warp sums in a
+// fixed order (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(256) k_grad_adam(const T* __restrict__ gpart, int nblk,
                                                    int nparams, T* grad, T* theta, T* m, T* v,
                                                    const double* bc, const double* lr, int upd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nparams) return;
+  __shared__ T part[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + tx;
+  T s0 = T(0), s1 = T(0);
+  if (i < nparams) {
+    int b = ty;
+    for (; b + 8 < nblk; b += 16) {
+      s0 += gpart[(size_t)b * nparams + i];
+      s1 += gpart[(size_t)(b + 8) * nparams + i];
+    }
+    if (b < nblk) s0 += gpart[(size_t)b * nparams + i];
+  }
+  part[ty][tx] = s0 + s1;
+  __syncthreads();
+  if (ty != 0 || i >= nparams) return;
   T g = T(0);
-  for (int b = 0; b < nblk; ++b) g += gpart[(size_t)b * nparams + i];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) g += part[k][tx];
   grad[i] = g;
   if (!upd) return;
   const T b1 = T(0.9), b2 = T(0.999), eps = T(1e-8);
@@ -531,8 +549,8 @@ template <typename T>
 cudaError_t launch_grad_reduce_adam(const T* gpart, int nblk, int nparams, T* grad, T* theta, T* m,
                                     T* v, const double* bc, const double* lr, int do_update,
                                     cudaStream_t st) {
-  k_grad_adam<T><<<(nparams + 255) / 256, 256, 0, st>>>(gpart, nblk, nparams, grad, theta, m, v,
-                                                         bc, lr, do_update);
+  k_grad_adam<T><<<(nparams + 31) / 32, 256, 0, st>>>(gpart, nblk, nparams, grad, theta, m, v, bc,
+                                                       lr, do_update);
   return cudaGetLastError();
 }
 
