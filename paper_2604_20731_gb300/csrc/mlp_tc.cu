@@ -372,20 +372,23 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// backward, width 64: every gradient on the tensor cores, one CTA per SM (the
-// accumulators fill the 512 TMEM columns).  Warp-specialised: warps 0-3 own
-// the 128 point rows of a tile (delta epilogues), warp 4 issues every product.
-// A product is a single-thread instruction that takes tens of cycles to issue
-// while these shapes (N = 16..64) take fewer cycles to run, so only each
-// layer's delta product Delta_L W_L sits on the epilogues' path; the weight
-// and bias gradient products run under the epilogues.  One thread issues all
-// products of an accumulator, in a fixed order (deterministic sums); products
-// complete in issue order.  The four stored activation tiles of a point tile
-// (64 KB, the forward's layout) arrive by one bulk copy into a double buffer,
-// the next tile's copy running under the current tile.  Bias gradients come
-// from a product against a constant ones tile; delta tiles are zero-padded to
-// M = 128.
-constexpr int kBwdThreads = kTP + 32;  // four epilogue warps, one issuing warp
+// backward, width 64: the products on the tensor cores, one CTA per SM (the
+// accumulators fill the 512 TMEM columns).  Warp-specialised: warps 0-7 run
+// the delta epilogues (point row tid % 128, feature columns 32 (tid / 128) ..
+// + 32), warp 8 issues every product.  A product is a single-thread
+// instruction that takes tens of cycles to issue while these shapes (N = 16..64)
+// take fewer cycles to run, so only each layer's delta product Delta_L W_L
+// sits on the epilogues' path; the weight and bias gradient products run under
+// the epilogues.  One thread issues all products of an accumulator, in a fixed
+// order (deterministic sums); products complete in issue order.  The output
+// layer's gradient (a_4^T g, sum g) is a per-thread running sum over the CTA's
+// tiles, reduced over the rows once at the end in a fixed order.  The four
+// stored activation tiles of a point tile (64 KB, the forward's layout) arrive
+// by one bulk copy into a double buffer, the next tile's copy running under
+// the current tile.  Bias gradients come from a product against a constant
+// ones tile; delta tiles are zero-padded to M = 128.
+constexpr int kBwdEpi = 2 * kTP;          // epilogue threads: two per point row
+constexpr int kBwdThreads = kBwdEpi + 32;  // eight epilogue warps, one issuing warp
 struct TcSmemB {
   static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
   static constexpr int ACT_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
@@ -437,28 +440,31 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 40);
   volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 44);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool epi = tid < kTP;
+  const bool epi = tid < kBwdEpi;
+  const int row = tid & (kTP - 1), c0 = 32 * (tid >> 7);  // epilogue: point row, first column
   constexpr int RGW = (kW / 8) * 128, RGD = (kDP / 8) * 128, RGX = (kXP / 8) * 128;
   constexpr uint32_t kTileBytes = 4 * TcSmemB::ACT_SZ;
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
   const int ntiles = (a.npts + kTP - 1) / kTP;
   if (epi) {
-    load_hidden_weights<kW>(th, o2, wt, tid, kTP);
-    for (int i = tid; i < kW; i += kTP) fW5[i] = th[o5 + i];
+    load_hidden_weights<kW>(th, o2, wt, tid, kBwdEpi);
+    for (int i = tid; i < kW; i += kBwdEpi) fW5[i] = th[o5 + i];
     // constant tiles: the ones column, the zero padding of the delta tiles
     float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    st_atom(ones, RGX, tid, 0, one);
-    st_atom(ones, RGX, tid, 8, zero);
+    if (c0 == 0) {
+      st_atom(ones, RGX, row, 0, one);
+      st_atom(ones, RGX, row, 8, zero);
+    }
     for (int b = 0; b < 2; ++b)
-      for (int c = kW; c < kDP; c += 8) st_atom(del + b * TcSmemB::DEL_SZ, RGD, tid, c, zero);
+      for (int c = kW + c0; c < kW + c0 + 32; c += 8) st_atom(del + b * TcSmemB::DEL_SZ, RGD, row, c, zero);
   }
   if (tid == 0) {
     *abort_flag = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_prod)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_load)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_load + 1)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(mb_ready)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(mb_ready)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_done)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -474,7 +480,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   const uint32_t tmem = *tbase;
   bool first = true;  // this CTA has not finished a tile
 
-  if (tid == kTP) {
+  float acc5[32];  // epilogue: running sums of g a_4 over the CTA's tiles (this row, 32 columns)
+  float acc5b = 0.0f;  // and of g
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc5[j] = 0.0f;
+  if (tid == kBwdEpi) {
     // ---------------- issuing thread ----------------
     const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
                    xin_s = smem_addr(xin), ones_s = smem_addr(ones);
@@ -508,18 +518,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
                   kTileBytes, mb_load + 1 - buf);
         pend = 1 - buf;
       }
-      // Delta_5, x' and Delta_4 written
+      // x' and Delta_4 written
       if (!mbar_wait(mb_ready, ph_ready)) { fail(); break; }
       ph_ready ^= 1;
       tc_fence_after();
-      // output layer: dW_5 (row 0) and db_5 from Delta_5^T [a_4 | 1]
-#pragma unroll
-      for (int ks = 0; ks < kTP / 16; ++ks) {
-        const uint64_t da = desc_mn(del_s, RGD, ks);
-        const uint32_t acc = (ks > 0 || !first) ? 1u : 0u;
-        mma_bf16(tmem + col_dw(5), da, desc_mn(actb_s + 3 * TcSmemB::ACT_SZ, RGW, ks), id_dw, acc);
-        mma_bf16(tmem + col_dw(5) + kW, da, desc_mn(ones_s, RGX, ks), id_db, acc);
-      }
       int cur = 1;  // delta tile holding Delta_L
       bool bad = false;
       for (int L = 4; L >= 2; --L) {
@@ -565,8 +567,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     // shared memory is released
     if (*abort_flag && pend >= 0) mbar_wait(mb_load + pend, (lph >> pend) & 1u);
   } else if (epi) {
-    // ---------------- epilogue warps: point row tid ----------------
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    // ---------------- epilogue warps: point row `row`, columns c0 .. c0 + 32 ----------------
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t ph_prod = 0, ph_done = 0, lph = 0;
     auto arrive_ready = [&]() {
       fence_async_smem();  // generic stores before the tensor cores read them
@@ -575,11 +577,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       if (lane == 0) mbar_arrive1(mb_ready);
     };
     int it = 0;
+    // dL/du of this row: loaded one tile ahead
+    float g_next = 0.0f;
+    if ((int)blockIdx.x < ntiles) {
+      const int i0 = blockIdx.x * kTP + row;
+      g_next = i0 < a.npts ? a.gu[i0] : 0.0f;
+    }
     for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       const int buf = it & 1;
       const unsigned char* actb = act + buf * kTileBytes;
-      const int idx = tile * kTP + tid;
-      const float g = idx < a.npts ? a.gu[idx] : 0.0f;
+      const int idx = tile * kTP + row;
+      const float g = g_next;
+      if (tile + (int)gridDim.x < ntiles) {
+        const int i1 = idx + (int)gridDim.x * kTP;
+        g_next = i1 < a.npts ? a.gu[i1] : 0.0f;
+      }
       float x[3];
       coords<DIN>(min(idx, a.npts - 1), a.N, x);
       // the previous tile's products read x' and the delta tiles
@@ -588,30 +600,30 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         ph_done ^= 1;
         tc_fence_after();
       }
-      {
+      if (c0 == 0) {
         float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int d = 0; d < DIN; ++d) v[d] = x[d];
         v[DIN] = 1.0f;
-        st_atom(xin, RGX, tid, 0, v);
-        st_atom(xin, RGX, tid, 8, z);
-        // Delta_5 = [g, 0, ..., 0] in delta tile 0
-        float d5[8] = {g, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        st_atom(del, RGD, tid, 0, d5);
-        for (int c = 8; c < kW; c += 8) st_atom(del, RGD, tid, c, z);
+        st_atom(xin, RGX, row, 0, v);
+        st_atom(xin, RGX, row, 8, z);
       }
       if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { *abort_flag = 1; break; }
       lph ^= 1u << buf;
-      // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1
+      // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1; output-layer sums
       {
         unsigned char* d4 = del + TcSmemB::DEL_SZ;
 #pragma unroll
-        for (int c = 0; c < kW; c += 8) {
+        for (int c = 0; c < 32; c += 8) {
           float av[8], v[8];
-          ld_atom(actb + 3 * TcSmemB::ACT_SZ, RGW, tid, c, av);
+          ld_atom(actb + 3 * TcSmemB::ACT_SZ, RGW, row, c0 + c, av);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = fW5[c + j] * g * (1.0f - av[j] * av[j]);
-          st_atom(d4, RGD, tid, c, v);
+          for (int j = 0; j < 8; ++j) {
+            v[j] = fW5[c0 + c + j] * g * (1.0f - av[j] * av[j]);
+            acc5[c + j] += g * av[j];
+          }
+          st_atom(d4, RGD, row, c0 + c, v);
         }
+        acc5b += g;
       }
       arrive_ready();
       int cur = 1;
@@ -623,15 +635,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
         unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
         const unsigned char* aprev = actb + (L - 2) * TcSmemB::ACT_SZ;
-        float dv[64];
-        tmem_ld64(lane_base + kColDel, dv);
+        uint32_t dr[32];
+        tmem_ld32_async(lane_base + kColDel + c0, dr);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        reg_pin32(dr);
 #pragma unroll
-        for (int c = 0; c < kW; c += 8) {
+        for (int c = 0; c < 32; c += 8) {
           float av[8], v[8];
-          ld_atom(aprev, RGW, tid, c, av);
+          ld_atom(aprev, RGW, row, c0 + c, av);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = dv[c + j] * (1.0f - av[j] * av[j]);
-          st_atom(dn, RGD, tid, c, v);
+          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(dr[c + j]) * (1.0f - av[j] * av[j]);
+          st_atom(dn, RGD, row, c0 + c, v);
         }
         arrive_ready();
         cur = 1 - cur;
@@ -647,14 +661,30 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   }
   __syncthreads();
   const bool aborted = *abort_flag != 0;
-  if (epi) {
+  const bool had_tiles = (int)blockIdx.x < ntiles;
+  float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
+  // output layer: the rows' running sums through shared memory (the
+  // activation buffers are idle now), added over the rows in a fixed order
+  if (!aborted && had_tiles) {
+    float* red = reinterpret_cast<float*>(act);  // [128 rows][65]
+    if (epi) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) red[row * 65 + c0 + j] = acc5[j];
+      if (c0 == 0) red[row * 65 + kW] = acc5b;
+    }
+    __syncthreads();
+    if (tid <= kW) {
+      float sum = 0.0f;
+      for (int r = 0; r < kTP; ++r) sum += red[r * 65 + tid];
+      gacc[o5 + tid] = sum;
+    }
+  }
+  if (tid < kTP) {
     // gradient row of this CTA: TMEM lane o = thread; rows o >= 64 are
-    // padding.  Every epilogue thread issues the same TMEM loads (they are
-    // warp-collective).
+    // padding.  Every thread of warps 0-3 issues the same TMEM loads (they
+    // are warp-collective).
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
     const int o = tid;
-    const bool had_tiles = (int)blockIdx.x < ntiles;
     if (!aborted && had_tiles) {
       for (int L = 4; L >= 2; --L) {
         const int ow = o2 + (L - 2) * (kW * kW + kW);
@@ -677,18 +707,6 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         if (o < kW) {
           for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
           gacc[ob1 + o] = v[DIN];
-        }
-      }
-      for (int c = 0; c < kWP; c += 16) {
-        float v[16];
-        tmem_ld16(lane_base + col_dw(5) + c, v);
-        if (o == 0) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int k = c + j;
-            if (k < kW) gacc[o5 + k] = v[j];
-            else if (k == kW) gacc[o5 + kW] = v[j];
-          }
         }
       }
     } else if (!had_tiles) {
