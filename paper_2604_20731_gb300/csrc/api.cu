@@ -317,8 +317,14 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   const int m = c->m1;
   const TC h = TC(1.0 / c->N);
   LK(0, launch_fwd<TC>(c, true));
-  LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->u,
-                           (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr, c->stream));
+  if (c->dim == 2 && c->gram_fft) {
+    // the residual is computed inside the first transform pass
+    if (c->prof) cudaEventRecord(c->prof[1], c->stream);
+  } else {
+    LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha,
+                             (const TC*)c->u, (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr,
+                             c->stream));
+  }
   if (c->dim == 3) {
     // G^-1 r: sine transforms along x (one GEMM over all (z, y) rows) and y
     // (batched over z), shifted tridiagonal sweeps along z, inverse transforms
@@ -337,7 +343,8 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
     for (int pass = 0; pass < 3; ++pass)
       LK(2 + pass, launch_gram_fft<TC>(pass, c->N, (const TC*)c->res, (TC*)c->rhat, (TC*)c->z,
                                        (const TC*)c->gtw, (const TC*)c->glam, h * h, c->dot_part,
-                                       c->stream));
+                                       c->stream, (const TC*)c->u, (const TC*)c->alpha,
+                                       (const TC*)c->f, (TC*)c->res));
   } else {
     LK(2, launch_gemm<TC>(m, m, m, (const TC*)c->res, m, (const TC*)c->Sdst, m, (TC*)c->rhat, m,
                           TC(1), nullptr, nullptr, c->stream));

@@ -105,13 +105,42 @@ __device__ __forceinline__ T odd_ext(const T* v, int j, int N, int stride) {
   return T(0);
 }
 
+// RES = A u + h^2 f on the interior nodes (Eqs. 24-25, 5-point form): the
+// residual the first row pass computes itself when given the network values
+template <typename T>
+struct ResidualIn {
+  const T* u;      // network values on the interior nodes, [m][m]; nullptr: read `in`
+  const T* alpha;  // coefficients on all nodes, [N+1][N+1]
+  const T* f;      // right-hand side on the interior nodes, [m][m]
+  T h2;
+  T* res;          // written: RES, [m][m]
+};
+template <typename T>
+__device__ __forceinline__ T residual_at(const ResidualIn<T>& q, int N, int jj, int ii) {
+  const int m = N - 1, n1 = N + 1;
+  const size_t t = (size_t)jj * m + ii;
+  const int j = jj + 1, i = ii + 1;  // node index
+  const T c = q.u[t];
+  const T w = ii > 0 ? q.u[t - 1] : T(0);
+  const T e = ii < m - 1 ? q.u[t + 1] : T(0);
+  const T s = jj > 0 ? q.u[t - m] : T(0);
+  const T nn = jj < m - 1 ? q.u[t + m] : T(0);
+  const T ac = q.alpha[(size_t)j * n1 + i];
+  const T aw = q.alpha[(size_t)j * n1 + i - 1];
+  const T as = q.alpha[(size_t)(j - 1) * n1 + i];
+  T r = aw * (c - w) - ac * (e - c) + as * (c - s) - ac * (nn - c);
+  return r + q.h2 * q.f[t];
+}
+
 // D along x for rows [r0, r0 + 2P) of `in` into `out` (rows 2p and 2p + 1 of
-// the CTA share line p).  With dotw != nullptr, also a partial of
-// sum dotw * out over the CTA's rows.
+// the CTA share line p).  With rin.u set, the rows are first computed as
+// RES = A u + h^2 f and written to rin.res.  With dotw != nullptr, also a
+// partial of sum dotw * out over the CTA's rows.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
     k_dst_rows(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int P,
-               const Cx<T>* __restrict__ tw, const T* __restrict__ dotw, double* dot_part) {
+               const Cx<T>* __restrict__ tw, const T* __restrict__ dotw, double* dot_part,
+               ResidualIn<T> rin) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int L = 1 << lg, m = N - 1;
   Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
@@ -120,11 +149,31 @@ __global__ void __launch_bounds__(kFftThreads)
   __shared__ double red[32];
   const int r0 = blockIdx.x * 2 * P;
   for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
+  const T* src = in;
+  int sstride = m;  // row stride of the source rows
+  size_t soff = (size_t)r0 * m;
+  if (rin.u) {
+    // the CTA's residual rows, staged in the second buffer ([2P][m] reals)
+    T* stage = reinterpret_cast<T*>(buf1);
+    for (int idx = threadIdx.x; idx < 2 * P * m; idx += blockDim.x) {
+      const int rr = idx / m, ii = idx - rr * m;
+      const int row = r0 + rr;
+      T v = T(0);
+      if (row < m) {
+        v = residual_at(rin, N, row, ii);
+        rin.res[(size_t)row * m + ii] = v;
+      }
+      stage[idx] = v;
+    }
+    __syncthreads();
+    src = stage;
+    soff = 0;
+  }
   for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
     const int line = idx >> lg, j = idx & (L - 1);
     const int ra = r0 + 2 * line, rb = ra + 1;
-    const T va = ra < m ? odd_ext(in + (size_t)ra * m, j, N, 1) : T(0);
-    const T vb = rb < m ? odd_ext(in + (size_t)rb * m, j, N, 1) : T(0);
+    const T va = ra < m ? odd_ext(src + soff + (size_t)(2 * line) * sstride, j, N, 1) : T(0);
+    const T vb = rb < m ? odd_ext(src + soff + (size_t)(2 * line + 1) * sstride, j, N, 1) : T(0);
     buf0[idx] = Cx<T>{va, vb};
   }
   __syncthreads();
@@ -251,7 +300,8 @@ cudaError_t gram_fft_tables(int N, T* tw, T* lam) {
 // pass 2: z = D_x work and the partials of res^T z
 template <typename T>
 cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const T* tw, const T* lam,
-                            T h2, double* dot_part, cudaStream_t st) {
+                            T h2, double* dot_part, cudaStream_t st, const T* u, const T* alpha,
+                            const T* f, T* res_out) {
   const int lg = log2_exact(N) + 1, L = 2 * N, m = N - 1;
   if (lg < 4 || lg > 12) return cudaErrorInvalidValue;
   const Cx<T>* twc = reinterpret_cast<const Cx<T>*>(tw);
@@ -268,8 +318,13 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
     auto k = k_dst_rows<T>;
     smem_optin(k);
     const int g = (m + 2 * P - 1) / (2 * P);
-    if (pass == 0) k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, P, twc, nullptr, nullptr);
-    else k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, P, twc, res, dot_part);
+    ResidualIn<T> rin{nullptr, nullptr, nullptr, T(0), nullptr};
+    if (pass == 0) {
+      if (u) rin = ResidualIn<T>{u, alpha, f, h2, res_out};
+      k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, P, twc, nullptr, nullptr, rin);
+    } else {
+      k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, P, twc, res, dot_part, rin);
+    }
   }
   return cudaGetLastError();
 }
@@ -277,9 +332,11 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
 template cudaError_t gram_fft_tables<float>(int, float*, float*);
 template cudaError_t gram_fft_tables<double>(int, double*, double*);
 template cudaError_t launch_gram_fft<float>(int, int, const float*, float*, float*, const float*,
-                                            const float*, float, double*, cudaStream_t);
+                                            const float*, float, double*, cudaStream_t, const float*,
+                                            const float*, const float*, float*);
 template cudaError_t launch_gram_fft<double>(int, int, const double*, double*, double*,
                                              const double*, const double*, double, double*,
-                                             cudaStream_t);
+                                             cudaStream_t, const double*, const double*,
+                                             const double*, double*);
 
 }  // namespace adsgb

@@ -189,9 +189,12 @@ bool gram_fft_supported(int dim, int N);
 int gram_fft_dot_parts(int N);
 template <typename T>
 cudaError_t gram_fft_tables(int N, T* tw /*4N: 2N complex twiddles*/, T* lam /*N-1*/);
+// pass 0 with u != nullptr first computes RES = A u + h^2 f (written to
+// res_out) and transforms it (res is then unused)
 template <typename T>
 cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const T* tw, const T* lam,
-                            T h2, double* dot_part, cudaStream_t st);
+                            T h2, double* dot_part, cudaStream_t st, const T* u = nullptr,
+                            const T* alpha = nullptr, const T* f = nullptr, T* res_out = nullptr);
 
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
