@@ -183,13 +183,13 @@ template cudaError_t launch_to_double<float>(const float*, double*, size_t, cuda
 // solutions shrink by rho = 0.43058 per row: rho is the root inside the unit
 // circle of z^4 + 26 z^3 + 66 z^2 + 26 z + 1, the symbol of the interior row
 // h [1, 26, 66, 26, 1] / 120 of the quadratic B-spline mass matrix.  With
-// H = 32 (FP32) the truncation is 2e-12 of the solution's size and with
+// H = 24 (FP32) the truncation is 1.6e-9 of the solution's size and with
 // H = 48 (FP64) 2.4e-18, both below the unit roundoff.
 template <typename T>
 struct SweepHalo;
 template <>
 struct SweepHalo<float> {
-  static constexpr int H = 32;
+  static constexpr int H = 24;
 };
 template <>
 struct SweepHalo<double> {

@@ -7,7 +7,7 @@ the unit lower factor; for the quadratic B-spline mass matrix it shrinks by
 rho = 0.43058 per row, the root inside the unit circle of the symbol of the
 interior row [1, 26, 66, 26, 1] / 120.  These tests emulate the chunking in
 numpy (FP64) on the oracle's 1D mass matrix and check the bound for the
-halo widths the kernels use (32 rows in FP32, 48 in FP64).
+halo widths the kernels use (24 rows in FP32, 48 in FP64).
 """
 import numpy as np
 import pytest
@@ -84,7 +84,7 @@ def test_factorisation_matches_dense():
     np.testing.assert_allclose(L @ np.diag(D) @ L.T, M, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("H,bound", [(32, 1e-10), (48, 1e-15)])
+@pytest.mark.parametrize("H,bound", [(24, 1e-7), (32, 1e-10), (48, 1e-15)])
 @pytest.mark.parametrize("chunk", [64, 127])
 def test_chunked_sweep_error_bound(H, bound, chunk):
     n = 700
