@@ -33,14 +33,14 @@ struct PhysParams {
 template <typename T>
 ADS_D T clamp01(T s) { return s < T(0) ? T(0) : (s > T(1) ? T(1) : s); }
 
-// tanh from the exponential identity tanh|x| = (1 - e^{-2|x|}) / (1 + e^{-2|x|})
-// with the hardware base-2 exponential; absolute error a few 1e-7.
+// tanh from the exponential identity tanh x = 2 / (1 + e^{-2x}) - 1 with the
+// hardware base-2 exponential and reciprocal (absolute error a few 1e-7; the
+// limits come out exactly: e^{-2x} -> inf gives -1, -> 0 gives 1).
 ADS_D float tanh_f32(float x) {
-  float ax = fabsf(x);
-  float t;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(-2.8853900817779268f * ax));  // -2 log2(e) |x|
-  float r = __fdividef(1.0f - t, 1.0f + t);
-  return copysignf(r, x);
+  float t, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(-2.8853900817779268f * x));  // -2 log2(e) x
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + t));
+  return fmaf(2.0f, r, -1.0f);
 }
 ADS_D double tanh_any(double x) { return tanh(x); }
 ADS_D float tanh_any(float x) { return tanh_f32(x); }

@@ -204,6 +204,25 @@ ADS_D void st_atom_split(unsigned char* hi, unsigned char* lo, int rg, int r, in
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
+// st_atom_split, and the hi half also to `g` (a global tile of the same
+// layout; nullptr: not stored)
+ADS_D void st_atom_split_g(unsigned char* hi, unsigned char* lo, unsigned char* g, int rg, int r, int c,
+                           const float v[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    float2 bf = __bfloat1622float2(b);
+    __nv_bfloat162 r2 = __floats2bfloat162_rn(v[2 * j] - bf.x, v[2 * j + 1] - bf.y);
+    h[j] = *reinterpret_cast<uint32_t*>(&b);
+    l[j] = *reinterpret_cast<uint32_t*>(&r2);
+  }
+  const uint32_t off = core_off(r, c, rg);
+  const uint4 qh = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(hi + off) = qh;
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  if (g) *reinterpret_cast<uint4*>(g + off) = qh;
+}
 
 ADS_D void ld_atom(const unsigned char* tile, int rg, int r, int c, float v[8]) {
   uint4 q = *reinterpret_cast<const uint4*>(tile + core_off(r, c, rg));
@@ -316,8 +335,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
         for (int d = 0; d < DIN; ++d) z += fW1[o * 3 + d] * x[d];
         v[j] = tanh_f32(z);
       }
-      st_atom_split(act, actlo, RG, tid, c, v);
-      if (gtile) st_atom(gtile, RG, tid, c, v);
+      st_atom_split_g(act, actlo, gtile, RG, tid, c, v);
     }
     float u = b5;
     for (int l = 0; l < 3; ++l) {
@@ -350,10 +368,9 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[c + j] + bl[c0 + c + j]);
           if (l < 2) {
-            st_atom_split(act, actlo, RG, tid, c0 + c, v);
-            st_atom_split(act, actlo, RG, tid, c0 + c + 8, v + 8);
-          }
-          if (g) {
+            st_atom_split_g(act, actlo, g, RG, tid, c0 + c, v);
+            st_atom_split_g(act, actlo, g, RG, tid, c0 + c + 8, v + 8);
+          } else if (g) {
             st_atom(g, RG, tid, c0 + c, v);
             st_atom(g, RG, tid, c0 + c + 8, v + 8);
           }
