@@ -918,13 +918,13 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     }
     AL(c->loss, 1);
     AL(c->loss_log, kLossRing);
-    AL(c->bc, 2);
+    AL(c->bc, 4);
     AL(c->lr, 1);
     AL(c->t, 1);
     if (cudaMemsetAsync(c->theta, 0, tc * c->nparams, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->am, 0, tc * c->nparams, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->av, 0, tc * c->nparams, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->t, 0, sizeof(int), c->stream) != cudaSuccess ||
+        launch_adam_reset(c->t, c->bc, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->loss, 0, sizeof(double), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->loss_log, 0, kLossRing * sizeof(double), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->u, 0, tc * c->M, c->stream) != cudaSuccess)
@@ -1004,7 +1004,7 @@ ads_status crvpinn_set_theta(ads_ctx* c, const double* theta) {
   size_t tc = tsize(c->tc);
   CK(cudaMemsetAsync(c->am, 0, tc * c->nparams, c->stream));
   CK(cudaMemsetAsync(c->av, 0, tc * c->nparams, c->stream));
-  CK(cudaMemsetAsync(c->t, 0, sizeof(int), c->stream));
+  CK(launch_adam_reset(c->t, c->bc, c->stream));
   return wait(c, kDefaultTimeout);
 }
 
@@ -1045,7 +1045,7 @@ static ads_status pressure_update(ads_ctx* c, int iters, double lr, double* loss
     size_t tc = tsize(c->tc);
     CK(cudaMemsetAsync(c->am, 0, tc * c->nparams, c->stream));
     CK(cudaMemsetAsync(c->av, 0, tc * c->nparams, c->stream));
-    CK(cudaMemsetAsync(c->t, 0, sizeof(int), c->stream));
+    CK(launch_adam_reset(c->t, c->bc, c->stream));
   }
   CA(set_scalar(c, c->lr, lr));
   CA(dispatch2<CoeffF>(c));

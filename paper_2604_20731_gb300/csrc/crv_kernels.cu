@@ -151,8 +151,13 @@ __device__ __forceinline__ void loss_finalize_dev(const LossFin& lf) {
     int tt = *lf.t + 1;
     *lf.t = tt;
     lf.log[(tt - 1) % kLossRing] = s;
-    lf.bc[0] = 1.0 / (1.0 - pow(0.9, (double)tt));
-    lf.bc[1] = 1.0 / (1.0 - pow(0.999, (double)tt));
+    // beta^t as running products (bc[2], bc[3]) instead of pow: FP64
+    // transcendentals are slow on this GPU and this warp holds the grid open
+    const double b1t = lf.bc[2] * 0.9, b2t = lf.bc[3] * 0.999;
+    lf.bc[2] = b1t;
+    lf.bc[3] = b2t;
+    lf.bc[0] = 1.0 / (1.0 - b1t);
+    lf.bc[1] = 1.0 / (1.0 - b2t);
   }
 }
 
@@ -545,9 +550,26 @@ __global__ void k_loss_finalize(const double* part, int nblk, double* loss, doub
     int tt = *t + 1;
     *t = tt;
     log[(tt - 1) % kLossRing] = s;
-    bc[0] = 1.0 / (1.0 - pow(0.9, (double)tt));
-    bc[1] = 1.0 / (1.0 - pow(0.999, (double)tt));
+    const double b1t = bc[2] * 0.9, b2t = bc[3] * 0.999;
+    bc[2] = b1t;
+    bc[3] = b2t;
+    bc[0] = 1.0 / (1.0 - b1t);
+    bc[1] = 1.0 / (1.0 - b2t);
   }
+}
+
+// Adam's step counter and bias-correction state: t = 0, beta_1^t = beta_2^t = 1
+__global__ void k_adam_reset(int* t, double* bc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *t = 0;
+    bc[0] = bc[1] = 0.0;
+    bc[2] = bc[3] = 1.0;
+  }
+}
+
+cudaError_t launch_adam_reset(int* t, double* bc, cudaStream_t st) {
+  k_adam_reset<<<1, 32, 0, st>>>(t, bc);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_loss_finalize(const double* part, int nblk, double* loss, double* loss_log,

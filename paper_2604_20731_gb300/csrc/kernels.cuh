@@ -74,6 +74,8 @@ int ysolve_blocks(int dim, int n);       // partial-sum slots (largest layout of
 int ysweep_blocks(int n, size_t esize);  // slots one 2D y sweep writes
 int sweep_ld(int n);  // row stride of the 2D sweep intermediates
 // mass bookkeeping: mode 0 = set int S from partials; mode 1 = step update
+// Adam state reset: t = 0 and the running powers of the betas to 1
+cudaError_t launch_adam_reset(int* t, double* bc, cudaStream_t st);
 cudaError_t launch_mass_finalize(const double* mass_part, int nmass, const double* src_part,
                                  int nsrc, int mode, double* stats, int* flags, cudaStream_t st);
 template <typename T>
@@ -122,7 +124,7 @@ struct LossFin {
   double* loss;
   double* log;
   int* t;
-  double* bc;
+  double* bc;  // [1/(1 - beta_1^t), 1/(1 - beta_2^t), beta_1^t, beta_2^t]
   int* flags;
   int bump;
 };
