@@ -274,7 +274,10 @@ void ads_server_destroy(ads_server* s);
 
 /* ---- data access -------------------------------------------------------------
  * ads_get: copy a field to host doubles (count = number of values expected
- * for the field; ADS_ERR_INVALID_ARG if it differs).  Waits for the stream.
+ * for the field; ADS_ERR_INVALID_ARG if it differs).  Waits for the stream;
+ * ADS_ERR_TIMEOUT also when a kernel's bounded wait on its own bulk copies or
+ * tensor-core work has given up on this context (the flag is sticky; the
+ * field may be incomplete).
  * ads_device_ptr: borrowed device pointer, its element count and dtype. */
 ads_status ads_get(ads_ctx* ctx, int field, double* host_dst, size_t count);
 ads_status ads_field_count(const ads_ctx* ctx, int field, size_t* count);

@@ -756,6 +756,198 @@ __global__ void __launch_bounds__(YTile<T>::CW)
   if (tid == 0) mass_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
+// Packed FP32 y-sweep factor rows: mesh row l at table row l + kYTabPad holds
+// (l1[l], l2[l]) in the forward table and (1/D[l], l1[l+1], l2[l+2], int B_l)
+// in the backward table, zeros for rows outside [0, n + 2), so a tile's
+// factors arrive with one bulk copy per table and rows outside the mesh stay
+// zero through both sweeps.
+constexpr int kYTabPad = 32;
+static size_t ysweep_table_rows(int n) {
+  const size_t r = (size_t)n + 2 + 2 * kYTabPad + ytile_rows<float>() + YTile<float>::M;
+  return (r + 1) & ~size_t(1);  // even: the backward table starts 16-byte aligned
+}
+size_t ysweep_table_bytes(int n) { return ysweep_table_rows(n) * (sizeof(float2) + sizeof(float4)); }
+
+__global__ void k_ysweep_table(int n, int rows, const float* __restrict__ l1, const float* __restrict__ l2,
+                               const float* __restrict__ dinv, const float* __restrict__ Iw, float2* fw,
+                               float4* bw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= rows) return;
+  const int l = k - kYTabPad, nb = n + 2;
+  const bool in = l >= 0 && l < nb;
+  fw[k] = in ? make_float2(l1[l], l2[l]) : make_float2(0.f, 0.f);
+  bw[k] = in ? make_float4(dinv[l], l1[l + 1], l2[l + 2], Iw[l]) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t launch_ysweep_table(int n, const float* l1, const float* l2, const float* dinv, const float* Iw,
+                                void* tab, cudaStream_t st) {
+  const int rows = (int)ysweep_table_rows(n);
+  float2* fw = reinterpret_cast<float2*>(tab);
+  float4* bw = reinterpret_cast<float4*>(fw + rows);
+  k_ysweep_table<<<(rows + 255) / 256, 256, 0, st>>>(n, rows, l1, l2, dinv, Iw, fw, bw);
+  return cudaGetLastError();
+}
+
+// Forward and backward substitution of one tile column held in registers
+// (rows [0, RB), owned rows [H, H + M)), and the int N-weighted sum of the
+// owned rows.  UNI: every row of the tile has the factors (cf, cb), so they
+// come from registers; the arithmetic is the same either way.
+template <bool UNI, int RB, int H, int M>
+__device__ __forceinline__ float ysweep_column(float (&v)[RB], const float2* fw, const float4* bw, float2 cf,
+                                               float4 cb) {
+  float y1 = 0.f, y2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    const float2 f = UNI ? cf : fw[i];
+    const float y = fmaf(-f.x, y1, fmaf(-f.y, y2, v[i]));
+    v[i] = y;
+    y2 = y1;
+    y1 = y;
+  }
+  float x1 = 0.f, x2 = 0.f, ms[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = RB - 1; i >= H; --i) {
+    const float4 f = UNI ? cb : bw[i];
+    const float x = fmaf(-f.y, x1, fmaf(-f.z, x2, v[i] * f.x));
+    v[i] = x;
+    x2 = x1;
+    x1 = x;
+    if (i < H + M) ms[i & 7] = fmaf(x, f.w, ms[i & 7]);
+  }
+  return ((ms[0] + ms[1]) + (ms[2] + ms[3])) + ((ms[4] + ms[5]) + (ms[6] + ms[7]));
+}
+
+// FP32 y sweep, persistent, pipelined and register-resident.  One CTA per SM
+// takes the tiles t = blockIdx.x + k gridDim.x (row chunk fastest, so that
+// neighbouring CTAs share halo rows in L2) through NST shared-memory stages;
+// the factor rows of a tile come by bulk copy from the packed table into one
+// of NST + 1 slots.  Each thread lifts its column of the tile into registers,
+// then the stage goes back to the bulk copies (tile k + NST) while the
+// forward and backward substitutions, the int S partials and the stores run
+// from registers.  Away from the ends of the mesh the factors of the
+// uniform-knot mass matrix settle to one value; tiles whose factors all equal
+// it take them from registers.  M and H are multiples of RE: every tile starts
+// on a strip boundary, so its strip-shared rows are fixed by the row index
+// alone, and the spill box starts at the spill row of the tile's first strip
+// (rows before the first or after the last spill row read as zero).
+template <int RE, int NST>
+__global__ void __launch_bounds__(YTile<float>::CW, 3 - NST)
+    k_ysweep_reg_2d(const __grid_constant__ CUtensorMap xm_map, const __grid_constant__ CUtensorMap xs_map,
+                    int n, int nsp, int sb, int gx, int ntile, float* __restrict__ out,
+                    const float2* __restrict__ tfw, const float4* __restrict__ tbw,
+                    const float* __restrict__ Iw, double* mass_part, int* flags) {
+  constexpr int CW = YTile<float>::CW, M = YTile<float>::M, H = SweepHalo<float>::H;
+  constexpr int RB = ytile_rows<float>(), NF = NST + 1;
+  static_assert(M % RE == 0 && H % RE == 0 && RB <= CW && H <= kYTabPad, "tile geometry");
+  extern __shared__ __align__(1024) unsigned char yrg[];
+  const size_t stage = (size_t)(RB + sb) * CW;  // floats per stage: tile, then spill rows
+  float* st = reinterpret_cast<float*>(yrg);
+  float4* fbw = reinterpret_cast<float4*>(st + NST * stage);  // [NF][RB]
+  float2* ffw = reinterpret_cast<float2*>(fbw + NF * RB);     // [NF][RB]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ffw + NF * RB);  // [NST]
+  double* red = reinterpret_cast<double*>(mbar + 2);
+  const int nb = n + 2, tid = threadIdx.x, G = gridDim.x;
+  const unsigned tx = (unsigned)((RB + (nsp > 0 ? sb : 0)) * CW * sizeof(float) +
+                                 RB * (sizeof(float2) + sizeof(float4)));
+  // tile k of this CTA (t = blockIdx.x + k G) into stage k % NST, slot k % NF
+  auto issue = [&](int t, int k) {
+    const int r0 = (t % gx) * M - H, c0 = (t / gx) * CW, sg = k % NST, fs = k % NF;
+    float* dst = st + sg * stage;
+    mbar_arrive_tx(mbar + sg, tx);
+    tma_load_2d(dst, &xm_map, c0, r0, mbar + sg);
+    if (nsp > 0) tma_load_2d(dst + (size_t)RB * CW, &xs_map, c0, 2 * (r0 / RE - 1), mbar + sg);
+    bulk_load(ffw + fs * RB, tfw + r0 + kYTabPad, RB * sizeof(float2), mbar + sg);
+    bulk_load(fbw + fs * RB, tbw + r0 + kYTabPad, RB * sizeof(float4), mbar + sg);
+  };
+  if (tid < NST) mbar_init_cta(mbar + tid, 1);
+  __syncthreads();
+  if (tid == 0)
+    for (int k = 0; k < NST; ++k)
+      if ((int)blockIdx.x + k * G < ntile) issue(blockIdx.x + k * G, k);
+  const int lm = nb / 2 + kYTabPad;
+  const float2 cf = tfw[lm];
+  const float4 cb = tbw[lm];
+  double macc = 0.0;
+  int it = 0;
+  for (int t = blockIdx.x; t < ntile; t += G, ++it) {
+    const int sg = it % NST, fs = it % NF;
+    const int r0 = (t % gx) * M - H, col = (t / gx) * CW + tid;
+    const float iwc = col < nb ? __ldg(Iw + col) : 0.f;
+    const bool ok = mbar_wait_for(mbar + sg, (it / NST) & 1, kCopyWaitNs);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not land in time: record it and let the copies in flight
+      // land (bounded) before the CTA's shared memory is released
+      if (tid == 0) {
+        atomicOr(flags, 8);
+        for (int d = 0; d < NST; ++d)
+          if (t + d * G < ntile) mbar_wait_for(mbar + (it + d) % NST, ((it + d) / NST) & 1, kCopyWaitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    bool uni = true;
+    if (tid < RB) {
+      const float2 f2 = ffw[fs * RB + tid];
+      const float4 f4 = fbw[fs * RB + tid];
+      uni = f2.x == cf.x && f2.y == cf.y && f4.x == cb.x && f4.y == cb.y && f4.z == cb.z && f4.w == cb.w;
+    }
+    const float* cp = st + sg * stage + tid;
+    float v[RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) v[i] = cp[i * CW];
+    if (nsp > 0) {
+      // DOF row r0 + i with i mod RE = j < 2 also holds the part of the strip
+      // above it: box row 2 floor(i / RE) + j
+      const float* sp = cp + (size_t)RB * CW;
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        if (i % RE < 2) v[i] += sp[(2 * (i / RE) + i % RE) * CW];
+    }
+    // the tile is in registers: hand the stage back to the copies (the
+    // block reduction is also the barrier that releases it)
+    fence_async_smem();
+    const bool generic = __syncthreads_or(!uni);
+    if (tid == 0 && t + NST * G < ntile) issue(t + NST * G, it + NST);
+    if (!generic) {
+      const float m = ysweep_column<true, RB, H, M>(v, nullptr, nullptr, cf, cb);
+      if (col < nb) {
+        float* o = out + (size_t)(r0 + H) * nb + col;
+#pragma unroll
+        for (int i = H; i < H + M; ++i, o += nb) *o = v[i];
+        macc += (double)m * (double)iwc;
+      }
+    } else {
+      const float m = ysweep_column<false, RB, H, M>(v, ffw + fs * RB, fbw + fs * RB, cf, cb);
+      if (col < nb) {
+        float* o = out + (size_t)(r0 + H) * nb + col;
+#pragma unroll
+        for (int i = H; i < H + M; ++i, o += nb)
+          if (r0 + i < nb) *o = v[i];
+        macc += (double)m * (double)iwc;
+      }
+    }
+  }
+  const double tot = block_sum(macc, red);
+  if (tid == 0) mass_part[blockIdx.x] = tot;
+}
+
+static size_t ysweep_reg_smem(int sb, int nst) {
+  constexpr int RB = ytile_rows<float>();
+  return (size_t)nst * (RB + sb) * YTile<float>::CW * sizeof(float) +
+         (size_t)(nst + 1) * RB * (sizeof(float4) + sizeof(float2)) + 16 + 32 * sizeof(double);
+}
+
+static int device_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 template <typename T>
 static size_t ysweep_smem(int sb) {
   constexpr int RB = ytile_rows<T>();
@@ -769,19 +961,63 @@ static void ysweep_grid(int n, int* gx, int* gy) {
   *gy = (nb + YTile<T>::CW - 1) / YTile<T>::CW;
 }
 
+// launch shape of the register-resident FP32 y sweep for strips of `re` rows:
+// the kernel, its stages and CTAs per SM.  Taken: the shape with the most
+// tiles in flight per SM, then the most CTAs (one stage each in two CTAs
+// beats two stages in one: a second CTA also hides the sweep's latency).
+// kernel = nullptr: not taken (strips of other heights).
+struct YRegCfg {
+  void (*kernel)(CUtensorMap, CUtensorMap, int, int, int, int, int, float*, const float2*, const float4*,
+                 const float*, double*, int*) = nullptr;
+  int nst = 0, cps = 0;
+  size_t smem = 0;
+};
+static YRegCfg ysweep_reg_cfg(int re) {
+  static YRegCfg memo[5];
+  static bool done[5] = {false, false, false, false, false};
+  YRegCfg c;
+  if (re != 2 && re != 4) return c;
+  if (done[re]) return memo[re];
+  const int sb = yspill_rows(ytile_rows<float>(), re);
+  for (int nst = 1; nst <= 2; ++nst) {
+    auto k = re == 4 ? (nst == 2 ? k_ysweep_reg_2d<4, 2> : k_ysweep_reg_2d<4, 1>)
+                     : (nst == 2 ? k_ysweep_reg_2d<2, 2> : k_ysweep_reg_2d<2, 1>);
+    smem_optin(k);
+    const size_t smem = ysweep_reg_smem(sb, nst);
+    int cps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k, YTile<float>::CW, smem) != cudaSuccess) {
+      cudaGetLastError();
+      cps = 0;
+    }
+    if (cps > 2) cps = 2;
+    if (cps > 0 && (nst * cps > c.nst * c.cps || (nst * cps == c.nst * c.cps && cps > c.cps))) {
+      c.kernel = k;
+      c.nst = nst;
+      c.cps = cps;
+      c.smem = smem;
+    }
+  }
+  memo[re] = c;
+  done[re] = true;
+  return c;
+}
+
 int ysweep_blocks(int n, size_t esize) {
   int gx, gy;
-  if (esize == sizeof(float)) ysweep_grid<float>(n, &gx, &gy);
-  else ysweep_grid<double>(n, &gx, &gy);
+  if (esize == sizeof(float)) {
+    ysweep_grid<float>(n, &gx, &gy);
+    const YRegCfg c = ysweep_reg_cfg(quad_rows(n, esize));
+    if (c.kernel) return gx * gy < c.cps * device_sms() ? gx * gy : c.cps * device_sms();  // persistent
+    return gx * gy;
+  }
+  ysweep_grid<double>(n, &gx, &gy);
   return gx * gy;
 }
 
 int ysolve_blocks(int dim, int n) {
   if (dim != 2) return ((n + 2) * (n + 2) + 127) / 128;
-  int a, b, c, d;
-  ysweep_grid<float>(n, &a, &b);
-  ysweep_grid<double>(n, &c, &d);
-  return a * b > c * d ? a * b : c * d;
+  const int a = ysweep_blocks(n, sizeof(float)), b = ysweep_blocks(n, sizeof(double));
+  return a > b ? a : b;
 }
 
 // cuTensorMapEncodeTiled, taken from the driver at run time
@@ -841,6 +1077,18 @@ cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs
   if (err != cudaSuccess) return err;
   int gx, gy;
   ysweep_grid<T>(a.n, &gx, &gy);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const YRegCfg c = ysweep_reg_cfg(re);
+    if (re == quad_rows(a.n, sizeof(T)) && c.kernel) {
+      if (!a.ax.ytab) return cudaErrorInvalidValue;
+      const int ntile = gx * gy, grid = ysweep_blocks(a.n, sizeof(T));
+      const float2* tfw = reinterpret_cast<const float2*>(a.ax.ytab);
+      const float4* tbw = reinterpret_cast<const float4*>(tfw + ysweep_table_rows(a.n));
+      c.kernel<<<grid, CW, c.smem, st>>>(xm_map, xs_map, a.n, nsp, sb, gx, ntile, out, tfw, tbw, a.ax.Iw,
+                                         mass_part, flags);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = ysweep_smem<T>(sb);
   auto k = k_ysweep_2d<T>;
   smem_optin(k);

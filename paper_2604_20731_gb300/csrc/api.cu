@@ -48,7 +48,7 @@ struct ads_ctx {
          *cen64 = nullptr, *sig64 = nullptr;
   // ADS-precision tables and fields
   void *B = nullptr, *dB = nullptr, *l1 = nullptr, *l2 = nullptr, *dinv = nullptr, *Iw = nullptr,
-       *gsrc = nullptr, *gnode = nullptr;
+       *gsrc = nullptr, *gnode = nullptr, *ytab = nullptr;
   void *S[2] = {nullptr, nullptr}, *P = nullptr, *K = nullptr, *phi = nullptr, *Xs = nullptr,
        *Xm = nullptr, *nodal = nullptr;
   int cur = 0;
@@ -174,6 +174,7 @@ QuadArgs<TA> quad_args(ads_ctx* c, const void* S) {
   a.ax.Iw = (const TA*)c->Iw;
   a.ax.gsrc = (const TA*)c->gsrc;
   a.ax.gnode = (const TA*)c->gnode;
+  a.ax.ytab = c->ytab;
   a.n_src = c->prm.n_src;
   for (int s = 0; s < kMaxSrc; ++s) {
     a.rate[s] = s < c->prm.n_src ? (TA)c->prm.src[s].rate : TA(0);
@@ -293,6 +294,7 @@ ads_status enq_coeffs(ads_ctx* c) {
   a.S = (const TA*)c->S[c->cur];
   a.K = (const TA*)c->K;
   a.ax.gnode = (const TA*)c->gnode;
+  a.ax.ytab = c->ytab;
   a.n_src = c->prm.n_src;
   for (int s = 0; s < kMaxSrc; ++s) {
     a.rate[s] = s < c->prm.n_src ? c->prm.src[s].rate : 0.0;
@@ -593,6 +595,7 @@ size_t estimate(const ads_params* p, const crvpinn_params* cp) {
   b += ta * (3 * nc + 2 * nn);  // S (2), P, K, nodal (phi optional)
   if (d == 3) b += ta * n * n * n * 27;           // per-element contributions
   else b += ta * (nb + 2 * ((n + 1) / 2)) * (size_t)sweep_ld((int)n);  // x-swept rows + spill rows
+  if (d == 2 && ta == 4) b += ysweep_table_bytes((int)n);
   b += 8 * 4 * (nb * nb + 1024);                  // partial sums
   if (cp) {
     const size_t tc = cp->dtype == ADS_BF16 ? 4 : tsize(cp->dtype);
@@ -815,6 +818,11 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     launch_convert<float>(c->Iw64, (float*)c->Iw, (size_t)nb, c->stream);
     launch_convert<float>(c->gsrc64, (float*)c->gsrc, 3 * (size_t)kMaxSrc * n * 3, c->stream);
     launch_convert<float>(c->gnode64, (float*)c->gnode, 3 * (size_t)kMaxSrc * (n + 1), c->stream);
+    if (c->dim == 2) {
+      ALV(c->ytab, ysweep_table_bytes(n));
+      launch_ysweep_table(n, (const float*)c->l1, (const float*)c->l2, (const float*)c->dinv,
+                          (const float*)c->Iw, c->ytab, c->stream);
+    }
   }
   // fields
   ALV(c->S[0], ta * nc);
@@ -1188,14 +1196,20 @@ ads_status ads_get(ads_ctx* c, int field, double* host_dst, size_t count) {
   if (cnt != count) return fail(c, ADS_ERR_INVALID_ARG, "ads_get: count mismatch");
   if (dt == ADS_F64) {
     CK(cudaMemcpyAsync(host_dst, p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    return wait(c, kDefaultTimeout);
+  } else {
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, cnt * sizeof(double), c->stream));
+    CK(launch_to_double<float>((const float*)p, tmp, cnt, c->stream));
+    CK(cudaMemcpyAsync(host_dst, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaFreeAsync(tmp, c->stream));
   }
-  double* tmp = nullptr;
-  CK(cudaMallocAsync((void**)&tmp, cnt * sizeof(double), c->stream));
-  CK(launch_to_double<float>((const float*)p, tmp, cnt, c->stream));
-  CK(cudaMemcpyAsync(host_dst, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaFreeAsync(tmp, c->stream));
-  return wait(c, kDefaultTimeout);
+  // a kernel whose bounded wait gave up left its output incomplete
+  CK(cudaMemcpyAsync(c->h_stage, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CA(wait(c, kDefaultTimeout));
+  int fl;
+  std::memcpy(&fl, c->h_stage, sizeof(int));
+  if (fl & 8) return fail(c, ADS_ERR_TIMEOUT, "a bounded device wait (tensor core or bulk copy) timed out");
+  return ADS_OK;
 }
 
 }  // extern "C"

@@ -151,6 +151,18 @@ ADS_D bool mbar_wait_for(uint64_t* mbar, unsigned parity, unsigned long long lim
 // 2D tile load: box at element coordinates (x, y) of the tensor map into
 // shared memory, completing on `mbar`.  x must be a multiple of 16 bytes'
 // worth of elements; y may be negative (rows outside the tensor read as 0).
+// one-dimensional bulk copy global -> shared, completing on `mbar` (both
+// addresses 16-byte aligned, bytes a multiple of 16)
+ADS_D void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+// order this thread's generic-proxy accesses to shared memory before later
+// bulk-copy (async-proxy) accesses
+ADS_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 ADS_D void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* mbar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"

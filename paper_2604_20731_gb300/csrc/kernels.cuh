@@ -19,6 +19,7 @@ struct AxisTabs {
   const T* Iw;     // [n+2] int B_l
   const T* gsrc;   // [3 axes][kMaxSrc][n][3] per-axis Gaussian factor at Gauss points
   const T* gnode;  // [3 axes][kMaxSrc][n+1] per-axis Gaussian factor at nodes
+  const void* ytab = nullptr;  // FP32 2D: packed y-sweep factor rows (launch_ysweep_table)
 };
 
 template <typename T>
@@ -62,7 +63,7 @@ cudaError_t launch_quad_xsweep(const QuadArgs<T>& a, int mode, int re, T* Xm, T*
                                double* src_part, cudaStream_t st);
 // y-direction sweep of Xm plus the spill rows Xs into `out` (row stride n+2),
 // with per-block partials of int S; sets bit 8 of flags if a bulk copy wait
-// timed out.
+// timed out.  FP32 with strips of quad_rows rows needs a.ax.ytab.
 template <typename T>
 cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs, int ldx, T* out,
                           double* mass_part, int* flags, cudaStream_t st);
@@ -71,6 +72,11 @@ cudaError_t launch_zsolve(const QuadArgs<T>& a, T* X, double* mass_part, cudaStr
 int quad_rows(int n, size_t esize);  // element rows per strip of the 2D quadrature
 int quad_blocks(int dim, int n, int re);
 int ysolve_blocks(int dim, int n);       // partial-sum slots (largest layout of either precision)
+// packed FP32 factor rows for the 2D y sweep, built once per mesh from the
+// FP32 LDL^T factors
+size_t ysweep_table_bytes(int n);
+cudaError_t launch_ysweep_table(int n, const float* l1, const float* l2, const float* dinv, const float* Iw,
+                                void* tab, cudaStream_t st);
 int ysweep_blocks(int n, size_t esize);  // slots one 2D y sweep writes
 int sweep_ld(int n);  // row stride of the 2D sweep intermediates
 // mass bookkeeping: mode 0 = set int S from partials; mode 1 = step update

@@ -84,7 +84,6 @@ ADS_D void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
       smem_addr(mbar)));
 }
-ADS_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 ADS_D void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 ADS_D void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -424,14 +423,6 @@ struct TcSmemB {
 constexpr int kColDel = 0, kColW5 = 64, kColW4 = 144, kColW1 = 384;
 ADS_D int col_dw(int L) { return L == 5 ? kColW5 : (L == 1 ? kColW1 : kColW4 + (4 - L) * kWP); }
 
-// one-dimensional bulk copy global -> shared, completing on `mbar`
-ADS_D void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(smem_dst)),
-      "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar))
-      : "memory");
-}
 ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
                : "memory");
