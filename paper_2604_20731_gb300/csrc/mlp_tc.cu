@@ -243,19 +243,71 @@ ADS_D void coords(int idx, int N, float c[3]) {
   c[2] = DIN == 3 ? 2.0f * (float)(idx / (m * m) + 1) * invN - 1.0f : 0.0f;
 }
 
-// load the three hidden weight matrices W_l[o][k] (FP32 master) as BF16 tiles
-template <int W = kW>
-ADS_D void load_hidden_weights(const float* th, int o2, unsigned char* wt, int tid, int nthr) {
-  constexpr int RG = (W / 8) * 128;
-  for (int e = tid; e < 3 * W * (W / 8); e += nthr) {
-    const int l = e / (W * (W / 8)), rem = e % (W * (W / 8));
-    const int o = rem / (W / 8), c = (rem % (W / 8)) * 8;
-    const float* src = th + o2 + l * (W * W + W) + o * W + c;
-    float v[8];
+// load the three hidden weight matrices W_l[o][k] (FP32 master, 16-byte
+// aligned rows) as BF16 tiles.  Each thread takes atoms e = tid + i NTHR and
+// issues the loads of a batch of them before any store, so the CTA waits
+// for about one memory latency per batch instead of one per atom.
+template <int W, int NTHR>
+ADS_D void load_hidden_weights(const float* __restrict__ th, int o2, unsigned char* wt, int tid) {
+  constexpr int RG = (W / 8) * 128, NA = 3 * W * (W / 8), PER = (NA + NTHR - 1) / NTHR, B = 6;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = src[j];
-    st_atom(wt + l * W * W * 2, RG, o, c, v);
+  for (int i0 = 0; i0 < PER; i0 += B) {
+    float4 q[B][2];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int e = tid + (i0 + i) * NTHR;
+      if (i0 + i < PER && e < NA) {
+        const int l = e / (W * (W / 8)), rem = e % (W * (W / 8));
+        const int o = rem / (W / 8), c = (rem % (W / 8)) * 8;
+        const float4* src = reinterpret_cast<const float4*>(th + o2 + l * (W * W + W) + o * W + c);
+        q[i][0] = __ldg(src);
+        q[i][1] = __ldg(src + 1);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int e = tid + (i0 + i) * NTHR;
+      if (i0 + i < PER && e < NA) {
+        const int l = e / (W * (W / 8)), rem = e % (W * (W / 8));
+        const int o = rem / (W / 8), c = (rem % (W / 8)) * 8;
+        const float v[8] = {q[i][0].x, q[i][0].y, q[i][0].z, q[i][0].w, q[i][1].x, q[i][1].y, q[i][1].z, q[i][1].w};
+        st_atom(wt + l * W * W * 2, RG, o, c, v);
+      }
+    }
   }
+}
+
+// One hidden layer's gradient into the CTA's partial row: dW[o][k] (o, k < W)
+// sits in TMEM lane o, columns k of `lane_col` (tmem address with the warp's
+// lane offset and the layer's first column); its bias gradient is TMEM column
+// W (TB) or `bias_o`.  Threads of warps 0-3 read their lanes (warp-collective
+// loads), the rows meet in shared memory S (W x (W + 1) floats), and the CTA
+// writes g[o W + k] and g[W W + o] with consecutive threads on consecutive
+// addresses.  Called by every thread of the CTA (two barriers inside).
+template <int W, int NTHR, bool TB>
+ADS_D void dw_layer_out(uint32_t lane_col, bool live, float bias_o, float* S, float* g, int tid) {
+  constexpr int SW = W + 1;
+  if (live && tid < kTP) {
+#pragma unroll 1
+    for (int c = 0; c < (TB ? W + 16 : W); c += 16) {
+      float v[16];
+      tmem_ld16(lane_col + c, v);  // warp-collective
+      if (tid < W) {
+        if (c < W) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) S[tid * SW + c + j] = v[j];
+        } else {
+          S[tid * SW + W] = v[0];
+        }
+      }
+    }
+    if (!TB && tid < W) S[tid * SW + W] = bias_o;
+  }
+  __syncthreads();
+  if (live)
+    for (int e = tid; e < W * W + W; e += NTHR)
+      g[e] = e < W * W ? S[(e / W) * SW + (e % W)] : S[(e - W * W) * SW + W];
+  __syncthreads();
 }
 
 template <int W>
@@ -286,7 +338,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   constexpr int RG = (W / 8) * 128;
   const float* th = a.theta;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
-  load_hidden_weights<W>(th, o2, wt, tid, kTP);
+  load_hidden_weights<W, kTP>(th, o2, wt, tid);
   for (int i = tid; i < W; i += kTP) {
     fb[i] = th[ob1 + i];
     for (int l = 0; l < 3; ++l) fb[(l + 1) * W + i] = th[o2 + l * (W * W + W) + W * W + i];
@@ -456,7 +508,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
   const int ntiles = (a.npts + kTP - 1) / kTP;
   if (epi) {
-    load_hidden_weights<kW>(th, o2, wt, tid, kBwdEpi);
+    load_hidden_weights<kW, kBwdEpi>(th, o2, wt, tid);
     for (int i = tid; i < kW; i += kBwdEpi) fW5[i] = th[o5 + i];
     // constant tiles: the ones column, the zero padding of the delta tiles
     float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -670,10 +722,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   __syncthreads();
   const bool aborted = *abort_flag != 0;
   const bool had_tiles = (int)blockIdx.x < ntiles;
+  const bool live = !aborted && had_tiles;
   float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
   // output layer: the rows' running sums through shared memory (the
   // activation buffers are idle now), added over the rows in a fixed order
-  if (!aborted && had_tiles) {
+  constexpr int kRedBytes = (kTP * (kW + 1) * 4 + 1023) / 1024 * 1024;
+  if (live) {
     float* red = reinterpret_cast<float*>(act);  // [128 rows][65]
     if (epi) {
 #pragma unroll
@@ -687,35 +741,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       gacc[o5 + tid] = sum;
     }
   }
+  // hidden layers: TMEM lane o = thread o of warps 0-3 (rows o >= 64 are
+  // padding), through shared memory past the output-layer sums
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  float* S = reinterpret_cast<float*>(act + kRedBytes);
+  for (int L = 4; L >= 2; --L)
+    dw_layer_out<kW, kBwdThreads, true>(lane_base + col_dw(L), live, 0.0f, S,
+                                        gacc + o2 + (L - 2) * (kW * kW + kW), tid);
   if (tid < kTP) {
-    // gradient row of this CTA: TMEM lane o = thread; rows o >= 64 are
-    // padding.  Every thread of warps 0-3 issues the same TMEM loads (they
-    // are warp-collective).
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
     const int o = tid;
-    if (!aborted && had_tiles) {
-      for (int L = 4; L >= 2; --L) {
-        const int ow = o2 + (L - 2) * (kW * kW + kW);
-        for (int c = 0; c < kWP; c += 16) {
-          float v[16];
-          tmem_ld16(lane_base + col_dw(L) + c, v);
-          if (o < kW) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int k = c + j;
-              if (k < kW) gacc[ow + o * kW + k] = v[j];
-              else if (k == kW) gacc[ow + kW * kW + o] = v[j];
-            }
-          }
-        }
-      }
-      {
-        float v[16];
-        tmem_ld16(lane_base + col_dw(1), v);
-        if (o < kW) {
-          for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
-          gacc[ob1 + o] = v[DIN];
-        }
+    if (live) {
+      float v[16];
+      tmem_ld16(lane_base + col_dw(1), v);  // warp-collective
+      if (o < kW) {
+        for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
+        gacc[ob1 + o] = v[DIN];
       }
     } else if (!had_tiles) {
       for (int i = tid; i < a.nparams; i += kTP) gacc[i] = 0.0f;  // CTA without tiles
@@ -814,7 +854,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
   constexpr int RG = (W / 8) * 128, RGD = (kDP / 8) * 128;
   const float* th = a.theta;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
-  load_hidden_weights<W>(th, o2, wt, tid, kTP);
+  load_hidden_weights<W, kTP>(th, o2, wt, tid);
   if (tid < W) fW5[tid] = th[o5 + tid];
   if (W < kDP) {  // zero padding columns of the delta tile (never rewritten)
     const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -959,19 +999,14 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
   float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
   const int o = tid;
   aborted = sync_abort(abort_flag);
+  // hidden layers through shared memory (the weight tiles are idle now:
+  // every product that read them has completed)
+  float* S = reinterpret_cast<float*>(wt);
+  static_assert(W * (W + 1) * 4 <= 3 * W * W * 2, "one layer's rows fit the weight tiles");
+  for (int L = 4; L >= 2; --L)
+    dw_layer_out<W, kTP, false>(lane_base + col_dw2(L), !aborted && !first, g_bh[L - 2], S,
+                                gacc + o2 + (L - 2) * (W * W + W), tid);
   if (!aborted && !first) {
-    for (int L = 4; L >= 2; --L) {
-      const int ow = o2 + (L - 2) * (W * W + W);
-      for (int c = 0; c < W; c += 16) {
-        float v[16];
-        tmem_ld16(lane_base + col_dw2(L) + c, v);  // warp-collective: every thread issues it
-        if (o < W) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) gacc[ow + o * W + c + j] = v[j];
-        }
-      }
-      if (o < W) gacc[ow + W * W + o] = g_bh[L - 2];
-    }
     if (o < W) {
       gacc[o5 + o] = g_w5;
       for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = g_w1[d];
@@ -1062,6 +1097,7 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
 
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   if (a.npts <= 0) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(a.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
   if (a.width == 64) return a.din == 2 ? fwd_tc<64, 2>(a, st) : fwd_tc<64, 3>(a, st);
   if (a.width == 128) return a.din == 2 ? fwd_tc<128, 2>(a, st) : fwd_tc<128, 3>(a, st);
   return cudaErrorNotSupported;
@@ -1077,6 +1113,7 @@ static cudaError_t bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
 }
 
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
+  if (reinterpret_cast<uintptr_t>(a.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
   if (a.width == 64) {
     const size_t smem = TcSmemB::TOTAL;
     auto k = a.din == 2 ? k_mlp_bwd_tc<2> : k_mlp_bwd_tc<3>;
