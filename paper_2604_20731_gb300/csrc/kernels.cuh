@@ -190,6 +190,7 @@ struct MlpTcArgs {
   float* gpart;           // [nblk][nparams]
   int nparams;
   int* flags;             // bit 8: a tensor-core wait timed out
+  int min_tiles = 1;      // forward: fewest 128-point tiles per CTA (a smaller grid)
 };
 // Gram solve by sine transforms computed with FFTs (2D, N a power of two,
 // 8 <= N <= 2048): tables, partial count of the loss, and the three passes
@@ -207,6 +208,8 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
 size_t mlp_tc_acts_bytes(int npts, int width);
-int mlp_tc_bwd_blocks(int npts, int width, int din);
+// backward CTAs (= gradient partial rows): one per SM at most, and at least
+// `min_tiles` 128-point tiles per CTA
+int mlp_tc_bwd_blocks(int npts, int width, int din, int min_tiles = 1);
 
 }  // namespace adsgb

@@ -1074,12 +1074,15 @@ static int bwd_tc_occ() {
   return tc_residency(k, smem, 4 * W);
 }
 
-int mlp_tc_bwd_blocks(int npts, int width, int din) {
+int mlp_tc_bwd_blocks(int npts, int width, int din, int min_tiles) {
   const int ntiles = (npts + kTP - 1) / kTP;
   int occ = 1;
   if (width != 64) occ = din == 2 ? bwd_tc_occ<128, 2>() : bwd_tc_occ<128, 3>();
   // width 64: the all-tensor-core kernel holds 512 TMEM columns, one CTA per SM
-  const int nb = occ * sms();
+  int nb = occ * sms();
+  const int want = (ntiles + min_tiles - 1) / (min_tiles > 0 ? min_tiles : 1);
+  if (want < nb) nb = want;
+  if (nb < 1) nb = 1;
   return ntiles < nb ? ntiles : nb;
 }
 
@@ -1090,7 +1093,9 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   smem_optin(k);
   const int occ = tc_residency(k, smem, W);
   const int ntiles = (a.npts + kTP - 1) / kTP;
-  const int grid = ntiles < occ * sms() ? ntiles : occ * sms();
+  int grid = ntiles < occ * sms() ? ntiles : occ * sms();
+  const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
+  if (want < grid) grid = want > 0 ? want : 1;
   k<<<grid, kTP, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -123,6 +123,12 @@ ads_status admit(ads_server* s, const std::shared_ptr<Request>& r) {
                            r->has_phi ? r->phi.data() : nullptr,
                            r->has_S0 ? r->S0.data() : nullptr, (void*)r->stream, &r->ctx);
   if (st != ADS_OK) return st;
+  {
+    // resident scenarios overlap on the streams: launch for total throughput
+    const int conc = s->cfg.n_streams < s->cfg.max_active ? s->cfg.n_streams : s->cfg.max_active;
+    st = ads_set_concurrency(r->ctx, conc);
+    if (st != ADS_OK) return st;
+  }
   if (r->has_theta) {
     st = crvpinn_set_theta(r->ctx, r->theta0.data());
     if (st != ADS_OK) return st;

@@ -170,6 +170,11 @@ class HybridSolver:
                         mass_total=s.mass_total)
         return None
 
+    def set_concurrency(self, contexts: int):
+        """Expect `contexts` contexts on the GPU at once (launch shapes for
+        throughput rather than this context's latency)."""
+        self._check(self.lib.ads_set_concurrency(self.ctx, int(contexts)), "ads_set_concurrency")
+
     def kernel_launches(self) -> int:
         v = C.c_ulonglong()
         self._check(self.lib.ads_kernel_launches(self.ctx, C.byref(v)), "ads_kernel_launches")

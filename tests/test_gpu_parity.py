@@ -427,6 +427,28 @@ def test_loss_and_gradient_bf16_width128(n):
     s.close()
 
 
+@pytest.mark.parametrize("n,width", [(33, 64), (256, 64), (70, 128)])
+def test_concurrency_launch_shape_same_results(n, width):
+    """ads_set_concurrency > 1 launches the network kernels on fewer CTAs with
+    more tiles each (256: 509 tiles on 16 backward CTAs).  The network values
+    and the loss are the same bit for bit; the gradient partials are summed in
+    another grouping, so the gradient agrees to FP32 rounding."""
+    sc, s, crv, theta, alpha, f = _crv_case(n, "bf16", width=width)
+    loss1 = s.loss_grad()
+    u1, g1 = s.get("U"), s.get("GRAD")
+    s.set_concurrency(8)
+    loss8 = s.loss_grad()
+    u8, g8 = s.get("U"), s.get("GRAD")
+    assert np.array_equal(u1, u8)
+    assert loss8 == loss1
+    assert rel_l2(g8, g1) <= 1e-5
+    ref_loss, ref_grad, _ = crv.loss_grad(MLP(2, width, 4), theta, alpha, f)
+    assert g8 @ ref_grad / (np.linalg.norm(g8) * np.linalg.norm(ref_grad)) >= 0.9995
+    with pytest.raises(Exception):
+        s.set_concurrency(0)
+    s.close()
+
+
 def test_config3_mesh_1024_mixed_precision():
     """1024^2 elements, FP32 saturation step vs the FP64 oracle (1e-5) and the
     BF16 width-128 network's loss and gradient vs the FP64 oracle at the
