@@ -23,6 +23,7 @@
 //   columns: D along y, times s / (lambda_i + lambda_j), D along y again,
 //            for a block of x-modes i                         (k_gram_cols)
 //   rows:    D along x, and per-CTA partials of RES^T z        (k_dst_rows)
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -40,6 +41,7 @@ struct __align__(2 * sizeof(T)) Cx {
 };
 
 constexpr int kFftThreads = 256;
+constexpr int KB = 4;  // values a thread loads together before it stores any
 
 template <typename T>
 __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> w) {
@@ -153,40 +155,85 @@ __global__ void __launch_bounds__(kFftThreads)
   int sstride = m;  // row stride of the source rows
   size_t soff = (size_t)r0 * m;
   if (rin.u) {
-    // the CTA's residual rows, staged in the second buffer ([2P][m] reals)
+    // the CTA's residual rows, staged in the second buffer ([2P][m] reals);
+    // each thread computes a batch of KB values (loads issued together)
+    // before it stores any
     T* stage = reinterpret_cast<T*>(buf1);
-    for (int idx = threadIdx.x; idx < 2 * P * m; idx += blockDim.x) {
-      const int rr = idx / m, ii = idx - rr * m;
-      const int row = r0 + rr;
-      T v = T(0);
-      if (row < m) {
-        v = residual_at(rin, N, row, ii);
-        rin.res[(size_t)row * m + ii] = v;
+    const int tot = 2 * P * m;
+    for (int b0 = 0; b0 < tot; b0 += KB * (int)blockDim.x) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        const int rr = idx / m, ii = idx - rr * m, row = r0 + rr;
+        v[q] = (idx < tot && row < m) ? residual_at(rin, N, row, ii) : T(0);
       }
-      stage[idx] = v;
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        const int rr = idx / m, ii = idx - rr * m, row = r0 + rr;
+        if (idx < tot) {
+          if (row < m) rin.res[(size_t)row * m + ii] = v[q];
+          stage[idx] = v[q];
+        }
+      }
     }
     __syncthreads();
     src = stage;
     soff = 0;
   }
-  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
-    const int line = idx >> lg, j = idx & (L - 1);
-    const int ra = r0 + 2 * line, rb = ra + 1;
-    const T va = ra < m ? odd_ext(src + soff + (size_t)(2 * line) * sstride, j, N, 1) : T(0);
-    const T vb = rb < m ? odd_ext(src + soff + (size_t)(2 * line + 1) * sstride, j, N, 1) : T(0);
-    buf0[idx] = Cx<T>{va, vb};
+  // odd extensions: value i of row r goes to positions i + 1 and 2N - 1 - i
+  // of its line (the real part for the even row of a pair, the imaginary
+  // part for the odd row); positions 0 and N are zero
+  {
+    T* b0r = reinterpret_cast<T*>(buf0);
+    for (int idx = threadIdx.x; idx < P * 2; idx += blockDim.x) {
+      const int line = idx >> 1, part = idx & 1;
+      b0r[2 * ((line << lg) + 0) + part] = T(0);
+      b0r[2 * ((line << lg) + N) + part] = T(0);
+    }
+    const int tot = 2 * P * m;
+    for (int b0 = 0; b0 < tot; b0 += KB * (int)blockDim.x) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        const int rr = idx / m, ii = idx - rr * m;
+        v[q] = (idx < tot && r0 + rr < m) ? src[soff + (size_t)rr * sstride + ii] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        if (idx < tot) {
+          const int rr = idx / m, ii = idx - rr * m, line = rr >> 1, part = rr & 1;
+          b0r[2 * ((line << lg) + ii + 1) + part] = v[q];
+          b0r[2 * ((line << lg) + 2 * N - 1 - ii) + part] = -v[q];
+        }
+      }
+    }
   }
   __syncthreads();
   const Cx<T>* z = fft_stockham(buf0, buf1, P, lg, tws);
   CompSum<T> dot;
-  for (int idx = threadIdx.x; idx < 2 * P * m; idx += blockDim.x) {
-    const int rr = idx / m, k = idx - rr * m + 1;
-    const int row = r0 + rr;
-    if (row < m) {
-      const Cx<T> zk = z[((rr >> 1) << lg) + k];
-      const T v = (rr & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
-      out[(size_t)row * m + k - 1] = v;
-      if (dotw) dot.add(v * dotw[(size_t)row * m + k - 1]);
+  const int tot = 2 * P * m;
+  for (int b0 = 0; b0 < tot; b0 += KB * (int)blockDim.x) {
+    T w[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int idx = b0 + q * blockDim.x + threadIdx.x;
+      const int rr = idx / m, ii = idx - rr * m, row = r0 + rr;
+      w[q] = (dotw && idx < tot && row < m) ? dotw[(size_t)row * m + ii] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int idx = b0 + q * blockDim.x + threadIdx.x;
+      const int rr = idx / m, k = idx - rr * m + 1, row = r0 + rr;
+      if (idx < tot && row < m) {
+        const Cx<T> zk = z[((rr >> 1) << lg) + k];
+        const T v = (rr & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
+        out[(size_t)row * m + k - 1] = v;
+        if (dotw) dot.add(v * w[q]);
+      }
     }
   }
   if (dotw) {
@@ -207,21 +254,68 @@ __global__ void __launch_bounds__(kFftThreads)
   Cx<T>* buf0 = tws + L;                       // [P][L]
   Cx<T>* buf1 = buf0 + (size_t)P * L;          // [P][L]
   const int c0 = blockIdx.x * C;
+  T* lams = reinterpret_cast<T*>(buf1);  // [m] eigenvalues until the first transform is done
   for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
-  // column c of the CTA fastest: a warp reads C neighbouring values of rows
-  for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-    const int c = idx % C, j = idx / C;
-    const int col = c0 + c;
-    const T v = col < m ? odd_ext(data + col, j, N, m) : T(0);
-    T* slot = reinterpret_cast<T*>(buf0 + ((c >> 1) << lg) + j);
-    slot[c & 1] = v;
+  for (int q = threadIdx.x; q < m; q += blockDim.x) lams[q] = lam[q];
+  // odd extensions of the CTA's columns (column c of the CTA fastest: a warp
+  // reads C neighbouring values of rows): value j of column c goes to
+  // positions j + 1 and 2N - 1 - j of line c / 2 (part c % 2)
+  {
+    T* b0r = reinterpret_cast<T*>(buf0);
+    for (int idx = threadIdx.x; idx < C; idx += blockDim.x) {
+      const int line = idx >> 1, part = idx & 1;
+      b0r[2 * ((line << lg) + 0) + part] = T(0);
+      b0r[2 * ((line << lg) + N) + part] = T(0);
+    }
+    const int tot = C * m;
+    for (int b0 = 0; b0 < tot; b0 += KB * (int)blockDim.x) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        const int c = idx % C, j = idx / C, col = c0 + c;
+        v[q] = (idx < tot && col < m) ? data[(size_t)j * m + col] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        if (idx < tot) {
+          const int c = idx % C, j = idx / C, line = c >> 1, part = c & 1;
+          b0r[2 * ((line << lg) + j + 1) + part] = v[q];
+          b0r[2 * ((line << lg) + 2 * N - 1 - j) + part] = -v[q];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the eigenvalues to registers before the transform overwrites buf1
+  T lc[KB], lk[KB];
+  {
+    const int tot = C * m;
+    // (this thread's first KB scaled values; C m <= KB blockDim.x whenever
+    // P L <= 1024, else the rest reread lams after the copy below)
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int idx = q * blockDim.x + threadIdx.x;
+      const int c = idx / m, k = idx - c * m + 1, col = c0 + c;
+      lc[q] = (idx < tot && col < m) ? lams[col] : T(1);
+      lk[q] = idx < tot ? lams[k - 1] : T(1);
+    }
   }
   __syncthreads();
   Cx<T>* z = fft_stockham(buf0, buf1, P, lg, tws);
   T* vt = reinterpret_cast<T*>(z == buf0 ? buf1 : buf0);  // [C][N] scaled transforms
-  for (int idx = threadIdx.x; idx < C * m; idx += blockDim.x) {
-    const int c = idx / m, k = idx - c * m + 1;
-    const int col = c0 + c;
+  for (int q = 0; q < KB; ++q) {
+    const int idx = q * blockDim.x + threadIdx.x;
+    if (idx < C * m) {
+      const int c = idx / m, k = idx - c * m + 1;
+      const Cx<T> zk = z[((c >> 1) << lg) + k];
+      const T d = (c & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
+      vt[c * N + k - 1] = d * (scale / (lc[q] + lk[q]));
+    }
+  }
+  for (int idx = KB * blockDim.x + threadIdx.x; idx < C * m; idx += blockDim.x) {
+    const int c = idx / m, k = idx - c * m + 1, col = c0 + c;
     const Cx<T> zk = z[((c >> 1) << lg) + k];
     const T d = (c & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
     const T li = col < m ? lam[col] : T(1);
@@ -264,7 +358,244 @@ int lines_per_cta(int L, int minP) {
   return P;
 }
 
+// ---------------------------------------------------------------------------
+// The whole Gram solve (residual, rows, columns, rows, RES^T z) in one
+// thread-block cluster, for FP32 and N <= 128: CTA r of the cluster owns rows
+// [r R, r R + R) of the m x m grid and, for the column pass, the same range of
+// columns.  The row transforms of its rows stay in its shared memory (slab);
+// the column pass reads and writes the slabs of the other CTAs of the cluster
+// through distributed shared memory, so the intermediate grid never leaves the
+// chip and the solve is one launch instead of three.
+// ---------------------------------------------------------------------------
+namespace cgx = cooperative_groups;
+
+// zero positions 0 and N of each of the P lines of buf (the odd extension's
+// fixed zeros)
+__device__ __forceinline__ void clear_ext_zeros(Cx<float>* buf, int P, int lg, int N) {
+  for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+    buf[(idx << lg) + 0] = Cx<float>{0.f, 0.f};
+    buf[(idx << lg) + N] = Cx<float>{0.f, 0.f};
+  }
+}
+// value v of row (or column) q of the batch at index i of its line: positions
+// i + 1 and 2N - 1 - i of line q / 2, part q % 2 (real, imaginary)
+__device__ __forceinline__ void put_ext(Cx<float>* buf, int lg, int N, int q, int i, float v) {
+  float* b = reinterpret_cast<float*>(buf);
+  const int line = q >> 1, part = q & 1;
+  b[2 * ((line << lg) + i + 1) + part] = v;
+  b[2 * ((line << lg) + 2 * N - 1 - i) + part] = -v;
+}
+// (D x)_k of row (or column) q of the batch from the transform z
+__device__ __forceinline__ float take_dst(const Cx<float>* z, int lg, int q, int k) {
+  const Cx<float> zk = z[((q >> 1) << lg) + k];
+  return (q & 1) ? 0.5f * zk.re : -0.5f * zk.im;
+}
+
+__global__ void __launch_bounds__(1024) k_gram_cluster(ResidualIn<float> rin, float* __restrict__ zout,
+                                                       const Cx<float>* __restrict__ tw,
+                                                       const float* __restrict__ lam, float scale,
+                                                       double* dot_part, int N, int lg, int R, int P) {
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int L = 1 << lg, m = N - 1, tid = threadIdx.x, T = blockDim.x;
+  Cx<float>* tws = reinterpret_cast<Cx<float>*>(fsm);  // [L]
+  Cx<float>* buf0 = tws + L;                           // [P][L]
+  Cx<float>* buf1 = buf0 + (size_t)P * L;              // [P][L]
+  float* lams = reinterpret_cast<float*>(buf1 + (size_t)P * L);  // [m], padded to 4
+  float* slab = lams + ((m + 3) & ~3);                           // [R][m]: this CTA's rows
+  __shared__ double red[32];
+  for (int q = tid; q < L; q += T) tws[q] = tw[q];
+  for (int q = tid; q < m; q += T) lams[q] = lam[q];
+  const int r0 = rank * R, nr = max(0, min(R, m - r0));
+  const int bt = 2 * P * m;  // values per batch of 2P rows or columns
+  // ---- rows: RES = A u + h^2 f, then D along x, into the slab ----
+  for (int p0 = 0; p0 < nr; p0 += 2 * P) {
+    __syncthreads();  // the buffers are free
+    clear_ext_zeros(buf0, P, lg, N);
+    for (int b0 = 0; b0 < bt; b0 += KB * T) {
+      float v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * T + tid, rr = idx / m, ii = idx - rr * m;
+        v[q] = (idx < bt && p0 + rr < nr) ? residual_at(rin, N, r0 + p0 + rr, ii) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * T + tid, rr = idx / m, ii = idx - rr * m;
+        if (idx < bt) {
+          if (p0 + rr < nr) rin.res[(size_t)(r0 + p0 + rr) * m + ii] = v[q];
+          put_ext(buf0, lg, N, rr, ii, v[q]);
+        }
+      }
+    }
+    __syncthreads();
+    const Cx<float>* z = fft_stockham(buf0, buf1, P, lg, tws);
+    for (int idx = tid; idx < bt; idx += T) {
+      const int rr = idx / m, k = idx - rr * m + 1;
+      if (p0 + rr < nr) slab[(p0 + rr) * m + k - 1] = take_dst(z, lg, rr, k);
+    }
+  }
+  cl.sync();  // every slab holds its rows' transforms
+  // ---- columns: D along y, times scale / (lam_i + lam_j), D along y ----
+  for (int p0 = 0; p0 < nr; p0 += 2 * P) {
+    __syncthreads();
+    clear_ext_zeros(buf0, P, lg, N);
+    // column c of the batch fastest: a warp reads 2P neighbouring values of a
+    // row of one slab
+    for (int b0 = 0; b0 < bt; b0 += KB * T) {
+      float v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * T + tid, c = idx % (2 * P), j = idx / (2 * P);
+        float x = 0.f;
+        if (idx < bt && p0 + c < nr) {
+          const float* rs = cl.map_shared_rank(slab, j / R);
+          x = rs[(j % R) * m + r0 + p0 + c];
+        }
+        v[q] = x;
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * T + tid, c = idx % (2 * P), j = idx / (2 * P);
+        if (idx < bt) put_ext(buf0, lg, N, c, j, v[q]);
+      }
+    }
+    __syncthreads();
+    Cx<float>* z = fft_stockham(buf0, buf1, P, lg, tws);
+    Cx<float>* other = z == buf0 ? buf1 : buf0;
+    float* vt = reinterpret_cast<float*>(other);  // [2P][N] scaled transforms
+    for (int idx = tid; idx < bt; idx += T) {
+      const int c = idx / m, k = idx - c * m + 1, col = r0 + p0 + c;
+      const float li = p0 + c < nr ? lams[col] : 1.f;
+      vt[c * N + k - 1] = take_dst(z, lg, c, k) * (scale / (li + lams[k - 1]));
+    }
+    __syncthreads();
+    clear_ext_zeros(z, P, lg, N);
+    for (int idx = tid; idx < bt; idx += T) {
+      const int c = idx / m, i = idx - c * m;
+      put_ext(z, lg, N, c, i, vt[c * N + i]);
+    }
+    __syncthreads();
+    const Cx<float>* w = fft_stockham(z, other, P, lg, tws);
+    // back into the slabs, column c of the batch fastest
+    for (int idx = tid; idx < bt; idx += T) {
+      const int c = idx % (2 * P), k = idx / (2 * P) + 1;
+      if (p0 + c < nr) {
+        float* rs = cl.map_shared_rank(slab, (k - 1) / R);
+        rs[((k - 1) % R) * m + r0 + p0 + c] = take_dst(w, lg, c, k);
+      }
+    }
+  }
+  cl.sync();  // every slab holds its rows of the column pass
+  // ---- rows: D along x gives z; partial of RES^T z ----
+  CompSum<float> dot;
+  for (int p0 = 0; p0 < nr; p0 += 2 * P) {
+    __syncthreads();
+    clear_ext_zeros(buf0, P, lg, N);
+    for (int idx = tid; idx < bt; idx += T) {
+      const int rr = idx / m, ii = idx - rr * m;
+      put_ext(buf0, lg, N, rr, ii, p0 + rr < nr ? slab[(p0 + rr) * m + ii] : 0.f);
+    }
+    __syncthreads();
+    const Cx<float>* z = fft_stockham(buf0, buf1, P, lg, tws);
+    for (int b0 = 0; b0 < bt; b0 += KB * T) {
+      float rv[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * T + tid, rr = idx / m, ii = idx - rr * m;
+        rv[q] = (idx < bt && p0 + rr < nr) ? rin.res[(size_t)(r0 + p0 + rr) * m + ii] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * T + tid, rr = idx / m, k = idx - rr * m + 1;
+        if (idx < bt && p0 + rr < nr) {
+          const float v = take_dst(z, lg, rr, k);
+          zout[(size_t)(r0 + p0 + rr) * m + k - 1] = v;
+          dot.add(v * rv[q]);
+        }
+      }
+    }
+  }
+  const double tot = block_sum(dot.value(), red);
+  if (tid == 0) dot_part[rank] = tot;
+}
+
 }  // namespace
+
+// cluster size, rows per CTA, line pairs per batch, threads and shared memory
+// of the one-cluster solve for N; CL = 0 when it does not apply (or the
+// device cannot co-schedule the cluster)
+GramClusterShape gram_cluster_shape(int N) {
+  GramClusterShape s;
+  const int lg = log2_exact(N);
+  // 8 <= N <= 128: at N = 256 and 512 the cluster's 8-16 SMs take longer
+  // (75 and 157 us) than the three passes over the whole GPU (39 and 51 us)
+  if (lg < 3 || lg > 7) return s;
+  const int L = 2 * N, m = N - 1, T = 1024;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  for (int CL : {8}) {
+    int R = (m + CL - 1) / CL;
+    R += R & 1;
+    int P = 4 * T / L;
+    if (P > R / 2) P = R / 2;
+    if (P < 1) P = 1;
+    const size_t smem = ((size_t)L + 2 * (size_t)P * L) * sizeof(Cx<float>) +
+                        (((size_t)m + 3) & ~size_t(3)) * sizeof(float) + (size_t)R * m * sizeof(float);
+    if (smem + 1024 > (size_t)optin) continue;
+    auto k = k_gram_cluster;
+    // raise-only limit: contexts of other N launch this kernel with their own size
+    smem_optin(k);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    s.CL = CL;
+    s.R = R;
+    s.P = P;
+    s.threads = T;
+    s.smem = smem;
+    return s;
+  }
+  return s;
+}
+
+cudaError_t launch_gram_cluster(const GramClusterShape& sh, int N, const float* u, const float* alpha,
+                                const float* f, float h2, float* res_out, float* z, const float* tw,
+                                const float* lam, double* dot_part, cudaStream_t st) {
+  if (sh.CL <= 0) return cudaErrorNotSupported;
+  const int lg = log2_exact(N) + 1;
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = sh.CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(sh.CL);
+  cfg.blockDim = dim3(sh.threads);
+  cfg.dynamicSmemBytes = sh.smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const ResidualIn<float> rin{u, alpha, f, h2, res_out};
+  const float scale = h2 * (float)(4.0 / ((double)N * N));  // h^2 (2 / N)^2
+  return cudaLaunchKernelEx(&cfg, k_gram_cluster, rin, z, reinterpret_cast<const Cx<float>*>(tw), lam, scale,
+                            dot_part, N, lg, sh.R, sh.P);
+}
 
 bool gram_fft_supported(int dim, int N) {
   const int lg = log2_exact(N);

@@ -205,6 +205,17 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
                             T h2, double* dot_part, cudaStream_t st, const T* u = nullptr,
                             const T* alpha = nullptr, const T* f = nullptr, T* res_out = nullptr);
 
+// the whole FP32 Gram solve (residual, the three transform passes, the
+// partials of RES^T z, one per CTA) in one thread-block cluster, 8 <= N <= 128
+struct GramClusterShape {
+  int CL = 0, R = 0, P = 0, threads = 0;  // CL = 0: not available
+  size_t smem = 0;
+};
+GramClusterShape gram_cluster_shape(int N);
+cudaError_t launch_gram_cluster(const GramClusterShape& sh, int N, const float* u, const float* alpha,
+                                const float* f, float h2, float* res_out, float* z, const float* tw,
+                                const float* lam, double* dot_part, cudaStream_t st);
+
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
 size_t mlp_tc_acts_bytes(int npts, int width);

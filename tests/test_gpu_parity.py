@@ -449,6 +449,27 @@ def test_concurrency_launch_shape_same_results(n, width):
     s.close()
 
 
+@pytest.mark.parametrize("n", [8, 64, 128])
+def test_gram_solve_cluster_and_three_pass_forms_agree(n):
+    """A context alone at N <= 128 solves G z = RES in one thread-block
+    cluster (rows, columns through distributed shared memory, rows); with
+    ads_set_concurrency > 1 it takes the three-pass form.  Both are the same
+    sine-transform solve in another order of rounding: z, the residual and the
+    loss agree to FP32 rounding, and z agrees with the oracle's direct solve."""
+    sc, s, crv, theta, alpha, f = _crv_case(n, "f32", width=64)
+    loss1 = s.loss_grad()
+    z1, r1 = s.get("Z"), s.get("RES")
+    s.set_concurrency(4)
+    loss4 = s.loss_grad()
+    z4, r4 = s.get("Z"), s.get("RES")
+    assert np.array_equal(r1, r4)
+    assert rel_l2(z1, z4) <= 1e-5
+    assert loss1 == pytest.approx(loss4, rel=1e-5)
+    _, _, parts = crv.loss_grad(MLP(2, 64, 4), theta, alpha, f)
+    assert rel_l2(z1, parts["z"]) <= 1e-4
+    s.close()
+
+
 def test_config3_mesh_1024_mixed_precision():
     """1024^2 elements, FP32 saturation step vs the FP64 oracle (1e-5) and the
     BF16 width-128 network's loss and gradient vs the FP64 oracle at the
