@@ -158,6 +158,15 @@ ADS_D void reg_pin32(uint32_t r[32]) {
                  "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
                  "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
 }
+// 32 consecutive TMEM columns
+ADS_D void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  tmem_ld32_async(taddr, r);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  reg_pin32(r);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
 // 64 consecutive TMEM columns with one wait
 ADS_D void tmem_ld64(uint32_t taddr, float v[64]) {
   uint32_t r0[32], r1[32];
@@ -319,11 +328,16 @@ struct TcSmemF {
   static constexpr int BIAS = ACTLO + kTP * W * 2;     // fp32: b1 b2 b3 b4 [4][W], W1 [W][3], W5 [W], b5
   static constexpr int NBIAS = 4 * W + 3 * W + W + 4;
   static constexpr int BAR = BIAS + NBIAS * 4;         // mbarrier (8 B), tmem base (4 B), abort flag (4 B)
-  static constexpr int TOTAL = BAR + 32;
+  static constexpr int UPART = BAR + 32;               // fp32 [128]: output-layer sums of the second half
+  static constexpr int TOTAL = UPART + kTP * 4;
 };
 
+// forward: two threads per point row, each taking half of the feature columns
+// (eight warps: warps w and w + 4 read the same TMEM lanes)
+constexpr int kFwdThreads = 2 * kTP;
+
 template <int W, int DIN>
-__global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemF<W>::WT;
   unsigned char* act = sm + TcSmemF<W>::ACT;
@@ -334,12 +348,14 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemF<W>::BAR);
   uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemF<W>::BAR + 8);
   volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemF<W>::BAR + 12);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int RG = (W / 8) * 128;
+  float* upart = reinterpret_cast<float*>(sm + TcSmemF<W>::UPART);
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTP - 1), half = tid / kTP;
+  constexpr int RG = (W / 8) * 128, WH = W / 2;
+  const int cb = half * WH;  // this thread's first feature column
   const float* th = a.theta;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
-  load_hidden_weights<W, kTP>(th, o2, wt, tid);
-  for (int i = tid; i < W; i += kTP) {
+  load_hidden_weights<W, kFwdThreads>(th, o2, wt, tid);
+  for (int i = tid; i < W; i += kFwdThreads) {
     fb[i] = th[ob1 + i];
     for (int l = 0; l < 3; ++l) fb[(l + 1) * W + i] = th[o2 + l * (W * W + W) + W * W + i];
     for (int d = 0; d < DIN; ++d) fW1[i * 3 + d] = th[i * DIN + d];
@@ -361,7 +377,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tbase;
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   const uint32_t idesc = idesc_bf16(kTP, W, 0, 0);
   const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(wt);
   uint32_t phase = 0;
@@ -370,25 +386,25 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
   const float b5 = fW5[W];
   for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
     const int p0 = tile * kTP;
-    const int idx = min(p0 + tid, a.npts - 1);
+    const int idx = min(p0 + row, a.npts - 1);
     float x[3];
     coords<DIN>(idx, a.N, x);
     unsigned char* gtile = a.acts ? a.acts + (size_t)tile * 4 * kTP * W * 2 : nullptr;
     // layer 1 on the CUDA cores
 #pragma unroll
-    for (int c = 0; c < W; c += 8) {
+    for (int c = 0; c < WH; c += 8) {
       float v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int o = c + j;
+        const int o = cb + c + j;
         float z = fb[o];
 #pragma unroll
         for (int d = 0; d < DIN; ++d) z += fW1[o * 3 + d] * x[d];
         v[j] = tanh_f32(z);
       }
-      st_atom_split_g(act, actlo, gtile, RG, tid, c, v);
+      st_atom_split_g(act, actlo, gtile, RG, row, cb + c, v);
     }
-    float u = b5;
+    float u = half == 0 ? b5 : 0.0f;
     for (int l = 0; l < 3; ++l) {
       if (sync_abort(abort_flag)) {
         aborted = true;
@@ -408,32 +424,36 @@ __global__ void __launch_bounds__(kTP) k_mlp_fwd_tc(MlpTcArgs a) {
       if (!mbar_wait(mbar, phase)) *abort_flag = 1;
       phase ^= 1;
       tc_fence_after();
-      const float* bl = fb + (l + 1) * W;
+      const float* bl = fb + (l + 1) * W + cb;
       unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * W * 2 : nullptr;
-      for (int c0 = 0; c0 < W; c0 += 64) {
-        float d[64];
-        tmem_ld64(lane_base + c0, d);  // 64 columns, one wait
 #pragma unroll
-        for (int c = 0; c < 64; c += 16) {
+      for (int c0 = 0; c0 < WH; c0 += 32) {
+        float d[32];
+        tmem_ld32(lane_base + cb + c0, d);
+#pragma unroll
+        for (int c = 0; c < 32; c += 16) {
           float v[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[c + j] + bl[c0 + c + j]);
           if (l < 2) {
-            st_atom_split_g(act, actlo, g, RG, tid, c0 + c, v);
-            st_atom_split_g(act, actlo, g, RG, tid, c0 + c + 8, v + 8);
+            st_atom_split_g(act, actlo, g, RG, row, cb + c0 + c, v);
+            st_atom_split_g(act, actlo, g, RG, row, cb + c0 + c + 8, v + 8);
           } else if (g) {
-            st_atom(g, RG, tid, c0 + c, v);
-            st_atom(g, RG, tid, c0 + c + 8, v + 8);
+            st_atom(g, RG, row, cb + c0 + c, v);
+            st_atom(g, RG, row, cb + c0 + c + 8, v + 8);
           }
           if (l == 2) {
             // the output layer in FP32 from the unrounded activations
 #pragma unroll
-            for (int j = 0; j < 16; ++j) u += fW5[c0 + c + j] * v[j];
+            for (int j = 0; j < 16; ++j) u += fW5[cb + c0 + c + j] * v[j];
           }
         }
       }
     }
-    if (!aborted && p0 + tid < a.npts) a.u[p0 + tid] = u;
+    // the two halves of the output-layer sum
+    if (half) upart[row] = u;
+    __syncthreads();
+    if (!half && !aborted && p0 + row < a.npts) a.u[p0 + row] = u + upart[row];
   }
   if (sync_abort(abort_flag) && tid == 0) atomicOr(a.flags, 8);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(W));
@@ -1046,7 +1066,7 @@ size_t mlp_tc_acts_bytes(int npts, int width) {
 // per-block reservation), registers, threads and TMEM columns.  (The runtime's
 // occupancy query reports one block per SM for kernels that allocate TMEM.)
 template <typename K>
-static int tc_residency(K k, size_t smem, int tmem_cols) {
+static int tc_residency(K k, size_t smem, int tmem_cols, int threads = kTP) {
   static int per_sm = 0, reserved = 0;
   if (!per_sm) {
     int dev = 0;
@@ -1059,9 +1079,9 @@ static int tc_residency(K k, size_t smem, int tmem_cols) {
   cudaFuncGetAttributes(&fa, k);
   int occ = per_sm / (int)(smem + reserved);
   const int regs_per_warp = ((fa.numRegs > 0 ? fa.numRegs : 255) * 32 + 255) / 256 * 256;
-  const int by_regs = 65536 / (regs_per_warp * (kTP / 32));
+  const int by_regs = 65536 / (regs_per_warp * (threads / 32));
   if (by_regs < occ) occ = by_regs;
-  if (2048 / kTP < occ) occ = 2048 / kTP;
+  if (2048 / threads < occ) occ = 2048 / threads;
   if (512 / tmem_cols < occ) occ = 512 / tmem_cols;
   return occ < 1 ? 1 : occ;
 }
@@ -1091,12 +1111,12 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   const size_t smem = TcSmemF<W>::TOTAL;
   auto k = k_mlp_fwd_tc<W, DIN>;
   smem_optin(k);
-  const int occ = tc_residency(k, smem, W);
+  const int occ = tc_residency(k, smem, W, kFwdThreads);
   const int ntiles = (a.npts + kTP - 1) / kTP;
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
   if (want < grid) grid = want > 0 ? want : 1;
-  k<<<grid, kTP, smem, st>>>(a);
+  k<<<grid, kFwdThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
