@@ -631,7 +631,7 @@ size_t estimate(const ads_params* p, const crvpinn_params* cp) {
     const size_t m = n - 1, M = d == 3 ? m * m * m : m * m, w = cp->width;
     const size_t np = mlp_params((int)d, cp->width, cp->hidden_layers);
     const size_t ld = ((M + 127) / 128) * 128;
-    const size_t acts = cp->dtype == ADS_BF16 ? 2 * 4 * w * ld : tc * 4 * w * ld;
+    const size_t acts = cp->dtype == ADS_BF16 ? mlp_tc_acts_bytes((int)M, (int)w) : tc * 4 * w * ld;
     b += tc * (nn + 6 * M + m * m + 5 * np + 2 * 152 * np) + acts;
     b += 8 * (m * m + (d == 3 ? m * m * m : m * m) + kLossRing + 4096);
   }

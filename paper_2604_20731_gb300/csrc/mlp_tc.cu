@@ -22,7 +22,7 @@
 // Backward, per tile (persistent CTAs; gradients accumulate in TMEM over all
 // of a CTA's tiles):
 //   D_l (for dW_l, db_l) += Delta_l^T [a_{l-1} | 1] -- M = 128 output rows
-//   (zero-padded), N = 80 (64 inputs + a ones column giving db), K = 128
+//   (64 used), N = 80 (64 inputs + the stored ones column giving db), K = 128
 //   points, both operands MN-major views of the [point][feature] tiles;
 //   Delta_{l-1} = (Delta_l W_l) (1 - a_{l-1}^2) -- M = 128 points, N = 64,
 //   K = 64, W_l read MN-major from the same weight tile as the forward.
@@ -40,13 +40,27 @@ namespace {
 constexpr int kW = 64;           // hidden width of this path
 constexpr int kTP = 128;         // points per tile = MMA M = TMEM lanes
 constexpr int kWP = kW + 16;     // activation tile width incl. ones column
-constexpr int kDP = 128;         // delta tile width (zero-padded to M = 128)
+constexpr int kDP = 128;         // M of the weight-gradient products (64 output rows used)
 constexpr int kXP = 16;          // input tile width: x', 1, zeros
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
 ADS_D uint32_t core_off(int r, int c, int rg) {
   return (uint32_t)((r >> 3) * rg + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
+
+// Stored activations of a 128-point tile: a_1 .. a_4 one after another, each
+// in the core-matrix layout.  For width 64, a_1 .. a_3 carry 16 more columns,
+// [1, 0, ..., 0], so that the backward's weight-gradient product
+// Delta_L^T [a_{L-1} | 1] also gives the bias gradient: one N = 80 product per
+// k-step instead of an N = 64 and an N = 16 one.
+ADS_HD constexpr int act_cols(int W, int l) { return (W == 64 && l < 3) ? W + 16 : W; }
+ADS_HD constexpr int act_rg(int W, int l) { return (act_cols(W, l) / 8) * 128; }
+ADS_HD constexpr int act_off(int W, int l) {
+  int o = 0;
+  for (int i = 0; i < l; ++i) o += kTP * act_cols(W, i) * 2;
+  return o;
+}
+ADS_HD constexpr int act_tile_bytes(int W) { return act_off(W, 4); }
 
 // Shared-memory matrix descriptor (no swizzle): bits 0-13 start address >> 4,
 // 16-29 leading-dimension byte offset >> 4, 32-45 stride-dimension byte offset
@@ -167,20 +181,6 @@ ADS_D void tmem_ld32(uint32_t taddr, float v[32]) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
-// 64 consecutive TMEM columns with one wait
-ADS_D void tmem_ld64(uint32_t taddr, float v[64]) {
-  uint32_t r0[32], r1[32];
-  tmem_ld32_async(taddr, r0);
-  tmem_ld32_async(taddr + 32, r1);
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  reg_pin32(r0);
-  reg_pin32(r1);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    v[j] = __uint_as_float(r0[j]);
-    v[32 + j] = __uint_as_float(r1[j]);
-  }
-}
 
 ADS_D uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -196,26 +196,12 @@ ADS_D void st_atom(unsigned char* tile, int rg, int r, int c, const float v[8]) 
   q.w = pack_bf16(v[6], v[7]);
   *reinterpret_cast<uint4*>(tile + core_off(r, c, rg)) = q;
 }
-// the same 8 values as a BF16 pair hi + lo (hi = bf16(v), lo = bf16(v - hi)):
-// together they carry about 16 significant bits
-ADS_D void st_atom_split(unsigned char* hi, unsigned char* lo, int rg, int r, int c, const float v[8]) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-    float2 bf = __bfloat1622float2(b);
-    __nv_bfloat162 r2 = __floats2bfloat162_rn(v[2 * j] - bf.x, v[2 * j + 1] - bf.y);
-    h[j] = *reinterpret_cast<uint32_t*>(&b);
-    l[j] = *reinterpret_cast<uint32_t*>(&r2);
-  }
-  const uint32_t off = core_off(r, c, rg);
-  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-// st_atom_split, and the hi half also to `g` (a global tile of the same
-// layout; nullptr: not stored)
-ADS_D void st_atom_split_g(unsigned char* hi, unsigned char* lo, unsigned char* g, int rg, int r, int c,
-                           const float v[8]) {
+// 8 values (one 16-byte atom) as a BF16 pair hi + lo (hi = bf16(v),
+// lo = bf16(v - hi): together about 16 significant bits), and the hi half
+// also to `g` (a global tile in the layout of row-group stride grg; nullptr:
+// not stored)
+ADS_D void st_atom_split_g(unsigned char* hi, unsigned char* lo, unsigned char* g, int rg, int grg, int r,
+                           int c, const float v[8]) {
   uint32_t h[4], l[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -229,7 +215,7 @@ ADS_D void st_atom_split_g(unsigned char* hi, unsigned char* lo, unsigned char* 
   const uint4 qh = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(hi + off) = qh;
   *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-  if (g) *reinterpret_cast<uint4*>(g + off) = qh;
+  if (g) *reinterpret_cast<uint4*>(g + core_off(r, c, grg)) = qh;
 }
 
 ADS_D void ld_atom(const unsigned char* tile, int rg, int r, int c, float v[8]) {
@@ -389,7 +375,14 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
     const int idx = min(p0 + row, a.npts - 1);
     float x[3];
     coords<DIN>(idx, a.N, x);
-    unsigned char* gtile = a.acts ? a.acts + (size_t)tile * 4 * kTP * W * 2 : nullptr;
+    unsigned char* gtile = a.acts ? a.acts + (size_t)tile * act_tile_bytes(W) : nullptr;
+    if (gtile && act_cols(W, 0) > W) {
+      // the constant columns [1, 0, ..., 0] of the stored a_1 .. a_3
+      const uint4 q = half == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        *reinterpret_cast<uint4*>(gtile + act_off(W, l) + core_off(row, W + 8 * half, act_rg(W, l))) = q;
+    }
     // layer 1 on the CUDA cores
 #pragma unroll
     for (int c = 0; c < WH; c += 8) {
@@ -402,7 +395,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
         for (int d = 0; d < DIN; ++d) z += fW1[o * 3 + d] * x[d];
         v[j] = tanh_f32(z);
       }
-      st_atom_split_g(act, actlo, gtile, RG, row, cb + c, v);
+      st_atom_split_g(act, actlo, gtile, RG, act_rg(W, 0), row, cb + c, v);
     }
     float u = half == 0 ? b5 : 0.0f;
     for (int l = 0; l < 3; ++l) {
@@ -425,7 +418,8 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
       phase ^= 1;
       tc_fence_after();
       const float* bl = fb + (l + 1) * W + cb;
-      unsigned char* g = gtile ? gtile + (size_t)(l + 1) * kTP * W * 2 : nullptr;
+      unsigned char* g = gtile ? gtile + act_off(W, l + 1) : nullptr;
+      const int grg = act_rg(W, l + 1);
 #pragma unroll
       for (int c0 = 0; c0 < WH; c0 += 32) {
         float d[32];
@@ -436,11 +430,11 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[c + j] + bl[c0 + c + j]);
           if (l < 2) {
-            st_atom_split_g(act, actlo, g, RG, row, cb + c0 + c, v);
-            st_atom_split_g(act, actlo, g, RG, row, cb + c0 + c + 8, v + 8);
+            st_atom_split_g(act, actlo, g, RG, grg, row, cb + c0 + c, v);
+            st_atom_split_g(act, actlo, g, RG, grg, row, cb + c0 + c + 8, v + 8);
           } else if (g) {
-            st_atom(g, RG, row, cb + c0 + c, v);
-            st_atom(g, RG, row, cb + c0 + c + 8, v + 8);
+            st_atom(g, grg, row, cb + c0 + c, v);
+            st_atom(g, grg, row, cb + c0 + c + 8, v + 8);
           }
           if (l == 2) {
             // the output layer in FP32 from the unrounded activations
@@ -473,19 +467,20 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
 // tiles, reduced over the rows once at the end in a fixed order.  The four
 // stored activation tiles of a point tile (64 KB, the forward's layout) arrive
 // by one bulk copy into a double buffer, the next tile's copy running under
-// the current tile.  Bias gradients come from a product against a constant
-// ones tile; delta tiles are zero-padded to M = 128.
+// the current tile.  Bias gradients come with the weight gradients from the
+// stored [a | 1] tiles.  The delta tiles are 64 columns wide; the weight-
+// gradient products read them as M = 128 operands whose rows 64 .. 127 (the
+// next rows' values) land in accumulator rows that are never read.
 constexpr int kBwdEpi = 2 * kTP;          // epilogue threads: two per point row
 constexpr int kBwdThreads = kBwdEpi + 32;  // eight epilogue warps, one issuing warp
 struct TcSmemB {
   static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
-  static constexpr int ACT_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
-  static constexpr int ACT = W + 3 * kW * kW * 2;          // 2 buffers x 4 tiles    128 KB
-  static constexpr int DEL_SZ = kTP * kDP * 2;
-  static constexpr int DEL = ACT + 8 * ACT_SZ;             // 2 x [128][128] bf16     64 KB
+  static constexpr int ACT_TILE = act_tile_bytes(kW);      // a_1..a_3 [128][80], a_4 [128][64]  76 KB
+  static constexpr int ACT = W + 3 * kW * kW * 2;          // 2 buffers             152 KB
+  static constexpr int DEL_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
+  static constexpr int DEL = ACT + 2 * ACT_TILE;           // 2 delta tiles           32 KB
   static constexpr int XIN = DEL + 2 * DEL_SZ;             // [128][16] bf16: x', 1, 0  4 KB
-  static constexpr int ONES = XIN + kTP * kXP * 2;         // [128][16] bf16: 1, 0     4 KB
-  static constexpr int VEC = ONES + kTP * kXP * 2;         // fp32: W5 [64]
+  static constexpr int VEC = XIN + kTP * kXP * 2;          // fp32: W5 [64]
   static constexpr int BAR = VEC + kW * 4;                 // 5 mbarriers, tmem base, abort flag
   static constexpr int TOTAL = BAR + 64;
 };
@@ -510,7 +505,6 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   unsigned char* act = sm + TcSmemB::ACT;  // [buffer][a_1..a_4]
   unsigned char* del = sm + TcSmemB::DEL;  // two delta tiles
   unsigned char* xin = sm + TcSmemB::XIN;
-  unsigned char* ones = sm + TcSmemB::ONES;
   float* fW5 = reinterpret_cast<float*>(sm + TcSmemB::VEC);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemB::BAR);
   uint64_t* mb_prod = mbar;       // delta product of a layer complete (issuer commit)
@@ -522,22 +516,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool epi = tid < kBwdEpi;
   const int row = tid & (kTP - 1), c0 = 32 * (tid >> 7);  // epilogue: point row, first column
-  constexpr int RGW = (kW / 8) * 128, RGD = (kDP / 8) * 128, RGX = (kXP / 8) * 128;
-  constexpr uint32_t kTileBytes = 4 * TcSmemB::ACT_SZ;
+  constexpr int RGW = (kW / 8) * 128, RGD = RGW, RGX = (kXP / 8) * 128;
+  constexpr uint32_t kTileBytes = TcSmemB::ACT_TILE;
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
   const int ntiles = (a.npts + kTP - 1) / kTP;
   if (epi) {
     load_hidden_weights<kW, kBwdEpi>(th, o2, wt, tid);
     for (int i = tid; i < kW; i += kBwdEpi) fW5[i] = th[o5 + i];
-    // constant tiles: the ones column, the zero padding of the delta tiles
-    float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (c0 == 0) {
-      st_atom(ones, RGX, row, 0, one);
-      st_atom(ones, RGX, row, 8, zero);
-    }
-    for (int b = 0; b < 2; ++b)
-      for (int c = kW + c0; c < kW + c0 + 32; c += 8) st_atom(del + b * TcSmemB::DEL_SZ, RGD, row, c, zero);
   }
   if (tid == 0) {
     *abort_flag = 0;
@@ -567,9 +553,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   if (tid == kBwdEpi) {
     // ---------------- issuing thread ----------------
     const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
-                   xin_s = smem_addr(xin), ones_s = smem_addr(ones);
-    const uint32_t id_dw = idesc_bf16(kDP, kW, 1, 1);   // dW_l weights: M = 128 (o), N = 64, K = points
-    const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // bias column (and dW_1): N = 16
+                   xin_s = smem_addr(xin);
+    // dW_l | db_l: M = 128 (o; rows 64 .. 127 unused), N = 80 ([a | 1]), K = points
+    const uint32_t id_dw = idesc_bf16(kDP, act_cols(kW, 0), 1, 1);
+    const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // dW_1 | db_1: N = 16 ([x' | 1])
     const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
     uint32_t ph_ready = 0, ph_done = 0, lph = 0;
     int pend = -1;  // buffer whose bulk copy is in flight (at most one), or -1
@@ -611,20 +598,19 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
           tc_fence_after();
         }
         const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
-        const uint32_t ain = actb_s + (L - 2) * TcSmemB::ACT_SZ;  // a_{L-1}
+        const uint32_t ain = actb_s + act_off(kW, L - 2);  // [a_{L-1} | 1]
         const uint32_t wl = wt_s + (L - 2) * kW * kW * 2;
         // Delta_L W_L, then its commit: the epilogues wait for this alone
 #pragma unroll
         for (int ks = 0; ks < kW / 16; ++ks)
           mma_bf16(tmem + kColDel, desc_k(dcur, RGD, ks), desc_mn(wl, RGW, ks), id_dp, ks > 0);
         mma_commit(mb_prod);
-        // dW_L, db_L += Delta_L^T [a_{L-1} | 1]
+        // dW_L | db_L += Delta_L^T [a_{L-1} | 1]
 #pragma unroll
         for (int ks = 0; ks < kTP / 16; ++ks) {
           const uint64_t da = desc_mn(dcur, RGD, ks);
           const uint32_t acc = (ks > 0 || !first) ? 1u : 0u;
-          mma_bf16(tmem + col_dw(L), da, desc_mn(ain, RGW, ks), id_dw, acc);
-          mma_bf16(tmem + col_dw(L) + kW, da, desc_mn(ones_s, RGX, ks), id_db, acc);
+          mma_bf16(tmem + col_dw(L), da, desc_mn(ain, act_rg(kW, L - 2), ks), id_dw, acc);
         }
         cur = 1 - cur;
       }
@@ -695,7 +681,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
 #pragma unroll
         for (int c = 0; c < 32; c += 8) {
           float av[8], v[8];
-          ld_atom(actb + 3 * TcSmemB::ACT_SZ, RGW, row, c0 + c, av);
+          ld_atom(actb + act_off(kW, 3), act_rg(kW, 3), row, c0 + c, av);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             v[j] = fW5[c0 + c + j] * g * (1.0f - av[j] * av[j]);
@@ -714,7 +700,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         tc_fence_after();
         // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
         unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
-        const unsigned char* aprev = actb + (L - 2) * TcSmemB::ACT_SZ;
+        const unsigned char* aprev = actb + act_off(kW, L - 2);
         uint32_t dr[32];
         tmem_ld32_async(lane_base + kColDel + c0, dr);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -722,7 +708,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
 #pragma unroll
         for (int c = 0; c < 32; c += 8) {
           float av[8], v[8];
-          ld_atom(aprev, RGW, row, c0 + c, av);
+          ld_atom(aprev, act_rg(kW, L - 2), row, c0 + c, av);
 #pragma unroll
           for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(dr[c + j]) * (1.0f - av[j] * av[j]);
           st_atom(dn, RGD, row, c0 + c, v);
@@ -858,6 +844,7 @@ struct TcSmemB2 {
 
 template <int W, int DIN>
 __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
+  static_assert(act_cols(W, 0) == W, "ring form: stored tiles without the ones column");
   constexpr int NCOL = 4 * W;  // TMEM columns: delta product + three dW
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemB2<W>::WT;
@@ -906,7 +893,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
   bool aborted = false, first = true;
   const int ntiles = (a.npts + kTP - 1) / kTP;
   auto stage = [&](int slot, int L, int tile) {  // activations a_{L+1} (L = 0..3) of `tile`
-    const unsigned char* src = a.acts + ((size_t)tile * 4 + L) * kTP * W * 2;
+    const unsigned char* src = a.acts + (size_t)tile * act_tile_bytes(W) + act_off(W, L);
     unsigned char* dst = act + slot * TcSmemB2<W>::ACT_SZ;
     for (int ch = tid; ch < kTP * W * 2 / 16; ch += kTP) cp_async16(dst + ch * 16, src + ch * 16);
     cp_async_commit();
@@ -1057,7 +1044,7 @@ int sms() {
 
 size_t mlp_tc_acts_bytes(int npts, int width) {
   int ntiles = (npts + kTP - 1) / kTP;
-  return (size_t)ntiles * 4 * kTP * width * 2;
+  return (size_t)ntiles * act_tile_bytes(width);
 }
 
 
