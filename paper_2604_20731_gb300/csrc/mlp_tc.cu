@@ -660,6 +660,23 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       }
       float x[3];
       coords<DIN>(min(idx, a.npts - 1), a.N, x);
+      // this tile's activations; Delta_4 = W_5 g (1 - a_4^2) and the
+      // output-layer sums in registers before the previous tile's products
+      // have released x' and the delta tiles
+      if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { *abort_flag = 1; break; }
+      lph ^= 1u << buf;
+      float v4[32];
+#pragma unroll
+      for (int c = 0; c < 32; c += 8) {
+        float av[8];
+        ld_atom(actb + act_off(kW, 3), act_rg(kW, 3), row, c0 + c, av);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          v4[c + j] = fW5[c0 + c + j] * g * (1.0f - av[j] * av[j]);
+          acc5[c + j] += g * av[j];
+        }
+      }
+      acc5b += g;
       // the previous tile's products read x' and the delta tiles
       if (it > 0) {
         if (!mbar_wait(mb_done, ph_done)) { *abort_flag = 1; break; }
@@ -673,44 +690,36 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         st_atom(xin, RGX, row, 0, v);
         st_atom(xin, RGX, row, 8, z);
       }
-      if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { *abort_flag = 1; break; }
-      lph ^= 1u << buf;
-      // Delta_4 = W_5 g (1 - a_4^2) into delta tile 1; output-layer sums
-      {
-        unsigned char* d4 = del + TcSmemB::DEL_SZ;
 #pragma unroll
-        for (int c = 0; c < 32; c += 8) {
-          float av[8], v[8];
-          ld_atom(actb + act_off(kW, 3), act_rg(kW, 3), row, c0 + c, av);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            v[j] = fW5[c0 + c + j] * g * (1.0f - av[j] * av[j]);
-            acc5[c + j] += g * av[j];
-          }
-          st_atom(d4, RGD, row, c0 + c, v);
-        }
-        acc5b += g;
-      }
+      for (int c = 0; c < 32; c += 8) st_atom(del + TcSmemB::DEL_SZ, RGD, row, c0 + c, v4 + c);
       arrive_ready();
       int cur = 1;
       bool bad = false;
       for (int L = 4; L >= 2; --L) {
+        // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta
+        // tile; the second factor before the product is ready
+        const unsigned char* aprev = actb + act_off(kW, L - 2);
+        float sq[32];
+#pragma unroll
+        for (int c = 0; c < 32; c += 8) {
+          float av[8];
+          ld_atom(aprev, act_rg(kW, L - 2), row, c0 + c, av);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sq[c + j] = 1.0f - av[j] * av[j];
+        }
         if (!mbar_wait(mb_prod, ph_prod)) { bad = true; break; }
         ph_prod ^= 1;
         tc_fence_after();
-        // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta tile
         unsigned char* dn = del + (1 - cur) * TcSmemB::DEL_SZ;
-        const unsigned char* aprev = actb + act_off(kW, L - 2);
         uint32_t dr[32];
         tmem_ld32_async(lane_base + kColDel + c0, dr);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         reg_pin32(dr);
 #pragma unroll
         for (int c = 0; c < 32; c += 8) {
-          float av[8], v[8];
-          ld_atom(aprev, act_rg(kW, L - 2), row, c0 + c, av);
+          float v[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(dr[c + j]) * (1.0f - av[j] * av[j]);
+          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(dr[c + j]) * sq[c + j];
           st_atom(dn, RGD, row, c0 + c, v);
         }
         arrive_ready();
