@@ -382,6 +382,10 @@ def run_ours(a, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = sum(s.kernel_launches() for s in ctxs) - l0
+    # every kernel's bounded waits completed (a timed-out wait leaves a status
+    # bit that ads_get reports)
+    for s in ctxs:
+        s.get("DT")
     total_ms = max(ev0[0].elapsed_time(e) for e in ev1)
     round_end = [max(ev0[0].elapsed_time(e) for e in round_ev[r]) for r in range(a.steps)]
     round_ms = [round_end[0]] + [round_end[r] - round_end[r - 1] for r in range(1, a.steps)]

@@ -479,9 +479,10 @@ struct TcSmemB {
   static constexpr int ACT = W + 3 * kW * kW * 2;          // 2 buffers             152 KB
   static constexpr int DEL_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
   static constexpr int DEL = ACT + 2 * ACT_TILE;           // 2 delta tiles           32 KB
-  static constexpr int XIN = DEL + 2 * DEL_SZ;             // [128][16] bf16: x', 1, 0  4 KB
-  static constexpr int VEC = XIN + kTP * kXP * 2;          // fp32: W5 [64]
-  static constexpr int BAR = VEC + kW * 4;                 // 5 mbarriers, tmem base, abort flag
+  static constexpr int XIN_SZ = kTP * kXP * 2;
+  static constexpr int XIN = DEL + 2 * DEL_SZ;             // 2 x [128][16] bf16: x', 1, 0  8 KB
+  static constexpr int VEC = XIN + 2 * XIN_SZ;             // fp32: W5 [64]
+  static constexpr int BAR = VEC + kW * 4;                 // 7 mbarriers, tmem base, abort flag
   static constexpr int TOTAL = BAR + 64;
 };
 // TMEM columns: delta product [0,64), dW5 [64,144), dW4 [144,224),
@@ -511,8 +512,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   uint64_t* mb_load = mbar + 1;   // [2] activation buffers loaded (bulk copy)
   uint64_t* mb_ready = mbar + 3;  // a delta tile written (one arrive per epilogue warp)
   uint64_t* mb_done = mbar + 4;   // every product of a tile complete (issuer commit)
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 40);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 44);
+  uint64_t* mb_free = mbar + 5;   // a tile's products up to dW_2 complete: its activation
+                                  // buffer and delta tiles are free (issuer commit)
+  // x' and Delta_4 of a tile written (one arrive per epilogue warp).  Apart
+  // from mb_ready: a warp may write the next tile's Delta_4 once mb_free has
+  // completed, before a slower warp has arrived for the previous Delta_1
+  uint64_t* mb_ready4 = mbar + 6;
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemB::BAR + 56);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemB::BAR + 60);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool epi = tid < kBwdEpi;
   const int row = tid & (kTP - 1), c0 = 32 * (tid >> 7);  // epilogue: point row, first column
@@ -532,6 +539,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_load + 1)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(mb_ready)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_done)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_free)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(mb_ready4)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -558,7 +567,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     const uint32_t id_dw = idesc_bf16(kDP, act_cols(kW, 0), 1, 1);
     const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // dW_1 | db_1: N = 16 ([x' | 1])
     const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
-    uint32_t ph_ready = 0, ph_done = 0, lph = 0;
+    uint32_t ph_ready = 0, ph_ready4 = 0, ph_free = 0, lph = 0;
     int pend = -1;  // buffer whose bulk copy is in flight (at most one), or -1
     auto fail = [&]() { *abort_flag = 1; };
     if ((int)blockIdx.x < ntiles) {
@@ -576,8 +585,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       // the previous tile's products have read the other buffer: wait for
       // them, then fetch the next tile into it
       if (it > 0) {
-        if (!mbar_wait(mb_done, ph_done)) { fail(); break; }
-        ph_done ^= 1;
+        if (!mbar_wait(mb_free, ph_free)) { fail(); break; }
+        ph_free ^= 1;
       }
       if (tile + (int)gridDim.x < ntiles) {
         mbar_expect(mb_load + 1 - buf, kTileBytes);
@@ -586,8 +595,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         pend = 1 - buf;
       }
       // x' and Delta_4 written
-      if (!mbar_wait(mb_ready, ph_ready)) { fail(); break; }
-      ph_ready ^= 1;
+      if (!mbar_wait(mb_ready4, ph_ready4)) { fail(); break; }
+      ph_ready4 ^= 1;
       tc_fence_after();
       int cur = 1;  // delta tile holding Delta_L
       bool bad = false;
@@ -615,6 +624,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         cur = 1 - cur;
       }
       if (bad) { fail(); break; }
+      // the activation buffer and delta tile 1 are free once these complete
+      // (products complete in issue order); dW_1 reads only Delta_1 and x'
+      mma_commit(mb_free);
       // Delta_1 written: dW_1, db_1 += Delta_1^T [x' | 1]
       if (!mbar_wait(mb_ready, ph_ready)) { fail(); break; }
       ph_ready ^= 1;
@@ -623,7 +635,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
 #pragma unroll
         for (int ks = 0; ks < kTP / 16; ++ks)
-          mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s, RGX, ks), id_db,
+          mma_bf16(tmem + col_dw(1), desc_mn(dcur, RGD, ks), desc_mn(xin_s + buf * TcSmemB::XIN_SZ, RGX, ks), id_db,
                    (ks > 0 || !first) ? 1u : 0u);
       }
       mma_commit(mb_done);
@@ -635,12 +647,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   } else if (epi) {
     // ---------------- epilogue warps: point row `row`, columns c0 .. c0 + 32 ----------------
     const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    uint32_t ph_prod = 0, ph_done = 0, lph = 0;
-    auto arrive_ready = [&]() {
+    uint32_t ph_prod = 0, ph_free = 0, lph = 0;
+    auto arrive_ready = [&](uint64_t* mb) {
       fence_async_smem();  // generic stores before the tensor cores read them
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive1(mb_ready);
+      if (lane == 0) mbar_arrive1(mb);
     };
     int it = 0;
     // dL/du of this row: loaded one tile ahead
@@ -677,22 +689,24 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         }
       }
       acc5b += g;
-      // the previous tile's products read x' and the delta tiles
+      // the previous tile's products up to dW_2 have released delta tile 1;
+      // x' goes to this tile's buffer (the tile before the previous one
+      // read it, and its dW_1 completed before the previous tile's dW_2)
       if (it > 0) {
-        if (!mbar_wait(mb_done, ph_done)) { *abort_flag = 1; break; }
-        ph_done ^= 1;
+        if (!mbar_wait(mb_free, ph_free)) { *abort_flag = 1; break; }
+        ph_free ^= 1;
         tc_fence_after();
       }
       if (c0 == 0) {
         float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int d = 0; d < DIN; ++d) v[d] = x[d];
         v[DIN] = 1.0f;
-        st_atom(xin, RGX, row, 0, v);
-        st_atom(xin, RGX, row, 8, z);
+        st_atom(xin + buf * TcSmemB::XIN_SZ, RGX, row, 0, v);
+        st_atom(xin + buf * TcSmemB::XIN_SZ, RGX, row, 8, z);
       }
 #pragma unroll
       for (int c = 0; c < 32; c += 8) st_atom(del + TcSmemB::DEL_SZ, RGD, row, c0 + c, v4 + c);
-      arrive_ready();
+      arrive_ready(mb_ready4);
       int cur = 1;
       bool bad = false;
       for (int L = 4; L >= 2; --L) {
@@ -722,15 +736,16 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
           for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(dr[c + j]) * sq[c + j];
           st_atom(dn, RGD, row, c0 + c, v);
         }
-        arrive_ready();
+        arrive_ready(mb_ready);
         cur = 1 - cur;
       }
       if (bad) { *abort_flag = 1; break; }
       first = false;
     }
-    // the last tile's products, before the accumulators are read
+    // the last tile's products, before the accumulators are read (mb_done
+    // completes once per tile; the last tile's phase has parity (it - 1) & 1)
     if (!first && !*abort_flag) {
-      if (!mbar_wait(mb_done, ph_done)) *abort_flag = 1;
+      if (!mbar_wait(mb_done, (uint32_t)(it - 1) & 1u)) *abort_flag = 1;
       tc_fence_after();
     }
   }
