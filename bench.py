@@ -33,6 +33,7 @@ METRIC = ("hybrid time steps/s (batched mixed-precision vs plain FP64) at stated
 UNIT = "steps/s"
 FP32_LANES_PER_SM = 128
 N_SM = 152
+MUFU_PER_SM_CLK = 16  # special-function results per SM per clock (ex2, rcp, ...)
 
 
 def args_parse():
@@ -476,7 +477,24 @@ def run_ours(a, world, rank, local):
     flops_pt = {"mlp_fwd": fwd_f, "mlp_bwd": bwd_f}
     nbig = max(prof_by_n)
     roof = {"kernel": dom, "share_of_mix_kernel_time": tot[dom] / sum(tot.values())}
-    if dom in flops_pt:
+    if dom == "mlp_fwd":
+        # the forward's binding unit is the special-function pipe: tanh takes one
+        # ex2 and one rcp for each of the 4 hidden layers' W units of a point
+        M = (nbig - 1) ** 2
+        t = prof_by_n[nbig][dom] * 1e-3
+        ops = 2 * 4 * a.width * M
+        ach = ops / t / 1e12
+        pk = N_SM * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+        fl = flops_pt[dom] * M
+        tpk = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        tr = traffic_record(dom + "_tc")
+        roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "T special-function ops/s",
+                     "frac": ach / pk, "traffic": tr["bytes_per_launch"] if tr else None,
+                     "peak_note": f"MUFU: {N_SM} SMs x {MUFU_PER_SM_CLK} results/clock x {sm_mhz:.0f} MHz",
+                     "algorithmic_ops_per_launch": ops, "avg_launch_ms": prof_by_n[nbig][dom],
+                     "tensor_achieved_tflops": fl / t / 1e12, "tensor_frac_of_sustained_bf16": fl / t / 1e12 / tpk,
+                     "workload": f"{nbig}^2 member of the mix"})
+    elif dom in flops_pt:
         M = (nbig - 1) ** 2
         fl = flops_pt[dom] * M
         ach = fl / (prof_by_n[nbig][dom] * 1e-3) / 1e12
