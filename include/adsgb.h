@@ -51,7 +51,8 @@ typedef enum {
   ADS_ERR_NONFINITE = 4,    /* a loss, step size or field became non-finite  */
   ADS_ERR_TIMEOUT = 5,      /* waiting for the stream exceeded the deadline  */
   ADS_ERR_STATE = 6,        /* call not valid in this state (e.g. no network)*/
-  ADS_ERR_UNSUPPORTED = 7   /* valid request this build does not implement   */
+  ADS_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement   */
+  ADS_ERR_IO = 8            /* a checkpoint file could not be written or read */
 } ads_status;
 
 /* arithmetic types */
@@ -293,6 +294,24 @@ ads_status ads_get(ads_ctx* ctx, int field, double* host_dst, size_t count);
 ads_status ads_field_count(const ads_ctx* ctx, int field, size_t* count);
 ads_status ads_device_ptr(ads_ctx* ctx, int field, void** dptr, size_t* count, int* dtype);
 ads_status ads_sync(ads_ctx* ctx, double timeout_s);
+
+/* ---- checkpoint / resume -----------------------------------------------------
+ * ads_save: wait for the stream, then write the context's evolving state to
+ * `path` (created or truncated): the current saturation, the pressure
+ * coefficients, K and phi, the step size and mass statistics, and with a
+ * network the coefficients alpha and f, the network values, theta, the Adam
+ * moments, step counter and bias-correction state, the learning rate and the
+ * loss log.  Tables and scratch that follow from the parameters are not
+ * written.  Binary, host byte order: an 8-byte magic, a version, the shape
+ * fields below, then (id, byte count, bytes) sections.
+ * ads_load: read such a file into a context made by ads_init with the same
+ * dim, n, saturation precision, phi map presence and network (width, layers,
+ * precision, parameter count); the next calls continue bit for bit as the
+ * saved context would have.  Drops cached graphs.
+ * Errors: ADS_ERR_INVALID_ARG (NULL path; a file of another shape or not a
+ * checkpoint), ADS_ERR_IO (open, write or short read), ADS_ERR_CUDA. */
+ads_status ads_save(ads_ctx* ctx, const char* path);
+ads_status ads_load(ads_ctx* ctx, const char* path);
 
 /* ---- saturation step without allocation (no counterpart in the paper) -------
  * For callers that cannot call cudaMalloc -- e.g. a serving process whose own

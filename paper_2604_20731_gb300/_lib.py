@@ -80,6 +80,8 @@ SIGNATURES = {
     "ads_destroy": (None, [_P]),
     "ads_hbm_estimate": (C.c_size_t, [C.POINTER(ads_params), C.POINTER(crvpinn_params)]),
     "ads_set_concurrency": (C.c_int, [_P, C.c_int]),
+    "ads_save": (C.c_int, [_P, C.c_char_p]),
+    "ads_load": (C.c_int, [_P, C.c_char_p]),
     "ads_saturation_step": (C.c_int, [_P, C.c_double, C.c_int]),
     "ads_cfl_dt": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _D]),
     "ads_set_pressure_coeffs": (C.c_int, [_P, _D]),

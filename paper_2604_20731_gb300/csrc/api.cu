@@ -721,6 +721,7 @@ const char* ads_status_str(ads_status st) {
     case ADS_ERR_TIMEOUT: return "timeout";
     case ADS_ERR_STATE: return "invalid state";
     case ADS_ERR_UNSUPPORTED: return "unsupported";
+    case ADS_ERR_IO: return "checkpoint file error";
   }
   return "unknown";
 }
@@ -999,6 +1000,122 @@ ads_status ads_sync(ads_ctx* c, double timeout_s) {
   ads_status s = check(c);
   if (s != ADS_OK) return s;
   return wait(c, timeout_s > 0 ? timeout_s : kDefaultTimeout);
+}
+
+// ---- checkpoint / resume ----
+namespace {
+constexpr char kCkptMagic[8] = {'A', 'D', 'S', 'G', 'B', 'C', 'K', '1'};
+struct CkptShape {
+  int32_t version, dim, n, ta, has_phi, has_crv, width, hidden, tc, nparams, cur, pad;
+};
+struct CkptSection {
+  uint32_t id;
+  void* ptr;
+  size_t bytes;
+};
+// the evolving state of a context (ids are part of the file format)
+std::vector<CkptSection> ckpt_sections(ads_ctx* c) {
+  const size_t nc = ncoef(c), nn = nnode(c), ta = tsize(c->ta), tc = tsize(c->tc);
+  std::vector<CkptSection> v = {{1, c->S[c->cur], ta * nc}, {2, c->P, ta * nc}, {3, c->K, ta * nn},
+                                {5, c->stats, 8 * sizeof(double)}, {6, c->dt, sizeof(double)}};
+  if (c->phi) v.push_back({4, c->phi, ta * nn});
+  if (c->has_crv) {
+    const size_t np = (size_t)c->nparams;
+    std::vector<CkptSection> w = {{7, c->alpha, tc * nn},        {8, c->f, tc * c->M},
+                                  {9, c->u, tc * c->M},          {10, c->theta, tc * np},
+                                  {11, c->am, tc * np},          {12, c->av, tc * np},
+                                  {13, c->t, sizeof(int)},       {14, c->bc, 4 * sizeof(double)},
+                                  {15, c->lr, sizeof(double)},   {16, c->loss, sizeof(double)},
+                                  {17, c->loss_log, kLossRing * sizeof(double)}};
+    v.insert(v.end(), w.begin(), w.end());
+  }
+  return v;
+}
+CkptShape ckpt_shape(const ads_ctx* c) {
+  CkptShape h{};
+  h.version = 1;
+  h.dim = c->dim;
+  h.n = c->n;
+  h.ta = c->ta;
+  h.has_phi = c->phi ? 1 : 0;
+  h.has_crv = c->has_crv ? 1 : 0;
+  h.width = c->has_crv ? c->cp.width : 0;
+  h.hidden = c->has_crv ? c->cp.hidden_layers : 0;
+  h.tc = c->has_crv ? c->cp.dtype : 0;
+  h.nparams = c->has_crv ? c->nparams : 0;
+  h.cur = c->cur;
+  return h;
+}
+struct FileCloser {
+  std::FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+}  // namespace
+
+ads_status ads_save(ads_ctx* c, const char* path) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!path) return ADS_ERR_INVALID_ARG;
+  CA(wait(c, kDefaultTimeout));
+  FileCloser fc{std::fopen(path, "wb")};
+  if (!fc.f) return fail(c, ADS_ERR_IO, std::string("ads_save: cannot open ") + path);
+  const CkptShape h = ckpt_shape(c);
+  const auto secs = ckpt_sections(c);
+  const uint32_t nsec = (uint32_t)secs.size();
+  bool ok = std::fwrite(kCkptMagic, 1, 8, fc.f) == 8 && std::fwrite(&h, sizeof(h), 1, fc.f) == 1 &&
+            std::fwrite(&nsec, sizeof(nsec), 1, fc.f) == 1;
+  std::vector<unsigned char> buf;
+  for (const auto& sec : secs) {
+    if (!ok) break;
+    buf.resize(sec.bytes);
+    CK(cudaMemcpy(buf.data(), sec.ptr, sec.bytes, cudaMemcpyDeviceToHost));
+    const uint64_t nb = sec.bytes;
+    ok = std::fwrite(&sec.id, sizeof(sec.id), 1, fc.f) == 1 && std::fwrite(&nb, sizeof(nb), 1, fc.f) == 1 &&
+         std::fwrite(buf.data(), 1, sec.bytes, fc.f) == sec.bytes;
+  }
+  if (!ok || std::fflush(fc.f) != 0) return fail(c, ADS_ERR_IO, std::string("ads_save: write failed: ") + path);
+  return ADS_OK;
+}
+
+ads_status ads_load(ads_ctx* c, const char* path) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!path) return ADS_ERR_INVALID_ARG;
+  CA(wait(c, kDefaultTimeout));
+  FileCloser fc{std::fopen(path, "rb")};
+  if (!fc.f) return fail(c, ADS_ERR_IO, std::string("ads_load: cannot open ") + path);
+  char magic[8];
+  CkptShape h{};
+  uint32_t nsec = 0;
+  if (std::fread(magic, 1, 8, fc.f) != 8 || std::fread(&h, sizeof(h), 1, fc.f) != 1 ||
+      std::fread(&nsec, sizeof(nsec), 1, fc.f) != 1)
+    return fail(c, ADS_ERR_IO, "ads_load: short read");
+  if (std::memcmp(magic, kCkptMagic, 8) != 0 || h.version != 1)
+    return fail(c, ADS_ERR_INVALID_ARG, "ads_load: not a checkpoint of this format");
+  CkptShape mine = ckpt_shape(c);
+  mine.cur = h.cur;
+  if (std::memcmp(&mine, &h, sizeof(h)) != 0 || (h.cur != 0 && h.cur != 1))
+    return fail(c, ADS_ERR_INVALID_ARG, "ads_load: checkpoint of another shape");
+  // the saved saturation goes to the buffer the saved context was using
+  c->cur = h.cur;
+  const auto secs = ckpt_sections(c);
+  if (nsec != secs.size()) return fail(c, ADS_ERR_INVALID_ARG, "ads_load: section count differs");
+  std::vector<unsigned char> buf;
+  for (const auto& sec : secs) {
+    uint32_t id = 0;
+    uint64_t nb = 0;
+    if (std::fread(&id, sizeof(id), 1, fc.f) != 1 || std::fread(&nb, sizeof(nb), 1, fc.f) != 1)
+      return fail(c, ADS_ERR_IO, "ads_load: short read");
+    if (id != sec.id || nb != sec.bytes) return fail(c, ADS_ERR_INVALID_ARG, "ads_load: unexpected section");
+    buf.resize(sec.bytes);
+    if (std::fread(buf.data(), 1, sec.bytes, fc.f) != sec.bytes) return fail(c, ADS_ERR_IO, "ads_load: short read");
+    CK(cudaMemcpy(sec.ptr, buf.data(), sec.bytes, cudaMemcpyHostToDevice));
+  }
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+  return ADS_OK;
 }
 
 ads_status ads_set_pressure_coeffs(ads_ctx* c, const double* host_p) {

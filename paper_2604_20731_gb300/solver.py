@@ -170,6 +170,14 @@ class HybridSolver:
                         mass_total=s.mass_total)
         return None
 
+    def save(self, path: str):
+        """Write the context's evolving state to a checkpoint file."""
+        self._check(self.lib.ads_save(self.ctx, str(path).encode()), "ads_save")
+
+    def load(self, path: str):
+        """Read a checkpoint written by save() from a context of the same shape."""
+        self._check(self.lib.ads_load(self.ctx, str(path).encode()), "ads_load")
+
     def set_concurrency(self, contexts: int):
         """Expect `contexts` contexts on the GPU at once (launch shapes for
         throughput rather than this context's latency)."""
