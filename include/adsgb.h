@@ -90,6 +90,15 @@ typedef struct {
                         with BF16 operands and FP32 accumulation, stored
                         activations in BF16, everything else (residual, Gram,
                         Adam, master parameters) in FP32.                     */
+  int act_chunks;    /* ADS_BF16: stored activations.  1: all points' at once.
+                        k > 1: activation recomputation -- the forward of an
+                        iteration stores none; the backward runs over k chunks
+                        of the 128-point tiles, each preceded by a forward of
+                        that chunk that stores its activations, so the buffer
+                        holds one chunk.  0: 1 unless all points' activations
+                        would take more than a quarter of the free device
+                        memory, then the fewest chunks that fit.  Ignored for
+                        ADS_F32 / ADS_F64.                                   */
 } crvpinn_params;
 
 typedef struct {

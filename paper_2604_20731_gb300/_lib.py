@@ -35,7 +35,7 @@ class ads_params(C.Structure):
 
 
 class crvpinn_params(C.Structure):
-    _fields_ = [("width", C.c_int), ("hidden_layers", C.c_int), ("dtype", C.c_int)]
+    _fields_ = [("width", C.c_int), ("hidden_layers", C.c_int), ("dtype", C.c_int), ("act_chunks", C.c_int)]
 
 
 class hybrid_params(C.Structure):

@@ -65,6 +65,9 @@ struct ads_ctx {
   int* t = nullptr;
   int ndot = 0, nbwd = 0, ld = 0;
   int concurrency = 1;  // contexts expected to share the GPU (ads_set_concurrency)
+  // activation recomputation (tensor-core network): the backward runs over
+  // `chunks` chunks of `chunk_tiles` 128-point tiles, nbwd partial rows each
+  int chunks = 1, chunk_tiles = 0;
   bool gram_fft = false;  // 2D, N a power of two: Gram solve by FFT sine transforms
   GramClusterShape gcs;   // FP32, N <= 512: the whole Gram solve in one cluster (CL > 0)
   // host staging (pinned)
@@ -324,6 +327,11 @@ ads_status enq_coeffs(ads_ctx* c) {
   return ADS_OK;
 }
 
+// points one backward launch covers: all, or one chunk of tiles
+static int bwd_points(const ads_ctx* c) {
+  return c->chunks > 1 ? c->chunk_tiles * 128 : c->M;
+}
+
 // The one-cluster Gram solve shortens a context's own iteration at small N
 // (128^2: 34 -> 26 us) but keeps up to 8 SMs half-occupied for its length;
 // with other contexts on the GPU the three-pass form, whose small CTAs share
@@ -339,7 +347,7 @@ template <typename TC>
 ads_status enq_train_iter(ads_ctx* c, int upd) {
   const int m = c->m1;
   const TC h = TC(1.0 / c->N);
-  LK(0, launch_fwd<TC>(c, true));
+  LK(0, launch_fwd<TC>(c, !(c->use_tc && c->chunks > 1)));
   if (c->dim == 2 && c->gram_fft) {
     // the residual is computed inside the first transform pass
     if (c->prof) cudaEventRecord(c->prof[1], c->stream);
@@ -388,8 +396,24 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   LossFin lf{c->dot_part, nparts, c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
   LK(5, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
                            nullptr, TC(0), TC(2), (TC*)c->gu, &lf, c->stream));
-  LK(6, launch_bwd<TC>(c));
-  LK(7, launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->nbwd, c->nparams, (TC*)c->grad,
+  if (c->use_tc && c->chunks > 1) {
+    // activation recomputation: per chunk of tiles, a forward that stores the
+    // chunk's activations, then its backward into its own partial rows
+    if (c->prof) cudaEventRecord(c->prof[6], c->stream);
+    for (int k = 0; k < c->chunks; ++k) {
+      MlpTcArgs ka = mlp_tc_args(c, true);
+      ka.tile0 = k * c->chunk_tiles;
+      ka.tile_count = c->chunk_tiles;
+      CK(launch_mlp_fwd_tc(ka, c->stream));
+      ka.gpart = (float*)c->gpart + (size_t)k * c->nbwd * c->nparams;
+      CK(launch_mlp_bwd_tc(ka, c->nbwd, c->stream));
+      c->nlaunch += 2;
+    }
+    if (c->prof) cudaEventRecord(c->prof[7], c->stream);
+  } else {
+    LK(6, launch_bwd<TC>(c));
+  }
+  LK(7, launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->chunks * c->nbwd, c->nparams, (TC*)c->grad,
                                     (TC*)c->theta, (TC*)c->am, (TC*)c->av, c->bc, c->lr, upd,
                                     c->stream));
   return ADS_OK;
@@ -631,7 +655,14 @@ size_t estimate(const ads_params* p, const crvpinn_params* cp) {
     const size_t m = n - 1, M = d == 3 ? m * m * m : m * m, w = cp->width;
     const size_t np = mlp_params((int)d, cp->width, cp->hidden_layers);
     const size_t ld = ((M + 127) / 128) * 128;
-    const size_t acts = cp->dtype == ADS_BF16 ? mlp_tc_acts_bytes((int)M, (int)w) : tc * 4 * w * ld;
+    size_t acts = tc * 4 * w * ld;
+    if (cp->dtype == ADS_BF16) {
+      const int tiles = (int)((M + 127) / 128);
+      int k = cp->act_chunks > 0 ? cp->act_chunks : 1;  // (automatic: estimated as all stored)
+      if (k > tiles) k = tiles;
+      const int ct = (tiles + k - 1) / k;
+      acts = mlp_tc_acts_bytes(ct * 128, (int)w);
+    }
     b += tc * (nn + 6 * M + m * m + 5 * np + 2 * 152 * np) + acts;
     b += 8 * (m * m + (d == 3 ? m * m * m : m * m) + kLossRing + 4096);
   }
@@ -739,7 +770,7 @@ ads_status ads_set_concurrency(ads_ctx* c, int contexts) {
   c->concurrency = contexts;
   if (c->has_crv && c->use_tc) {
     // never more partial rows than ads_init allocated (the one-tile shape)
-    const int nb = mlp_tc_bwd_blocks(c->M, c->cp.width, c->dim, contexts > 1 ? kBwdTilesShared : 1);
+    const int nb = mlp_tc_bwd_blocks(bwd_points(c), c->cp.width, c->dim, contexts > 1 ? kBwdTilesShared : 1);
     c->nbwd = nb;
   }
   return ADS_OK;
@@ -923,7 +954,23 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     c->nparams = mlp_params(c->dim, crv->width, crv->hidden_layers);
     c->ld = ((c->M + 63) / 64) * 64;
     c->ndot = dot_blocks(c->M);
-    c->nbwd = c->use_tc ? mlp_tc_bwd_blocks(c->M, crv->width, c->dim) : mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
+    if (c->use_tc) {
+      const int tiles = (c->M + 127) / 128;
+      int k = crv->act_chunks;
+      if (k <= 0) {
+        size_t fr = 0, tot = 0;
+        const size_t full = mlp_tc_acts_bytes(c->M, crv->width);
+        k = 1;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && full > fr / 4)
+          k = (int)((full + fr / 4 - 1) / (fr / 4));
+      }
+      if (k > tiles) k = tiles;
+      if (k < 1) k = 1;
+      c->chunk_tiles = (tiles + k - 1) / k;
+      c->chunks = (tiles + c->chunk_tiles - 1) / c->chunk_tiles;
+    }
+    c->nbwd = c->use_tc ? mlp_tc_bwd_blocks(bwd_points(c), crv->width, c->dim)
+                        : mlp_bwd_blocks(c->M, crv->width, (int)tc, c->dim);
     ALV(c->alpha, tc * nn);
     ALV(c->f, tc * c->M);
     ALV(c->u, tc * c->M);
@@ -935,9 +982,9 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const d
     ALV(c->am, tc * c->nparams);
     ALV(c->av, tc * c->nparams);
     ALV(c->grad, tc * c->nparams);
-    ALV(c->gpart, tc * (size_t)c->nbwd * c->nparams);
+    ALV(c->gpart, tc * (size_t)c->chunks * c->nbwd * c->nparams);
     if (c->use_tc) {
-      ALV(c->acts, mlp_tc_acts_bytes(c->M, crv->width));
+      ALV(c->acts, mlp_tc_acts_bytes(bwd_points(c), crv->width));
     } else {
       ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
     }

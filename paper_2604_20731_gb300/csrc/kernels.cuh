@@ -191,6 +191,9 @@ struct MlpTcArgs {
   int nparams;
   int* flags;             // bit 8: a tensor-core wait timed out
   int min_tiles = 1;      // forward: fewest 128-point tiles per CTA (a smaller grid)
+  // 128-point tiles of this launch: [tile0, tile0 + tile_count) (tile_count <= 0:
+  // to the last tile).  acts holds the launch's tiles from its start, tile0 first.
+  int tile0 = 0, tile_count = 0;
 };
 // Gram solve by sine transforms computed with FFTs (2D, N a power of two,
 // 8 <= N <= 2048): tables, partial count of the loss, and the three passes

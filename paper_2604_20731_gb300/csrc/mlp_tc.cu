@@ -368,10 +368,10 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
   const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(wt);
   uint32_t phase = 0;
   bool aborted = false;
-  const int ntiles = (a.npts + kTP - 1) / kTP;
+  const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
   const float b5 = fW5[W];
   for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
-    const int p0 = tile * kTP;
+    const int p0 = (a.tile0 + tile) * kTP;
     const int idx = min(p0 + row, a.npts - 1);
     float x[3];
     coords<DIN>(idx, a.N, x);
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   constexpr uint32_t kTileBytes = TcSmemB::ACT_TILE;
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
-  const int ntiles = (a.npts + kTP - 1) / kTP;
+  const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
   if (epi) {
     load_hidden_weights<kW, kBwdEpi>(th, o2, wt, tid);
     for (int i = tid; i < kW; i += kBwdEpi) fW5[i] = th[o5 + i];
@@ -658,13 +658,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     // dL/du of this row: loaded one tile ahead
     float g_next = 0.0f;
     if ((int)blockIdx.x < ntiles) {
-      const int i0 = blockIdx.x * kTP + row;
+      const int i0 = (a.tile0 + (int)blockIdx.x) * kTP + row;
       g_next = i0 < a.npts ? a.gu[i0] : 0.0f;
     }
     for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       const int buf = it & 1;
       const unsigned char* actb = act + buf * kTileBytes;
-      const int idx = tile * kTP + row;
+      const int idx = (a.tile0 + tile) * kTP + row;
       const float g = g_next;
       if (tile + (int)gridDim.x < ntiles) {
         const int i1 = idx + (int)gridDim.x * kTP;
@@ -915,7 +915,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
   float g_w5 = 0.f, g_b5 = 0.f, g_b1 = 0.f, g_w1[3] = {0.f, 0.f, 0.f}, g_bh[3] = {0.f, 0.f, 0.f};
   uint32_t phase = 0;
   bool aborted = false, first = true;
-  const int ntiles = (a.npts + kTP - 1) / kTP;
+  const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
   auto stage = [&](int slot, int L, int tile) {  // activations a_{L+1} (L = 0..3) of `tile`
     const unsigned char* src = a.acts + (size_t)tile * act_tile_bytes(W) + act_off(W, L);
     unsigned char* dst = act + slot * TcSmemB2<W>::ACT_SZ;
@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
   };
   if ((int)blockIdx.x < ntiles) stage(0, 3, blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
-    const int p0 = tile * kTP;
+    const int p0 = (a.tile0 + tile) * kTP;
     const int idx = p0 + tid;
     const float g = idx < a.npts ? a.gu[idx] : 0.0f;
     {
@@ -1117,13 +1117,23 @@ int mlp_tc_bwd_blocks(int npts, int width, int din, int min_tiles) {
   return ntiles < nb ? ntiles : nb;
 }
 
+// the launch's tile range made explicit
+static MlpTcArgs tile_range(MlpTcArgs a) {
+  const int tot = (a.npts + kTP - 1) / kTP;
+  if (a.tile0 < 0) a.tile0 = 0;
+  if (a.tile0 > tot) a.tile0 = tot;
+  if (a.tile_count <= 0 || a.tile0 + a.tile_count > tot) a.tile_count = tot - a.tile0;
+  return a;
+}
+
 template <int W, int DIN>
 static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   const size_t smem = TcSmemF<W>::TOTAL;
   auto k = k_mlp_fwd_tc<W, DIN>;
   smem_optin(k);
   const int occ = tc_residency(k, smem, W, kFwdThreads);
-  const int ntiles = (a.npts + kTP - 1) / kTP;
+  const int ntiles = a.tile_count;
+  if (ntiles <= 0) return cudaSuccess;
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
   if (want < grid) grid = want > 0 ? want : 1;
@@ -1131,9 +1141,10 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
-  if (a.npts <= 0) return cudaSuccess;
-  if (reinterpret_cast<uintptr_t>(a.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
+cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a0, cudaStream_t st) {
+  if (a0.npts <= 0) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(a0.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
+  const MlpTcArgs a = tile_range(a0);
   if (a.width == 64) return a.din == 2 ? fwd_tc<64, 2>(a, st) : fwd_tc<64, 3>(a, st);
   if (a.width == 128) return a.din == 2 ? fwd_tc<128, 2>(a, st) : fwd_tc<128, 3>(a, st);
   return cudaErrorNotSupported;
@@ -1148,8 +1159,9 @@ static cudaError_t bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st) {
-  if (reinterpret_cast<uintptr_t>(a.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
+cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a0, int nblk, cudaStream_t st) {
+  if (reinterpret_cast<uintptr_t>(a0.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
+  const MlpTcArgs a = tile_range(a0);
   if (a.width == 64) {
     const size_t smem = TcSmemB::TOTAL;
     auto k = a.din == 2 ? k_mlp_bwd_tc<2> : k_mlp_bwd_tc<3>;

@@ -39,7 +39,7 @@ class HybridSolver:
     """One scenario resident on the GPU: saturation, pressure, network, Adam."""
 
     def __init__(self, sc, width: Optional[int] = 64, crv_dtype: str = "f32",
-                 ads_dtype: str = "f64", stream=None):
+                 ads_dtype: str = "f64", stream=None, act_chunks: int = 0):
         self.lib = L.load()
         self.sc = sc
         if ads_dtype not in ("f64", "f32"):
@@ -47,7 +47,7 @@ class HybridSolver:
         self.params = make_params(sc, ads_dtype)
         self.crv = None
         if width is not None:
-            self.crv = L.crvpinn_params(width, 4, _DT[crv_dtype])
+            self.crv = L.crvpinn_params(width, 4, _DT[crv_dtype], int(act_chunks))
         K = np.ascontiguousarray(sc.K, dtype=np.float64)
         phi = None if sc.phi_map is None else np.ascontiguousarray(sc.phi_map, dtype=np.float64)
         S0 = np.ascontiguousarray(sc.S0_or_zero(), dtype=np.float64)

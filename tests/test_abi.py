@@ -43,6 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings(lib):
     assert lib.ads_status_str(0) == b"ok"
     assert lib.ads_status_str(5) == b"timeout"
+    assert lib.ads_status_str(8) == b"checkpoint file error"
     assert lib.ads_status_str(99) == b"unknown"
 
 
@@ -50,7 +51,7 @@ def test_struct_layouts_match_header():
     from paper_2604_20731_gb300 import _lib
     # ads_source: 3 doubles + sigma + rate + int (padded to 8)
     assert C.sizeof(_lib.ads_source) == 48
-    assert C.sizeof(_lib.crvpinn_params) == 12
+    assert C.sizeof(_lib.crvpinn_params) == 16  # width, hidden_layers, dtype, act_chunks
     assert C.sizeof(_lib.hybrid_stats) == 32
 
 
@@ -65,6 +66,10 @@ def test_hbm_estimate_and_validation(lib):
     assert 10e6 < b < 2e9
     b0 = lib.ads_hbm_estimate(C.byref(p), None)
     assert 0 < b0 < b
+    # activation recomputation: the stored activations shrink to one chunk
+    all_acts = _lib.crvpinn_params(128, 4, _lib.ADS_BF16, 1)
+    chunked = _lib.crvpinn_params(128, 4, _lib.ADS_BF16, 4)
+    assert lib.ads_hbm_estimate(C.byref(p), C.byref(chunked)) < lib.ads_hbm_estimate(C.byref(p), C.byref(all_acts))
     p.n = 1  # invalid
     assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) == 0
     p.n = 256

@@ -470,6 +470,29 @@ def test_gram_solve_cluster_and_three_pass_forms_agree(n):
     s.close()
 
 
+@pytest.mark.parametrize("n,width,chunks", [(64, 64, 3), (256, 64, 4), (70, 128, 2)])
+def test_activation_recomputation_same_results(n, width, chunks):
+    """act_chunks > 1: the iteration's forward stores no activations; the
+    backward runs chunk by chunk, each chunk's forward storing only that
+    chunk's (the last chunk shorter when the tiles do not divide).  Network
+    values and loss are the same bit for bit; the gradient partials are
+    grouped by chunk, so the gradient agrees to FP32 rounding; and an Adam
+    trajectory stays together."""
+    sc, s1, crv, theta, alpha, f = _crv_case(n, "bf16", width=width)
+    s2 = solver(sc, width=width, crv_dtype="bf16", act_chunks=chunks)
+    s2.set_theta(theta)
+    s2.update_coefficients()
+    loss1, loss2 = s1.loss_grad(), s2.loss_grad()
+    assert loss1 == loss2
+    assert np.array_equal(s1.get("U"), s2.get("U"))
+    assert rel_l2(s2.get("GRAD"), s1.get("GRAD")) <= 1e-5
+    s1.pressure_update(20, 1e-3)
+    s2.pressure_update(20, 1e-3)
+    assert rel_l2(s2.get("THETA"), s1.get("THETA")) <= 1e-4
+    s1.close()
+    s2.close()
+
+
 def test_config3_mesh_1024_mixed_precision():
     """1024^2 elements, FP32 saturation step vs the FP64 oracle (1e-5) and the
     BF16 width-128 network's loss and gradient vs the FP64 oracle at the
