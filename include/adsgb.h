@@ -155,6 +155,25 @@ ads_status ads_init(const ads_params* params, const crvpinn_params* crv,
                     const double* S0, void* stream, ads_ctx** out);
 void ads_destroy(ads_ctx* ctx);
 
+/* ads_init_with_allocator: ads_init whose context buffers come from the
+ * caller's allocator (e.g. a serving process's own pool).  alloc(bytes, user)
+ * returns device memory of this context's device, 256-byte aligned, or NULL
+ * (-> ADS_ERR_OOM); a misaligned block is handed back to free() and
+ * ads_init fails with ADS_ERR_INVALID_ARG.  free(ptr, user) is called for
+ * every block, by ads_destroy after the context's stream has finished or by
+ * a failing ads_init.  The short-lived staging buffers of ads_get and of the
+ * host uploads stay stream-ordered cudaMallocAsync blocks.  allocator NULL or
+ * with a NULL function: ads_init. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} ads_allocator;
+ads_status ads_init_with_allocator(const ads_params* params, const crvpinn_params* crv,
+                                   const double* K_nodal, const double* phi_nodal,
+                                   const double* S0, void* stream, const ads_allocator* allocator,
+                                   ads_ctx** out);
+
 /* Bytes of device memory ads_init would allocate (for admission control). */
 size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv);
 

@@ -38,6 +38,14 @@ class crvpinn_params(C.Structure):
     _fields_ = [("width", C.c_int), ("hidden_layers", C.c_int), ("dtype", C.c_int), ("act_chunks", C.c_int)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class ads_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
 class hybrid_params(C.Structure):
     _fields_ = [("n_sub", C.c_int), ("dt", C.c_double), ("dt_policy", C.c_int),
                 ("cfl", C.c_double), ("src_frac", C.c_double), ("adam_iters", C.c_int),
@@ -78,6 +86,8 @@ SIGNATURES = {
     "ads_init": (C.c_int, [C.POINTER(ads_params), C.POINTER(crvpinn_params), _D, _D, _D, _P,
                            C.POINTER(_P)]),
     "ads_destroy": (None, [_P]),
+    "ads_init_with_allocator": (C.c_int, [C.POINTER(ads_params), C.POINTER(crvpinn_params), _D, _D, _D, _P,
+                                          C.POINTER(ads_allocator), C.POINTER(_P)]),
     "ads_hbm_estimate": (C.c_size_t, [C.POINTER(ads_params), C.POINTER(crvpinn_params)]),
     "ads_set_concurrency": (C.c_int, [_P, C.c_int]),
     "ads_save": (C.c_int, [_P, C.c_char_p]),

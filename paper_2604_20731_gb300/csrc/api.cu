@@ -41,6 +41,7 @@ struct ads_ctx {
   std::string err;
   std::vector<void*> allocs;
   size_t bytes = 0;
+  ads_allocator user_alloc{};  // caller's allocator (ads_init_with_allocator), else cudaMalloc
 
   // FP64 tables
   double *B64 = nullptr, *dB64 = nullptr, *l1_64 = nullptr, *l2_64 = nullptr, *dinv64 = nullptr,
@@ -103,6 +104,18 @@ ads_status fail(ads_ctx* c, ads_status st, const std::string& msg) {
 ads_status alloc(ads_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (c->user_alloc.alloc) {
+    *p = c->user_alloc.alloc(bytes, c->user_alloc.user);
+    if (!*p) return fail(c, ADS_ERR_OOM, "allocator: no memory");
+    if (reinterpret_cast<uintptr_t>(*p) & 255) {
+      c->user_alloc.free(*p, c->user_alloc.user);
+      *p = nullptr;
+      return fail(c, ADS_ERR_INVALID_ARG, "allocator: block not 256-byte aligned");
+    }
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    return ADS_OK;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -785,7 +798,10 @@ void ads_destroy(ads_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) {
+    if (c->user_alloc.alloc) c->user_alloc.free(p, c->user_alloc.user);
+    else cudaFree(p);
+  }
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -793,12 +809,20 @@ void ads_destroy(ads_ctx* c) {
 
 ads_status ads_init(const ads_params* params, const crvpinn_params* crv, const double* K_nodal,
                     const double* phi_nodal, const double* S0, void* stream, ads_ctx** out) {
+  return ads_init_with_allocator(params, crv, K_nodal, phi_nodal, S0, stream, nullptr, out);
+}
+
+ads_status ads_init_with_allocator(const ads_params* params, const crvpinn_params* crv,
+                                   const double* K_nodal, const double* phi_nodal,
+                                   const double* S0, void* stream, const ads_allocator* allocator,
+                                   ads_ctx** out) {
   if (!out) return ADS_ERR_INVALID_ARG;
   *out = nullptr;
   ads_status v = validate(params, crv);
   if (v != ADS_OK) return v;
   if (!K_nodal) return ADS_ERR_INVALID_ARG;
   ads_ctx* c = new ads_ctx();
+  if (allocator && allocator->alloc && allocator->free) c->user_alloc = *allocator;
   c->prm = *params;
   c->dim = params->dim;
   c->n = params->n;

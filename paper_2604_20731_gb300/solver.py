@@ -39,7 +39,7 @@ class HybridSolver:
     """One scenario resident on the GPU: saturation, pressure, network, Adam."""
 
     def __init__(self, sc, width: Optional[int] = 64, crv_dtype: str = "f32",
-                 ads_dtype: str = "f64", stream=None, act_chunks: int = 0):
+                 ads_dtype: str = "f64", stream=None, act_chunks: int = 0, allocator=None):
         self.lib = L.load()
         self.sc = sc
         if ads_dtype not in ("f64", "f32"):
@@ -55,9 +55,20 @@ class HybridSolver:
         st = None
         if stream is not None:
             st = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-        rc = self.lib.ads_init(C.byref(self.params), C.byref(self.crv) if self.crv else None,
-                               _dptr(K), _dptr(phi) if phi is not None else None, _dptr(S0),
-                               st, C.byref(handle))
+        if allocator is None:
+            rc = self.lib.ads_init(C.byref(self.params), C.byref(self.crv) if self.crv else None,
+                                   _dptr(K), _dptr(phi) if phi is not None else None, _dptr(S0),
+                                   st, C.byref(handle))
+        else:
+            # allocator = (alloc(bytes) -> device pointer or 0, free(pointer)); the
+            # callbacks live as long as this object
+            fa, ff = allocator
+            self._alloc = L.ads_allocator(L.ALLOC_FN(lambda nbytes, user: fa(nbytes) or None),
+                                          L.FREE_FN(lambda ptr, user: ff(ptr)), None)
+            rc = self.lib.ads_init_with_allocator(C.byref(self.params),
+                                                  C.byref(self.crv) if self.crv else None, _dptr(K),
+                                                  _dptr(phi) if phi is not None else None, _dptr(S0),
+                                                  st, C.byref(self._alloc), C.byref(handle))
         if rc != L.ADS_OK:
             raise L.AdsError(rc, "ads_init")
         self.ctx = handle
