@@ -361,8 +361,9 @@ def run_ours(a, world, rank, local):
         for s in ctxs:
             s.hybrid_step(hp, stats=False)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local, path=os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    # raw samples to a CSV when ADSGB_CLOCKS_CSV names a file (rank appended)
+    csv_path = os.environ.get("ADSGB_CLOCKS_CSV")
+    clocks = ClockSampler(local, path=f"{csv_path}.rank{rank}" if csv_path else None)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in streams]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in streams]
     round_ev = [[torch.cuda.Event(enable_timing=True) for _ in streams] for _ in range(a.steps)]

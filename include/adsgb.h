@@ -254,8 +254,8 @@ ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stat
 ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
                              hybrid_stats* stats);
 
-/* ---- serving: continuous batching of many scenarios (the benchmark spec pattern; the
- * paper has one scenario) ---------------------------------------------------
+/* ---- serving: continuous batching of many scenarios (the paper steps one
+ * scenario at a time) ----------------------------------------------------------
  * A server owns a worker thread and n_streams CUDA streams on the current
  * device.  ads_server_submit copies a scenario (parameters, network, hybrid
  * step parameters, number of hybrid steps, pretraining at admission, and its
