@@ -2,11 +2,12 @@
 // unit cube; Secs. 3-4 of the paper, written there for 2D, extended with the
 // third Kronecker factor: M = Mx (x) My (x) Mz).
 //
-//   k_elem3d:   one thread per element; fields at its 27 Gauss points are
-//               sum-factorised along x, y, z; the 27 local contributions to
-//               the right-hand side of the L2 projection are written to a
-//               per-element buffer (MODE 0: saturation step, MODE 1: L2
-//               projection of nodal values).
+//   k_elem3d:   one thread per element; the Gauss points are taken plane by
+//               plane along z, the fields sum-factorised (z, then y, then x)
+//               and the test functions applied back (x, then y, then z into
+//               the element's 27 right-hand-side entries, which are written
+//               component-major: entry i of all elements contiguous).  MODE
+//               0: saturation step; MODE 1: L2 projection of nodal values.
 //   k_gather3d: one thread per DOF sums the contributions of its (up to) 27
 //               elements in a fixed order (deterministic, no atomics).
 //   k_xsolve3d: LDL^T sweeps along x (contiguous rows staged in shared memory).
@@ -20,6 +21,12 @@
 
 namespace adsgb {
 
+// the fractional flow's quotient (the fast single-precision divide in FP32)
+template <typename T>
+ADS_D T frac3(T a, T b) { return a / b; }
+template <>
+ADS_D float frac3<float>(float a, float b) { return __fdividef(a, b); }
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_elem3d(QuadArgs<T> a, T* C, double* src_part) {
   __shared__ double red[32];
@@ -29,168 +36,173 @@ __global__ void __launch_bounds__(128) k_elem3d(QuadArgs<T> a, T* C, double* src
   double src = 0.0;
   if (e < ne) {
     const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((long long)n * n));
-    T bx[3][3], dbx[3][3], by[3][3], dby[3][3], bz[3][3], dbz[3][3];
+    const T* Bx = a.ax.B + ex * 9;
+    const T* dBx = a.ax.dB + ex * 9;
+    const T* By = a.ax.B + ey * 9;
+    const T* dBy = a.ax.dB + ey * 9;
+    const T* Bz = a.ax.B + ez * 9;
+    const T* dBz = a.ax.dB + ez * 9;
+    T bx[3][3], dbx[3][3];  // [function][point], used at every point
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      bx[i / 3][i % 3] = a.ax.B[ex * 9 + i];
-      dbx[i / 3][i % 3] = a.ax.dB[ex * 9 + i];
-      by[i / 3][i % 3] = a.ax.B[ey * 9 + i];
-      dby[i / 3][i % 3] = a.ax.dB[ey * 9 + i];
-      bz[i / 3][i % 3] = a.ax.B[ez * 9 + i];
-      dbz[i / 3][i % 3] = a.ax.dB[ez * 9 + i];
+      bx[i / 3][i % 3] = __ldg(Bx + i);
+      dbx[i / 3][i % 3] = __ldg(dBx + i);
     }
-    // c-coefficients at the 27 Gauss points [qz][qy][qx]
-    T c0[3][3][3], cx[3][3][3], cy[3][3][3], cz[3][3][3];
     const T h3 = a.h * a.h * a.h;
-    if (MODE == 0) {
-      // contraction along x for each (bz, by) row: S, P, dP/dx
-      T Sx[3][3][3], Px[3][3][3], Pdx[3][3][3];  // [bz][by][qx]
+    // element right-hand side, accumulated plane by plane of Gauss points
+    T R[3][3][3];  // [z fn][y fn][x fn]
+#pragma unroll
+    for (int i = 0; i < 27; ++i) R[i / 9][(i / 3) % 3][i % 3] = T(0);
+    // coefficients (MODE 0: S and P) held for all planes in FP32; in FP64
+    // (twice the registers) reread for each plane from the L1 cache
+    constexpr bool kHold = sizeof(T) == sizeof(float);
+    T s[3][3][3], p[3][3][3];
+    T kc[2][2][2], fc[2][2][2];
+    auto load_sp = [&]() {
 #pragma unroll
       for (int b2 = 0; b2 < 3; ++b2)
 #pragma unroll
         for (int b1 = 0; b1 < 3; ++b1) {
           const size_t row = ((size_t)(ez + b2) * nb + (ey + b1)) * nb + ex;
-          const T s0 = a.S[row], s1 = a.S[row + 1], s2 = a.S[row + 2];
-          const T p0 = a.P[row], p1 = a.P[row + 1], p2 = a.P[row + 2];
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            Sx[b2][b1][q] = s0 * bx[0][q] + s1 * bx[1][q] + s2 * bx[2][q];
-            Px[b2][b1][q] = p0 * bx[0][q] + p1 * bx[1][q] + p2 * bx[2][q];
-            Pdx[b2][b1][q] = p0 * dbx[0][q] + p1 * dbx[1][q] + p2 * dbx[2][q];
+          for (int b0 = 0; b0 < 3; ++b0) {
+            s[b2][b1][b0] = __ldg(a.S + row + b0);
+            p[b2][b1][b0] = __ldg(a.P + row + b0);
           }
         }
-      // along y: S, P, dP/dx, dP/dy at (bz, qy, qx)
-      T Sy[3][3][3], Py[3][3][3], Pdxy[3][3][3], Pdy[3][3][3];
+    };
+    if (MODE == 0 && kHold) load_sp();
 #pragma unroll
-      for (int b2 = 0; b2 < 3; ++b2)
-#pragma unroll
-        for (int qy = 0; qy < 3; ++qy)
-#pragma unroll
-          for (int qx = 0; qx < 3; ++qx) {
-            Sy[b2][qy][qx] = by[0][qy] * Sx[b2][0][qx] + by[1][qy] * Sx[b2][1][qx] + by[2][qy] * Sx[b2][2][qx];
-            Py[b2][qy][qx] = by[0][qy] * Px[b2][0][qx] + by[1][qy] * Px[b2][1][qx] + by[2][qy] * Px[b2][2][qx];
-            Pdxy[b2][qy][qx] = by[0][qy] * Pdx[b2][0][qx] + by[1][qy] * Pdx[b2][1][qx] + by[2][qy] * Pdx[b2][2][qx];
-            Pdy[b2][qy][qx] = dby[0][qy] * Px[b2][0][qx] + dby[1][qy] * Px[b2][1][qx] + dby[2][qy] * Px[b2][2][qx];
-          }
-      // nodal K and phi at the 8 corners
-      T kc[2][2][2], fc[2][2][2];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
-        const size_t nd = ((size_t)(ez + dz) * n1 + (ey + dy)) * n1 + (ex + dx);
-        kc[dz][dy][dx] = a.K[nd];
-        fc[dz][dy][dx] = a.phi ? a.phi[nd] : a.phi_c;
-      }
-      const T dt = (T)(*a.dt);
-      for (int qz = 0; qz < 3; ++qz) {
-        const T zeta = (T)gauss_x(qz);
-        for (int qy = 0; qy < 3; ++qy) {
-          const T eta = (T)gauss_x(qy);
-          for (int qx = 0; qx < 3; ++qx) {
-            const T xi = (T)gauss_x(qx);
-            T Sv = bz[0][qz] * Sy[0][qy][qx] + bz[1][qz] * Sy[1][qy][qx] + bz[2][qz] * Sy[2][qy][qx];
-            T dpx = bz[0][qz] * Pdxy[0][qy][qx] + bz[1][qz] * Pdxy[1][qy][qx] + bz[2][qz] * Pdxy[2][qy][qx];
-            T dpy = bz[0][qz] * Pdy[0][qy][qx] + bz[1][qz] * Pdy[1][qy][qx] + bz[2][qz] * Pdy[2][qy][qx];
-            T dpz = dbz[0][qz] * Py[0][qy][qx] + dbz[1][qz] * Py[1][qy][qx] + dbz[2][qz] * Py[2][qy][qx];
-            T wz[2] = {T(1) - zeta, zeta}, wy[2] = {T(1) - eta, eta}, wx[2] = {T(1) - xi, xi};
-            T Kq = T(0), phq = T(0);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
-              const T w = wz[dz] * wy[dy] * wx[dx];
-              Kq += w * kc[dz][dy][dx];
-              phq += w * fc[dz][dy][dx];
-            }
-            T St = clamp01(Sv);
-            T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
-            T qi = T(0), qp = T(0);
-            for (int s = 0; s < a.n_src; ++s) {
-              T g = a.rate[s] * a.ax.gsrc[((size_t)(0 * kMaxSrc + s) * n + ex) * 3 + qx] *
-                    a.ax.gsrc[((size_t)(1 * kMaxSrc + s) * n + ey) * 3 + qy] *
-                    a.ax.gsrc[((size_t)(2 * kMaxSrc + s) * n + ez) * 3 + qz];
-              if (a.kind[s] == 0) qi += g; else qp += g;
-            }
-            T qg = qi - lg / (lg + lw) * qp;
-            T w = (T)(gauss_w(qx) * gauss_w(qy) * gauss_w(qz)) * h3;
-            T dtphi = dt / phq;
-            c0[qz][qy][qx] = w * (Sv + dtphi * qg);
-            T cf = -w * dtphi * lg * Kq;
-            cx[qz][qy][qx] = cf * dpx;
-            cy[qz][qy][qx] = cf * dpy;
-            cz[qz][qy][qx] = cf * a.kz * (dpz + a.grav_term);
-            src += (double)(w * dtphi * qg);
-          }
-        }
-      }
-    } else {
-      T uc[2][2][2];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
-        uc[dz][dy][dx] = a.nodal[((size_t)(ez + dz) * n1 + (ey + dy)) * n1 + (ex + dx)];
-      }
-      for (int qz = 0; qz < 3; ++qz)
-        for (int qy = 0; qy < 3; ++qy)
-          for (int qx = 0; qx < 3; ++qx) {
-            const T zeta = (T)gauss_x(qz), eta = (T)gauss_x(qy), xi = (T)gauss_x(qx);
-            T wz[2] = {T(1) - zeta, zeta}, wy[2] = {T(1) - eta, eta}, wx[2] = {T(1) - xi, xi};
-            T uq = T(0);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
-              uq += wz[dz] * wy[dy] * wx[dx] * uc[dz][dy][dx];
-            }
-            c0[qz][qy][qx] = (T)(gauss_w(qx) * gauss_w(qy) * gauss_w(qz)) * h3 * uq;
-            cx[qz][qy][qx] = cy[qz][qy][qx] = cz[qz][qy][qx] = T(0);
-          }
+    for (int i = 0; i < 8; ++i) {
+      const int dz = i >> 2, dy = (i >> 1) & 1, dx = i & 1;
+      const size_t nd = ((size_t)(ez + dz) * n1 + (ey + dy)) * n1 + (ex + dx);
+      kc[dz][dy][dx] = MODE == 0 ? __ldg(a.K + nd) : __ldg(a.nodal + nd);
+      fc[dz][dy][dx] = (MODE == 0 && a.phi) ? __ldg(a.phi + nd) : a.phi_c;
     }
-    // test functions: along x, then y, then z
-    T Tx0[3][3][3], Txy[3][3][3], Txz[3][3][3];  // [qz][qy][a]
+    const T dt = MODE == 0 ? (T)(*a.dt) : T(0);
+    const T dtphi_c = MODE == 0 ? dt / a.phi_c : T(0);  // porosity without a map
+    T src_e = T(0);  // this element's source integral (27 terms), then one FP64 add
+    // (one plane's code, run three times: the unrolled body is large)
+#pragma unroll 1
+    for (int qz = 0; qz < 3; ++qz) {
+      const T zeta = (T)gauss_x(qz), wzh3 = (T)gauss_w(qz) * h3;
+      T bzq[3], dbzq[3];  // the z factors at this plane
 #pragma unroll
-    for (int qz = 0; qz < 3; ++qz)
+      for (int c = 0; c < 3; ++c) {
+        bzq[c] = __ldg(Bz + c * 3 + qz);
+        dbzq[c] = __ldg(dBz + c * 3 + qz);
+      }
+      // z contraction: S, P and dP/dz on this plane, per (y, x) function
+      T Sz[3][3], Pz[3][3], Pzd[3][3];
+      if (MODE == 0) {
+        if (!kHold) load_sp();
 #pragma unroll
-      for (int qy = 0; qy < 3; ++qy)
+        for (int b1 = 0; b1 < 3; ++b1)
 #pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          T t0 = T(0), t1 = T(0), t2 = T(0);
-#pragma unroll
-          for (int qx = 0; qx < 3; ++qx) {
-            t0 += c0[qz][qy][qx] * bx[aa][qx] + cx[qz][qy][qx] * dbx[aa][qx];
-            t1 += cy[qz][qy][qx] * bx[aa][qx];
-            t2 += cz[qz][qy][qx] * bx[aa][qx];
+          for (int b0 = 0; b0 < 3; ++b0) {
+            Sz[b1][b0] = bzq[0] * s[0][b1][b0] + bzq[1] * s[1][b1][b0] + bzq[2] * s[2][b1][b0];
+            Pz[b1][b0] = bzq[0] * p[0][b1][b0] + bzq[1] * p[1][b1][b0] + bzq[2] * p[2][b1][b0];
+            Pzd[b1][b0] = dbzq[0] * p[0][b1][b0] + dbzq[1] * p[1][b1][b0] + dbzq[2] * p[2][b1][b0];
           }
-          Tx0[qz][qy][aa] = t0;
-          Txy[qz][qy][aa] = t1;
-          Txz[qz][qy][aa] = t2;
+      }
+      // trilinear K, phi: the z interpolation on this plane
+      T kz[2][2], fz[2][2];
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          kz[dy][dx] = (T(1) - zeta) * kc[0][dy][dx] + zeta * kc[1][dy][dx];
+          fz[dy][dx] = (T(1) - zeta) * fc[0][dy][dx] + zeta * fc[1][dy][dx];
         }
-    T Ty0[3][3][3], Tyz[3][3][3];  // [qz][b][a]
+      T Ty0[3][3], Tyz[3][3];  // [y fn][x fn]: y contraction of this plane
 #pragma unroll
-    for (int qz = 0; qz < 3; ++qz)
+      for (int i = 0; i < 9; ++i) Ty0[i / 3][i % 3] = Tyz[i / 3][i % 3] = T(0);
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
+      for (int qy = 0; qy < 3; ++qy) {
+        const T eta = (T)gauss_x(qy);
+        T byq[3], dbyq[3];
 #pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          T t0 = T(0), t2 = T(0);
+        for (int c = 0; c < 3; ++c) {
+          byq[c] = __ldg(By + c * 3 + qy);
+          dbyq[c] = __ldg(dBy + c * 3 + qy);
+        }
+        T Syz[3], Pyz[3], Pydy[3], Pzy[3];  // per x function
+        if (MODE == 0) {
 #pragma unroll
-          for (int qy = 0; qy < 3; ++qy) {
-            t0 += by[b][qy] * Tx0[qz][qy][aa] + dby[b][qy] * Txy[qz][qy][aa];
-            t2 += by[b][qy] * Txz[qz][qy][aa];
+          for (int b0 = 0; b0 < 3; ++b0) {
+            Syz[b0] = byq[0] * Sz[0][b0] + byq[1] * Sz[1][b0] + byq[2] * Sz[2][b0];
+            Pyz[b0] = byq[0] * Pz[0][b0] + byq[1] * Pz[1][b0] + byq[2] * Pz[2][b0];
+            Pydy[b0] = dbyq[0] * Pz[0][b0] + dbyq[1] * Pz[1][b0] + dbyq[2] * Pz[2][b0];
+            Pzy[b0] = byq[0] * Pzd[0][b0] + byq[1] * Pzd[1][b0] + byq[2] * Pzd[2][b0];
           }
-          Ty0[qz][b][aa] = t0;
-          Tyz[qz][b][aa] = t2;
         }
-    T* out = C + (size_t)e * 27;
+        const T ky[2] = {(T(1) - eta) * kz[0][0] + eta * kz[1][0], (T(1) - eta) * kz[0][1] + eta * kz[1][1]};
+        const T fy[2] = {(T(1) - eta) * fz[0][0] + eta * fz[1][0], (T(1) - eta) * fz[0][1] + eta * fz[1][1]};
+        T Tx0[3] = {T(0), T(0), T(0)}, Txy[3] = {T(0), T(0), T(0)}, Txz[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int cz2 = 0; cz2 < 3; ++cz2)
+        for (int qx = 0; qx < 3; ++qx) {
+          const T xi = (T)gauss_x(qx);
+          const T w = (T)(gauss_w(qx) * gauss_w(qy)) * wzh3;
+          const T Kq = (T(1) - xi) * ky[0] + xi * ky[1];
+          T c0, cx = T(0), cy = T(0), cz = T(0);
+          if (MODE == 0) {
+            const T Sv = bx[0][qx] * Syz[0] + bx[1][qx] * Syz[1] + bx[2][qx] * Syz[2];
+            const T dpx = dbx[0][qx] * Pyz[0] + dbx[1][qx] * Pyz[1] + dbx[2][qx] * Pyz[2];
+            const T dpy = bx[0][qx] * Pydy[0] + bx[1][qx] * Pydy[1] + bx[2][qx] * Pydy[2];
+            const T dpz = bx[0][qx] * Pzy[0] + bx[1][qx] * Pzy[1] + bx[2][qx] * Pzy[2];
+            const T phq = (T(1) - xi) * fy[0] + xi * fy[1];
+            const T St = clamp01(Sv);
+            const T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
+            T qi = T(0), qp = T(0);
+            for (int sidx = 0; sidx < a.n_src; ++sidx) {
+              const T gv = a.rate[sidx] * __ldg(a.ax.gsrc + ((size_t)(0 * kMaxSrc + sidx) * n + ex) * 3 + qx) *
+                           __ldg(a.ax.gsrc + ((size_t)(1 * kMaxSrc + sidx) * n + ey) * 3 + qy) *
+                           __ldg(a.ax.gsrc + ((size_t)(2 * kMaxSrc + sidx) * n + ez) * 3 + qz);
+              if (a.kind[sidx] == 0) qi += gv;
+              else qp += gv;
+            }
+            T qg = qi;
+            if (qp != T(0)) qg -= frac3(lg, lg + lw) * qp;
+            const T dtphi = a.phi ? dt / phq : dtphi_c;
+            const T wq = w * dtphi * qg;
+            c0 = w * Sv + wq;
+            const T cf = -w * dtphi * lg * Kq;
+            cx = cf * dpx;
+            cy = cf * dpy;
+            cz = cf * a.kz * (dpz + a.grav_term);
+            src_e += wq;
+          } else {
+            c0 = w * Kq;  // (MODE 1: kc holds the nodal values)
+          }
+          // test functions along x
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          T v = T(0);
-#pragma unroll
-          for (int qz = 0; qz < 3; ++qz) v += bz[cz2][qz] * Ty0[qz][b][aa] + dbz[cz2][qz] * Tyz[qz][b][aa];
-          out[(cz2 * 3 + b) * 3 + aa] = v;
+          for (int aa = 0; aa < 3; ++aa) {
+            Tx0[aa] += c0 * bx[aa][qx] + cx * dbx[aa][qx];
+            Txy[aa] += cy * bx[aa][qx];
+            Txz[aa] += cz * bx[aa][qx];
+          }
         }
+        // along y
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) {
+            Ty0[b][aa] += byq[b] * Tx0[aa] + dbyq[b] * Txy[aa];
+            Tyz[b][aa] += byq[b] * Txz[aa];
+          }
+      }
+      // along z, into the element's right-hand side
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) R[c2][b][aa] += bzq[c2] * Ty0[b][aa] + dbzq[c2] * Tyz[b][aa];
+    }
+    src = (double)src_e;
+    // component-major: component i of all elements is contiguous (coalesced)
+#pragma unroll
+    for (int i = 0; i < 27; ++i) C[(size_t)i * ne + e] = R[i / 9][(i / 3) % 3][i % 3];
   }
   if (MODE == 0) {
     double tot = block_sum(src, red);
@@ -199,13 +211,14 @@ __global__ void __launch_bounds__(128) k_elem3d(QuadArgs<T> a, T* C, double* src
 }
 
 // R[kz][ky][kx] = sum over elements e with e_d in [k_d - 2, k_d] of
-// C[e][(kz-ez)*9 + (ky-ey)*3 + (kx-ex)], in a fixed order
+// C[(kz-ez)*9 + (ky-ey)*3 + (kx-ex)][e], in a fixed order
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather3d(int n, const T* __restrict__ C, T* __restrict__ R) {
   const int nb = n + 2;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nb * nb * nb) return;
   const int kx = (int)(t % nb), ky = (int)((t / nb) % nb), kz = (int)(t / ((long long)nb * nb));
+  const size_t ne = (size_t)n * n * n;
   T v = T(0);
   for (int dz = 0; dz < 3; ++dz) {
     const int ez = kz - dz;
@@ -217,7 +230,7 @@ __global__ void __launch_bounds__(256) k_gather3d(int n, const T* __restrict__ C
         const int ex = kx - dx;
         if (ex < 0 || ex >= n) continue;
         const size_t e = ((size_t)ez * n + ey) * n + ex;
-        v += C[e * 27 + (dz * 3 + dy) * 3 + dx];
+        v += C[(size_t)((dz * 3 + dy) * 3 + dx) * ne + e];
       }
     }
   }
