@@ -638,6 +638,7 @@ ads_status validate(const ads_params* p, const crvpinn_params* cp) {
     if (cp->width != 64 && cp->width != 128) return ADS_ERR_UNSUPPORTED;
     if (cp->dtype != ADS_F64 && cp->dtype != ADS_F32 && cp->dtype != ADS_BF16) return ADS_ERR_UNSUPPORTED;
     if (cp->dtype == ADS_F64 && cp->width != 64) return ADS_ERR_UNSUPPORTED;
+    if (cp->act_chunks < 0) return ADS_ERR_INVALID_ARG;
     if (p->n < 3) return ADS_ERR_INVALID_ARG;
   }
   return ADS_OK;

@@ -70,6 +70,7 @@ def test_hbm_estimate_and_validation(lib):
     all_acts = _lib.crvpinn_params(128, 4, _lib.ADS_BF16, 1)
     chunked = _lib.crvpinn_params(128, 4, _lib.ADS_BF16, 4)
     assert lib.ads_hbm_estimate(C.byref(p), C.byref(chunked)) < lib.ads_hbm_estimate(C.byref(p), C.byref(all_acts))
+    assert lib.ads_hbm_estimate(C.byref(p), C.byref(_lib.crvpinn_params(128, 4, _lib.ADS_BF16, -1))) == 0
     p.n = 1  # invalid
     assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) == 0
     p.n = 256
