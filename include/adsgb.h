@@ -335,7 +335,9 @@ ads_status ads_sync(ads_ctx* ctx, double timeout_s);
  * ads_load: read such a file into a context made by ads_init with the same
  * dim, n, saturation precision, phi map presence and network (width, layers,
  * precision, parameter count); the next calls continue bit for bit as the
- * saved context would have.  Drops cached graphs.
+ * saved context would have with the same launch settings (ads_set_concurrency
+ * and act_chunks are settings of the context, not part of the checkpoint).
+ * Drops cached graphs.
  * Errors: ADS_ERR_INVALID_ARG (NULL path; a file of another shape or not a
  * checkpoint), ADS_ERR_IO (open, write or short read), ADS_ERR_CUDA. */
 ads_status ads_save(ads_ctx* ctx, const char* path);
