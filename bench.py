@@ -49,7 +49,7 @@ def args_parse():
     ap.add_argument("--pretrain", type=int, default=300)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--scenarios", type=int, default=64)
-    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--streams", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--arrival-ms", type=float, default=20.0)
     ap.add_argument("--e2e-steps", type=int, default=10)
