@@ -180,7 +180,7 @@ size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv);
 /* ads_set_concurrency: the number of contexts expected to run on the GPU at
  * the same time as this one (default 1).  Above 1, the tensor-core network
  * kernels launch fewer CTAs that each take more 128-point tiles (at least 4
- * per forward CTA and 32 per backward CTA): the context's own iterations take
+ * per forward CTA and 64 per backward CTA): the context's own iterations take
  * longer, the GPU's total throughput over the concurrent contexts rises.
  * Results agree within rounding (the gradient partials are summed in another
  * grouping).  Drops the context's cached graphs; waits for its stream.

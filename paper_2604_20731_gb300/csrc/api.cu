@@ -279,9 +279,10 @@ MlpArgs<TC> mlp_args(ads_ctx* c, bool store) {
 // the GPU with other concurrent contexts: fewer CTAs that each take at least
 // this many 128-point tiles.  Each CTA pays a fixed cost (weight staging,
 // TMEM set-up, the gradient partial); with other work to fill the SMs, fewer
-// and longer CTAs raise the total throughput (measured on a 64-scenario mix
-// over 8 streams: +16 % steps/s against one tile per CTA).
-constexpr int kFwdTilesShared = 4, kBwdTilesShared = 32;
+// and longer CTAs raise the total throughput.  On a 64-scenario mix over 16
+// streams, 32/64/96/128 tiles per backward CTA gave 244/252/251/230 steps/s
+// and 8 tiles per forward CTA no gain over 4.
+constexpr int kFwdTilesShared = 4, kBwdTilesShared = 64;
 
 MlpTcArgs mlp_tc_args(ads_ctx* c, bool store) {
   MlpTcArgs a{};
