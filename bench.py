@@ -55,6 +55,7 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--c2-steps", type=int, default=20)
+    ap.add_argument("--c1-steps", type=int, default=20)
     ap.add_argument("--err-iters", type=int, default=60000)
     ap.add_argument("--err-steps", type=int, default=3)
     ap.add_argument("--sat-n", type=int, default=4096)
@@ -285,6 +286,54 @@ def serving_mix(count, seed=3):
         rate = float(rng.uniform(0.5, 2.0))
         out.append(scn.make_scenario(2, n, seed=1000 + i + 100000 * (seed - 3), sigma=sigma, rate=rate))
     return out
+
+
+def plain_method_c1(a, scn, HybridSolver, device):
+    """Configuration 1: the plain method of Sec. 7 on 32 x 32 elements in FP64.
+    Each step is the Galerkin pressure, solved directly on the GPU, followed by
+    n_sub explicit saturation steps with the CFL step size.  Timed with CUDA
+    events on the solver's stream.  Reported beside it: the error against the
+    oracle's plain step and the oracle's own time on the host cores."""
+    import numpy as np
+    import torch
+    from oracle.hybrid import plain_step
+    sc = scn.make_scenario(2, 32, seed=1000)
+    st = torch.cuda.Stream(device=device)
+    s = HybridSolver(sc, width=None, ads_dtype="f64", stream=st)
+    s.plain_step(a.n_sub)
+    t0 = time.perf_counter()
+    S_ref, P_ref, dt_ref = plain_step(sc, sc.S0_or_zero(), a.n_sub, cfl=0.1)
+    cpu_ms = (time.perf_counter() - t0) * 1e3
+    rel = lambda x, y: float(np.abs(x - y).max() / np.abs(y).max())
+    err = {"pressure_rel_linf_vs_oracle_direct": rel(s.get("P"), P_ref),
+           "saturation_rel_linf_vs_oracle": rel(s.get("S"), S_ref),
+           "dt_rel": abs(float(s.get("DT")[0]) - dt_ref) / dt_ref}
+    for _ in range(3):
+        s.plain_step(a.n_sub)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(a.c1_steps):
+        s.plain_step(a.n_sub)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.c1_steps
+    e0.record(st)
+    for _ in range(a.c1_steps):
+        s.galerkin_pressure()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_gal = e0.elapsed_time(e1) / a.c1_steps
+    s.get("S")  # a bounded wait that gave up, or a non-finite pivot, fails here
+    s.close()
+    n = 32
+    nu, bw = n * n, 2 * n + 2
+    return {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "galerkin_pressure_ms": ms_gal,
+            "cholesky_flop": nu * bw * (bw + 1), "error": err,
+            "oracle_ms_per_step": cpu_ms, "oracle_cores": 1,
+            "note": f"32^2 elements, FP64, {a.n_sub} saturation steps per step, CFL dt; the Galerkin "
+                    "pressure (assembly + banded Cholesky + two triangular sweeps, one thread block "
+                    "for the sequential pivots) is latency-bound; the oracle uses SuperLU"}
 
 
 def saturation_roofline(n, scn, HybridSolver):
@@ -604,7 +653,12 @@ def run_ours(a, world, rank, local):
               "note": "single scenario, L2-resident working set"}
         s.close()
 
-    # ---- (4b) saturation kernels on a mesh larger than L2 (FP32 and FP64) ----
+    # ---- (4b) config 1: the plain method (Galerkin pressure, direct FP64 solve) ----
+    c1 = None
+    if rank == 0 and a.c1_steps > 0:
+        c1 = plain_method_c1(a, scn, HybridSolver, device)
+
+    # ---- (4c) saturation kernels on a mesh larger than L2 (FP32 and FP64) ----
     sat = None
     if rank == 0 and a.sat_n > 0:
         sat = saturation_roofline(a.sat_n, scn, HybridSolver)
@@ -634,7 +688,8 @@ def run_ours(a, world, rank, local):
                "latency_note": "resident run: a scenario's step latency is the round time (all "
                                "scenarios step once per round); e2e holds the server's per-step latency",
                "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2, "saturation": sat,
+               "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2, "c1_plain_galerkin": c1,
+               "saturation": sat,
                "gpu_launches": launches, "clocks": clk, "kernel_ms_by_n": prof_by_n,
                "server": server_stats}
         print(json.dumps(out), flush=True)

@@ -204,6 +204,28 @@ ads_status ads_saturation_step(ads_ctx* ctx, double dt, int n_sub);
 ads_status ads_cfl_dt(ads_ctx* ctx, double cfl, double src_frac, double dt_cap,
                       double* dt_out);
 
+/* ---- Galerkin pressure: the plain method (Sec. 7; system of Sec. 4) ---------
+ * ads_galerkin_pressure: sets the pressure coefficients to the solution of the
+ * B-spline Galerkin pressure system for the current saturation -- the weak
+ * form Eq. 12a in the space of Eqs. 15-20:
+ *   (lambda K grad p, grad v) = (q_w + q_g, v) - (g K rho lambda, dv/dy)
+ * for every interior tensor B-spline v, p = 0 on the boundary (Sec. 8.1),
+ * lambda = lambda_w + lambda_g and rho lambda = rho_w lambda_w + rho_g lambda_g
+ * of the clamped saturation, K the bilinear nodal map.  This is the pressure
+ * the IGA-ADS + direct solver baseline uses instead of the network.  It is
+ * assembled by 3-point Gauss quadrature and solved by a banded Cholesky
+ * factorisation, all in FP64 whatever ads_dtype is (the result is stored in
+ * ads_dtype).  The factorisation and the two triangular sweeps run in one
+ * thread block each: n^2 sequential pivots, meant for the baseline's sizes.
+ * 2D with n <= 512 only (else ADS_ERR_UNSUPPORTED).  The first call allocates
+ * the workspace, n^2 (2n + 32) doubles (2.2 GB at n = 512; 0.8 MB at n = 32),
+ * through the context's allocator and keeps it (ADS_ERR_OOM if it cannot);
+ * ads_hbm_estimate does not count it.  Work is enqueued on the context's
+ * stream; the call returns after enqueueing.  A pivot that is not positive
+ * and finite (non-finite or negative inputs) sets every coefficient to NaN and
+ * the context's non-finite flag, which hybrid_step then reports. */
+ads_status ads_galerkin_pressure(ads_ctx* ctx);
+
 /* Replace the pressure / saturation coefficients ((n+2)^dim host doubles). */
 ads_status ads_set_pressure_coeffs(ads_ctx* ctx, const double* host_p);
 ads_status ads_set_saturation(ads_ctx* ctx, const double* host_s);

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "libadsgb.so")
 
 ADS_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
-                4: "non-finite value", 5: "timeout", 6: "invalid state", 7: "unsupported"}
+                4: "non-finite value", 5: "timeout", 6: "invalid state", 7: "unsupported",
+                8: "checkpoint file error"}
 ADS_F64, ADS_F32, ADS_BF16 = 0, 1, 2
 MAX_SOURCES = 8
 
@@ -94,6 +95,7 @@ SIGNATURES = {
     "ads_load": (C.c_int, [_P, C.c_char_p]),
     "ads_saturation_step": (C.c_int, [_P, C.c_double, C.c_int]),
     "ads_cfl_dt": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _D]),
+    "ads_galerkin_pressure": (C.c_int, [_P]),
     "ads_set_pressure_coeffs": (C.c_int, [_P, _D]),
     "ads_set_saturation": (C.c_int, [_P, _D]),
     "crvpinn_set_theta": (C.c_int, [_P, _D]),

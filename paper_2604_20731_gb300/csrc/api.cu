@@ -56,6 +56,7 @@ struct ads_ctx {
   double *src_part = nullptr, *mass_part = nullptr, *cfl_part = nullptr, *stats = nullptr,
          *dt = nullptr, *scal = nullptr;
   int* flags = nullptr;
+  double* gal = nullptr;  // Galerkin pressure workspace (allocated on first use)
   int re = 4, nquad = 0, nys = 0, ncfl = 0, ldx = 0;  // ldx: row stride of Xm / Xs (2D)
   // CRVPINN (network precision)
   void *alpha = nullptr, *f = nullptr, *u = nullptr, *res = nullptr, *rhat = nullptr, *z = nullptr,
@@ -749,6 +750,33 @@ ads_status profile_sat_t(ads_ctx* c, int steps, double* ms) {
   return st;
 }
 
+// Galerkin pressure system assembled and solved for the current saturation
+template <typename TA>
+ads_status enq_galerkin(ads_ctx* c) {
+  GalArgs<TA> a{};
+  a.n = c->n;
+  a.S = (const TA*)c->S[c->cur];
+  a.K = (const TA*)c->K;
+  a.B = c->B64;
+  a.dB = c->dB64;
+  a.gsrc = c->gsrc64;
+  a.n_src = c->prm.n_src;
+  for (int s = 0; s < kMaxSrc; ++s) {
+    a.rate[s] = s < c->prm.n_src ? c->prm.src[s].rate : 0.0;
+    a.kind[s] = s < c->prm.n_src ? c->prm.src[s].kind : 0;
+  }
+  a.inv_mu_g = 1.0 / c->prm.mu_g;
+  a.inv_mu_w = 1.0 / c->prm.mu_w;
+  a.rho_w = c->prm.rho_w;
+  a.rho_g = c->prm.rho_g;
+  a.grav = c->prm.grav;
+  a.work = c->gal;
+  a.P = (TA*)c->P;
+  a.flags = c->flags;
+  CK(launch_galerkin_pressure<TA>(a, c->stream));
+  c->nlaunch += 4;
+  return ADS_OK;
+}
 
 }  // namespace
 
@@ -1231,6 +1259,19 @@ ads_status ads_cfl_dt(ads_ctx* c, double cfl, double src_frac, double dt_cap, do
     if (!std::isfinite(*dt_out) || *dt_out <= 0) return ADS_ERR_NONFINITE;
   }
   return ADS_OK;
+}
+
+ads_status ads_galerkin_pressure(ads_ctx* c) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!galerkin_supported(c->dim, c->n))
+    return fail(c, ADS_ERR_UNSUPPORTED, "Galerkin pressure: 2D with n <= 512 only");
+  if (!c->gal) {
+    void* p = nullptr;
+    CA(alloc(c, &p, galerkin_work_bytes(c->n)));
+    c->gal = (double*)p;
+  }
+  return c->ta == ADS_F64 ? enq_galerkin<double>(c) : enq_galerkin<float>(c);
 }
 
 ads_status crvpinn_num_params(const ads_ctx* c, int* np) {

@@ -226,4 +226,27 @@ size_t mlp_tc_acts_bytes(int npts, int width);
 // `min_tiles` 128-point tiles per CTA
 int mlp_tc_bwd_blocks(int npts, int width, int din, int min_tiles = 1);
 
+// ---- Galerkin B-spline pressure (the plain method; 2D, FP64 arithmetic) ----
+constexpr int kGalMaxN = 512;
+template <typename TA>
+struct GalArgs {
+  int n;
+  const TA* S;            // saturation coefficients (n+2)^2
+  const TA* K;            // nodal permeability (n+1)^2
+  const double* B;        // FP64 axis tables [n][3][3]
+  const double* dB;
+  const double* gsrc;     // FP64 per-axis source factors
+  int n_src;
+  double rate[kMaxSrc];
+  int kind[kMaxSrc];
+  double inv_mu_g, inv_mu_w, rho_w, rho_g, grav;
+  double* work;           // galerkin_work_bytes(n)
+  TA* P;                  // out: pressure coefficients (n+2)^2, boundary ring 0
+  int* flags;             // bit 0 set when a pivot is not positive and finite
+};
+bool galerkin_supported(int dim, int n);
+size_t galerkin_work_bytes(int n);
+template <typename TA>
+cudaError_t launch_galerkin_pressure(const GalArgs<TA>& a, cudaStream_t st);
+
 }  // namespace adsgb

@@ -142,6 +142,21 @@ class HybridSolver:
         self._check(self.lib.ads_cfl_dt(self.ctx, cfl, src_frac, dt_cap, C.byref(out)), "ads_cfl_dt")
         return out.value
 
+    def galerkin_pressure(self):
+        """Pressure coefficients from the Galerkin system (the plain method)."""
+        self._check(self.lib.ads_galerkin_pressure(self.ctx), "ads_galerkin_pressure")
+
+    def plain_step(self, n_sub: int = 10, dt: Optional[float] = None, cfl: float = 0.1,
+                   src_frac: float = 0.05, dt_cap: float = 1e30):
+        """One step of the IGA-ADS + direct-solver method (Sec. 7): the Galerkin
+        pressure, then n_sub explicit saturation steps with it (CFL step size
+        when dt is None).  Stays on the device; returns nothing."""
+        self.galerkin_pressure()
+        if dt is None:
+            self._check(self.lib.ads_cfl_dt(self.ctx, cfl, src_frac, dt_cap, None), "ads_cfl_dt")
+            dt = 0.0
+        self.saturation_step(dt, n_sub)
+
     def update_coefficients(self):
         self._check(self.lib.crvpinn_update_coefficients(self.ctx), "crvpinn_update_coefficients")
 
