@@ -51,7 +51,7 @@ typedef enum {
   ADS_ERR_NONFINITE = 4,    /* a loss, step size or field became non-finite  */
   ADS_ERR_TIMEOUT = 5,      /* waiting for the stream exceeded the deadline  */
   ADS_ERR_STATE = 6,        /* call not valid in this state (e.g. no network)*/
-  ADS_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement   */
+  ADS_ERR_UNSUPPORTED = 7,  /* valid request the library does not implement  */
   ADS_ERR_IO = 8            /* a checkpoint file could not be written or read */
 } ads_status;
 
