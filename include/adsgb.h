@@ -10,7 +10,9 @@
  *     the discrete residual (Eqs. 23b-25), the robust loss RES^T G^-1 RES
  *     (Eqs. 26-28), its hand-written gradient and Adam (Sec. 8.3);
  *   - the hybrid loop of Sec. 6 (projection of the network pressure into the
- *     B-spline space, 10 saturation steps, 100 Adam iterations).
+ *     B-spline space, 10 saturation steps, 100 Adam iterations);
+ *   - the plain method of Sec. 7: the Galerkin B-spline pressure (Sec. 4,
+ *     Eqs. 15-20) solved directly, in place of the network (2D).
  *
  * Conventions (every entry point):
  *   - Every call returns an ads_status; no exception crosses the ABI.
