@@ -333,6 +333,60 @@ def test_galerkin_pressure_manufactured_h3():
     assert min(rates) > 2.7, (errs, rates)
 
 
+def test_galerkin_pressure_matches_element_loop():
+    """The Galerkin system assembled element by element with scalar basis
+    evaluation: (lambda K grad B_kl, grad B_ij) p = (q_w + q_g, B_ij)
+    - (g K (rho_w lambda_w + rho_g lambda_g), dB_ij/dy) over interior i, j,
+    with a saturation that puts both mobilities to work (and the clamp) and
+    gravity on -- the cases the S = 0 pins above cannot tell apart."""
+    n = 4
+    sc = scn.make_scenario(2, n, seed=9, S0="random", grav=0.8)
+    sc.sources[0].center = (0.3, 0.4)
+    sc.sources[1].center = (0.6, 0.7)
+    sc.sources[0].sigma = sc.sources[1].sigma = 0.2
+    S = np.random.default_rng(13).uniform(-0.2, 1.2, size=(n + 2, n + 2))
+    knots = open_uniform_knots(n, 2)
+    hat = open_uniform_knots(n, 1)
+    xg, wg = np.polynomial.legendre.leggauss(3)
+    xg, wg = 0.5 * (xg + 1), 0.5 * wg
+    h = 1.0 / n
+    nb = n + 2
+    A = np.zeros((nb * nb, nb * nb))
+    F = np.zeros(nb * nb)
+    for ey in range(n):
+        for ex in range(n):
+            for qy in range(3):
+                for qx in range(3):
+                    x, y = (ex + xg[qx]) * h, (ey + xg[qy]) * h
+                    w = wg[qx] * wg[qy] * h * h
+                    fn = [(j, i) for j in range(ey, ey + 3) for i in range(ex, ex + 3)]
+                    val = {(j, i): bspline_scalar(knots, i, 2, x) * bspline_scalar(knots, j, 2, y) for j, i in fn}
+                    gx = {(j, i): bspline_scalar_deriv(knots, i, 2, x) * bspline_scalar(knots, j, 2, y) for j, i in fn}
+                    gy = {(j, i): bspline_scalar(knots, i, 2, x) * bspline_scalar_deriv(knots, j, 2, y) for j, i in fn}
+                    s = min(max(sum(S[j, i] * val[j, i] for j, i in fn), 0.0), 1.0)
+                    kk = sum(sc.K[j, i] * bspline_scalar(hat, j, 1, y) * bspline_scalar(hat, i, 1, x)
+                             for i in (ex, ex + 1) for j in (ey, ey + 1))
+                    lg, lw = s / sc.mu_g, (1 - s) / sc.mu_w
+                    q = 0.0
+                    for src in sc.sources:
+                        G = math.exp(-((x - src.center[0]) ** 2 + (y - src.center[1]) ** 2)
+                                     / (2 * src.sigma ** 2)) / (2 * math.pi * src.sigma ** 2)
+                        q += src.rate * G if src.kind == 0 else -src.rate * G
+                    for a in fn:
+                        ia = a[0] * nb + a[1]
+                        F[ia] += w * (q * val[a] - sc.grav * kk * (sc.rho_w * lw + sc.rho_g * lg) * gy[a])
+                        for b in fn:
+                            A[ia, b[0] * nb + b[1]] += w * (lg + lw) * kk * (gx[a] * gx[b] + gy[a] * gy[b])
+    inner = [j * nb + i for j in range(1, nb - 1) for i in range(1, nb - 1)]
+    p = np.linalg.solve(A[np.ix_(inner, inner)], F[inner])
+    expect = np.zeros(nb * nb)
+    expect[inner] = p
+    P = galerkin_pressure(sc, S)
+    # the scalar derivative is a central difference (error ~1e-9); a dropped
+    # mobility or swapped density moves P by O(1e-2) or more
+    np.testing.assert_allclose(P.ravel(), expect, rtol=0, atol=1e-7 * np.abs(expect).max())
+
+
 def test_galerkin_pressure_sign():
     """An injector raises the pressure (Eq. 5: div(lambda K grad p) = -q)."""
     sc = scn.make_scenario(2, 16, seed=1)
