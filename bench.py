@@ -56,6 +56,7 @@ def args_parse():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--c2-steps", type=int, default=20)
     ap.add_argument("--c1-steps", type=int, default=20)
+    ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--err-iters", type=int, default=60000)
     ap.add_argument("--err-steps", type=int, default=3)
     ap.add_argument("--sat-n", type=int, default=4096)
@@ -334,6 +335,48 @@ def plain_method_c1(a, scn, HybridSolver, device):
             "note": f"32^2 elements, FP64, {a.n_sub} saturation steps per step, CFL dt; the Galerkin "
                     "pressure (assembly + banded Cholesky + two triangular sweeps, one thread block "
                     "for the sequential pivots) is latency-bound; the oracle uses SuperLU"}
+
+
+def large_configs(a, scn, HybridSolver, device):
+    """Configurations 3 (2D, 1024^2 elements) and 5 (3D, 128^3 elements, K_z =
+    0.1 K), one scenario each in mixed precision: FP32 saturation with FP64
+    factors and the 128-wide network with BF16 tensor-core products (FP32
+    accumulation).  Reports the per-kernel Adam-iteration and saturation
+    sub-step times (CUDA events inside the library) and the hybrid step
+    (CUDA events on the solver's stream, after one warm-up step); configuration
+    5 also with 8 activation-recomputation chunks."""
+    import torch
+    out = {}
+    hp = HybridSolver.hybrid_params(n_sub=a.n_sub, adam_iters=a.adam_iters, lr=a.lr)
+    cases = (("c3_2d_1024_w128", 2, 1024, 0), ("c5_3d_128_w128", 3, 128, 0),
+             ("c5_3d_128_w128_recompute8", 3, 128, 8))
+    for name, dim, n, chunks in cases:
+        sc = scn.make_scenario(dim, n, seed=1000, kz_ratio=0.1 if dim == 3 else 1.0)
+        st = torch.cuda.Stream(device=device)
+        s = HybridSolver(sc, width=128, crv_dtype="bf16", ads_dtype="f32", stream=st, act_chunks=chunks)
+        s.set_theta(scn.make_theta0(dim, 128, 4, seed=7))
+        s.update_coefficients()
+        s.pretrain(5, a.lr)
+        prof = s.profile_train(5)
+        sat = s.profile_saturation(5)
+        s.hybrid_step(hp, stats=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(a.large_steps):
+            s.hybrid_step(hp, stats=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.large_steps
+        s.get("S")  # a bounded wait that gave up fails here
+        s.close()
+        it_ms = sum(prof.values())
+        npts = (n - 1) ** dim
+        out[name] = {"hybrid_step_ms": ms, "adam_iteration_ms": it_ms,
+                     "point_iterations_per_s": npts / (it_ms * 1e-3), "kernel_ms": prof,
+                     "saturation_substep_ms": sum(sat.values()), "saturation_kernel_ms": sat,
+                     "act_chunks": chunks, "hybrid_steps_timed": a.large_steps}
+    return out
 
 
 def saturation_roofline(n, scn, HybridSolver):
@@ -658,7 +701,12 @@ def run_ours(a, world, rank, local):
     if rank == 0 and a.c1_steps > 0:
         c1 = plain_method_c1(a, scn, HybridSolver, device)
 
-    # ---- (4c) saturation kernels on a mesh larger than L2 (FP32 and FP64) ----
+    # ---- (4c) configurations 3 and 5: the 128-wide network in 2D and 3D ----
+    large = None
+    if rank == 0 and a.large_steps > 0:
+        large = large_configs(a, scn, HybridSolver, device)
+
+    # ---- (4d) saturation kernels on a mesh larger than L2 (FP32 and FP64) ----
     sat = None
     if rank == 0 and a.sat_n > 0:
         sat = saturation_roofline(a.sat_n, scn, HybridSolver)
@@ -689,6 +737,7 @@ def run_ours(a, world, rank, local):
                                "scenarios step once per round); e2e holds the server's per-step latency",
                "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2, "c1_plain_galerkin": c1,
+               "c3_c5_w128": large,
                "saturation": sat,
                "gpu_launches": launches, "clocks": clk, "kernel_ms_by_n": prof_by_n,
                "server": server_stats}
