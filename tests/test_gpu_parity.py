@@ -195,24 +195,6 @@ def test_loss_and_gradient_fp64(n):
     s.close()
 
 
-def test_autograd_function_fp64():
-    """The loss as a torch.autograd.Function: its value and its autograd
-    gradient are the kernels' (forward, adjoint, hand-written backward) and
-    match the oracle within the bounds of test_loss_and_gradient_fp64."""
-    import torch
-    from paper_2604_20731_gb300.torch_loss import crvpinn_loss
-    sc, s, crv, theta, alpha, f = _crv_case(8, "f64")
-    try:
-        t = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
-        loss = crvpinn_loss(s, t)
-        loss.backward()
-        ref_loss, ref_grad, _ = crv.loss_grad(MLP(2, 64, 4), theta, alpha, f)
-        assert loss.item() == pytest.approx(ref_loss, rel=1e-9)
-        assert rel_l2(t.grad.numpy(), ref_grad) <= 1e-8
-    finally:
-        s.close()
-
-
 @pytest.mark.parametrize("n,width", [(3, 64), (8, 64), (33, 64), (64, 64), (65, 128), (128, 128),
                                      (130, 64)])
 def test_loss_and_gradient_fp32(n, width):

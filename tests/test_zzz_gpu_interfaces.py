@@ -1,0 +1,66 @@
+"""Interfaces around the kernels, through the C ABI: the loss as a
+torch.autograd.Function, and the host-side deadline of a wait.  Collected
+after every other file, so that a run stopping at the first failure has
+already run the rest.
+
+Bounds: the autograd loss and gradient are the kernels' own, so they meet
+the FP64 bounds of the direct loss/gradient parity test (loss 1e-9 relative,
+gradient 1e-8 relative L2).
+"""
+import numpy as np
+import pytest
+
+from oracle.crvpinn import CrvOracle, MLP
+from paper_2604_20731_gb300 import scenario as scn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _case(n=8, width=64, seed=21):
+    from paper_2604_20731_gb300.solver import HybridSolver
+    sc = scn.make_scenario(2, n, seed=seed, S0="random", grav=0.6)
+    theta = scn.make_theta0(2, width, 4, seed=seed) + 0.01 * np.random.default_rng(seed).normal(
+        size=scn.mlp_num_params(2, width, 4))
+    s = HybridSolver(sc, width=width, crv_dtype="f64")
+    s.set_theta(theta)
+    s.update_coefficients()
+    return sc, s, theta
+
+
+def test_autograd_function_fp64():
+    torch = pytest.importorskip("torch")
+    from paper_2604_20731_gb300.torch_loss import crvpinn_loss
+    sc, s, theta = _case()
+    try:
+        t = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        loss = crvpinn_loss(s, t)
+        loss.backward()
+        crv = CrvOracle(sc)
+        alpha, f = crv.coefficients(sc.S0)
+        ref_loss, ref_grad, _ = crv.loss_grad(MLP(2, 64, 4), theta, alpha, f)
+        assert loss.item() == pytest.approx(ref_loss, rel=1e-9)
+        g = t.grad.numpy()
+        assert np.linalg.norm(g - ref_grad) <= 1e-8 * np.linalg.norm(ref_grad)
+    finally:
+        s.close()
+
+
+def test_host_wait_deadline_reports_timeout_and_context_survives():
+    """A wait whose deadline passes while queued work runs returns
+    ADS_ERR_TIMEOUT; the context stays usable and a later wait succeeds."""
+    from paper_2604_20731_gb300._lib import AdsError
+    sc, s, theta = _case(n=64)
+    try:
+        s.pressure_update(2000, 1e-3, sync=False)  # enqueued, not waited for
+        with pytest.raises(AdsError, match="timeout"):
+            s.sync(1e-6)
+        s.sync(600.0)
+        assert np.isfinite(s.get("LOSS")).all()
+    finally:
+        s.close()
