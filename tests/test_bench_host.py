@@ -1,0 +1,33 @@
+"""Host-side pieces of bench.py that decide what a run reports: the clock
+summary that rejects throttled runs, and the per-point work of the network."""
+import pytest
+
+import bench
+
+
+def _line(sm, smax, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
+    return f"0, {sm}, {smax}, 850.20, 0x0000000000000000, {hw}, {hwt}, {swt}, {cap}"
+
+
+def test_clock_summary_median_max_and_reasons():
+    lines = [_line(2070, 2070), _line(1980, 2070, cap="Active"), _line(2055, 2070),
+             "garbage", "0, [N/A], 2070, 1, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    out = bench.clock_summary(lines)
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_flags_thermal_and_nothing_parsed():
+    out = bench.clock_summary([_line(1500, 2070, hwt="Active", swt="Active")])
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_thermal_slowdown"]
+    assert bench.clock_summary([]) is None
+    assert bench.clock_summary(["index, clocks.sm"]) is None
+
+
+def test_network_flops_per_point():
+    # 2-64x4-1: forward 2(2W + 3W^2 + W), backward 2(6W^2 + W + 2W)
+    fwd, bwd = bench.mlp_flops_per_point(2, 64)
+    assert fwd == 24960
+    assert bwd == 2 * (6 * 64 * 64 + 64 + 2 * 64)
+    assert bench.mlp_flops_per_point(3, 128)[0] == 2 * (3 * 128 + 3 * 128 * 128 + 128)
