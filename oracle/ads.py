@@ -163,7 +163,7 @@ class AdsOracle:
 
     def __init__(self, sc):
         self.sc = sc
-        self.mesh = Mesh(sc.dim, sc.n)
+        self.mesh = Mesh(sc.dim, sc.n, getattr(sc, "p", 2))
         m = self.mesh
         self.W = m.gauss_weights()
         self.coords = m.gauss_coords()

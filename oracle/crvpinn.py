@@ -122,7 +122,8 @@ class CrvOracle:
         self.M = (self.N - 1) ** self.dim
         self.K = np.asarray(sc.K, dtype=np.float64)
         nodes = np.arange(self.N + 1) / self.N
-        self.Bnode = basis_values(open_uniform_knots(sc.n, 2), 2, nodes)
+        deg = getattr(sc, "p", 2)
+        self.Bnode = basis_values(open_uniform_knots(sc.n, deg), deg, nodes)
         grids = np.meshgrid(*([nodes] * self.dim), indexing="ij")
         self.node_coords = list(reversed(grids))
         self.X = interior_coords(self.dim, self.N)

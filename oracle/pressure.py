@@ -29,9 +29,10 @@ def _kron_all(mats):
 
 
 def galerkin_pressure(sc, S: np.ndarray) -> np.ndarray:
-    """Pressure B-spline coefficients (n+2)^d with zero boundary ring."""
+    """Pressure B-spline coefficients (n+p)^d with zero boundary ring."""
     d = sc.dim
-    m = Mesh(d, sc.n)
+    deg = getattr(sc, "p", 2)
+    m = Mesh(d, sc.n, deg)
     ax = m.ax
     W = m.gauss_weights().ravel()
     coords = m.gauss_coords()
@@ -54,7 +55,7 @@ def galerkin_pressure(sc, S: np.ndarray) -> np.ndarray:
         Smat = term if Smat is None else Smat + term
         if c == d - 1:  # g points down the vertical axis
             F = F + Phic.T @ (W * (-sc.grav) * Kc * rho_lam)
-    nb = sc.n + 2
+    nb = sc.n + deg
     interior = np.zeros((nb,) * d, dtype=bool)
     interior[tuple([slice(1, -1)] * d)] = True
     idx = np.flatnonzero(interior.ravel())

@@ -53,7 +53,7 @@ class Scenario:
     K: np.ndarray               # nodal permeability, (n+1)^dim, float64
     phi: float = PHI            # constant porosity ...
     phi_map: Optional[np.ndarray] = None  # ... or nodal porosity (n+1)^dim
-    S0: Optional[np.ndarray] = None       # B-spline coefficients (n+2)^dim
+    S0: Optional[np.ndarray] = None       # B-spline coefficients (n+p)^dim
     sources: List[Source] = dataclasses.field(default_factory=list)
     mu_w: float = MU_W
     mu_g: float = MU_G
@@ -63,6 +63,7 @@ class Scenario:
     grav_sign: float = 1.0      # +1: gravity term as derived from Eq. 2; -1: as printed in Eq. 9
     kz_ratio: float = 1.0       # 3D vertical/horizontal permeability ratio
     seed: int = 0
+    p: int = 2                  # B-spline degree (the library implements p = 2)
 
     @property
     def nodes_shape(self):
@@ -70,7 +71,7 @@ class Scenario:
 
     @property
     def coeffs_shape(self):
-        return (self.n + 2,) * self.dim
+        return (self.n + self.p,) * self.dim
 
     def S0_or_zero(self) -> np.ndarray:
         if self.S0 is None:
@@ -107,12 +108,13 @@ def gaussian_random_field(shape, corr_len, rng: np.random.Generator) -> np.ndarr
 
 def make_scenario(dim: int = 2, n: int = 32, seed: int = 1000, sigma: float = 1.0,
                   corr_len=0.1, rate: float = 1.0, grav: float = 0.0,
-                  kz_ratio: float = 1.0, S0: str = "zero") -> Scenario:
+                  kz_ratio: float = 1.0, S0: str = "zero", p: int = 2) -> Scenario:
     """Scenario shaped like the configurations: log-normal K, injector at
     (0.25,...) and producer at (0.75,...), constant porosity 0.2.
 
     S0: "zero" (the configurations' initial state) or "random" (coefficients
     uniform in [0, 0.6], used by the parity tests so that every term is live).
+    p: B-spline degree, n + p coefficients per axis.
     """
     rng = np.random.default_rng(seed)
     shape = (n + 1,) * dim
@@ -121,15 +123,15 @@ def make_scenario(dim: int = 2, n: int = 32, seed: int = 1000, sigma: float = 1.
     Z = gaussian_random_field(shape, corr_len, rng)
     K = np.exp(sigma * Z)
     if S0 == "zero":
-        s0 = np.zeros((n + 2,) * dim)
+        s0 = np.zeros((n + p,) * dim)
     elif S0 == "random":
-        s0 = rng.uniform(0.0, 0.6, size=(n + 2,) * dim)
+        s0 = rng.uniform(0.0, 0.6, size=(n + p,) * dim)
     else:
         raise ValueError(S0)
     inj = Source(center=(0.25,) * dim, rate=rate, kind=SRC_INJECT)
     prod = Source(center=(0.75,) * dim, rate=rate, kind=SRC_PRODUCE)
     return Scenario(dim=dim, n=n, K=K, S0=s0, sources=[inj, prod], grav=grav,
-                    kz_ratio=kz_ratio, seed=seed)
+                    kz_ratio=kz_ratio, seed=seed, p=p)
 
 
 def mlp_layer_sizes(in_dim: int, width: int, hidden_layers: int = 4) -> List[int]:

@@ -19,6 +19,8 @@ def _dptr(a: np.ndarray):
 
 
 def make_params(sc, ads_dtype: str = "f64") -> L.ads_params:
+    if getattr(sc, "p", 2) != 2:
+        raise ValueError("the library implements quadratic B-splines (p = 2) only")
     p = L.ads_params()
     p.dim, p.n = sc.dim, sc.n
     p.phi = float(sc.phi)

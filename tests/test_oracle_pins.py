@@ -158,25 +158,27 @@ def test_kronecker_solve_equals_dense(dim, n):
 
 def _brute_rhs(sc, S, P, dt):
     """Element loop, pointwise scalar basis evaluation: the definition of the
-    right-hand side of Eq. 10b with the gravity reading of the scenario."""
+    right-hand side of Eq. 10b with the gravity reading of the scenario, for
+    B-splines of the scenario's degree with p + 1 Gauss points per axis."""
     n = sc.n
-    knots = open_uniform_knots(n, 2)
+    deg = getattr(sc, "p", 2)
+    knots = open_uniform_knots(n, deg)
     hat = open_uniform_knots(n, 1)
-    xg, wg = np.polynomial.legendre.leggauss(3)
+    xg, wg = np.polynomial.legendre.leggauss(deg + 1)
     xg, wg = 0.5 * (xg + 1), 0.5 * wg
     h = 1.0 / n
-    R = np.zeros((n + 2, n + 2))
+    R = np.zeros((n + deg, n + deg))
     for ey in range(n):
         for ex in range(n):
-            for qy in range(3):
-                for qx in range(3):
+            for qy in range(deg + 1):
+                for qx in range(deg + 1):
                     x = (ex + xg[qx]) * h
                     y = (ey + xg[qy]) * h
                     w = wg[qx] * wg[qy] * h * h
-                    bx = {i: bspline_scalar(knots, i, 2, x) for i in range(ex, ex + 3)}
-                    by = {j: bspline_scalar(knots, j, 2, y) for j in range(ey, ey + 3)}
-                    dbx = {i: bspline_scalar_deriv(knots, i, 2, x) for i in range(ex, ex + 3)}
-                    dby = {j: bspline_scalar_deriv(knots, j, 2, y) for j in range(ey, ey + 3)}
+                    bx = {i: bspline_scalar(knots, i, deg, x) for i in range(ex, ex + deg + 1)}
+                    by = {j: bspline_scalar(knots, j, deg, y) for j in range(ey, ey + deg + 1)}
+                    dbx = {i: bspline_scalar_deriv(knots, i, deg, x) for i in range(ex, ex + deg + 1)}
+                    dby = {j: bspline_scalar_deriv(knots, j, deg, y) for j in range(ey, ey + deg + 1)}
                     s = sum(S[j, i] * by[j] * bx[i] for i in bx for j in by)
                     px = sum(P[j, i] * by[j] * dbx[i] for i in bx for j in by)
                     py = sum(P[j, i] * dby[j] * bx[i] for i in bx for j in by)
@@ -395,6 +397,123 @@ def test_galerkin_pressure_sign():
     vals = m.ax.values_at([0.25, 0.75])
     pv = vals @ P @ vals.T  # [y][x] at (0.25,0.25),(0.75,0.25),...
     assert pv[0, 0] > 0 and pv[1, 1] < 0
+
+
+# ----------------------------------------------------------------------------
+# Higher spline degree (p = 3, 4): the same discretisation of Secs. 3-4 with
+# B-splines of degree p, n + p functions per axis and p + 1 Gauss points
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,n", [(3, 1), (3, 6), (4, 2), (4, 9)])
+def test_partition_of_unity_higher_degree(p, n):
+    knots = open_uniform_knots(n, p)
+    x = np.concatenate([np.random.default_rng(n + p).uniform(0, 1, 150), [0.0, 1.0, 0.5]])
+    B = basis_values(knots, p, x)
+    D = basis_derivatives(knots, p, x)
+    assert B.shape[1] == n + p
+    assert np.all(B >= -1e-15)
+    np.testing.assert_allclose(B.sum(1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(D.sum(1), 0.0, atol=1e-10)
+    xi = np.array([0.07, 0.33, 0.61, 0.94])
+    Bi = basis_values(knots, p, xi)
+    for i in range(n + p):
+        for k, xv in enumerate(xi):
+            assert Bi[k, i] == pytest.approx(bspline_scalar(knots, i, p, xv), abs=1e-14)
+
+
+@pytest.mark.parametrize("p,n", [(3, 2), (3, 7), (4, 3), (4, 8)])
+def test_basis_integrals_higher_degree(p, n):
+    """int B_i = (t_{i+p+1} - t_i)/(p+1), with p + 1 Gauss points."""
+    ax = Axis1D(n, p)
+    t = ax.knots
+    expect = np.array([(t[i + p + 1] - t[i]) / (p + 1) for i in range(n + p)])
+    np.testing.assert_allclose(ax.B.T @ ax.w, expect, rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_mass_rows_are_cardinal_bspline_values(p):
+    with open(os.path.join(GOLDEN, "bspline_mass_rows_p234.json")) as f:
+        g = json.load(f)
+    row = np.array(g["rows_times_factorial"][str(p)], dtype=float) / g["factorial"][str(p)]
+    # the fixture is the closed form: N_{2p+1} at the integers, evaluated here
+    m = 2 * p + 1
+    card = [bspline_scalar(np.arange(m + 2, dtype=float), 0, m, float(k)) for k in range(1, m + 1)]
+    np.testing.assert_allclose(card, row, rtol=1e-13)
+    n = 20
+    ax = Axis1D(n, p)
+    M, h = ax.M, 1.0 / n
+    np.testing.assert_allclose(M, M.T, atol=1e-17)
+    for i in range(2 * p, n - p):
+        np.testing.assert_allclose(M[i, i - p:i + p + 1] / h, row, rtol=1e-12)
+        assert np.all(M[i, :i - p] == 0) and np.all(M[i, i + p + 1:] == 0)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 3), (2, 6, 4), (3, 2, 3)])
+def test_kronecker_solve_equals_dense_higher_degree(dim, n, p):
+    m = Mesh(dim, n, p)
+    R = np.random.default_rng(dim + n + p).normal(size=(n + p,) * dim)
+    Xk = m.mass_solve_kron(R)
+    np.testing.assert_allclose(Xk, m.mass_solve_dense(R), rtol=0, atol=1e-11 * np.abs(Xk).max())
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 5, 3), (2, 4, 4), (3, 3, 3)])
+def test_constant_and_mass_balance_higher_degree(dim, n, p):
+    sc = scn.make_scenario(dim, n, seed=2, p=p)
+    sc.sources = []
+    sc.grav = 0.0
+    S = np.full((n + p,) * dim, 0.37)
+    np.testing.assert_allclose(AdsOracle(sc).step(S, np.zeros_like(S), 0.01), 0.37, atol=1e-12)
+    sc = scn.make_scenario(dim, n, seed=3, S0="random", grav=1.0, p=p)
+    sc.phi_map = 0.1 + 0.3 * np.random.default_rng(9).uniform(size=(n + 1,) * dim)
+    P = np.random.default_rng(4).normal(size=(n + p,) * dim)
+    a = AdsOracle(sc)
+    Sn = a.step(sc.S0, P, 0.002)
+    assert abs(a.mass_error(sc.S0, Sn, 0.002)) <= 1e-13 * max(1.0, abs(a.mesh.integral(Sn)))
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_rhs_matches_element_loop_higher_degree(p):
+    sc = scn.make_scenario(2, 3, seed=5, S0="random", grav=0.7, p=p)
+    sc.sources[0].center = (0.3, 0.4)
+    sc.sources[1].center = (0.6, 0.7)
+    sc.sources[0].sigma = sc.sources[1].sigma = 0.2
+    rng = np.random.default_rng(12)
+    S = rng.uniform(-0.1, 1.1, size=(3 + p, 3 + p))
+    P = rng.normal(size=(3 + p, 3 + p))
+    R = AdsOracle(sc).rhs(S, P, 0.013)
+    Rb = _brute_rhs(sc, S, P, 0.013)
+    np.testing.assert_allclose(R, Rb, rtol=0, atol=2e-7 * np.abs(Rb).max())
+
+
+def test_galerkin_pressure_manufactured_cubic_h4():
+    """As the quadratic case, with cubic B-splines: the L2 error falls like
+    h^(p+1) = h^4."""
+    import oracle.pressure as pr
+    errs = []
+    for n in (4, 8, 16):
+        sc = scn.make_scenario(2, n, seed=1, p=3)
+        sc.K = np.ones_like(sc.K)
+        lam = 1.0 / sc.mu_w
+        m = Mesh(2, n, 3)
+        coords = m.gauss_coords()
+        orig = pr.gaussian_sources
+        pr.gaussian_sources = lambda s, c: (2 * np.pi ** 2 * lam * np.sin(np.pi * c[0]) * np.sin(np.pi * c[1]),
+                                            np.zeros_like(c[0]))
+        try:
+            P = galerkin_pressure(sc, np.zeros((n + 3, n + 3)))
+        finally:
+            pr.gaussian_sources = orig
+        ph = m.at_gauss(P)
+        ex = np.sin(np.pi * coords[0]) * np.sin(np.pi * coords[1])
+        errs.append(math.sqrt(np.sum(m.gauss_weights() * (ph - ex) ** 2)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.6, (errs, rates)
+
+
+def test_library_refuses_other_degrees():
+    from paper_2604_20731_gb300.solver import make_params
+    with pytest.raises(ValueError):
+        make_params(scn.make_scenario(2, 4, p=3))
 
 
 # ----------------------------------------------------------------------------
