@@ -120,3 +120,90 @@ def test_single_chunk_is_exact():
     r = np.random.default_rng(7).standard_normal(n + 2)
     np.testing.assert_allclose(_chunked_solve(l1, l2, D, r, 127, 32), np.linalg.solve(M, r),
                                rtol=1e-12, atol=1e-12 * np.abs(r).max())
+
+
+# ----------------------------------------------------------------------------
+# Higher spline degree (p = 3, 4): halos the chunked sweeps will need.  The
+# band has p sub-diagonals; the truncation shrinks by the root inside the unit
+# circle of the interior row's symbol (the cardinal B-spline of degree 2p+1 at
+# the integers).  Halos of 32 / 64 rows (p = 3) and 40 / 80 rows (p = 4) keep
+# it below FP32 / FP64 rounding; the quadratic halos (24 / 48) do not.
+# ----------------------------------------------------------------------------
+
+HALOS = {3: (32, 64), 4: (40, 80)}
+
+
+def _golden_row(p):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "bspline_mass_rows_p234.json")) as f:
+        return np.array(json.load(f)["rows_times_factorial"][str(p)], dtype=float)
+
+
+def _ldlt_band(M, p):
+    """Unit lower factor L[i, k] = L_{i, i-k} (k = 1..p) and D of a symmetric
+    banded SPD matrix, by the column recurrences written out directly."""
+    nb = M.shape[0]
+    L = np.zeros((nb, p + 1))
+    D = np.zeros(nb)
+    for i in range(nb):
+        for k in range(p, 0, -1):
+            j = i - k
+            if j < 0:
+                continue
+            v = M[i, j] - sum(L[i, i - m] * L[j, j - m] * D[m] for m in range(max(0, i - p), j))
+            L[i, k] = v / D[j]
+        D[i] = M[i, i] - sum(L[i, k] ** 2 * D[i - k] for k in range(1, p + 1) if i - k >= 0)
+    return L, D
+
+
+def _chunked_band_solve(L, D, r, p, chunk, H):
+    nb = r.size
+    y = np.zeros(nb)
+    x = np.zeros(nb)
+    for s in range(0, nb, chunk):
+        e = min(nb, s + chunk)
+        st = {}
+        for l in range(max(0, s - H), e):
+            st[l] = r[l] - sum(L[l, k] * st.get(l - k, 0.0) for k in range(1, p + 1))
+            if l >= s:
+                y[l] = st[l]
+    for s in range(0, nb, chunk):
+        e = min(nb, s + chunk)
+        st = {}
+        for l in range(min(nb, e + H) - 1, s - 1, -1):
+            st[l] = y[l] / D[l] - sum(L[l + k, k] * st.get(l + k, 0.0)
+                                      for k in range(1, p + 1) if l + k < nb)
+            if l < e:
+                x[l] = st[l]
+    return x
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_decay_rate_higher_degree(p):
+    roots = np.roots(_golden_row(p))
+    rho = np.abs(roots[np.abs(roots) < 1]).max()
+    Minv = np.linalg.inv(np.asarray(Axis1D(200, p).M))
+    col = np.abs(Minv[:, 100])
+    assert col[131] / col[130] == pytest.approx(rho, rel=1e-5)
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_chunked_sweep_halos_higher_degree(p):
+    n = 200
+    M = np.asarray(Axis1D(n, p).M)
+    L, D = _ldlt_band(M, p)
+    r = np.random.default_rng(p).normal(size=M.shape[0])
+    xe = np.linalg.solve(M, r)
+
+    def err(H):
+        x = _chunked_band_solve(L, D, r, p, 64, H)
+        return np.abs(x - xe).max() / np.abs(xe).max()
+
+    floor = err(n + p)  # no truncation: the emulation's own rounding
+    h32, h64 = HALOS[p]
+    assert err(h32) <= 2.0 ** -24 / 8
+    assert err(h64) <= 2 * floor + 2.0 ** -53
+    # the quadratic splines' halos are too short here
+    assert err(24) > 2.0 ** -24 / 8
+    assert err(48) > 8 * 2.0 ** -53
