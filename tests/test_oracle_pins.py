@@ -726,10 +726,10 @@ def test_adam_closed_form():
 # projection and the loops (Sec. 6, Sec. 7)
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_projection_reproduces_multilinear(dim):
+@pytest.mark.parametrize("dim,p", [(2, 2), (3, 2), (2, 3), (2, 4), (3, 3)])
+def test_projection_reproduces_multilinear(dim, p):
     n = 6
-    m = Mesh(dim, n)
+    m = Mesh(dim, n, p)
     nodes = np.arange(n + 1) / n
     grids = list(reversed(np.meshgrid(*([nodes] * dim), indexing="ij")))
     nodal = 0.4 + 1.3 * grids[0] - 0.7 * grids[1] + 2.1 * grids[0] * grids[1]
@@ -744,8 +744,9 @@ def test_projection_reproduces_multilinear(dim):
         assert v == pytest.approx(0.4 + 1.3 * x - 0.7 * y + 2.1 * x * y, abs=1e-12)
 
 
-def test_plain_step_mass_balance_over_ten_steps():
-    sc = scn.make_scenario(2, 12, seed=1000)
+@pytest.mark.parametrize("p", [2, 3])
+def test_plain_step_mass_balance_over_ten_steps(p):
+    sc = scn.make_scenario(2, 12, seed=1000, p=p)
     S0 = sc.S0_or_zero()
     S, P, dt = plain_step(sc, S0, 10)
     a = AdsOracle(sc)
