@@ -97,3 +97,70 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
     K[3] = float("nan")
     assert lib.ads_init(C.byref(p), None, K, None, None, None, C.byref(out)) == 4
     assert not out.value
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "adsgb.h"
+
+int main(void) {
+  ads_params p;
+  crvpinn_params c = {64, 4, ADS_F32, 0};
+  ads_ctx* ctx = NULL;
+  ads_status st;
+  size_t b, b0;
+  memset(&p, 0, sizeof p);
+  p.dim = 2;
+  p.n = 256;
+  p.phi = 0.2;
+  p.mu_w = 6.4;
+  p.mu_g = 1.0;
+  p.rho_w = 1.0;
+  p.rho_g = 0.46;
+  p.grav_sign = 1.0;
+  p.kz_ratio = 1.0;
+  p.n_src = 1;
+  p.src[0].center[0] = 0.25;
+  p.src[0].center[1] = 0.25;
+  p.src[0].sigma = 0.03;
+  p.src[0].rate = 1.0;
+  p.src[0].kind = 0;
+  p.ads_dtype = ADS_F64;
+  b = ads_hbm_estimate(&p, &c);
+  b0 = ads_hbm_estimate(&p, NULL);
+  /* a missing K is refused before any CUDA call */
+  st = ads_init(&p, NULL, NULL, NULL, NULL, NULL, &ctx);
+  printf("%s %lu %lu %lu %lu %lu %lu %lu %d %d\n", ads_status_str(ADS_OK), (unsigned long)b,
+         (unsigned long)b0, (unsigned long)sizeof(ads_params), (unsigned long)sizeof(crvpinn_params),
+         (unsigned long)sizeof(hybrid_params), (unsigned long)sizeof(hybrid_stats),
+         (unsigned long)sizeof(ads_allocator), (int)st, ctx == NULL);
+  return 0;
+}
+"""
+
+
+def test_c99_consumer_compiles_links_and_runs(lib, tmp_path):
+    """The header is plain C99 and the library links into a C program; its
+    struct sizes agree with the binding's and the host-only calls work."""
+    import shutil
+    import subprocess
+    from paper_2604_20731_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "consumer.c"
+    src.write_text(C_CONSUMER)
+    exe = tmp_path / "consumer"
+    pkg = os.path.dirname(_lib.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-L", pkg, "-ladsgb",
+                    f"-Wl,-rpath,{pkg}", "-o", str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out[0] == "ok"
+    b, b0 = int(out[1]), int(out[2])
+    assert 0 < b0 < b
+    assert [int(v) for v in out[3:8]] == [C.sizeof(_lib.ads_params), C.sizeof(_lib.crvpinn_params),
+                                          C.sizeof(_lib.hybrid_params), C.sizeof(_lib.hybrid_stats),
+                                          C.sizeof(_lib.ads_allocator)]
+    assert int(out[8]) == 1 and int(out[9]) == 1  # ADS_ERR_INVALID_ARG, no context
