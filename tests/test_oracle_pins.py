@@ -707,7 +707,7 @@ def test_gradient_matches_torch_autograd():
     r = A @ a[:, 0] + c.h ** 2 * torch.from_numpy(f)
     lt = r @ (Ginv @ r)
     lt.backward()
-    assert float(lt) == pytest.approx(loss, rel=1e-12)
+    assert float(lt.detach()) == pytest.approx(loss, rel=1e-12)
     np.testing.assert_allclose(g, t.grad.numpy(), rtol=1e-9, atol=1e-12 * np.abs(g).max())
 
 
