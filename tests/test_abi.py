@@ -164,3 +164,32 @@ def test_c99_consumer_compiles_links_and_runs(lib, tmp_path):
                                           C.sizeof(_lib.hybrid_params), C.sizeof(_lib.hybrid_stats),
                                           C.sizeof(_lib.ads_allocator)]
     assert int(out[8]) == 1 and int(out[9]) == 1  # ADS_ERR_INVALID_ARG, no context
+
+
+def _prototypes():
+    """name -> parameter count for every function prototype in the header."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"typedef[^;]*;", "", src)  # typedefs (incl. function-pointer types)
+    out = {}
+    for m in re.finditer(r"([a-z_][a-z0-9_]*)\s*\(([^()]*(?:\([^()]*\)[^()]*)*)\)\s*;", src):
+        name, params = m.group(1), m.group(2).strip()
+        if params in ("", "void"):
+            out[name] = 0
+        else:
+            depth, count = 0, 1
+            for ch in params:
+                depth += ch == "("
+                depth -= ch == ")"
+                count += ch == "," and depth == 0
+            out[name] = count
+    return out
+
+
+def test_binding_signatures_match_header_prototypes():
+    from paper_2604_20731_gb300 import _lib
+    protos = _prototypes()
+    assert set(protos) >= set(declared_functions())
+    for name, (_, argtypes) in _lib.SIGNATURES.items():
+        assert name in protos, name
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
