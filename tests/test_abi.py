@@ -193,3 +193,33 @@ def test_binding_signatures_match_header_prototypes():
     for name, (_, argtypes) in _lib.SIGNATURES.items():
         assert name in protos, name
         assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+
+
+def _prototype_params():
+    """name -> list of parameter declarations for every prototype."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"typedef[^;]*;", "", src)
+    out = {}
+    for m in re.finditer(r"([a-z_][a-z0-9_]*)\s*\(([^()]*)\)\s*;", src):
+        params = [p.strip() for p in m.group(2).split(",")] if m.group(2).strip() not in ("", "void") else []
+        out[m.group(1)] = params
+    return out
+
+
+def test_binding_parameter_types_match_header():
+    from paper_2604_20731_gb300 import _lib
+    scalars = {"double": C.c_double, "int": C.c_int, "size_t": C.c_size_t, "int64_t": C.c_int64,
+               "float": C.c_float}
+    for name, params in _prototype_params().items():
+        argtypes = _lib.SIGNATURES[name][1]
+        assert len(params) == len(argtypes), name
+        for decl, at in zip(params, argtypes):
+            if "*" in decl:
+                assert at is C.c_void_p or at is C.c_char_p or issubclass(at, C._Pointer), (name, decl, at)
+            else:
+                base = decl.replace("const ", "").split()[0]
+                if base in scalars:
+                    assert at is scalars[base], (name, decl, at)
+                else:  # enums travel as int
+                    assert at is C.c_int, (name, decl, at)
