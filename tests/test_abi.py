@@ -223,3 +223,20 @@ def test_binding_parameter_types_match_header():
                     assert at is scalars[base], (name, decl, at)
                 else:  # enums travel as int
                     assert at is C.c_int, (name, decl, at)
+
+
+def test_binding_return_types_match_header():
+    from paper_2604_20731_gb300 import _lib
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"typedef[^;]*;", "", src)
+    expect = {"ads_status": C.c_int, "size_t": C.c_size_t, "void": None, "const char*": C.c_char_p}
+    seen = 0
+    for m in re.finditer(r"^\s*((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?)\s*([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
+        ret, name = re.sub(r"\s+\*", "*", m.group(1).strip()), m.group(2)
+        if name not in _lib.SIGNATURES:
+            continue
+        assert ret in expect, (name, ret)
+        assert _lib.SIGNATURES[name][0] is expect[ret], (name, ret, _lib.SIGNATURES[name][0])
+        seen += 1
+    assert seen == len(_lib.SIGNATURES)
