@@ -240,3 +240,34 @@ def test_binding_return_types_match_header():
         assert _lib.SIGNATURES[name][0] is expect[ret], (name, ret, _lib.SIGNATURES[name][0])
         seen += 1
     assert seen == len(_lib.SIGNATURES)
+
+
+def test_struct_field_offsets_match_c(lib, tmp_path):
+    """Every field of every ctypes structure sits at the offset a C compiler
+    gives the header's struct (offsetof), and every struct has the C size."""
+    import shutil
+    import subprocess
+    from paper_2604_20731_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [_lib.ads_source, _lib.ads_params, _lib.crvpinn_params, _lib.ads_allocator,
+               _lib.hybrid_params, _lib.hybrid_stats, _lib.ads_server_config, _lib.ads_request_spec,
+               _lib.ads_request_result, _lib.ads_server_stats_t]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "adsgb.h"', "int main(void) {"]
+    expect = []
+    for S in structs:
+        lines.append(f'  printf("%lu\\n", (unsigned long)sizeof({S.__name__}));')
+        expect.append(C.sizeof(S))
+        for fname, _ in S._fields_:
+            lines.append(f'  printf("%lu\\n", (unsigned long)offsetof({S.__name__}, {fname}));')
+            expect.append(getattr(S, fname).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "offsets.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "offsets"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True, capture_output=True, text=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect
