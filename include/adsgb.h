@@ -155,6 +155,9 @@ typedef enum {
 ads_status ads_init(const ads_params* params, const crvpinn_params* crv,
                     const double* K_nodal, const double* phi_nodal,
                     const double* S0, void* stream, ads_ctx** out);
+/* ads_destroy: waits for the context's stream, frees every device buffer
+ * (through the caller's allocator when one was given), the pinned staging
+ * buffer, a stream the context created, and the context.  NULL: no-op. */
 void ads_destroy(ads_ctx* ctx);
 
 /* ads_init_with_allocator: ads_init whose context buffers come from the
@@ -176,7 +179,11 @@ ads_status ads_init_with_allocator(const ads_params* params, const crvpinn_param
                                    const double* S0, void* stream, const ads_allocator* allocator,
                                    ads_ctx** out);
 
-/* Bytes of device memory ads_init would allocate (for admission control). */
+/* ads_hbm_estimate (no counterpart in the paper; admission control): bytes of
+ * device memory ads_init would allocate for these parameters (crv NULL: a
+ * saturation-only context); 0 when ads_init would refuse them.  Host-only: no
+ * CUDA call.  Not counted: the Galerkin-pressure workspace, which
+ * ads_galerkin_pressure allocates on first use. */
 size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv);
 
 /* ads_set_concurrency: the number of contexts expected to run on the GPU at
@@ -228,19 +235,26 @@ ads_status ads_cfl_dt(ads_ctx* ctx, double cfl, double src_frac, double dt_cap,
  * the context's non-finite flag, which hybrid_step then reports. */
 ads_status ads_galerkin_pressure(ads_ctx* ctx);
 
-/* Replace the pressure / saturation coefficients ((n+2)^dim host doubles). */
+/* ads_set_pressure_coeffs / ads_set_saturation: replace the B-spline
+ * coefficients of p or S (the unknowns of Eq. 10a; (n+2)^dim host doubles,
+ * copied; the call waits for the stream).  ads_set_saturation also makes the
+ * new int S the reference of the mass balance.
+ * Errors: ADS_ERR_INVALID_ARG (NULL), ADS_ERR_NONFINITE (a non-finite value). */
 ads_status ads_set_pressure_coeffs(ads_ctx* ctx, const double* host_p);
 ads_status ads_set_saturation(ads_ctx* ctx, const double* host_s);
 
 /* ---- CRVPINN pressure (Sec. 5) ---------------------------------------------
  * crvpinn_set_theta: load network parameters (nparams host doubles, layout
  * [W_1 (out x in, row-major), b_1, ..., W_5, b_5]) and reset Adam (m=v=0,t=0).
- * crvpinn_num_params: nparams for this context's network. */
+ * crvpinn_num_params: nparams for this context's network.
+ * Errors: ADS_ERR_STATE (a context without a network), ADS_ERR_INVALID_ARG
+ * (NULL), ADS_ERR_NONFINITE (a non-finite parameter). */
 ads_status crvpinn_set_theta(ads_ctx* ctx, const double* theta);
 ads_status crvpinn_num_params(const ads_ctx* ctx, int* nparams);
 
 /* crvpinn_update_coefficients: alpha = lambda(S) K and RHS (Eq. 23b) at the
- * collocation nodes from the current saturation coefficients. */
+ * collocation nodes from the current saturation coefficients.
+ * Errors: ADS_ERR_STATE (no network). */
 ads_status crvpinn_update_coefficients(ads_ctx* ctx);
 
 /* crvpinn_loss_grad: one evaluation of the robust loss (Eq. 27) and its
@@ -248,20 +262,24 @@ ads_status crvpinn_update_coefficients(ads_ctx* ctx);
  * MLP forward, residual (Eq. 25), G^-1 RES through the sine transform along x
  * and shifted tridiagonal line solves along y (Eq. 28), loss, adjoint
  * 2 A G^-1 RES, MLP backward.  loss_out (nullable) is filled after a
- * synchronisation; the gradient is kept on the device (ADS_FIELD_GRAD). */
+ * synchronisation; the gradient is kept on the device (ADS_FIELD_GRAD).
+ * Errors: ADS_ERR_STATE (no network), ADS_ERR_NONFINITE (non-finite loss). */
 ads_status crvpinn_loss_grad(ads_ctx* ctx, double* loss_out);
 
 /* crvpinn_pretrain: coefficients from the current saturation, reset Adam,
  * then `iters` Adam iterations at learning rate lr (Sec. 6 step 2).
  * crvpinn_pressure_update: same without the Adam reset (Sec. 6 step 7; Adam
  * moments persist across updates).  loss_out (nullable): loss of the last
- * iteration, after a synchronisation. */
+ * iteration, after a synchronisation.
+ * Errors: ADS_ERR_STATE (no network), ADS_ERR_INVALID_ARG (iters < 0, lr not
+ * positive and finite), ADS_ERR_NONFINITE (non-finite loss). */
 ads_status crvpinn_pretrain(ads_ctx* ctx, int iters, double lr, double* loss_out);
 ads_status crvpinn_pressure_update(ads_ctx* ctx, int iters, double lr, double* loss_out);
 
 /* ads_project_pressure: network at the interior nodes (boundary 0), L2
  * projection of its piecewise-(bi)linear interpolant into the B-spline space
- * (Sec. 6 step 4) -> pressure coefficients. */
+ * (Sec. 6 step 4) -> pressure coefficients.  Errors: ADS_ERR_STATE (no
+ * network). */
 ads_status ads_project_pressure(ads_ctx* ctx);
 
 /* ---- hybrid step (Sec. 6) ---------------------------------------------------
@@ -269,12 +287,18 @@ ads_status ads_project_pressure(ads_ctx* ctx);
  * saturation steps; coefficients from the new saturation; adam_iters Adam
  * iterations.  The whole step is replayed from a CUDA graph.  stats (nullable)
  * is filled after a synchronisation; ADS_ERR_NONFINITE if the loss or dt is
- * not finite. */
+ * not finite.
+ * Errors: ADS_ERR_INVALID_ARG (hp NULL, n_sub or adam_iters < 0, dt, lr, cfl
+ * or src_frac out of range), ADS_ERR_STATE (no network), ADS_ERR_NONFINITE,
+ * ADS_ERR_TIMEOUT (a kernel's bounded device wait gave up). */
 ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stats);
 
-/* hybrid_step_batch: hybrid_step for n independent contexts sharing the
- * same stream; the contexts' work is enqueued back to back on that stream
- * so that it overlaps on the device.  stats: NULL or n entries. */
+/* hybrid_step_batch (no counterpart in the paper: it steps one scenario at a
+ * time): hybrid_step for n independent contexts, every step enqueued before
+ * any statistics are read, so that contexts on different streams overlap on
+ * the device.  stats: NULL or n entries.  Errors: ADS_ERR_INVALID_ARG (ctxs or
+ * hp NULL, n < 0), else the first failing context's status (the contexts
+ * after it are not stepped, or not read). */
 ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
                              hybrid_stats* stats);
 
@@ -297,7 +321,13 @@ ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* h
  * statistics, and forgets the request.  A scenario whose estimate exceeds the
  * whole budget is refused at submission (ADS_ERR_OOM).
  * ads_server_destroy stops the worker, releases resident scenarios and drops
- * waiting ones. */
+ * waiting ones.
+ * Errors: create: ADS_ERR_INVALID_ARG (NULL, hbm_budget 0, n_streams outside
+ * 1..64 or max_active < 1), ADS_ERR_CUDA.  submit: ADS_ERR_INVALID_ARG (NULL
+ * spec, K or id_out, n_steps < 0, parameters ads_init would refuse),
+ * ADS_ERR_OOM (more than the whole budget).  wait: ADS_ERR_INVALID_ARG
+ * (unknown id), ADS_ERR_TIMEOUT, else the request's own status.  stats:
+ * ADS_ERR_INVALID_ARG (NULL). */
 typedef struct ads_server ads_server;
 typedef struct {
   size_t hbm_budget;   /* bytes of device memory for resident scenarios      */
@@ -406,6 +436,10 @@ ads_status ads_kernel_launches(const ads_ctx* ctx, unsigned long long* count);
 ads_status ads_profile_train(ads_ctx* ctx, int iters, double* ms_out);
 ads_status ads_profile_saturation(ads_ctx* ctx, int steps, double* ms_out);
 
+/* ads_last_error: the message of the context's last failure ("" if none;
+ * "null context" for NULL), owned by the context and valid until its next
+ * call or ads_destroy.  ads_status_str: a static name for a status ("unknown"
+ * for other values).  Neither touches the GPU. */
 const char* ads_last_error(const ads_ctx* ctx);
 const char* ads_status_str(ads_status st);
 
