@@ -335,6 +335,34 @@ def test_galerkin_pressure_manufactured_h3():
     assert min(rates) > 2.7, (errs, rates)
 
 
+def test_galerkin_pressure_manufactured_3d_h3():
+    """3D with anisotropy K_z = kz K: p* = sin(pi x) sin(pi y) sin(2 pi z) with
+    its source q = (2 + 4 kz) pi^2 lambda_w p* (a kz on another axis would
+    give another source); the L2 error falls like h^3."""
+    import oracle.pressure as pr
+    kz = 0.3
+    errs = []
+    for n in (4, 8, 16):
+        sc = scn.make_scenario(3, n, seed=1, kz_ratio=kz)
+        sc.K = np.ones_like(sc.K)
+        lam = 1.0 / sc.mu_w
+        m = Mesh(3, n)
+        coords = m.gauss_coords()
+        orig = pr.gaussian_sources
+        pr.gaussian_sources = lambda s, c: ((2 + 4 * kz) * np.pi ** 2 * lam * np.sin(np.pi * c[0])
+                                            * np.sin(np.pi * c[1]) * np.sin(2 * np.pi * c[2]),
+                                            np.zeros_like(c[0]))
+        try:
+            P = galerkin_pressure(sc, np.zeros((n + 2,) * 3))
+        finally:
+            pr.gaussian_sources = orig
+        ph = m.at_gauss(P)
+        ex = np.sin(np.pi * coords[0]) * np.sin(np.pi * coords[1]) * np.sin(2 * np.pi * coords[2])
+        errs.append(math.sqrt(np.sum(m.gauss_weights() * (ph - ex) ** 2)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 2.6, (errs, rates)
+
+
 def test_galerkin_pressure_matches_element_loop():
     """The Galerkin system assembled element by element with scalar basis
     evaluation: (lambda K grad B_kl, grad B_ij) p = (q_w + q_g, B_ij)
