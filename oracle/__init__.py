@@ -19,6 +19,10 @@ Modules:
   hybrid    -- projection of the network pressure (Sec. 6, step 4) and the
                hybrid loop (Sec. 6)
 
+The spline degree follows the scenario (`p`, default 2: the quadratic C1
+splines of Sec. 4): n + p functions per axis and p + 1 Gauss points, so the
+same code serves the higher degrees the paper mentions (p = 3, 4).
+
 Readings of the paper where it is silent or garbled are documented at each
 function; the gravity sign, boundary conditions and residual sign follow the
 derivation from Eqs. 1-5 (see each docstring).
