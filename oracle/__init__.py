@@ -20,8 +20,9 @@ Modules:
                hybrid loop (Sec. 6)
 
 The spline degree follows the scenario (`p`, default 2: the quadratic C1
-splines of Sec. 4): n + p functions per axis and p + 1 Gauss points, so the
-same code serves the higher degrees the paper mentions (p = 3, 4).
+splines the configurations use): n + p functions per axis and p + 1 Gauss
+points.  This is the general order-r, C^(r-1) basis of Eq. 11; the pins cover
+p = 2, 3, 4.
 
 Readings of the paper where it is silent or garbled are documented at each
 function; the gravity sign, boundary conditions and residual sign follow the
