@@ -271,3 +271,54 @@ def test_struct_field_offsets_match_c(lib, tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                           text=True).stdout.split()]
     assert got == expect
+
+
+def _mutate(p, crv, what):
+    import math
+    if what == "dim=1": p.dim = 1
+    elif what == "n=1": p.n = 1
+    elif what == "n 2D too large": p.n = 8193
+    elif what == "n 3D too large": p.dim, p.n = 3, 513
+    elif what == "n 2D FP64 strip": p.n, p.ads_dtype = 7169, 0
+    elif what == "phi=0": p.phi = 0.0
+    elif what == "mu_w=0": p.mu_w = 0.0
+    elif what == "mu_g=nan": p.mu_g = math.nan
+    elif what == "grav<0": p.grav = -1.0
+    elif what == "grav=inf": p.grav = math.inf
+    elif what == "grav_sign=nan": p.grav_sign = math.nan
+    elif what == "n_src=9": p.n_src = 9
+    elif what == "n_src=-1": p.n_src = -1
+    elif what == "sigma=0": p.src[0].sigma = 0.0
+    elif what == "rate<0": p.src[0].rate = -1.0
+    elif what == "rate=inf": p.src[0].rate = math.inf
+    elif what == "kind=2": p.src[0].kind = 2
+    elif what == "ads_dtype=bf16": p.ads_dtype = 2
+    elif what == "layers=3": crv.hidden_layers = 3
+    elif what == "width=96": crv.width = 96
+    elif what == "dtype=5": crv.dtype = 5
+    elif what == "f64 width 128": crv.width, crv.dtype = 128, 0
+    elif what == "act_chunks<0": crv.act_chunks = -1
+    elif what == "n=2 with network": p.n = 2
+    else: raise KeyError(what)
+
+
+@pytest.mark.parametrize("what,code", [
+    ("dim=1", 7), ("n=1", 1), ("n 2D too large", 1), ("n 3D too large", 1), ("n 2D FP64 strip", 1),
+    ("phi=0", 1), ("mu_w=0", 1), ("mu_g=nan", 1), ("grav<0", 1), ("grav=inf", 1),
+    ("grav_sign=nan", 1), ("n_src=9", 1), ("n_src=-1", 1), ("sigma=0", 1), ("rate<0", 1),
+    ("rate=inf", 1), ("kind=2", 1), ("ads_dtype=bf16", 1), ("layers=3", 7), ("width=96", 7),
+    ("dtype=5", 7), ("f64 width 128", 7), ("act_chunks<0", 1), ("n=2 with network", 1)])
+def test_parameter_validation_before_any_cuda_call(lib, what, code):
+    """Each refusal of the parameter check: ads_init returns its status before
+    touching the GPU (K is not even looked at), and ads_hbm_estimate gives 0."""
+    from paper_2604_20731_gb300 import _lib
+    from paper_2604_20731_gb300 import scenario as scn
+    from paper_2604_20731_gb300.solver import make_params
+    p = make_params(scn.make_scenario(2, 16), "f32")
+    crv = _lib.crvpinn_params(64, 4, _lib.ADS_F32, 0)
+    assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) > 0
+    _mutate(p, crv, what)
+    out = C.c_void_p()
+    assert lib.ads_init(C.byref(p), C.byref(crv), None, None, None, None, C.byref(out)) == code
+    assert not out.value
+    assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) == 0
