@@ -322,3 +322,72 @@ def test_parameter_validation_before_any_cuda_call(lib, what, code):
     assert lib.ads_init(C.byref(p), C.byref(crv), None, None, None, None, C.byref(out)) == code
     assert not out.value
     assert lib.ads_hbm_estimate(C.byref(p), C.byref(crv)) == 0
+
+
+NULL_SWEEP = r"""
+import ctypes as C, json, math
+from paper_2604_20731_gb300 import _lib
+lib = _lib.load()
+skip = {"ads_init", "ads_init_with_allocator", "ads_hbm_estimate", "ads_status_str",
+        "ads_saturation_step_noalloc", "hybrid_step_batch"}
+res = {}
+for name, (rt, args) in _lib.SIGNATURES.items():
+    if name in skip or name.startswith("ads_server_") or not args or args[0] is not C.c_void_p:
+        continue
+    vals = [None]
+    for a in args[1:]:
+        vals.append(0.0 if a is C.c_double else (0 if a in (C.c_int, C.c_size_t, C.c_int64) else None))
+    r = getattr(lib, name)(*vals)
+    res[name] = r.decode() if isinstance(r, bytes) else r
+# server: NULL handles and invalid configurations (checked before any CUDA call)
+out = C.c_void_p()
+srv = {"create_null": lib.ads_server_create(None, C.byref(out)),
+       "wait_null": lib.ads_server_wait(None, 0, 1.0, None, None, None),
+       "stats_null": lib.ads_server_stats(None, None),
+       "submit_null": lib.ads_server_submit(None, None, None, None, None, None, None)}
+for label, cfg in (("budget0", (0, 4, 2)), ("active0", (1 << 30, 0, 2)), ("streams0", (1 << 30, 4, 0)),
+                   ("streams65", (1 << 30, 4, 65))):
+    srv[label] = lib.ads_server_create(C.byref(_lib.ads_server_config(*cfg)), C.byref(out))
+lib.ads_server_destroy(None)
+# batch
+hp = _lib.hybrid_params(10, 1.0, 1, 0.1, 0.05, 100, 1e-3)
+arr = (C.c_void_p * 1)()
+srv["batch_null"] = lib.hybrid_step_batch(None, 0, C.byref(hp), None)
+srv["batch_negative"] = lib.hybrid_step_batch(arr, -1, C.byref(hp), None)
+# allocation-free step: argument checks before any CUDA call
+from paper_2604_20731_gb300 import scenario as scn
+from paper_2604_20731_gb300.solver import make_params
+def noalloc(mut, same=False, dt=1e-3):
+    p = make_params(scn.make_scenario(2, 8), "f64")
+    mut(p)
+    a, b = C.c_void_p(0x1000), C.c_void_p(0x2000)
+    return lib.ads_saturation_step_noalloc(C.byref(p), a, None, a, a, dt, a if same else b, None)
+na = {"same_in_out": noalloc(lambda p: None, same=True), "dim3": noalloc(lambda p: setattr(p, "dim", 3)),
+      "f32": noalloc(lambda p: setattr(p, "ads_dtype", 1)), "n513": noalloc(lambda p: setattr(p, "n", 513)),
+      "dt0": noalloc(lambda p: None, dt=0.0), "nsrc9": noalloc(lambda p: setattr(p, "n_src", 9))}
+na["null"] = lib.ads_saturation_step_noalloc(None, None, None, None, None, 1e-3, None, None)
+print(json.dumps({"ctx": res, "server": srv, "noalloc": na}))
+"""
+
+
+def test_null_handles_and_refused_arguments_before_any_cuda_call(lib):
+    """Every ctx-taking entry point refuses a NULL context with
+    ADS_ERR_INVALID_ARG; the server and the allocation-free step refuse bad
+    arguments before touching the GPU.  Run in a child process: a crash fails
+    the test instead of the session."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, "-c", NULL_SWEEP], cwd=ROOT, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    ctx = r["ctx"]
+    assert ctx.pop("ads_last_error") == "null context"
+    assert ctx.pop("ads_destroy") is None
+    assert len(ctx) >= 20
+    assert all(v == 1 for v in ctx.values()), {k: v for k, v in ctx.items() if v != 1}
+    assert all(v == 1 for v in r["server"].values()), r["server"]
+    na = r["noalloc"]
+    assert na["dim3"] == 7 and na["f32"] == 7
+    assert all(na[k] == 1 for k in ("same_in_out", "n513", "dt0", "nsrc9", "null")), na
