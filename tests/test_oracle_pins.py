@@ -796,3 +796,179 @@ def test_hybrid_short_run_reduces_loss():
     assert losses[-1] < 0.2 * losses[0]
     S, P, th2, dt, l2 = h.hybrid_step(sc.S0_or_zero(), th, opt, n_sub=2, adam_iters=3, lr=1e-2)
     assert np.isfinite(S).all() and dt > 0 and len(l2) == 3
+
+
+# ----------------------------------------------------------------------------
+# 3D with a vertical permeability K_z = kz K (reading R23): the flux of the
+# saturation step, the 7-point operator and the gravity divergence of Eq. 23b
+# ----------------------------------------------------------------------------
+
+def _brute_rhs_3d(sc, S, P, dt):
+    """Element loop over a 3D mesh with pointwise scalar basis evaluation: the
+    right-hand side of Eq. 10b with the vertical (z, array axis 0) Darcy flux
+    scaled by kz and gravity acting along -z."""
+    n = sc.n
+    knots = open_uniform_knots(n, 2)
+    hat = open_uniform_knots(n, 1)
+    xg, wg = np.polynomial.legendre.leggauss(3)
+    xg, wg = 0.5 * (xg + 1), 0.5 * wg
+    h = 1.0 / n
+    R = np.zeros((n + 2,) * 3)
+    for ez in range(n):
+        for ey in range(n):
+            for ex in range(n):
+                for qz in range(3):
+                    for qy in range(3):
+                        for qx in range(3):
+                            x, y, z = (ex + xg[qx]) * h, (ey + xg[qy]) * h, (ez + xg[qz]) * h
+                            w = wg[qx] * wg[qy] * wg[qz] * h ** 3
+                            bx = {i: bspline_scalar(knots, i, 2, x) for i in range(ex, ex + 3)}
+                            by = {j: bspline_scalar(knots, j, 2, y) for j in range(ey, ey + 3)}
+                            bz = {k: bspline_scalar(knots, k, 2, z) for k in range(ez, ez + 3)}
+                            dbx = {i: bspline_scalar_deriv(knots, i, 2, x) for i in bx}
+                            dby = {j: bspline_scalar_deriv(knots, j, 2, y) for j in by}
+                            dbz = {k: bspline_scalar_deriv(knots, k, 2, z) for k in bz}
+                            idx = [(k, j, i) for k in bz for j in by for i in bx]
+                            s = sum(S[k, j, i] * bz[k] * by[j] * bx[i] for k, j, i in idx)
+                            px = sum(P[k, j, i] * bz[k] * by[j] * dbx[i] for k, j, i in idx)
+                            py = sum(P[k, j, i] * bz[k] * dby[j] * bx[i] for k, j, i in idx)
+                            pz = sum(P[k, j, i] * dbz[k] * by[j] * bx[i] for k, j, i in idx)
+                            kk = sum(sc.K[k, j, i] * bspline_scalar(hat, k, 1, z) * bspline_scalar(hat, j, 1, y)
+                                     * bspline_scalar(hat, i, 1, x)
+                                     for k in (ez, ez + 1) for j in (ey, ey + 1) for i in (ex, ex + 1))
+                            st = min(max(s, 0.0), 1.0)
+                            lg, lw = st / sc.mu_g, (1 - st) / sc.mu_w
+                            qi = qp = 0.0
+                            for src in sc.sources:
+                                r2 = (x - src.center[0]) ** 2 + (y - src.center[1]) ** 2 + (z - src.center[2]) ** 2
+                                G = math.exp(-r2 / (2 * src.sigma ** 2)) / (2 * math.pi * src.sigma ** 2) ** 1.5
+                                if src.kind == 0:
+                                    qi += src.rate * G
+                                else:
+                                    qp += src.rate * G
+                            qg = qi - lg / (lg + lw) * qp
+                            fx = kk * px
+                            fy = kk * py
+                            fz = sc.kz_ratio * kk * (pz + sc.grav_sign * sc.rho_g * sc.grav)
+                            for k, j, i in idx:
+                                v = bx[i] * by[j] * bz[k]
+                                vx = dbx[i] * by[j] * bz[k]
+                                vy = bx[i] * dby[j] * bz[k]
+                                vz = bx[i] * by[j] * dbz[k]
+                                R[k, j, i] += w * (s * v + dt / sc.phi * (qg * v - lg * (fx * vx + fy * vy + fz * vz)))
+    return R
+
+
+def test_rhs_matches_element_loop_3d_anisotropic():
+    """The 3D saturation right-hand side with K_z = 0.1 K, gravity on and the
+    clamp active, against the element loop.  A K_z on the wrong axis or on the
+    wrong velocity component changes R by far more than the tolerance."""
+    sc = scn.make_scenario(3, 3, seed=12, S0="random", grav=0.9, kz_ratio=0.1)
+    sc.sources[0].center = (0.3, 0.45, 0.6)
+    sc.sources[1].center = (0.7, 0.35, 0.25)
+    sc.sources[0].sigma = sc.sources[1].sigma = 0.25
+    rng = np.random.default_rng(13)
+    S = rng.uniform(-0.1, 1.1, size=(5, 5, 5))
+    P = rng.normal(size=(5, 5, 5))
+    dt = 0.011
+    R = AdsOracle(sc).rhs(S, P, dt)
+    Rb = _brute_rhs_3d(sc, S, P, dt)
+    np.testing.assert_allclose(R, Rb, rtol=0, atol=2e-7 * np.abs(Rb).max())
+    # the anisotropy is visible at this tolerance: the isotropic flux differs
+    sc_iso = scn.make_scenario(3, 3, seed=12, S0="random", grav=0.9, kz_ratio=1.0)
+    sc_iso.sources = sc.sources
+    R_iso = AdsOracle(sc_iso).rhs(S, P, dt)
+    assert np.abs(R_iso - Rb).max() > 1e-3 * np.abs(Rb).max()
+
+
+def test_cfl_dt_rule_3d_vertical_gradient():
+    """With p linear in z only, |K (grad p)| = kz K dp/dz: the velocity limit
+    sees the vertical permeability, not K."""
+    n = 4
+    sc = scn.make_scenario(3, n, seed=1, kz_ratio=0.25)
+    sc.sources = []
+    sc.K = np.full_like(sc.K, 2.0)
+    knots = open_uniform_knots(n, 2)
+    grev = np.array([(knots[i + 1] + knots[i + 2]) / 2 for i in range(n + 2)])
+    P = np.broadcast_to(100.0 * grev[:, None, None], (n + 2,) * 3).copy()  # p = 100 z
+    dt = AdsOracle(sc).cfl_dt(P)
+    vmax = 0.25 * 2.0 * 100.0 / (sc.mu_g * sc.phi)
+    assert dt == pytest.approx(0.1 * (1 / n) / vmax, rel=1e-12)
+    # the same gradient along x sees K itself
+    Px = np.broadcast_to(100.0 * grev[None, None, :], (n + 2,) * 3).copy()
+    dtx = AdsOracle(sc).cfl_dt(Px)
+    assert dtx == pytest.approx(0.1 * (1 / n) / (2.0 * 100.0 / (sc.mu_g * sc.phi)), rel=1e-12)
+
+
+def test_operator_matches_stencil_brute_force_3d_anisotropic():
+    """7-point residual with the vertical differences weighted by kz."""
+    N = 4
+    sc = scn.make_scenario(3, N, seed=4, S0="random", grav=0.8, kz_ratio=0.3)
+    c = CrvOracle(sc)
+    alpha, f = c.coefficients(sc.S0)
+    u_int = np.random.default_rng(2).normal(size=c.M)
+    u = embed_interior(u_int, 3, N)
+    h = 1.0 / N
+    res = []
+    for k in range(1, N):
+        for j in range(1, N):
+            for i in range(1, N):
+                r = (alpha[k, j, i - 1] * (u[k, j, i] - u[k, j, i - 1])
+                     - alpha[k, j, i] * (u[k, j, i + 1] - u[k, j, i])
+                     + alpha[k, j - 1, i] * (u[k, j, i] - u[k, j - 1, i])
+                     - alpha[k, j, i] * (u[k, j + 1, i] - u[k, j, i])
+                     + 0.3 * (alpha[k - 1, j, i] * (u[k, j, i] - u[k - 1, j, i])
+                              - alpha[k, j, i] * (u[k + 1, j, i] - u[k, j, i])))
+                res.append(r)
+    np.testing.assert_allclose(c.residual(alpha, f, u_int), np.array(res) + h * h * f, atol=1e-13)
+
+
+def test_rhs_closed_form_brute_force_3d():
+    """Eq. 23b at one interior 3D node, written out by hand: the gravity
+    divergence is a forward difference along z of kz K (rho_w lambda_w +
+    rho_g lambda_g), and the Gaussians carry the 3D normalisation."""
+    N = 5
+    sc = scn.make_scenario(3, N, seed=8, S0="random", grav=1.3, kz_ratio=0.2)
+    c = CrvOracle(sc)
+    alpha, f = c.coefficients(sc.S0)
+    knots = open_uniform_knots(N, 2)
+    k0, j0, i0 = 2, 1, 3
+
+    def s_at(kk, jj, ii):
+        x, y, z = ii / N, jj / N, kk / N
+        v = sum(sc.S0[cz, b, a] * bspline_scalar(knots, a, 2, x) * bspline_scalar(knots, b, 2, y)
+                * bspline_scalar(knots, cz, 2, z)
+                for a in range(N + 2) for b in range(N + 2) for cz in range(N + 2))
+        return min(max(v, 0), 1)
+
+    def rl(kk, jj, ii):
+        s = s_at(kk, jj, ii)
+        return 0.2 * sc.K[kk, jj, ii] * ((1 - s) / sc.mu_w * sc.rho_w + s / sc.mu_g * sc.rho_g)
+    s = s_at(k0, j0, i0)
+    assert alpha[k0, j0, i0] == pytest.approx(((1 - s) / sc.mu_w + s / sc.mu_g) * sc.K[k0, j0, i0], rel=1e-13)
+    x, y, z = i0 / N, j0 / N, k0 / N
+    norm = (2 * math.pi * 0.03 ** 2) ** 1.5
+    qi = sc.sources[0].rate * math.exp(-((x - .25) ** 2 + (y - .25) ** 2 + (z - .25) ** 2) / (2 * .03 ** 2)) / norm
+    qp = sc.sources[1].rate * math.exp(-((x - .75) ** 2 + (y - .75) ** 2 + (z - .75) ** 2) / (2 * .03 ** 2)) / norm
+    expect = -sc.grav * (rl(k0 + 1, j0, i0) - rl(k0, j0, i0)) * N - (qi - qp)
+    m = N - 1
+    assert f[((k0 - 1) * m + (j0 - 1)) * m + (i0 - 1)] == pytest.approx(expect, rel=1e-12, abs=1e-12)
+
+
+def test_loss_equals_discrete_h1_error_for_unit_alpha_3d():
+    """3D twin of the inf-sup identity: with alpha = 1 and kz = 1 the 7-point
+    residual operator is h^2 G, so LOSS = h^2 sum over grid edges of the
+    squared jump of u - u* (Eq. 26 with the {6, -1} stencil)."""
+    N = 6
+    sc = scn.make_scenario(3, N, seed=6)
+    c = CrvOracle(sc)
+    alpha = np.ones((N + 1,) * 3)
+    f = np.random.default_rng(1).normal(size=c.M)
+    ustar = c.direct_solution(alpha, f)
+    u = np.random.default_rng(2).normal(size=c.M)
+    r = c.residual(alpha, f, u)
+    e = embed_interior(u - ustar, 3, N)
+    jumps = sum(np.sum(np.diff(e, axis=a) ** 2) for a in range(3))
+    h = c.h
+    for loss in (r @ c.gram_solve_lu(r), r @ c.gram_solve_fd(r)):
+        assert loss == pytest.approx(h * h * jumps, rel=1e-10)
