@@ -409,7 +409,8 @@ ads_status ads_load(ads_ctx* ctx, const char* path);
  * memory lives in one fixed 4 MiB device array inside the library, reserved on
  * every GPU that loads the library until the process exits; meshes up to
  * n = 512 fit, larger n returns ADS_ERR_INVALID_ARG.  2D, ads_dtype = ADS_F64
- * only (else ADS_ERR_UNSUPPORTED).  The first call on a device looks up that
+ * only (else ADS_ERR_UNSUPPORTED).  The parameters pass the same check as
+ * ads_init (same statuses), before any CUDA call.  The first call on a device looks up that
  * array's device address (set-up), so make the first call before any stream
  * capture.  Every call shares the one array: calls that may overlap on the
  * GPU (different streams, or different host threads) race and must be
@@ -420,6 +421,17 @@ ads_status ads_saturation_step_noalloc(const ads_params* params, const double* d
                                        const double* d_phi, const double* d_S,
                                        const double* d_P, double dt, double* d_S_out,
                                        void* stream);
+/* The step above reports problems in a status word inside the same array,
+ * since it returns before its kernels run.  The word is sticky: every step
+ * ORs into it and none clears it.  ads_saturation_step_noalloc_status waits
+ * for `stream` (10 s deadline -> ADS_ERR_TIMEOUT), reads the word into
+ * *flags_out (nullable) and clears it.  It returns ADS_ERR_TIMEOUT when a
+ * bounded device wait of a step gave up (bit 8: that step's d_S_out is
+ * incomplete), ADS_ERR_NONFINITE when a step's int S_out was not finite
+ * (bit 0), else ADS_OK.  Call it on the stream of the steps it should cover.
+ * The array's device address is looked up once per device and kept, so
+ * neither call may be used after cudaDeviceReset in the same process. */
+ads_status ads_saturation_step_noalloc_status(void* stream, int* flags_out);
 
 /* ---- diagnostics (no counterpart in the paper) ------------------------------
  * ads_kernel_launches: number of library kernels enqueued on this context so
@@ -433,6 +445,16 @@ ads_status ads_saturation_step_noalloc(const ads_params* params, const double* d
  * ads_profile_saturation: `steps` saturation steps (current dt) likewise;
  * ms_out[3]: quadrature + x sweep, y sweep, mass bookkeeping. */
 ads_status ads_kernel_launches(const ads_ctx* ctx, unsigned long long* count);
+/* ads_measure_unit_rates: measured peak rates of the arithmetic units the
+ * rooflines use, on the current device (no counterpart in the paper).  One
+ * wave of CTAs runs 8 independent chains per thread of one operation;
+ * out[0..4] = results per second of ex2.approx.f32, rcp.approx.f32, the
+ * tanh pair (one ex2 + one rcp, counted as one result), scalar FP32 fma and
+ * packed fma.rn.f32x2 (two results per instruction); out[5..9] = the same per
+ * SM per clock; out[10] = the SM clock (MHz) the chains ran at.  nout >= 11.
+ * Allocates a few MB of device memory for the run and frees it; synchronous.
+ * Errors: ADS_ERR_INVALID_ARG (NULL or nout < 11), ADS_ERR_CUDA. */
+ads_status ads_measure_unit_rates(double* out, int nout);
 ads_status ads_profile_train(ads_ctx* ctx, int iters, double* ms_out);
 ads_status ads_profile_saturation(ads_ctx* ctx, int steps, double* ms_out);
 

@@ -780,6 +780,11 @@ ads_status enq_galerkin(ads_ctx* c) {
 
 }  // namespace
 
+namespace adsgb {
+// the parameter check of ads_init, for entry points defined in other files
+ads_status validate_params(const ads_params* p, const crvpinn_params* cp) { return validate(p, cp); }
+}  // namespace adsgb
+
 // =============================================================================
 // exported entry points
 // =============================================================================

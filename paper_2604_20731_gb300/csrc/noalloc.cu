@@ -11,10 +11,17 @@
 // that loads the library for as long as the library stays loaded.
 #include <cuda_runtime.h>
 
+#include <chrono>
+#include <cmath>
 #include <mutex>
+#include <thread>
 
 #include "../../include/adsgb.h"
 #include "kernels.cuh"
+
+namespace adsgb {
+ads_status validate_params(const ads_params* p, const crvpinn_params* cp);  // api.cu
+}
 
 using namespace adsgb;
 
@@ -50,15 +57,27 @@ struct SrcVals {
   double dt;
 };
 
-// writes the sources' centres/widths and the step size into the scratch and
-// clears the device status word
-__global__ void k_noalloc_put(SrcVals v, double* cen, double* sig, double* dt, int* flags) {
+// writes the sources' centres/widths and the step size into the scratch; the
+// status word is left alone, so a problem seen by any step stays visible until
+// ads_saturation_step_noalloc_status reads and clears it
+__global__ void k_noalloc_put(SrcVals v, double* cen, double* sig, double* dt) {
   int t = threadIdx.x;
   if (t < 3 * kMaxSrc) cen[t] = v.cen[t];
   if (t < kMaxSrc) sig[t] = v.sig[t];
-  if (t == 0) {
-    *dt = v.dt;
-    *flags = 0;
+  if (t == 0) *dt = v.dt;
+}
+
+// polls the stream until its work is done: cudaSuccess, or cudaErrorNotReady
+// once kWaitSeconds have passed, or the stream's error
+constexpr double kWaitSeconds = 10.0;
+cudaError_t wait_stream(cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e != cudaErrorNotReady) return e;
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kWaitSeconds)
+      return cudaErrorNotReady;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
 
@@ -82,13 +101,12 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
                                                   void* stream) {
   if (!p || !d_K || !d_S || !d_P || !d_S_out) return ADS_ERR_INVALID_ARG;
   if (d_S == d_S_out) return ADS_ERR_INVALID_ARG;
+  // the same parameter check as ads_init (no CUDA call), then this step's limits
+  const ads_status v0 = validate_params(p, nullptr);
+  if (v0 != ADS_OK) return v0;
   if (p->dim != 2 || p->ads_dtype != ADS_F64) return ADS_ERR_UNSUPPORTED;
-  if (p->n < 2 || p->n > kMaxN) return ADS_ERR_INVALID_ARG;
-  if (!(dt > 0) || !(p->phi > 0) || !(p->mu_g > 0) || !(p->mu_w > 0)) return ADS_ERR_INVALID_ARG;
-  if (p->n_src < 0 || p->n_src > ADS_MAX_SOURCES) return ADS_ERR_INVALID_ARG;
-  for (int s = 0; s < p->n_src; ++s)
-    if (!(p->src[s].sigma > 0) || (p->src[s].kind != 0 && p->src[s].kind != 1))
-      return ADS_ERR_INVALID_ARG;
+  if (p->n > kMaxN) return ADS_ERR_INVALID_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return ADS_ERR_INVALID_ARG;
   const int n = p->n, nb = n + 2;
   const int nquad = quad_blocks(2, n, kStripRows);
   const int nys = ysolve_blocks(2, n);
@@ -100,6 +118,9 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
   if (scratch_address(dev, &base) != cudaSuccess) return ADS_ERR_CUDA;
 
   Carve cv{static_cast<unsigned char*>(base)};
+  // the status word first, at a fixed place, so that the status call finds it
+  int* flags = reinterpret_cast<int*>(cv.take(1));
+  double* stats = cv.take(3);
   double* B = cv.take(9 * (size_t)n);
   double* dB = cv.take(9 * (size_t)n);
   double* l1 = cv.take((size_t)n + 4);
@@ -114,7 +135,6 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
   double* dtp = cv.take(1);
   double* Xs = cv.take(2 * (size_t)nquad * ldx);
   double* Xm = cv.take((size_t)nb * ldx);
-  int* flags = reinterpret_cast<int*>(cv.take(1));
   double* src_part = cv.take((size_t)nquad);
   double* mass_part = cv.take((size_t)nys);
   if (cv.off > kScratchBytes) return ADS_ERR_INVALID_ARG;  // cannot happen for n <= kMaxN
@@ -127,7 +147,7 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
     v.sig[s] = p->src[s].sigma;
   }
   v.dt = dt;
-  k_noalloc_put<<<1, 32, 0, st>>>(v, cen, sig, dtp, flags);
+  k_noalloc_put<<<1, 32, 0, st>>>(v, cen, sig, dtp);
   // every table, spill row and partial below is fully rewritten before it is
   // read, so nothing in the shared array has to start at zero
   if (launch_axis_init(n, cen, sig, p->n_src, B, dB, l1, l2, dinv, Iw, gsrc, gnode, tmp, st) !=
@@ -168,5 +188,30 @@ extern "C" ads_status ads_saturation_step_noalloc(const ads_params* p, const dou
   if (launch_ysweep<double>(a, kStripRows, Xm, Xs, ldx, d_S_out, mass_part, flags, st) !=
       cudaSuccess)
     return ADS_ERR_CUDA;
+  // int S_out from the y sweep's partials: sets bit 0 of the status word when
+  // it is not finite (the context path runs the same check)
+  if (launch_mass_finalize(mass_part, ysweep_blocks(n, sizeof(double)), nullptr, 0, 0, stats, flags,
+                           st) != cudaSuccess)
+    return ADS_ERR_CUDA;
+  return ADS_OK;
+}
+
+extern "C" ads_status ads_saturation_step_noalloc_status(void* stream, int* flags_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ADS_ERR_CUDA;
+  void* base = nullptr;
+  if (scratch_address(dev, &base) != cudaSuccess) return ADS_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  // wait for the stream's queued steps, with a deadline, before the read
+  // (a plain synchronise could block for ever behind a stuck kernel)
+  if (wait_stream(st) != cudaSuccess) return ADS_ERR_TIMEOUT;
+  int word = 0;
+  if (cudaMemcpyAsync(&word, base, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return ADS_ERR_CUDA;
+  if (cudaMemsetAsync(base, 0, sizeof(int), st) != cudaSuccess) return ADS_ERR_CUDA;
+  if (wait_stream(st) != cudaSuccess) return ADS_ERR_TIMEOUT;
+  if (flags_out) *flags_out = word;
+  if (word & 8) return ADS_ERR_TIMEOUT;
+  if (word & 1) return ADS_ERR_NONFINITE;
   return ADS_OK;
 }

@@ -329,7 +329,7 @@ import ctypes as C, json, math
 from paper_2604_20731_gb300 import _lib
 lib = _lib.load()
 skip = {"ads_init", "ads_init_with_allocator", "ads_hbm_estimate", "ads_status_str",
-        "ads_saturation_step_noalloc", "hybrid_step_batch"}
+        "ads_saturation_step_noalloc", "ads_saturation_step_noalloc_status", "hybrid_step_batch"}
 res = {}
 for name, (rt, args) in _lib.SIGNATURES.items():
     if name in skip or name.startswith("ads_server_") or not args or args[0] is not C.c_void_p:
@@ -364,7 +364,15 @@ def noalloc(mut, same=False, dt=1e-3):
     return lib.ads_saturation_step_noalloc(C.byref(p), a, None, a, a, dt, a if same else b, None)
 na = {"same_in_out": noalloc(lambda p: None, same=True), "dim3": noalloc(lambda p: setattr(p, "dim", 3)),
       "f32": noalloc(lambda p: setattr(p, "ads_dtype", 1)), "n513": noalloc(lambda p: setattr(p, "n", 513)),
-      "dt0": noalloc(lambda p: None, dt=0.0), "nsrc9": noalloc(lambda p: setattr(p, "n_src", 9))}
+      "dt0": noalloc(lambda p: None, dt=0.0), "dt_inf": noalloc(lambda p: None, dt=math.inf),
+      "nsrc9": noalloc(lambda p: setattr(p, "n_src", 9)), "n1": noalloc(lambda p: setattr(p, "n", 1)),
+      "grav_nan": noalloc(lambda p: setattr(p, "grav", math.nan)),
+      "grav_neg": noalloc(lambda p: setattr(p, "grav", -1.0)),
+      "grav_sign_nan": noalloc(lambda p: setattr(p, "grav_sign", math.nan)),
+      "rate_neg": noalloc(lambda p: setattr(p.src[0], "rate", -1.0)),
+      "rate_inf": noalloc(lambda p: setattr(p.src[0], "rate", math.inf)),
+      "sigma0": noalloc(lambda p: setattr(p.src[0], "sigma", 0.0)),
+      "kind2": noalloc(lambda p: setattr(p.src[0], "kind", 2))}
 na["null"] = lib.ads_saturation_step_noalloc(None, None, None, None, None, 1e-3, None, None)
 print(json.dumps({"ctx": res, "server": srv, "noalloc": na}))
 """
@@ -378,8 +386,11 @@ def test_null_handles_and_refused_arguments_before_any_cuda_call(lib):
     import json
     import subprocess
     import sys
+    # no GPU visible to the child: a check that slipped ends in a CUDA error
+    # (a status the test rejects), never in a kernel launch on fake pointers
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "-c", NULL_SWEEP], cwd=ROOT, capture_output=True, text=True,
-                         timeout=300)
+                         timeout=300, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     r = json.loads(out.stdout.strip().splitlines()[-1])
     ctx = r["ctx"]
@@ -390,4 +401,6 @@ def test_null_handles_and_refused_arguments_before_any_cuda_call(lib):
     assert all(v == 1 for v in r["server"].values()), r["server"]
     na = r["noalloc"]
     assert na["dim3"] == 7 and na["f32"] == 7
-    assert all(na[k] == 1 for k in ("same_in_out", "n513", "dt0", "nsrc9", "null")), na
+    refused = ("same_in_out", "n513", "dt0", "dt_inf", "nsrc9", "n1", "grav_nan", "grav_neg",
+               "grav_sign_nan", "rate_neg", "rate_inf", "sigma0", "kind2", "null")
+    assert all(na[k] == 1 for k in refused), na
