@@ -31,3 +31,15 @@ def test_network_flops_per_point():
     assert fwd == 24960
     assert bwd == 2 * (6 * 64 * 64 + 64 + 2 * 64)
     assert bench.mlp_flops_per_point(3, 128)[0] == 2 * (3 * 128 + 3 * 128 * 128 + 128)
+
+
+def test_oracle_workers_are_single_threaded_and_time_a_step():
+    """The CPU-baseline workers are spawned with one BLAS thread each and
+    return (non-network seconds, seconds per Adam iteration, threads)."""
+    from paper_2604_20731_gb300 import scenario as scn
+    jobs = [(scn.make_scenario(2, n, seed=1000 + n), 2, 4, 2, 1e-3, 64) for n in (8, 12)]
+    with bench._oracle_pool(2) as pool:
+        res = pool.map(bench._oracle_step, jobs, chunksize=1)
+    for t_sat, t_iter, threads in res:
+        assert t_sat > 0 and t_iter > 0
+        assert threads in (None, 1)
