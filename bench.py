@@ -33,7 +33,7 @@ METRIC = ("hybrid time steps/s (batched mixed-precision vs plain FP64) at stated
 UNIT = "steps/s"
 FP32_LANES_PER_SM = 128
 N_SM = 152
-MUFU_PER_SM_CLK = 16  # special-function results per SM per clock (ex2, rcp, ...)
+SM_MAX_MHZ = 2070.0
 
 
 def args_parse():
@@ -453,7 +453,26 @@ def large_configs(a, scn, HybridSolver, device):
     return out
 
 
-def saturation_roofline(n, scn, HybridSolver):
+QUAD_FLOP_PER_ELEMENT = 600      # sum-factorised quadrature of one element (3 x 3 Gauss points)
+QUAD_FP32_OPS_PER_ELEMENT = 513  # FP32 pipe operations of k_quad_xsweep_2d per element, counted in its source
+
+
+def unit_rates():
+    """Measured per-SM-per-clock rates of the special-function unit and the
+    FP32 pipe (ads_measure_unit_rates), or None if the probe failed."""
+    import ctypes as C
+    from paper_2604_20731_gb300 import _lib
+    lib = _lib.load()
+    out = (C.c_double * 11)()
+    if lib.ads_measure_unit_rates(out, 11) != 0:
+        return None
+    names = ["ex2", "rcp", "tanh_pair", "ffma", "ffma2"]
+    return {"per_sm_per_clock": {k: out[5 + i] for i, k in enumerate(names)},
+            "per_s_at_probe_clock": {k: out[i] for i, k in enumerate(names)},
+            "probe_sm_mhz": out[10]}
+
+
+def saturation_roofline(n, scn, HybridSolver, rates=None):
     """One 2D saturation sub-step (quadrature + x sweep, y sweep, mass
     bookkeeping) on an n^2 mesh, FP32 and FP64, timed per kernel with CUDA
     events (20 sub-steps after 2 untimed).  Algorithmic bytes: the quadrature
@@ -479,13 +498,33 @@ def saturation_roofline(n, scn, HybridSolver):
         quad_b = es * (2 * nb * nb + (n + 1) ** 2 + nb * nb + nsp * nb)
         ysw_b = es * (2 * nb * nb + nsp * nb)
         tot = sum(ms.values())
+        # the line sweep's algorithmic traffic: one read and one write of
+        # every DOF per axis (the x sweep's share is fused into the quadrature)
+        ysw_alg = 2 * es * nb * nb
         out[dt] = {"ms_per_substep": tot, "kernel_ms": ms,
                    "element_steps_per_s": n * n / (tot * 1e-3),
                    "quad_xsweep_gbs": quad_b / (ms["quad_xsweep"] * 1e-3) / 1e9,
-                   "ysweep_gbs": ysw_b / (ms["ysweep"] * 1e-3) / 1e9,
-                   "ysweep_frac_of_hbm": ysw_b / (ms["ysweep"] * 1e-3) / 1e9 / hbm,
+                   "ysweep_gbs_algorithmic": ysw_alg / (ms["ysweep"] * 1e-3) / 1e9,
+                   "ysweep_frac_of_hbm": ysw_alg / (ms["ysweep"] * 1e-3) / 1e9 / hbm,
+                   "ysweep_gbs_moved": ysw_b / (ms["ysweep"] * 1e-3) / 1e9,
+                   "ysweep_frac_of_hbm_moved": ysw_b / (ms["ysweep"] * 1e-3) / 1e9 / hbm,
                    "quad_xsweep_frac_of_hbm": quad_b / (ms["quad_xsweep"] * 1e-3) / 1e9 / hbm,
-                   "algorithmic_bytes": {"quad_xsweep": quad_b, "ysweep": ysw_b}}
+                   "bytes_per_substep": {"quad_xsweep_moved": quad_b, "ysweep_algorithmic": ysw_alg,
+                                         "ysweep_moved": ysw_b}}
+        if dt == "f32" and rates:
+            ffma = rates["per_sm_per_clock"]["ffma"]
+            peak_flop = 2.0 * ffma * N_SM * SM_MAX_MHZ * 1e6
+            peak_ops = ffma * N_SM * SM_MAX_MHZ * 1e6
+            tq = ms["quad_xsweep"] * 1e-3
+            out[dt]["quad_alu"] = {
+                "bound": "alu", "unit": "TFLOP/s",
+                "achieved": QUAD_FLOP_PER_ELEMENT * n * n / tq / 1e12, "peak": peak_flop / 1e12,
+                "frac": QUAD_FLOP_PER_ELEMENT * n * n / tq / peak_flop,
+                "flop_per_element": QUAD_FLOP_PER_ELEMENT,
+                "fp32_ops_per_element": QUAD_FP32_OPS_PER_ELEMENT,
+                "fp32_issue_frac": QUAD_FP32_OPS_PER_ELEMENT * n * n / tq / peak_ops,
+                "peak_note": f"measured FP32 fma rate {ffma:.1f} results/clock/SM x {N_SM} SMs x "
+                             f"{SM_MAX_MHZ:.0f} MHz x 2 flop"}
     out["note"] = ("the quadrature + x sweep is bound by FP32 (FP64) instruction issue, not by "
                    "HBM; the y sweep is the bandwidth-bound line solve")
     return out
@@ -503,9 +542,10 @@ def run_ours(a, world, rank, local):
     from paper_2604_20731_gb300 import scenario as scn
     from paper_2604_20731_gb300.solver import HybridSolver, Server
 
+    rates = unit_rates() if rank == 0 else None
     if a.only_saturation:
         if rank == 0:
-            print(json.dumps({"saturation": saturation_roofline(a.sat_n, scn, HybridSolver)}), flush=True)
+            print(json.dumps({"saturation": saturation_roofline(a.sat_n, scn, HybridSolver, rates)}), flush=True)
         return 0
     hp = HybridSolver.hybrid_params(n_sub=a.n_sub, dt=1.0, dt_policy=1, cfl=0.1, src_frac=0.05,
                                     adam_iters=a.adam_iters, lr=a.lr)
@@ -644,20 +684,24 @@ def run_ours(a, world, rank, local):
     flops_pt = {"mlp_fwd": fwd_f, "mlp_bwd": bwd_f}
     nbig = max(prof_by_n)
     roof = {"kernel": dom, "share_of_mix_kernel_time": tot[dom] / sum(tot.values())}
-    if dom == "mlp_fwd":
-        # the forward's binding unit is the special-function pipe: tanh takes one
-        # ex2 and one rcp for each of the 4 hidden layers' W units of a point
+    if dom == "mlp_fwd" and rates:
+        # the forward's binding unit is the special-function pipe: each of
+        # the 4 hidden layers' W units of a point takes one tanh = one ex2 +
+        # one rcp; the peak is the measured rate of that pair
         M = (nbig - 1) ** 2
         t = prof_by_n[nbig][dom] * 1e-3
-        ops = 2 * 4 * a.width * M
+        ops = 4 * a.width * M
         ach = ops / t / 1e12
-        pk = N_SM * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+        pair = rates["per_sm_per_clock"]["tanh_pair"]
+        pk = N_SM * pair * sm_mhz * 1e6 / 1e12
         fl = flops_pt[dom] * M
         tpk = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
         tr = traffic_record(dom + "_tc")
-        roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "T special-function ops/s",
+        roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "T tanh/s",
                      "frac": ach / pk, "traffic": tr["bytes_per_launch"] if tr else None,
-                     "peak_note": f"MUFU: {N_SM} SMs x {MUFU_PER_SM_CLK} results/clock x {sm_mhz:.0f} MHz",
+                     "peak_note": f"measured ex2 + rcp pair rate {pair:.2f}/clock/SM (ex2 "
+                                  f"{rates['per_sm_per_clock']['ex2']:.1f}, rcp {rates['per_sm_per_clock']['rcp']:.1f}) "
+                                  f"x {N_SM} SMs x {sm_mhz:.0f} MHz",
                      "algorithmic_ops_per_launch": ops, "avg_launch_ms": prof_by_n[nbig][dom],
                      "tensor_achieved_tflops": fl / t / 1e12, "tensor_frac_of_sustained_bf16": fl / t / 1e12 / tpk,
                      "workload": f"{nbig}^2 member of the mix"})
@@ -783,7 +827,7 @@ def run_ours(a, world, rank, local):
     # ---- (4d) saturation kernels on a mesh larger than L2 (FP32 and FP64) ----
     sat = None
     if rank == 0 and a.sat_n > 0:
-        sat = saturation_roofline(a.sat_n, scn, HybridSolver)
+        sat = saturation_roofline(a.sat_n, scn, HybridSolver, rates)
 
     # ---- (5) CPU baseline (rank 0, N=1 only): the oracle on the mix ----
     cpu = None
@@ -804,7 +848,7 @@ def run_ours(a, world, rank, local):
                "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2, "c1_plain_galerkin": c1,
                "c3_c5_w128": large,
                "saturation": sat,
-               "gpu_launches": launches, "clocks": clk, "kernel_ms_by_n": prof_by_n,
+               "gpu_launches": launches, "clocks": clk, "kernel_ms_by_n": prof_by_n, "unit_rates": rates,
                "server": server_stats}
         print(json.dumps(out), flush=True)
     return 0

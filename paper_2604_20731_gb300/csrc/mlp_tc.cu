@@ -305,57 +305,168 @@ ADS_D void dw_layer_out(uint32_t lane_col, bool live, float bias_o, float* S, fl
   __syncthreads();
 }
 
+// Forward operands.  The hidden weights are staged as BF16 tiles of
+// s W_l and the bias s b_l (s = -2 log2 e) in one more K block of 16 columns
+// (column W: bf16(s b), column W + 1: bf16(s b - bf16(s b)), the rest 0),
+// and the activation hi tile carries the matching columns [1, 1, 0, ...].  A
+// layer's products then leave z' = s (W_l a + b_l) in TMEM, and tanh z =
+// 2 / (1 + 2^z') - 1 needs neither a bias add nor a multiply.
+constexpr float kTanhScale = -2.8853900817779268f;  // -2 log2(e)
+
 template <int W>
 struct TcSmemF {
+  static constexpr int NS = W == 64 ? 2 : 1;           // tiles in flight per CTA
+  static constexpr int KC = W + 16;                    // K of the hi operands
+  static constexpr int ACT_SZ = kTP * KC * 2;          // [128][KC] bf16 hi | 1 1 0 ...
+  static constexpr int ACTLO_SZ = kTP * W * 2;         // [128][W] bf16 lo
   // byte offsets
-  static constexpr int WT = 0;                         // 3 x [W][W] bf16
-  static constexpr int ACT = WT + 3 * W * W * 2;       // [128][W] bf16 hi
-  static constexpr int ACTLO = ACT + kTP * W * 2;      // [128][W] bf16 lo
-  static constexpr int BIAS = ACTLO + kTP * W * 2;     // fp32: b1 b2 b3 b4 [4][W], W1 [W][3], W5 [W], b5
-  static constexpr int NBIAS = 4 * W + 3 * W + W + 4;
-  static constexpr int BAR = BIAS + NBIAS * 4;         // mbarrier (8 B), tmem base (4 B), abort flag (4 B)
-  static constexpr int UPART = BAR + 32;               // fp32 [128]: output-layer sums of the second half
-  static constexpr int TOTAL = UPART + kTP * 4;
+  static constexpr int WT = 0;                         // 3 x [W][KC] bf16: s W_l | s b_l
+  static constexpr int ACT = WT + 3 * W * KC * 2;      // NS hi tiles
+  static constexpr int ACTLO = ACT + NS * ACT_SZ;      // NS lo tiles
+  static constexpr int VEC = ACTLO + NS * ACTLO_SZ;    // fp32: s b_1 [W], s W_1 [3][W], W_5 [W], b_5
+  static constexpr int NVEC = W + 3 * W + W + 4;
+  static constexpr int BAR = VEC + NVEC * 4;           // NS mbarriers (8 B each), tmem base, abort flag
+  static constexpr int UPART = BAR + 32;               // fp32 [NS][128]: output-layer sums of the second half
+  static constexpr int TOTAL = UPART + NS * kTP * 4;
 };
 
+// the three hidden layers as above: atoms e = tid + i NTHR, each thread
+// issuing a batch of loads before its stores (one memory latency per batch)
+template <int W, int NTHR>
+ADS_D void load_fwd_weights(const float* __restrict__ th, int o2, unsigned char* wt, int tid) {
+  constexpr int KC = W + 16, RG = (KC / 8) * 128, APR = KC / 8, NA = 3 * W * APR;
+  constexpr int PER = (NA + NTHR - 1) / NTHR, B = 6;
+#pragma unroll
+  for (int i0 = 0; i0 < PER; i0 += B) {
+    float4 q[B][2];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int e = tid + (i0 + i) * NTHR;
+      q[i][0] = q[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + i < PER && e < NA) {
+        const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
+        const float* Wl = th + o2 + l * (W * W + W);
+        if (c < W) {
+          const float4* src = reinterpret_cast<const float4*>(Wl + o * W + c);
+          q[i][0] = __ldg(src);
+          q[i][1] = __ldg(src + 1);
+        } else if (c == W) {
+          q[i][0].x = __ldg(Wl + W * W + o);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int e = tid + (i0 + i) * NTHR;
+      if (i0 + i < PER && e < NA) {
+        const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
+        float v[8] = {q[i][0].x, q[i][0].y, q[i][0].z, q[i][0].w, q[i][1].x, q[i][1].y, q[i][1].z, q[i][1].w};
+        if (c == W) {
+          const float sb = kTanhScale * v[0];
+          const float hi = __bfloat162float(__float2bfloat16_rn(sb));
+          v[0] = sb;       // rounds to hi in st_atom
+          v[1] = sb - hi;  // the remainder, rounded there too
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] *= kTanhScale;
+        }
+        st_atom(wt + l * W * KC * 2, RG, o, c, v);
+      }
+    }
+  }
+}
+
+ADS_D float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+ADS_D float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// tanh of two pre-activations given as z' = -2 log2(e) z: 2 / (1 + 2^z') - 1,
+// the FP32 steps on packed pairs (one instruction per pair)
+ADS_D float2 tanh2_scaled(float2 zs) {
+  const float2 t = make_float2(ex2_approx(zs.x), ex2_approx(zs.y));
+  const float2 d = __fadd2_rn(t, make_float2(1.0f, 1.0f));
+  const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  return __ffma2_rn(r, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f));
+}
+// 8 values (one atom) as a BF16 pair hi + lo, to tiles of row-group strides
+// rgh and rgl, and the hi half also to `g` (nullable); the remainder v - hi
+// is formed on packed pairs
+ADS_D void st_atom_split2(unsigned char* hi, int rgh, unsigned char* lo, int rgl, unsigned char* g, int grg,
+                          int r, int c, const float v[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    const uint32_t hb = *reinterpret_cast<uint32_t*>(&b);
+    const float2 bf = make_float2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u));
+    const float2 rem = __ffma2_rn(bf, make_float2(-1.0f, -1.0f), make_float2(v[2 * j], v[2 * j + 1]));
+    __nv_bfloat162 lb = __floats2bfloat162_rn(rem.x, rem.y);
+    h[j] = hb;
+    l[j] = *reinterpret_cast<uint32_t*>(&lb);
+  }
+  const uint4 qh = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(hi + core_off(r, c, rgh)) = qh;
+  *reinterpret_cast<uint4*>(lo + core_off(r, c, rgl)) = make_uint4(l[0], l[1], l[2], l[3]);
+  if (g) *reinterpret_cast<uint4*>(g + core_off(r, c, grg)) = qh;
+}
+
 // forward: two threads per point row, each taking half of the feature columns
-// (eight warps: warps w and w + 4 read the same TMEM lanes)
+// (eight warps: warps w and w + 4 read the same TMEM lanes).  For W = 64 a
+// CTA carries two tiles at once (slots 0 and 1, each with its own operand
+// tiles, TMEM accumulator and mbarrier): a slot's products run while the
+// threads work on the other slot's epilogue.
 constexpr int kFwdThreads = 2 * kTP;
 
 template <int W, int DIN>
-__global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(MlpTcArgs a) {
+  using L = TcSmemF<W>;
+  constexpr int NS = L::NS;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* wt = sm + TcSmemF<W>::WT;
-  unsigned char* act = sm + TcSmemF<W>::ACT;
-  unsigned char* actlo = sm + TcSmemF<W>::ACTLO;
-  float* fb = reinterpret_cast<float*>(sm + TcSmemF<W>::BIAS);
-  float* fW1 = fb + 4 * W;
+  unsigned char* wt = sm + L::WT;
+  unsigned char* act = sm + L::ACT;
+  unsigned char* actlo = sm + L::ACTLO;
+  float* fb1 = reinterpret_cast<float*>(sm + L::VEC);  // s b_1
+  float* fW1 = fb1 + W;                                // s W_1, [DIN][W]
   float* fW5 = fW1 + 3 * W;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmemF<W>::BAR);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + TcSmemF<W>::BAR + 8);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + TcSmemF<W>::BAR + 12);
-  float* upart = reinterpret_cast<float*>(sm + TcSmemF<W>::UPART);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::BAR);  // [NS]
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + L::BAR + 16);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + L::BAR + 20);
+  float* upart = reinterpret_cast<float*>(sm + L::UPART);
   const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTP - 1), half = tid / kTP;
-  constexpr int RG = (W / 8) * 128, WH = W / 2;
+  constexpr int KC = L::KC, RGH = (KC / 8) * 128, RGL = (W / 8) * 128, WH = W / 2;
   const int cb = half * WH;  // this thread's first feature column
   const float* th = a.theta;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
-  load_hidden_weights<W, kFwdThreads>(th, o2, wt, tid);
+  load_fwd_weights<W, kFwdThreads>(th, o2, wt, tid);
   for (int i = tid; i < W; i += kFwdThreads) {
-    fb[i] = th[ob1 + i];
-    for (int l = 0; l < 3; ++l) fb[(l + 1) * W + i] = th[o2 + l * (W * W + W) + W * W + i];
-    for (int d = 0; d < DIN; ++d) fW1[i * 3 + d] = th[i * DIN + d];
+    fb1[i] = kTanhScale * th[ob1 + i];
+    for (int d = 0; d < DIN; ++d) fW1[d * W + i] = kTanhScale * th[i * DIN + d];
     fW5[i] = th[o5 + i];
+  }
+  if (tid < kTP) {
+    // the constant columns of the hi operands: [1, 1, 0, ..., 0] (bias hi, lo)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      unsigned char* ah = act + s * L::ACT_SZ;
+      *reinterpret_cast<uint4*>(ah + core_off(tid, W, RGH)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(ah + core_off(tid, W + 8, RGH)) = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   if (tid == 0) {
     fW5[W] = th[o5 + W];
     *abort_flag = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    for (int s = 0; s < NS; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + s)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(tbase)), "r"(W));
+                     smem_addr(tbase)), "r"(NS * W));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_async_smem();
@@ -366,91 +477,144 @@ __global__ void __launch_bounds__(kFwdThreads, 3) k_mlp_fwd_tc(MlpTcArgs a) {
   const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   const uint32_t idesc = idesc_bf16(kTP, W, 0, 0);
   const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(wt);
-  uint32_t phase = 0;
+  uint32_t phase[NS];
+  bool pend[NS];  // products issued and not yet waited for (CTA-uniform)
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    phase[s] = 0;
+    pend[s] = false;
+  }
   bool aborted = false;
   const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
   const float b5 = fW5[W];
-  for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
-    const int p0 = (a.tile0 + tile) * kTP;
-    const int idx = min(p0 + row, a.npts - 1);
-    float x[3];
-    coords<DIN>(idx, a.N, x);
-    unsigned char* gtile = a.acts ? a.acts + (size_t)tile * act_tile_bytes(W) : nullptr;
-    if (gtile && act_cols(W, 0) > W) {
-      // the constant columns [1, 0, ..., 0] of the stored a_1 .. a_3
-      const uint4 q = half == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+  // [a_hi | 1 1] [s W | s b_hi s b_lo]^T + a_lo (s W)^T for slot s, layer l:
+  // two BF16 chains into the slot's FP32 accumulator (one thread)
+  auto issue = [&](int s, int l) {
+    const uint32_t wl = wt_s + l * W * KC * 2, d = tmem + s * W;
+    const uint32_t ah = act_s + s * L::ACT_SZ, al = actlo_s + s * L::ACTLO_SZ;
 #pragma unroll
-      for (int l = 0; l < 3; ++l)
-        *reinterpret_cast<uint4*>(gtile + act_off(W, l) + core_off(row, W + 8 * half, act_rg(W, l))) = q;
-    }
-    // layer 1 on the CUDA cores
+    for (int ks = 0; ks < KC / 16; ++ks) mma_bf16(d, desc_k(ah, RGH, ks), desc_k(wl, RGH, ks), idesc, ks > 0);
 #pragma unroll
-    for (int c = 0; c < WH; c += 8) {
-      float v[8];
+    for (int ks = 0; ks < W / 16; ++ks) mma_bf16(d, desc_k(al, RGL, ks), desc_k(wl, RGH, ks), idesc, 1u);
+    mma_commit(mbar + s);
+  };
+  for (int tb = blockIdx.x; tb < ntiles && !aborted; tb += NS * gridDim.x) {
+    int p0[NS];
+    bool valid[NS];
+    unsigned char* gt[NS];
+    float2 u2[NS];
+    // layer 1 of each slot on the CUDA cores, z' = s (W_1 x' + b_1) on pairs
+    // of units, then the slot's first products
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int o = cb + c + j;
-        float z = fb[o];
+    for (int s = 0; s < NS; ++s) {
+      const int tile = tb + s * gridDim.x;
+      valid[s] = tile < ntiles;  // CTA-uniform
+      p0[s] = (a.tile0 + tile) * kTP;
+      gt[s] = nullptr;
+      u2[s] = make_float2(half == 0 ? b5 : 0.0f, 0.0f);
+      if (!valid[s]) continue;
+      float x[3];
+      coords<DIN>(min(p0[s] + row, a.npts - 1), a.N, x);
+      gt[s] = a.acts ? a.acts + (size_t)tile * act_tile_bytes(W) : nullptr;
+      if (gt[s] && act_cols(W, 0) > W) {
+        // the constant columns [1, 0, ..., 0] of the stored a_1 .. a_3
+        const uint4 q = half == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int d = 0; d < DIN; ++d) z += fW1[o * 3 + d] * x[d];
-        v[j] = tanh_f32(z);
+        for (int l = 0; l < 3; ++l)
+          *reinterpret_cast<uint4*>(gt[s] + act_off(W, l) + core_off(row, W + 8 * half, act_rg(W, l))) = q;
       }
-      st_atom_split_g(act, actlo, gtile, RG, act_rg(W, 0), row, cb + c, v);
-    }
-    float u = half == 0 ? b5 : 0.0f;
-    for (int l = 0; l < 3; ++l) {
+      unsigned char* ah = act + s * L::ACT_SZ;
+      unsigned char* al = actlo + s * L::ACTLO_SZ;
+#pragma unroll
+      for (int c = 0; c < WH; c += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const int o = cb + c + j;
+          float2 z = *reinterpret_cast<const float2*>(fb1 + o);
+#pragma unroll
+          for (int d = 0; d < DIN; ++d)
+            z = __ffma2_rn(*reinterpret_cast<const float2*>(fW1 + d * W + o), make_float2(x[d], x[d]), z);
+          const float2 t = tanh2_scaled(z);
+          v[j] = t.x;
+          v[j + 1] = t.y;
+        }
+        st_atom_split2(ah, RGH, al, RGL, gt[s], act_rg(W, 0), row, cb + c, v);
+      }
       if (sync_abort(abort_flag)) {
         aborted = true;
         break;
       }
-      if (tid == 0) {
-        // (a_hi + a_lo) W: two BF16 products into one FP32 accumulator
+      if (tid == 0) issue(s, 0);
+      pend[s] = true;
+    }
+    // hidden layers 2..4: per slot, wait for its products, the epilogue, and
+    // (layers 2, 3) the products of its next layer
+    for (int l = 0; l < 3 && !aborted; ++l) {
 #pragma unroll
-        for (int ks = 0; ks < W / 16; ++ks)
-          mma_bf16(tmem, desc_k(act_s, RG, ks), desc_k(wt_s + l * W * W * 2, RG, ks), idesc,
-                   ks > 0);
+      for (int s = 0; s < NS; ++s) {
+        if (!valid[s]) continue;
+        if (!mbar_wait(mbar + s, phase[s])) *abort_flag = 1;
+        phase[s] ^= 1;
+        pend[s] = false;
+        tc_fence_after();
+        unsigned char* ah = act + s * L::ACT_SZ;
+        unsigned char* al = actlo + s * L::ACTLO_SZ;
+        unsigned char* g = gt[s] ? gt[s] + act_off(W, l + 1) : nullptr;
+        const int grg = act_rg(W, l + 1);
 #pragma unroll
-        for (int ks = 0; ks < W / 16; ++ks)
-          mma_bf16(tmem, desc_k(actlo_s, RG, ks), desc_k(wt_s + l * W * W * 2, RG, ks), idesc, 1u);
-        mma_commit(mbar);
-      }
-      if (!mbar_wait(mbar, phase)) *abort_flag = 1;
-      phase ^= 1;
-      tc_fence_after();
-      const float* bl = fb + (l + 1) * W + cb;
-      unsigned char* g = gtile ? gtile + act_off(W, l + 1) : nullptr;
-      const int grg = act_rg(W, l + 1);
+        for (int c0 = 0; c0 < WH; c0 += 32) {
+          float d[32];
+          tmem_ld32(lane_base + s * W + cb + c0, d);
 #pragma unroll
-      for (int c0 = 0; c0 < WH; c0 += 32) {
-        float d[32];
-        tmem_ld32(lane_base + cb + c0, d);
+          for (int c = 0; c < 32; c += 8) {
+            float v[8];
 #pragma unroll
-        for (int c = 0; c < 32; c += 16) {
-          float v[16];
+            for (int j = 0; j < 8; j += 2) {
+              const float2 t = tanh2_scaled(make_float2(d[c + j], d[c + j + 1]));
+              v[j] = t.x;
+              v[j + 1] = t.y;
+            }
+            if (l < 2) {
+              st_atom_split2(ah, RGH, al, RGL, g, grg, row, cb + c0 + c, v);
+            } else {
+              if (g) st_atom(g, grg, row, cb + c0 + c, v);
+              // the output layer in FP32 from the unrounded activations
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = tanh_f32(d[c + j] + bl[c0 + c + j]);
-          if (l < 2) {
-            st_atom_split_g(act, actlo, g, RG, grg, row, cb + c0 + c, v);
-            st_atom_split_g(act, actlo, g, RG, grg, row, cb + c0 + c + 8, v + 8);
-          } else if (g) {
-            st_atom(g, grg, row, cb + c0 + c, v);
-            st_atom(g, grg, row, cb + c0 + c + 8, v + 8);
+              for (int j = 0; j < 8; j += 2)
+                u2[s] = __ffma2_rn(make_float2(v[j], v[j + 1]),
+                                   *reinterpret_cast<const float2*>(fW5 + cb + c0 + c + j), u2[s]);
+            }
           }
-          if (l == 2) {
-            // the output layer in FP32 from the unrounded activations
-#pragma unroll
-            for (int j = 0; j < 16; ++j) u += fW5[cb + c0 + c + j] * v[j];
+        }
+        if (l < 2) {
+          if (sync_abort(abort_flag)) {
+            aborted = true;
+            break;
           }
+          if (tid == 0) issue(s, l + 1);
+          pend[s] = true;
         }
       }
     }
-    // the two halves of the output-layer sum
-    if (half) upart[row] = u;
+    // the two halves of each slot's output-layer sums
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (half) upart[s * kTP + row] = u2[s].x + u2[s].y;
     __syncthreads();
-    if (!half && !aborted && p0 + row < a.npts) a.u[p0 + row] = u + upart[row];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (!half && valid[s] && !aborted && p0[s] + row < a.npts)
+        a.u[p0[s] + row] = u2[s].x + u2[s].y + upart[s * kTP + row];
   }
+  // after an abort, products still in flight finish (bounded wait) before
+  // their accumulator is freed
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    if (pend[s]) mbar_wait(mbar + s, phase[s]);
   if (sync_abort(abort_flag) && tid == 0) atomicOr(a.flags, 8);
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(W));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NS * W));
 }
 
 // ---------------------------------------------------------------------------
@@ -1131,7 +1295,7 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   const size_t smem = TcSmemF<W>::TOTAL;
   auto k = k_mlp_fwd_tc<W, DIN>;
   smem_optin(k);
-  const int occ = tc_residency(k, smem, W, kFwdThreads);
+  const int occ = tc_residency(k, smem, TcSmemF<W>::NS * W, kFwdThreads);
   const int ntiles = a.tile_count;
   if (ntiles <= 0) return cudaSuccess;
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();

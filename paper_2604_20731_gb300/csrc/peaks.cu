@@ -41,8 +41,10 @@ __global__ void __launch_bounds__(kThreads) k_unit_rate(float* sink, int iters, 
         x[c] = t;
       } else if (OP == kRcp) {
         float t;
-        asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(x[c]));  // x, 1/x, x, ...
-        x[c] = t;
+        // x <- 1/x + 1/2 (converges to about 1.21); the add keeps the two
+        // reciprocals of a pair from folding into the identity
+        asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(x[c]));
+        x[c] = t + 0.5f;
       } else if (OP == kTanh) {
         float t, r;
         asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(-x[c]));

@@ -350,6 +350,54 @@ def test_loss_and_gradient_bf16_tensor_cores(n):
     s.close()
 
 
+def _bf16_rn(x):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _tc_effective_theta(theta, din, w):
+    """The parameters the tensor-core forward evaluates: the hidden layers'
+    weights as bf16(s W) / s and their biases as (bf16(s b) + bf16(s b -
+    bf16(s b))) / s, with s = -2 log2 e in FP32 (the kernels fold s into the
+    staged operands); the first and the output layer stay in FP32."""
+    s32 = np.float32(-2.8853900817779268)
+    th = np.asarray(theta, dtype=np.float64).copy()
+    sizes = [din, w, w, w, w, 1]
+    o = 0
+    for l in range(5):
+        fi, fo = sizes[l], sizes[l + 1]
+        Wl = th[o:o + fo * fi]
+        bl = th[o + fo * fi:o + fo * fi + fo]
+        if 1 <= l <= 3:
+            sw = np.float32(Wl.astype(np.float32) * s32)
+            th[o:o + fo * fi] = _bf16_rn(sw).astype(np.float64) / float(s32)
+            sb = np.float32(bl.astype(np.float32) * s32)
+            hi = _bf16_rn(sb)
+            lo = _bf16_rn(np.float32(sb - hi))
+            th[o + fo * fi:o + fo * fi + fo] = (hi.astype(np.float64) + lo.astype(np.float64)) / float(s32)
+        o += fo * fi + fo
+    return th
+
+
+@pytest.mark.parametrize("n,width", [(33, 64), (256, 64), (70, 128)])
+def test_bf16_forward_on_its_effective_weights(n, width):
+    """The tensor-core forward against the FP64 network on the weights it
+    actually multiplies (BF16-rounded, see _tc_effective_theta).  What is left
+    is the forward's own arithmetic: hidden activations carried as BF16
+    hi + lo (about 2^-17 relative each), FP32 accumulation and the ex2/rcp
+    tanh (about 2^-21).  A wrong bias, scale, column or layer shows up as an
+    error of order 1e-2 or more."""
+    sc, s, crv, theta, alpha, f = _crv_case(n, "bf16", width=width)
+    s.loss_grad()
+    u_ref, _ = MLP(2, width, 4).forward(_tc_effective_theta(theta, 2, width), crv.X)
+    err = np.abs(s.get("U") - u_ref).max() / max(1.0, np.abs(u_ref).max())
+    print(f"BF16 forward vs the FP64 network on its effective weights, n={n}, W={width}: {err:.2e}")
+    assert err <= 2e-4
+    s.close()
+
+
 def test_bf16_training_converges_to_direct_solution():
     n = 64
     sc = scn.make_scenario(2, n, seed=1000)
