@@ -62,7 +62,8 @@ struct ads_ctx {
   void *alpha = nullptr, *f = nullptr, *u = nullptr, *res = nullptr, *rhat = nullptr, *z = nullptr,
        *gu = nullptr, *Sdst = nullptr, *invd = nullptr, *gtw = nullptr, *glam = nullptr,
        *theta = nullptr, *am = nullptr,
-       *av = nullptr, *grad = nullptr, *gpart = nullptr, *acts = nullptr;
+       *av = nullptr, *grad = nullptr, *gpart = nullptr, *acts = nullptr,
+       *fwimg = nullptr;  // tensor-core forward: weight image
   double *dot_part = nullptr, *loss = nullptr, *loss_log = nullptr, *bc = nullptr, *lr = nullptr;
   int* t = nullptr;
   int ndot = 0, nbwd = 0, ld = 0;
@@ -294,6 +295,7 @@ MlpTcArgs mlp_tc_args(ads_ctx* c, bool store) {
   a.theta = (const float*)c->theta;
   a.u = (float*)c->u;
   a.acts = store ? (unsigned char*)c->acts : nullptr;
+  a.wimage = (unsigned char*)c->fwimg;
   a.gu = (const float*)c->gu;
   a.gpart = (float*)c->gpart;
   a.nparams = c->nparams;
@@ -363,6 +365,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   const int m = c->m1;
   const TC h = TC(1.0 / c->N);
   LK(0, launch_fwd<TC>(c, !(c->use_tc && c->chunks > 1)));
+  if (c->use_tc) c->nlaunch += kMlpTcFwdLaunches - 1;
   if (c->dim == 2 && c->gram_fft) {
     // the residual is computed inside the first transform pass
     if (c->prof) cudaEventRecord(c->prof[1], c->stream);
@@ -422,7 +425,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
       CK(launch_mlp_fwd_tc(ka, c->stream));
       ka.gpart = (float*)c->gpart + (size_t)k * c->nbwd * c->nparams;
       CK(launch_mlp_bwd_tc(ka, c->nbwd, c->stream));
-      c->nlaunch += 2;
+      c->nlaunch += kMlpTcFwdLaunches + 1;
     }
     if (c->prof) cudaEventRecord(c->prof[7], c->stream);
   } else {
@@ -447,7 +450,7 @@ ads_status enq_project(ads_ctx* c) {
     CK(launch_ysweep<TA>(a, c->re, (const TA*)c->Xm, (const TA*)c->Xs, c->ldx, (TA*)c->P,
                          c->mass_part, c->flags, c->stream));
   }
-  c->nlaunch += 4;
+  c->nlaunch += 4 + (c->use_tc ? kMlpTcFwdLaunches - 1 : 0);
   return ADS_OK;
 }
 
@@ -677,7 +680,7 @@ size_t estimate(const ads_params* p, const crvpinn_params* cp) {
       int k = cp->act_chunks > 0 ? cp->act_chunks : 1;  // (automatic: estimated as all stored)
       if (k > tiles) k = tiles;
       const int ct = (tiles + k - 1) / k;
-      acts = mlp_tc_acts_bytes(ct * 128, (int)w);
+      acts = mlp_tc_acts_bytes(ct * 128, (int)w) + mlp_tc_fwd_image_bytes((int)w);
     }
     b += tc * (nn + 6 * M + m * m + 5 * np + 2 * 152 * np) + acts;
     b += 8 * (m * m + (d == 3 ? m * m * m : m * m) + kLossRing + 4096);
@@ -1044,6 +1047,7 @@ ads_status ads_init_with_allocator(const ads_params* params, const crvpinn_param
     ALV(c->gpart, tc * (size_t)c->chunks * c->nbwd * c->nparams);
     if (c->use_tc) {
       ALV(c->acts, mlp_tc_acts_bytes(bwd_points(c), crv->width));
+      ALV(c->fwimg, mlp_tc_fwd_image_bytes(crv->width));
     } else {
       ALV(c->acts, tc * 4 * (size_t)crv->width * c->ld);
     }

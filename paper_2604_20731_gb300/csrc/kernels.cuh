@@ -186,6 +186,8 @@ struct MlpTcArgs {
   const float* theta;     // FP32 master parameters
   float* u;               // [npts]
   unsigned char* acts;    // BF16 activations, [tile][4][128 x width] core-matrix tiles (nullable)
+  unsigned char* wimage;  // forward: weight image, mlp_tc_fwd_image_bytes(width), 16-byte aligned;
+                          // rewritten from theta by every forward launch
   const float* gu;        // [npts] dL/du
   float* gpart;           // [nblk][nparams]
   int nparams;
@@ -219,7 +221,10 @@ cudaError_t launch_gram_cluster(const GramClusterShape& sh, int N, const float* 
                                 const float* f, float h2, float* res_out, float* z, const float* tw,
                                 const float* lam, double* dot_part, cudaStream_t st);
 
+// the forward is two launches: the weight image from theta, then the network
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a, cudaStream_t st);
+constexpr int kMlpTcFwdLaunches = 2;
+size_t mlp_tc_fwd_image_bytes(int width);
 cudaError_t launch_mlp_bwd_tc(const MlpTcArgs& a, int nblk, cudaStream_t st);
 size_t mlp_tc_acts_bytes(int npts, int width);
 // backward CTAs (= gradient partial rows): one per SM at most, and at least

@@ -319,61 +319,80 @@ struct TcSmemF {
   static constexpr int KC = W + 16;                    // K of the hi operands
   static constexpr int ACT_SZ = kTP * KC * 2;          // [128][KC] bf16 hi | 1 1 0 ...
   static constexpr int ACTLO_SZ = kTP * W * 2;         // [128][W] bf16 lo
-  // byte offsets
-  static constexpr int WT = 0;                         // 3 x [W][KC] bf16: s W_l | s b_l
-  static constexpr int ACT = WT + 3 * W * KC * 2;      // NS hi tiles
+  static constexpr int NVEC = W + 3 * W + W + 4;       // fp32: s b_1 [W], s W_1 [3][W], W_5 [W], b_5
+  // byte offsets.  [VEC | WT] is the weight image, staged in global memory by
+  // k_stage_fwd and brought in by two bulk copies.
+  static constexpr int VEC = 0;
+  static constexpr int VEC_SZ = (NVEC * 4 + 127) / 128 * 128;
+  static constexpr int WT = VEC + VEC_SZ;              // 3 x [W][KC] bf16: s W_l | s b_l
+  static constexpr int WT_SZ = 3 * W * KC * 2;
+  static constexpr int IMG = WT + WT_SZ;               // bytes of the image
+  static constexpr int ACT = IMG;                      // NS hi tiles
   static constexpr int ACTLO = ACT + NS * ACT_SZ;      // NS lo tiles
-  static constexpr int VEC = ACTLO + NS * ACTLO_SZ;    // fp32: s b_1 [W], s W_1 [3][W], W_5 [W], b_5
-  static constexpr int NVEC = W + 3 * W + W + 4;
-  static constexpr int BAR = VEC + NVEC * 4;           // NS mbarriers (8 B each), tmem base, abort flag
-  static constexpr int UPART = BAR + 32;               // fp32 [NS][128]: output-layer sums of the second half
-  static constexpr int TOTAL = UPART + NS * kTP * 4;
+  static constexpr int BAR = ACTLO + NS * ACTLO_SZ;    // mbarriers: vec, wt, ready[NS], prod[NS]; tmem base; abort
+  static constexpr int UPART = BAR + 64;               // fp32 [2][NS][128]: output-layer sums of the second half
+  static constexpr int TOTAL = UPART + 2 * NS * kTP * 4;
 };
 
-// the three hidden layers as above: atoms e = tid + i NTHR, each thread
-// issuing a batch of loads before its stores (one memory latency per batch)
-template <int W, int NTHR>
-ADS_D void load_fwd_weights(const float* __restrict__ th, int o2, unsigned char* wt, int tid) {
-  constexpr int KC = W + 16, RG = (KC / 8) * 128, APR = KC / 8, NA = 3 * W * APR;
-  constexpr int PER = (NA + NTHR - 1) / NTHR, B = 6;
+// The weight image of the forward, from the FP32 master parameters: the
+// constant vectors (FP32) and the three hidden layers as BF16 K-major tiles
+// (one 16-byte atom of 8 values per thread)
+template <int W, int DIN>
+__global__ void __launch_bounds__(256) k_stage_fwd(const float* __restrict__ th, unsigned char* __restrict__ img) {
+  using L = TcSmemF<W>;
+  constexpr int KC = L::KC, RG = (KC / 8) * 128, APR = KC / 8, NA = 3 * W * APR, NV = L::VEC_SZ / 4;
+  const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e < NA) {
+    const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
+    const float* Wl = th + o2 + l * (W * W + W);
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (c < W) {
+      const float4* src = reinterpret_cast<const float4*>(Wl + o * W + c);
+      const float4 q0 = __ldg(src), q1 = __ldg(src + 1);
+      const float q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-  for (int i0 = 0; i0 < PER; i0 += B) {
-    float4 q[B][2];
-#pragma unroll
-    for (int i = 0; i < B; ++i) {
-      const int e = tid + (i0 + i) * NTHR;
-      q[i][0] = q[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i0 + i < PER && e < NA) {
-        const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
-        const float* Wl = th + o2 + l * (W * W + W);
-        if (c < W) {
-          const float4* src = reinterpret_cast<const float4*>(Wl + o * W + c);
-          q[i][0] = __ldg(src);
-          q[i][1] = __ldg(src + 1);
-        } else if (c == W) {
-          q[i][0].x = __ldg(Wl + W * W + o);
-        }
-      }
+      for (int j = 0; j < 8; ++j) v[j] = kTanhScale * q[j];
+    } else if (c == W) {
+      const float sb = kTanhScale * __ldg(Wl + W * W + o);
+      v[0] = sb;                                              // rounds to bf16(s b) in st_atom
+      v[1] = sb - __bfloat162float(__float2bfloat16_rn(sb));  // the remainder, rounded there too
     }
-#pragma unroll
-    for (int i = 0; i < B; ++i) {
-      const int e = tid + (i0 + i) * NTHR;
-      if (i0 + i < PER && e < NA) {
-        const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
-        float v[8] = {q[i][0].x, q[i][0].y, q[i][0].z, q[i][0].w, q[i][1].x, q[i][1].y, q[i][1].z, q[i][1].w};
-        if (c == W) {
-          const float sb = kTanhScale * v[0];
-          const float hi = __bfloat162float(__float2bfloat16_rn(sb));
-          v[0] = sb;       // rounds to hi in st_atom
-          v[1] = sb - hi;  // the remainder, rounded there too
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] *= kTanhScale;
-        }
-        st_atom(wt + l * W * KC * 2, RG, o, c, v);
-      }
+    st_atom(img + L::WT + l * W * KC * 2, RG, o, c, v);
+  } else if (e < NA + NV) {
+    const int i = e - NA;
+    float val = 0.0f;
+    if (i < W) {
+      val = kTanhScale * th[ob1 + i];
+    } else if (i < 4 * W) {
+      const int d = (i - W) / W, o = (i - W) % W;
+      val = d < DIN ? kTanhScale * th[o * DIN + d] : 0.0f;
+    } else if (i < 5 * W) {
+      val = th[o5 + i - 4 * W];
+    } else if (i == 5 * W) {
+      val = th[o5 + W];
     }
+    reinterpret_cast<float*>(img + L::VEC)[i] = val;
   }
+}
+
+ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+ADS_D void mbar_arrive1(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+// barrier 1 over the 256 epilogue threads of the forward; returns whether any
+// of them passed `v` true (the same answer in every thread)
+ADS_D bool epi_barrier_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, 1, 256, pi;\nselp.u32 %0, 1, 0, po;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
 }
 
 ADS_D float ex2_approx(float x) {
@@ -416,38 +435,54 @@ ADS_D void st_atom_split2(unsigned char* hi, int rgh, unsigned char* lo, int rgl
   if (g) *reinterpret_cast<uint4*>(g + core_off(r, c, grg)) = qh;
 }
 
-// forward: two threads per point row, each taking half of the feature columns
-// (eight warps: warps w and w + 4 read the same TMEM lanes).  For W = 64 a
-// CTA carries two tiles at once (slots 0 and 1, each with its own operand
-// tiles, TMEM accumulator and mbarrier): a slot's products run while the
-// threads work on the other slot's epilogue.
-constexpr int kFwdThreads = 2 * kTP;
+// forward: eight epilogue warps (two threads per point row, each taking half
+// of the feature columns; warps w and w + 4 read the same TMEM lanes) and one
+// issuing warp.  For W = 64 a CTA carries two tiles at once (slots 0 and 1,
+// each with its own operand tiles, TMEM accumulator, "written" and
+// "products done" mbarriers): the tensor cores work on one slot while the
+// epilogue warps work on the other.  The issuing warp only waits for a slot's
+// operand tiles and issues its products, so the epilogue warps never wait for
+// an issue; they meet only at the end of each tile pair, to add the two halves
+// of the output layer.
+constexpr int kFwdEpi = 2 * kTP;
+constexpr int kFwdThreads = kFwdEpi + 32;
 
 template <int W, int DIN>
 __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(MlpTcArgs a) {
   using L = TcSmemF<W>;
   constexpr int NS = L::NS;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* wt = sm + L::WT;
   unsigned char* act = sm + L::ACT;
   unsigned char* actlo = sm + L::ACTLO;
-  float* fb1 = reinterpret_cast<float*>(sm + L::VEC);  // s b_1
-  float* fW1 = fb1 + W;                                // s W_1, [DIN][W]
-  float* fW5 = fW1 + 3 * W;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::BAR);  // [NS]
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + L::BAR + 16);
-  volatile int* abort_flag = reinterpret_cast<int*>(sm + L::BAR + 20);
+  const float* fb1 = reinterpret_cast<const float*>(sm + L::VEC);  // s b_1
+  const float* fW1 = fb1 + W;                                       // s W_1, [3][W]
+  const float* fW5 = fW1 + 3 * W;
+  uint64_t* mb_vec = reinterpret_cast<uint64_t*>(sm + L::BAR);
+  uint64_t* mb_wt = mb_vec + 1;
+  uint64_t* mb_ready = mb_vec + 2;    // [NS] a slot's operand tiles written (one arrive per epilogue warp)
+  uint64_t* mb_prod = mb_ready + NS;  // [NS] a slot's products complete (issuer commit)
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + L::BAR + 48);
+  volatile int* abort_flag = reinterpret_cast<int*>(sm + L::BAR + 52);
   float* upart = reinterpret_cast<float*>(sm + L::UPART);
-  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTP - 1), half = tid / kTP;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool epi = tid < kFwdEpi;
+  const int row = tid & (kTP - 1), half = (tid >> 7) & 1;
   constexpr int KC = L::KC, RGH = (KC / 8) * 128, RGL = (W / 8) * 128, WH = W / 2;
-  const int cb = half * WH;  // this thread's first feature column
-  const float* th = a.theta;
-  const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
-  load_fwd_weights<W, kFwdThreads>(th, o2, wt, tid);
-  for (int i = tid; i < W; i += kFwdThreads) {
-    fb1[i] = kTanhScale * th[ob1 + i];
-    for (int d = 0; d < DIN; ++d) fW1[d * W + i] = kTanhScale * th[i * DIN + d];
-    fW5[i] = th[o5 + i];
+  const int cb = half * WH;  // an epilogue thread's first feature column
+  if (tid == kFwdEpi) {
+    *abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_vec)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_wt)));
+    for (int s = 0; s < NS; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(mb_ready + s)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_prod + s)));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the constant vectors first: layer 1 needs only them
+    mbar_expect(mb_vec, L::VEC_SZ);
+    bulk_load(sm + L::VEC, a.wimage + L::VEC, L::VEC_SZ, mb_vec);
+    mbar_expect(mb_wt, L::WT_SZ);
+    bulk_load(sm + L::WT, a.wimage + L::WT, L::WT_SZ, mb_wt);
   }
   if (tid < kTP) {
     // the constant columns of the hi operands: [1, 1, 0, ..., 0] (bias hi, lo)
@@ -457,12 +492,6 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
       *reinterpret_cast<uint4*>(ah + core_off(tid, W, RGH)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
       *reinterpret_cast<uint4*>(ah + core_off(tid, W + 8, RGH)) = make_uint4(0u, 0u, 0u, 0u);
     }
-  }
-  if (tid == 0) {
-    fW5[W] = th[o5 + W];
-    *abort_flag = 0;
-    for (int s = 0; s < NS; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + s)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -474,145 +503,172 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tbase;
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-  const uint32_t idesc = idesc_bf16(kTP, W, 0, 0);
-  const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(wt);
-  uint32_t phase[NS];
-  bool pend[NS];  // products issued and not yet waited for (CTA-uniform)
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    phase[s] = 0;
-    pend[s] = false;
-  }
-  bool aborted = false;
   const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
-  const float b5 = fW5[W];
-  // [a_hi | 1 1] [s W | s b_hi s b_lo]^T + a_lo (s W)^T for slot s, layer l:
-  // two BF16 chains into the slot's FP32 accumulator (one thread)
-  auto issue = [&](int s, int l) {
-    const uint32_t wl = wt_s + l * W * KC * 2, d = tmem + s * W;
-    const uint32_t ah = act_s + s * L::ACT_SZ, al = actlo_s + s * L::ACTLO_SZ;
-#pragma unroll
-    for (int ks = 0; ks < KC / 16; ++ks) mma_bf16(d, desc_k(ah, RGH, ks), desc_k(wl, RGH, ks), idesc, ks > 0);
-#pragma unroll
-    for (int ks = 0; ks < W / 16; ++ks) mma_bf16(d, desc_k(al, RGL, ks), desc_k(wl, RGH, ks), idesc, 1u);
-    mma_commit(mbar + s);
-  };
-  for (int tb = blockIdx.x; tb < ntiles && !aborted; tb += NS * gridDim.x) {
-    int p0[NS];
-    bool valid[NS];
-    unsigned char* gt[NS];
-    float2 u2[NS];
-    // layer 1 of each slot on the CUDA cores, z' = s (W_1 x' + b_1) on pairs
-    // of units, then the slot's first products
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int tile = tb + s * gridDim.x;
-      valid[s] = tile < ntiles;  // CTA-uniform
-      p0[s] = (a.tile0 + tile) * kTP;
-      gt[s] = nullptr;
-      u2[s] = make_float2(half == 0 ? b5 : 0.0f, 0.0f);
-      if (!valid[s]) continue;
-      float x[3];
-      coords<DIN>(min(p0[s] + row, a.npts - 1), a.N, x);
-      gt[s] = a.acts ? a.acts + (size_t)tile * act_tile_bytes(W) : nullptr;
-      if (gt[s] && act_cols(W, 0) > W) {
-        // the constant columns [1, 0, ..., 0] of the stored a_1 .. a_3
-        const uint4 q = half == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-          *reinterpret_cast<uint4*>(gt[s] + act_off(W, l) + core_off(row, W + 8 * half, act_rg(W, l))) = q;
-      }
-      unsigned char* ah = act + s * L::ACT_SZ;
-      unsigned char* al = actlo + s * L::ACTLO_SZ;
-#pragma unroll
-      for (int c = 0; c < WH; c += 8) {
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          const int o = cb + c + j;
-          float2 z = *reinterpret_cast<const float2*>(fb1 + o);
-#pragma unroll
-          for (int d = 0; d < DIN; ++d)
-            z = __ffma2_rn(*reinterpret_cast<const float2*>(fW1 + d * W + o), make_float2(x[d], x[d]), z);
-          const float2 t = tanh2_scaled(z);
-          v[j] = t.x;
-          v[j + 1] = t.y;
-        }
-        st_atom_split2(ah, RGH, al, RGL, gt[s], act_rg(W, 0), row, cb + c, v);
-      }
-      if (sync_abort(abort_flag)) {
-        aborted = true;
-        break;
-      }
-      if (tid == 0) issue(s, 0);
-      pend[s] = true;
-    }
-    // hidden layers 2..4: per slot, wait for its products, the epilogue, and
-    // (layers 2, 3) the products of its next layer
-    for (int l = 0; l < 3 && !aborted; ++l) {
+  const int G = gridDim.x;
+  if (!epi) {
+    // ---------------- issuing thread ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kTP, W, 0, 0);
+      const uint32_t act_s = smem_addr(act), actlo_s = smem_addr(actlo), wt_s = smem_addr(sm + L::WT);
+      uint32_t ph_ready[NS];
+      int issued[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        if (!valid[s]) continue;
-        if (!mbar_wait(mbar + s, phase[s])) *abort_flag = 1;
-        phase[s] ^= 1;
-        pend[s] = false;
-        tc_fence_after();
-        unsigned char* ah = act + s * L::ACT_SZ;
-        unsigned char* al = actlo + s * L::ACTLO_SZ;
-        unsigned char* g = gt[s] ? gt[s] + act_off(W, l + 1) : nullptr;
-        const int grg = act_rg(W, l + 1);
+        ph_ready[s] = 0;
+        issued[s] = 0;
+      }
+      bool ok = mbar_wait(mb_wt, 0);
+      for (int tb = blockIdx.x; ok && tb < ntiles; tb += NS * G) {
+        for (int l = 0; ok && l < 3; ++l) {
 #pragma unroll
-        for (int c0 = 0; c0 < WH; c0 += 32) {
-          float d[32];
-          tmem_ld32(lane_base + s * W + cb + c0, d);
-#pragma unroll
-          for (int c = 0; c < 32; c += 8) {
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; j += 2) {
-              const float2 t = tanh2_scaled(make_float2(d[c + j], d[c + j + 1]));
-              v[j] = t.x;
-              v[j + 1] = t.y;
+          for (int s = 0; s < NS; ++s) {
+            if (!ok || tb + s * G >= ntiles) continue;
+            if (*abort_flag || !mbar_wait(mb_ready + s, ph_ready[s])) {
+              *abort_flag = 1;
+              ok = false;
+              continue;
             }
-            if (l < 2) {
-              st_atom_split2(ah, RGH, al, RGL, g, grg, row, cb + c0 + c, v);
-            } else {
-              if (g) st_atom(g, grg, row, cb + c0 + c, v);
-              // the output layer in FP32 from the unrounded activations
+            ph_ready[s] ^= 1;
+            tc_fence_after();
+            // [a_hi | 1 1] [s W | s b_hi s b_lo]^T + a_lo (s W)^T: two BF16
+            // chains into the slot's FP32 accumulator
+            const uint32_t wl = wt_s + l * W * KC * 2, d = tmem + s * W;
+            const uint32_t ah = act_s + s * L::ACT_SZ, al = actlo_s + s * L::ACTLO_SZ;
 #pragma unroll
-              for (int j = 0; j < 8; j += 2)
-                u2[s] = __ffma2_rn(make_float2(v[j], v[j + 1]),
-                                   *reinterpret_cast<const float2*>(fW5 + cb + c0 + c + j), u2[s]);
-            }
+            for (int ks = 0; ks < KC / 16; ++ks)
+              mma_bf16(d, desc_k(ah, RGH, ks), desc_k(wl, RGH, ks), idesc, ks > 0);
+#pragma unroll
+            for (int ks = 0; ks < W / 16; ++ks) mma_bf16(d, desc_k(al, RGL, ks), desc_k(wl, RGH, ks), idesc, 1u);
+            mma_commit(mb_prod + s);
+            ++issued[s];
           }
-        }
-        if (l < 2) {
-          if (sync_abort(abort_flag)) {
-            aborted = true;
-            break;
-          }
-          if (tid == 0) issue(s, l + 1);
-          pend[s] = true;
         }
       }
+      if (!ok) *abort_flag = 1;
+      // every product has completed before the accumulators are freed (a
+      // no-op wait unless the epilogue warps stopped early)
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (issued[s] > 0) mbar_wait(mb_prod + s, (uint32_t)(issued[s] - 1) & 1u);
     }
-    // the two halves of each slot's output-layer sums
+  } else {
+    // ---------------- epilogue warps ----------------
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    if (!mbar_wait(mb_vec, 0)) *abort_flag = 1;
+    const float b5 = fW5[W];
+    uint32_t ph_prod[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if (half) upart[s * kTP + row] = u2[s].x + u2[s].y;
-    __syncthreads();
+    for (int s = 0; s < NS; ++s) ph_prod[s] = 0;
+    auto ready = [&](int s) {
+      fence_async_smem();  // generic stores before the tensor cores read them
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(mb_ready + s);
+    };
+    int pass = 0;
+    for (int tb = blockIdx.x; tb < ntiles; tb += NS * G, ++pass) {
+      int p0[NS];
+      bool valid[NS];
+      unsigned char* gt[NS];
+      float2 u2[NS];
+      // layer 1 of each slot on the CUDA cores, z' = s (W_1 x' + b_1) on
+      // pairs of units
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if (!half && valid[s] && !aborted && p0[s] + row < a.npts)
-        a.u[p0[s] + row] = u2[s].x + u2[s].y + upart[s * kTP + row];
+      for (int s = 0; s < NS; ++s) {
+        const int tile = tb + s * G;
+        valid[s] = tile < ntiles;  // CTA-uniform
+        p0[s] = (a.tile0 + tile) * kTP;
+        gt[s] = nullptr;
+        u2[s] = make_float2(half == 0 ? b5 : 0.0f, 0.0f);
+        if (!valid[s]) continue;
+        float x[3];
+        coords<DIN>(min(p0[s] + row, a.npts - 1), a.N, x);
+        gt[s] = a.acts ? a.acts + (size_t)tile * act_tile_bytes(W) : nullptr;
+        if (gt[s] && act_cols(W, 0) > W) {
+          // the constant columns [1, 0, ..., 0] of the stored a_1 .. a_3
+          const uint4 q = half == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            *reinterpret_cast<uint4*>(gt[s] + act_off(W, l) + core_off(row, W + 8 * half, act_rg(W, l))) = q;
+        }
+        unsigned char* ah = act + s * L::ACT_SZ;
+        unsigned char* al = actlo + s * L::ACTLO_SZ;
+#pragma unroll
+        for (int c = 0; c < WH; c += 8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            const int o = cb + c + j;
+            float2 z = *reinterpret_cast<const float2*>(fb1 + o);
+#pragma unroll
+            for (int d = 0; d < DIN; ++d)
+              z = __ffma2_rn(*reinterpret_cast<const float2*>(fW1 + d * W + o), make_float2(x[d], x[d]), z);
+            const float2 t = tanh2_scaled(z);
+            v[j] = t.x;
+            v[j + 1] = t.y;
+          }
+          st_atom_split2(ah, RGH, al, RGL, gt[s], act_rg(W, 0), row, cb + c, v);
+        }
+        ready(s);
+      }
+      // hidden layers 2..4: per slot, wait for its products, then the
+      // epilogue, whose tiles (layers 2, 3) feed the slot's next products
+      for (int l = 0; l < 3; ++l) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          if (!valid[s]) continue;
+          if (!*abort_flag && !mbar_wait(mb_prod + s, ph_prod[s])) *abort_flag = 1;
+          ph_prod[s] ^= 1;
+          tc_fence_after();
+          unsigned char* ah = act + s * L::ACT_SZ;
+          unsigned char* al = actlo + s * L::ACTLO_SZ;
+          unsigned char* g = gt[s] ? gt[s] + act_off(W, l + 1) : nullptr;
+          const int grg = act_rg(W, l + 1);
+#pragma unroll
+          for (int c0 = 0; c0 < WH; c0 += 32) {
+            float d[32];
+            tmem_ld32(lane_base + s * W + cb + c0, d);
+#pragma unroll
+            for (int c = 0; c < 32; c += 8) {
+              float v[8];
+#pragma unroll
+              for (int j = 0; j < 8; j += 2) {
+                const float2 t = tanh2_scaled(make_float2(d[c + j], d[c + j + 1]));
+                v[j] = t.x;
+                v[j + 1] = t.y;
+              }
+              if (l < 2) {
+                st_atom_split2(ah, RGH, al, RGL, g, grg, row, cb + c0 + c, v);
+              } else {
+                if (g) st_atom(g, grg, row, cb + c0 + c, v);
+                // the output layer in FP32 from the unrounded activations
+#pragma unroll
+                for (int j = 0; j < 8; j += 2)
+                  u2[s] = __ffma2_rn(make_float2(v[j], v[j + 1]),
+                                     *reinterpret_cast<const float2*>(fW5 + cb + c0 + c + j), u2[s]);
+              }
+            }
+          }
+          if (l < 2) ready(s);
+        }
+      }
+      // the two halves of each slot's output-layer sums (double-buffered by
+      // pass); the barrier also makes the stop decision the same everywhere
+      float* up = upart + (pass & 1) * NS * kTP;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (half) up[s * kTP + row] = u2[s].x + u2[s].y;
+      const bool stop = epi_barrier_any(*abort_flag != 0);
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (!half && valid[s] && !stop && p0[s] + row < a.npts)
+          a.u[p0[s] + row] = u2[s].x + u2[s].y + up[s * kTP + row];
+      if (stop) break;
+    }
   }
-  // after an abort, products still in flight finish (bounded wait) before
-  // their accumulator is freed
-#pragma unroll
-  for (int s = 0; s < NS; ++s)
-    if (pend[s]) mbar_wait(mbar + s, phase[s]);
-  if (sync_abort(abort_flag) && tid == 0) atomicOr(a.flags, 8);
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && tid == 0) atomicOr(a.flags, 8);
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NS * W));
 }
@@ -655,13 +711,6 @@ struct TcSmemB {
 constexpr int kColDel = 0, kColW5 = 64, kColW4 = 144, kColW1 = 384;
 ADS_D int col_dw(int L) { return L == 5 ? kColW5 : (L == 1 ? kColW1 : kColW4 + (4 - L) * kWP); }
 
-ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
-               : "memory");
-}
-ADS_D void mbar_arrive1(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
-}
 
 template <int DIN>
 __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
@@ -1292,12 +1341,16 @@ static MlpTcArgs tile_range(MlpTcArgs a) {
 
 template <int W, int DIN>
 static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
-  const size_t smem = TcSmemF<W>::TOTAL;
-  auto k = k_mlp_fwd_tc<W, DIN>;
-  smem_optin(k);
-  const int occ = tc_residency(k, smem, TcSmemF<W>::NS * W, kFwdThreads);
+  using L = TcSmemF<W>;
   const int ntiles = a.tile_count;
   if (ntiles <= 0) return cudaSuccess;
+  // the weight image from the current parameters, then the forward
+  constexpr int nstage = 3 * W * (L::KC / 8) + L::VEC_SZ / 4;
+  k_stage_fwd<W, DIN><<<(nstage + 255) / 256, 256, 0, st>>>(a.theta, a.wimage);
+  const size_t smem = L::TOTAL;
+  auto k = k_mlp_fwd_tc<W, DIN>;
+  smem_optin(k);
+  const int occ = tc_residency(k, smem, L::NS * W, kFwdThreads);
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
   if (want < grid) grid = want > 0 ? want : 1;
@@ -1305,9 +1358,14 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+size_t mlp_tc_fwd_image_bytes(int width) {
+  return width == 64 ? TcSmemF<64>::IMG : TcSmemF<128>::IMG;
+}
+
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a0, cudaStream_t st) {
   if (a0.npts <= 0) return cudaSuccess;
   if (reinterpret_cast<uintptr_t>(a0.theta) & 15) return cudaErrorInvalidValue;  // 16-byte weight rows
+  if (!a0.wimage || (reinterpret_cast<uintptr_t>(a0.wimage) & 15)) return cudaErrorInvalidValue;
   const MlpTcArgs a = tile_range(a0);
   if (a.width == 64) return a.din == 2 ? fwd_tc<64, 2>(a, st) : fwd_tc<64, 3>(a, st);
   if (a.width == 128) return a.din == 2 ? fwd_tc<128, 2>(a, st) : fwd_tc<128, 3>(a, st);
