@@ -445,6 +445,18 @@ ads_status ads_saturation_step_noalloc_status(void* stream, int* flags_out);
  * ads_profile_saturation: `steps` saturation steps (current dt) likewise;
  * ms_out[3]: quadrature + x sweep, y sweep, mass bookkeeping. */
 ads_status ads_kernel_launches(const ads_ctx* ctx, unsigned long long* count);
+/* ads_probe_wait_expiry: runs, on the context's stream, one kernel that waits
+ * on an mbarrier the way every kernel here does -- bounded, with tensor
+ * memory held and a bulk copy of its own in flight -- but that nobody
+ * completes (arrive = 0) or that a second thread completes (arrive != 0).
+ * After `limit_s` seconds (0 < limit_s <= 10) without completion the kernel
+ * records bit 8 (the same bit the real kernels set on a timed-out wait), lets
+ * its copy land, frees its tensor memory and returns.  Waits for the stream;
+ * *bits_out (nullable) receives the probe's status word.  The context's own
+ * status word is not touched, so the context carries on.  Returns
+ * ADS_ERR_TIMEOUT when the wait expired, else ADS_OK.  No counterpart in the
+ * paper.  Errors: ADS_ERR_INVALID_ARG (NULL context, limit out of range). */
+ads_status ads_probe_wait_expiry(ads_ctx* ctx, double limit_s, int arrive, int* bits_out);
 /* ads_measure_unit_rates: measured peak rates of the arithmetic units the
  * rooflines use, on the current device (no counterpart in the paper).  One
  * wave of CTAs runs 8 independent chains per thread of one operation;

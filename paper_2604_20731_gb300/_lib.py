@@ -118,6 +118,7 @@ SIGNATURES = {
     "ads_saturation_step_noalloc_status": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "ads_kernel_launches": (C.c_int, [_P, C.POINTER(C.c_ulonglong)]),
     "ads_measure_unit_rates": (C.c_int, [_D, C.c_int]),
+    "ads_probe_wait_expiry": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "ads_profile_train": (C.c_int, [_P, C.c_int, _D]),
     "ads_profile_saturation": (C.c_int, [_P, C.c_int, _D]),
     "ads_server_create": (C.c_int, [C.POINTER(ads_server_config), C.POINTER(_P)]),

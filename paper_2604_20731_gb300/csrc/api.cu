@@ -1436,6 +1436,24 @@ ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* h
   return ADS_OK;
 }
 
+ads_status ads_probe_wait_expiry(ads_ctx* c, double limit_s, int arrive, int* bits_out) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!(limit_s > 0) || limit_s > 10.0) return ADS_ERR_INVALID_ARG;
+  // the probe reports into word 3 of the flag block; the context's own
+  // status word (word 0) is not touched
+  int* word = c->flags + 3;
+  CK(cudaMemsetAsync(word, 0, sizeof(int), c->stream));
+  CK(launch_wait_probe(c->flags, (unsigned long long)(limit_s * 1e9), arrive, word, c->stream));
+  c->nlaunch++;
+  CK(cudaMemcpyAsync(c->h_stage, word, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CA(wait(c, 2.0 * limit_s + kDefaultTimeout));
+  int bits = 0;
+  std::memcpy(&bits, c->h_stage, sizeof(int));
+  if (bits_out) *bits_out = bits;
+  return (bits & 8) ? ADS_ERR_TIMEOUT : ADS_OK;
+}
+
 ads_status ads_kernel_launches(const ads_ctx* c, unsigned long long* count) {
   if (!c || !count) return ADS_ERR_INVALID_ARG;
   *count = c->nlaunch;

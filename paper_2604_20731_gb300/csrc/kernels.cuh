@@ -231,6 +231,12 @@ size_t mlp_tc_acts_bytes(int npts, int width);
 // `min_tiles` 128-point tiles per CTA
 int mlp_tc_bwd_blocks(int npts, int width, int din, int min_tiles = 1);
 
+// ---- diagnostics: one bounded mbarrier wait run to its limit (or completed,
+// with arrive != 0); bit 8 goes to *word on expiry.  src16: 16 readable,
+// 16-byte aligned device bytes (the probe's own bulk copy)
+cudaError_t launch_wait_probe(const void* src16, unsigned long long limit_ns, int arrive, int* word,
+                              cudaStream_t st);
+
 // ---- Galerkin B-spline pressure (the plain method; 2D, FP64 arithmetic) ----
 constexpr int kGalMaxN = 512;
 template <typename TA>

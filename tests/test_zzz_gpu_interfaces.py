@@ -64,3 +64,34 @@ def test_host_wait_deadline_reports_timeout_and_context_survives():
         assert np.isfinite(s.get("LOSS")).all()
     finally:
         s.close()
+
+
+def test_device_wait_expiry_is_reported_and_the_context_carries_on():
+    """A device-side mbarrier wait with no producer runs out: the probe kernel
+    (the kernels' own bounded wait, with tensor memory held and a bulk copy in
+    flight) records the timeout bit and returns ADS_ERR_TIMEOUT after its
+    limit; with a producer the same wait completes.  The context's state and
+    status are untouched: the loss is bit-identical afterwards and a hybrid
+    step reads a clean status."""
+    import ctypes as C
+    import time
+    from paper_2604_20731_gb300.solver import HybridSolver
+    n = 33
+    sc = scn.make_scenario(2, n, seed=5, S0="random")
+    s = HybridSolver(sc, width=64, crv_dtype="bf16", ads_dtype="f32")
+    try:
+        s.set_theta(scn.make_theta0(2, 64, 4, seed=7))
+        s.update_coefficients()
+        l0 = s.loss_grad()
+        bits = C.c_int(-1)
+        t0 = time.perf_counter()
+        assert s.lib.ads_probe_wait_expiry(s.ctx, 0.05, 0, C.byref(bits)) == 5  # ADS_ERR_TIMEOUT
+        assert time.perf_counter() - t0 >= 0.05
+        assert bits.value == 8
+        assert s.lib.ads_probe_wait_expiry(s.ctx, 0.05, 1, C.byref(bits)) == 0
+        assert bits.value == 0
+        assert s.loss_grad() == l0
+        st = s.hybrid_step(HybridSolver.hybrid_params(n_sub=2, adam_iters=5, lr=1e-3))
+        assert np.isfinite(st["loss_last"])
+    finally:
+        s.close()
