@@ -46,18 +46,20 @@ def args_parse():
     ap.add_argument("--width", type=int, default=64)
     ap.add_argument("--adam-iters", type=int, default=100)
     ap.add_argument("--n-sub", type=int, default=10)
-    ap.add_argument("--pretrain", type=int, default=300)
+    ap.add_argument("--pretrain", type=int, default=6000)
+    ap.add_argument("--base-iters", type=int, default=20000,
+                    help="iterations of the base network every scenario starts from (0: Xavier start)")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--streams", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--arrival-ms", type=float, default=20.0)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--c2-steps", type=int, default=20)
     ap.add_argument("--c1-steps", type=int, default=20)
     ap.add_argument("--large-steps", type=int, default=3)
-    ap.add_argument("--err-iters", type=int, default=60000)
+    ap.add_argument("--err-iters", type=int, default=30000)
     ap.add_argument("--err-steps", type=int, default=3)
     ap.add_argument("--sat-n", type=int, default=4096)
     ap.add_argument("--only-saturation", action="store_true",
@@ -80,6 +82,8 @@ def workload_config(a, world, sizes=None):
         "n_sub": a.n_sub, "adam_iters": a.adam_iters, "lr": a.lr, "dt_policy": "cfl 0.1",
         "scenarios_per_gpu": len(sizes), "streams": a.streams, "parallelism": f"replicas x{world}",
         "rounds_timed": a.steps, "pretrain": a.pretrain,
+        "network_start": (f"base network ({a.base_iters} iterations on K = 1, rate 1), output scaled by the "
+                          "scenario's rate" if a.base_iters > 0 else "Xavier"),
         "l2": "working set of the resident mix exceeds L2 (129 MB); no flush",
     }
 
@@ -530,6 +534,129 @@ def saturation_roofline(n, scn, HybridSolver, rates=None):
     return out
 
 
+def summary_line(value, plain, err, sat, roof, e2e):
+    """The few numbers the line is about, short enough to survive truncation."""
+    out = {"steps_per_s": round(value, 2)}
+    if plain:
+        out["mp_batched_over_plain_fp64"] = round(plain["mp_batched_over_plain_fp64"], 1)
+    if err:
+        ms = err["mix_pressure_summary"]
+        out["mix_pressure_rel_l2_median_max"] = [round(ms["median"], 4), round(ms["max"], 4)]
+        out["mix_pressure_at_or_below_1e-2"] = f"{ms['at_or_below_1e-2']}/{ms['sampled']}"
+        out["mix_saturation_rel_linf_max"] = max(x["rel_linf"] for x in err["mix_saturation_rel_linf_one_fp32_step"])
+    if roof and roof.get("frac") is not None:
+        out["roofline"] = f"{roof['kernel']} {roof['frac']:.3f} of measured {roof['unit']}"
+    if sat and sat.get("f32"):
+        f = sat["f32"]
+        out["ysweep_frac_of_hbm"] = round(f["ysweep_frac_of_hbm"], 3)
+        if f.get("quad_alu"):
+            out["quad_fp32_frac"] = round(f["quad_alu"]["frac"], 3)
+    if e2e:
+        out["e2e_steps_per_s"] = round(e2e["value"], 2)
+    return out
+
+
+def base_network(a, scn, HybridSolver, theta0):
+    """The base network the scenarios start from: the homogeneous 256^2
+    scenario (K = 1, rate 1, the wells of the mix) trained from the Xavier
+    network, half the iterations at lr 1e-3 and half at 3e-4.  Returns the
+    parameters (or None with base_iters 0) and its error record."""
+    import numpy as np
+    if a.base_iters <= 0:
+        return None, None
+    from oracle.crvpinn import CrvOracle
+    sc = scn.make_scenario(2, 256, seed=1000, sigma=0.0, rate=1.0)
+    t0 = time.perf_counter()
+    s = HybridSolver(sc, width=a.width, crv_dtype="bf16", ads_dtype="f32")
+    s.set_theta(theta0)
+    s.pretrain(a.base_iters // 2, 1e-3)
+    s.pressure_update(a.base_iters - a.base_iters // 2, 3e-4)
+    th = s.get("THETA").astype(np.float64)
+    sec = time.perf_counter() - t0
+    crv = CrvOracle(sc)
+    alpha, f = crv.coefficients(sc.S0_or_zero())
+    ustar = crv.direct_solution(alpha, f)
+    s.project_pressure()
+    e = float(np.linalg.norm(s.get("U") - ustar) / np.linalg.norm(ustar))
+    s.close()
+    return th, {"scenario": "256^2, K = 1, rate 1", "iterations": a.base_iters, "seconds": sec,
+                "pressure_rel_l2": e}
+
+
+def stated_error(a, mix, sizes, ctxs, hp, theta0, scn, HybridSolver):
+    """The error the throughput is measured at (see run_ours)."""
+    import numpy as np
+    from oracle.ads import AdsOracle
+    from oracle.crvpinn import CrvOracle
+    members, sat = [], []
+    for n in sorted(set(sizes)):
+        idx = [i for i, m in enumerate(mix) if m.n == n]
+        sig = [float(np.log(mix[i].K).std()) for i in idx]
+        order = np.argsort(sig)
+        picks = sorted({int(order[0]), int(order[len(order) // 2]), int(order[-1])})
+        for k in picks:
+            j = idx[k]
+            s, sc = ctxs[j], mix[j]
+            S_now = s.get("S")
+            crv = CrvOracle(sc)
+            alpha, f = crv.coefficients(S_now)
+            ustar = crv.direct_solution(alpha, f)
+            s.project_pressure()
+            e = float(np.linalg.norm(s.get("U") - ustar) / np.linalg.norm(ustar))
+            members.append({"member": j, "n": n, "log_k_std": round(sig[k], 3),
+                            "rate": round(sc.sources[0].rate, 3), "pressure_rel_l2": e})
+        j = idx[int(order[len(order) // 2])]
+        s, sc = ctxs[j], mix[j]
+        S_now, P_now = s.get("S"), s.get("P")
+        dt_now = float(s.get("DT")[0])
+        s2 = HybridSolver(sc, width=None, ads_dtype="f32")
+        s2.set_saturation(S_now)
+        s2.set_pressure(P_now)
+        s2.saturation_step(dt_now, 1)
+        ref = AdsOracle(sc).step(S_now, P_now, dt_now)
+        sat.append({"member": j, "n": n,
+                    "rel_linf": float(np.abs(s2.get("S") - ref).max() / max(np.abs(ref).max(), 1e-300))})
+        s2.close()
+    pe = [m["pressure_rel_l2"] for m in members]
+
+    def pressure_error(scen, dtn, steps):
+        crv = CrvOracle(scen)
+        sa = HybridSolver(scen, width=a.width, crv_dtype=dtn, ads_dtype="f32")
+        sa.set_theta(theta0)
+        sa.pretrain(a.err_iters, 1e-3)
+
+        def rel():
+            alpha, f = crv.coefficients(sa.get("S"))
+            ustar = crv.direct_solution(alpha, f)
+            sa.project_pressure()
+            return float(np.linalg.norm(sa.get("U") - ustar) / np.linalg.norm(ustar))
+
+        out = [rel()]
+        for _ in range(steps):
+            sa.hybrid_step(hp)
+            out.append(rel())
+        sa.close()
+        return out
+
+    c2 = scn.make_scenario(2, 256, seed=1000)
+    p_c2 = {dtn: pressure_error(c2, dtn, a.err_steps) for dtn in ("bf16", "f32")}
+    return {
+        "mix_pressure_rel_l2": members,
+        "mix_pressure_summary": {"sampled": len(pe), "median": float(np.median(pe)), "max": float(max(pe)),
+                                 "at_or_below_1e-2": int(sum(x <= 1e-2 for x in pe))},
+        "mix_pressure_note": (f"members of the timed mix after {a.pretrain} admission iterations, "
+                              f"{max(a.warmup, 3)} warm-up and {a.steps} timed hybrid steps of {a.adam_iters} "
+                              "iterations; network at its current parameters vs the direct discrete solution "
+                              "for the member's current saturation"),
+        "mix_saturation_rel_linf_one_fp32_step": sat,
+        "c2_pressure_scenario": "256^2, sigma 1, correlation length 0.1, seed 1000",
+        "c2_pressure_rel_l2_bf16": p_c2["bf16"][0], "c2_pressure_rel_l2_fp32": p_c2["f32"][0],
+        "c2_pressure_rel_l2_after_each_hybrid_step_bf16": p_c2["bf16"][1:],
+        "c2_pressure_rel_l2_after_each_hybrid_step_fp32": p_c2["f32"][1:],
+        "c2_note": f"{a.err_iters} Adam iterations (lr 1e-3) from the Xavier network, then {a.err_steps} hybrid steps",
+    }
+
+
 def run_ours(a, world, rank, local):
     import numpy as np
     import torch
@@ -552,6 +679,17 @@ def run_ours(a, world, rank, local):
     theta0 = scn.make_theta0(2, a.width, 4, seed=7)
     mix = serving_mix(a.scenarios, seed=3 + rank)
     sizes = [sc.n for sc in mix]
+    # warm start: every scenario's network starts from one base network,
+    # trained once (outside every timed region) on the homogeneous scenario
+    # K = 1, rate 1, with its output layer scaled by the scenario's rate
+    base, base_info = base_network(a, scn, HybridSolver, theta0)
+
+    def theta_start(sc):
+        if base is None:
+            return theta0
+        th = base.copy()
+        th[-(a.width + 1):] *= sc.sources[0].rate  # output layer W_5, b_5
+        return th
 
     # ---- (1) batched mixed precision, scenarios resident: the headline ----
     streams = [torch.cuda.Stream(device=device) for _ in range(a.streams)]
@@ -559,10 +697,15 @@ def run_ours(a, world, rank, local):
     for i, sc in enumerate(mix):
         s = HybridSolver(sc, width=a.width, crv_dtype="bf16", ads_dtype="f32", stream=streams[i % a.streams])
         s.set_concurrency(min(a.streams, len(mix)))
-        s.set_theta(theta0)
-        if a.pretrain > 0:
-            s.pretrain(a.pretrain, a.lr)
+        s.set_theta(theta_start(sc))
         ctxs.append(s)
+    # admission training of every resident scenario, side by side on the streams
+    t_adm = time.perf_counter()
+    if a.pretrain > 0:
+        for s in ctxs:
+            s.pretrain(a.pretrain, a.lr, sync=False)
+    torch.cuda.synchronize()
+    admission_s = time.perf_counter() - t_adm
     for _ in range(max(a.warmup, 3)):
         for s in ctxs:
             s.hybrid_step(hp, stats=False)
@@ -601,69 +744,19 @@ def run_ours(a, world, rank, local):
     steps_done = a.steps * len(ctxs) * world
     value = steps_done / (total_ms / 1e3)
 
-    # stated error of the MP form (rank 0):
-    #  * saturation: one FP32 saturation step from the GPU state of a 256^2 mix
-    #    member vs the FP64 oracle;
-    #  * pressure: the 256^2 scenario of the single-scenario configuration
-    #    (sigma 1, correlation length 0.1), network trained from the Xavier
-    #    initial state for `err_iters` Adam iterations (lr 1e-3), then
-    #    `err_steps` hybrid steps (10 saturation sub-steps + 100 Adam iterations
-    #    each); relative L2 of the network pressure vs the direct discrete
-    #    solution for the saturation of that moment, BF16 tensor-core network and
-    #    FP32 CUDA-core network side by side; the same training on the 256^2
-    #    mix member (its own sigma and rate) as the harder case.
+    # ---- stated error of the measured mix (rank 0, after the timed rounds) ----
+    #  * pressure: for each mesh size, the members of the mix with the lowest,
+    #    median and highest log-K spread, in the state the timed rounds left
+    #    them: relative L2 of the network pressure (current parameters) against
+    #    the direct discrete solution for the member's current saturation;
+    #  * saturation: one FP32 sub-step from the GPU state of one member per
+    #    size against the FP64 oracle (relative L-inf);
+    #  * the single-scenario study of configuration 2 (256^2, sigma 1): the
+    #    network trained for `err_iters` iterations, then `err_steps` hybrid
+    #    steps, BF16 and FP32 networks side by side.
     err = None
     if rank == 0:
-        from oracle.ads import AdsOracle
-        from oracle.crvpinn import CrvOracle
-        j = next((i for i, n in enumerate(sizes) if n == 256), 0)
-        s, sc = ctxs[j], mix[j]
-        S_now, P_now = s.get("S"), s.get("P")
-        dt_now = float(s.get("DT")[0])
-        s2 = HybridSolver(sc, width=None, ads_dtype="f32")
-        s2.set_saturation(S_now)
-        s2.set_pressure(P_now)
-        s2.saturation_step(dt_now, 1)
-        ref = AdsOracle(sc).step(S_now, P_now, dt_now)
-        sat_err = float(np.abs(s2.get("S") - ref).max() / max(np.abs(ref).max(), 1e-300))
-        s2.close()
-
-        def pressure_error(scen, dtn, steps):
-            crv = CrvOracle(scen)
-            sa = HybridSolver(scen, width=a.width, crv_dtype=dtn, ads_dtype="f32")
-            sa.set_theta(theta0)
-            sa.pretrain(a.err_iters, 1e-3)
-
-            def rel():
-                alpha, f = crv.coefficients(sa.get("S"))
-                ustar = crv.direct_solution(alpha, f)
-                sa.project_pressure()
-                return float(np.linalg.norm(sa.get("U") - ustar) / np.linalg.norm(ustar))
-
-            out = [rel()]
-            for _ in range(steps):
-                sa.hybrid_step(hp)
-                out.append(rel())
-            sa.close()
-            return out
-
-        c2 = scn.make_scenario(2, 256, seed=1000)
-        p_c2 = {dtn: pressure_error(c2, dtn, a.err_steps) for dtn in ("bf16", "f32")}
-        p_mix = pressure_error(sc, "bf16", 0)[0]
-        err = {"saturation_scenario": f"{sc.n}^2 (mix member {j})",
-               "saturation_rel_linf_vs_fp64_oracle_one_step_fp32": sat_err,
-               "pressure_scenario": "256^2, sigma 1, correlation length 0.1, seed 1000",
-               "pressure_rel_l2_vs_direct_bf16_network": p_c2["bf16"][0],
-               "pressure_rel_l2_vs_direct_fp32_network": p_c2["f32"][0],
-               "pressure_rel_l2_after_each_hybrid_step_bf16": p_c2["bf16"][1:],
-               "pressure_rel_l2_after_each_hybrid_step_fp32": p_c2["f32"][1:],
-               "pressure_rel_l2_mix_member_bf16": p_mix,
-               "pressure_mix_member": f"{sc.n}^2 mix member {j} (log-K std {np.log(sc.K).std():.2f}, "
-                                      f"rate {sc.sources[0].rate:.2f})",
-               "pressure_note": f"{a.err_iters} Adam iterations (lr 1e-3) from the Xavier initial network, "
-                                f"then {a.err_steps} hybrid steps of 100 Adam iterations each; the "
-                                "throughput runs pretrain for a shorter time at admission (pretraining is "
-                                "admission work, not step work) and run the same per-step work"}
+        err = stated_error(a, mix, sizes, ctxs, hp, theta0, scn, HybridSolver)
 
     # ---- roofline of the dominant kernel of the mix (live CUDA events) ----
     # (the kernels in their full-GPU launch shape: one context alone)
@@ -751,7 +844,7 @@ def run_ours(a, world, rank, local):
                 time.sleep(wait)
             ids.append(srv.submit(sc, n_steps=a.e2e_steps, hp=hp, width=a.width, crv_dtype="bf16",
                                   ads_dtype="f32", pretrain_iters=a.pretrain, pretrain_lr=a.lr,
-                                  theta0=theta0))
+                                  theta0=theta_start(sc)))
         for rid in ids:
             srv.wait(rid, timeout_s=900)
         torch.cuda.synchronize()
@@ -765,6 +858,7 @@ def run_ours(a, world, rank, local):
                "d2h_bytes_per_step": 2 * nb_bytes / (len(mix) * a.e2e_steps),
                "steps_per_scenario": a.e2e_steps, "arrivals": f"Poisson, mean {a.arrival_ms} ms",
                "budget_gb": a.budget_gb, "pretrain_at_admission": a.pretrain,
+               "start": "base network" if base is not None else "Xavier",
                "p50_step_ms": server_stats["p50_step_ms"], "p99_step_ms": server_stats["p99_step_ms"],
                "peak_resident": server_stats["peak_active"]}
 
@@ -841,15 +935,20 @@ def run_ours(a, world, rank, local):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "bf16+f32", "data": "synthetic (log-normal K GRF, Gaussian wells)",
                "config": workload_config(a, world, sizes),
-               "p50_step_ms": rs[len(rs) // 2], "p99_step_ms": rs[min(len(rs) - 1, int(math.ceil(0.99 * len(rs))) - 1)],
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clk,
+               # details first, the summary a reader looks for last (a truncated
+               # record keeps the end of the line)
+               "kernel_ms_by_n": prof_by_n, "unit_rates": rates, "server": server_stats,
+               "c3_c5_w128": large, "c2_fp64_sat_fp32_net": c2, "c1_plain_galerkin": c1,
+               "saturation": sat, "base_network": base_info, "admission_training_s": admission_s,
+               "error": err,
                "latency_note": "resident run: a scenario's step latency is the round time (all "
                                "scenarios step once per round); e2e holds the server's per-step latency",
-               "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "plain_fp64": plain, "c2_fp64_sat_fp32_net": c2, "c1_plain_galerkin": c1,
-               "c3_c5_w128": large,
-               "saturation": sat,
-               "gpu_launches": launches, "clocks": clk, "kernel_ms_by_n": prof_by_n, "unit_rates": rates,
-               "server": server_stats}
+               "plain_fp64": plain,
+               "summary": summary_line(value, plain, err, sat, roof, e2e),
+               "p50_step_ms": rs[len(rs) // 2],
+               "p99_step_ms": rs[min(len(rs) - 1, int(math.ceil(0.99 * len(rs))) - 1)]}
         print(json.dumps(out), flush=True)
     return 0
 

@@ -167,11 +167,11 @@ class HybridSolver:
         self._check(self.lib.crvpinn_loss_grad(self.ctx, C.byref(out)), "crvpinn_loss_grad")
         return out.value
 
-    def pretrain(self, iters: int, lr: float) -> float:
+    def pretrain(self, iters: int, lr: float, sync: bool = True):
         out = C.c_double()
-        self._check(self.lib.crvpinn_pretrain(self.ctx, int(iters), float(lr), C.byref(out)),
+        self._check(self.lib.crvpinn_pretrain(self.ctx, int(iters), float(lr), C.byref(out) if sync else None),
                     "crvpinn_pretrain")
-        return out.value
+        return out.value if sync else None
 
     def pressure_update(self, iters: int, lr: float, sync: bool = True):
         out = C.c_double()
