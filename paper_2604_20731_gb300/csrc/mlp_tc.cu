@@ -1,5 +1,5 @@
 // CRVPINN network on the 5th-generation tensor cores (tcgen05, sm_103a):
-// BF16 operands, FP32 accumulation in tensor memory (TMEM).  Width 64.
+// BF16 operands, FP32 accumulation in tensor memory (TMEM).  Widths 64, 128.
 //
 // Operand tiles live in shared memory in the no-swizzle canonical layout:
 // 8-row x 16-byte core matrices; within a tile of R rows and C columns the
@@ -8,24 +8,27 @@
 // N, columns = K; descriptor LBO = 128, SBO = RG) or as an MN-major operand
 // (rows = K, columns = M or N; LBO = RG, SBO = 128).
 //
-// Forward, per tile of 128 collocation points (one CTA of 128 threads, thread
-// t = point t = TMEM lane t):
+// Forward, per tile of 128 collocation points (TMEM lane t = point t; two
+// epilogue threads per point, one issuing thread):
 //   a_1 = tanh(W_1 x' + b_1) on the CUDA cores (K = 2 or 3);
-//   for the three hidden layers: D[t][o] = sum_k a[t][k] W[o][k] with the
-//   activations held as a BF16 pair a = a_hi + a_lo (two 128 x 64 x 64 MMA
-//   chains into one FP32 accumulator, issued by one thread) -- the residual
-//   differences neighbouring network values, so per-point rounding of the
-//   activations to BF16 alone would swamp it on fine grids; each thread then
-//   reads its row of D from TMEM, adds the bias, applies tanh and writes the
-//   next pair (and, for the backward pass, the BF16 row to HBM);
+//   for the three hidden layers: D[t][o] = s (sum_k a[t][k] W[o][k] + b[o])
+//   with s = -2 log2 e folded into the staged weights and the bias carried by
+//   an extra K block (see TcSmemF), the activations held as a BF16 pair
+//   a = a_hi + a_lo (two MMA chains into one FP32 accumulator) -- the
+//   residual differences neighbouring network values, so per-point rounding
+//   of the activations to BF16 alone would swamp it on fine grids; the
+//   epilogue reads its row of D from TMEM, applies tanh = 2 / (1 + 2^D) - 1
+//   and writes the next pair (and, for the backward pass, the BF16 row to
+//   HBM);
 //   u = W_5 a_4 + b_5 in FP32 from registers.
 // Backward, per tile (persistent CTAs; gradients accumulate in TMEM over all
 // of a CTA's tiles):
-//   D_l (for dW_l, db_l) += Delta_l^T [a_{l-1} | 1] -- M = 128 output rows
-//   (64 used), N = 80 (64 inputs + the stored ones column giving db), K = 128
-//   points, both operands MN-major views of the [point][feature] tiles;
+//   D_l (for dW_l, db_l) += Delta_l^T [a_{l-1} | 1] -- M = 64 output rows
+//   (width 64; the ring form for width 128 uses M = 128), N = 80 (64 inputs +
+//   the stored ones column giving db), K = 128 points, both operands
+//   MN-major views of the [point][feature] tiles;
 //   Delta_{l-1} = (Delta_l W_l) (1 - a_{l-1}^2) -- M = 128 points, N = 64,
-//   K = 64, W_l read MN-major from the same weight tile as the forward.
+//   K = 64, W_l read MN-major from the backward's own weight tiles.
 //   The output layer is the same product with Delta_5 = [g, 0, ...] and the
 //   first layer with [x' | 1] as the second operand.
 #include <cuda_bf16.h>
@@ -40,7 +43,7 @@ namespace {
 constexpr int kW = 64;           // hidden width of this path
 constexpr int kTP = 128;         // points per tile = MMA M = TMEM lanes
 constexpr int kWP = kW + 16;     // activation tile width incl. ones column
-constexpr int kDP = 128;         // M of the weight-gradient products (64 output rows used)
+constexpr int kDP = 128;         // M of the ring form's weight-gradient products (rows past W unused)
 constexpr int kXP = 16;          // input tile width: x', 1, zeros
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
@@ -272,31 +275,38 @@ ADS_D void load_hidden_weights(const float* __restrict__ th, int o2, unsigned ch
   }
 }
 
+// TMEM lane of row o of an M = 64 accumulator: 16 rows in the first 16 lanes
+// of each 32-lane quadrant (measured with a probe MMA on this GPU); the row a
+// thread of warps 0-3 reads, or -1
+ADS_HD constexpr int m64_row(int tid) { return (tid & 31) < 16 ? 16 * (tid >> 5) + (tid & 31) : -1; }
+
 // One hidden layer's gradient into the CTA's partial row: dW[o][k] (o, k < W)
-// sits in TMEM lane o, columns k of `lane_col` (tmem address with the warp's
-// lane offset and the layer's first column); its bias gradient is TMEM column
-// W (TB) or `bias_o`.  Threads of warps 0-3 read their lanes (warp-collective
-// loads), the rows meet in shared memory S (W x (W + 1) floats), and the CTA
-// writes g[o W + k] and g[W W + o] with consecutive threads on consecutive
-// addresses.  Called by every thread of the CTA (two barriers inside).
-template <int W, int NTHR, bool TB>
+// sits in TMEM row o (lane o, or the M = 64 lane of row o with M64), columns
+// k of `lane_col` (tmem address with the warp's lane offset and the layer's
+// first column); its bias gradient is TMEM column W (TB) or `bias_o`.
+// Threads of warps 0-3 read their lanes (warp-collective loads), the rows meet
+// in shared memory S (W x (W + 1) floats), and the CTA writes g[o W + k] and
+// g[W W + o] with consecutive threads on consecutive addresses.  Called by
+// every thread of the CTA (two barriers inside).
+template <int W, int NTHR, bool TB, bool M64 = false>
 ADS_D void dw_layer_out(uint32_t lane_col, bool live, float bias_o, float* S, float* g, int tid) {
   constexpr int SW = W + 1;
+  const int o = M64 ? m64_row(tid) : tid;
   if (live && tid < kTP) {
 #pragma unroll 1
     for (int c = 0; c < (TB ? W + 16 : W); c += 16) {
       float v[16];
       tmem_ld16(lane_col + c, v);  // warp-collective
-      if (tid < W) {
+      if (o >= 0 && o < W) {
         if (c < W) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) S[tid * SW + c + j] = v[j];
+          for (int j = 0; j < 16; ++j) S[o * SW + c + j] = v[j];
         } else {
-          S[tid * SW + W] = v[0];
+          S[o * SW + W] = v[0];
         }
       }
     }
-    if (!TB && tid < W) S[tid * SW + W] = bias_o;
+    if (!TB && o >= 0 && o < W) S[o * SW + W] = bias_o;
   }
   __syncthreads();
   if (live)
@@ -777,8 +787,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     const uint32_t wt_s = smem_addr(wt), act_s = smem_addr(act), del_s = smem_addr(del),
                    xin_s = smem_addr(xin);
     // dW_l | db_l: M = 128 (o; rows 64 .. 127 unused), N = 80 ([a | 1]), K = points
-    const uint32_t id_dw = idesc_bf16(kDP, act_cols(kW, 0), 1, 1);
-    const uint32_t id_db = idesc_bf16(kDP, kXP, 1, 1);  // dW_1 | db_1: N = 16 ([x' | 1])
+    // M = 64: exactly the 64 output rows (the M = 64 accumulator layout, m64_row)
+    const uint32_t id_dw = idesc_bf16(kW, act_cols(kW, 0), 1, 1);
+    const uint32_t id_db = idesc_bf16(kW, kXP, 1, 1);  // dW_1 | db_1: N = 16 ([x' | 1])
     const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
     uint32_t ph_ready = 0, ph_ready4 = 0, ph_free = 0, lph = 0;
     int pend = -1;  // buffer whose bulk copy is in flight (at most one), or -1
@@ -984,19 +995,19 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       gacc[o5 + tid] = sum;
     }
   }
-  // hidden layers: TMEM lane o = thread o of warps 0-3 (rows o >= 64 are
-  // padding), through shared memory past the output-layer sums
+  // hidden layers: row o of the M = 64 accumulators in lane m64_row of warps
+  // 0-3, through shared memory past the output-layer sums
   const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   float* S = reinterpret_cast<float*>(act + kRedBytes);
   for (int L = 4; L >= 2; --L)
-    dw_layer_out<kW, kBwdThreads, true>(lane_base + col_dw(L), live, 0.0f, S,
-                                        gacc + o2 + (L - 2) * (kW * kW + kW), tid);
+    dw_layer_out<kW, kBwdThreads, true, true>(lane_base + col_dw(L), live, 0.0f, S,
+                                              gacc + o2 + (L - 2) * (kW * kW + kW), tid);
   if (tid < kTP) {
-    const int o = tid;
+    const int o = m64_row(tid);
     if (live) {
       float v[16];
       tmem_ld16(lane_base + col_dw(1), v);  // warp-collective
-      if (o < kW) {
+      if (o >= 0 && o < kW) {
         for (int d = 0; d < DIN; ++d) gacc[o * DIN + d] = v[d];
         gacc[ob1 + o] = v[DIN];
       }
