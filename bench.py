@@ -498,7 +498,8 @@ def saturation_roofline(n, scn, HybridSolver, rates=None):
         s.close()
         nb = n + 2
         re = 4 if 6 * nb * es <= 110 * 1024 else 2
-        nsp = 2 * ((n + re - 1) // re - 1)
+        csz = {4: 2, 2: 4}[re]  # strips per quadrature cluster: one spill pair per cluster
+        nsp = 2 * (((n + re - 1) // re + csz - 1) // csz - 1)
         quad_b = es * (2 * nb * nb + (n + 1) ** 2 + nb * nb + nsp * nb)
         ysw_b = es * (2 * nb * nb + nsp * nb)
         tot = sum(ms.values())

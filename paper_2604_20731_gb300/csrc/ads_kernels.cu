@@ -10,6 +10,7 @@
 //    strip's rows in shared memory (M^-1 = Mx^-1 (x) My^-1, Eq. 14);
 //  * the y-direction sweep: one thread per column, coalesced row access,
 //    adding the rows the strip above spilled, and accumulating int S.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -348,20 +349,21 @@ ADS_D float frac_div<float>(float a, float b) { return __fdividef(a, b); }
 template <typename T, int MODE, int NS>
 __global__ void __launch_bounds__(kQuadThreads, sizeof(T) == 4 ? 2 : 1)
     k_quad_xsweep_2d(QuadArgs<T> a, int re, int xchunk, T* __restrict__ Xm, T* __restrict__ Xs,
-                     int ldx, double* src_part) {
+                     int ldx, double* src_part, int nstrip, int csz) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   T* acc = reinterpret_cast<T*>(smraw);  // [re + 2][nb]
   const int nb = a.nb, n = a.n, n1 = n + 1, tid = threadIdx.x, lane = tid & 31;
   const int nwarp = blockDim.x >> 5;
   const int b = blockIdx.x;
-  const int e0 = b * re, e1 = min(e0 + re, n);
-  const int nrows = e1 - e0 + 2;
+  const bool real = b < nstrip;  // the grid is padded to whole clusters
+  const int e0 = b * re, e1 = real ? min(e0 + re, n) : e0;
+  const int nrows = real ? e1 - e0 + 2 : 0;
   const T h2 = a.h * a.h;
   const T dt = MODE == 0 ? (T)(*a.dt) : T(0);
   const T dtphi_c = MODE == 0 ? dt / a.phi_c : T(0);
   CompSum<T> src;
-  const int ngroups = (nb + kQuadCols - 1) / kQuadCols;
+  const int ngroups = real ? (nb + kQuadCols - 1) / kQuadCols : 0;
   for (int g = tid >> 5; g < ngroups; g += nwarp) {
     const int ex = g * kQuadCols - 2 + lane;  // element column of this lane = its DOF column
     const bool live = ex >= 0 && ex < n;
@@ -542,15 +544,43 @@ __global__ void __launch_bounds__(kQuadThreads, sizeof(T) == 4 ? 2 : 1)
     }
   }
   __syncthreads();
-  sweep_lines_smem<T>(acc, nrows, nb, nb, xchunk, a.ax.l1, a.ax.l2, a.ax.dinv);
+  if (real) sweep_lines_smem<T>(acc, nrows, nb, nb, xchunk, a.ax.l1, a.ax.l2, a.ax.dinv);
+  // The two rows after the strip's own (DOF rows e1, e1 + 1) are the first
+  // two rows of strip b + 1.  Within a cluster they are added into the next
+  // CTA's rows through distributed shared memory (after both x sweeps; the
+  // sweep is linear, and own + shared is the one addition the y sweep would
+  // do), so only the last strip of a cluster spills them to Xs, pair m of Xs
+  // for cluster m.
   const int own = e1 - e0;
-  for (int r = 0; r < nrows; ++r) {
-    T* dst = (r < own || e1 == n) ? Xm + (size_t)(e0 + r) * ldx : Xs + ((size_t)b * 2 + (r - own)) * ldx;
+  const bool shared_rows = real && e1 < n;
+  const int q = b % csz;
+  const bool to_next = shared_rows && q + 1 < csz;
+  const bool from_prev = real && q > 0;  // rows 0, 1 receive the previous strip's part
+  auto put = [&](int r) {
+    const bool spill = r >= own && shared_rows;
+    if (spill && to_next) return;
+    T* dst = spill ? Xs + ((size_t)(b / csz) * 2 + (r - own)) * ldx : Xm + (size_t)(e0 + r) * ldx;
     for (int k = tid; k < nb; k += blockDim.x) dst[k] = acc[(size_t)r * nb + k];
+  };
+  // rows no other CTA touches go out first, under the wait for the cluster
+  for (int r = from_prev ? 2 : 0; r < nrows; ++r)
+    if (!(r >= own && shared_rows && to_next)) put(r);
+  if (csz > 1) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (to_next) {
+      T* nxt = cl.map_shared_rank(acc, (int)cl.block_rank() + 1);
+      for (int j = 0; j < 2; ++j)
+        for (int k = tid; k < nb; k += blockDim.x) nxt[(size_t)j * nb + k] += acc[(size_t)(own + j) * nb + k];
+    }
+    cl.sync();
   }
+  if (from_prev)
+    for (int r = 0; r < 2 && r < nrows; ++r) put(r);
   if (MODE == 0) {
     const double tot = block_sum(src.value(), red);
-    if (tid == 0) src_part[b] = tot;
+    if (tid == 0 && real) src_part[b] = tot;
   }
 }
 
@@ -559,6 +589,8 @@ int quad_rows(int n, size_t esize) {
   // one SM's shared memory, else 2
   return (size_t)6 * (n + 2) * esize <= 110 * 1024 ? 4 : 2;
 }
+
+int quad_cluster(int re) { return re == 4 ? 2 : (re == 2 ? 4 : 1); }
 
 int quad_blocks(int dim, int n, int re) {
   if (dim == 2) return (n + re - 1) / re;
@@ -573,20 +605,36 @@ static int xsweep_chunk(int nrows, int nb) {
   return ch;
 }
 
+template <typename K, typename T>
+static cudaError_t quad_launch_one(K k, const QuadArgs<T>& a, int re, int xch, T* Xm, T* Xs, int ldx,
+                                   double* src_part, size_t smem, cudaStream_t st) {
+  const int nblk = quad_blocks(2, a.n, re), csz = quad_cluster(re);
+  smem_optin(k);
+  if (csz == 1) {
+    k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part, nblk, 1);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((nblk + csz - 1) / csz * csz));
+  cfg.blockDim = dim3(kQuadThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)csz;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a, re, xch, Xm, Xs, ldx, src_part, nblk, csz);
+}
+
 template <typename T, int MODE>
 static cudaError_t quad_launch(const QuadArgs<T>& a, int re, int xch, T* Xm, T* Xs, int ldx,
                                double* src_part, size_t smem, cudaStream_t st) {
-  const int nblk = quad_blocks(2, a.n, re);
-  if (a.n_src <= 2) {
-    auto k = k_quad_xsweep_2d<T, MODE, 2>;
-    smem_optin(k);
-    k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
-  } else {
-    auto k = k_quad_xsweep_2d<T, MODE, kMaxSrc>;
-    smem_optin(k);
-    k<<<nblk, kQuadThreads, smem, st>>>(a, re, xch, Xm, Xs, ldx, src_part);
-  }
-  return cudaGetLastError();
+  if (a.n_src <= 2)
+    return quad_launch_one(k_quad_xsweep_2d<T, MODE, 2>, a, re, xch, Xm, Xs, ldx, src_part, smem, st);
+  return quad_launch_one(k_quad_xsweep_2d<T, MODE, kMaxSrc>, a, re, xch, Xm, Xs, ldx, src_part, smem, st);
 }
 
 template <typename T>
@@ -826,10 +874,11 @@ __device__ __forceinline__ float ysweep_column(float (&v)[RB], const float2* fw,
 // forward and backward substitutions, the int S partials and the stores run
 // from registers.  Away from the ends of the mesh the factors of the
 // uniform-knot mass matrix settle to one value; tiles whose factors all equal
-// it take them from registers.  M and H are multiples of RE: every tile starts
-// on a strip boundary, so its strip-shared rows are fixed by the row index
-// alone, and the spill box starts at the spill row of the tile's first strip
-// (rows before the first or after the last spill row read as zero).
+// it take them from registers.  RE is the period of the spill rows (the
+// quadrature's strip height times its cluster size); M and H are multiples of
+// RE, so the spill rows of a tile are fixed by the row index alone, and the
+// spill box starts at the spill pair of the tile's first period (rows before
+// the first or after the last spill row read as zero).
 template <int RE, int NST>
 __global__ void __launch_bounds__(YTile<float>::CW, 3 - NST)
     k_ysweep_reg_2d(const __grid_constant__ CUtensorMap xm_map, const __grid_constant__ CUtensorMap xs_map,
@@ -972,16 +1021,17 @@ struct YRegCfg {
   int nst = 0, cps = 0;
   size_t smem = 0;
 };
-static YRegCfg ysweep_reg_cfg(int re) {
-  static YRegCfg memo[5];
-  static bool done[5] = {false, false, false, false, false};
+// per: the period of the spill rows (strip height times the quadrature's
+// cluster size), 8 for the strips the quadrature uses
+static YRegCfg ysweep_reg_cfg(int per) {
+  static YRegCfg memo;
+  static bool done = false;
   YRegCfg c;
-  if (re != 2 && re != 4) return c;
-  if (done[re]) return memo[re];
-  const int sb = yspill_rows(ytile_rows<float>(), re);
+  if (per != 8) return c;
+  if (done) return memo;
+  const int sb = yspill_rows(ytile_rows<float>(), per);
   for (int nst = 1; nst <= 2; ++nst) {
-    auto k = re == 4 ? (nst == 2 ? k_ysweep_reg_2d<4, 2> : k_ysweep_reg_2d<4, 1>)
-                     : (nst == 2 ? k_ysweep_reg_2d<2, 2> : k_ysweep_reg_2d<2, 1>);
+    auto k = nst == 2 ? k_ysweep_reg_2d<8, 2> : k_ysweep_reg_2d<8, 1>;
     smem_optin(k);
     const size_t smem = ysweep_reg_smem(sb, nst);
     int cps = 0;
@@ -997,8 +1047,8 @@ static YRegCfg ysweep_reg_cfg(int re) {
       c.smem = smem;
     }
   }
-  memo[re] = c;
-  done[re] = true;
+  memo = c;
+  done = true;
   return c;
 }
 
@@ -1006,7 +1056,8 @@ int ysweep_blocks(int n, size_t esize) {
   int gx, gy;
   if (esize == sizeof(float)) {
     ysweep_grid<float>(n, &gx, &gy);
-    const YRegCfg c = ysweep_reg_cfg(quad_rows(n, esize));
+    const int re = quad_rows(n, esize);
+    const YRegCfg c = ysweep_reg_cfg(re * quad_cluster(re));
     if (c.kernel) return gx * gy < c.cps * device_sms() ? gx * gy : c.cps * device_sms();  // persistent
     return gx * gy;
   }
@@ -1066,8 +1117,11 @@ cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs
     return cudaErrorInvalidValue;
   constexpr int RB = ytile_rows<T>(), CW = YTile<T>::CW;
   const int nb = a.nb;
-  const int nstrip = (a.n + re - 1) / re, nsp = 2 * (nstrip - 1);
-  const int sb = yspill_rows(RB, re);
+  // the quadrature's clusters of csz strips leave one spill pair per cluster:
+  // DOF rows q per + {0, 1} (q >= 1) take Xs rows 2 (q - 1) + {0, 1}
+  const int csz = quad_cluster(re), per = re * csz;
+  const int nstrip = (a.n + re - 1) / re, ncl = (nstrip + csz - 1) / csz, nsp = 2 * (ncl - 1);
+  const int sb = yspill_rows(RB, per);
   if (sb > 256) return cudaErrorInvalidValue;
   CUtensorMap xm_map, xs_map;
   cudaError_t err = tile_map<T>(Xm, nb, nb, ldx, RB, CW, &xm_map);
@@ -1078,7 +1132,7 @@ cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs
   int gx, gy;
   ysweep_grid<T>(a.n, &gx, &gy);
   if constexpr (sizeof(T) == sizeof(float)) {
-    const YRegCfg c = ysweep_reg_cfg(re);
+    const YRegCfg c = ysweep_reg_cfg(per);
     if (re == quad_rows(a.n, sizeof(T)) && c.kernel) {
       if (!a.ax.ytab) return cudaErrorInvalidValue;
       const int ntile = gx * gy, grid = ysweep_blocks(a.n, sizeof(T));
@@ -1092,7 +1146,7 @@ cudaError_t launch_ysweep(const QuadArgs<T>& a, int re, const T* Xm, const T* Xs
   const size_t smem = ysweep_smem<T>(sb);
   auto k = k_ysweep_2d<T>;
   smem_optin(k);
-  k<<<dim3(gx, gy), CW, smem, st>>>(xm_map, xs_map, a.n, re, nsp, sb, out, a.ax.l1, a.ax.l2,
+  k<<<dim3(gx, gy), CW, smem, st>>>(xm_map, xs_map, a.n, per, nsp, sb, out, a.ax.l1, a.ax.l2,
                                     a.ax.dinv, a.ax.Iw, mass_part, flags);
   return cudaGetLastError();
 }

@@ -71,6 +71,11 @@ template <typename T>
 cudaError_t launch_zsolve(const QuadArgs<T>& a, T* X, double* mass_part, cudaStream_t st);
 int quad_rows(int n, size_t esize);  // element rows per strip of the 2D quadrature
 int quad_blocks(int dim, int n, int re);
+// strips per thread-block cluster of the 2D quadrature: a cluster adds the
+// rows its strips share through distributed shared memory, so only one pair of
+// spill rows per cluster (every re * quad_cluster(re) = 8 rows for re = 2, 4)
+// goes through Xs
+int quad_cluster(int re);
 int ysolve_blocks(int dim, int n);       // partial-sum slots (largest layout of either precision)
 // packed FP32 factor rows for the 2D y sweep, built once per mesh from the
 // FP32 LDL^T factors
@@ -200,7 +205,7 @@ struct MlpTcArgs {
 // Gram solve by sine transforms computed with FFTs (2D, N a power of two,
 // 8 <= N <= 2048): tables, partial count of the loss, and the three passes
 bool gram_fft_supported(int dim, int N);
-int gram_fft_dot_parts(int N);
+int gram_fft_dot_parts(int N, int dim = 2);
 template <typename T>
 cudaError_t gram_fft_tables(int N, T* tw /*4N: 2N complex twiddles*/, T* lam /*N-1*/);
 // pass 0 with u != nullptr first computes RES = A u + h^2 f (written to
@@ -209,6 +214,13 @@ template <typename T>
 cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const T* tw, const T* lam,
                             T h2, double* dot_part, cudaStream_t st, const T* u = nullptr,
                             const T* alpha = nullptr, const T* f = nullptr, T* res_out = nullptr);
+
+// 3D: pass 0 = the x and y transforms of res into work, pass 2 = the inverse
+// transforms of work into z (times h^2 (2/N)^2) with the loss partials; the
+// z tridiagonal solves in between are the caller's (launch_tridiag_cols)
+template <typename T>
+cudaError_t launch_gram_fft3d(int pass, int N, const T* res, T* work, T* z, const T* tw, T h2,
+                              double* dot_part, cudaStream_t st);
 
 // the whole FP32 Gram solve (residual, the three transform passes, the
 // partials of RES^T z, one per CTA) in one thread-block cluster, 8 <= N <= 128
