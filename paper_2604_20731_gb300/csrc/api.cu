@@ -374,7 +374,17 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
                              (const TC*)c->u, (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr,
                              c->stream));
   }
-  if (c->dim == 3) {
+  if (c->dim == 3 && c->gram_fft) {
+    // G^-1 r: FFT sine transforms along x (all (z, y) rows) and y (every
+    // plane), shifted tridiagonal sweeps along z, inverse transforms with the
+    // loss partials
+    LK(2, launch_gram_fft3d<TC>(0, c->N, (const TC*)c->res, (TC*)c->rhat, (TC*)c->z, (const TC*)c->gtw,
+                                h * h, c->dot_part, c->stream));
+    LK(3, launch_tridiag_cols<TC>(m, m * m, (const TC*)c->invd, (TC*)c->rhat, c->stream));
+    LK(4, launch_gram_fft3d<TC>(2, c->N, (const TC*)c->res, (TC*)c->rhat, (TC*)c->z, (const TC*)c->gtw,
+                                h * h, c->dot_part, c->stream));
+    c->nlaunch += 2;
+  } else if (c->dim == 3) {
     // G^-1 r: sine transforms along x (one GEMM over all (z, y) rows) and y
     // (batched over z), shifted tridiagonal sweeps along z, inverse transforms
     const long long mm = (long long)m * m;
@@ -409,7 +419,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
                           h * h, (const TC*)c->res, c->dot_part, c->stream));
   }
   const int nparts = c->dim == 3 ? gemm_blocks(m * m, m)
-                                 : (c->gram_fft ? (gram_in_cluster(c) ? c->gcs.CL : gram_fft_dot_parts(c->N))
+                                 : (c->gram_fft ? (gram_in_cluster(c) ? c->gcs.CL : gram_fft_dot_parts(c->N, c->dim))
                                                 : gemm_blocks(m, m));
   LossFin lf{c->dot_part, nparts, c->loss, c->loss_log, c->t, c->bc, c->flags, upd};
   LK(5, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha, (const TC*)c->z,
@@ -1060,7 +1070,10 @@ ads_status ads_init_with_allocator(const ads_params* params, const crvpinn_param
                                 : gram_fft_tables<float>(c->N, (float*)c->gtw, (float*)c->glam);
       if (e != cudaSuccess) return bail(fail(c, ADS_ERR_CUDA, "gram tables"));
       if (c->tc != ADS_F64 && c->dim == 2) c->gcs = gram_cluster_shape(c->N);
-    } else {
+    }
+    if (!c->gram_fft || c->dim == 3) {
+      // the dense sine matrix and the shifted tridiagonal pivots (3D: the z
+      // sweeps of the FFT route too)
       double *S64 = nullptr, *inv64 = nullptr;
       const size_t npiv = (size_t)m * m * (c->dim == 3 ? m : 1);
       AL(S64, (size_t)m * m);
@@ -1079,7 +1092,7 @@ ads_status ads_init_with_allocator(const ads_params* params, const crvpinn_param
     }
     {
       const int ng = gemm_blocks(c->dim == 3 ? c->m1 * c->m1 : c->m1, c->m1);
-      int nf = c->gram_fft ? gram_fft_dot_parts(c->N) : 0;
+      int nf = c->gram_fft ? gram_fft_dot_parts(c->N, c->dim) : 0;
       if (c->gcs.CL > nf) nf = c->gcs.CL;
       AL(c->dot_part, (size_t)(ng > nf ? ng : nf) + 1);
     }

@@ -134,15 +134,16 @@ __device__ __forceinline__ T residual_at(const ResidualIn<T>& q, int N, int jj, 
   return r + q.h2 * q.f[t];
 }
 
-// D along x for rows [r0, r0 + 2P) of `in` into `out` (rows 2p and 2p + 1 of
-// the CTA share line p).  With rin.u set, the rows are first computed as
-// RES = A u + h^2 f and written to rin.res.  With dotw != nullptr, also a
-// partial of sum dotw * out over the CTA's rows.
+// D along x for rows [r0, r0 + 2P) of the nrows rows of `in` into `out`,
+// times `scale` (rows 2p and 2p + 1 of the CTA share line p).  With rin.u
+// set (2D), the rows are first computed as RES = A u + h^2 f and written to
+// rin.res.  With dotw != nullptr, also a partial of sum dotw * out over the
+// CTA's rows.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
     k_dst_rows(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int P,
                const Cx<T>* __restrict__ tw, const T* __restrict__ dotw, double* dot_part,
-               ResidualIn<T> rin) {
+               ResidualIn<T> rin, int nrows, T scale) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int L = 1 << lg, m = N - 1;
   Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
@@ -166,14 +167,14 @@ __global__ void __launch_bounds__(kFftThreads)
       for (int q = 0; q < KB; ++q) {
         const int idx = b0 + q * blockDim.x + threadIdx.x;
         const int rr = idx / m, ii = idx - rr * m, row = r0 + rr;
-        v[q] = (idx < tot && row < m) ? residual_at(rin, N, row, ii) : T(0);
+        v[q] = (idx < tot && row < nrows) ? residual_at(rin, N, row, ii) : T(0);
       }
 #pragma unroll
       for (int q = 0; q < KB; ++q) {
         const int idx = b0 + q * blockDim.x + threadIdx.x;
         const int rr = idx / m, ii = idx - rr * m, row = r0 + rr;
         if (idx < tot) {
-          if (row < m) rin.res[(size_t)row * m + ii] = v[q];
+          if (row < nrows) rin.res[(size_t)row * m + ii] = v[q];
           stage[idx] = v[q];
         }
       }
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kFftThreads)
       for (int q = 0; q < KB; ++q) {
         const int idx = b0 + q * blockDim.x + threadIdx.x;
         const int rr = idx / m, ii = idx - rr * m;
-        v[q] = (idx < tot && r0 + rr < m) ? src[soff + (size_t)rr * sstride + ii] : T(0);
+        v[q] = (idx < tot && r0 + rr < nrows) ? src[soff + (size_t)rr * sstride + ii] : T(0);
       }
 #pragma unroll
       for (int q = 0; q < KB; ++q) {
@@ -222,15 +223,15 @@ __global__ void __launch_bounds__(kFftThreads)
     for (int q = 0; q < KB; ++q) {
       const int idx = b0 + q * blockDim.x + threadIdx.x;
       const int rr = idx / m, ii = idx - rr * m, row = r0 + rr;
-      w[q] = (dotw && idx < tot && row < m) ? dotw[(size_t)row * m + ii] : T(0);
+      w[q] = (dotw && idx < tot && row < nrows) ? dotw[(size_t)row * m + ii] : T(0);
     }
 #pragma unroll
     for (int q = 0; q < KB; ++q) {
       const int idx = b0 + q * blockDim.x + threadIdx.x;
       const int rr = idx / m, k = idx - rr * m + 1, row = r0 + rr;
-      if (idx < tot && row < m) {
+      if (idx < tot && row < nrows) {
         const Cx<T> zk = z[((rr >> 1) << lg) + k];
-        const T v = (rr & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
+        const T v = scale * ((rr & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im);
         out[(size_t)row * m + k - 1] = v;
         if (dotw) dot.add(v * w[q]);
       }
@@ -333,6 +334,55 @@ __global__ void __launch_bounds__(kFftThreads)
     const int col = c0 + c;
     const Cx<T> wk = w[((c >> 1) << lg) + k];
     if (col < m) data[(size_t)(k - 1) * m + col] = (c & 1) ? T(0.5) * wk.re : T(-0.5) * wk.im;
+  }
+}
+
+// 3D: D along y of columns [c0, c0 + 2P) of plane blockIdx.y of the m x m x m
+// grid ([z][y][x]), in place (columns 2p and 2p + 1 of the CTA share line p)
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    k_dst_cols(T* __restrict__ data, int N, int lg, int P, const Cx<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int L = 1 << lg, m = N - 1, C = 2 * P;
+  Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
+  Cx<T>* buf0 = tws + L;                       // [P][L]
+  Cx<T>* buf1 = buf0 + (size_t)P * L;          // [P][L]
+  const int c0 = blockIdx.x * C;
+  T* plane = data + (size_t)blockIdx.y * m * m;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
+  {
+    T* b0r = reinterpret_cast<T*>(buf0);
+    for (int idx = threadIdx.x; idx < C; idx += blockDim.x) {
+      const int line = idx >> 1, part = idx & 1;
+      b0r[2 * ((line << lg) + 0) + part] = T(0);
+      b0r[2 * ((line << lg) + N) + part] = T(0);
+    }
+    const int tot = C * m;
+    for (int b0 = 0; b0 < tot; b0 += KB * (int)blockDim.x) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        const int c = idx % C, j = idx / C, col = c0 + c;
+        v[q] = (idx < tot && col < m) ? plane[(size_t)j * m + col] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int idx = b0 + q * blockDim.x + threadIdx.x;
+        if (idx < tot) {
+          const int c = idx % C, j = idx / C, line = c >> 1, part = c & 1;
+          b0r[2 * ((line << lg) + j + 1) + part] = v[q];
+          b0r[2 * ((line << lg) + 2 * N - 1 - j) + part] = -v[q];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const Cx<T>* z = fft_stockham(buf0, buf1, P, lg, tws);
+  for (int idx = threadIdx.x; idx < C * m; idx += blockDim.x) {
+    const int c = idx % C, k = idx / C + 1, col = c0 + c;
+    const Cx<T> zk = z[((c >> 1) << lg) + k];
+    if (col < m) plane[(size_t)(k - 1) * m + col] = (c & 1) ? T(0.5) * zk.re : T(-0.5) * zk.im;
   }
 }
 
@@ -599,13 +649,15 @@ cudaError_t launch_gram_cluster(const GramClusterShape& sh, int N, const float* 
 
 bool gram_fft_supported(int dim, int N) {
   const int lg = log2_exact(N);
+  if (dim == 3) return lg >= 3 && lg <= 9;  // N <= 512 (the 3D mesh limit)
   return dim == 2 && lg >= 3 && lg <= 11;  // L = 2N <= 4096
 }
 
-int gram_fft_dot_parts(int N) {
-  const int m = N - 1, P = lines_per_cta<double>(2 * N, 1);  // the row kernel's grid (FP64 bound)
+int gram_fft_dot_parts(int N, int dim) {
+  const int m = N - 1, rows = dim == 3 ? m * m : m;
+  const int P = lines_per_cta<double>(2 * N, 1);  // the row kernel's grid (FP64 bound)
   const int Pf = lines_per_cta<float>(2 * N, 1);
-  const int g = (m + 2 * P - 1) / (2 * P), gf = (m + 2 * Pf - 1) / (2 * Pf);
+  const int g = (rows + 2 * P - 1) / (2 * P), gf = (rows + 2 * Pf - 1) / (2 * Pf);
   return g > gf ? g : gf;
 }
 
@@ -652,15 +704,48 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
     ResidualIn<T> rin{nullptr, nullptr, nullptr, T(0), nullptr};
     if (pass == 0) {
       if (u) rin = ResidualIn<T>{u, alpha, f, h2, res_out};
-      k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, P, twc, nullptr, nullptr, rin);
+      k<<<g, kFftThreads, smem, st>>>(res, work, N, lg, P, twc, nullptr, nullptr, rin, m, T(1));
     } else {
-      k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, P, twc, res, dot_part, rin);
+      k<<<g, kFftThreads, smem, st>>>(work, z, N, lg, P, twc, res, dot_part, rin, m, T(1));
     }
   }
   return cudaGetLastError();
 }
 
+// 3D (G = h^-2 (T (+) T (+) T)): pass 0: work = D_y D_x res (rows, then the
+// columns of every plane); pass 2: z = h^2 (2/N)^2 D_x D_y work and the
+// partials of res^T z.  Between them the caller solves the shifted
+// tridiagonal systems along z for every (ky, kx) mode in place.
+template <typename T>
+cudaError_t launch_gram_fft3d(int pass, int N, const T* res, T* work, T* z, const T* tw, T h2,
+                              double* dot_part, cudaStream_t st) {
+  const int lg = log2_exact(N) + 1, L = 2 * N, m = N - 1;
+  if (lg < 4 || lg > 10) return cudaErrorInvalidValue;
+  const Cx<T>* twc = reinterpret_cast<const Cx<T>*>(tw);
+  const int Pr = lines_per_cta<T>(L, 1), Pc = lines_per_cta<T>(L, 2);
+  auto kr = k_dst_rows<T>;
+  auto kc = k_dst_cols<T>;
+  smem_optin(kr);
+  smem_optin(kc);
+  const int gr = (m * m + 2 * Pr - 1) / (2 * Pr);
+  const dim3 gc((m + 2 * Pc - 1) / (2 * Pc), m);
+  const ResidualIn<T> rin{nullptr, nullptr, nullptr, T(0), nullptr};
+  if (pass == 0) {
+    kr<<<gr, kFftThreads, fft_smem<T>(L, Pr), st>>>(res, work, N, lg, Pr, twc, nullptr, nullptr, rin, m * m, T(1));
+    kc<<<gc, kFftThreads, fft_smem<T>(L, Pc), st>>>(work, N, lg, Pc, twc);
+  } else {
+    kc<<<gc, kFftThreads, fft_smem<T>(L, Pc), st>>>(work, N, lg, Pc, twc);
+    const T s = h2 * T(4.0 / ((double)N * N));  // h^2 (2 / N)^2
+    kr<<<gr, kFftThreads, fft_smem<T>(L, Pr), st>>>(work, z, N, lg, Pr, twc, res, dot_part, rin, m * m, s);
+  }
+  return cudaGetLastError();
+}
+
 template cudaError_t gram_fft_tables<float>(int, float*, float*);
+template cudaError_t launch_gram_fft3d<float>(int, int, const float*, float*, float*, const float*, float,
+                                              double*, cudaStream_t);
+template cudaError_t launch_gram_fft3d<double>(int, int, const double*, double*, double*, const double*,
+                                               double, double*, cudaStream_t);
 template cudaError_t gram_fft_tables<double>(int, double*, double*);
 template cudaError_t launch_gram_fft<float>(int, int, const float*, float*, float*, const float*,
                                             const float*, float, double*, cudaStream_t, const float*,

@@ -96,7 +96,9 @@ def _crv3(n, dtype, width=64, seed=21):
     return sc, s, crv, theta, alpha, f
 
 
-@pytest.mark.parametrize("n", [3, 6, 9])
+# 8 and 16 are powers of two: the Gram solve takes the FFT sine transforms
+# (the others the dense transforms)
+@pytest.mark.parametrize("n", [3, 6, 8, 9, 16])
 def test_coefficients_loss_gradient_3d_fp64(n):
     sc, s, crv, theta, alpha, f = _crv3(n, "f64")
     assert rel_inf(s.get("ALPHA").ravel(), alpha.ravel()) <= 1e-13
@@ -111,10 +113,11 @@ def test_coefficients_loss_gradient_3d_fp64(n):
     s.close()
 
 
+@pytest.mark.parametrize("n", [17, 32])  # 32: the FFT route
 @pytest.mark.parametrize("dtype,width,tol_loss,tol_grad", [("f32", 64, 1e-3, 2e-2), ("f32", 128, 1e-3, 2e-2),
                                                             ("bf16", 64, 1e-2, 2e-2)])
-def test_loss_gradient_3d_reduced_precision(dtype, width, tol_loss, tol_grad):
-    sc, s, crv, theta, alpha, f = _crv3(17, dtype, width=width)
+def test_loss_gradient_3d_reduced_precision(dtype, width, tol_loss, tol_grad, n):
+    sc, s, crv, theta, alpha, f = _crv3(n, dtype, width=width)
     loss = s.loss_grad()
     ref_loss, ref_grad, _ = crv.loss_grad(MLP(3, width, 4), theta, alpha, f, gram="fd")
     assert loss == pytest.approx(ref_loss, rel=tol_loss)
