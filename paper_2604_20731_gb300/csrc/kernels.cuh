@@ -193,6 +193,7 @@ struct MlpTcArgs {
   unsigned char* acts;    // BF16 activations, [tile][4][128 x width] core-matrix tiles (nullable)
   unsigned char* wimage;  // forward: weight image, mlp_tc_fwd_image_bytes(width), 16-byte aligned;
                           // rewritten from theta by every forward launch
+  int* wimage_ctr = nullptr;  // forward: tile-group counter at the end of the image (set by the launcher)
   const float* gu;        // [npts] dL/du
   float* gpart;           // [nblk][nparams]
   int nparams;
