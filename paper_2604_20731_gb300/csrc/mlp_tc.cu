@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(256) k_stage_fwd(const float* __restrict__ th,
   constexpr int KC = L::KC, RG = (KC / 8) * 128, APR = KC / 8, NA = 3 * W * APR, NV = L::VEC_SZ / 4;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
   const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e == 0) *reinterpret_cast<int*>(img + L::IMG) = 0;  // the forward's tile-group counter
   if (e < NA) {
     const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
     const float* Wl = th + o2 + l * (W * W + W);
@@ -473,6 +474,7 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
   uint64_t* mb_prod = mb_ready + NS;  // [NS] a slot's products complete (issuer commit)
   uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + L::BAR + 48);
   volatile int* abort_flag = reinterpret_cast<int*>(sm + L::BAR + 52);
+  volatile int* group = reinterpret_cast<int*>(sm + L::BAR + 56);  // the current tile group
   float* upart = reinterpret_cast<float*>(sm + L::UPART);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool epi = tid < kFwdEpi;
@@ -514,7 +516,6 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
   tc_fence_after();
   const uint32_t tmem = *tbase;
   const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
-  const int G = gridDim.x;
   if (!epi) {
     // ---------------- issuing thread ----------------
     if (lane == 0) {
@@ -528,17 +529,26 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
         issued[s] = 0;
       }
       bool ok = mbar_wait(mb_wt, 0);
-      for (int tb = blockIdx.x; ok && tb < ntiles; tb += NS * G) {
+      while (ok) {
+        // slot 0's first operands announce the tile group (or the end)
+        if (*abort_flag || !mbar_wait(mb_ready, ph_ready[0])) {
+          ok = false;
+          break;
+        }
+        ph_ready[0] ^= 1;
+        const int t0 = NS * *group;
+        if (t0 >= ntiles) break;
         for (int l = 0; ok && l < 3; ++l) {
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
-            if (!ok || tb + s * G >= ntiles) continue;
-            if (*abort_flag || !mbar_wait(mb_ready + s, ph_ready[s])) {
-              *abort_flag = 1;
-              ok = false;
-              continue;
+            if (!ok || t0 + s >= ntiles) continue;
+            if (l > 0 || s > 0) {
+              if (*abort_flag || !mbar_wait(mb_ready + s, ph_ready[s])) {
+                ok = false;
+                continue;
+              }
+              ph_ready[s] ^= 1;
             }
-            ph_ready[s] ^= 1;
             tc_fence_after();
             // [a_hi | 1 1] [s W | s b_hi s b_lo]^T + a_lo (s W)^T: two BF16
             // chains into the slot's FP32 accumulator
@@ -575,8 +585,18 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
       __syncwarp();
       if (lane == 0) mbar_arrive1(mb_ready + s);
     };
+    // tile groups (NS adjacent tiles) come from a counter shared by the
+    // launch, so that the CTAs on an SM finish together however the warps
+    // are scheduled; thread 0 takes the next group while the current one runs
+    if (tid == 0) *group = atomicAdd(a.wimage_ctr, 1);
+    epi_barrier_any(false);
     int pass = 0;
-    for (int tb = blockIdx.x; tb < ntiles; tb += NS * G, ++pass) {
+    for (;; ++pass) {
+      const int tb = NS * *group;
+      if (tb >= ntiles) {
+        ready(0);  // tells the issuer that there is no further group
+        break;
+      }
       int p0[NS];
       bool valid[NS];
       unsigned char* gt[NS];
@@ -585,7 +605,7 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
       // pairs of units
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        const int tile = tb + s * G;
+        const int tile = tb + s;
         valid[s] = tile < ntiles;  // CTA-uniform
         p0[s] = (a.tile0 + tile) * kTP;
         gt[s] = nullptr;
@@ -663,11 +683,14 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
         }
       }
       // the two halves of each slot's output-layer sums (double-buffered by
-      // pass); the barrier also makes the stop decision the same everywhere
+      // pass); the barrier also publishes the next group and makes the stop
+      // decision the same everywhere.  (The issuer read this pass's group
+      // before it issued the products these epilogues waited for.)
       float* up = upart + (pass & 1) * NS * kTP;
 #pragma unroll
       for (int s = 0; s < NS; ++s)
         if (half) up[s * kTP + row] = u2[s].x + u2[s].y;
+      if (tid == 0) *group = atomicAdd(a.wimage_ctr, 1);
       const bool stop = epi_barrier_any(*abort_flag != 0);
 #pragma unroll
       for (int s = 0; s < NS; ++s)
@@ -1365,12 +1388,14 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
   if (want < grid) grid = want > 0 ? want : 1;
-  k<<<grid, kFwdThreads, smem, st>>>(a);
+  MlpTcArgs b = a;
+  b.wimage_ctr = reinterpret_cast<int*>(a.wimage + L::IMG);
+  k<<<grid, kFwdThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 
 size_t mlp_tc_fwd_image_bytes(int width) {
-  return width == 64 ? TcSmemF<64>::IMG : TcSmemF<128>::IMG;
+  return (width == 64 ? TcSmemF<64>::IMG : TcSmemF<128>::IMG) + 16;  // + the tile-group counter
 }
 
 cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a0, cudaStream_t st) {
