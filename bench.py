@@ -65,6 +65,7 @@ def args_parse():
     ap.add_argument("--only-saturation", action="store_true",
                     help="run only the saturation-kernel block (a profiling aid) and print it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true", help="skip the stated-error measurement")
     ap.add_argument("--profile-iters", type=int, default=30)
     return ap.parse_args()
 
@@ -756,7 +757,7 @@ def run_ours(a, world, rank, local):
     #    network trained for `err_iters` iterations, then `err_steps` hybrid
     #    steps, BF16 and FP32 networks side by side.
     err = None
-    if rank == 0:
+    if rank == 0 and not a.no_error:
         err = stated_error(a, mix, sizes, ctxs, hp, theta0, scn, HybridSolver)
 
     # ---- roofline of the dominant kernel of the mix (live CUDA events) ----
