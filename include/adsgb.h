@@ -436,14 +436,18 @@ ads_status ads_saturation_step_noalloc_status(void* stream, int* flags_out);
 /* ---- diagnostics (no counterpart in the paper) ------------------------------
  * ads_kernel_launches: number of library kernels enqueued on this context so
  * far (a graph replay counts the kernels it contains).
- * ads_profile_train: run `iters` Adam iterations without a graph, each kernel
- * bracketed by CUDA events on the context's stream; ms_out[8] receives the
+ * ads_profile_train: one Adam iteration with CUDA event records between its
+ * kernels is captured into a graph, which is launched `iters` times on the
+ * context's stream (the kernels run back to back, as in the hybrid step's
+ * graphs); ms_out[8] receives the
  * average duration of: network forward, residual, sine transform, tridiagonal
  * sweeps, inverse transform (+ loss partials), adjoint stencil (+ loss
  * finalise), network backward, gradient sum + Adam.  Updates the parameters like
  * crvpinn_pressure_update at the learning rate last set.
- * ads_profile_saturation: `steps` saturation steps (current dt) likewise;
- * ms_out[3]: quadrature + x sweep, y sweep, mass bookkeeping. */
+ * ads_profile_saturation: one saturation step (current dt) captured likewise
+ * and launched `steps` times (each launch repeats the same step from the same
+ * state; afterwards the state is one step on); ms_out[3]: quadrature + x
+ * sweep, y sweep, mass bookkeeping. */
 ads_status ads_kernel_launches(const ads_ctx* ctx, unsigned long long* count);
 /* ads_probe_wait_expiry: runs, on the context's stream, one kernel that waits
  * on an mbarrier the way every kernel here does -- bounded, with tensor

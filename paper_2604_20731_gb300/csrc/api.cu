@@ -132,13 +132,20 @@ ads_status allocT(ads_ctx* c, X** p, size_t count) {
   return alloc(c, reinterpret_cast<void**>(p), count * sizeof(X));
 }
 
+// a profiling event on the context's stream; the profiles capture their
+// iteration into a graph, where the record must become a node of its own
+#define PROF(k)                                                                                  \
+  do {                                                                                           \
+    if (c->prof) cudaEventRecordWithFlags(c->prof[(k)], c->stream, cudaEventRecordExternal);    \
+  } while (0)
+
 // enqueue one kernel: check, count, and bracket it with profiling events
-#define LK(k, ...)                                                        \
-  do {                                                                    \
-    if (c->prof) cudaEventRecord(c->prof[(k)], c->stream);                \
-    CK(__VA_ARGS__);                                                      \
-    if (c->prof) cudaEventRecord(c->prof[(k) + 1], c->stream);            \
-    c->nlaunch++;                                                         \
+#define LK(k, ...)         \
+  do {                     \
+    PROF(k);               \
+    CK(__VA_ARGS__);       \
+    PROF((k) + 1);         \
+    c->nlaunch++;          \
   } while (0)
 
 #define CA(...)                      \
@@ -368,7 +375,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   if (c->use_tc) c->nlaunch += kMlpTcFwdLaunches - 1;
   if (c->dim == 2 && c->gram_fft) {
     // the residual is computed inside the first transform pass
-    if (c->prof) cudaEventRecord(c->prof[1], c->stream);
+    PROF(1);
   } else {
     LK(1, launch_stencil<TC>(c->dim, c->N, TC(c->prm.kz_ratio), (const TC*)c->alpha,
                              (const TC*)c->u, (const TC*)c->f, h * h, TC(1), (TC*)c->res, nullptr,
@@ -404,7 +411,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
     LK(2, launch_gram_cluster(c->gcs, c->N, (const float*)c->u, (const float*)c->alpha,
                               (const float*)c->f, float(h * h), (float*)c->res, (float*)c->z,
                               (const float*)c->gtw, (const float*)c->glam, c->dot_part, c->stream));
-    if (c->prof) cudaEventRecord(c->prof[4], c->stream);
+    PROF(4);
   } else if (c->gram_fft) {
     for (int pass = 0; pass < 3; ++pass)
       LK(2 + pass, launch_gram_fft<TC>(pass, c->N, (const TC*)c->res, (TC*)c->rhat, (TC*)c->z,
@@ -427,7 +434,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
   if (c->use_tc && c->chunks > 1) {
     // activation recomputation: per chunk of tiles, a forward that stores the
     // chunk's activations, then its backward into its own partial rows
-    if (c->prof) cudaEventRecord(c->prof[6], c->stream);
+    PROF(6);
     for (int k = 0; k < c->chunks; ++k) {
       MlpTcArgs ka = mlp_tc_args(c, true);
       ka.tile0 = k * c->chunk_tiles;
@@ -437,7 +444,7 @@ ads_status enq_train_iter(ads_ctx* c, int upd) {
       CK(launch_mlp_bwd_tc(ka, c->nbwd, c->stream));
       c->nlaunch += kMlpTcFwdLaunches + 1;
     }
-    if (c->prof) cudaEventRecord(c->prof[7], c->stream);
+    PROF(7);
   } else {
     LK(6, launch_bwd<TC>(c));
   }
@@ -715,52 +722,61 @@ struct TrainRun {
   static ads_status go(ads_ctx* c, int iters) { return train<TC, TA>(c, iters, 1); }
 };
 
-template <typename TC>
-ads_status profile_train_t(ads_ctx* c, int iters, double* ms) {
-  const int NK = 8;
-  cudaEvent_t ev[NK + 1];
-  for (int k = 0; k <= NK; ++k) CK(cudaEventCreate(&ev[k]));
-  for (int k = 0; k < NK; ++k) ms[k] = 0.0;
-  ads_status st = ADS_OK;
-  for (int it = 0; it < iters && st == ADS_OK; ++it) {
-    c->prof = ev;
-    st = enq_train_iter<TC>(c, 1);
-    c->prof = nullptr;
-    if (st != ADS_OK) break;
+// Per-kernel times: one iteration (or sub-step) with event records between
+// its kernels is captured into a graph and replayed, so that the kernels run
+// back to back as the hybrid step's graphs run them (no host launch gaps
+// between the events); each replay is one more iteration (or the same
+// sub-step again).
+template <typename Enq>
+ads_status profile_graph(ads_ctx* c, int reps, int nk, double* ms, Enq enq) {
+  cudaEvent_t ev[9];
+  for (int k = 0; k <= nk; ++k) CK(cudaEventCreate(&ev[k]));
+  for (int k = 0; k < nk; ++k) ms[k] = 0.0;
+  const unsigned long long n0 = c->nlaunch;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  c->prof = ev;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  ads_status st = e == cudaSuccess ? enq(c) : ADS_ERR_CUDA;
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  c->prof = nullptr;
+  const unsigned long long nk_launch = c->nlaunch - n0;
+  c->nlaunch = n0;
+  if (st == ADS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (st == ADS_OK && e != cudaSuccess) st = fail(c, ADS_ERR_CUDA, std::string("profile graph: ") + cudaGetErrorString(e));
+  for (int it = 0; it < reps && st == ADS_OK; ++it) {
+    if ((e = cudaGraphLaunch(ex, c->stream)) != cudaSuccess) {
+      st = fail(c, ADS_ERR_CUDA, std::string("profile launch: ") + cudaGetErrorString(e));
+      break;
+    }
+    c->nlaunch += nk_launch;
     st = wait(c, kDefaultTimeout);
-    for (int k = 0; k < NK && st == ADS_OK; ++k) {
+    for (int k = 0; k < nk && st == ADS_OK; ++k) {
       float f = 0.f;
-      cudaEventElapsedTime(&f, ev[k], ev[k + 1]);
+      if ((e = cudaEventElapsedTime(&f, ev[k], ev[k + 1])) != cudaSuccess)
+        st = fail(c, ADS_ERR_CUDA, std::string("profile events: ") + cudaGetErrorString(e));
       ms[k] += f;
     }
   }
-  for (int k = 0; k <= NK; ++k) cudaEventDestroy(ev[k]);
-  for (int k = 0; k < NK; ++k) ms[k] /= (iters > 0 ? iters : 1);
+  cudaGetLastError();  // a failed call above leaves nothing for the next launch check
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  for (int k = 0; k <= nk; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < nk; ++k) ms[k] /= (reps > 0 ? reps : 1);
   return st;
+}
+
+template <typename TC>
+ads_status profile_train_t(ads_ctx* c, int iters, double* ms) {
+  return profile_graph(c, iters, 8, ms, [](ads_ctx* cc) { return enq_train_iter<TC>(cc, 1); });
 }
 
 template <typename TA>
 ads_status profile_sat_t(ads_ctx* c, int steps, double* ms) {
-  const int NK = 3;
-  cudaEvent_t ev[NK + 1];
-  for (int k = 0; k <= NK; ++k) CK(cudaEventCreate(&ev[k]));
-  for (int k = 0; k < NK; ++k) ms[k] = 0.0;
-  ads_status st = ADS_OK;
-  for (int it = 0; it < steps && st == ADS_OK; ++it) {
-    c->prof = ev;
-    st = enq_sat_steps<TA>(c, 1);
-    c->prof = nullptr;
-    if (st != ADS_OK) break;
-    st = wait(c, kDefaultTimeout);
-    for (int k = 0; k < NK && st == ADS_OK; ++k) {
-      float f = 0.f;
-      cudaEventElapsedTime(&f, ev[k], ev[k + 1]);
-      ms[k] += f;
-    }
-  }
-  for (int k = 0; k <= NK; ++k) cudaEventDestroy(ev[k]);
-  for (int k = 0; k < NK; ++k) ms[k] /= (steps > 0 ? steps : 1);
-  return st;
+  return profile_graph(c, steps, 3, ms, [](ads_ctx* cc) { return enq_sat_steps<TA>(cc, 1); });
 }
 
 // Galerkin pressure system assembled and solved for the current saturation

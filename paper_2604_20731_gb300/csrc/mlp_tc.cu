@@ -25,8 +25,8 @@
 // of a CTA's tiles):
 //   D_l (for dW_l, db_l) += Delta_l^T [a_{l-1} | 1] -- M = 64 output rows
 //   (width 64; the ring form for width 128 uses M = 128), N = 80 (64 inputs +
-//   the stored ones column giving db), K = 128 points, both operands
-//   MN-major views of the [point][feature] tiles;
+//   a ones column, appended in shared memory, giving db), K = 128 points,
+//   both operands MN-major views of the [point][feature] tiles;
 //   Delta_{l-1} = (Delta_l W_l) (1 - a_{l-1}^2) -- M = 128 points, N = 64,
 //   K = 64, W_l read MN-major from the backward's own weight tiles.
 //   The output layer is the same product with Delta_5 = [g, 0, ...] and the
@@ -51,19 +51,23 @@ ADS_D uint32_t core_off(int r, int c, int rg) {
   return (uint32_t)((r >> 3) * rg + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
 
-// Stored activations of a 128-point tile: a_1 .. a_4 one after another, each
-// in the core-matrix layout.  For width 64, a_1 .. a_3 carry 16 more columns,
-// [1, 0, ..., 0], so that the backward's weight-gradient product
-// Delta_L^T [a_{L-1} | 1] also gives the bias gradient: one N = 80 product per
-// k-step instead of an N = 64 and an N = 16 one.
-ADS_HD constexpr int act_cols(int W, int l) { return (W == 64 && l < 3) ? W + 16 : W; }
-ADS_HD constexpr int act_rg(int W, int l) { return (act_cols(W, l) / 8) * 128; }
-ADS_HD constexpr int act_off(int W, int l) {
-  int o = 0;
-  for (int i = 0; i < l; ++i) o += kTP * act_cols(W, i) * 2;
-  return o;
+// Stored activations of a 128-point tile (written by the forward, read by the
+// backward): a_1 .. a_4 one after another, [128][W] BF16 each, nothing else.
+// Width 128 keeps the core-matrix layout of the shared tiles (row groups
+// outermost).  Width 64 keeps each 8-column chunk's 128 rows together (2 KB
+// per chunk, 16 B per row), so that a warp's 32 rows of one chunk are 512
+// contiguous bytes, and so that the backward's shared copy of a_1 .. a_3 can
+// place two constant chunks, [1, 0, ..., 0] and zeros, behind the 64 columns
+// and read [a | 1] as one N = 80 operand whose product gives the bias
+// gradient with the weight gradient: the constant columns never travel
+// through HBM.
+ADS_HD constexpr int st_layer_bytes(int W) { return kTP * W * 2; }
+ADS_HD constexpr int st_tile_bytes(int W) { return 4 * st_layer_bytes(W); }
+constexpr int kChunk = kTP * 16;  // one 8-column chunk of a width-64 stored layer
+ADS_HD constexpr uint32_t st_off(int W, int r, int c) {
+  return W == 64 ? (uint32_t)((c >> 3) * kChunk + r * 16 + (c & 7) * 2)
+                 : (uint32_t)((r >> 3) * (W / 8) * 128 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
-ADS_HD constexpr int act_tile_bytes(int W) { return act_off(W, 4); }
 
 // Shared-memory matrix descriptor (no swizzle): bits 0-13 start address >> 4,
 // 16-29 leading-dimension byte offset >> 4, 32-45 stride-dimension byte offset
@@ -199,26 +203,22 @@ ADS_D void st_atom(unsigned char* tile, int rg, int r, int c, const float v[8]) 
   q.w = pack_bf16(v[6], v[7]);
   *reinterpret_cast<uint4*>(tile + core_off(r, c, rg)) = q;
 }
-// 8 values (one 16-byte atom) as a BF16 pair hi + lo (hi = bf16(v),
-// lo = bf16(v - hi): together about 16 significant bits), and the hi half
-// also to `g` (a global tile in the layout of row-group stride grg; nullptr:
-// not stored)
-ADS_D void st_atom_split_g(unsigned char* hi, unsigned char* lo, unsigned char* g, int rg, int grg, int r,
-                           int c, const float v[8]) {
-  uint32_t h[4], l[4];
+// the same 8 values at a given address (16-byte aligned)
+ADS_D void st_atom_at(unsigned char* p, const float v[8]) {
+  *reinterpret_cast<uint4*>(p) =
+      make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+
+// 8 BF16 values (one 16-byte atom) at a given address, as FP32
+ADS_D void ld_atom_at(const unsigned char* p, float v[8]) {
+  uint4 q = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-    float2 bf = __bfloat1622float2(b);
-    __nv_bfloat162 r2 = __floats2bfloat162_rn(v[2 * j] - bf.x, v[2 * j + 1] - bf.y);
-    h[j] = *reinterpret_cast<uint32_t*>(&b);
-    l[j] = *reinterpret_cast<uint32_t*>(&r2);
+    float2 f = __bfloat1622float2(h[j]);
+    v[2 * j] = f.x;
+    v[2 * j + 1] = f.y;
   }
-  const uint32_t off = core_off(r, c, rg);
-  const uint4 qh = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(hi + off) = qh;
-  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-  if (g) *reinterpret_cast<uint4*>(g + core_off(r, c, grg)) = qh;
 }
 
 ADS_D void ld_atom(const unsigned char* tile, int rg, int r, int c, float v[8]) {
@@ -340,8 +340,9 @@ struct TcSmemF {
   static constexpr int ACT = IMG;                      // NS hi tiles
   static constexpr int ACTLO = ACT + NS * ACT_SZ;      // NS lo tiles
   static constexpr int BAR = ACTLO + NS * ACTLO_SZ;    // mbarriers: vec, wt, ready[NS], prod[NS]; tmem base; abort
-  static constexpr int UPART = BAR + 64;               // fp32 [2][NS][128]: output-layer sums of the second half
-  static constexpr int TOTAL = UPART + 2 * NS * kTP * 4;
+  static constexpr int TPR = 2;                        // epilogue threads per point row (W / 2 columns each)
+  static constexpr int UPART = BAR + 64;               // fp32 [2][NS][TPR - 1][128]: output-layer partial sums
+  static constexpr int TOTAL = UPART + 2 * NS * (TPR - 1) * kTP * 4;
 };
 
 // The weight image of the forward, from the FP32 master parameters: the
@@ -394,14 +395,15 @@ ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
 ADS_D void mbar_arrive1(uint64_t* mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
-// barrier 1 over the 256 epilogue threads of the forward; returns whether any
-// of them passed `v` true (the same answer in every thread)
+// barrier 1 over the NTHR epilogue threads of the forward; returns whether
+// any of them passed `v` true (the same answer in every thread)
+template <int NTHR>
 ADS_D bool epi_barrier_any(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, 1, 256, pi;\nselp.u32 %0, 1, 0, po;\n}"
+      "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, 1, %2, pi;\nselp.u32 %0, 1, 0, po;\n}"
       : "=r"(r)
-      : "r"((uint32_t)v)
+      : "r"((uint32_t)v), "n"(NTHR)
       : "memory");
   return r != 0;
 }
@@ -425,10 +427,10 @@ ADS_D float2 tanh2_scaled(float2 zs) {
   return __ffma2_rn(r, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f));
 }
 // 8 values (one atom) as a BF16 pair hi + lo, to tiles of row-group strides
-// rgh and rgl, and the hi half also to `g` (nullable); the remainder v - hi
-// is formed on packed pairs
-ADS_D void st_atom_split2(unsigned char* hi, int rgh, unsigned char* lo, int rgl, unsigned char* g, int grg,
-                          int r, int c, const float v[8]) {
+// rgh and rgl, and the hi half also to the address `g` (nullable); the
+// remainder v - hi is formed on packed pairs
+ADS_D void st_atom_split2(unsigned char* hi, int rgh, unsigned char* lo, int rgl, unsigned char* g, int r, int c,
+                          const float v[8]) {
   uint32_t h[4], l[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -443,23 +445,26 @@ ADS_D void st_atom_split2(unsigned char* hi, int rgh, unsigned char* lo, int rgl
   const uint4 qh = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(hi + core_off(r, c, rgh)) = qh;
   *reinterpret_cast<uint4*>(lo + core_off(r, c, rgl)) = make_uint4(l[0], l[1], l[2], l[3]);
-  if (g) *reinterpret_cast<uint4*>(g + core_off(r, c, grg)) = qh;
+  if (g) *reinterpret_cast<uint4*>(g) = qh;
 }
 
-// forward: eight epilogue warps (two threads per point row, each taking half
-// of the feature columns; warps w and w + 4 read the same TMEM lanes) and one
-// issuing warp.  For W = 64 a CTA carries two tiles at once (slots 0 and 1,
-// each with its own operand tiles, TMEM accumulator, "written" and
-// "products done" mbarriers): the tensor cores work on one slot while the
-// epilogue warps work on the other.  The issuing warp only waits for a slot's
-// operand tiles and issues its products, so the epilogue warps never wait for
-// an issue; they meet only at the end of each tile pair, to add the two halves
-// of the output layer.
-constexpr int kFwdEpi = 2 * kTP;
-constexpr int kFwdThreads = kFwdEpi + 32;
+// forward: TPR = 2 epilogue threads per point row, W / 2 feature columns each
+// (eight warps; warps w and w + 4 read the same TMEM lanes; sixteen warps of
+// 32 columns each were measured slower at W = 128), and one issuing warp.  For W = 64 a CTA carries two tiles
+// at once (slots 0 and 1, each with its own operand tiles, TMEM accumulator,
+// "written" and "products done" mbarriers): the tensor cores work on one slot
+// while the epilogue warps work on the other.  The issuing warp only waits for
+// a slot's operand tiles and issues its products, so the epilogue warps never
+// wait for an issue; they meet only at the end of each tile group, to add the
+// parts of the output layer (in a fixed order).
+// epilogue threads (TPR per point row) and the issuing warp
+template <int W>
+constexpr int fwd_epi() { return TcSmemF<W>::TPR * kTP; }
+template <int W>
+constexpr int fwd_threads() { return fwd_epi<W>() + 32; }
 
 template <int W, int DIN>
-__global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(MlpTcArgs a) {
+__global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1) k_mlp_fwd_tc(MlpTcArgs a) {
   using L = TcSmemF<W>;
   constexpr int NS = L::NS;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -477,16 +482,17 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
   volatile int* group = reinterpret_cast<int*>(sm + L::BAR + 56);  // the current tile group
   float* upart = reinterpret_cast<float*>(sm + L::UPART);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kFwdEpi = fwd_epi<W>(), TPR = L::TPR, NEW = kFwdEpi / 32;  // NEW: epilogue warps
   const bool epi = tid < kFwdEpi;
-  const int row = tid & (kTP - 1), half = (tid >> 7) & 1;
-  constexpr int KC = L::KC, RGH = (KC / 8) * 128, RGL = (W / 8) * 128, WH = W / 2;
-  const int cb = half * WH;  // an epilogue thread's first feature column
+  const int row = tid & (kTP - 1), part = tid >> 7;
+  constexpr int KC = L::KC, RGH = (KC / 8) * 128, RGL = (W / 8) * 128, WH = W / TPR;
+  const int cb = part * WH;  // an epilogue thread's first feature column
   if (tid == kFwdEpi) {
     *abort_flag = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_vec)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_wt)));
     for (int s = 0; s < NS; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(mb_ready + s)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb_ready + s)), "r"(NEW));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_prod + s)));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -589,7 +595,7 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
     // launch, so that the CTAs on an SM finish together however the warps
     // are scheduled; thread 0 takes the next group while the current one runs
     if (tid == 0) *group = atomicAdd(a.wimage_ctr, 1);
-    epi_barrier_any(false);
+    epi_barrier_any<kFwdEpi>(false);
     int pass = 0;
     for (;; ++pass) {
       const int tb = NS * *group;
@@ -609,18 +615,11 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
         valid[s] = tile < ntiles;  // CTA-uniform
         p0[s] = (a.tile0 + tile) * kTP;
         gt[s] = nullptr;
-        u2[s] = make_float2(half == 0 ? b5 : 0.0f, 0.0f);
+        u2[s] = make_float2(part == 0 ? b5 : 0.0f, 0.0f);
         if (!valid[s]) continue;
         float x[3];
         coords<DIN>(min(p0[s] + row, a.npts - 1), a.N, x);
-        gt[s] = a.acts ? a.acts + (size_t)tile * act_tile_bytes(W) : nullptr;
-        if (gt[s] && act_cols(W, 0) > W) {
-          // the constant columns [1, 0, ..., 0] of the stored a_1 .. a_3
-          const uint4 q = half == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-          for (int l = 0; l < 3; ++l)
-            *reinterpret_cast<uint4*>(gt[s] + act_off(W, l) + core_off(row, W + 8 * half, act_rg(W, l))) = q;
-        }
+        gt[s] = a.acts ? a.acts + (size_t)tile * st_tile_bytes(W) : nullptr;
         unsigned char* ah = act + s * L::ACT_SZ;
         unsigned char* al = actlo + s * L::ACTLO_SZ;
 #pragma unroll
@@ -637,7 +636,7 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
             v[j] = t.x;
             v[j + 1] = t.y;
           }
-          st_atom_split2(ah, RGH, al, RGL, gt[s], act_rg(W, 0), row, cb + c, v);
+          st_atom_split2(ah, RGH, al, RGL, gt[s] ? gt[s] + st_off(W, row, cb + c) : nullptr, row, cb + c, v);
         }
         ready(s);
       }
@@ -652,8 +651,7 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
           tc_fence_after();
           unsigned char* ah = act + s * L::ACT_SZ;
           unsigned char* al = actlo + s * L::ACTLO_SZ;
-          unsigned char* g = gt[s] ? gt[s] + act_off(W, l + 1) : nullptr;
-          const int grg = act_rg(W, l + 1);
+          unsigned char* g = gt[s] ? gt[s] + (l + 1) * st_layer_bytes(W) : nullptr;
 #pragma unroll
           for (int c0 = 0; c0 < WH; c0 += 32) {
             float d[32];
@@ -667,10 +665,11 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
                 v[j] = t.x;
                 v[j + 1] = t.y;
               }
+              unsigned char* gp = g ? g + st_off(W, row, cb + c0 + c) : nullptr;
               if (l < 2) {
-                st_atom_split2(ah, RGH, al, RGL, g, grg, row, cb + c0 + c, v);
+                st_atom_split2(ah, RGH, al, RGL, gp, row, cb + c0 + c, v);
               } else {
-                if (g) st_atom(g, grg, row, cb + c0 + c, v);
+                if (gp) st_atom_at(gp, v);
                 // the output layer in FP32 from the unrounded activations
 #pragma unroll
                 for (int j = 0; j < 8; j += 2)
@@ -686,16 +685,20 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
       // pass); the barrier also publishes the next group and makes the stop
       // decision the same everywhere.  (The issuer read this pass's group
       // before it issued the products these epilogues waited for.)
-      float* up = upart + (pass & 1) * NS * kTP;
+      float* up = upart + (pass & 1) * NS * (TPR - 1) * kTP;
 #pragma unroll
       for (int s = 0; s < NS; ++s)
-        if (half) up[s * kTP + row] = u2[s].x + u2[s].y;
+        if (part) up[(s * (TPR - 1) + part - 1) * kTP + row] = u2[s].x + u2[s].y;
       if (tid == 0) *group = atomicAdd(a.wimage_ctr, 1);
-      const bool stop = epi_barrier_any(*abort_flag != 0);
+      const bool stop = epi_barrier_any<kFwdEpi>(*abort_flag != 0);
 #pragma unroll
       for (int s = 0; s < NS; ++s)
-        if (!half && valid[s] && !stop && p0[s] + row < a.npts)
-          a.u[p0[s] + row] = u2[s].x + u2[s].y + up[s * kTP + row];
+        if (!part && valid[s] && !stop && p0[s] + row < a.npts) {
+          float u = u2[s].x + u2[s].y;
+#pragma unroll
+          for (int q = 0; q < TPR - 1; ++q) u += up[(s * (TPR - 1) + q) * kTP + row];
+          a.u[p0[s] + row] = u;
+        }
       if (stop) break;
     }
   }
@@ -718,17 +721,18 @@ __global__ void __launch_bounds__(kFwdThreads, W == 64 ? 2 : 1) k_mlp_fwd_tc(Mlp
 // order (deterministic sums); products complete in issue order.  The output
 // layer's gradient (a_4^T g, sum g) is a per-thread running sum over the CTA's
 // tiles, reduced over the rows once at the end in a fixed order.  The four
-// stored activation tiles of a point tile (64 KB, the forward's layout) arrive
-// by one bulk copy into a double buffer, the next tile's copy running under
-// the current tile.  Bias gradients come with the weight gradients from the
-// stored [a | 1] tiles.  The delta tiles are 64 columns wide; the weight-
+// stored activation layers of a point tile (64 KB) arrive by four bulk
+// copies on one barrier into a double buffer, the next tile's copies running
+// under the current tile.  Bias gradients come with the weight gradients from
+// the [a | 1] copies (the constant chunks are written once per launch).  The delta tiles are 64 columns wide; the weight-
 // gradient products read them as M = 128 operands whose rows 64 .. 127 (the
 // next rows' values) land in accumulator rows that are never read.
 constexpr int kBwdEpi = 2 * kTP;          // epilogue threads: two per point row
 constexpr int kBwdThreads = kBwdEpi + 32;  // eight epilogue warps, one issuing warp
 struct TcSmemB {
   static constexpr int W = 0;                              // 3 x [64][64] bf16       24 KB
-  static constexpr int ACT_TILE = act_tile_bytes(kW);      // a_1..a_3 [128][80], a_4 [128][64]  76 KB
+  static constexpr int LAYER = (kWP / 8) * kChunk;         // [a | 1]: 10 chunks of 2 KB  20 KB
+  static constexpr int ACT_TILE = 3 * LAYER + st_layer_bytes(kW);  // a_1..a_3 as [a | 1], a_4  76 KB
   static constexpr int ACT = W + 3 * kW * kW * 2;          // 2 buffers             152 KB
   static constexpr int DEL_SZ = kTP * kW * 2;              // [128][64] bf16          16 KB
   static constexpr int DEL = ACT + 2 * ACT_TILE;           // 2 delta tiles           32 KB
@@ -738,6 +742,16 @@ struct TcSmemB {
   static constexpr int BAR = VEC + kW * 4;                 // 7 mbarriers, tmem base, abort flag
   static constexpr int TOTAL = BAR + 64;
 };
+// the backward's copy of stored layer l (a_1 .. a_4 for l = 0 .. 3) in a buffer
+ADS_HD constexpr int bwd_layer(int l) { return l * TcSmemB::LAYER; }
+// MN-major view of a width-64 [a | 1] copy (rows = K = points, columns = N):
+// 8-point groups 128 B apart (LBO), 8-column chunks 2 KB apart (SBO); a
+// k-step of 16 points is 256 B
+ADS_D uint64_t desc_mn_chunk(uint32_t base, int kstep) {
+  const uint32_t lo = (base >> 4) + (uint32_t)kstep * 16u + (8u << 16);
+  const uint32_t hi = ((uint32_t)kChunk >> 4) | (1u << 14);
+  return ((uint64_t)hi << 32) | lo;
+}
 // TMEM columns: delta product [0,64), dW5 [64,144), dW4 [144,224),
 // dW3 [224,304), dW2 [304,384), dW1 [384,400); in each dW block the weight
 // part is columns [0,64) and the bias part column 64 (of [64,80))
@@ -770,13 +784,22 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   const bool epi = tid < kBwdEpi;
   const int row = tid & (kTP - 1), c0 = 32 * (tid >> 7);  // epilogue: point row, first column
   constexpr int RGW = (kW / 8) * 128, RGD = RGW, RGX = (kXP / 8) * 128;
-  constexpr uint32_t kTileBytes = TcSmemB::ACT_TILE;
+  // a tile's activations: 64 KB in HBM (four layers of 16 KB), 76 KB in a
+  // shared buffer (a_1 .. a_3 followed by their constant chunks)
+  constexpr uint32_t kSmTile = TcSmemB::ACT_TILE, kGlTile = st_tile_bytes(kW), kGlLayer = st_layer_bytes(kW);
   const float* th = a.theta;
   const int ob1 = kW * DIN, o2 = ob1 + kW, o5 = o2 + 3 * (kW * kW + kW);
   const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
   if (epi) {
     load_hidden_weights<kW, kBwdEpi>(th, o2, wt, tid);
     for (int i = tid; i < kW; i += kBwdEpi) fW5[i] = th[o5 + i];
+    // the constant chunks of [a_l | 1] in both buffers: [1, 0, ..., 0] and
+    // zeros in every row (the copies of a tile never write them)
+    for (int i = tid; i < 2 * 3 * 2 * kTP; i += kBwdEpi) {
+      const int r = i % kTP, ch = (i / kTP) % 2, l = (i / (2 * kTP)) % 3, b = i / (6 * kTP);
+      *reinterpret_cast<uint4*>(act + b * kSmTile + bwd_layer(l) + (8 + ch) * kChunk + r * 16) =
+          ch == 0 ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   if (tid == 0) {
     *abort_flag = 0;
@@ -811,21 +834,25 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
                    xin_s = smem_addr(xin);
     // dW_l | db_l: M = 128 (o; rows 64 .. 127 unused), N = 80 ([a | 1]), K = points
     // M = 64: exactly the 64 output rows (the M = 64 accumulator layout, m64_row)
-    const uint32_t id_dw = idesc_bf16(kW, act_cols(kW, 0), 1, 1);
+    const uint32_t id_dw = idesc_bf16(kW, kWP, 1, 1);
     const uint32_t id_db = idesc_bf16(kW, kXP, 1, 1);  // dW_1 | db_1: N = 16 ([x' | 1])
     const uint32_t id_dp = idesc_bf16(kTP, kW, 0, 1);   // delta product: M = points, N = 64, K = 64
     uint32_t ph_ready = 0, ph_ready4 = 0, ph_free = 0, lph = 0;
     int pend = -1;  // buffer whose bulk copy is in flight (at most one), or -1
     auto fail = [&]() { *abort_flag = 1; };
-    if ((int)blockIdx.x < ntiles) {
-      mbar_expect(mb_load, kTileBytes);
-      bulk_load(act, a.acts + (size_t)blockIdx.x * kTileBytes, kTileBytes, mb_load);
-      pend = 0;
-    }
+    // the four stored layers of a tile into buffer b (one barrier)
+    auto load_tile = [&](int b, int t) {
+      mbar_expect(mb_load + b, kGlTile);
+      const unsigned char* src = a.acts + (size_t)t * kGlTile;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) bulk_load(act + b * kSmTile + bwd_layer(l), src + l * kGlLayer, kGlLayer, mb_load + b);
+      pend = b;
+    };
+    if ((int)blockIdx.x < ntiles) load_tile(0, blockIdx.x);
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       const int buf = it & 1;
-      const uint32_t actb_s = act_s + buf * kTileBytes;
+      const uint32_t actb_s = act_s + buf * kSmTile;
       if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { fail(); break; }
       lph ^= 1u << buf;
       pend = -1;
@@ -835,12 +862,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         if (!mbar_wait(mb_free, ph_free)) { fail(); break; }
         ph_free ^= 1;
       }
-      if (tile + (int)gridDim.x < ntiles) {
-        mbar_expect(mb_load + 1 - buf, kTileBytes);
-        bulk_load(act + (1 - buf) * kTileBytes, a.acts + (size_t)(tile + gridDim.x) * kTileBytes,
-                  kTileBytes, mb_load + 1 - buf);
-        pend = 1 - buf;
-      }
+      if (tile + (int)gridDim.x < ntiles) load_tile(1 - buf, tile + gridDim.x);
       // x' and Delta_4 written
       if (!mbar_wait(mb_ready4, ph_ready4)) { fail(); break; }
       ph_ready4 ^= 1;
@@ -854,7 +876,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
           tc_fence_after();
         }
         const uint32_t dcur = del_s + cur * TcSmemB::DEL_SZ;
-        const uint32_t ain = actb_s + act_off(kW, L - 2);  // [a_{L-1} | 1]
+        const uint32_t ain = actb_s + bwd_layer(L - 2);  // [a_{L-1} | 1]
         const uint32_t wl = wt_s + (L - 2) * kW * kW * 2;
         // Delta_L W_L, then its commit: the epilogues wait for this alone
 #pragma unroll
@@ -866,7 +888,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         for (int ks = 0; ks < kTP / 16; ++ks) {
           const uint64_t da = desc_mn(dcur, RGD, ks);
           const uint32_t acc = (ks > 0 || !first) ? 1u : 0u;
-          mma_bf16(tmem + col_dw(L), da, desc_mn(ain, act_rg(kW, L - 2), ks), id_dw, acc);
+          mma_bf16(tmem + col_dw(L), da, desc_mn_chunk(ain, ks), id_dw, acc);
         }
         cur = 1 - cur;
       }
@@ -910,7 +932,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     }
     for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       const int buf = it & 1;
-      const unsigned char* actb = act + buf * kTileBytes;
+      const unsigned char* actb = act + buf * kSmTile;
       const int idx = (a.tile0 + tile) * kTP + row;
       const float g = g_next;
       if (tile + (int)gridDim.x < ntiles) {
@@ -928,7 +950,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
 #pragma unroll
       for (int c = 0; c < 32; c += 8) {
         float av[8];
-        ld_atom(actb + act_off(kW, 3), act_rg(kW, 3), row, c0 + c, av);
+        ld_atom_at(actb + bwd_layer(3) + st_off(kW, row, c0 + c), av);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           v4[c + j] = fW5[c0 + c + j] * g * (1.0f - av[j] * av[j]);
@@ -959,12 +981,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       for (int L = 4; L >= 2; --L) {
         // Delta_{L-1} = (Delta_L W_L)(1 - a_{L-1}^2) into the other delta
         // tile; the second factor before the product is ready
-        const unsigned char* aprev = actb + act_off(kW, L - 2);
+        const unsigned char* aprev = actb + bwd_layer(L - 2);
         float sq[32];
 #pragma unroll
         for (int c = 0; c < 32; c += 8) {
           float av[8];
-          ld_atom(aprev, act_rg(kW, L - 2), row, c0 + c, av);
+          ld_atom_at(aprev + st_off(kW, row, c0 + c), av);
 #pragma unroll
           for (int j = 0; j < 8; ++j) sq[c + j] = 1.0f - av[j] * av[j];
         }
@@ -1115,7 +1137,7 @@ struct TcSmemB2 {
 
 template <int W, int DIN>
 __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
-  static_assert(act_cols(W, 0) == W, "ring form: stored tiles without the ones column");
+  static_assert(W == 128, "ring form: the core-matrix layout of stored width-128 tiles");
   constexpr int NCOL = 4 * W;  // TMEM columns: delta product + three dW
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemB2<W>::WT;
@@ -1164,7 +1186,7 @@ __global__ void __launch_bounds__(kTP) k_mlp_bwd_tcr(MlpTcArgs a) {
   bool aborted = false, first = true;
   const int ntiles = a.tile_count;  // local tile t is global tile a.tile0 + t
   auto stage = [&](int slot, int L, int tile) {  // activations a_{L+1} (L = 0..3) of `tile`
-    const unsigned char* src = a.acts + (size_t)tile * act_tile_bytes(W) + act_off(W, L);
+    const unsigned char* src = a.acts + (size_t)tile * st_tile_bytes(W) + L * st_layer_bytes(W);
     unsigned char* dst = act + slot * TcSmemB2<W>::ACT_SZ;
     for (int ch = tid; ch < kTP * W * 2 / 16; ch += kTP) cp_async16(dst + ch * 16, src + ch * 16);
     cp_async_commit();
@@ -1315,7 +1337,7 @@ int sms() {
 
 size_t mlp_tc_acts_bytes(int npts, int width) {
   int ntiles = (npts + kTP - 1) / kTP;
-  return (size_t)ntiles * act_tile_bytes(width);
+  return (size_t)ntiles * st_tile_bytes(width);
 }
 
 
@@ -1384,13 +1406,13 @@ static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
   const size_t smem = L::TOTAL;
   auto k = k_mlp_fwd_tc<W, DIN>;
   smem_optin(k);
-  const int occ = tc_residency(k, smem, L::NS * W, kFwdThreads);
+  const int occ = tc_residency(k, smem, L::NS * W, fwd_threads<W>());
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
   if (want < grid) grid = want > 0 ? want : 1;
   MlpTcArgs b = a;
   b.wimage_ctr = reinterpret_cast<int*>(a.wimage + L::IMG);
-  k<<<grid, kFwdThreads, smem, st>>>(b);
+  k<<<grid, fwd_threads<W>(), smem, st>>>(b);
   return cudaGetLastError();
 }
 

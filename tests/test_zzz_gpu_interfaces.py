@@ -95,3 +95,30 @@ def test_device_wait_expiry_is_reported_and_the_context_carries_on():
         assert np.isfinite(st["loss_last"])
     finally:
         s.close()
+
+
+def test_profiles_time_every_kernel_and_advance_like_updates():
+    """The per-kernel profiles replay a captured iteration (sub-step): the
+    times are positive and finite, and the parameters advance exactly as
+    through crvpinn_pressure_update (same kernels, same order)."""
+    from paper_2604_20731_gb300.solver import HybridSolver
+    n = 33
+    sc = scn.make_scenario(2, n, seed=5, S0="random")
+    theta = scn.make_theta0(2, 64, 4, seed=7)
+    a = HybridSolver(sc, width=64, crv_dtype="bf16", ads_dtype="f32")
+    b = HybridSolver(sc, width=64, crv_dtype="bf16", ads_dtype="f32")
+    try:
+        for s in (a, b):
+            s.set_theta(theta)
+            s.update_coefficients()
+            s.pressure_update(1, 1e-3)  # sets the learning rate the profile uses
+        ms = a.profile_train(3)
+        b.pressure_update(3, 1e-3)
+        assert len(ms) == 8 and all(np.isfinite(v) and v >= 0 for v in ms.values())
+        assert ms["mlp_fwd"] > 0 and ms["mlp_bwd"] > 0
+        assert np.array_equal(a.get("THETA"), b.get("THETA"))
+        sat = a.profile_saturation(2)
+        assert all(np.isfinite(v) and v > 0 for v in sat.values())
+    finally:
+        a.close()
+        b.close()
