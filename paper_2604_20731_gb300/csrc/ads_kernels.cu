@@ -311,24 +311,46 @@ ADS_D void sweep_lines_smem(T* buf, int nrows, int nb, int ld, int chunk,
   __syncthreads();
 }
 
-// x-contractions of the coefficients of one DOF row over the three basis
-// functions of element column ex, at the three Gauss abscissae
+// Pairs for the packed FP32 instructions of this GPU (fma.rn.f32x2: two
+// correctly rounded FMAs in one issue slot); FP64 takes two scalar FMAs.
+// The 1D basis tables pair up naturally: (B, dB) of an element column along
+// x and (dB, B) of an element row along y, so that one packed FMA advances
+// two of the sum-factorised contractions at once.
 template <typename T>
-struct XRow {
-  T s[3], p[3], pd[3];
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
 };
 template <typename T>
-ADS_D void xrow_load(const QuadArgs<T>& a, int r, int ex, const T (&bx)[3][3],
-                     const T (&dbx)[3][3], XRow<T>& w) {
+using P2 = typename PairOf<T>::type;
+ADS_D float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+ADS_D double2 pfma(double2 a, double2 b, double2 c) { return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)); }
+ADS_D float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+ADS_D double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
+// x-contractions of the coefficients of one DOF row over the three basis
+// functions of element column ex, at the three Gauss abscissae: S, and the
+// pair (P, dP/dx)
+template <typename T>
+struct XRow {
+  T s[3];
+  P2<T> ppd[3];
+};
+template <typename T>
+ADS_D void xrow_load(const QuadArgs<T>& a, int r, int ex, const P2<T> (&xb)[3][3], XRow<T>& w) {
   const T* srow = a.S + (size_t)r * a.nb + ex;
   const T* prow = a.P + (size_t)r * a.nb + ex;
   const T s0 = __ldg(srow), s1 = __ldg(srow + 1), s2 = __ldg(srow + 2);
   const T p0 = __ldg(prow), p1 = __ldg(prow + 1), p2 = __ldg(prow + 2);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    w.s[q] = s0 * bx[0][q] + s1 * bx[1][q] + s2 * bx[2][q];
-    w.p[q] = p0 * bx[0][q] + p1 * bx[1][q] + p2 * bx[2][q];
-    w.pd[q] = p0 * dbx[0][q] + p1 * dbx[1][q] + p2 * dbx[2][q];
+    w.s[q] = s0 * xb[0][q].x + s1 * xb[1][q].x + s2 * xb[2][q].x;
+    w.ppd[q] = pfma(P2<T>{p2, p2}, xb[2][q], pfma(P2<T>{p1, p1}, xb[1][q], pmul(P2<T>{p0, p0}, xb[0][q])));
   }
 }
 
@@ -368,55 +390,53 @@ __global__ void __launch_bounds__(kQuadThreads, sizeof(T) == 4 ? 2 : 1)
     const int ex = g * kQuadCols - 2 + lane;  // element column of this lane = its DOF column
     const bool live = ex >= 0 && ex < n;
     const int xc = live ? ex : 0;
-    T bx[3][3], dbx[3][3];
+    // (B, dB) of the lane's element column at the three abscissae
+    P2<T> xb[3][3];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      bx[i / 3][i % 3] = __ldg(a.ax.B + xc * 9 + i);
-      dbx[i / 3][i % 3] = __ldg(a.ax.dB + xc * 9 + i);
-    }
-    T gx[NS][3];
+    for (int i = 0; i < 9; ++i) xb[i / 3][i % 3] = P2<T>{__ldg(a.ax.B + xc * 9 + i), __ldg(a.ax.dB + xc * 9 + i)};
+    // the sources' x profiles times their rates
+    T gxr[NS][3];
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int q = 0; q < 3; ++q)
-        gx[s][q] = s < a.n_src ? __ldg(a.ax.gsrc + ((size_t)(0 * kMaxSrc + s) * n + xc) * 3 + q) : T(0);
+        gxr[s][q] = s < a.n_src ? a.rate[s] * __ldg(a.ax.gsrc + ((size_t)(0 * kMaxSrc + s) * n + xc) * 3 + q) : T(0);
     XRow<T> w0, w1, w2;
-    // K (or the nodal values) and phi at the element's lower and upper nodes
-    T k0[2] = {T(0), T(0)}, k1[2] = {T(0), T(0)}, f0[2] = {T(0), T(0)}, f1[2] = {T(0), T(0)};
+    // K (or the nodal values) interpolated along x to the three abscissae on
+    // the element's lower (0) and upper (1) node rows; phi at the nodes
+    T kx0[3], kx1[3], f0[2] = {T(0), T(0)}, f1[2] = {T(0), T(0)};
+    auto xinterp = [&](const T* row, T (&out)[3]) {
+      const T v0 = __ldg(row), v1 = __ldg(row + 1);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const T xi = (T)gauss_x(q);
+        out[q] = (T(1) - xi) * v0 + xi * v1;
+      }
+    };
     if (MODE == 0) {
-      xrow_load(a, e0, xc, bx, dbx, w0);
-      xrow_load(a, e0 + 1, xc, bx, dbx, w1);
-      const T* Kr = a.K + (size_t)e0 * n1 + xc;
-      k0[0] = __ldg(Kr);
-      k0[1] = __ldg(Kr + 1);
+      xrow_load(a, e0, xc, xb, w0);
+      xrow_load(a, e0 + 1, xc, xb, w1);
+      xinterp(a.K + (size_t)e0 * n1 + xc, kx0);
       if (a.phi) {
-        const T* Fr = a.phi + (size_t)e0 * n1 + xc;
-        f0[0] = __ldg(Fr);
-        f0[1] = __ldg(Fr + 1);
+        f0[0] = __ldg(a.phi + (size_t)e0 * n1 + xc);
+        f0[1] = __ldg(a.phi + (size_t)e0 * n1 + xc + 1);
       }
     } else {
-      const T* Ur = a.nodal + (size_t)e0 * n1 + xc;
-      k0[0] = __ldg(Ur);
-      k0[1] = __ldg(Ur + 1);
+      xinterp(a.nodal + (size_t)e0 * n1 + xc, kx0);
     }
     T A0 = T(0), A1 = T(0), A2 = T(0);
     for (int er = e0; er < e1; ++er) {
-      T by[3][3], dby[3][3];
+      // (dB, B) of the element row at the three abscissae
+      P2<T> yb[3][3];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        by[i / 3][i % 3] = __ldg(a.ax.B + er * 9 + i);
-        dby[i / 3][i % 3] = __ldg(a.ax.dB + er * 9 + i);
-      }
+      for (int i = 0; i < 9; ++i) yb[i / 3][i % 3] = P2<T>{__ldg(a.ax.dB + er * 9 + i), __ldg(a.ax.B + er * 9 + i)};
       T loc[3][3];
       if (MODE == 0) {
-        xrow_load(a, er + 2, xc, bx, dbx, w2);
-        const T* Kr = a.K + (size_t)(er + 1) * n1 + xc;
-        k1[0] = __ldg(Kr);
-        k1[1] = __ldg(Kr + 1);
+        xrow_load(a, er + 2, xc, xb, w2);
+        xinterp(a.K + (size_t)(er + 1) * n1 + xc, kx1);
         if (a.phi) {
-          const T* Fr = a.phi + (size_t)(er + 1) * n1 + xc;
-          f1[0] = __ldg(Fr);
-          f1[1] = __ldg(Fr + 1);
+          f1[0] = __ldg(a.phi + (size_t)(er + 1) * n1 + xc);
+          f1[1] = __ldg(a.phi + (size_t)(er + 1) * n1 + xc + 1);
         }
         T gy[NS][3];
 #pragma unroll
@@ -424,32 +444,31 @@ __global__ void __launch_bounds__(kQuadThreads, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
           for (int q = 0; q < 3; ++q)
             gy[s][q] = s < a.n_src ? __ldg(a.ax.gsrc + ((size_t)(1 * kMaxSrc + s) * n + er) * 3 + q) : T(0);
-        T T0[3][3], T1[3][3];  // [qy][a]: test functions along x applied
-        T esrc = T(0);  // tau/phi int q_g over the element (9 terms)
+        P2<T> tt[3][3];  // [qy][aa]: (T1, T0), the test functions along x applied
+        T esrc = T(0);   // tau/phi int q_g over the element (9 terms)
 #pragma unroll
         for (int qy = 0; qy < 3; ++qy) {
           const T eta = (T)gauss_x(qy);
-          T c0[3], cx[3], cy[3];
+          P2<T> cc[3];  // (c0, cx) at the row's three points
+          T cy[3];
 #pragma unroll
           for (int qx = 0; qx < 3; ++qx) {
-            const T xi = (T)gauss_x(qx);
-            const T Sv = by[0][qy] * w0.s[qx] + by[1][qy] * w1.s[qx] + by[2][qy] * w2.s[qx];
-            const T dpx = by[0][qy] * w0.pd[qx] + by[1][qy] * w1.pd[qx] + by[2][qy] * w2.pd[qx];
-            const T dpy = dby[0][qy] * w0.p[qx] + dby[1][qy] * w1.p[qx] + dby[2][qy] * w2.p[qx];
-            const T Kq = (T(1) - eta) * ((T(1) - xi) * k0[0] + xi * k0[1]) +
-                         eta * ((T(1) - xi) * k1[0] + xi * k1[1]);
+            // (dP/dy, dP/dx) and S at the point
+            const P2<T> dp =
+                pfma(yb[2][qy], w2.ppd[qx], pfma(yb[1][qy], w1.ppd[qx], pmul(yb[0][qy], w0.ppd[qx])));
+            const T Sv = yb[0][qy].y * w0.s[qx] + yb[1][qy].y * w1.s[qx] + yb[2][qy].y * w2.s[qx];
+            const T Kq = (T(1) - eta) * kx0[qx] + eta * kx1[qx];
             T dtphi = dtphi_c;
             if (a.phi) {
-              const T phq = (T(1) - eta) * ((T(1) - xi) * f0[0] + xi * f0[1]) +
-                            eta * ((T(1) - xi) * f1[0] + xi * f1[1]);
-              dtphi = dt / phq;
+              const T xi = (T)gauss_x(qx);
+              dtphi = dt / ((T(1) - eta) * ((T(1) - xi) * f0[0] + xi * f0[1]) + eta * ((T(1) - xi) * f1[0] + xi * f1[1]));
             }
             const T St = clamp01(Sv);
             const T lg = St * a.inv_mu_g, lw = (T(1) - St) * a.inv_mu_w;
             T qi = T(0), qp = T(0);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-              const T gv = a.rate[s] * gx[s][qx] * gy[s][qy];
+              const T gv = gxr[s][qx] * gy[s][qy];
               if (a.kind[s] == 0) qi += gv;
               else qp += gv;
             }
@@ -457,70 +476,56 @@ __global__ void __launch_bounds__(kQuadThreads, sizeof(T) == 4 ? 2 : 1)
             T qg = qi;
             if (qp != T(0)) qg -= frac_div(lg, lg + lw) * qp;
             const T w = (T)(gauss_w(qx) * gauss_w(qy)) * h2;
-            c0[qx] = w * (Sv + dtphi * qg);
             const T cf = -w * dtphi * lg * Kq;
-            cx[qx] = cf * dpx;
-            cy[qx] = cf * (dpy + a.grav_term);
+            cc[qx] = P2<T>{w * (Sv + dtphi * qg), cf * dp.y};
+            cy[qx] = cf * (dp.x + a.grav_term);
             esrc += w * dtphi * qg;
           }
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa) {
-            T t0 = T(0), t1 = T(0);
-#pragma unroll
-            for (int qx = 0; qx < 3; ++qx) {
-              t0 += c0[qx] * bx[aa][qx] + cx[qx] * dbx[aa][qx];
-              t1 += cy[qx] * bx[aa][qx];
-            }
-            T0[qy][aa] = t0;
-            T1[qy][aa] = t1;
+            const P2<T> t0 = pfma(cc[2], xb[aa][2], pfma(cc[1], xb[aa][1], pmul(cc[0], xb[aa][0])));
+            const T t1 = cy[0] * xb[aa][0].x + cy[1] * xb[aa][1].x + cy[2] * xb[aa][2].x;
+            tt[qy][aa] = P2<T>{t1, t0.x + t0.y};
           }
         }
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb)
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa) {
-            T v = T(0);
-#pragma unroll
-            for (int qy = 0; qy < 3; ++qy) v += by[bb][qy] * T0[qy][aa] + dby[bb][qy] * T1[qy][aa];
-            loc[bb][aa] = live ? v : T(0);
+            const P2<T> v = pfma(yb[bb][2], tt[2][aa], pfma(yb[bb][1], tt[1][aa], pmul(yb[bb][0], tt[0][aa])));
+            loc[bb][aa] = live ? v.x + v.y : T(0);
           }
         // lanes 0 and 1 recompute elements the previous group owns
         if (live && lane >= 2) src.add(esrc);
         w0 = w1;
         w1 = w2;
-        k0[0] = k1[0];
-        k0[1] = k1[1];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) kx0[q] = kx1[q];
         f0[0] = f1[0];
         f0[1] = f1[1];
       } else {
-        const T* Ur = a.nodal + (size_t)(er + 1) * n1 + xc;
-        k1[0] = __ldg(Ur);
-        k1[1] = __ldg(Ur + 1);
+        xinterp(a.nodal + (size_t)(er + 1) * n1 + xc, kx1);
         T T0[3][3];
 #pragma unroll
         for (int qy = 0; qy < 3; ++qy) {
           const T eta = (T)gauss_x(qy);
           T c0[3];
 #pragma unroll
-          for (int qx = 0; qx < 3; ++qx) {
-            const T xi = (T)gauss_x(qx);
-            const T uq = (T(1) - eta) * ((T(1) - xi) * k0[0] + xi * k0[1]) +
-                         eta * ((T(1) - xi) * k1[0] + xi * k1[1]);
-            c0[qx] = (T)(gauss_w(qx) * gauss_w(qy)) * h2 * uq;
-          }
+          for (int qx = 0; qx < 3; ++qx)
+            c0[qx] = (T)(gauss_w(qx) * gauss_w(qy)) * h2 * ((T(1) - eta) * kx0[qx] + eta * kx1[qx]);
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa)
-            T0[qy][aa] = c0[0] * bx[aa][0] + c0[1] * bx[aa][1] + c0[2] * bx[aa][2];
+            T0[qy][aa] = c0[0] * xb[aa][0].x + c0[1] * xb[aa][1].x + c0[2] * xb[aa][2].x;
         }
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb)
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa) {
-            const T v = by[bb][0] * T0[0][aa] + by[bb][1] * T0[1][aa] + by[bb][2] * T0[2][aa];
+            const T v = yb[bb][0].y * T0[0][aa] + yb[bb][1].y * T0[1][aa] + yb[bb][2].y * T0[2][aa];
             loc[bb][aa] = live ? v : T(0);
           }
-        k0[0] = k1[0];
-        k0[1] = k1[1];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) kx0[q] = kx1[q];
       }
       // column sums across the warp: own first-column term + neighbours' terms
       T col[3];

@@ -107,7 +107,14 @@ def test_saturation_step_four_wells(n, dtype, tol):
         ref = a.step(ref, P, dt)
     assert rel_inf(s.get("S"), ref) <= tol
     mass = s.get("MASS")
-    assert mass[0] == pytest.approx(a.mesh.integral(ref), rel=1e-12 if dtype == "f64" else 1e-6)
+    if dtype == "f64":
+        assert mass[0] == pytest.approx(a.mesh.integral(ref), rel=1e-12)
+    else:
+        # |int (S - S_ref)| <= max |S - S_ref| times the area of the unit
+        # square (the basis integrals sum to 1): the saturation tolerance
+        # bounds the mass error.  The random pressure drives S far from its
+        # mean, so a bound relative to the mass itself would be rounding luck.
+        assert abs(mass[0] - a.mesh.integral(ref)) <= tol * np.abs(ref).max()
     s.close()
 
 
