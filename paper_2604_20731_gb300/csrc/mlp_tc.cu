@@ -426,6 +426,29 @@ ADS_D float2 tanh2_scaled(float2 zs) {
   const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
   return __ffma2_rn(r, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f));
 }
+// The same with the reciprocal on the FP32 pipe instead of the special-
+// function unit, for a share of the activations (the unit then carries one
+// ex2 per activation and only some of the reciprocals).  Newton-Raphson for
+// 1/d: the initial guess is the integer difference R - bits(d), whose value
+// read as a float is within 5.1 % of 1/d for every normal d (R = 0x7EF311C0
+// minimises the largest relative error over the mantissa; found by direct
+// search), then three steps y <- y + y (1 - d y), each squaring the relative
+// error: 5.1e-2, 2.6e-3, 6.5e-6, 4e-11 -- below FP32 rounding.  z' is capped
+// at 64 so that d stays finite; 2 / (1 + 2^64) - 1 is -1 in FP32, as the
+// uncapped form gives.
+constexpr int kRcpSeed = 0x7EF311C0;
+ADS_D float2 tanh2_scaled_nr(float2 zs) {
+  const float2 t = make_float2(ex2_approx(fminf(zs.x, 64.0f)), ex2_approx(fminf(zs.y, 64.0f)));
+  const float2 d = __fadd2_rn(t, make_float2(1.0f, 1.0f));
+  const float2 nd = make_float2(-d.x, -d.y);
+  float2 y = make_float2(__int_as_float(kRcpSeed - __float_as_int(d.x)), __int_as_float(kRcpSeed - __float_as_int(d.y)));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 e = __ffma2_rn(nd, y, make_float2(1.0f, 1.0f));
+    y = __ffma2_rn(y, e, y);
+  }
+  return __ffma2_rn(y, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f));
+}
 // 8 values (one atom) as a BF16 pair hi + lo, to tiles of row-group strides
 // rgh and rgl, and the hi half also to the address `g` (nullable); the
 // remainder v - hi is formed on packed pairs
@@ -632,7 +655,8 @@ __global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1) k_mlp_fwd_t
 #pragma unroll
             for (int d = 0; d < DIN; ++d)
               z = __ffma2_rn(*reinterpret_cast<const float2*>(fW1 + d * W + o), make_float2(x[d], x[d]), z);
-            const float2 t = tanh2_scaled(z);
+            // one pair in two with its reciprocal on the FP32 pipe
+            const float2 t = (j & 2) ? tanh2_scaled_nr(z) : tanh2_scaled(z);
             v[j] = t.x;
             v[j + 1] = t.y;
           }
@@ -661,7 +685,8 @@ __global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1) k_mlp_fwd_t
               float v[8];
 #pragma unroll
               for (int j = 0; j < 8; j += 2) {
-                const float2 t = tanh2_scaled(make_float2(d[c + j], d[c + j + 1]));
+                const float2 zz = make_float2(d[c + j], d[c + j + 1]);
+                const float2 t = (j & 2) ? tanh2_scaled_nr(zz) : tanh2_scaled(zz);
                 v[j] = t.x;
                 v[j + 1] = t.y;
               }
