@@ -64,6 +64,8 @@ def args_parse():
     ap.add_argument("--err-iters", type=int, default=30000)
     ap.add_argument("--err-steps", type=int, default=3)
     ap.add_argument("--sat-n", type=int, default=4096)
+    ap.add_argument("--degree-n", type=int, default=512,
+                    help="mesh of the degree-2/3/4 FP64 saturation-step leg (0: skip)")
     ap.add_argument("--only-saturation", action="store_true",
                     help="run only the saturation-kernel block (a profiling aid) and print it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -496,6 +498,66 @@ def unit_rates():
     return {"per_sm_per_clock": {k: out[5 + i] for i, k in enumerate(names)},
             "per_s_at_probe_clock": {k: out[i] for i, k in enumerate(names)},
             "probe_sm_mhz": out[10]}
+
+
+# FP64 work of the degree-p element kernel per element, counted from its
+# loops: per Gauss point S, dP/dx, dP/dy (3 Q^2 + 3 Q FMA), the integrand
+# (~40 operations with the sources) and the (p+1)^2 test-function updates
+# (4 Q^2); two flops per FMA.  Q = p + 1 points per axis.
+def degree_flop_per_element(p):
+    q = p + 1
+    return q * q * 2 * (7 * q * q + 3 * q + 40)
+
+
+def degree_step_bench(n, scn, steps=10):
+    """The saturation step for B-splines of degree 2, 3 and 4 (FP64, the
+    generic path, ads_degree_step) on an n^2 mesh: ms per step by CUDA events
+    over `steps` steps after two untimed ones, element-steps/s, and the
+    element kernel's FP64 rate against the FP64 peak (2 FMA per clock per SM
+    on this GPU: 152 x 2 x 2 x 2070 MHz = 1.26 TFLOP/s)."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    from paper_2604_20731_gb300 import _lib
+    from paper_2604_20731_gb300.solver import make_params
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    out = {"mesh": f"{n}^2 elements", "fp64_peak_tflops": 152 * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12}
+    for p in (2, 3, 4):
+        sc = scn.make_scenario(2, n, seed=1000, S0="random")
+        params = make_params(sc, "f64")
+        plan = C.c_void_p()
+        if lib.ads_degree_plan_create(C.byref(params), p, C.byref(plan)) != 0:
+            out[f"p{p}"] = None
+            continue
+        nb = n + p
+        rng = np.random.default_rng(p)
+        K = torch.from_numpy(np.ascontiguousarray(sc.K, dtype=np.float64)).to(dev)
+        S = torch.from_numpy(rng.uniform(0, 1, size=(nb, nb))).to(dev)
+        P = torch.from_numpy(rng.normal(size=(nb, nb))).to(dev)
+        o1, o2 = torch.empty_like(S), torch.empty_like(S)
+        st = torch.cuda.Stream(device=dev)
+        h = C.c_void_p(st.cuda_stream)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            lib.ads_degree_step(plan, K.data_ptr(), None, S.data_ptr(), P.data_ptr(), 1e-4, o1.data_ptr(), h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        src, dst = o1, o2
+        for _ in range(steps):
+            rc = lib.ads_degree_step(plan, K.data_ptr(), None, src.data_ptr(), P.data_ptr(), 1e-4,
+                                     dst.data_ptr(), h)
+            src, dst = dst, src
+        e1.record(st)
+        st.synchronize()
+        lib.ads_degree_plan_destroy(plan)
+        ms = e0.elapsed_time(e1) / steps
+        fl = degree_flop_per_element(p) * n * n
+        out[f"p{p}"] = {"ms_per_step": ms, "element_steps_per_s": n * n / (ms / 1e3), "status": rc,
+                        "flop_per_element": degree_flop_per_element(p),
+                        "fp64_tflops_whole_step": fl / (ms / 1e3) / 1e12,
+                        "frac_of_fp64_peak": fl / (ms / 1e3) / 1e12 / out["fp64_peak_tflops"]}
+    return out
 
 
 def saturation_roofline(n, scn, HybridSolver, rates=None):
@@ -946,6 +1008,9 @@ def run_ours(a, world, rank, local):
     sat = None
     if rank == 0 and a.sat_n > 0:
         sat = saturation_roofline(a.sat_n, scn, HybridSolver, rates)
+    degree = None
+    if rank == 0 and a.degree_n > 0:
+        degree = degree_step_bench(a.degree_n, scn)
 
     # ---- (5) CPU baseline (rank 0, N=1 only): the oracle on the mix ----
     cpu = None
@@ -965,7 +1030,8 @@ def run_ours(a, world, rank, local):
                # record keeps the end of the line)
                "kernel_ms_by_n": prof_by_n, "unit_rates": rates, "server": server_stats,
                "c3_c5_w128": large, "c2_fp64_sat_fp32_net": c2, "c1_plain_galerkin": c1,
-               "saturation": sat, "base_network": base_info, "admission_training_s": admission_s,
+               "saturation": sat, "degree_p": degree, "base_network": base_info,
+               "admission_training_s": admission_s,
                "error": err,
                "latency_note": "resident run: a scenario's step latency is the round time (all "
                                "scenarios step once per round); e2e holds the server's per-step latency",

@@ -433,6 +433,43 @@ ads_status ads_saturation_step_noalloc(const ads_params* params, const double* d
  * neither call may be used after cudaDeviceReset in the same process. */
 ads_status ads_saturation_step_noalloc_status(void* stream, int* flags_out);
 
+/* ---- saturation step for B-splines of degree 2, 3 or 4 ---------------------
+ * Sec. 4 writes the basis for a general order r with continuity C^{r-1}
+ * (Eq. 11); Sec. 8 runs r = 2, which is what the context path implements.
+ * These calls take the explicit step of Eqs. 10b-13 with the Kronecker mass
+ * solve of Eq. 14 for degree p in {2, 3, 4} on an open uniform knot vector,
+ * 2D, FP64 (same readings as ads_saturation_step: clamped mobility, phi inside
+ * the integrand, nodal K and phi interpolated bilinearly, normalised Gaussian
+ * sources with the producer's gas share f_g(S), no-flux boundary).  Written for
+ * any p and for correctness first: (p+1)^2 Gauss points per element, one
+ * thread per element, per degree of freedom and per line; not the quadratic
+ * path's tuned kernels.
+ *   ads_degree_plan_create: builds the tables for params (the same check as
+ *     ads_init; dim 2 and ads_dtype ADS_F64 only, else ADS_ERR_UNSUPPORTED;
+ *     degree outside 2..4 or n > 4096: ADS_ERR_INVALID_ARG) and allocates
+ *     the device memory of the plan (about n^2 (p+1)^2 doubles), which the
+ *     plan owns; *plan = NULL on failure.  Synchronous.
+ *   ads_degree_coeffs: coefficients per axis, n + p (0 for NULL).
+ *   ads_degree_step: S_out = M^-1 R(S, P) with the step size dt (> 0,
+ *     finite).  Device pointers, row-major with x fastest: d_K and d_phi
+ *     (NULL: params->phi) (n+1)^2 nodal values; d_S, d_P, d_S_out (n+p)^2
+ *     coefficients; d_S_out must differ from d_S and d_P.  Enqueued on
+ *     `stream` (cudaStream_t; NULL = legacy default stream), returns after
+ *     enqueueing.  One plan's calls must not overlap on the GPU (they share
+ *     its working memory).
+ *   ads_degree_mass: int S over the unit square for the (n+p)^2 coefficients
+ *     d_S; waits (bounded: ADS_ERR_TIMEOUT after 10 s) for `stream` and
+ *     writes *mass.
+ *   ads_degree_plan_destroy: frees the plan (NULL: no-op); call it after the
+ *     plan's work has completed. */
+typedef struct ads_degree_plan ads_degree_plan;
+ads_status ads_degree_plan_create(const ads_params* params, int degree, ads_degree_plan** plan);
+int ads_degree_coeffs(const ads_degree_plan* plan);
+ads_status ads_degree_step(ads_degree_plan* plan, const double* d_K, const double* d_phi, const double* d_S,
+                           const double* d_P, double dt, double* d_S_out, void* stream);
+ads_status ads_degree_mass(ads_degree_plan* plan, const double* d_S, double* mass, void* stream);
+void ads_degree_plan_destroy(ads_degree_plan* plan);
+
 /* ---- diagnostics (no counterpart in the paper) ------------------------------
  * ads_kernel_launches: number of library kernels enqueued on this context so
  * far (a graph replay counts the kernels it contains).

@@ -1,0 +1,470 @@
+// Explicit saturation step for tensor B-splines of degree p = 2, 3 or 4 (Sec. 4:
+// the basis of order r with continuity C^{r-1}, Eq. 11; the step of Eqs.
+// 10b-13 and the Kronecker mass solve of Eq. 14), 2D, FP64.
+//
+// The quadratic path of ads_kernels.cu is shaped around p = 2 (three Gauss
+// points, three functions per element, warp-shuffle assembly).  This path is
+// written for any p up to 4 and for correctness first:
+//   * the tables -- Gauss-Legendre points (p + 1 per element), the values and
+//     derivatives of the p + 1 functions alive on each element, the banded
+//     1D mass matrix M (bandwidth p), its LDL^T factors, the basis integrals
+//     and the sources' per-axis Gaussian factors -- are computed on the host
+//     once per plan (Cox-de Boor recursion on the open uniform knot vector)
+//     and copied to the device;
+//   * one thread per element evaluates the (p + 1)^2 Gauss points and writes
+//     its (p + 1)^2 local right-hand-side terms;
+//   * one thread per degree of freedom adds the terms of the (p + 1)^2
+//     elements around it in a fixed order (no atomics: the sums do not depend
+//     on scheduling);
+//   * one thread per line solves M x = r along x, then along y, with the
+//     banded factors (forward, diagonal, backward substitution).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "adsgb.h"
+#include "kernels.cuh"
+
+namespace adsgb {
+ads_status validate_params(const ads_params* p, const crvpinn_params* cp);  // api.cu
+
+namespace {
+
+constexpr int kMaxDeg = 4;
+constexpr int kMaxDegN = 4096;  // largest mesh a plan takes
+
+// arguments of the element kernel
+struct DegArgs {
+  int n, nb, n_src;
+  double h2;                      // h^2 (the Jacobian of an element)
+  double wq[kMaxDeg + 1];         // Gauss weights on [0, 1]
+  double xi[kMaxDeg + 1];         // Gauss points on [0, 1] (the hat functions of the nodal maps)
+  const double* B;                // [n][p+1 functions][p+1 points]
+  const double* dB;               // d/dx, same layout
+  const double* g;                // [2 axes][n_src][n][p+1]: per-axis Gaussian factors
+  double rate[kMaxSrc];
+  int kind[kMaxSrc];
+  double inv_mu_g, inv_mu_w, grav_term, phi_c, dt;
+  const double *K, *phi, *S, *P;  // K, phi nodal (n+1)^2 (phi nullable); S, P (n+p)^2
+  double* part;                   // [n][n][p+1][p+1] local terms
+};
+
+// One element: the weak form's integrand at the (p+1)^2 Gauss points (the
+// same terms as the quadratic path) and its local terms against the (p+1)^2
+// test functions alive on the element.
+template <int P>
+__global__ void __launch_bounds__(128) k_deg_elem(DegArgs a) {
+  constexpr int Q = P + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n * a.n) return;
+  const int ex = e % a.n, ey = e / a.n, n1 = a.n + 1;
+  double s[Q][Q], pp[Q][Q];  // coefficients [row b][column c] of S and P on the element
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+      s[b][c] = a.S[(size_t)(ey + b) * a.nb + ex + c];
+      pp[b][c] = a.P[(size_t)(ey + b) * a.nb + ex + c];
+    }
+  const double* Bx = a.B + (size_t)ex * Q * Q;
+  const double* dBx = a.dB + (size_t)ex * Q * Q;
+  const double* By = a.B + (size_t)ey * Q * Q;
+  const double* dBy = a.dB + (size_t)ey * Q * Q;
+  const double k00 = a.K[(size_t)ey * n1 + ex], k01 = a.K[(size_t)ey * n1 + ex + 1];
+  const double k10 = a.K[(size_t)(ey + 1) * n1 + ex], k11 = a.K[(size_t)(ey + 1) * n1 + ex + 1];
+  double f00 = a.phi_c, f01 = a.phi_c, f10 = a.phi_c, f11 = a.phi_c;
+  if (a.phi) {
+    f00 = a.phi[(size_t)ey * n1 + ex];
+    f01 = a.phi[(size_t)ey * n1 + ex + 1];
+    f10 = a.phi[(size_t)(ey + 1) * n1 + ex];
+    f11 = a.phi[(size_t)(ey + 1) * n1 + ex + 1];
+  }
+  double r[Q][Q];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) r[b][c] = 0.0;
+  for (int qy = 0; qy < Q; ++qy) {
+    const double eta = a.xi[qy];
+    for (int qx = 0; qx < Q; ++qx) {
+      const double xi = a.xi[qx];
+      // S, dP/dx, dP/dy at the point
+      double Sv = 0.0, px = 0.0, py = 0.0;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        double sb = 0.0, pb = 0.0, pdb = 0.0;
+#pragma unroll
+        for (int c = 0; c < Q; ++c) {
+          sb += s[b][c] * Bx[c * Q + qx];
+          pb += pp[b][c] * Bx[c * Q + qx];
+          pdb += pp[b][c] * dBx[c * Q + qx];
+        }
+        Sv += By[b * Q + qy] * sb;
+        px += By[b * Q + qy] * pdb;
+        py += dBy[b * Q + qy] * pb;
+      }
+      const double Kq = (1.0 - eta) * ((1.0 - xi) * k00 + xi * k01) + eta * ((1.0 - xi) * k10 + xi * k11);
+      const double phq = (1.0 - eta) * ((1.0 - xi) * f00 + xi * f01) + eta * ((1.0 - xi) * f10 + xi * f11);
+      const double St = Sv < 0.0 ? 0.0 : (Sv > 1.0 ? 1.0 : Sv);
+      const double lg = St * a.inv_mu_g, lw = (1.0 - St) * a.inv_mu_w;
+      double qi = 0.0, qp = 0.0;
+      for (int k = 0; k < a.n_src; ++k) {
+        const double gv = a.rate[k] * a.g[((size_t)(0 * a.n_src + k) * a.n + ex) * Q + qx] *
+                          a.g[((size_t)(1 * a.n_src + k) * a.n + ey) * Q + qy];
+        if (a.kind[k] == 0) qi += gv;
+        else qp += gv;
+      }
+      const double qg = qi - lg / (lg + lw) * qp;
+      const double W = a.wq[qx] * a.wq[qy] * a.h2;
+      const double c0 = W * (Sv + a.dt / phq * qg);
+      const double cf = -W * a.dt / phq * lg * Kq;
+      const double cx = cf * px, cy = cf * (py + a.grav_term);
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        const double vb = By[b * Q + qy], dvb = dBy[b * Q + qy];
+#pragma unroll
+        for (int c = 0; c < Q; ++c)
+          r[b][c] += (c0 * vb + cy * dvb) * Bx[c * Q + qx] + cx * vb * dBx[c * Q + qx];
+      }
+    }
+  }
+  double* o = a.part + (size_t)e * Q * Q;
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) o[b * Q + c] = r[b][c];
+}
+
+// One degree of freedom (j, i): the local terms of the elements (ey, ex) with
+// ey in [j - p, j], ex in [i - p, i], added in a fixed order
+template <int P>
+__global__ void __launch_bounds__(256) k_deg_gather(const double* __restrict__ part, int n, double* __restrict__ R) {
+  constexpr int Q = P + 1;
+  const int nb = n + P;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nb * nb) return;
+  const int i = d % nb, j = d / nb;
+  double v = 0.0;
+  for (int ey = j - P; ey <= j; ++ey) {
+    if (ey < 0 || ey >= n) continue;
+    for (int ex = i - P; ex <= i; ++ex) {
+      if (ex < 0 || ex >= n) continue;
+      v += part[((size_t)ey * n + ex) * Q * Q + (j - ey) * Q + (i - ex)];
+    }
+  }
+  R[d] = v;
+}
+
+// M x = r along lines of nb values, in place: line t starts at R + t * lstride
+// and steps by estride.  L[k][l] = L_{l, l-k} (k = 1..p) of the unit lower
+// factor, dinv[l] = 1 / D_l.
+template <int P>
+__global__ void __launch_bounds__(128) k_deg_lines(double* R, int nb, int nlines, size_t lstride, size_t estride,
+                                                   const double* __restrict__ L, const double* __restrict__ dinv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlines) return;
+  double* x = R + (size_t)t * lstride;
+  double y[P];  // the last p values of the forward (or backward) recurrence
+#pragma unroll
+  for (int k = 0; k < P; ++k) y[k] = 0.0;
+  for (int l = 0; l < nb; ++l) {
+    double v = x[(size_t)l * estride];
+#pragma unroll
+    for (int k = 1; k <= P; ++k) v -= L[(size_t)(k - 1) * nb + l] * y[k - 1];
+#pragma unroll
+    for (int k = P - 1; k > 0; --k) y[k] = y[k - 1];
+    y[0] = v;
+    x[(size_t)l * estride] = v * dinv[l];
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) y[k] = 0.0;
+  for (int l = nb - 1; l >= 0; --l) {
+    double v = x[(size_t)l * estride];
+#pragma unroll
+    for (int k = 1; k <= P; ++k)
+      if (l + k < nb) v -= L[(size_t)(k - 1) * nb + l + k] * y[k - 1];
+#pragma unroll
+    for (int k = P - 1; k > 0; --k) y[k] = y[k - 1];
+    y[0] = v;
+    x[(size_t)l * estride] = v;
+  }
+}
+
+// int S = sum_j sum_i Iw_j Iw_i S_ji, one block, a fixed order
+__global__ void __launch_bounds__(1024) k_deg_mass(const double* __restrict__ S, int nb, const double* __restrict__ Iw,
+                                                   double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (size_t d = threadIdx.x; d < (size_t)nb * nb; d += blockDim.x) m += Iw[d / nb] * Iw[d % nb] * S[d];
+  const double tot = block_sum(m, red);
+  if (threadIdx.x == 0) *out = tot;
+}
+
+// ---------------------------------------------------------------- host tables
+
+// Gauss-Legendre rule with q points on [0, 1]: the roots of the Legendre
+// polynomial P_q by Newton's method (three-term recurrence for P_q and its
+// derivative), weights 1 / ((1 - t^2) P_q'(t)^2) on [0, 1].
+void gauss_legendre01(int q, double* x, double* w) {
+  for (int i = 0; i < q; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (q + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= q; ++k) {
+        const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q * (t * p1 - p0) / (t * t - 1.0);
+      const double step = p1 / dp;
+      t -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= q; ++k) {
+      const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = q * (t * p1 - p0) / (t * t - 1.0);
+    x[q - 1 - i] = 0.5 * (t + 1.0);  // ascending
+    w[q - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+// Cox-de Boor: the B-spline i of degree k on the knots t, at x (0/0 read as 0)
+double bspline(const std::vector<double>& t, int i, int k, double x) {
+  if (k == 0) return (t[i] <= x && x < t[i + 1]) ? 1.0 : 0.0;
+  double v = 0.0;
+  const double d1 = t[i + k] - t[i], d2 = t[i + k + 1] - t[i + 1];
+  if (d1 > 0) v += (x - t[i]) / d1 * bspline(t, i, k - 1, x);
+  if (d2 > 0) v += (t[i + k + 1] - x) / d2 * bspline(t, i + 1, k - 1, x);
+  return v;
+}
+// its derivative: k (N_{i,k-1} / (t_{i+k} - t_i) - N_{i+1,k-1} / (t_{i+k+1} - t_{i+1}))
+double bspline_d(const std::vector<double>& t, int i, int k, double x) {
+  double v = 0.0;
+  const double d1 = t[i + k] - t[i], d2 = t[i + k + 1] - t[i + 1];
+  if (d1 > 0) v += k / d1 * bspline(t, i, k - 1, x);
+  if (d2 > 0) v -= k / d2 * bspline(t, i + 1, k - 1, x);
+  return v;
+}
+
+cudaError_t wait_stream_for(cudaStream_t st, double seconds) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e != cudaErrorNotReady) return e;
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds)
+      return cudaErrorNotReady;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+}  // namespace
+}  // namespace adsgb
+
+struct ads_degree_plan {
+  int p = 0, n = 0, nb = 0;
+  adsgb::DegArgs args{};              // everything but the per-call fields
+  double* dev = nullptr;              // one allocation: tables, local terms, mass
+  double *B = nullptr, *dB = nullptr, *g = nullptr, *L = nullptr, *dinv = nullptr, *Iw = nullptr;
+  double *part = nullptr, *mass = nullptr;
+};
+
+using adsgb::DegArgs;
+
+extern "C" ads_status ads_degree_plan_create(const ads_params* params, int degree, ads_degree_plan** out) {
+  using namespace adsgb;
+  if (!out) return ADS_ERR_INVALID_ARG;
+  *out = nullptr;
+  const ads_status v = validate_params(params, nullptr);
+  if (v != ADS_OK) return v;
+  if (params->dim != 2 || params->ads_dtype != ADS_F64) return ADS_ERR_UNSUPPORTED;
+  if (degree < 2 || degree > kMaxDeg) return ADS_ERR_INVALID_ARG;
+  if (params->n > kMaxDegN) return ADS_ERR_INVALID_ARG;
+  const int p = degree, q = p + 1, n = params->n, nb = n + p;
+  const double h = 1.0 / n;
+  // knots: p + 1 zeros, the interior nodes, p + 1 ones
+  std::vector<double> t(n + 2 * p + 1);
+  for (int k = 0; k < (int)t.size(); ++k) t[k] = k <= p ? 0.0 : (k >= n + p ? 1.0 : (double)(k - p) / n);
+  double xq[kMaxDeg + 1], wq[kMaxDeg + 1];
+  gauss_legendre01(q, xq, wq);
+  // values and derivatives of functions e .. e + p on element e at its points
+  std::vector<double> B((size_t)n * q * q), dB((size_t)n * q * q);
+  for (int e = 0; e < n; ++e)
+    for (int a = 0; a < q; ++a)
+      for (int k = 0; k < q; ++k) {
+        const double x = (e + xq[k]) * h;
+        B[((size_t)e * q + a) * q + k] = bspline(t, e + a, p, x);
+        dB[((size_t)e * q + a) * q + k] = bspline_d(t, e + a, p, x);
+      }
+  // banded mass matrix Mb[k][i] = M_{i, i+k} (k = 0..p) and the basis integrals
+  std::vector<double> Mb((size_t)q * nb, 0.0), Iw(nb, 0.0);
+  for (int e = 0; e < n; ++e)
+    for (int k = 0; k < q; ++k) {
+      const double wk = wq[k] * h;
+      for (int a = 0; a < q; ++a) {
+        const double ba = B[((size_t)e * q + a) * q + k];
+        Iw[e + a] += wk * ba;
+        for (int c = a; c < q; ++c) Mb[(size_t)(c - a) * nb + e + a] += wk * ba * B[((size_t)e * q + c) * q + k];
+      }
+    }
+  // M = L D L^T, L unit lower with bandwidth p: Lf[k][l] = L_{l, l-k}
+  std::vector<double> Lf((size_t)p * nb, 0.0), D(nb, 0.0), dinv(nb, 0.0);
+  auto Lget = [&](int l, int k) { return k == 0 ? 1.0 : Lf[(size_t)(k - 1) * nb + l]; };
+  for (int l = 0; l < nb; ++l) {
+    for (int k = std::min(p, l); k >= 1; --k) {
+      double v = Mb[(size_t)k * nb + (l - k)];  // M_{l-k, l}
+      for (int j = k + 1; j <= std::min(p, l); ++j) v -= Lget(l, j) * D[l - j] * Lget(l - k, j - k);
+      Lf[(size_t)(k - 1) * nb + l] = v / D[l - k];
+    }
+    double d = Mb[l];
+    for (int j = 1; j <= std::min(p, l); ++j) d -= Lget(l, j) * Lget(l, j) * D[l - j];
+    if (!(d > 0)) return ADS_ERR_INVALID_ARG;  // M is SPD; a zero pivot means a broken table
+    D[l] = d;
+    dinv[l] = 1.0 / d;
+  }
+  // per-axis Gaussian factors: exp(-(x - c)^2 / (2 s^2)) / sqrt(2 pi s^2); their
+  // product over the two axes is the normalised 2D Gaussian of each source
+  const int ns = params->n_src;
+  std::vector<double> g((size_t)2 * (ns > 0 ? ns : 1) * n * q, 0.0);
+  for (int ax = 0; ax < 2; ++ax)
+    for (int k = 0; k < ns; ++k) {
+      const double c = params->src[k].center[ax], s = params->src[k].sigma;
+      for (int e = 0; e < n; ++e)
+        for (int j = 0; j < q; ++j) {
+          const double x = (e + xq[j]) * h;
+          g[((size_t)(ax * ns + k) * n + e) * q + j] =
+              std::exp(-(x - c) * (x - c) / (2.0 * s * s)) / std::sqrt(2.0 * M_PI * s * s);
+        }
+    }
+  auto* pl = new (std::nothrow) ads_degree_plan();
+  if (!pl) return ADS_ERR_OOM;
+  pl->p = p;
+  pl->n = n;
+  pl->nb = nb;
+  const size_t nB = B.size(), ng = g.size(), nL = Lf.size(), npart = (size_t)n * n * q * q;
+  const size_t total = 2 * nB + ng + nL + 2 * (size_t)nb + npart + 1;
+  if (cudaMalloc(&pl->dev, total * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return ADS_ERR_OOM;
+  }
+  double* c = pl->dev;
+  pl->B = c; c += nB;
+  pl->dB = c; c += nB;
+  pl->g = c; c += ng;
+  pl->L = c; c += nL;
+  pl->dinv = c; c += nb;
+  pl->Iw = c; c += nb;
+  pl->part = c; c += npart;
+  pl->mass = c;
+  bool ok = cudaMemcpy(pl->B, B.data(), nB * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->dB, dB.data(), nB * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->g, g.data(), ng * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->L, Lf.data(), nL * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->dinv, dinv.data(), (size_t)nb * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->Iw, Iw.data(), (size_t)nb * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(pl->dev);
+    delete pl;
+    return ADS_ERR_CUDA;
+  }
+  DegArgs& a = pl->args;
+  a.n = n;
+  a.nb = nb;
+  a.n_src = ns;
+  a.h2 = h * h;
+  for (int k = 0; k < q; ++k) {
+    a.wq[k] = wq[k];
+    a.xi[k] = xq[k];
+  }
+  a.B = pl->B;
+  a.dB = pl->dB;
+  a.g = pl->g;
+  for (int k = 0; k < ns; ++k) {
+    a.rate[k] = params->src[k].rate;
+    a.kind[k] = params->src[k].kind;
+  }
+  a.inv_mu_g = 1.0 / params->mu_g;
+  a.inv_mu_w = 1.0 / params->mu_w;
+  a.grav_term = params->grav_sign * params->rho_g * params->grav;
+  a.phi_c = params->phi;
+  a.part = pl->part;
+  *out = pl;
+  return ADS_OK;
+}
+
+extern "C" ads_status ads_degree_step(ads_degree_plan* pl, const double* d_K, const double* d_phi,
+                                      const double* d_S, const double* d_P, double dt, double* d_S_out,
+                                      void* stream) {
+  using namespace adsgb;
+  if (!pl || !d_K || !d_S || !d_P || !d_S_out) return ADS_ERR_INVALID_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return ADS_ERR_INVALID_ARG;
+  if (d_S_out == d_S || d_S_out == d_P) return ADS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DegArgs a = pl->args;
+  a.K = d_K;
+  a.phi = d_phi;
+  a.S = d_S;
+  a.P = d_P;
+  a.dt = dt;
+  const int n = pl->n, nb = pl->nb, ne = n * n;
+  switch (pl->p) {
+    case 2: k_deg_elem<2><<<(ne + 127) / 128, 128, 0, st>>>(a); break;
+    case 3: k_deg_elem<3><<<(ne + 127) / 128, 128, 0, st>>>(a); break;
+    default: k_deg_elem<4><<<(ne + 127) / 128, 128, 0, st>>>(a); break;
+  }
+  const int nd = nb * nb;
+  switch (pl->p) {
+    case 2: k_deg_gather<2><<<(nd + 255) / 256, 256, 0, st>>>(pl->part, n, d_S_out); break;
+    case 3: k_deg_gather<3><<<(nd + 255) / 256, 256, 0, st>>>(pl->part, n, d_S_out); break;
+    default: k_deg_gather<4><<<(nd + 255) / 256, 256, 0, st>>>(pl->part, n, d_S_out); break;
+  }
+  // along x (rows: lines nb apart, entries adjacent), then along y
+  const int g = (nb + 127) / 128;
+  switch (pl->p) {
+    case 2:
+      k_deg_lines<2><<<g, 128, 0, st>>>(d_S_out, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
+      k_deg_lines<2><<<g, 128, 0, st>>>(d_S_out, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
+      break;
+    case 3:
+      k_deg_lines<3><<<g, 128, 0, st>>>(d_S_out, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
+      k_deg_lines<3><<<g, 128, 0, st>>>(d_S_out, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
+      break;
+    default:
+      k_deg_lines<4><<<g, 128, 0, st>>>(d_S_out, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
+      k_deg_lines<4><<<g, 128, 0, st>>>(d_S_out, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
+      break;
+  }
+  return cudaGetLastError() == cudaSuccess ? ADS_OK : ADS_ERR_CUDA;
+}
+
+extern "C" ads_status ads_degree_mass(ads_degree_plan* pl, const double* d_S, double* mass, void* stream) {
+  using namespace adsgb;
+  if (!pl || !d_S || !mass) return ADS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_deg_mass<<<1, 1024, 0, st>>>(d_S, pl->nb, pl->Iw, pl->mass);
+  if (cudaGetLastError() != cudaSuccess) return ADS_ERR_CUDA;
+  if (cudaMemcpyAsync(mass, pl->mass, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    return ADS_ERR_CUDA;
+  }
+  const cudaError_t e = wait_stream_for(st, 10.0);
+  if (e == cudaErrorNotReady) return ADS_ERR_TIMEOUT;
+  return e == cudaSuccess ? ADS_OK : ADS_ERR_CUDA;
+}
+
+extern "C" int ads_degree_coeffs(const ads_degree_plan* pl) { return pl ? pl->nb : 0; }
+
+extern "C" void ads_degree_plan_destroy(ads_degree_plan* pl) {
+  if (!pl) return;
+  cudaFree(pl->dev);
+  delete pl;
+}

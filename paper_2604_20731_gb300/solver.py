@@ -18,9 +18,13 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_params(sc, ads_dtype: str = "f64") -> L.ads_params:
-    if getattr(sc, "p", 2) != 2:
-        raise ValueError("the library implements quadratic B-splines (p = 2) only")
+def make_params(sc, ads_dtype: str = "f64", any_degree: bool = False) -> L.ads_params:
+    """ads_params of a scenario.  The context path (ads_init) is quadratic
+    (p = 2); any_degree=True is for the degree-p plans (ads_degree_*), which
+    take the degree as an argument of their own."""
+    if getattr(sc, "p", 2) != 2 and not any_degree:
+        raise ValueError("the context path implements quadratic B-splines (p = 2); "
+                         "use the degree-p plans (ads_degree_*) for p = 3, 4")
     p = L.ads_params()
     p.dim, p.n = sc.dim, sc.n
     p.phi = float(sc.phi)

@@ -230,7 +230,8 @@ def test_binding_return_types_match_header():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"typedef[^;]*;", "", src)
-    expect = {"ads_status": C.c_int, "size_t": C.c_size_t, "void": None, "const char*": C.c_char_p}
+    expect = {"ads_status": C.c_int, "size_t": C.c_size_t, "void": None, "const char*": C.c_char_p,
+              "int": C.c_int}
     seen = 0
     for m in re.finditer(r"^\s*((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?)\s*([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
         ret, name = re.sub(r"\s+\*", "*", m.group(1).strip()), m.group(2)
@@ -332,7 +333,8 @@ skip = {"ads_init", "ads_init_with_allocator", "ads_hbm_estimate", "ads_status_s
         "ads_saturation_step_noalloc", "ads_saturation_step_noalloc_status", "hybrid_step_batch"}
 res = {}
 for name, (rt, args) in _lib.SIGNATURES.items():
-    if name in skip or name.startswith("ads_server_") or not args or args[0] is not C.c_void_p:
+    if (name in skip or name.startswith("ads_server_") or name.startswith("ads_degree_") or not args
+            or args[0] is not C.c_void_p):
         continue
     vals = [None]
     for a in args[1:]:
@@ -374,7 +376,25 @@ na = {"same_in_out": noalloc(lambda p: None, same=True), "dim3": noalloc(lambda 
       "sigma0": noalloc(lambda p: setattr(p.src[0], "sigma", 0.0)),
       "kind2": noalloc(lambda p: setattr(p.src[0], "kind", 2))}
 na["null"] = lib.ads_saturation_step_noalloc(None, None, None, None, None, 1e-3, None, None)
-print(json.dumps({"ctx": res, "server": srv, "noalloc": na}))
+# degree-p plans: refusals before any CUDA call; the steps refuse a NULL plan
+def degree(mut, deg=3):
+    p = make_params(scn.make_scenario(2, 8), "f64")
+    mut(p)
+    plan = C.c_void_p(0x1)
+    rc = lib.ads_degree_plan_create(C.byref(p), deg, C.byref(plan))
+    return [rc, plan.value is None]
+dg = {"deg1": degree(lambda p: None, 1), "deg5": degree(lambda p: None, 5),
+      "dim3": degree(lambda p: setattr(p, "dim", 3)), "f32": degree(lambda p: setattr(p, "ads_dtype", 1)),
+      "n4097": degree(lambda p: setattr(p, "n", 4097)), "n1": degree(lambda p: setattr(p, "n", 1)),
+      "rate_neg": degree(lambda p: setattr(p.src[0], "rate", -1.0)),
+      "grav_nan": degree(lambda p: setattr(p, "grav", math.nan))}
+dg["null_out"] = [lib.ads_degree_plan_create(C.byref(make_params(scn.make_scenario(2, 8), "f64")), 3, None), True]
+dg["null_params"] = [lib.ads_degree_plan_create(None, 3, C.byref(C.c_void_p())), True]
+dg["step_null_plan"] = [lib.ads_degree_step(None, None, None, None, None, 1e-3, None, None), True]
+dg["mass_null_plan"] = [lib.ads_degree_mass(None, None, C.byref(C.c_double()), None), True]
+dg["coeffs_null"] = [lib.ads_degree_coeffs(None), True]
+lib.ads_degree_plan_destroy(None)
+print(json.dumps({"ctx": res, "server": srv, "noalloc": na, "degree": dg}))
 """
 
 
@@ -404,3 +424,7 @@ def test_null_handles_and_refused_arguments_before_any_cuda_call(lib):
     refused = ("same_in_out", "n513", "dt0", "dt_inf", "nsrc9", "n1", "grav_nan", "grav_neg",
                "grav_sign_nan", "rate_neg", "rate_inf", "sigma0", "kind2", "null")
     assert all(na[k] == 1 for k in refused), na
+    dg = r["degree"]
+    assert dg.pop("dim3") == [7, True] and dg.pop("f32") == [7, True]
+    assert dg.pop("coeffs_null") == [0, True]
+    assert all(v == [1, True] for v in dg.values()), dg

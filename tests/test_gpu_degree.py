@@ -1,0 +1,155 @@
+"""The saturation step for B-splines of degree 2, 3 and 4 (ads_degree_*)
+against the FP64 oracle of the same degree, through the C ABI.
+
+The oracle's degree-p path is pinned on the CPU (test_oracle_pins.py: mass
+matrix, partition of unity, the Kronecker solve against a dense one).  Here
+the GPU step must agree with it to FP64 rounding on meshes that are small,
+ragged and larger than one block of threads, with a porosity map, gravity and
+injectors as well as producers; at degree 2 it must also agree with the
+quadratic context path (ads_saturation_step).
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle.ads import AdsOracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n, p, seed):
+    from paper_2604_20731_gb300 import scenario as scn
+    sc = scn.make_scenario(2, n, seed=seed, S0="random", grav=0.4)
+    sc.sources = [
+        scn.Source(center=(0.2, 0.3), rate=1.3, kind=scn.SRC_INJECT),
+        scn.Source(center=(0.7, 0.25), rate=0.6, sigma=0.05, kind=scn.SRC_INJECT),
+        scn.Source(center=(0.8, 0.8), rate=1.1, kind=scn.SRC_PRODUCE),
+    ]
+    rng = np.random.default_rng(seed + 1)
+    sc.phi_map = 0.1 + 0.3 * rng.uniform(size=(n + 1, n + 1))
+    sc.p = p
+    nb = n + p
+    S = rng.uniform(-0.1, 1.1, size=(nb, nb))
+    P = rng.normal(size=(nb, nb))
+    return sc, S, P
+
+
+def _plan(lib, sc, p):
+    from paper_2604_20731_gb300.solver import make_params
+    params = make_params(sc, "f64", any_degree=True)
+    plan = C.c_void_p()
+    rc = lib.ads_degree_plan_create(C.byref(params), p, C.byref(plan))
+    assert rc == 0 and plan.value
+    return plan, params
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("n", [4, 33, 160])
+def test_degree_step_matches_oracle(p, n):
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_20731_gb300 import _lib
+    lib = _lib.load()
+    sc, S, P = _case(n, p, seed=100 + 7 * n + p)
+    plan, _ = _plan(lib, sc, p)
+    try:
+        assert lib.ads_degree_coeffs(plan) == n + p
+        dev = torch.device("cuda", 0)
+        K = torch.from_numpy(np.ascontiguousarray(sc.K, dtype=np.float64)).to(dev)
+        phi = torch.from_numpy(np.ascontiguousarray(sc.phi_map)).to(dev)
+        Sd = torch.from_numpy(S).to(dev)
+        Pd = torch.from_numpy(P).to(dev)
+        out = torch.empty_like(Sd)
+        out2 = torch.empty_like(Sd)
+        dt = 2e-4
+        st = torch.cuda.Stream(device=dev)
+        h = C.c_void_p(st.cuda_stream)
+        torch.cuda.synchronize()
+        # two steps: S1 = step(S), S2 = step(S1)
+        assert lib.ads_degree_step(plan, K.data_ptr(), phi.data_ptr(), Sd.data_ptr(), Pd.data_ptr(), dt,
+                                   out.data_ptr(), h) == 0
+        assert lib.ads_degree_step(plan, K.data_ptr(), phi.data_ptr(), out.data_ptr(), Pd.data_ptr(), dt,
+                                   out2.data_ptr(), h) == 0
+        mass = C.c_double()
+        assert lib.ads_degree_mass(plan, out2.data_ptr(), C.byref(mass), h) == 0
+        a = AdsOracle(sc)
+        ref1 = a.step(S, P, dt)
+        ref2 = a.step(ref1, P, dt)
+        for got, ref in ((out.cpu().numpy(), ref1), (out2.cpu().numpy(), ref2)):
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert mass.value == pytest.approx(a.mesh.integral(ref2), rel=1e-12, abs=1e-14)
+        # the step conserves mass up to the sources: int S1 - int S - dt int q_g / phi = 0
+        m0 = C.c_double()
+        assert lib.ads_degree_mass(plan, Sd.data_ptr(), C.byref(m0), h) == 0
+        m1 = C.c_double()
+        assert lib.ads_degree_mass(plan, out.data_ptr(), C.byref(m1), h) == 0
+        assert m1.value - m0.value == pytest.approx(a.source_integral(S, dt), rel=1e-9, abs=1e-15)
+        # without a porosity map: params.phi everywhere
+        sc.phi_map = None
+        assert lib.ads_degree_step(plan, K.data_ptr(), None, Sd.data_ptr(), Pd.data_ptr(), dt,
+                                   out.data_ptr(), h) == 0
+        st.synchronize()
+        ref = AdsOracle(sc).step(S, P, dt)
+        assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    finally:
+        lib.ads_degree_plan_destroy(plan)
+
+
+def test_degree_two_matches_the_quadratic_context_path():
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_20731_gb300 import _lib
+    from paper_2604_20731_gb300.solver import HybridSolver
+    lib = _lib.load()
+    n = 77
+    sc, S, P = _case(n, 2, seed=5)
+    s = HybridSolver(sc, width=None, ads_dtype="f64")
+    plan, _ = _plan(lib, sc, 2)
+    try:
+        s.set_saturation(S)
+        s.set_pressure(P)
+        dt = 3e-4
+        s.saturation_step(dt, 1)
+        ref = s.get("S")
+        dev = torch.device("cuda", 0)
+        K = torch.from_numpy(np.ascontiguousarray(sc.K, dtype=np.float64)).to(dev)
+        phi = torch.from_numpy(np.ascontiguousarray(sc.phi_map)).to(dev)
+        Sd, Pd = torch.from_numpy(S).to(dev), torch.from_numpy(P).to(dev)
+        out = torch.empty_like(Sd)
+        torch.cuda.synchronize()
+        assert lib.ads_degree_step(plan, K.data_ptr(), phi.data_ptr(), Sd.data_ptr(), Pd.data_ptr(), dt,
+                                   out.data_ptr(), None) == 0
+        torch.cuda.synchronize()
+        assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    finally:
+        lib.ads_degree_plan_destroy(plan)
+        s.close()
+
+
+def test_degree_step_refuses_aliasing_and_bad_steps():
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_20731_gb300 import _lib
+    lib = _lib.load()
+    sc, S, P = _case(8, 3, seed=9)
+    plan, _ = _plan(lib, sc, 3)
+    try:
+        dev = torch.device("cuda", 0)
+        K = torch.from_numpy(np.ascontiguousarray(sc.K, dtype=np.float64)).to(dev)
+        Sd, Pd = torch.from_numpy(S).to(dev), torch.from_numpy(P).to(dev)
+        out = torch.empty_like(Sd)
+        for dt in (0.0, -1.0, float("inf"), float("nan")):
+            assert lib.ads_degree_step(plan, K.data_ptr(), None, Sd.data_ptr(), Pd.data_ptr(), dt,
+                                       out.data_ptr(), None) == 1
+        assert lib.ads_degree_step(plan, K.data_ptr(), None, Sd.data_ptr(), Pd.data_ptr(), 1e-4,
+                                   Sd.data_ptr(), None) == 1
+        assert lib.ads_degree_step(plan, K.data_ptr(), None, Sd.data_ptr(), Pd.data_ptr(), 1e-4,
+                                   Pd.data_ptr(), None) == 1
+        assert lib.ads_degree_step(plan, None, None, Sd.data_ptr(), Pd.data_ptr(), 1e-4,
+                                   out.data_ptr(), None) == 1
+    finally:
+        lib.ads_degree_plan_destroy(plan)
