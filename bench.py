@@ -64,6 +64,8 @@ def args_parse():
     ap.add_argument("--err-iters", type=int, default=30000)
     ap.add_argument("--err-steps", type=int, default=3)
     ap.add_argument("--sat-n", type=int, default=4096)
+    ap.add_argument("--only-degree", action="store_true",
+                    help="only the degree-2/3/4 saturation-step leg")
     ap.add_argument("--degree-n", type=int, default=512,
                     help="mesh of the degree-2/3/4 FP64 saturation-step leg (0: skip)")
     ap.add_argument("--only-saturation", action="store_true",
@@ -758,6 +760,10 @@ def run_ours(a, world, rank, local):
     if a.only_saturation:
         if rank == 0:
             print(json.dumps({"saturation": saturation_roofline(a.sat_n, scn, HybridSolver, rates)}), flush=True)
+        return 0
+    if a.only_degree:
+        if rank == 0:
+            print(json.dumps({"degree_p": degree_step_bench(a.degree_n, scn)}), flush=True)
         return 0
     hp = HybridSolver.hybrid_params(n_sub=a.n_sub, dt=1.0, dt_policy=1, cfl=0.1, src_frac=0.05,
                                     adam_iters=a.adam_iters, lr=a.lr)
