@@ -468,6 +468,23 @@ int ads_degree_coeffs(const ads_degree_plan* plan);
 ads_status ads_degree_step(ads_degree_plan* plan, const double* d_K, const double* d_phi, const double* d_S,
                            const double* d_P, double dt, double* d_S_out, void* stream);
 ads_status ads_degree_mass(ads_degree_plan* plan, const double* d_S, double* mass, void* stream);
+/* Vector-Jacobian product of ads_degree_step (a building block of gradients
+ * through the explicit steps, e.g. for placing wells: Sec. 9 names the inverse
+ * problem as future work).  For J = lambda . S_out with S_out the step of the
+ * same arguments (d_K, d_phi, d_S, d_P, dt), it writes
+ *   d_gS = dJ/dS and d_gP = dJ/dP ((n+p)^2 each, device), and, when h_gsrc is
+ *   not NULL, h_gsrc[3k + 0, 1, 2] = dJ/d(rate, centre x, centre y) of
+ *   source k (host, 3 n_src doubles; the call then waits, bounded, for
+ *   `stream`).
+ * d_lambda: (n+p)^2 (device).  Through mu = M^-1 lambda (M symmetric):
+ * J = mu . R(S, P, sources), differentiated at the Gauss points; the clamp
+ * of the mobility is differentiated inside (0, 1) and flat outside, so
+ * gradients are exact away from S = 0 and S = 1 at the Gauss points.
+ * d_gS and d_gP must differ from each other and from the inputs.
+ * ADS_ERR_INVALID_ARG for NULL pointers, aliasing or dt not > 0. */
+ads_status ads_degree_step_vjp(ads_degree_plan* plan, const double* d_K, const double* d_phi, const double* d_S,
+                               const double* d_P, double dt, const double* d_lambda, double* d_gS, double* d_gP,
+                               double* h_gsrc, void* stream);
 void ads_degree_plan_destroy(ads_degree_plan* plan);
 
 /* ---- diagnostics (no counterpart in the paper) ------------------------------

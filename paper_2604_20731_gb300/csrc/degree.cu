@@ -18,6 +18,10 @@
 //     on scheduling);
 //   * one thread per line solves M x = r along x, then along y, with the
 //     banded factors (forward, diagonal, backward substitution).
+// The step's vector-Jacobian product (gradients of J = lambda . S_out with
+// respect to S, P and the sources' rates and centres) serves the inverse
+// problem the conclusions name as future work -- where to put the injection
+// well: it reuses the same tables, line solves and gathers.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -51,6 +55,11 @@ struct DegArgs {
   double inv_mu_g, inv_mu_w, grav_term, phi_c, dt;
   const double *K, *phi, *S, *P;  // K, phi nodal (n+1)^2 (phi nullable); S, P (n+p)^2
   double* part;                   // [n][n][p+1][p+1] local terms
+  // vector-Jacobian product only
+  double cen[kMaxSrc][2], sig[kMaxSrc];
+  const double* mu;               // M^-1 lambda, (n+p)^2
+  double* part2;                  // [n][n][p+1][p+1] local terms of dJ/dP
+  double* psrc;                   // [n][n][3 n_src] per-element d/d(rate, cx, cy) terms
 };
 
 // One element: the weak form's integrand at the (p+1)^2 Gauss points (the
@@ -137,6 +146,134 @@ __global__ void __launch_bounds__(128) k_deg_elem(DegArgs a) {
   for (int b = 0; b < Q; ++b)
 #pragma unroll
     for (int c = 0; c < Q; ++c) o[b * Q + c] = r[b][c];
+}
+
+// Vector-Jacobian product of the step on one element.  With mu = M^-1 lambda
+// (M symmetric), J = lambda . S_out = mu . R(S, P, sources), and
+//   mu . R = sum_q W [ (S + tau/phi q_g(S)) mu_h - tau/phi lambda_g(S) K
+//                      (grad p + s rho_g g e_y) . grad mu_h ]
+// at the Gauss points, mu_h the spline with coefficients mu.  Its partial
+// derivatives at a point, times the basis, give the element's terms of
+// dJ/dS (through S at the point), of dJ/dP (through grad p) and of the
+// sources' rates and centres (through q_g).  The clamp of the mobility is
+// differentiated inside (0, 1) and taken as flat outside.
+template <int P>
+__global__ void __launch_bounds__(128) k_deg_vjp(DegArgs a) {
+  constexpr int Q = P + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n * a.n) return;
+  const int ex = e % a.n, ey = e / a.n, n1 = a.n + 1;
+  const double h = sqrt(a.h2);
+  double s[Q][Q], pp[Q][Q], mu[Q][Q];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+      const size_t o = (size_t)(ey + b) * a.nb + ex + c;
+      s[b][c] = a.S[o];
+      pp[b][c] = a.P[o];
+      mu[b][c] = a.mu[o];
+    }
+  const double* Bx = a.B + (size_t)ex * Q * Q;
+  const double* dBx = a.dB + (size_t)ex * Q * Q;
+  const double* By = a.B + (size_t)ey * Q * Q;
+  const double* dBy = a.dB + (size_t)ey * Q * Q;
+  const double k00 = a.K[(size_t)ey * n1 + ex], k01 = a.K[(size_t)ey * n1 + ex + 1];
+  const double k10 = a.K[(size_t)(ey + 1) * n1 + ex], k11 = a.K[(size_t)(ey + 1) * n1 + ex + 1];
+  double f00 = a.phi_c, f01 = a.phi_c, f10 = a.phi_c, f11 = a.phi_c;
+  if (a.phi) {
+    f00 = a.phi[(size_t)ey * n1 + ex];
+    f01 = a.phi[(size_t)ey * n1 + ex + 1];
+    f10 = a.phi[(size_t)(ey + 1) * n1 + ex];
+    f11 = a.phi[(size_t)(ey + 1) * n1 + ex + 1];
+  }
+  double gs[Q][Q], gp[Q][Q], ps[3 * kMaxSrc];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) gs[b][c] = gp[b][c] = 0.0;
+  for (int k = 0; k < 3 * kMaxSrc; ++k) ps[k] = 0.0;
+  for (int qy = 0; qy < Q; ++qy) {
+    const double eta = a.xi[qy], y = (ey + eta) * h;
+    for (int qx = 0; qx < Q; ++qx) {
+      const double xi = a.xi[qx], x = (ex + xi) * h;
+      double Sv = 0.0, px = 0.0, py = 0.0, mq = 0.0, mqx = 0.0, mqy = 0.0;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        double sb = 0.0, pb = 0.0, pdb = 0.0, mb = 0.0, mdb = 0.0;
+#pragma unroll
+        for (int c = 0; c < Q; ++c) {
+          sb += s[b][c] * Bx[c * Q + qx];
+          pb += pp[b][c] * Bx[c * Q + qx];
+          pdb += pp[b][c] * dBx[c * Q + qx];
+          mb += mu[b][c] * Bx[c * Q + qx];
+          mdb += mu[b][c] * dBx[c * Q + qx];
+        }
+        Sv += By[b * Q + qy] * sb;
+        px += By[b * Q + qy] * pdb;
+        py += dBy[b * Q + qy] * pb;
+        mq += By[b * Q + qy] * mb;
+        mqx += By[b * Q + qy] * mdb;
+        mqy += dBy[b * Q + qy] * mb;
+      }
+      const double Kq = (1.0 - eta) * ((1.0 - xi) * k00 + xi * k01) + eta * ((1.0 - xi) * k10 + xi * k11);
+      const double phq = (1.0 - eta) * ((1.0 - xi) * f00 + xi * f01) + eta * ((1.0 - xi) * f10 + xi * f11);
+      const bool inside = Sv > 0.0 && Sv < 1.0;
+      const double St = Sv < 0.0 ? 0.0 : (Sv > 1.0 ? 1.0 : Sv);
+      const double lg = St * a.inv_mu_g, lw = (1.0 - St) * a.inv_mu_w;
+      const double dlg = inside ? a.inv_mu_g : 0.0, dlw = inside ? -a.inv_mu_w : 0.0;
+      const double lt = lg + lw, fg = lg / lt, dfg = (dlg * lw - lg * dlw) / (lt * lt);
+      double qp = 0.0;
+      for (int k = 0; k < a.n_src; ++k)
+        if (a.kind[k] != 0)
+          qp += a.rate[k] * a.g[((size_t)(0 * a.n_src + k) * a.n + ex) * Q + qx] *
+                a.g[((size_t)(1 * a.n_src + k) * a.n + ey) * Q + qy];
+      const double W = a.wq[qx] * a.wq[qy] * a.h2, tp = a.dt / phq;
+      const double flux = Kq * (px * mqx + (py + a.grav_term) * mqy);
+      const double dFdS = W * ((1.0 - tp * dfg * qp) * mq - tp * dlg * flux);
+      const double dFdpx = -W * tp * lg * Kq * mqx, dFdpy = -W * tp * lg * Kq * mqy;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        const double vb = By[b * Q + qy], dvb = dBy[b * Q + qy];
+#pragma unroll
+        for (int c = 0; c < Q; ++c) {
+          gs[b][c] += dFdS * vb * Bx[c * Q + qx];
+          gp[b][c] += dFdpx * vb * dBx[c * Q + qx] + dFdpy * dvb * Bx[c * Q + qx];
+        }
+      }
+      // sources: q_g = sum_inj rate G - f_g sum_prod rate G, G the normalised
+      // Gaussian; dG/dc = G (x - c) / sigma^2 per coordinate
+      const double wm = W * tp * mq;
+      for (int k = 0; k < a.n_src; ++k) {
+        const double G = a.g[((size_t)(0 * a.n_src + k) * a.n + ex) * Q + qx] *
+                         a.g[((size_t)(1 * a.n_src + k) * a.n + ey) * Q + qy];
+        const double sgn = a.kind[k] == 0 ? 1.0 : -fg, is2 = 1.0 / (a.sig[k] * a.sig[k]);
+        ps[3 * k] += wm * sgn * G;
+        ps[3 * k + 1] += wm * sgn * a.rate[k] * G * (x - a.cen[k][0]) * is2;
+        ps[3 * k + 2] += wm * sgn * a.rate[k] * G * (y - a.cen[k][1]) * is2;
+      }
+    }
+  }
+  double* o = a.part + (size_t)e * Q * Q;
+  double* o2 = a.part2 + (size_t)e * Q * Q;
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+      o[b * Q + c] = gs[b][c];
+      o2[b * Q + c] = gp[b][c];
+    }
+  for (int k = 0; k < 3 * a.n_src; ++k) a.psrc[(size_t)e * 3 * a.n_src + k] = ps[k];
+}
+
+// the per-element source terms summed over the elements in a fixed order:
+// block j sums column j of psrc [ne][ncol]
+__global__ void __launch_bounds__(256) k_deg_colsum(const double* __restrict__ psrc, int ne, int ncol, double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) v += psrc[(size_t)e * ncol + blockIdx.x];
+  const double t = block_sum(v, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
 // One degree of freedom (j, i): the local terms of the elements (ey, ex) with
@@ -274,9 +411,32 @@ struct ads_degree_plan {
   double* dev = nullptr;              // one allocation: tables, local terms, mass
   double *B = nullptr, *dB = nullptr, *g = nullptr, *L = nullptr, *dinv = nullptr, *Iw = nullptr;
   double *part = nullptr, *mass = nullptr;
+  double *part2 = nullptr, *psrc = nullptr, *work = nullptr, *dsrc = nullptr;  // the vector-Jacobian product
 };
 
 using adsgb::DegArgs;
+
+namespace {
+// the fixed-order gather of an element-term array into (n+p)^2 coefficients
+void deg_gather(const ads_degree_plan* pl, const double* part, double* out, cudaStream_t st) {
+  using namespace adsgb;
+  const int nd = pl->nb * pl->nb, g = (nd + 255) / 256;
+  switch (pl->p) {
+    case 2: k_deg_gather<2><<<g, 256, 0, st>>>(part, pl->n, out); break;
+    case 3: k_deg_gather<3><<<g, 256, 0, st>>>(part, pl->n, out); break;
+    default: k_deg_gather<4><<<g, 256, 0, st>>>(part, pl->n, out); break;
+  }
+}
+// x <- M^-1 x in place: the banded solves along x (rows nb apart, entries
+// adjacent), then along y
+void deg_mass_solve(const ads_degree_plan* pl, double* x, cudaStream_t st) {
+  using namespace adsgb;
+  const int nb = pl->nb, g = (nb + 127) / 128;
+  auto k = pl->p == 2 ? k_deg_lines<2> : (pl->p == 3 ? k_deg_lines<3> : k_deg_lines<4>);
+  k<<<g, 128, 0, st>>>(x, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
+  k<<<g, 128, 0, st>>>(x, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
+}
+}  // namespace
 
 extern "C" ads_status ads_degree_plan_create(const ads_params* params, int degree, ads_degree_plan** out) {
   using namespace adsgb;
@@ -349,7 +509,8 @@ extern "C" ads_status ads_degree_plan_create(const ads_params* params, int degre
   pl->n = n;
   pl->nb = nb;
   const size_t nB = B.size(), ng = g.size(), nL = Lf.size(), npart = (size_t)n * n * q * q;
-  const size_t total = 2 * nB + ng + nL + 2 * (size_t)nb + npart + 1;
+  const size_t nps = (size_t)n * n * 3 * (ns > 0 ? ns : 1);
+  const size_t total = 2 * nB + ng + nL + 2 * (size_t)nb + 2 * npart + 1 + nps + (size_t)nb * nb + 3 * kMaxSrc;
   if (cudaMalloc(&pl->dev, total * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     delete pl;
@@ -363,6 +524,10 @@ extern "C" ads_status ads_degree_plan_create(const ads_params* params, int degre
   pl->dinv = c; c += nb;
   pl->Iw = c; c += nb;
   pl->part = c; c += npart;
+  pl->part2 = c; c += npart;
+  pl->psrc = c; c += nps;
+  pl->work = c; c += (size_t)nb * nb;
+  pl->dsrc = c; c += 3 * kMaxSrc;
   pl->mass = c;
   bool ok = cudaMemcpy(pl->B, B.data(), nB * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->dB, dB.data(), nB * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -391,12 +556,17 @@ extern "C" ads_status ads_degree_plan_create(const ads_params* params, int degre
   for (int k = 0; k < ns; ++k) {
     a.rate[k] = params->src[k].rate;
     a.kind[k] = params->src[k].kind;
+    a.cen[k][0] = params->src[k].center[0];
+    a.cen[k][1] = params->src[k].center[1];
+    a.sig[k] = params->src[k].sigma;
   }
   a.inv_mu_g = 1.0 / params->mu_g;
   a.inv_mu_w = 1.0 / params->mu_w;
   a.grav_term = params->grav_sign * params->rho_g * params->grav;
   a.phi_c = params->phi;
   a.part = pl->part;
+  a.part2 = pl->part2;
+  a.psrc = pl->psrc;
   *out = pl;
   return ADS_OK;
 }
@@ -415,35 +585,62 @@ extern "C" ads_status ads_degree_step(ads_degree_plan* pl, const double* d_K, co
   a.S = d_S;
   a.P = d_P;
   a.dt = dt;
-  const int n = pl->n, nb = pl->nb, ne = n * n;
+  const int n = pl->n, ne = n * n;
   switch (pl->p) {
     case 2: k_deg_elem<2><<<(ne + 127) / 128, 128, 0, st>>>(a); break;
     case 3: k_deg_elem<3><<<(ne + 127) / 128, 128, 0, st>>>(a); break;
     default: k_deg_elem<4><<<(ne + 127) / 128, 128, 0, st>>>(a); break;
   }
-  const int nd = nb * nb;
-  switch (pl->p) {
-    case 2: k_deg_gather<2><<<(nd + 255) / 256, 256, 0, st>>>(pl->part, n, d_S_out); break;
-    case 3: k_deg_gather<3><<<(nd + 255) / 256, 256, 0, st>>>(pl->part, n, d_S_out); break;
-    default: k_deg_gather<4><<<(nd + 255) / 256, 256, 0, st>>>(pl->part, n, d_S_out); break;
-  }
-  // along x (rows: lines nb apart, entries adjacent), then along y
-  const int g = (nb + 127) / 128;
-  switch (pl->p) {
-    case 2:
-      k_deg_lines<2><<<g, 128, 0, st>>>(d_S_out, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
-      k_deg_lines<2><<<g, 128, 0, st>>>(d_S_out, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
-      break;
-    case 3:
-      k_deg_lines<3><<<g, 128, 0, st>>>(d_S_out, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
-      k_deg_lines<3><<<g, 128, 0, st>>>(d_S_out, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
-      break;
-    default:
-      k_deg_lines<4><<<g, 128, 0, st>>>(d_S_out, nb, nb, (size_t)nb, 1, pl->L, pl->dinv);
-      k_deg_lines<4><<<g, 128, 0, st>>>(d_S_out, nb, nb, 1, (size_t)nb, pl->L, pl->dinv);
-      break;
-  }
+  deg_gather(pl, pl->part, d_S_out, st);
+  deg_mass_solve(pl, d_S_out, st);
   return cudaGetLastError() == cudaSuccess ? ADS_OK : ADS_ERR_CUDA;
+}
+
+extern "C" ads_status ads_degree_step_vjp(ads_degree_plan* pl, const double* d_K, const double* d_phi,
+                                          const double* d_S, const double* d_P, double dt, const double* d_lambda,
+                                          double* d_gS, double* d_gP, double* h_gsrc, void* stream) {
+  using namespace adsgb;
+  if (!pl || !d_K || !d_S || !d_P || !d_lambda || !d_gS || !d_gP) return ADS_ERR_INVALID_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return ADS_ERR_INVALID_ARG;
+  if (d_gS == d_gP || d_gS == d_S || d_gS == d_P || d_gS == d_lambda || d_gP == d_S || d_gP == d_P ||
+      d_gP == d_lambda)
+    return ADS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = pl->n, nb = pl->nb, ne = n * n, ns = pl->args.n_src;
+  // mu = M^-1 lambda
+  if (cudaMemcpyAsync(pl->work, d_lambda, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return ADS_ERR_CUDA;
+  }
+  deg_mass_solve(pl, pl->work, st);
+  DegArgs a = pl->args;
+  a.K = d_K;
+  a.phi = d_phi;
+  a.S = d_S;
+  a.P = d_P;
+  a.dt = dt;
+  a.mu = pl->work;
+  const int g = (ne + 127) / 128;
+  switch (pl->p) {
+    case 2: k_deg_vjp<2><<<g, 128, 0, st>>>(a); break;
+    case 3: k_deg_vjp<3><<<g, 128, 0, st>>>(a); break;
+    default: k_deg_vjp<4><<<g, 128, 0, st>>>(a); break;
+  }
+  deg_gather(pl, pl->part, d_gS, st);
+  deg_gather(pl, pl->part2, d_gP, st);
+  if (ns > 0) k_deg_colsum<<<3 * ns, 256, 0, st>>>(pl->psrc, ne, 3 * ns, pl->dsrc);
+  if (cudaGetLastError() != cudaSuccess) return ADS_ERR_CUDA;
+  if (h_gsrc && ns > 0) {
+    if (cudaMemcpyAsync(h_gsrc, pl->dsrc, 3 * ns * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+      cudaGetLastError();
+      return ADS_ERR_CUDA;
+    }
+    const cudaError_t e = wait_stream_for(st, 10.0);
+    if (e == cudaErrorNotReady) return ADS_ERR_TIMEOUT;
+    if (e != cudaSuccess) return ADS_ERR_CUDA;
+  }
+  return ADS_OK;
 }
 
 extern "C" ads_status ads_degree_mass(ads_degree_plan* pl, const double* d_S, double* mass, void* stream) {

@@ -392,6 +392,7 @@ dg["null_out"] = [lib.ads_degree_plan_create(C.byref(make_params(scn.make_scenar
 dg["null_params"] = [lib.ads_degree_plan_create(None, 3, C.byref(C.c_void_p())), True]
 dg["step_null_plan"] = [lib.ads_degree_step(None, None, None, None, None, 1e-3, None, None), True]
 dg["mass_null_plan"] = [lib.ads_degree_mass(None, None, C.byref(C.c_double()), None), True]
+dg["vjp_null_plan"] = [lib.ads_degree_step_vjp(None, None, None, None, None, 1e-3, None, None, None, None, None), True]
 dg["coeffs_null"] = [lib.ads_degree_coeffs(None), True]
 lib.ads_degree_plan_destroy(None)
 print(json.dumps({"ctx": res, "server": srv, "noalloc": na, "degree": dg}))

@@ -153,3 +153,72 @@ def test_degree_step_refuses_aliasing_and_bad_steps():
                                    out.data_ptr(), None) == 1
     finally:
         lib.ads_degree_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("p,n", [(2, 6), (3, 5), (4, 7)])
+def test_degree_step_vjp_matches_oracle_finite_differences(p, n):
+    """ads_degree_step_vjp against central differences of the oracle's step:
+    J = lambda . step(S, P, sources), along random directions in S and P and
+    along each source's rate and centre.  S stays inside (0, 1) at the Gauss
+    points, where the mobility is smooth."""
+    import dataclasses
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_20731_gb300 import _lib
+    lib = _lib.load()
+    sc, _, P = _case(n, p, seed=300 + n + p)
+    nb = n + p
+    rng = np.random.default_rng(40 + p)
+    S = rng.uniform(0.3, 0.7, size=(nb, nb))
+    lam = rng.normal(size=(nb, nb))
+    dt = 5e-3
+    plan, _ = _plan(lib, sc, p)
+    try:
+        dev = torch.device("cuda", 0)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev)
+        K, phi, Sd, Pd, Ld = t(sc.K), t(sc.phi_map), t(S), t(P), t(lam)
+        gS, gP = torch.empty_like(Sd), torch.empty_like(Sd)
+        gsrc = (C.c_double * (3 * len(sc.sources)))()
+        torch.cuda.synchronize()
+        assert lib.ads_degree_step_vjp(plan, K.data_ptr(), phi.data_ptr(), Sd.data_ptr(), Pd.data_ptr(), dt,
+                                       Ld.data_ptr(), gS.data_ptr(), gP.data_ptr(), gsrc, None) == 0
+        torch.cuda.synchronize()
+        gS, gP, gsrc = gS.cpu().numpy(), gP.cpu().numpy(), np.array(gsrc[:])
+    finally:
+        lib.ads_degree_plan_destroy(plan)
+
+    def J(S_, P_, sources=None):
+        sc2 = dataclasses.replace(sc, sources=sources if sources is not None else sc.sources)
+        sc2.p = p
+        return float(np.sum(lam * AdsOracle(sc2).step(S_, P_, dt)))
+
+    # central differences with one Richardson step: (4 D(e/2) - D(e)) / 3
+    # cancels the e^2 term (the Gaussians of width 0.03 on a coarse mesh make
+    # J vary quickly with a source's centre)
+    eps = 1e-4
+
+    def rich(f):
+        d1 = (f(eps) - f(-eps)) / (2 * eps)
+        d2 = (f(eps / 2) - f(-eps / 2)) / eps
+        return (4 * d2 - d1) / 3
+
+    for _ in range(2):
+        dS, dP = rng.normal(size=(nb, nb)), rng.normal(size=(nb, nb))
+        fd_S = rich(lambda e: J(S + e * dS, P))
+        fd_P = rich(lambda e: J(S, P + e * dP))
+        assert np.sum(gS * dS) == pytest.approx(fd_S, rel=1e-6, abs=1e-9)
+        assert np.sum(gP * dP) == pytest.approx(fd_P, rel=1e-6, abs=1e-9)
+    for k, src in enumerate(sc.sources):
+        for j, field in enumerate(("rate", "cx", "cy")):
+            def moved(d):
+                out = list(sc.sources)
+                if field == "rate":
+                    out[k] = dataclasses.replace(src, rate=src.rate + d)
+                else:
+                    c = list(src.center)
+                    c[0 if field == "cx" else 1] += d
+                    out[k] = dataclasses.replace(src, center=tuple(c))
+                return out
+            fd = rich(lambda e: J(S, P, moved(e)))
+            assert gsrc[3 * k + j] == pytest.approx(fd, rel=1e-6, abs=1e-9), (k, field)
