@@ -74,3 +74,37 @@ def test_admission_respects_budget_and_rejects_oversize():
     with pytest.raises(_lib.AdsError):
         srv.submit(big, n_steps=1, hp=hp)
     srv.close()
+
+
+def test_hybrid_step_batch_equals_per_context_steps():
+    """hybrid_step_batch over a batch of three contexts of different sizes,
+    each on its own stream, gives bit for bit what hybrid_step gives for each
+    context alone (the same kernels in the same order on each context's
+    stream), twice in a row, with the step statistics of each."""
+    import torch
+    from paper_2604_20731_gb300.solver import HybridSolver, hybrid_step_batch
+    hp = _hp(HybridSolver, steps_adam=10)
+    theta = scn.make_theta0(2, 64, 4, seed=7)
+    scs = [scn.make_scenario(2, n, seed=1400 + n, sigma=0.8, rate=1.1) for n in (24, 40, 33)]
+    dev = torch.device("cuda", 0)
+
+    def make(sc):
+        s = HybridSolver(sc, width=64, crv_dtype="bf16", ads_dtype="f32", stream=torch.cuda.Stream(device=dev))
+        s.set_theta(theta)
+        s.pretrain(20, 1e-3)
+        return s
+
+    batch = [make(sc) for sc in scs]
+    alone = [make(sc) for sc in scs]
+    try:
+        for _ in range(2):
+            st_b = hybrid_step_batch(batch, hp, stats=True)
+            st_a = [s.hybrid_step(hp) for s in alone]
+            for b, a, sb, sa in zip(batch, alone, st_b, st_a):
+                for f in ("S", "P", "THETA"):
+                    assert np.array_equal(b.get(f), a.get(f)), f
+                assert sb["dt_used"] == sa["dt_used"] and sb["mass_total"] == sa["mass_total"]
+                assert sb["loss_last"] == sa["loss_last"]
+    finally:
+        for s in batch + alone:
+            s.close()
