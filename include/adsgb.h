@@ -468,6 +468,20 @@ int ads_degree_coeffs(const ads_degree_plan* plan);
 ads_status ads_degree_step(ads_degree_plan* plan, const double* d_K, const double* d_phi, const double* d_S,
                            const double* d_P, double dt, double* d_S_out, void* stream);
 ads_status ads_degree_mass(ads_degree_plan* plan, const double* d_S, double* mass, void* stream);
+/* ads_degree_project: the L2 projection (Sec. 6, step 4) of nodal values
+ *   d_nodal ((n+1)^2, device; their bilinear interpolant) into the degree-p
+ *   splines: d_out ((n+p)^2, device) = M^-1 F with F = int I_h u v.
+ *   Enqueued on `stream`.
+ * ads_degree_cfl_dt: the step size min(dt_cap, cfl h / v_max, src_frac / s_max)
+ *   with v_max = max |K (grad p + s rho_g g e_y)| / (mu_g phi) and
+ *   s_max = max q_inj / phi over the Gauss points, for pressure coefficients
+ *   d_P ((n+p)^2) and the nodal d_K, d_phi (NULL: params->phi); a term is left
+ *   out when its maximum is 0.  cfl, src_frac > 0, finite; dt_cap > 0 (may be
+ *   +inf).  Waits (bounded: ADS_ERR_TIMEOUT) for `stream` and writes *dt;
+ *   ADS_ERR_NONFINITE for a non-finite maximum. */
+ads_status ads_degree_project(ads_degree_plan* plan, const double* d_nodal, double* d_out, void* stream);
+ads_status ads_degree_cfl_dt(ads_degree_plan* plan, const double* d_K, const double* d_phi, const double* d_P,
+                             double cfl, double src_frac, double dt_cap, double* dt, void* stream);
 /* Vector-Jacobian product of ads_degree_step (a building block of gradients
  * through the explicit steps, e.g. for placing wells: Sec. 9 names the inverse
  * problem as future work).  For J = lambda . S_out with S_out the step of the

@@ -121,6 +121,8 @@ SIGNATURES = {
     "ads_degree_plan_create": (C.c_int, [C.POINTER(ads_params), C.c_int, C.POINTER(_P)]),
     "ads_degree_step": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, _P]),
     "ads_degree_mass": (C.c_int, [_P, _P, _D, _P]),
+    "ads_degree_project": (C.c_int, [_P, _P, _P, _P]),
+    "ads_degree_cfl_dt": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _D, _P]),
     "ads_degree_step_vjp": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, _P, _P, _D, _P]),
     "ads_degree_coeffs": (C.c_int, [_P]),
     "ads_degree_plan_destroy": (None, [_P]),

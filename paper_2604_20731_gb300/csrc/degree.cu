@@ -24,6 +24,7 @@
 // well: it reuses the same tables, line solves and gathers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <new>
@@ -264,6 +265,133 @@ __global__ void __launch_bounds__(128) k_deg_vjp(DegArgs a) {
       o2[b * Q + c] = gp[b][c];
     }
   for (int k = 0; k < 3 * a.n_src; ++k) a.psrc[(size_t)e * 3 * a.n_src + k] = ps[k];
+}
+
+// L2 projection of a nodal field into the splines (Sec. 6, step 4: the
+// network pressure, known at the nodes, enters the saturation step through
+// its coefficients): local terms of int I_h u v for the element's test
+// functions, I_h u the bilinear interpolant of the nodal values
+template <int P>
+__global__ void __launch_bounds__(128) k_deg_proj(DegArgs a, const double* __restrict__ nodal) {
+  constexpr int Q = P + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n * a.n) return;
+  const int ex = e % a.n, ey = e / a.n, n1 = a.n + 1;
+  const double* Bx = a.B + (size_t)ex * Q * Q;
+  const double* By = a.B + (size_t)ey * Q * Q;
+  const double u00 = nodal[(size_t)ey * n1 + ex], u01 = nodal[(size_t)ey * n1 + ex + 1];
+  const double u10 = nodal[(size_t)(ey + 1) * n1 + ex], u11 = nodal[(size_t)(ey + 1) * n1 + ex + 1];
+  double r[Q][Q];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) r[b][c] = 0.0;
+  for (int qy = 0; qy < Q; ++qy) {
+    const double eta = a.xi[qy];
+    for (int qx = 0; qx < Q; ++qx) {
+      const double xi = a.xi[qx];
+      const double uq = (1.0 - eta) * ((1.0 - xi) * u00 + xi * u01) + eta * ((1.0 - xi) * u10 + xi * u11);
+      const double c0 = a.wq[qx] * a.wq[qy] * a.h2 * uq;
+#pragma unroll
+      for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int c = 0; c < Q; ++c) r[b][c] += c0 * By[b * Q + qy] * Bx[c * Q + qx];
+    }
+  }
+  double* o = a.part + (size_t)e * Q * Q;
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) o[b * Q + c] = r[b][c];
+}
+
+// per element, the largest Darcy speed |K (grad p + s rho_g g e_y)| /
+// (mu_g phi) and the largest injection rate q_inj / phi over its Gauss points
+// (the step-size rule's two maxima), to out[e] and out[n^2 + e]
+template <int P>
+__global__ void __launch_bounds__(128) k_deg_cfl(DegArgs a, double inv_mu_g, double* __restrict__ out) {
+  constexpr int Q = P + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ne = a.n * a.n;
+  if (e >= ne) return;
+  const int ex = e % a.n, ey = e / a.n, n1 = a.n + 1;
+  double pp[Q][Q];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) pp[b][c] = a.P[(size_t)(ey + b) * a.nb + ex + c];
+  const double* Bx = a.B + (size_t)ex * Q * Q;
+  const double* dBx = a.dB + (size_t)ex * Q * Q;
+  const double* By = a.B + (size_t)ey * Q * Q;
+  const double* dBy = a.dB + (size_t)ey * Q * Q;
+  const double k00 = a.K[(size_t)ey * n1 + ex], k01 = a.K[(size_t)ey * n1 + ex + 1];
+  const double k10 = a.K[(size_t)(ey + 1) * n1 + ex], k11 = a.K[(size_t)(ey + 1) * n1 + ex + 1];
+  double f00 = a.phi_c, f01 = a.phi_c, f10 = a.phi_c, f11 = a.phi_c;
+  if (a.phi) {
+    f00 = a.phi[(size_t)ey * n1 + ex];
+    f01 = a.phi[(size_t)ey * n1 + ex + 1];
+    f10 = a.phi[(size_t)(ey + 1) * n1 + ex];
+    f11 = a.phi[(size_t)(ey + 1) * n1 + ex + 1];
+  }
+  double vmax = 0.0, smax = 0.0;
+  for (int qy = 0; qy < Q; ++qy) {
+    const double eta = a.xi[qy];
+    for (int qx = 0; qx < Q; ++qx) {
+      const double xi = a.xi[qx];
+      double px = 0.0, py = 0.0;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        double pb = 0.0, pdb = 0.0;
+#pragma unroll
+        for (int c = 0; c < Q; ++c) {
+          pb += pp[b][c] * Bx[c * Q + qx];
+          pdb += pp[b][c] * dBx[c * Q + qx];
+        }
+        px += By[b * Q + qy] * pdb;
+        py += dBy[b * Q + qy] * pb;
+      }
+      const double Kq = (1.0 - eta) * ((1.0 - xi) * k00 + xi * k01) + eta * ((1.0 - xi) * k10 + xi * k11);
+      const double phq = (1.0 - eta) * ((1.0 - xi) * f00 + xi * f01) + eta * ((1.0 - xi) * f10 + xi * f11);
+      const double fx = Kq * px, fy = Kq * (py + a.grav_term);
+      vmax = fmax(vmax, sqrt(fx * fx + fy * fy) * inv_mu_g / phq);
+      double qi = 0.0;
+      for (int k = 0; k < a.n_src; ++k)
+        if (a.kind[k] == 0)
+          qi += a.rate[k] * a.g[((size_t)(0 * a.n_src + k) * a.n + ex) * Q + qx] *
+                a.g[((size_t)(1 * a.n_src + k) * a.n + ey) * Q + qy];
+      smax = fmax(smax, qi / phq);
+    }
+  }
+  out[e] = vmax;
+  out[ne + e] = smax;
+}
+
+// the largest of each of the two per-element columns (one block)
+__global__ void __launch_bounds__(1024) k_deg_max2(const double* __restrict__ v, int ne, double* out) {
+  __shared__ double red[2][32];
+  double a = 0.0, b = 0.0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    a = fmax(a, v[e]);
+    b = fmax(b, v[ne + e]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x + 31) / 32; ++i) {
+      a = fmax(a, red[0][i]);
+      b = fmax(b, red[1][i]);
+    }
+    out[0] = a;
+    out[1] = b;
+  }
 }
 
 // the per-element source terms summed over the elements in a fixed order:
@@ -640,6 +768,58 @@ extern "C" ads_status ads_degree_step_vjp(ads_degree_plan* pl, const double* d_K
     if (e == cudaErrorNotReady) return ADS_ERR_TIMEOUT;
     if (e != cudaSuccess) return ADS_ERR_CUDA;
   }
+  return ADS_OK;
+}
+
+extern "C" ads_status ads_degree_project(ads_degree_plan* pl, const double* d_nodal, double* d_out, void* stream) {
+  using namespace adsgb;
+  if (!pl || !d_nodal || !d_out) return ADS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ne = pl->n * pl->n, g = (ne + 127) / 128;
+  switch (pl->p) {
+    case 2: k_deg_proj<2><<<g, 128, 0, st>>>(pl->args, d_nodal); break;
+    case 3: k_deg_proj<3><<<g, 128, 0, st>>>(pl->args, d_nodal); break;
+    default: k_deg_proj<4><<<g, 128, 0, st>>>(pl->args, d_nodal); break;
+  }
+  deg_gather(pl, pl->part, d_out, st);
+  deg_mass_solve(pl, d_out, st);
+  return cudaGetLastError() == cudaSuccess ? ADS_OK : ADS_ERR_CUDA;
+}
+
+extern "C" ads_status ads_degree_cfl_dt(ads_degree_plan* pl, const double* d_K, const double* d_phi,
+                                        const double* d_P, double cfl, double src_frac, double dt_cap, double* dt,
+                                        void* stream) {
+  using namespace adsgb;
+  if (!pl || !d_K || !d_P || !dt) return ADS_ERR_INVALID_ARG;
+  if (!(cfl > 0) || !std::isfinite(cfl) || !(src_frac > 0) || !std::isfinite(src_frac) || !(dt_cap > 0))
+    return ADS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DegArgs a = pl->args;
+  a.K = d_K;
+  a.phi = d_phi;
+  a.P = d_P;
+  const int ne = pl->n * pl->n, g = (ne + 127) / 128;
+  switch (pl->p) {
+    case 2: k_deg_cfl<2><<<g, 128, 0, st>>>(a, a.inv_mu_g, pl->part); break;
+    case 3: k_deg_cfl<3><<<g, 128, 0, st>>>(a, a.inv_mu_g, pl->part); break;
+    default: k_deg_cfl<4><<<g, 128, 0, st>>>(a, a.inv_mu_g, pl->part); break;
+  }
+  k_deg_max2<<<1, 1024, 0, st>>>(pl->part, ne, pl->dsrc);
+  if (cudaGetLastError() != cudaSuccess) return ADS_ERR_CUDA;
+  double mx[2] = {0.0, 0.0};
+  if (cudaMemcpyAsync(mx, pl->dsrc, sizeof(mx), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    return ADS_ERR_CUDA;
+  }
+  const cudaError_t e = wait_stream_for(st, 10.0);
+  if (e == cudaErrorNotReady) return ADS_ERR_TIMEOUT;
+  if (e != cudaSuccess) return ADS_ERR_CUDA;
+  if (!std::isfinite(mx[0]) || !std::isfinite(mx[1])) return ADS_ERR_NONFINITE;
+  // dt = min(dt_cap, cfl h / v_max, src_frac / s_max), the maxima over the Gauss points
+  double d = dt_cap;
+  if (mx[0] > 0) d = std::min(d, cfl / pl->n / mx[0]);
+  if (mx[1] > 0) d = std::min(d, src_frac / mx[1]);
+  *dt = d;
   return ADS_OK;
 }
 

@@ -222,3 +222,44 @@ def test_degree_step_vjp_matches_oracle_finite_differences(p, n):
                 return out
             fd = rich(lambda e: J(S, P, moved(e)))
             assert gsrc[3 * k + j] == pytest.approx(fd, rel=1e-6, abs=1e-9), (k, field)
+
+
+@pytest.mark.parametrize("p,n", [(2, 20), (3, 33), (4, 17)])
+def test_degree_projection_and_step_size_match_oracle(p, n):
+    """The projection of nodal values into the degree-p splines and the CFL
+    step size against the oracle (project_nodal, AdsOracle.cfl_dt)."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    from oracle.hybrid import project_nodal
+    from paper_2604_20731_gb300 import _lib
+    lib = _lib.load()
+    sc, _, P = _case(n, p, seed=500 + n + p)
+    rng = np.random.default_rng(n)
+    nodal = rng.normal(size=(n + 1, n + 1))
+    nodal[0, :] = nodal[-1, :] = nodal[:, 0] = nodal[:, -1] = 0.0
+    plan, _ = _plan(lib, sc, p)
+    try:
+        dev = torch.device("cuda", 0)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev)
+        K, phi, Pd, Nd = t(sc.K), t(sc.phi_map), t(P), t(nodal)
+        out = torch.empty((n + p, n + p), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        assert lib.ads_degree_project(plan, Nd.data_ptr(), out.data_ptr(), None) == 0
+        dt = C.c_double()
+        assert lib.ads_degree_cfl_dt(plan, K.data_ptr(), phi.data_ptr(), Pd.data_ptr(), 0.1, 0.05,
+                                     float("inf"), C.byref(dt), None) == 0
+        torch.cuda.synchronize()
+        a = AdsOracle(sc)
+        ref = project_nodal(a.mesh, nodal)
+        assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert dt.value == pytest.approx(a.cfl_dt(P, cfl=0.1, src_frac=0.05), rel=1e-12)
+        dt2 = C.c_double()
+        assert lib.ads_degree_cfl_dt(plan, K.data_ptr(), phi.data_ptr(), Pd.data_ptr(), 0.1, 0.05,
+                                     1e-9, C.byref(dt2), None) == 0
+        assert dt2.value == 1e-9
+        for bad in ((0.0, 0.05), (0.1, -1.0), (float("nan"), 0.05)):
+            assert lib.ads_degree_cfl_dt(plan, K.data_ptr(), None, Pd.data_ptr(), bad[0], bad[1], 1.0,
+                                         C.byref(dt2), None) == 1
+    finally:
+        lib.ads_degree_plan_destroy(plan)
