@@ -600,3 +600,24 @@ def test_adjoint_vs_finite_differences_1024_fp64():
     print(f"1024^2 FD check: max relative deviation {worst:.2e}")
     assert worst < 1e-4
     s.close()
+
+
+@pytest.mark.parametrize("conc", [1, 4])
+def test_gram_solve_at_512_against_the_direct_solve(conc):
+    """The three-pass sine-transform solve at N = 512 in FP32: z must solve
+    G z = RES for the GPU's own RES (the oracle's sparse LU of G, FP64) to
+    FP32 rounding, the loss must be RES . z, and the residual, loss and
+    gradient must agree with the oracle's within the FP32 network's error;
+    alone and in the shared launch shape."""
+    sc, s, crv, theta, alpha, f = _crv_case(512, "f32", width=64)
+    s.set_concurrency(conc)
+    loss = s.loss_grad()
+    z, r = s.get("Z").astype(np.float64), s.get("RES").astype(np.float64)
+    z_ref = crv.gram_solve_lu(r)
+    assert rel_l2(z, z_ref) <= 1e-5
+    assert loss == pytest.approx(float(r @ z), rel=1e-5)
+    ref_loss, ref_grad, parts = crv.loss_grad(MLP(2, 64, 4), theta, alpha, f)
+    assert rel_l2(r, parts["r"]) <= 1e-2
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    assert rel_l2(s.get("GRAD"), ref_grad) <= 2e-2
+    s.close()
