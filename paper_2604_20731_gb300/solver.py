@@ -318,3 +318,93 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class DegreePlan:
+    """A degree-p (2, 3 or 4) FP64 2D saturation plan (ads_degree_*): the
+    explicit step, its vector-Jacobian product, the projection of nodal
+    values, the CFL step size and the mass, on device arrays the caller owns
+    (torch CUDA tensors, float64, contiguous).  Marshalling only."""
+
+    def __init__(self, sc, degree: int):
+        self.lib = L.load()
+        self.n, self.p = sc.n, int(degree)
+        self.params = make_params(sc, "f64", any_degree=True)
+        self.n_src = self.params.n_src
+        plan = C.c_void_p()
+        rc = self.lib.ads_degree_plan_create(C.byref(self.params), self.p, C.byref(plan))
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, "ads_degree_plan_create", "")
+        self.plan = plan
+
+    @staticmethod
+    def _p(t):
+        return None if t is None else t.data_ptr()
+
+    def _check(self, rc, where):
+        if rc != L.ADS_OK:
+            raise L.AdsError(rc, where, "")
+
+    def step(self, K, phi, S, P, dt, out, stream=None):
+        self._check(self.lib.ads_degree_step(self.plan, self._p(K), self._p(phi), self._p(S), self._p(P),
+                                             float(dt), self._p(out), stream), "ads_degree_step")
+
+    def vjp(self, K, phi, S, P, dt, lam, gS, gP, stream=None):
+        """dJ/dS into gS, dJ/dP into gP for J = lam . step(S, P); returns
+        dJ/d(rate, centre x, centre y) per source, shape (n_src, 3)."""
+        g = (C.c_double * max(1, 3 * self.n_src))()
+        self._check(self.lib.ads_degree_step_vjp(self.plan, self._p(K), self._p(phi), self._p(S), self._p(P),
+                                                 float(dt), self._p(lam), self._p(gS), self._p(gP),
+                                                 g if self.n_src else None, stream), "ads_degree_step_vjp")
+        return np.array(g[:3 * self.n_src]).reshape(self.n_src, 3)
+
+    def project(self, nodal, out, stream=None):
+        self._check(self.lib.ads_degree_project(self.plan, self._p(nodal), self._p(out), stream),
+                    "ads_degree_project")
+
+    def cfl_dt(self, K, phi, P, cfl=0.1, src_frac=0.05, dt_cap=float("inf"), stream=None):
+        dt = C.c_double()
+        self._check(self.lib.ads_degree_cfl_dt(self.plan, self._p(K), self._p(phi), self._p(P), float(cfl),
+                                               float(src_frac), float(dt_cap), C.byref(dt), stream),
+                    "ads_degree_cfl_dt")
+        return dt.value
+
+    def mass(self, S, stream=None):
+        m = C.c_double()
+        self._check(self.lib.ads_degree_mass(self.plan, self._p(S), C.byref(m), stream), "ads_degree_mass")
+        return m.value
+
+    def steps_with_gradient(self, K, phi, S0, P, dt, n_steps, lam):
+        """n_steps explicit steps from S0 with the pressure P fixed, and the
+        gradient of J = lam . S_n: the states go forward on the device, then
+        the vector-Jacobian products run backward, the adjoint of each step
+        becoming the next one's lam.  Returns S_n, dJ/dS0, dJ/dP (tensors)
+        and dJ/d(rate, centre x, centre y) per source (the well-placement
+        gradient).  Everything runs on torch's current stream."""
+        import torch
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        states = [S0]
+        for _ in range(n_steps):
+            out = torch.empty_like(S0)
+            self.step(K, phi, states[-1], P, dt, out, stream)
+            states.append(out)
+        adj = lam.clone()
+        gP_tot = torch.zeros_like(P)
+        gsrc = np.zeros((self.n_src, 3))
+        gS, gP = torch.empty_like(S0), torch.empty_like(P)
+        for k in range(n_steps - 1, -1, -1):
+            gsrc += self.vjp(K, phi, states[k], P, dt, adj, gS, gP, stream)
+            gP_tot += gP
+            adj, gS = gS, adj
+        return states[-1], adj, gP_tot, gsrc
+
+    def close(self):
+        if self.plan:
+            self.lib.ads_degree_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
