@@ -18,6 +18,8 @@ Modules:
                (Eq. 26), robust loss (Eqs. 27-28), MLP, adjoint gradient, Adam
   hybrid    -- projection of the network pressure (Sec. 6, step 4) and the
                hybrid loop (Sec. 6)
+  maps      -- porosity and permeability maps given as images (Sec. 8.1),
+               averaged over the nodes' dual cells
 
 The spline degree follows the scenario (`p`, default 2: the quadratic C1
 splines the configurations use): n + p functions per axis and p + 1 Gauss
