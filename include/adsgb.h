@@ -501,6 +501,42 @@ ads_status ads_degree_step_vjp(ads_degree_plan* plan, const double* d_K, const d
                                double* h_gsrc, void* stream);
 void ads_degree_plan_destroy(ads_degree_plan* plan);
 
+/* ---- maps given as images (Sec. 8.1) -----------------------------------------
+ * Sec. 8.1 gives each reservoir's porosity (0 to 1) and permeability (mDarcy,
+ * used in SI units) as a picture of the domain.  The method takes K and phi as
+ * nodal values on the (n+1)^d vertex grid (K_nodal / phi_nodal of ads_init,
+ * d_K / d_phi of ads_degree_step); ads_map_from_image brings a picture there.
+ *   d_img: device pixels, ADS_PIXEL_F32 (float, 4-byte aligned) or
+ *     ADS_PIXEL_U8 (unsigned char); img_shape[0..dim-1] = {W, H(, D)}: W
+ *     columns along x, H rows along y, D slices along z; layout
+ *     [slice][row][column], columns fastest.  Row 0 is the picture's top edge
+ *     (y = 1) when flip_y != 0, its bottom edge (y = 0) otherwise; slice 0
+ *     lies at z = 0.  The caller keeps ownership.
+ *   A pixel holds offset + scale * pixel over its square (cube) of the unit
+ *     domain.  The nodal value is that field's average over the node's dual
+ *     cell, [x_i - h/2, x_i + h/2] per axis clipped to [0, 1]: the arithmetic
+ *     mean (ADS_MAP_ARITHMETIC; keeps the map's integral) or the geometric
+ *     mean exp(avg log) (ADS_MAP_GEOMETRIC; the usual upscaling of a
+ *     log-normal permeability; a zero pixel gives 0 to the cells that see it).
+ *     Overlaps are exact (integers in units of 1/(2 n W)) and the sums FP64,
+ *     so a picture finer or coarser than the mesh, in any ratio, is accepted.
+ *   n[0..dim-1]: elements per axis, 1 to 65536; at most 2^31 - 1 nodes.
+ *   d_nodal: device, prod(n_a + 1) doubles, [z][y][x] with x fastest,
+ *     8-byte aligned, not overlapping d_img.
+ * Enqueued on `stream`; the call then waits (bounded: ADS_ERR_TIMEOUT after
+ * 10 s) and returns ADS_ERR_NONFINITE if a nodal value is not finite (a NaN or
+ * infinite pixel, or a negative one under the geometric mean; every value is
+ * written all the same).  ADS_ERR_INVALID_ARG: a NULL pointer, dim not 2 or 3,
+ * an extent or count out of range, an unknown pixel type or mean, a
+ * non-finite scale or offset, misalignment or overlapping buffers.
+ * ADS_ERR_OOM / ADS_ERR_CUDA: the 4-byte counter could not be allocated / a
+ * CUDA call failed. */
+typedef enum { ADS_PIXEL_F32 = 0, ADS_PIXEL_U8 = 1 } ads_pixel_type;
+typedef enum { ADS_MAP_ARITHMETIC = 0, ADS_MAP_GEOMETRIC = 1 } ads_map_mean;
+ads_status ads_map_from_image(const void* d_img, int pixel_type, int dim, const int* img_shape, int flip_y,
+                              const int* n, int mean, double scale, double offset, double* d_nodal,
+                              void* stream);
+
 /* ---- diagnostics (no counterpart in the paper) ------------------------------
  * ads_kernel_launches: number of library kernels enqueued on this context so
  * far (a graph replay counts the kernels it contains).

@@ -17,6 +17,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "C
                 4: "non-finite value", 5: "timeout", 6: "invalid state", 7: "unsupported",
                 8: "checkpoint file error"}
 ADS_F64, ADS_F32, ADS_BF16 = 0, 1, 2
+ADS_PIXEL_F32, ADS_PIXEL_U8 = 0, 1
+ADS_MAP_ARITHMETIC, ADS_MAP_GEOMETRIC = 0, 1
 MAX_SOURCES = 8
 
 FIELD = dict(S=0, P=1, K=2, ALPHA=3, F=4, U=5, RES=6, Z=7, GU=8, THETA=9, GRAD=10, LOSS=11,
@@ -126,6 +128,8 @@ SIGNATURES = {
     "ads_degree_step_vjp": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, _P, _P, _D, _P]),
     "ads_degree_coeffs": (C.c_int, [_P]),
     "ads_degree_plan_destroy": (None, [_P]),
+    "ads_map_from_image": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                                     C.c_int, C.c_double, C.c_double, _P, _P]),
     "ads_probe_wait_expiry": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "ads_profile_train": (C.c_int, [_P, C.c_int, _D]),
     "ads_profile_saturation": (C.c_int, [_P, C.c_int, _D]),

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libadsgb.so")
 
-SOURCES = ["ads_kernels.cu", "ads3d.cu", "crv_kernels.cu", "gram_fft.cu", "mlp_kernels.cu", "mlp_tc.cu", "api.cu", "noalloc.cu", "serve.cu", "galerkin.cu", "peaks.cu", "waitprobe.cu", "degree.cu"]
+SOURCES = ["ads_kernels.cu", "ads3d.cu", "crv_kernels.cu", "gram_fft.cu", "mlp_kernels.cu", "mlp_tc.cu", "api.cu", "noalloc.cu", "serve.cu", "galerkin.cu", "peaks.cu", "waitprobe.cu", "degree.cu", "maps.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -158,3 +158,14 @@ def make_theta0(in_dim: int, width: int, hidden_layers: int = 4, seed: int = 7) 
         parts.append(rng.uniform(-a, a, size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts)
+
+
+def make_map_image(shape, seed: int, corr_len=0.08, contrast: float = 40.0) -> np.ndarray:
+    """A synthetic 8-bit grey picture standing in for the paper's reservoir
+    maps (Sec. 8.1), which are not available: a Gaussian random field on the
+    pixel grid, 128 + contrast * Z clipped to 0..255.  shape: (H, W) or
+    (D, H, W); row 0 is the picture's top edge.  Decode it as
+    offset + scale * pixel (e.g. porosity 0.05 + 0.35 * pixel / 255)."""
+    rng = np.random.default_rng(seed)
+    Z = gaussian_random_field(tuple(shape), corr_len, rng)
+    return np.clip(np.rint(128.0 + contrast * Z), 0, 255).astype(np.uint8)

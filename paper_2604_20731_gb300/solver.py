@@ -408,3 +408,47 @@ class DegreePlan:
             self.close()
         except Exception:
             pass
+
+
+def map_from_image(img, n, flip_y: bool = True, mean: str = "arithmetic", scale: float = 1.0,
+                   offset: float = 0.0, out=None):
+    """Nodal values on the (n+1)^d vertex grid of a porosity or permeability
+    picture (ads_map_from_image): each node averages the pixel field
+    offset + scale * pixel over its dual cell.
+
+    img: a contiguous CUDA tensor, float32 or uint8, (H, W) for 2D or
+    (D, H, W) for 3D; row 0 is the picture's top edge when flip_y.  n: elements
+    per axis, an int or (nx, ny(, nz)).  mean: "arithmetic" or "geometric".
+    Returns (or fills `out`) a float64 CUDA tensor [y][x] (or [z][y][x]).
+    Runs on torch's current stream and waits for it (bounded)."""
+    import torch
+    lib = L.load()
+    dim = img.dim()
+    if dim not in (2, 3):
+        raise ValueError("img must be (H, W) or (D, H, W)")
+    if img.dtype == torch.float32:
+        ptype = L.ADS_PIXEL_F32
+    elif img.dtype == torch.uint8:
+        ptype = L.ADS_PIXEL_U8
+    else:
+        raise TypeError("pixels must be float32 or uint8")
+    if not (img.is_cuda and img.is_contiguous()):
+        raise ValueError("img must be a contiguous CUDA tensor")
+    ns = (int(n),) * dim if np.isscalar(n) else tuple(int(v) for v in n)
+    if len(ns) != dim:
+        raise ValueError("one element count per axis")
+    shape = tuple(img.shape[::-1])  # W, H(, D)
+    means = {"arithmetic": L.ADS_MAP_ARITHMETIC, "geometric": L.ADS_MAP_GEOMETRIC}
+    nodes = tuple(v + 1 for v in ns[::-1])
+    if out is None:
+        out = torch.empty(nodes, dtype=torch.float64, device=img.device)
+    elif not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == np.prod(nodes)):
+        raise ValueError("out must be a contiguous float64 CUDA tensor of prod(n_a + 1) values")
+    stream = C.c_void_p(torch.cuda.current_stream(img.device).cuda_stream)
+    pad = [0] * (3 - dim)
+    rc = lib.ads_map_from_image(img.data_ptr(), ptype, dim, (C.c_int * 3)(*shape, *pad), int(flip_y),
+                                (C.c_int * 3)(*ns, *pad), means[mean], float(scale), float(offset),
+                                out.data_ptr(), stream)
+    if rc != L.ADS_OK:
+        raise L.AdsError(rc, "ads_map_from_image", "")
+    return out

@@ -333,7 +333,8 @@ skip = {"ads_init", "ads_init_with_allocator", "ads_hbm_estimate", "ads_status_s
         "ads_saturation_step_noalloc", "ads_saturation_step_noalloc_status", "hybrid_step_batch"}
 res = {}
 for name, (rt, args) in _lib.SIGNATURES.items():
-    if (name in skip or name.startswith("ads_server_") or name.startswith("ads_degree_") or not args
+    if (name in skip or name.startswith("ads_server_") or name.startswith("ads_degree_")
+            or name.startswith("ads_map_") or not args
             or args[0] is not C.c_void_p):
         continue
     vals = [None]
@@ -397,7 +398,20 @@ dg["coeffs_null"] = [lib.ads_degree_coeffs(None), True]
 dg["project_null_plan"] = [lib.ads_degree_project(None, None, None, None), True]
 dg["cfl_null_plan"] = [lib.ads_degree_cfl_dt(None, None, None, None, 0.1, 0.05, 1.0, C.byref(C.c_double()), None), True]
 lib.ads_degree_plan_destroy(None)
-print(json.dumps({"ctx": res, "server": srv, "noalloc": na, "degree": dg}))
+# image maps: refusals before any CUDA call (the pointers are never dereferenced)
+def mp(img=0x10000, ptype=0, dim=2, shape=(8, 8, 0), flip=1, n=(4, 4, 0), mean=0, scale=1.0, off=0.0,
+       out=0x20000):
+    sh = None if shape is None else (C.c_int * 3)(*shape)
+    nn = None if n is None else (C.c_int * 3)(*n)
+    return lib.ads_map_from_image(img, ptype, dim, sh, flip, nn, mean, scale, off, out, None)
+mps = {"null_img": mp(img=None), "null_out": mp(out=None), "null_shape": mp(shape=None), "null_n": mp(n=None),
+       "dim1": mp(dim=1), "dim4": mp(dim=4), "n0": mp(n=(0, 4, 0)), "n65537": mp(n=(4, 65537, 0)),
+       "shape0": mp(shape=(8, 0, 0)), "shape_big": mp(shape=(1 << 25, 8, 0)), "ptype2": mp(ptype=2),
+       "mean2": mp(mean=2), "scale_nan": mp(scale=math.nan), "offset_inf": mp(off=math.inf),
+       "overlap": mp(out=0x10000 + 128), "misaligned_f32": mp(img=0x10002),
+       "misaligned_out": mp(out=0x20004), "nodes_2e31": mp(n=(65536, 65536, 0)),
+       "z0_3d": mp(dim=3, shape=(8, 8, 0), n=(4, 4, 4)), "nz0_3d": mp(dim=3, shape=(8, 8, 8), n=(4, 4, 0))}
+print(json.dumps({"ctx": res, "server": srv, "noalloc": na, "degree": dg, "maps": mps}))
 """
 
 
@@ -431,3 +445,4 @@ def test_null_handles_and_refused_arguments_before_any_cuda_call(lib):
     assert dg.pop("dim3") == [7, True] and dg.pop("f32") == [7, True]
     assert dg.pop("coeffs_null") == [0, True]
     assert all(v == [1, True] for v in dg.values()), dg
+    assert all(v == 1 for v in r["maps"].values()), r["maps"]
