@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -817,6 +819,10 @@ ads_status validate_params(const ads_params* p, const crvpinn_params* cp) { retu
 // =============================================================================
 // exported entry points
 // =============================================================================
+namespace {
+void batch_plans_drop(const ads_ctx* c);  // below: the batched training's plans that hold c
+}  // namespace
+
 extern "C" {
 
 const char* ads_status_str(ads_status st) {
@@ -860,6 +866,7 @@ size_t ads_hbm_estimate(const ads_params* params, const crvpinn_params* crv) {
 
 void ads_destroy(ads_ctx* c) {
   if (!c) return;
+  batch_plans_drop(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
   for (void* p : c->allocs) {
@@ -1450,12 +1457,244 @@ ads_status hybrid_step(ads_ctx* c, const hybrid_params* hp, hybrid_stats* stats)
   return ADS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Batched training (the serving form of a hybrid step over many contexts):
+// for contexts of one shape, each kernel of an Adam iteration runs once for
+// the whole batch, its CTAs those of every context's own launch (grouped
+// launches over per-context argument tables), on the batch's own stream.
+// Each context's results are bit-identical to its own iteration's: the same
+// CTAs do the same work in the same order.  The saturation part of the step
+// stays on each context's stream (its work is per context and small).
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+  std::vector<ads_ctx*> ctxs;
+  std::vector<int> shape;  // per context: backward CTAs and concurrency when the plan was made
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> ready;  // per context: its saturation part enqueued before the training
+  DevGroup<MlpTcArgs> fwd, bwd;
+  GramGroup* gram = nullptr;
+  DevGroup<StencilArgs> sten;
+  DevGroup<AdamArgs> adam;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (iterations, update)
+  unsigned long long last_use = 0;
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchPlan*> g_batches;
+unsigned long long g_batch_clock = 0;
+constexpr int kMaxBatchPlans = 16;
+constexpr int kBatchLaunches = 8;  // kernels of one grouped Adam iteration
+
+void batch_plan_free(BatchPlan* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  dev_group_free(b->fwd);
+  dev_group_free(b->bwd);
+  gram_group_destroy(b->gram);
+  dev_group_free(b->sten);
+  dev_group_free(b->adam);
+  for (cudaEvent_t e : b->ready) cudaEventDestroy(e);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+// every batch plan that holds c goes (c is being destroyed or reshaped)
+void batch_plans_drop(const ads_ctx* c) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batches.size();) {
+    BatchPlan* b = g_batches[i];
+    bool has = false;
+    for (ads_ctx* x : b->ctxs) has |= x == c;
+    if (has) {
+      batch_plan_free(b);
+      g_batches.erase(g_batches.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+bool batch_groupable(const ads_ctx* c) {
+  return c && c->status == ADS_OK && c->has_crv && c->dim == 2 && c->use_tc && c->tc == ADS_F32 &&
+         c->cp.width == 64 && c->chunks == 1 && c->gram_fft && !gram_in_cluster(c);
+}
+
+std::vector<int> batch_shape(ads_ctx* const* ctxs, int n) {
+  std::vector<int> v;
+  for (int i = 0; i < n; ++i) {
+    v.push_back(ctxs[i]->nbwd);
+    v.push_back(ctxs[i]->concurrency);
+  }
+  return v;
+}
+
+cudaError_t batch_plan_make(ads_ctx* const* ctxs, int n, BatchPlan** out) {
+  *out = nullptr;
+  BatchPlan* b = new BatchPlan();
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->shape = batch_shape(ctxs, n);
+  std::vector<MlpTcArgs> ma(n);
+  std::vector<int> gf(n), gb(n), gs(n), ga(n);
+  std::vector<GramGroupEntry> ge(n);
+  std::vector<StencilArgs> sa(n);
+  std::vector<AdamArgs> aa(n);
+  for (int i = 0; i < n; ++i) {
+    ads_ctx* c = ctxs[i];
+    ma[i] = mlp_tc_group_args(mlp_tc_args(c, true), &gf[i]);
+    gb[i] = c->nbwd;
+    const float h = float(1.0 / c->N);
+    ge[i] = GramGroupEntry{c->N, (const float*)c->u, (const float*)c->alpha, (const float*)c->f, h * h,
+                           (float*)c->res, (float*)c->rhat, (float*)c->z, (const float*)c->gtw,
+                           (const float*)c->glam, c->dot_part};
+    const LossFin lf{c->dot_part, gram_fft_dot_parts(c->N, c->dim), c->loss, c->loss_log, c->t, c->bc,
+                     c->flags, 1};
+    sa[i] = StencilArgs{c->N, (const float*)c->alpha, (const float*)c->z, nullptr, 0.0f, 2.0f, (float*)c->gu, lf};
+    gs[i] = stencil_blocks(c->N);
+    aa[i] = AdamArgs{(const float*)c->gpart, c->chunks * c->nbwd, c->nparams, (float*)c->grad,
+                     (float*)c->theta, (float*)c->am, (float*)c->av, c->bc, c->lr, 1};
+    ga[i] = grad_adam_blocks(c->nparams);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ready.push_back(ev);
+  }
+  if (e == cudaSuccess) e = dev_group_create(b->fwd, ma.data(), gf.data(), n);
+  if (e == cudaSuccess) e = dev_group_create(b->bwd, ma.data(), gb.data(), n);
+  if (e == cudaSuccess) e = gram_group_create(ge.data(), n, &b->gram);
+  if (e == cudaSuccess) e = dev_group_create(b->sten, sa.data(), gs.data(), n);
+  if (e == cudaSuccess) e = dev_group_create(b->adam, aa.data(), ga.data(), n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_plan_free(b);
+    return e;
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
+// the batch's plan (made on first use); nullptr: the contexts are not all of
+// the grouped shape, or a plan could not be made (the caller steps them one
+// by one)
+BatchPlan* batch_plan_get(ads_ctx* const* ctxs, int n) {
+  if (n < 2) return nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!batch_groupable(ctxs[i])) return nullptr;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return nullptr;
+  }
+  const std::vector<int> shape = batch_shape(ctxs, n);
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batches.size(); ++i) {
+    BatchPlan* b = g_batches[i];
+    if ((int)b->ctxs.size() != n || !std::equal(b->ctxs.begin(), b->ctxs.end(), ctxs)) continue;
+    if (b->shape == shape) {
+      b->last_use = ++g_batch_clock;
+      return b;
+    }
+    batch_plan_free(b);  // a context was reshaped since
+    g_batches.erase(g_batches.begin() + (long)i);
+    break;
+  }
+  if ((int)g_batches.size() >= kMaxBatchPlans) {
+    size_t old = 0;
+    for (size_t i = 1; i < g_batches.size(); ++i)
+      if (g_batches[i]->last_use < g_batches[old]->last_use) old = i;
+    batch_plan_free(g_batches[old]);
+    g_batches.erase(g_batches.begin() + (long)old);
+  }
+  BatchPlan* b = nullptr;
+  if (batch_plan_make(ctxs, n, &b) != cudaSuccess) return nullptr;
+  b->last_use = ++g_batch_clock;
+  g_batches.push_back(b);
+  return b;
+}
+
+cudaError_t batch_iter(const BatchPlan* b) {
+  const int n = (int)b->ctxs.size();
+  cudaError_t e = launch_mlp_tc_grouped(0, 2, b->fwd.tab, n, b->fwd.map, n, b->st);
+  if (e == cudaSuccess) e = launch_mlp_tc_grouped(1, 2, b->fwd.tab, n, b->fwd.map, b->fwd.nctas, b->st);
+  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) e = launch_gram_group(b->gram, pass, b->st);
+  if (e == cudaSuccess) e = launch_stencil_grouped(b->sten.tab, b->sten.map, b->sten.nctas, b->st);
+  if (e == cudaSuccess) e = launch_mlp_tc_grouped(2, 2, b->bwd.tab, n, b->bwd.map, b->bwd.nctas, b->st);
+  if (e == cudaSuccess) e = launch_grad_adam_grouped(b->adam.tab, b->adam.map, b->adam.nctas, b->st);
+  return e;
+}
+
+// `iters` grouped Adam iterations on the batch stream, as one graph
+cudaError_t batch_train(BatchPlan* b, int iters) {
+  if (iters <= 0) return cudaSuccess;
+  const auto key = std::make_pair(iters, 1);
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < iters && le == cudaSuccess; ++i) le = batch_iter(b);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->st, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return le != cudaSuccess ? le : e;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    it = b->graphs.emplace(key, ex).first;
+  }
+  return cudaGraphLaunch(it->second, b->st);
+}
+
+}  // namespace
+
+extern "C" {
+
 ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
                              hybrid_stats* stats) {
   if (!ctxs || n < 0 || !hp) return ADS_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    ads_status s = hybrid_enqueue(ctxs[i], hp);
-    if (s != ADS_OK) return s;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return ADS_ERR_INVALID_ARG;
+  BatchPlan* b = hp->adam_iters > 0 ? batch_plan_get(ctxs, n) : nullptr;
+  if (b) {
+    // the saturation part of every context on its own stream, then the
+    // grouped training on the batch stream, which the contexts then wait for
+    hybrid_params pre = *hp;
+    pre.adam_iters = 0;
+    for (int i = 0; i < n; ++i) {
+      ads_status s = hybrid_enqueue(ctxs[i], &pre);
+      if (s != ADS_OK) return s;
+      ads_ctx* c = ctxs[i];
+      CK(cudaEventRecord(b->ready[i], c->stream));
+      CK(cudaStreamWaitEvent(b->st, b->ready[i], 0));
+    }
+    const cudaError_t e = batch_train(b, hp->adam_iters);
+    if (e != cudaSuccess) {
+      for (int i = 0; i < n; ++i) fail(ctxs[i], ADS_ERR_CUDA, std::string("batched training: ") + cudaGetErrorString(e));
+      return ADS_ERR_CUDA;
+    }
+    ctxs[0]->nlaunch += (unsigned long long)kBatchLaunches * hp->adam_iters;
+    ads_ctx* c = ctxs[0];
+    CK(cudaEventRecord(b->done, b->st));
+    for (int i = 0; i < n; ++i) {
+      c = ctxs[i];
+      CK(cudaStreamWaitEvent(c->stream, b->done, 0));
+    }
+  } else {
+    for (int i = 0; i < n; ++i) {
+      ads_status s = hybrid_enqueue(ctxs[i], hp);
+      if (s != ADS_OK) return s;
+    }
   }
   if (stats)
     for (int i = 0; i < n; ++i) {

@@ -162,11 +162,11 @@ __device__ __forceinline__ void loss_finalize_dev(const LossFin& lf) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__ alpha,
-                                                    const T* __restrict__ v, const T* __restrict__ f,
-                                                    T h2, T scale, T* __restrict__ out, LossFin lf) {
+__device__ __forceinline__ void stencil_2d_body(int N, const T* __restrict__ alpha, const T* __restrict__ v,
+                                                const T* __restrict__ f, T h2, T scale, T* __restrict__ out,
+                                                const LossFin& lf, int bid) {
   const int m = N - 1, n1 = N + 1;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = bid * blockDim.x + threadIdx.x;
   if (lf.part && t < 32) loss_finalize_dev(lf);
   if (t >= m * m) return;
   const int jj = t / m, ii = t % m;  // interior index
@@ -183,6 +183,18 @@ __global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__
   r *= scale;
   if (f) r += h2 * f[t];
   out[t] = r;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil_2d(int N, const T* __restrict__ alpha,
+                                                    const T* __restrict__ v, const T* __restrict__ f,
+                                                    T h2, T scale, T* __restrict__ out, LossFin lf) {
+  stencil_2d_body<T>(N, alpha, v, f, h2, scale, out, lf, blockIdx.x);
+}
+// grouped (FP32): CTA g.cta[b].y of context g.cta[b].x's launch
+__global__ void __launch_bounds__(256) k_stencil_2d_grp(const StencilArgs* __restrict__ tab, GroupMap g) {
+  const int2 c = g.cta[blockIdx.x];
+  const StencilArgs& a = tab[c.x];
+  stencil_2d_body<float>(a.N, a.alpha, a.v, a.f, a.h2, a.scale, a.out, a.lf, c.y);
 }
 
 // 7-point form: the z differences are weighted by kz
@@ -229,6 +241,13 @@ cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, con
   int m = (N - 1) * (N - 1);
   if (m <= 0) return cudaSuccess;
   k_stencil_2d<T><<<(m + 255) / 256, 256, 0, st>>>(N, alpha, u, f, h2, scale, out, lf ? *lf : none);
+  return cudaGetLastError();
+}
+
+int stencil_blocks(int N) { return ((N - 1) * (N - 1) + 255) / 256; }
+
+cudaError_t launch_stencil_grouped(const StencilArgs* tab, GroupMap g, int nctas, cudaStream_t st) {
+  if (nctas > 0) k_stencil_2d_grp<<<nctas, 256, 0, st>>>(tab, g);
   return cudaGetLastError();
 }
 

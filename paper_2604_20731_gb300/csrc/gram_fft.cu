@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -140,17 +141,17 @@ __device__ __forceinline__ T residual_at(const ResidualIn<T>& q, int N, int jj, 
 // rin.res.  With dotw != nullptr, also a partial of sum dotw * out over the
 // CTA's rows.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads)
-    k_dst_rows(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int P,
-               const Cx<T>* __restrict__ tw, const T* __restrict__ dotw, double* dot_part,
-               ResidualIn<T> rin, int nrows, T scale) {
+__device__ __forceinline__ void dst_rows_body(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int P,
+                                              const Cx<T>* __restrict__ tw, const T* __restrict__ dotw,
+                                              double* dot_part, const ResidualIn<T>& rin, int nrows, T scale,
+                                              int bid) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int L = 1 << lg, m = N - 1;
   Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
   Cx<T>* buf0 = tws + L;                       // [P][L]
   Cx<T>* buf1 = buf0 + (size_t)P * L;          // [P][L]
   __shared__ double red[32];
-  const int r0 = blockIdx.x * 2 * P;
+  const int r0 = bid * 2 * P;
   for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
   const T* src = in;
   int sstride = m;  // row stride of the source rows
@@ -239,22 +240,29 @@ __global__ void __launch_bounds__(kFftThreads)
   }
   if (dotw) {
     const double tot = block_sum(dot.value(), red);
-    if (threadIdx.x == 0) dot_part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) dot_part[bid] = tot;
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    k_dst_rows(const T* __restrict__ in, T* __restrict__ out, int N, int lg, int P,
+               const Cx<T>* __restrict__ tw, const T* __restrict__ dotw, double* dot_part,
+               ResidualIn<T> rin, int nrows, T scale) {
+  dst_rows_body<T>(in, out, N, lg, P, tw, dotw, dot_part, rin, nrows, scale, blockIdx.x);
 }
 
 // For x-modes i in [c0, c0 + 2P): D along y, times scale / (lam_i + lam_j),
 // D along y again; in place.  Columns 2p and 2p + 1 of the CTA share line p.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads)
-    k_gram_cols(T* __restrict__ data, int N, int lg, int P, const Cx<T>* __restrict__ tw,
-                const T* __restrict__ lam, T scale) {
+__device__ __forceinline__ void gram_cols_body(T* __restrict__ data, int N, int lg, int P,
+                                               const Cx<T>* __restrict__ tw, const T* __restrict__ lam, T scale,
+                                               int bid) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int L = 1 << lg, m = N - 1, C = 2 * P;
   Cx<T>* tws = reinterpret_cast<Cx<T>*>(fsm);  // [L]
   Cx<T>* buf0 = tws + L;                       // [P][L]
   Cx<T>* buf1 = buf0 + (size_t)P * L;          // [P][L]
-  const int c0 = blockIdx.x * C;
+  const int c0 = bid * C;
   T* lams = reinterpret_cast<T*>(buf1);  // [m] eigenvalues until the first transform is done
   for (int q = threadIdx.x; q < L; q += blockDim.x) tws[q] = tw[q];
   for (int q = threadIdx.x; q < m; q += blockDim.x) lams[q] = lam[q];
@@ -335,6 +343,41 @@ __global__ void __launch_bounds__(kFftThreads)
     const Cx<T> wk = w[((c >> 1) << lg) + k];
     if (col < m) data[(size_t)(k - 1) * m + col] = (c & 1) ? T(0.5) * wk.re : T(-0.5) * wk.im;
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    k_gram_cols(T* __restrict__ data, int N, int lg, int P, const Cx<T>* __restrict__ tw,
+                const T* __restrict__ lam, T scale) {
+  gram_cols_body<T>(data, N, lg, P, tw, lam, scale, blockIdx.x);
+}
+
+// ---- grouped passes (2D, FP32): one launch per pass over several contexts ----
+struct RowsArgs {
+  const float* in;
+  float* out;
+  int N, lg, P, nrows;
+  const Cx<float>* tw;
+  const float* dotw;
+  double* dot_part;
+  ResidualIn<float> rin;
+  float scale;
+};
+struct ColsArgs {
+  float* data;
+  int N, lg, P;
+  const Cx<float>* tw;
+  const float* lam;
+  float scale;
+};
+__global__ void __launch_bounds__(kFftThreads) k_dst_rows_grp(const RowsArgs* __restrict__ tab, GroupMap g) {
+  const int2 c = g.cta[blockIdx.x];
+  const RowsArgs& a = tab[c.x];
+  dst_rows_body<float>(a.in, a.out, a.N, a.lg, a.P, a.tw, a.dotw, a.dot_part, a.rin, a.nrows, a.scale, c.y);
+}
+__global__ void __launch_bounds__(kFftThreads) k_gram_cols_grp(const ColsArgs* __restrict__ tab, GroupMap g) {
+  const int2 c = g.cta[blockIdx.x];
+  const ColsArgs& a = tab[c.x];
+  gram_cols_body<float>(a.data, a.N, a.lg, a.P, a.tw, a.lam, a.scale, c.y);
 }
 
 // 3D: D along y of columns [c0, c0 + 2P) of plane blockIdx.y of the m x m x m
@@ -737,6 +780,70 @@ cudaError_t launch_gram_fft3d(int pass, int N, const T* res, T* work, T* z, cons
     kc<<<gc, kFftThreads, fft_smem<T>(L, Pc), st>>>(work, N, lg, Pc, twc);
     const T s = h2 * T(4.0 / ((double)N * N));  // h^2 (2 / N)^2
     kr<<<gr, kFftThreads, fft_smem<T>(L, Pr), st>>>(work, z, N, lg, Pr, twc, res, dot_part, rin, m * m, s);
+  }
+  return cudaGetLastError();
+}
+
+struct GramGroup {
+  DevGroup<RowsArgs> rows0, rows2;
+  DevGroup<ColsArgs> cols;
+  size_t smem_rows = 0, smem_cols = 0;
+};
+
+void gram_group_destroy(GramGroup* g) {
+  if (!g) return;
+  dev_group_free(g->rows0);
+  dev_group_free(g->rows2);
+  dev_group_free(g->cols);
+  delete g;
+}
+
+cudaError_t gram_group_create(const GramGroupEntry* e, int n, GramGroup** out) {
+  *out = nullptr;
+  std::vector<RowsArgs> r0(n), r2(n);
+  std::vector<ColsArgs> cc(n);
+  std::vector<int> gr(n), gc(n);
+  size_t sr = 0, sc = 0;
+  for (int k = 0; k < n; ++k) {
+    const int N = e[k].N, lg = log2_exact(N) + 1, L = 2 * N, m = N - 1;
+    if (lg < 4 || lg > 12) return cudaErrorInvalidValue;
+    const Cx<float>* twc = reinterpret_cast<const Cx<float>*>(e[k].tw);
+    const int Pr = lines_per_cta<float>(L, 1), Pc = lines_per_cta<float>(L, 2);
+    gr[k] = (m + 2 * Pr - 1) / (2 * Pr);
+    gc[k] = (m + 2 * Pc - 1) / (2 * Pc);
+    // the arguments launch_gram_fft gives its three passes
+    r0[k] = RowsArgs{e[k].res, e[k].rhat, N, lg, Pr, m, twc, nullptr, nullptr,
+                     ResidualIn<float>{e[k].u, e[k].alpha, e[k].f, e[k].h2, e[k].res}, 1.0f};
+    r2[k] = RowsArgs{e[k].rhat, e[k].z, N, lg, Pr, m, twc, e[k].res, e[k].dot_part,
+                     ResidualIn<float>{nullptr, nullptr, nullptr, 0.0f, nullptr}, 1.0f};
+    cc[k] = ColsArgs{e[k].rhat, N, lg, Pc, twc, e[k].lam, e[k].h2 * float(4.0 / ((double)N * N))};
+    sr = std::max(sr, fft_smem<float>(L, Pr));
+    sc = std::max(sc, fft_smem<float>(L, Pc));
+  }
+  GramGroup* g = new GramGroup();
+  cudaError_t err = dev_group_create(g->rows0, r0.data(), gr.data(), n);
+  if (err == cudaSuccess) err = dev_group_create(g->rows2, r2.data(), gr.data(), n);
+  if (err == cudaSuccess) err = dev_group_create(g->cols, cc.data(), gc.data(), n);
+  if (err != cudaSuccess) {
+    gram_group_destroy(g);
+    return err;
+  }
+  g->smem_rows = sr;
+  g->smem_cols = sc;
+  *out = g;
+  return cudaSuccess;
+}
+
+cudaError_t launch_gram_group(const GramGroup* g, int pass, cudaStream_t st) {
+  if (pass == 1) {
+    auto k = k_gram_cols_grp;
+    smem_optin(k);
+    if (g->cols.nctas > 0) k<<<g->cols.nctas, kFftThreads, g->smem_cols, st>>>(g->cols.tab, g->cols.map);
+  } else {
+    auto k = k_dst_rows_grp;
+    smem_optin(k);
+    const DevGroup<RowsArgs>& d = pass == 0 ? g->rows0 : g->rows2;
+    if (d.nctas > 0) k<<<d.nctas, kFftThreads, g->smem_rows, st>>>(d.tab, d.map);
   }
   return cudaGetLastError();
 }

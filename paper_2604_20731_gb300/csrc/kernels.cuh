@@ -2,9 +2,71 @@
 // translation units.  Every launcher enqueues on the given stream and
 // returns the launch status.
 #pragma once
+#include <cstring>
+#include <vector>
+
 #include "common.cuh"
 
 namespace adsgb {
+
+// ---------------------------------------------------------------------------
+// Grouped launches (the batched form of a training iteration over several
+// contexts of the same shape): one launch runs the CTAs of every context's
+// own launch of a kernel.  CTA b of the grouped grid plays CTA cta[b].y of
+// context cta[b].x's launch, whose grid is grid[cta[b].x]; the contexts'
+// arguments come from a device table.  A context's results are those of its
+// own launch: the same CTAs do the same work.
+// ---------------------------------------------------------------------------
+struct GroupMap {
+  const int2* cta;  // [grouped CTAs] (context, CTA of that context's launch)
+  const int* grid;  // [contexts] CTAs of the context's launch
+};
+
+// a device table of per-context arguments and its CTA map, in one allocation
+template <typename A>
+struct DevGroup {
+  A* tab = nullptr;
+  GroupMap map{nullptr, nullptr};
+  int nctx = 0, nctas = 0;
+  void* mem = nullptr;
+};
+template <typename A>
+cudaError_t dev_group_create(DevGroup<A>& g, const A* args, const int* grids, int n) {
+  int total = 0;
+  for (int k = 0; k < n; ++k) total += grids[k] > 0 ? grids[k] : 0;
+  const size_t tab_b = ((sizeof(A) * (size_t)n + 255) / 256) * 256;
+  const size_t grid_b = ((sizeof(int) * (size_t)n + 255) / 256) * 256;
+  const size_t map_b = sizeof(int2) * (size_t)(total > 0 ? total : 1);
+  std::vector<unsigned char> h(tab_b + grid_b + map_b, 0);
+  std::memcpy(h.data(), args, sizeof(A) * (size_t)n);
+  int* gh = reinterpret_cast<int*>(h.data() + tab_b);
+  int2* mh = reinterpret_cast<int2*>(h.data() + tab_b + grid_b);
+  int b = 0;
+  for (int k = 0; k < n; ++k) {
+    gh[k] = grids[k] > 0 ? grids[k] : 0;
+    for (int c = 0; c < gh[k]; ++c) mh[b++] = make_int2(k, c);
+  }
+  void* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, h.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(mem, h.data(), h.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return e;
+  }
+  unsigned char* d = static_cast<unsigned char*>(mem);
+  g.mem = mem;
+  g.tab = reinterpret_cast<A*>(d);
+  g.map = GroupMap{reinterpret_cast<const int2*>(d + tab_b + grid_b), reinterpret_cast<const int*>(d + tab_b)};
+  g.nctx = n;
+  g.nctas = total;
+  return cudaSuccess;
+}
+template <typename A>
+void dev_group_free(DevGroup<A>& g) {
+  if (g.mem) cudaFree(g.mem);
+  g = DevGroup<A>{};
+}
 
 // ---------------------------------------------------------------------------
 // per-axis tables (identical axes: uniform open knot vector, degree 2)
@@ -139,6 +201,17 @@ struct LossFin {
   int* flags;
   int bump;
 };
+// grouped 2D stencil (FP32): a context's arguments as launch_stencil gives
+// its kernel; stencil_blocks(N) CTAs per context
+struct StencilArgs {
+  int N;
+  const float *alpha, *v, *f;
+  float h2, scale;
+  float* out;
+  LossFin lf;
+};
+int stencil_blocks(int N);
+cudaError_t launch_stencil_grouped(const StencilArgs* tab, GroupMap g, int nctas, cudaStream_t st);
 // RES = A u + h^2 f (scale 1) or g = 2 A z (scale 2, f = nullptr)
 template <typename T>
 cudaError_t launch_stencil(int dim, int N, T kz, const T* alpha, const T* u, const T* f, T h2,
@@ -184,6 +257,17 @@ template <typename T>
 cudaError_t launch_grad_reduce_adam(const T* gpart, int nblk, int nparams, T* grad, T* theta,
                                     T* m, T* v, const double* bc, const double* lr, int do_update,
                                     cudaStream_t st);
+// grouped (FP32): a context's arguments as launch_grad_reduce_adam gives its
+// kernel; grad_adam_blocks(nparams) CTAs per context
+struct AdamArgs {
+  const float* gpart;
+  int nblk, nparams;
+  float *grad, *theta, *m, *v;
+  const double *bc, *lr;
+  int upd;
+};
+int grad_adam_blocks(int nparams);
+cudaError_t launch_grad_adam_grouped(const AdamArgs* tab, GroupMap g, int nctas, cudaStream_t st);
 
 // ---- MLP on tcgen05 tensor cores (BF16 operands, FP32 accumulation, width 64) ----
 struct MlpTcArgs {
@@ -216,6 +300,22 @@ cudaError_t launch_gram_fft(int pass, int N, const T* res, T* work, T* z, const 
                             T h2, double* dot_part, cudaStream_t st, const T* u = nullptr,
                             const T* alpha = nullptr, const T* f = nullptr, T* res_out = nullptr);
 
+// grouped (2D, FP32): each of the three passes over several contexts in one
+// launch, with the arguments launch_gram_fft gives the context's own pass
+// (pass 0 forms the residual from u)
+struct GramGroupEntry {
+  int N;
+  const float *u, *alpha, *f;
+  float h2;
+  float *res, *rhat, *z;
+  const float *tw, *lam;
+  double* dot_part;
+};
+struct GramGroup;
+cudaError_t gram_group_create(const GramGroupEntry* e, int n, GramGroup** out);
+cudaError_t launch_gram_group(const GramGroup* g, int pass, cudaStream_t st);
+void gram_group_destroy(GramGroup* g);
+
 // 3D: pass 0 = the x and y transforms of res into work, pass 2 = the inverse
 // transforms of work into z (times h^2 (2/N)^2) with the loss partials; the
 // z tridiagonal solves in between are the caller's (launch_tridiag_cols)
@@ -243,6 +343,13 @@ size_t mlp_tc_acts_bytes(int npts, int width);
 // backward CTAs (= gradient partial rows): one per SM at most, and at least
 // `min_tiles` 128-point tiles per CTA
 int mlp_tc_bwd_blocks(int npts, int width, int din, int min_tiles = 1);
+// grouped (width 64): a context's table entry (its launch arguments, with
+// the tile range and counter set) and its forward CTA count; which = 0: the
+// weight images (grid: stage blocks x contexts), 1: the forwards, 2: the
+// backwards (g maps each grouped CTA to its context's CTA / partial row)
+MlpTcArgs mlp_tc_group_args(const MlpTcArgs& a, int* fwd_ctas);
+cudaError_t launch_mlp_tc_grouped(int which, int din, const MlpTcArgs* tab, int nctx, GroupMap g, int nctas,
+                                  cudaStream_t st);
 
 // ---- diagnostics: one bounded mbarrier wait run to its limit (or completed,
 // with arrive != 0); bit 8 goes to *word on expiry.  src16: 16 readable,

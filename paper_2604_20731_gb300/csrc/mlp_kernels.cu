@@ -512,12 +512,12 @@ cudaError_t launch_mlp_bwd(const MlpArgs<T>& a, int nblk, cudaStream_t st) {
 // each, for memory-level parallelism) and warp 0 adds the 8 warp sums in a
 // fixed order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) k_grad_adam(const T* __restrict__ gpart, int nblk,
-                                                   int nparams, T* grad, T* theta, T* m, T* v,
-                                                   const double* bc, const double* lr, int upd) {
+__device__ __forceinline__ void grad_adam_body(const T* __restrict__ gpart, int nblk, int nparams, T* grad,
+                                               T* theta, T* m, T* v, const double* bc, const double* lr, int upd,
+                                               int bid) {
   __shared__ T part[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + tx;
+  const int i = bid * 32 + tx;
   T s0 = T(0), s1 = T(0);
   if (i < nparams) {
     int b = ty;
@@ -543,6 +543,25 @@ __global__ void __launch_bounds__(256) k_grad_adam(const T* __restrict__ gpart, 
   const T mh = mi * (T)bc[0];
   const T vh = vi * (T)bc[1];
   theta[i] -= (T)(*lr) * mh / (sqrt(vh) + eps);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_grad_adam(const T* __restrict__ gpart, int nblk,
+                                                   int nparams, T* grad, T* theta, T* m, T* v,
+                                                   const double* bc, const double* lr, int upd) {
+  grad_adam_body<T>(gpart, nblk, nparams, grad, theta, m, v, bc, lr, upd, blockIdx.x);
+}
+// grouped (FP32): CTA g.cta[b].y of context g.cta[b].x's launch
+__global__ void __launch_bounds__(256) k_grad_adam_grp(const AdamArgs* __restrict__ tab, GroupMap g) {
+  const int2 c = g.cta[blockIdx.x];
+  const AdamArgs& a = tab[c.x];
+  grad_adam_body<float>(a.gpart, a.nblk, a.nparams, a.grad, a.theta, a.m, a.v, a.bc, a.lr, a.upd, c.y);
+}
+
+int grad_adam_blocks(int nparams) { return (nparams + 31) / 32; }
+
+cudaError_t launch_grad_adam_grouped(const AdamArgs* tab, GroupMap g, int nctas, cudaStream_t st) {
+  if (nctas > 0) k_grad_adam_grp<<<nctas, 256, 0, st>>>(tab, g);
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -349,11 +349,12 @@ struct TcSmemF {
 // constant vectors (FP32) and the three hidden layers as BF16 K-major tiles
 // (one 16-byte atom of 8 values per thread)
 template <int W, int DIN>
-__global__ void __launch_bounds__(256) k_stage_fwd(const float* __restrict__ th, unsigned char* __restrict__ img) {
+__device__ __forceinline__ void stage_fwd_body(const float* __restrict__ th, unsigned char* __restrict__ img,
+                                               int bid) {
   using L = TcSmemF<W>;
   constexpr int KC = L::KC, RG = (KC / 8) * 128, APR = KC / 8, NA = 3 * W * APR, NV = L::VEC_SZ / 4;
   const int ob1 = W * DIN, o2 = ob1 + W, o5 = o2 + 3 * (W * W + W);
-  const int e = blockIdx.x * 256 + threadIdx.x;
+  const int e = bid * 256 + threadIdx.x;
   if (e == 0) *reinterpret_cast<int*>(img + L::IMG) = 0;  // the forward's tile-group counter
   if (e < NA) {
     const int l = e / (W * APR), rem = e % (W * APR), o = rem / APR, c = (rem % APR) * 8;
@@ -386,6 +387,16 @@ __global__ void __launch_bounds__(256) k_stage_fwd(const float* __restrict__ th,
     }
     reinterpret_cast<float*>(img + L::VEC)[i] = val;
   }
+}
+template <int W, int DIN>
+__global__ void __launch_bounds__(256) k_stage_fwd(const float* __restrict__ th, unsigned char* __restrict__ img) {
+  stage_fwd_body<W, DIN>(th, img, blockIdx.x);
+}
+// grouped: context blockIdx.y of the table
+template <int W, int DIN>
+__global__ void __launch_bounds__(256) k_stage_fwd_grp(const MlpTcArgs* __restrict__ tab) {
+  const MlpTcArgs& a = tab[blockIdx.y];
+  stage_fwd_body<W, DIN>(a.theta, a.wimage, blockIdx.x);
 }
 
 ADS_D void mbar_expect(uint64_t* mbar, uint32_t bytes) {
@@ -482,12 +493,12 @@ ADS_D void st_atom_split2(unsigned char* hi, int rgh, unsigned char* lo, int rgl
 // parts of the output layer (in a fixed order).
 // epilogue threads (TPR per point row) and the issuing warp
 template <int W>
-constexpr int fwd_epi() { return TcSmemF<W>::TPR * kTP; }
+ADS_HD constexpr int fwd_epi() { return TcSmemF<W>::TPR * kTP; }
 template <int W>
-constexpr int fwd_threads() { return fwd_epi<W>() + 32; }
+ADS_HD constexpr int fwd_threads() { return fwd_epi<W>() + 32; }
 
 template <int W, int DIN>
-__global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1) k_mlp_fwd_tc(MlpTcArgs a) {
+__device__ __forceinline__ void fwd_tc_body(const MlpTcArgs& a) {
   using L = TcSmemF<W>;
   constexpr int NS = L::NS;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -733,6 +744,17 @@ __global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1) k_mlp_fwd_t
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NS * W));
 }
+template <int W, int DIN>
+__global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1) k_mlp_fwd_tc(MlpTcArgs a) {
+  fwd_tc_body<W, DIN>(a);
+}
+// grouped: the CTAs of several contexts' forwards in one launch (each
+// context's tile groups come from its own counter)
+template <int W, int DIN>
+__global__ void __launch_bounds__(fwd_threads<W>(), W == 64 ? 2 : 1)
+    k_mlp_fwd_tc_grp(const MlpTcArgs* __restrict__ tab, GroupMap g) {
+  fwd_tc_body<W, DIN>(tab[g.cta[blockIdx.x].x]);
+}
 
 // ---------------------------------------------------------------------------
 // backward, width 64: the products on the tensor cores, one CTA per SM (the
@@ -785,7 +807,7 @@ ADS_D int col_dw(int L) { return L == 5 ? kColW5 : (L == 1 ? kColW1 : kColW4 + (
 
 
 template <int DIN>
-__global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
+__device__ __forceinline__ void bwd_tc_body(const MlpTcArgs& a, int bid, int nblk) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* wt = sm + TcSmemB::W;
   unsigned char* act = sm + TcSmemB::ACT;  // [buffer][a_1..a_4]
@@ -873,9 +895,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
       for (int l = 0; l < 4; ++l) bulk_load(act + b * kSmTile + bwd_layer(l), src + l * kGlLayer, kGlLayer, mb_load + b);
       pend = b;
     };
-    if ((int)blockIdx.x < ntiles) load_tile(0, blockIdx.x);
+    if (bid < ntiles) load_tile(0, bid);
     int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+    for (int tile = bid; tile < ntiles && !*abort_flag; tile += nblk, ++it) {
       const int buf = it & 1;
       const uint32_t actb_s = act_s + buf * kSmTile;
       if (!mbar_wait(mb_load + buf, (lph >> buf) & 1u)) { fail(); break; }
@@ -887,7 +909,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
         if (!mbar_wait(mb_free, ph_free)) { fail(); break; }
         ph_free ^= 1;
       }
-      if (tile + (int)gridDim.x < ntiles) load_tile(1 - buf, tile + gridDim.x);
+      if (tile + nblk < ntiles) load_tile(1 - buf, tile + nblk);
       // x' and Delta_4 written
       if (!mbar_wait(mb_ready4, ph_ready4)) { fail(); break; }
       ph_ready4 ^= 1;
@@ -951,17 +973,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
     int it = 0;
     // dL/du of this row: loaded one tile ahead
     float g_next = 0.0f;
-    if ((int)blockIdx.x < ntiles) {
-      const int i0 = (a.tile0 + (int)blockIdx.x) * kTP + row;
+    if (bid < ntiles) {
+      const int i0 = (a.tile0 + bid) * kTP + row;
       g_next = i0 < a.npts ? a.gu[i0] : 0.0f;
     }
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+    for (int tile = bid; tile < ntiles && !*abort_flag; tile += nblk, ++it) {
       const int buf = it & 1;
       const unsigned char* actb = act + buf * kSmTile;
       const int idx = (a.tile0 + tile) * kTP + row;
       const float g = g_next;
-      if (tile + (int)gridDim.x < ntiles) {
-        const int i1 = idx + (int)gridDim.x * kTP;
+      if (tile + nblk < ntiles) {
+        const int i1 = idx + nblk * kTP;
         g_next = i1 < a.npts ? a.gu[i1] : 0.0f;
       }
       float x[3];
@@ -1045,9 +1067,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   }
   __syncthreads();
   const bool aborted = *abort_flag != 0;
-  const bool had_tiles = (int)blockIdx.x < ntiles;
+  const bool had_tiles = bid < ntiles;
   const bool live = !aborted && had_tiles;
-  float* gacc = a.gpart + (size_t)blockIdx.x * a.nparams;
+  float* gacc = a.gpart + (size_t)bid * a.nparams;
   // output layer: the rows' running sums through shared memory (the
   // activation buffers are idle now), added over the rows in a fixed order
   constexpr int kRedBytes = (kTP * (kW + 1) * 4 + 1023) / 1024 * 1024;
@@ -1090,6 +1112,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
+template <int DIN>
+__global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc(MlpTcArgs a) {
+  bwd_tc_body<DIN>(a, blockIdx.x, gridDim.x);
+}
+// grouped: CTA g.cta[b].y of context g.cta[b].x's backward (its gradient
+// partial row), as in that context's own launch
+template <int DIN>
+__global__ void __launch_bounds__(kBwdThreads) k_mlp_bwd_tc_grp(const MlpTcArgs* __restrict__ tab, GroupMap g) {
+  const int2 m = g.cta[blockIdx.x];
+  bwd_tc_body<DIN>(tab[m.x], m.y, g.grid[m.x]);
+}
+
 
 // backward, ring form (W = 128; it also compiles for W = 64).  TMEM holds
 // the delta product (W columns) and the three hidden dW accumulators (3 x W):
@@ -1421,23 +1455,36 @@ static MlpTcArgs tile_range(MlpTcArgs a) {
 }
 
 template <int W, int DIN>
-static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
+static constexpr int stage_blocks() {
+  using L = TcSmemF<W>;
+  return (3 * W * (L::KC / 8) + L::VEC_SZ / 4 + 255) / 256;
+}
+
+// the forward kernel's grid: at most its residency, at least min_tiles tiles per CTA
+template <int W, int DIN>
+static int fwd_grid(const MlpTcArgs& a) {
   using L = TcSmemF<W>;
   const int ntiles = a.tile_count;
-  if (ntiles <= 0) return cudaSuccess;
-  // the weight image from the current parameters, then the forward
-  constexpr int nstage = 3 * W * (L::KC / 8) + L::VEC_SZ / 4;
-  k_stage_fwd<W, DIN><<<(nstage + 255) / 256, 256, 0, st>>>(a.theta, a.wimage);
-  const size_t smem = L::TOTAL;
+  if (ntiles <= 0) return 0;
   auto k = k_mlp_fwd_tc<W, DIN>;
   smem_optin(k);
-  const int occ = tc_residency(k, smem, L::NS * W, fwd_threads<W>());
+  const int occ = tc_residency(k, L::TOTAL, L::NS * W, fwd_threads<W>());
   int grid = ntiles < occ * sms() ? ntiles : occ * sms();
   const int want = (ntiles + a.min_tiles - 1) / (a.min_tiles > 0 ? a.min_tiles : 1);
   if (want < grid) grid = want > 0 ? want : 1;
+  return grid;
+}
+
+template <int W, int DIN>
+static cudaError_t fwd_tc(const MlpTcArgs& a, cudaStream_t st) {
+  using L = TcSmemF<W>;
+  const int grid = fwd_grid<W, DIN>(a);
+  if (grid <= 0) return cudaSuccess;
+  // the weight image from the current parameters, then the forward
+  k_stage_fwd<W, DIN><<<stage_blocks<W, DIN>(), 256, 0, st>>>(a.theta, a.wimage);
   MlpTcArgs b = a;
   b.wimage_ctr = reinterpret_cast<int*>(a.wimage + L::IMG);
-  k<<<grid, fwd_threads<W>(), smem, st>>>(b);
+  k_mlp_fwd_tc<W, DIN><<<grid, fwd_threads<W>(), L::TOTAL, st>>>(b);
   return cudaGetLastError();
 }
 
@@ -1453,6 +1500,37 @@ cudaError_t launch_mlp_fwd_tc(const MlpTcArgs& a0, cudaStream_t st) {
   if (a.width == 64) return a.din == 2 ? fwd_tc<64, 2>(a, st) : fwd_tc<64, 3>(a, st);
   if (a.width == 128) return a.din == 2 ? fwd_tc<128, 2>(a, st) : fwd_tc<128, 3>(a, st);
   return cudaErrorNotSupported;
+}
+
+// ---- grouped launches (width 64): the tables hold each context's launch
+// arguments as mlp_tc_group_args makes them ----
+MlpTcArgs mlp_tc_group_args(const MlpTcArgs& a0, int* fwd_ctas) {
+  MlpTcArgs a = tile_range(a0);
+  a.wimage_ctr = reinterpret_cast<int*>(a.wimage + TcSmemF<64>::IMG);
+  *fwd_ctas = a.width != 64 ? 0 : (a.din == 2 ? fwd_grid<64, 2>(a) : fwd_grid<64, 3>(a));
+  return a;
+}
+
+cudaError_t launch_mlp_tc_grouped(int which, int din, const MlpTcArgs* tab, int nctx, GroupMap g, int nctas,
+                                  cudaStream_t st) {
+  if (nctx <= 0 || nctas <= 0) return cudaSuccess;
+  if (din != 2 && din != 3) return cudaErrorInvalidValue;
+  if (which == 0) {  // the weight images
+    const dim3 grid(stage_blocks<64, 2>(), nctx);
+    if (din == 2) k_stage_fwd_grp<64, 2><<<grid, 256, 0, st>>>(tab);
+    else k_stage_fwd_grp<64, 3><<<grid, 256, 0, st>>>(tab);
+  } else if (which == 1) {  // the forwards
+    auto k = din == 2 ? k_mlp_fwd_tc_grp<64, 2> : k_mlp_fwd_tc_grp<64, 3>;
+    smem_optin(k);
+    k<<<nctas, fwd_threads<64>(), TcSmemF<64>::TOTAL, st>>>(tab, g);
+  } else if (which == 2) {  // the backwards
+    auto k = din == 2 ? k_mlp_bwd_tc_grp<2> : k_mlp_bwd_tc_grp<3>;
+    smem_optin(k);
+    k<<<nctas, kBwdThreads, TcSmemB::TOTAL, st>>>(tab, g);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 template <int W, int DIN>

@@ -108,3 +108,48 @@ def test_hybrid_step_batch_equals_per_context_steps():
     finally:
         for s in batch + alone:
             s.close()
+
+
+def test_grouped_batch_training_equals_per_context_steps():
+    """Contexts of the grouped shape (2D, width-64 tensor-core network, FFT
+    Gram solve in its three-pass form: the contexts are told they share the
+    GPU) are trained by grouped launches, each training kernel once for the
+    whole batch.  S, P, the parameters, the step statistics and the loss log
+    are bit for bit those of each context's own hybrid step, over mixed sizes
+    and two steps; the launch counts show the grouped path ran."""
+    import torch
+    from paper_2604_20731_gb300.solver import HybridSolver, hybrid_step_batch
+    hp = _hp(HybridSolver, steps_adam=12)
+    theta = scn.make_theta0(2, 64, 4, seed=7)
+    sizes = (32, 128, 64, 256, 64)
+    scs = [scn.make_scenario(2, n, seed=1500 + i, sigma=0.9, rate=0.7 + 0.2 * i) for i, n in enumerate(sizes)]
+    dev = torch.device("cuda", 0)
+
+    def make(sc):
+        s = HybridSolver(sc, width=64, crv_dtype="bf16", ads_dtype="f32", stream=torch.cuda.Stream(device=dev))
+        s.set_concurrency(len(sizes))
+        s.set_theta(theta)
+        s.pretrain(20, 1e-3)
+        return s
+
+    batch = [make(sc) for sc in scs]
+    alone = [make(sc) for sc in scs]
+    try:
+        for step in range(2):
+            l0 = [s.kernel_launches() for s in batch]
+            a0 = [s.kernel_launches() for s in alone]
+            st_b = hybrid_step_batch(batch, hp, stats=True)
+            st_a = [s.hybrid_step(hp) for s in alone]
+            dl = [s.kernel_launches() - v for s, v in zip(batch, l0)]
+            da = [s.kernel_launches() - v for s, v in zip(alone, a0)]
+            # an Adam iteration is 8 kernels per context alone; grouped, 8 for
+            # the whole batch (counted on the first context)
+            assert dl[0] == da[0] and all(d == e - 8 * hp.adam_iters for d, e in zip(dl[1:], da[1:])), (dl, da)
+            for b, a, sb, sa in zip(batch, alone, st_b, st_a):
+                for f in ("S", "P", "THETA", "LOSS_LOG"):
+                    assert np.array_equal(b.get(f), a.get(f)), (step, f)
+                assert sb["dt_used"] == sa["dt_used"] and sb["mass_total"] == sa["mass_total"]
+                assert sb["loss_last"] == sa["loss_last"]
+    finally:
+        for s in batch + alone:
+            s.close()
