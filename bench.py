@@ -54,6 +54,9 @@ def args_parse():
     ap.add_argument("--streams", type=int, default=16)
     ap.add_argument("--assign", default="rr", choices=["rr", "lpt"],
                     help="scenarios to streams: balanced by estimated work, or round robin")
+    ap.add_argument("--groups", type=int, default=2,
+                    help="step the resident scenarios as this many batches (hybrid_step_batch: each "
+                         "training kernel once per batch); 0: each scenario's own step on its stream")
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--arrival-ms", type=float, default=20.0)
     ap.add_argument("--e2e-steps", type=int, default=50)
@@ -88,6 +91,8 @@ def workload_config(a, world, sizes=None):
         "mlp": f"2-{a.width}x4-1", "ads_dtype": "f32", "crvpinn_dtype": "bf16 (tcgen05)",
         "n_sub": a.n_sub, "adam_iters": a.adam_iters, "lr": a.lr, "dt_policy": "cfl 0.1",
         "scenarios_per_gpu": len(sizes), "streams": a.streams, "stream_assignment": a.assign,
+        "batches": (f"{a.groups} (hybrid_step_batch: grouped training launches)" if a.groups > 0
+                    else "none (each scenario's own step graph on its stream)"),
         "parallelism": f"replicas x{world}",
         "rounds_timed": a.steps, "pretrain": a.pretrain,
         "network_start": (f"base network ({a.base_iters} iterations on K = 1, rate 1), output scaled by the "
@@ -754,7 +759,7 @@ def run_ours(a, world, rank, local):
         g.build()
     barrier(world)
     from paper_2604_20731_gb300 import scenario as scn
-    from paper_2604_20731_gb300.solver import HybridSolver, Server
+    from paper_2604_20731_gb300.solver import HybridSolver, Server, hybrid_step_batch
 
     rates = unit_rates() if rank == 0 else None
     if a.only_saturation:
@@ -798,9 +803,24 @@ def run_ours(a, world, rank, local):
             s.pretrain(a.pretrain, a.lr, sync=False)
     torch.cuda.synchronize()
     admission_s = time.perf_counter() - t_adm
+    # batched form: the scenarios on stream k form batch k mod groups, so that
+    # the scenarios sharing a stream share a batch (a stream holding members
+    # of two batches would hold one batch's saturation work behind the
+    # other's training)
+    batches = ([[s for i, s in enumerate(ctxs) if on[i] % a.groups == g] for g in range(a.groups)]
+               if a.groups > 0 else [])
+    batches = [b for b in batches if b]
+
+    def step_all():
+        if batches:
+            for b in batches:
+                hybrid_step_batch(b, hp)
+        else:
+            for s in ctxs:
+                s.hybrid_step(hp, stats=False)
+
     for _ in range(max(a.warmup, 3)):
-        for s in ctxs:
-            s.hybrid_step(hp, stats=False)
+        step_all()
     torch.cuda.synchronize()
     # raw samples to a CSV when ADSGB_CLOCKS_CSV names a file (rank appended)
     csv_path = os.environ.get("ADSGB_CLOCKS_CSV")
@@ -816,8 +836,7 @@ def run_ours(a, world, rank, local):
     for k, st in enumerate(streams):
         ev0[k].record(st)
     for r in range(a.steps):
-        for s in ctxs:
-            s.hybrid_step(hp, stats=False)
+        step_all()
         for k, st in enumerate(streams):
             round_ev[r][k].record(st)
     for k, st in enumerate(streams):

@@ -291,9 +291,18 @@ MlpArgs<TC> mlp_args(ads_ctx* c, bool store) {
 // this many 128-point tiles.  Each CTA pays a fixed cost (weight staging,
 // TMEM set-up, the gradient partial); with other work to fill the SMs, fewer
 // and longer CTAs raise the total throughput.  On a 64-scenario mix over 16
-// streams, 32/64/96/128 tiles per backward CTA gave 244/252/251/230 steps/s
-// and 8 tiles per forward CTA no gain over 4.
-constexpr int kFwdTilesShared = 4, kBwdTilesShared = 64;
+// streams, 16/32/64/128 tiles per backward CTA gave 244/258/265/237 steps/s
+// (each scenario's own step) and 257/267/275/277 (two batches of grouped
+// launches); 2/4/8 tiles per forward CTA gave 262/265/268 and 271/275/277,
+// but 8 slows a context training while few others run (a server admitting
+// scenarios one by one), so the forward keeps 4.
+#ifndef ADS_FWD_TILES_SHARED
+#define ADS_FWD_TILES_SHARED 4
+#endif
+#ifndef ADS_BWD_TILES_SHARED
+#define ADS_BWD_TILES_SHARED 64
+#endif
+constexpr int kFwdTilesShared = ADS_FWD_TILES_SHARED, kBwdTilesShared = ADS_BWD_TILES_SHARED;
 
 MlpTcArgs mlp_tc_args(ads_ctx* c, bool store) {
   MlpTcArgs a{};
