@@ -296,9 +296,26 @@ ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stat
 /* hybrid_step_batch (no counterpart in the paper: it steps one scenario at a
  * time): hybrid_step for n independent contexts, every step enqueued before
  * any statistics are read, so that contexts on different streams overlap on
- * the device.  stats: NULL or n entries.  Errors: ADS_ERR_INVALID_ARG (ctxs or
- * hp NULL, n < 0), else the first failing context's status (the contexts
- * after it are not stepped, or not read). */
+ * the device.
+ * Grouped training: when n >= 2 distinct contexts share the grouped shape
+ * (2D; width-64 tensor-core network with FP32 network arithmetic and stored
+ * activations; N a power of two, so the Gram solve takes the FFT route, in
+ * its three-pass form, i.e. not the one-cluster form that a context alone at
+ * N <= 128 takes: ads_set_concurrency > 1), each kernel of an Adam
+ * iteration runs once for the whole batch.  It is a grouped launch over
+ * per-context argument tables, on a stream of the batch's own, after each
+ * context's saturation part (on the context's stream), which then waits for
+ * it.  Every context's results are bit-identical to its own hybrid_step's.
+ * The batch's tables, stream and graphs are made on the first call with this
+ * list of contexts and kept (up to 16 lists; made again when a member's
+ * concurrency changes; released when a member is destroyed).  They come from
+ * cudaMalloc, not from a context's allocator.  Other batches are stepped
+ * context by context.  The grouped Adam iterations count in the first
+ * context's kernel launches (ads_kernel_launches).
+ * stats: NULL or n entries.  Errors: ADS_ERR_INVALID_ARG (ctxs or hp NULL, a
+ * NULL context, n < 0), else the first failing context's status (the
+ * contexts after it are not stepped, or not read); a failed grouped launch
+ * marks every context of the batch ADS_ERR_CUDA. */
 ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
                              hybrid_stats* stats);
 
