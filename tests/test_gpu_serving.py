@@ -153,3 +153,67 @@ def test_grouped_batch_training_equals_per_context_steps():
     finally:
         for s in batch + alone:
             s.close()
+
+
+def test_grouped_batch_plans_follow_their_members():
+    """A batch with a member outside the grouped shape is stepped context by
+    context; a batch plan goes with a destroyed member, and is made again when
+    a member's launch shape changes; the results stay those of the contexts'
+    own steps throughout."""
+    import torch
+    from paper_2604_20731_gb300.solver import HybridSolver, hybrid_step_batch
+    hp = _hp(HybridSolver, steps_adam=6)
+    theta = scn.make_theta0(2, 64, 4, seed=7)
+    dev = torch.device("cuda", 0)
+
+    def make(n, seed, conc=4):
+        s = HybridSolver(scn.make_scenario(2, n, seed=seed), width=64, crv_dtype="bf16", ads_dtype="f32",
+                         stream=torch.cuda.Stream(device=dev))
+        s.set_concurrency(conc)
+        s.set_theta(theta)
+        s.pretrain(10, 1e-3)
+        return s
+
+    def launches(ss):
+        return [s.kernel_launches() for s in ss]
+
+    def same(b, a):
+        for f in ("S", "P", "THETA"):
+            assert np.array_equal(b.get(f), a.get(f)), f
+
+    A, B, C, D = make(64, 1), make(32, 2), make(128, 3), make(24, 4)  # D: N = 24, no FFT Gram solve
+    A2, B2, C2, D2 = make(64, 1), make(32, 2), make(128, 3), make(24, 4)
+    try:
+        # a member outside the shape: every context steps on its own (8 kernels per iteration each)
+        l0, m0 = launches([A, B, C, D]), launches([A2, B2, C2, D2])
+        hybrid_step_batch([A, B, C, D], hp)
+        for s in (A2, B2, C2, D2):
+            s.hybrid_step(hp, stats=False)
+        assert [x - y for x, y in zip(launches([A, B, C, D]), l0)] == \
+               [x - y for x, y in zip(launches([A2, B2, C2, D2]), m0)]
+        for b, a in zip((A, B, C, D), (A2, B2, C2, D2)):
+            same(b, a)
+        # grouped, then a member destroyed: the remaining pair gets a plan of its own
+        l0 = launches([A, B, C])
+        hybrid_step_batch([A, B, C], hp)
+        for s in (A2, B2, C2):
+            s.hybrid_step(hp, stats=False)
+        assert launches([A, B, C])[1] - l0[1] < 8 * hp.adam_iters  # B's training ran grouped
+        B.close()
+        B2.close()
+        l0 = launches([A, C])
+        hybrid_step_batch([A, C], hp)
+        for s in (A2, C2):
+            s.hybrid_step(hp, stats=False)
+        assert launches([A, C])[1] - l0[1] < 8 * hp.adam_iters
+        # a member reshaped (another concurrency): the plan is made again
+        for s in (C, C2):
+            s.set_concurrency(2)
+        hybrid_step_batch([A, C], hp)
+        for s in (A2, C2):
+            s.hybrid_step(hp, stats=False)
+        for b, a in zip((A, C, D), (A2, C2, D2)):
+            same(b, a)
+    finally:
+        for s in (A, B, C, D, A2, B2, C2, D2):
+            s.close()
