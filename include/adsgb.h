@@ -318,6 +318,19 @@ ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stat
  * marks every context of the batch ADS_ERR_CUDA. */
 ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* hp,
                              hybrid_stats* stats);
+/* hybrid_step_batch_profile (diagnostic): for n >= 2 contexts of the grouped
+ * shape (see hybrid_step_batch), one grouped Adam iteration with event records
+ * between its 8 kernels is captured into a graph and replayed `iters` times on
+ * the batch's stream (each replay waited for, bounded), after the contexts'
+ * streams have been waited for.  The iterations train the networks as
+ * hybrid_step_batch's do.  ms_out[8] receives the average durations of: the
+ * weight images, the forward, the Gram rows pass with the residual, the Gram
+ * columns pass, the Gram rows pass with the loss partials, the adjoint with
+ * the loss, the backward, the gradient sum with Adam.
+ * Errors: ADS_ERR_INVALID_ARG (ctxs or ms_out NULL, a NULL context, n < 2,
+ * iters < 1), ADS_ERR_UNSUPPORTED (not of the grouped shape), ADS_ERR_TIMEOUT,
+ * ADS_ERR_CUDA (then set on every context of the batch). */
+ads_status hybrid_step_batch_profile(ads_ctx* const* ctxs, int n, int iters, double* ms_out);
 
 /* ---- serving: continuous batching of many scenarios (the paper steps one
  * scenario at a time) ----------------------------------------------------------

@@ -110,6 +110,7 @@ SIGNATURES = {
     "hybrid_step": (C.c_int, [_P, C.POINTER(hybrid_params), C.POINTER(hybrid_stats)]),
     "hybrid_step_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(hybrid_params),
                                     C.POINTER(hybrid_stats)]),
+    "hybrid_step_batch_profile": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, _D]),
     "ads_get": (C.c_int, [_P, C.c_int, _D, C.c_size_t]),
     "ads_field_count": (C.c_int, [_P, C.c_int, C.POINTER(C.c_size_t)]),
     "ads_device_ptr": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_size_t),

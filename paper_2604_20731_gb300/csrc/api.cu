@@ -1628,14 +1628,74 @@ BatchPlan* batch_plan_get(ads_ctx* const* ctxs, int n) {
   return b;
 }
 
-cudaError_t batch_iter(const BatchPlan* b) {
+// one grouped Adam iteration; with ev (9 events), an event record before
+// each of its 8 kernels and after the last (a profile)
+cudaError_t batch_iter(const BatchPlan* b, cudaEvent_t* ev = nullptr) {
   const int n = (int)b->ctxs.size();
-  cudaError_t e = launch_mlp_tc_grouped(0, 2, b->fwd.tab, n, b->fwd.map, n, b->st);
+  int k = 0;
+  auto mark = [&]() {
+    return ev ? cudaEventRecordWithFlags(ev[k++], b->st, cudaEventRecordExternal) : cudaSuccess;
+  };
+  cudaError_t e = mark();
+  if (e == cudaSuccess) e = launch_mlp_tc_grouped(0, 2, b->fwd.tab, n, b->fwd.map, n, b->st);
+  if (e == cudaSuccess) e = mark();
   if (e == cudaSuccess) e = launch_mlp_tc_grouped(1, 2, b->fwd.tab, n, b->fwd.map, b->fwd.nctas, b->st);
-  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) e = launch_gram_group(b->gram, pass, b->st);
+  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) {
+    e = mark();
+    if (e == cudaSuccess) e = launch_gram_group(b->gram, pass, b->st);
+  }
+  if (e == cudaSuccess) e = mark();
   if (e == cudaSuccess) e = launch_stencil_grouped(b->sten.tab, b->sten.map, b->sten.nctas, b->st);
+  if (e == cudaSuccess) e = mark();
   if (e == cudaSuccess) e = launch_mlp_tc_grouped(2, 2, b->bwd.tab, n, b->bwd.map, b->bwd.nctas, b->st);
+  if (e == cudaSuccess) e = mark();
   if (e == cudaSuccess) e = launch_grad_adam_grouped(b->adam.tab, b->adam.map, b->adam.nctas, b->st);
+  if (e == cudaSuccess) e = mark();
+  return e;
+}
+
+cudaError_t batch_stream_wait(cudaStream_t st, double seconds) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e != cudaErrorNotReady) return e;
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds)
+      return cudaErrorNotReady;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+// one grouped iteration with event records between its kernels, captured
+// into a graph and replayed `reps` times; ms[8]: average durations
+cudaError_t batch_profile(BatchPlan* b, int reps, double* ms) {
+  cudaEvent_t ev[9] = {};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  for (int k = 0; k < 8; ++k) ms[k] = 0.0;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t le = batch_iter(b, ev);
+    e = cudaStreamEndCapture(b->st, &g);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  for (int it = 0; it < reps && e == cudaSuccess; ++it) {
+    e = cudaGraphLaunch(ex, b->st);
+    if (e == cudaSuccess) e = batch_stream_wait(b->st, kDefaultTimeout);
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+      float f = 0.f;
+      e = cudaEventElapsedTime(&f, ev[k], ev[k + 1]);
+      ms[k] += f;
+    }
+  }
+  cudaGetLastError();
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  for (int k = 0; k < 9; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 8; ++k) ms[k] /= (reps > 0 ? reps : 1);
   return e;
 }
 
@@ -1710,6 +1770,23 @@ ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* h
       ads_status s = hybrid_stats_read(ctxs[i], &stats[i]);
       if (s != ADS_OK) return s;
     }
+  return ADS_OK;
+}
+
+ads_status hybrid_step_batch_profile(ads_ctx* const* ctxs, int n, int iters, double* ms_out) {
+  if (!ctxs || n < 2 || iters < 1 || !ms_out) return ADS_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return ADS_ERR_INVALID_ARG;
+  BatchPlan* b = batch_plan_get(ctxs, n);
+  if (!b) return ADS_ERR_UNSUPPORTED;
+  for (int i = 0; i < n; ++i) CA(wait(ctxs[i], kDefaultTimeout));
+  const cudaError_t e = batch_profile(b, iters, ms_out);
+  if (e == cudaErrorNotReady) return ADS_ERR_TIMEOUT;
+  if (e != cudaSuccess) {
+    for (int i = 0; i < n; ++i) fail(ctxs[i], ADS_ERR_CUDA, std::string("batch profile: ") + cudaGetErrorString(e));
+    return ADS_ERR_CUDA;
+  }
+  ctxs[0]->nlaunch += (unsigned long long)kBatchLaunches * iters;
   return ADS_OK;
 }
 

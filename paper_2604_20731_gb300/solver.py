@@ -248,6 +248,22 @@ def hybrid_step_batch(solvers, hp: L.hybrid_params, stats: bool = False):
     return None
 
 
+BATCH_PROFILE_KERNELS = ("stage_fwd", "mlp_fwd", "gram_rows_residual", "gram_cols", "gram_rows_loss",
+                         "adjoint_loss_finalize", "mlp_bwd", "grad_adam")
+
+
+def hybrid_step_batch_profile(solvers, iters: int = 20) -> dict:
+    """Average ms of each grouped kernel of one batched Adam iteration
+    (hybrid_step_batch_profile); the solvers must share the grouped shape."""
+    lib = L.load()
+    arr = (C.c_void_p * len(solvers))(*[s.ctx for s in solvers])
+    ms = (C.c_double * 8)()
+    rc = lib.hybrid_step_batch_profile(arr, len(solvers), int(iters), ms)
+    if rc != L.ADS_OK:
+        raise L.AdsError(rc, "hybrid_step_batch_profile")
+    return dict(zip(BATCH_PROFILE_KERNELS, list(ms)))
+
+
 class Server:
     """Continuous-batching server (ads_server_* in the C ABI): scenarios are
     submitted as they arrive, admitted by device-memory budget, stepped in

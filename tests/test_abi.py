@@ -356,6 +356,8 @@ lib.ads_server_destroy(None)
 hp = _lib.hybrid_params(10, 1.0, 1, 0.1, 0.05, 100, 1e-3)
 arr = (C.c_void_p * 1)()
 srv["batch_null"] = lib.hybrid_step_batch(None, 0, C.byref(hp), None)
+srv["batch_profile_null"] = lib.hybrid_step_batch_profile(None, 2, 1, None)
+srv["batch_profile_one"] = lib.hybrid_step_batch_profile((C.c_void_p * 1)(None), 1, 1, (C.c_double * 8)())
 srv["batch_negative"] = lib.hybrid_step_batch(arr, -1, C.byref(hp), None)
 # allocation-free step: argument checks before any CUDA call
 from paper_2604_20731_gb300 import scenario as scn
