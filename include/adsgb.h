@@ -265,6 +265,19 @@ ads_status crvpinn_update_coefficients(ads_ctx* ctx);
  * synchronisation; the gradient is kept on the device (ADS_FIELD_GRAD).
  * Errors: ADS_ERR_STATE (no network), ADS_ERR_NONFINITE (non-finite loss). */
 ads_status crvpinn_loss_grad(ads_ctx* ctx, double* loss_out);
+/* crvpinn_vjp: the network's vector-Jacobian product at the current
+ * parameters, g_theta = (du/dtheta)^T g_u, with u the network's values on
+ * the interior collocation nodes (Eq. 21, the boundary is 0) in the layout of
+ * ADS_FIELD_U.  It chains a gradient with respect to the network pressure
+ * (e.g. from ads_degree_project_vjp and ads_degree_step_vjp, the inverse
+ * problem of Sec. 9) back to the parameters, through the hand-written forward
+ * and backward kernels.  g_u: (N-1)^dim host doubles (copied in; they replace
+ * dLOSS/du in ADS_FIELD_GU); g_theta: nparams host doubles (written, in the
+ * crvpinn_set_theta layout; ADS_FIELD_GRAD holds them too).  In the network's
+ * precision.  Waits for the stream (bounded).
+ * Errors: ADS_ERR_INVALID_ARG (NULL pointers), ADS_ERR_STATE (no network),
+ * ADS_ERR_UNSUPPORTED (activation recomputation, act_chunks > 1). */
+ads_status crvpinn_vjp(ads_ctx* ctx, const double* g_u, double* g_theta);
 
 /* crvpinn_pretrain: coefficients from the current saturation, reset Adam,
  * then `iters` Adam iterations at learning rate lr (Sec. 6 step 2).
@@ -510,6 +523,11 @@ ads_status ads_degree_mass(ads_degree_plan* plan, const double* d_S, double* mas
  *   +inf).  Waits (bounded: ADS_ERR_TIMEOUT) for `stream` and writes *dt;
  *   ADS_ERR_NONFINITE for a non-finite maximum. */
 ads_status ads_degree_project(ads_degree_plan* plan, const double* d_nodal, double* d_out, void* stream);
+/* ads_degree_project_vjp: the adjoint of ads_degree_project.  For
+ * J = g . P with P the projection of the nodal values, d_gnodal ((n+1)^2,
+ * device) = dJ/d(nodal) = A^T M^-1 g, A the assembly of int I_h u v; d_g
+ * ((n+p)^2, device), distinct from d_gnodal.  Enqueued on `stream`. */
+ads_status ads_degree_project_vjp(ads_degree_plan* plan, const double* d_g, double* d_gnodal, void* stream);
 ads_status ads_degree_cfl_dt(ads_degree_plan* plan, const double* d_K, const double* d_phi, const double* d_P,
                              double cfl, double src_frac, double dt_cap, double* dt, void* stream);
 /* Vector-Jacobian product of ads_degree_step (a building block of gradients

@@ -104,6 +104,7 @@ SIGNATURES = {
     "crvpinn_num_params": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "crvpinn_update_coefficients": (C.c_int, [_P]),
     "crvpinn_loss_grad": (C.c_int, [_P, _D]),
+    "crvpinn_vjp": (C.c_int, [_P, _D, _D]),
     "crvpinn_pretrain": (C.c_int, [_P, C.c_int, C.c_double, _D]),
     "crvpinn_pressure_update": (C.c_int, [_P, C.c_int, C.c_double, _D]),
     "ads_project_pressure": (C.c_int, [_P]),
@@ -125,6 +126,7 @@ SIGNATURES = {
     "ads_degree_step": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, _P]),
     "ads_degree_mass": (C.c_int, [_P, _P, _D, _P]),
     "ads_degree_project": (C.c_int, [_P, _P, _P, _P]),
+    "ads_degree_project_vjp": (C.c_int, [_P, _P, _P, _P]),
     "ads_degree_cfl_dt": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _D, _P]),
     "ads_degree_step_vjp": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, _P, _P, _D, _P]),
     "ads_degree_coeffs": (C.c_int, [_P]),

@@ -728,6 +728,21 @@ template <typename TC, typename TA>
 struct EvalF {
   static ads_status run(ads_ctx* c) { return enq_train_iter<TC>(c, 0); }
 };
+// the network's vector-Jacobian product: forward (activations stored),
+// backward from the dL/du buffer, and the fixed-order sum of the partial
+// rows into grad (no update)
+template <typename TC, typename TA>
+struct VjpF {
+  static ads_status run(ads_ctx* c) {
+    CK(launch_fwd<TC>(c, true));
+    c->nlaunch += c->use_tc ? kMlpTcFwdLaunches : 1;
+    CK(launch_bwd<TC>(c));
+    CK(launch_grad_reduce_adam<TC>((const TC*)c->gpart, c->nbwd, c->nparams, (TC*)c->grad, (TC*)c->theta,
+                                   (TC*)c->am, (TC*)c->av, c->bc, c->lr, 0, c->stream));
+    c->nlaunch += 2;
+    return ADS_OK;
+  }
+};
 template <typename TC, typename TA>
 struct TrainRun {
   static ads_status go(ads_ctx* c, int iters) { return train<TC, TA>(c, iters, 1); }
@@ -1369,6 +1384,16 @@ ads_status crvpinn_loss_grad(ads_ctx* c, double* loss_out) {
   return ADS_OK;
 }
 
+ads_status crvpinn_vjp(ads_ctx* c, const double* g_u, double* g_theta) {
+  ads_status s = check(c);
+  if (s != ADS_OK) return s;
+  if (!c->has_crv) return ADS_ERR_STATE;
+  if (!g_u || !g_theta) return ADS_ERR_INVALID_ARG;
+  if (c->use_tc && c->chunks > 1) return ADS_ERR_UNSUPPORTED;
+  CA(upload(c, c->gu, c->tc, g_u, (size_t)c->M));
+  CA(dispatch2<VjpF>(c));
+  return ads_get(c, ADS_FIELD_GRAD, g_theta, (size_t)c->nparams);
+}
 
 static ads_status train_dispatch(ads_ctx* c, int iters) {
   if (c->tc == ADS_F64 && c->ta == ADS_F64) return TrainRun<double, double>::go(c, iters);

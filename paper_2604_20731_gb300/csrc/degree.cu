@@ -305,6 +305,65 @@ __global__ void __launch_bounds__(128) k_deg_proj(DegArgs a, const double* __res
     for (int c = 0; c < Q; ++c) o[b * Q + c] = r[b][c];
 }
 
+// Adjoint of the projection: with mu = M^-1 g (M symmetric), element e's part
+// of dJ/d(nodal) for J = g . M^-1 F(nodal): at each Gauss point the test sum
+// sum_bc mu_bc B_b(y) B_c(x), weighted and spread to the element's four
+// nodes by the bilinear hats (the transpose of the interpolation above);
+// part[e][0..3] = the terms of nodes (ex, ey), (ex + 1, ey), (ex, ey + 1),
+// (ex + 1, ey + 1)
+template <int P>
+__global__ void __launch_bounds__(128) k_deg_proj_vjp(DegArgs a, const double* __restrict__ mu,
+                                                     double* __restrict__ part) {
+  constexpr int Q = P + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n * a.n) return;
+  const int ex = e % a.n, ey = e / a.n, nb = a.nb;
+  const double* Bx = a.B + (size_t)ex * Q * Q;
+  const double* By = a.B + (size_t)ey * Q * Q;
+  double m[Q][Q];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int c = 0; c < Q; ++c) m[b][c] = mu[(size_t)(ey + b) * nb + ex + c];
+  double g00 = 0.0, g01 = 0.0, g10 = 0.0, g11 = 0.0;
+  for (int qy = 0; qy < Q; ++qy) {
+    const double eta = a.xi[qy];
+    for (int qx = 0; qx < Q; ++qx) {
+      const double xi = a.xi[qx];
+      double t = 0.0;
+#pragma unroll
+      for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int c = 0; c < Q; ++c) t += m[b][c] * By[b * Q + qy] * Bx[c * Q + qx];
+      const double c0 = a.wq[qx] * a.wq[qy] * a.h2 * t;
+      g00 += c0 * (1.0 - eta) * (1.0 - xi);
+      g01 += c0 * (1.0 - eta) * xi;
+      g10 += c0 * eta * (1.0 - xi);
+      g11 += c0 * eta * xi;
+    }
+  }
+  double* o = part + (size_t)e * 4;
+  o[0] = g00;
+  o[1] = g01;
+  o[2] = g10;
+  o[3] = g11;
+}
+
+// node (i, j) adds the terms of its (up to four) elements in a fixed order
+__global__ void __launch_bounds__(256) k_deg_node_gather(const double* __restrict__ part, int n,
+                                                         double* __restrict__ out) {
+  const int n1 = n + 1;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n1 * n1) return;
+  const int i = d % n1, j = d / n1;
+  double v = 0.0;
+  if (i < n && j < n) v += part[((size_t)j * n + i) * 4 + 0];
+  if (i > 0 && j < n) v += part[((size_t)j * n + i - 1) * 4 + 1];
+  if (i < n && j > 0) v += part[((size_t)(j - 1) * n + i) * 4 + 2];
+  if (i > 0 && j > 0) v += part[((size_t)(j - 1) * n + i - 1) * 4 + 3];
+  out[d] = v;
+}
+
 // per element, the largest Darcy speed |K (grad p + s rho_g g e_y)| /
 // (mu_g phi) and the largest injection rate q_inj / phi over its Gauss points
 // (the step-size rule's two maxima), to out[e] and out[n^2 + e]
@@ -783,6 +842,29 @@ extern "C" ads_status ads_degree_project(ads_degree_plan* pl, const double* d_no
   }
   deg_gather(pl, pl->part, d_out, st);
   deg_mass_solve(pl, d_out, st);
+  return cudaGetLastError() == cudaSuccess ? ADS_OK : ADS_ERR_CUDA;
+}
+
+extern "C" ads_status ads_degree_project_vjp(ads_degree_plan* pl, const double* d_g, double* d_gnodal,
+                                             void* stream) {
+  using namespace adsgb;
+  if (!pl || !d_g || !d_gnodal || d_g == d_gnodal) return ADS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nb = pl->nb, n = pl->n, ne = n * n;
+  if (cudaMemcpyAsync(pl->work, d_g, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return ADS_ERR_CUDA;
+  }
+  deg_mass_solve(pl, pl->work, st);
+  const int g = (ne + 127) / 128;
+  switch (pl->p) {
+    case 2: k_deg_proj_vjp<2><<<g, 128, 0, st>>>(pl->args, pl->work, pl->part); break;
+    case 3: k_deg_proj_vjp<3><<<g, 128, 0, st>>>(pl->args, pl->work, pl->part); break;
+    default: k_deg_proj_vjp<4><<<g, 128, 0, st>>>(pl->args, pl->work, pl->part); break;
+  }
+  const int n1 = n + 1;
+  k_deg_node_gather<<<(n1 * n1 + 255) / 256, 256, 0, st>>>(pl->part, n, d_gnodal);
   return cudaGetLastError() == cudaSuccess ? ADS_OK : ADS_ERR_CUDA;
 }
 

@@ -210,6 +210,25 @@ class HybridSolver:
         """Read a checkpoint written by save() from a context of the same shape."""
         self._check(self.lib.ads_load(self.ctx, str(path).encode()), "ads_load")
 
+    def vjp(self, g_u) -> np.ndarray:
+        """(du/dtheta)^T g_u for the network's values u on the interior
+        collocation nodes (crvpinn_vjp); returns nparams doubles."""
+        g = np.ascontiguousarray(np.asarray(g_u, dtype=np.float64).ravel())
+        if g.size != self.count("U"):
+            raise ValueError("one value per interior collocation node")
+        out = np.empty(self.nparams)
+        self._check(self.lib.crvpinn_vjp(self.ctx, _dptr(g), _dptr(out)), "crvpinn_vjp")
+        return out
+
+    def network_nodal(self) -> np.ndarray:
+        """The network's values on all (N+1)^dim nodes at the current
+        parameters (boundary 0), [y][x] (or [z][y][x])."""
+        self.vjp(np.zeros(self.count("U")))  # runs the forward (the cotangent is zero)
+        N, d = self.n, self.dim
+        out = np.zeros((N + 1,) * d)
+        out[(slice(1, N),) * d] = self.get("U").reshape((N - 1,) * d)
+        return out
+
     def set_concurrency(self, contexts: int):
         """Expect `contexts` contexts on the GPU at once (launch shapes for
         throughput rather than this context's latency)."""
@@ -246,6 +265,31 @@ def hybrid_step_batch(solvers, hp: L.hybrid_params, stats: bool = False):
         return [dict(dt_used=s.dt_used, loss_last=s.loss_last, mass_err=s.mass_err,
                      mass_total=s.mass_total) for s in out]
     return None
+
+
+def pressure_network_gradient(solver, plan, K, phi, S0, dt: float, n_steps: int, lam):
+    """Gradient of J = lam . S_n with respect to the network's parameters, for
+    S_n the state after n_steps explicit saturation steps (plan, degree p)
+    from S0 with the network pressure: the network's nodal values (solver,
+    2D, N = n) projected into the plan's splines (Sec. 6, step 4).  The
+    chain runs backward through the steps (steps_with_gradient), the
+    projection (project_vjp) and the network (crvpinn_vjp), every part a
+    hand-written adjoint.  K, phi (nullable), S0, lam: CUDA float64 tensors
+    as for steps_with_gradient.  Returns S_n, dJ/dS0 (tensors), dJ/dtheta
+    (nparams, numpy) and dJ/d(rate, centre x, centre y) per source."""
+    import torch
+    if solver.dim != 2 or solver.n != plan.n:
+        raise ValueError("the network's collocation grid must be the plan's 2D mesh")
+    dev = S0.device
+    stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    nodal = torch.from_numpy(solver.network_nodal()).to(dev)
+    P = torch.empty_like(S0)
+    plan.project(nodal, P, stream)
+    Sn, gS0, gP, gsrc = plan.steps_with_gradient(K, phi, S0, P, dt, n_steps, lam)
+    gnod = torch.empty_like(nodal)
+    plan.project_vjp(gP, gnod, stream)
+    g_u = gnod[1:-1, 1:-1].cpu().numpy()
+    return Sn, gS0, solver.vjp(g_u), gsrc
 
 
 BATCH_PROFILE_KERNELS = ("stage_fwd", "mlp_fwd", "gram_rows_residual", "gram_cols", "gram_rows_loss",
@@ -377,6 +421,11 @@ class DegreePlan:
     def project(self, nodal, out, stream=None):
         self._check(self.lib.ads_degree_project(self.plan, self._p(nodal), self._p(out), stream),
                     "ads_degree_project")
+
+    def project_vjp(self, g, out, stream=None):
+        """The adjoint of project: dJ/d(nodal) into out ((n+1)^2) for J = g . P."""
+        self._check(self.lib.ads_degree_project_vjp(self.plan, self._p(g), self._p(out), stream),
+                    "ads_degree_project_vjp")
 
     def cfl_dt(self, K, phi, P, cfl=0.1, src_frac=0.05, dt_cap=float("inf"), stream=None):
         dt = C.c_double()

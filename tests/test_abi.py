@@ -398,6 +398,7 @@ dg["mass_null_plan"] = [lib.ads_degree_mass(None, None, C.byref(C.c_double()), N
 dg["vjp_null_plan"] = [lib.ads_degree_step_vjp(None, None, None, None, None, 1e-3, None, None, None, None, None), True]
 dg["coeffs_null"] = [lib.ads_degree_coeffs(None), True]
 dg["project_null_plan"] = [lib.ads_degree_project(None, None, None, None), True]
+dg["project_vjp_null_plan"] = [lib.ads_degree_project_vjp(None, None, None, None), True]
 dg["cfl_null_plan"] = [lib.ads_degree_cfl_dt(None, None, None, None, 0.1, 0.05, 1.0, C.byref(C.c_double()), None), True]
 lib.ads_degree_plan_destroy(None)
 # image maps: refusals before any CUDA call (the pointers are never dereferenced)

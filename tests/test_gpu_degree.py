@@ -327,3 +327,91 @@ def test_gradient_through_several_steps_for_well_placement():
                 return out
             fd = rich(lambda e: J(S0, P, moved(e)))
             assert gsrc[k, j] == pytest.approx(fd, rel=1e-6, abs=1e-9), (k, field)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_projection_adjoint_dot_product(p):
+    """ads_degree_project_vjp is the adjoint of ads_degree_project (itself
+    pinned to the oracle's projection): g . project(u) = project_vjp(g) . u
+    for random u and g, on a ragged mesh."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g_
+    g_.build()
+    from paper_2604_20731_gb300.solver import DegreePlan
+    n = 37
+    sc, _, _ = _case(n, p, seed=300 + p)
+    rng = np.random.default_rng(301 + p)
+    u = rng.normal(size=(n + 1, n + 1))
+    g = rng.normal(size=(n + p, n + p))
+    plan = DegreePlan(sc, p)
+    try:
+        dev = torch.device("cuda", 0)
+        ud, gd = torch.from_numpy(u).to(dev), torch.from_numpy(g).to(dev)
+        P, gu = torch.empty_like(gd), torch.empty_like(ud)
+        plan.project(ud, P)
+        plan.project_vjp(gd, gu)
+        torch.cuda.synchronize()
+        lhs = float(np.sum(g * P.cpu().numpy()))
+        rhs = float(np.sum(gu.cpu().numpy() * u))
+    finally:
+        plan.close()
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_gradient_with_respect_to_the_network_parameters(p):
+    """pressure_network_gradient: J = lambda . S_n after two steps whose
+    pressure is the FP64 network's nodal values projected into the degree-p
+    splines.  The gradient with respect to theta (through the steps, the
+    projection and the network's hand-written backward) against
+    Richardson-extrapolated central differences of the oracle's J(theta):
+    its network, projection and steps."""
+    import dataclasses
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g_
+    g_.build()
+    from oracle.hybrid import HybridOracle
+    from paper_2604_20731_gb300 import scenario as scn
+    from paper_2604_20731_gb300.solver import DegreePlan, HybridSolver, pressure_network_gradient
+    n, steps, dt, width = 8, 2, 2e-3, 64
+    sc = scn.make_scenario(2, n, seed=410 + p, S0="random", grav=0.3)
+    theta = scn.make_theta0(2, width, 4, seed=411 + p)
+    rng = np.random.default_rng(412 + p)
+    nb = n + p
+    S0 = rng.uniform(0.2, 0.8, size=(nb, nb))
+    lam = rng.normal(size=(nb, nb))
+    solver = HybridSolver(sc, width=width, crv_dtype="f64", ads_dtype="f64")
+    scp = dataclasses.replace(sc)
+    scp.p = p
+    plan = DegreePlan(scp, p)
+    try:
+        solver.set_theta(theta)
+        dev = torch.device("cuda", 0)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev)
+        Sn, gS0, gth, gsrc = pressure_network_gradient(solver, plan, t(sc.K), None, t(S0), dt, steps, t(lam))
+        torch.cuda.synchronize()
+        Sn = Sn.cpu().numpy()
+    finally:
+        plan.close()
+        solver.close()
+    ho = HybridOracle(scp, width)
+
+    def run(th):
+        P = ho.project(th)
+        S = S0
+        for _ in range(steps):
+            S = ho.ads.step(S, P, dt)
+        return S
+
+    ref = run(theta)
+    assert np.abs(Sn - ref).max() <= 1e-12 * np.abs(ref).max()
+    J = lambda th: float(np.sum(lam * run(th)))
+    eps = 1e-4
+    for k in range(3):
+        d = rng.normal(size=theta.shape)
+        d /= np.linalg.norm(d)
+        f = lambda e: J(theta + e * d)
+        d1 = (f(eps) - f(-eps)) / (2 * eps)
+        d2 = (f(eps / 2) - f(-eps / 2)) / eps
+        fd = (4 * d2 - d1) / 3
+        assert float(np.dot(gth, d)) == pytest.approx(fd, rel=1e-6, abs=1e-10), k
