@@ -322,8 +322,10 @@ ads_status hybrid_step(ads_ctx* ctx, const hybrid_params* hp, hybrid_stats* stat
  * The batch's tables, stream and graphs are made on the first call with this
  * list of contexts and kept (up to 16 lists; made again when a member's
  * concurrency changes; released when a member is destroyed).  They come from
- * cudaMalloc, not from a context's allocator.  Other batches are stepped
- * context by context.  The grouped Adam iterations count in the first
+ * cudaMalloc, not from a context's allocator.  The list of plans is shared
+ * by the process and locked while a call enqueues a batch's work, so host
+ * threads that step batches of their own contexts may call at once.  Other
+ * batches are stepped context by context.  The grouped Adam iterations count in the first
  * context's kernel launches (ads_kernel_launches).
  * stats: NULL or n entries.  Errors: ADS_ERR_INVALID_ARG (ctxs or hp NULL, a
  * NULL context, n < 0), else the first failing context's status (the

@@ -1618,8 +1618,9 @@ cudaError_t batch_plan_make(ads_ctx* const* ctxs, int n, BatchPlan** out) {
 
 // the batch's plan (made on first use); nullptr: the contexts are not all of
 // the grouped shape, or a plan could not be made (the caller steps them one
-// by one)
-BatchPlan* batch_plan_get(ads_ctx* const* ctxs, int n) {
+// by one).  The caller holds g_batch_mu for as long as it uses the plan, so
+// that no other thread evicts it meanwhile.
+BatchPlan* batch_plan_get_locked(ads_ctx* const* ctxs, int n) {
   if (n < 2) return nullptr;
   for (int i = 0; i < n; ++i) {
     if (!batch_groupable(ctxs[i])) return nullptr;
@@ -1627,7 +1628,6 @@ BatchPlan* batch_plan_get(ads_ctx* const* ctxs, int n) {
       if (ctxs[j] == ctxs[i]) return nullptr;
   }
   const std::vector<int> shape = batch_shape(ctxs, n);
-  std::lock_guard<std::mutex> lk(g_batch_mu);
   for (size_t i = 0; i < g_batches.size(); ++i) {
     BatchPlan* b = g_batches[i];
     if ((int)b->ctxs.size() != n || !std::equal(b->ctxs.begin(), b->ctxs.end(), ctxs)) continue;
@@ -1759,7 +1759,9 @@ ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* h
   if (!ctxs || n < 0 || !hp) return ADS_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!ctxs[i]) return ADS_ERR_INVALID_ARG;
-  BatchPlan* b = hp->adam_iters > 0 ? batch_plan_get(ctxs, n) : nullptr;
+  std::unique_lock<std::mutex> lk(g_batch_mu);
+  BatchPlan* b = hp->adam_iters > 0 ? batch_plan_get_locked(ctxs, n) : nullptr;
+  if (!b) lk.unlock();
   if (b) {
     // the saturation part of every context on its own stream, then the
     // grouped training on the batch stream, which the contexts then wait for
@@ -1784,6 +1786,7 @@ ads_status hybrid_step_batch(ads_ctx* const* ctxs, int n, const hybrid_params* h
       c = ctxs[i];
       CK(cudaStreamWaitEvent(c->stream, b->done, 0));
     }
+    lk.unlock();  // the plan's work is enqueued; another thread may now evict it
   } else {
     for (int i = 0; i < n; ++i) {
       ads_status s = hybrid_enqueue(ctxs[i], hp);
@@ -1802,7 +1805,8 @@ ads_status hybrid_step_batch_profile(ads_ctx* const* ctxs, int n, int iters, dou
   if (!ctxs || n < 2 || iters < 1 || !ms_out) return ADS_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!ctxs[i]) return ADS_ERR_INVALID_ARG;
-  BatchPlan* b = batch_plan_get(ctxs, n);
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchPlan* b = batch_plan_get_locked(ctxs, n);
   if (!b) return ADS_ERR_UNSUPPORTED;
   for (int i = 0; i < n; ++i) CA(wait(ctxs[i], kDefaultTimeout));
   const cudaError_t e = batch_profile(b, iters, ms_out);
