@@ -217,3 +217,57 @@ def test_grouped_batch_plans_follow_their_members():
     finally:
         for s in (A, B, C, D, A2, B2, C2, D2):
             s.close()
+
+
+def test_grouped_batches_from_two_threads_with_plan_eviction():
+    """Two host threads step batches of their own contexts at once, through
+    24 distinct lists (more than the 16 kept plans, so plans are evicted
+    while the other thread steps); every context ends bit-identical to a twin
+    stepped alone the same number of times."""
+    import itertools
+    import threading
+    import torch
+    from paper_2604_20731_gb300.solver import HybridSolver, hybrid_step_batch
+    hp = HybridSolver.hybrid_params(n_sub=1, dt=1.0, dt_policy=1, cfl=0.1, src_frac=0.05, adam_iters=2, lr=1e-3)
+    theta = scn.make_theta0(2, 64, 4, seed=7)
+    dev = torch.device("cuda", 0)
+
+    def make(n, seed):
+        s = HybridSolver(scn.make_scenario(2, n, seed=seed), width=64, crv_dtype="bf16", ads_dtype="f32",
+                         stream=torch.cuda.Stream(device=dev))
+        s.set_concurrency(4)
+        s.set_theta(theta)
+        return s
+
+    sizes = (32, 64, 32, 64, 32, 64)
+    ctx = [make(n, 1700 + i) for i, n in enumerate(sizes)]
+    twin = [make(n, 1700 + i) for i, n in enumerate(sizes)]
+    groups = [ctx[:3], ctx[3:]]
+    lists = [[list(p) for p in itertools.permutations(g, 2)] + [list(p) for p in itertools.permutations(g, 3)]
+             for g in groups]
+    errors = []
+
+    def work(k):
+        try:
+            for lst in lists[k]:
+                hybrid_step_batch(lst, hp)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    try:
+        th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errors, errors
+        for s, t in zip(ctx, twin):
+            steps = sum(lst.count(s) for ls in lists for lst in ls)
+            assert steps == 10
+            for _ in range(steps):
+                t.hybrid_step(hp, stats=False)
+            for f in ("S", "P", "THETA"):
+                assert np.array_equal(s.get(f), t.get(f)), f
+    finally:
+        for s in ctx + twin:
+            s.close()
