@@ -293,9 +293,9 @@ MlpArgs<TC> mlp_args(ads_ctx* c, bool store) {
 // and longer CTAs raise the total throughput.  On a 64-scenario mix over 16
 // streams, 16/32/64/128 tiles per backward CTA gave 244/258/265/237 steps/s
 // (each scenario's own step) and 257/267/275/277 (two batches of grouped
-// launches); 2/4/8 tiles per forward CTA gave 262/265/268 and 271/275/277,
-// but 8 slows a context training while few others run (a server admitting
-// scenarios one by one), so the forward keeps 4.
+// launches); 2/4/8 tiles per forward CTA gave 262/265/268 and 271/275/277.
+// The forward keeps 4: the 1 % that 8 gains is within the spread of the
+// same run on different GPUs.
 #ifndef ADS_FWD_TILES_SHARED
 #define ADS_FWD_TILES_SHARED 4
 #endif
