@@ -398,6 +398,17 @@ def stream_assignment(sizes, nstreams, policy="lpt"):
     return out
 
 
+def batches_by_stream(items, on, groups):
+    """The batched form's batches: the scenarios on stream k form batch
+    k mod groups, so that the scenarios sharing a stream share a batch (a
+    stream holding members of two batches would hold one batch's saturation
+    work behind the other's training).  groups <= 0: no batches."""
+    if groups <= 0:
+        return []
+    out = [[x for i, x in enumerate(items) if on[i] % groups == g] for g in range(groups)]
+    return [b for b in out if b]
+
+
 def plain_method_c1(a, scn, HybridSolver, device):
     """Configuration 1: the plain method of Sec. 7 on 32 x 32 elements in FP64.
     Each step is the Galerkin pressure, solved directly on the GPU, followed by
@@ -803,13 +814,7 @@ def run_ours(a, world, rank, local):
             s.pretrain(a.pretrain, a.lr, sync=False)
     torch.cuda.synchronize()
     admission_s = time.perf_counter() - t_adm
-    # batched form: the scenarios on stream k form batch k mod groups, so that
-    # the scenarios sharing a stream share a batch (a stream holding members
-    # of two batches would hold one batch's saturation work behind the
-    # other's training)
-    batches = ([[s for i, s in enumerate(ctxs) if on[i] % a.groups == g] for g in range(a.groups)]
-               if a.groups > 0 else [])
-    batches = [b for b in batches if b]
+    batches = batches_by_stream(ctxs, on, a.groups)
 
     def step_all():
         if batches:

@@ -43,3 +43,19 @@ def test_oracle_workers_are_single_threaded_and_time_a_step():
     for t_sat, t_iter, threads in res:
         assert t_sat > 0 and t_iter > 0
         assert threads in (None, 1)
+
+
+@pytest.mark.parametrize("groups,nstreams", [(2, 16), (3, 16), (4, 16), (2, 5), (1, 16), (8, 4)])
+def test_batches_follow_the_streams(groups, nstreams):
+    """Every scenario is in exactly one batch, and the scenarios sharing a
+    stream share a batch, for any batch count against any stream count."""
+    sizes = [128, 256, 512] * 21 + [128]
+    on = bench.stream_assignment(sizes, nstreams, "rr")
+    items = list(range(len(sizes)))
+    batches = bench.batches_by_stream(items, on, groups)
+    assert sorted(x for b in batches for x in b) == items
+    assert all(b for b in batches) and len(batches) <= groups
+    batch_of = {x: k for k, b in enumerate(batches) for x in b}
+    for st in set(on):
+        assert len({batch_of[i] for i in items if on[i] == st}) == 1
+    assert bench.batches_by_stream(items, on, 0) == []
